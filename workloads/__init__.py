@@ -1,0 +1,138 @@
+"""Seeded synthetic inputs shared by the oracle checks, the tests and the bench.
+
+This module holds no arithmetic of the control method: it only draws and
+packages inputs (gate poses, latent codes, MLP weights, start states and the
+controller parameters of each workload).  It imports neither the oracle nor
+the CUDA package, and neither of them imports it.
+
+Workloads (stand-ins for the paper's simulated race tracks, whose layouts,
+depth images and trained networks are not available):
+
+* ``hover_gate``   K=256,  H=20, one gate at the origin facing +x, analytic
+                   frame SDF, start hovering 5 m in front of it (10 steps).
+* ``two_gate_mlp`` K=4096, H=50, two gates at seeded poses 6-10 m apart with
+                   yaw in [-60, 60] deg and pitch in [-30, 30] deg, Gate-SDF MLP
+                   with Xavier-uniform weights and N(0, 1) latents (100 steps).
+* ``four_gate_mlp`` K=16384, H=64, four such gates.
+"""
+
+import math
+
+import numpy as np
+
+LATENT_DIM = 64
+HIDDEN = 128
+N_HIDDEN_LAYERS = 4
+
+BASE_PARAMS = dict(
+    dt=0.02, mass=0.8, gravity=9.81,
+    thrust_min=0.0, thrust_max=30.0, rate_max=8.0,
+    sigma_thrust=2.0, sigma_rate=1.5, lam=0.1,
+    w_col=100.0, d_safe=0.3, w_u=1e-3,
+    seed=0, drone_id=0,
+)
+
+
+def params(K, H, **over):
+    d = dict(BASE_PARAMS)
+    d.update(K=K, H=H)
+    d.update(over)
+    return d
+
+
+def yaw_pitch_quat(yaw, pitch):
+    """Unit quaternion (w, x, y, z) of a yaw about world z followed by a pitch about the
+    yawed y axis, written out in closed form from the half-angle sines and cosines."""
+    cy, sy = math.cos(0.5 * yaw), math.sin(0.5 * yaw)
+    cp, sp = math.cos(0.5 * pitch), math.sin(0.5 * pitch)
+    return [cy * cp, -sy * sp, cy * sp, sy * cp]
+
+
+def gate_track(n_gates, seed=3, start=(0.0, 0.0, 0.0), spacing=(6.0, 10.0),
+               max_yaw_deg=60.0, max_pitch_deg=30.0):
+    """Gate poses [n, 7] = (t, q): gate i at t_{i-1} + d_i e_x with d_i ~ U(spacing)."""
+    rng = np.random.default_rng(seed)
+    poses = np.zeros((n_gates, 7), dtype=np.float32)
+    t = np.array(start, dtype=np.float64)
+    for i in range(n_gates):
+        t = t + np.array([rng.uniform(*spacing), 0.0, 0.0])
+        yaw = math.radians(rng.uniform(-max_yaw_deg, max_yaw_deg))
+        pitch = math.radians(rng.uniform(-max_pitch_deg, max_pitch_deg))
+        poses[i, 0:3] = t
+        poses[i, 3:7] = yaw_pitch_quat(yaw, pitch)
+    return poses
+
+
+def origin_gate():
+    """One gate at the origin, unrotated (normal +x)."""
+    return np.array([[0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0]], dtype=np.float32)
+
+
+def latents(n_gates, dim=LATENT_DIM, seed=2):
+    return np.random.default_rng(seed).standard_normal((n_gates, dim)).astype(np.float32)
+
+
+def xavier_mlp(seed=1, in_dim=3 + LATENT_DIM, hidden=HIDDEN, n_hidden=N_HIDDEN_LAYERS):
+    """Xavier-uniform weights U(-a, a), a = sqrt(6 / (fan_in + fan_out)); zero biases.
+
+    Returns [(W [out, in], b [out])] for in -> hidden x n_hidden -> 1, float32.
+    """
+    rng = np.random.default_rng(seed)
+    dims = [in_dim] + [hidden] * n_hidden + [1]
+    layers = []
+    for fi, fo in zip(dims[:-1], dims[1:]):
+        a = math.sqrt(6.0 / (fi + fo))
+        W = rng.uniform(-a, a, size=(fo, fi)).astype(np.float32)
+        layers.append((W, np.zeros(fo, dtype=np.float32)))
+    return layers
+
+
+def hover_state(position):
+    s = np.zeros(13, dtype=np.float32)
+    s[0:3] = position
+    s[6] = 1.0
+    return s
+
+
+def hover_nominal(H, mass=BASE_PARAMS["mass"], gravity=BASE_PARAMS["gravity"]):
+    U = np.zeros((H, 4), dtype=np.float32)
+    U[:, 0] = np.float32(mass * gravity)
+    return U
+
+
+def perturbed_states(n, seed, base):
+    """n start states near ``base``: position jitter, velocity, a small random attitude."""
+    rng = np.random.default_rng(seed)
+    out = np.repeat(np.asarray(base, dtype=np.float32)[None, :], n, axis=0)
+    out[:, 0:3] += rng.normal(0.0, 0.5, (n, 3)).astype(np.float32)
+    out[:, 3:6] = rng.normal(0.0, 1.0, (n, 3)).astype(np.float32)
+    q = rng.normal(0.0, 1.0, (n, 4))
+    q[:, 0] += 6.0
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    out[:, 6:10] = q.astype(np.float32)
+    out[:, 10:13] = rng.normal(0.0, 0.5, (n, 3)).astype(np.float32)
+    return out
+
+
+def hover_gate():
+    """K=256, H=20, one gate at the origin facing +x, analytic SDF, start 5 m in front."""
+    prm = params(256, 20)
+    return dict(name="hover_gate_K256_H20_G1_analytic", params=prm, poses=origin_gate(),
+                latents=np.zeros((1, LATENT_DIM), dtype=np.float32), layers=None,
+                state=hover_state([-5.0, 0.0, 0.0]), nominal=hover_nominal(20), steps=10)
+
+
+def two_gate_mlp():
+    """K=4096, H=50, two seeded gates, Gate-SDF MLP (Xavier seed 1, latents seed 2)."""
+    prm = params(4096, 50)
+    return dict(name="two_gate_mlp_K4096_H50_G2", params=prm, poses=gate_track(2),
+                latents=latents(2), layers=xavier_mlp(1),
+                state=hover_state([0.0, 0.0, 0.0]), nominal=hover_nominal(50), steps=100)
+
+
+def four_gate_mlp():
+    """K=16384, H=64, four seeded gates, Gate-SDF MLP."""
+    prm = params(16384, 64)
+    return dict(name="four_gate_mlp_K16384_H64_G4", params=prm, poses=gate_track(4),
+                latents=latents(4), layers=xavier_mlp(1),
+                state=hover_state([0.0, 0.0, 0.0]), nominal=hover_nominal(64), steps=3)
