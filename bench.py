@@ -1,0 +1,358 @@
+"""Throughput / latency benchmark of the MPPI + Gate-SDF control step on GB300.
+
+One step = one whole control step of the hot path on one batch of synthetic
+input: Philox noise -> RK4 rollouts -> Gate-SDF MLP at every rollout state ->
+costs, softmax weights and weighted update -> plant update and warm-start
+shift.  Workload: K = 4096 rollouts, H = 50 horizon steps, two gates at
+seeded poses (6-10 m apart, yaw +-60 deg, pitch +-30 deg), Gate-SDF MLP
+67 -> 4 x 128 -> 1 with Xavier-uniform weights (seed 1) and N(0, 1) latents
+(seed 2).  Headline path: hidden GEMMs in BF16 on tcgen05 (FP32 accumulate);
+the plain FP32 path is timed on the same workload for the speedup.
+
+Metric: rollout-steps/s = K * H / step time, with per-step p50/p99 latency.
+Timing: CUDA events on the library's stream around every step, L2 flushed
+(256 MiB write) between timed steps outside the events, inputs and the warm
+start resident on the device (closed loop on the device).  e2e: the same
+metric through the synchronous host-buffer call (state in, controls out).
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (there is no other reference implementation).
+
+Multi-GPU: replicas only (each rank runs its own drone's controller); value
+is the sum of all ranks' rollout-steps over the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MPPI rollout-steps/s at K=4096,H=50; p50/p99 solve latency vs plain FP32"
+UNIT = "rollout-steps/s"
+L2_FLUSH_BYTES = 256 << 20
+TENSOR_FLOPS_PER_QUERY = 3 * 2 * 128 * 128           # layers 2..4 on tcgen05
+FMA_FLOPS_PER_QUERY = 2 * 3 * 128 + 2 * 128           # layer 1 (point part) + output dot
+# dram__bytes_read.sum + dram__bytes_write.sum of one sdf_mlp_bf16 launch (ncu), or None
+SDF_BF16_DRAM_BYTES = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp32-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    import workloads as W
+    return W.two_gate_mlp()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ our arm
+def make_ctx(B, wl, mode, stream, drone_id):
+    prm = wl["params"]
+    cfg = B.mppi_config_default()
+    for key in ("K", "H", "dt", "mass", "gravity", "thrust_min", "thrust_max", "rate_max", "sigma_thrust",
+                "sigma_rate", "w_col", "d_safe", "w_u", "seed"):
+        setattr(cfg, key, prm[key])
+    cfg.lam = prm["lam"]
+    cfg.drone_id = drone_id
+    cfg.max_gates = wl["poses"].shape[0]
+    cfg.sdf_mode = {"bf16": B.MPPI_SDF_MLP_BF16, "fp32": B.MPPI_SDF_MLP_FP32}[mode]
+    ctx = B.mppi_create(cfg, stream)
+    keep = []
+    for Wm, b in wl["layers"]:
+        keep += [np.ascontiguousarray(Wm, np.float32), np.ascontiguousarray(b, np.float32)]
+    B.mppi_set_sdf_weights(ctx, keep)
+    B.mppi_set_gates(ctx, wl["poses"].shape[0], np.ascontiguousarray(wl["poses"]), np.ascontiguousarray(wl["latents"]))
+    return ctx
+
+
+def device_loop(torch, B, ctx, wl, steps, warmup, flush, dev):
+    """Warm-up then `steps` timed device-resident steps; returns per-step ms."""
+    K, H = wl["params"]["K"], wl["params"]["H"]
+    U = torch.zeros(H, 4, device=dev)
+    w = torch.zeros(K, device=dev)
+    J = torch.zeros(K, device=dev)
+    st = torch.from_numpy(wl["state"]).to(dev)
+    nom = torch.from_numpy(wl["nominal"]).to(dev)
+    B.mppi_step_async(ctx, st, None, None, nom, U, w, J)       # start of the closed loop
+    for _ in range(warmup):
+        B.mppi_step_async(ctx, None, None, None, None, U, w, J)
+    B.mppi_sync(ctx)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record()
+        B.mppi_step_async(ctx, None, None, None, None, U, w, J)
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    B.mppi_sync(ctx)
+    return np.array([a.elapsed_time(b) for a, b in ev])
+
+
+def kernel_times(torch, B, ctx, steps, flush, wl, dev):
+    """Per-kernel CUDA-event times (ms) averaged over `steps` separate timed steps."""
+    K, H = wl["params"]["K"], wl["params"]["H"]
+    U = torch.zeros(H, 4, device=dev)
+    B.mppi_set_timing(ctx, True)
+    acc = {}
+    for _ in range(steps):
+        flush.zero_()
+        B.mppi_step_async(ctx, None, None, None, None, U, None, None)
+        for name, ms in B.mppi_get_kernel_times(ctx):
+            acc.setdefault(name, []).append(ms)
+    B.mppi_set_timing(ctx, False)
+    B.mppi_sync(ctx)
+    return {k: float(np.mean(v)) for k, v in acc.items()}
+
+
+def e2e_loop(torch, B, ctx, wl, steps, flush):
+    """Synchronous host-buffer calls: state in (H2D), new controls out (D2H), per-step wall ms."""
+    K, H = wl["params"]["K"], wl["params"]["H"]
+    state = torch.from_numpy(wl["state"].copy()).pin_memory().numpy()
+    U = torch.zeros(H, 4).pin_memory().numpy()
+    B.mppi_step(ctx, state, None, None, None, U)
+    out = []
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.mppi_step(ctx, state, None, None, None, U)
+        out.append((time.perf_counter() - t0) * 1e3)
+    return np.array(out), 13 * 4, H * 4 * 4 + 4
+
+
+def cpu_baseline(wl, seconds):
+    """The FP64 oracle, as it stands, on the host cores: whole control steps until `seconds` pass."""
+    from oracle import mppi as O
+    prm = O.Params(**wl["params"])
+    n, t0 = 0, time.perf_counter()
+    while True:
+        O.mppi_step(wl["state"], wl["nominal"], wl["poses"], prm, n, wl["latents"], wl["layers"])
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": prm.K * prm.H * n / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+            "sample": f"{n} full oracle control steps (K={prm.K}, H={prm.H}, G=2, FP64 numpy) in {dt:.1f} s"}
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [d.get("num_threads", 1) for d in threadpool_info() if d.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    env = os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS")
+    return int(env) if env else (os.cpu_count() or 1)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2603_07199_gb300 import binding as B
+
+    wl = workload()
+    K, H, G = wl["params"]["K"], wl["params"]["H"], wl["poses"].shape[0]
+    stream = torch.cuda.current_stream().cuda_stream
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    ctx = make_ctx(B, wl, "bf16", stream, drone_id=rank)
+    per_launch = B.mppi_kernels_per_step(ctx)
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t_wall = time.perf_counter()
+    ms = device_loop(torch, B, ctx, wl, args.steps, max(3, args.warmup), flush, dev)
+    t_wall = time.perf_counter() - t_wall
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    total = float(ms.sum())
+    if world > 1:
+        t = torch.tensor([total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    value = world * K * H * args.steps / (total * 1e-3)
+
+    ktimes = kernel_times(torch, B, ctx, 20, flush, wl, dev)
+    e2e_ms, h2d, d2h = e2e_loop(torch, B, ctx, wl, args.e2e_steps, flush)
+    B.mppi_destroy(ctx)
+
+    ctx32 = make_ctx(B, wl, "fp32", stream, drone_id=rank)
+    ms32 = device_loop(torch, B, ctx32, wl, args.fp32_steps, 3, flush, dev)
+    kt32 = kernel_times(torch, B, ctx32, 5, flush, wl, dev)
+    B.mppi_destroy(ctx32)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    import json as _json
+    peaks = {}
+    try:
+        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    peak_tf = peaks.get("bf16_tflops")
+    peak_src = "measured burst bf16 (MEASURED_PEAKS.json)" if peak_tf else "fallback 1900 TFLOP/s"
+    peak_tf = peak_tf or 1900.0
+    t_sdf = ktimes.get("sdf_mlp_bf16")
+    tensor_flops = TENSOR_FLOPS_PER_QUERY * K * H * G
+    achieved = tensor_flops / (t_sdf * 1e-3) / 1e12 if t_sdf else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": wl["name"], "K": K, "H": H, "gates": G, "sdf": "Gate-SDF MLP, BF16 tcgen05",
+                   "dynamics": "fp32 RK4", "l2": "flushed (256 MiB write) between timed steps",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
+                       "mean": float(ms.mean()), "min": float(ms.min())},
+        "fp32": {"value": K * H / (ms32.mean() * 1e-3), "p50_ms": float(np.percentile(ms32, 50)),
+                 "p99_ms": float(np.percentile(ms32, 99)), "steps": args.fp32_steps, "kernel_ms": kt32},
+        "speedup_vs_fp32": float(ms32.mean() / ms.mean()),
+        "p99_speedup_vs_fp32": float(np.percentile(ms32, 99) / np.percentile(ms, 99)),
+        "sdf_queries_per_s": K * H * G / (t_sdf * 1e-3) if t_sdf else None,
+        "kernel_ms": ktimes,
+        "roofline": {"kernel": "sdf_mlp_bf16", "bound": "tensor", "achieved": achieved, "peak": peak_tf,
+                     "unit": "TFLOP/s", "frac": achieved / peak_tf if achieved else None,
+                     "traffic": SDF_BF16_DRAM_BYTES, "peak_source": peak_src,
+                     "algorithmic_flops_per_launch": tensor_flops},
+        "e2e": {"value": K * H / (e2e_ms.mean() * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "p50_ms": float(np.percentile(e2e_ms, 50)),
+                "p99_ms": float(np.percentile(e2e_ms, 99))},
+        "gpu_launches": per_launch * args.steps,
+        "clocks": clocks,
+        "wall_s_timed_region": t_wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference arm: the oracle
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import mppi as O
+    wl = workload()
+    K_SAMPLE = 512
+    prm = O.Params(**dict(wl["params"], K=K_SAMPLE))
+    H = prm.H
+    for i in range(max(0, args.warmup)):
+        O.mppi_step(wl["state"], wl["nominal"], wl["poses"], prm, i, wl["latents"], wl["layers"])
+    t = []
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        O.mppi_step(wl["state"], wl["nominal"], wl["poses"], prm, args.warmup + i, wl["latents"], wl["layers"])
+        t.append(time.perf_counter() - t0)
+    t = np.array(t)
+    value = K_SAMPLE * H / t.mean()
+    sample = (f"each step: one FP64 oracle control step on a {K_SAMPLE}-rollout sample of the K=4096, H=50, "
+              f"G=2 workload (rollout-steps/s scales with the sample)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(t.mean() * 1e3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "K": 4096, "H": H, "gates": 2, "sdf": "Gate-SDF MLP, FP64 numpy"},
+            "latency_ms": {"p50": float(np.percentile(t, 50) * 1e3), "p99": float(np.percentile(t, 99) * 1e3)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -1,0 +1,234 @@
+/*
+ * mppi.h -- C ABI of the GB300 MPPI + Gate-SDF control-step library.
+ *
+ * One control step of a sampling-based MPPI controller whose rollouts are
+ * scored by a gate-shaped signed distance field (Vision-Guided MPPI with a
+ * neural Gate-SDF, Sec. IV, Eq. 5-10):
+ *
+ *   (a) sample K Gaussian control-noise sequences over a horizon of H steps
+ *       from a counter-based Philox4x32-10 generator (Sec. IV-A, Eq. 5);
+ *   (b) roll out K quadrotor trajectories with RK4 (Sec. IV-A);
+ *   (c) query the gate SDF -- the exact rectangular-frame SDF or the Gate-SDF
+ *       MLP g_phi(z, p) (Sec. III-B, Fig. 2) -- at every rollout state and
+ *       fold the safety, progress and control costs (Eq. 8-10);
+ *   (d) turn the costs into softmax weights and the weighted control update
+ *       (Eq. 5), apply the first action and shift the sequence (receding
+ *       horizon, Sec. IV-A).
+ *
+ * Conventions for every call:
+ *   - All floats are IEEE binary32, row-major, SI units.  A state is 13
+ *     floats [p(3), v(3), q(4) = (w, x, y, z), w_body(3)]; a control is 4
+ *     floats [collective thrust T (N), body rates wx, wy, wz (rad/s)]; a gate
+ *     pose is 7 floats [t(3), q(4) (w, x, y, z) rotating gate -> world]; the
+ *     gate plane is x = 0 of the gate frame and its normal is R(q) e_x.
+ *   - The caller owns every pointer it passes.  The library never keeps a
+ *     caller pointer after the call returns.
+ *   - Return value: MPPI_OK (0) or a negative MPPI_E_* code; the message is
+ *     available from mppi_last_error().  The library never aborts or traps.
+ *   - A context is bound to the CUDA device that was current at
+ *     mppi_create() and to one CUDA stream.  Calls on one context must not
+ *     overlap (not thread-safe per context); distinct contexts are
+ *     independent.
+ */
+#ifndef MPPI_GB300_H
+#define MPPI_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define MPPI_OK             0
+#define MPPI_E_INVALID     -1   /* bad argument, NaN/Inf input, size out of range */
+#define MPPI_E_OOM         -2   /* device or pinned host allocation failed */
+#define MPPI_E_CUDA        -3   /* a CUDA runtime call failed (message has the CUDA error) */
+#define MPPI_E_TIMEOUT     -4   /* a device-side bounded wait gave up; the context stays usable */
+#define MPPI_E_NOT_READY   -5   /* weights or gates required by the SDF mode are not set */
+#define MPPI_E_UNSUPPORTED -6   /* the device is not an sm_103 GPU or the mode is not built */
+
+/* ---- SDF evaluation modes (mppi_config.sdf_mode) ---- */
+#define MPPI_SDF_ANALYTIC  0    /* exact signed distance to the rectangular gate frame */
+#define MPPI_SDF_MLP_FP32  1    /* Gate-SDF MLP, FP32 on the CUDA cores (plain FP32 path) */
+#define MPPI_SDF_MLP_BF16  2    /* Gate-SDF MLP, hidden GEMMs in BF16 on tcgen05, FP32 accumulate */
+
+/* Gate-SDF MLP shape: [p(3), z(MPPI_LATENT_DIM)] -> 4 x MPPI_HIDDEN softplus -> 1. */
+#define MPPI_LATENT_DIM 64
+#define MPPI_HIDDEN     128
+#define MPPI_MLP_LAYERS 5       /* affine maps */
+#define MPPI_MAX_GATES  8
+#define MPPI_MAX_K      (1 << 20)
+#define MPPI_MAX_H      1024
+
+/*
+ * Controller parameters.  mppi_config_default() fills the values of the
+ * single-gate hover workload (K = 256, H = 20).
+ *   K, H          rollouts and horizon steps (1 <= K <= MPPI_MAX_K, 1 <= H <= MPPI_MAX_H)
+ *   max_gates     gate capacity of the context (1 .. MPPI_MAX_GATES)
+ *   sdf_mode      MPPI_SDF_*
+ *   dt, mass, gravity                 RK4 step (s), vehicle mass (kg), g (m/s^2)
+ *   thrust_min/max, rate_max          control box: T in [min, max], |w_i| <= rate_max
+ *   sigma_thrust, sigma_rate          noise standard deviations (Sigma = diag)
+ *   lambda                            temperature of Eq. 5 (> 0)
+ *   w_col, d_safe, w_u                cost weights: w_col max(0, d_safe - s)^2 per
+ *                                     state, w_u |u - u_hover|^2 per control
+ *   gate_inner_half, gate_outer_half, gate_half_depth   frame geometry (m)
+ *   softplus_beta                     sharpness of the MLP's softplus
+ *   seed, drone_id                    Philox key and the counter's 4th word
+ */
+typedef struct mppi_config {
+    int32_t K;
+    int32_t H;
+    int32_t max_gates;
+    int32_t sdf_mode;
+    float dt, mass, gravity;
+    float thrust_min, thrust_max, rate_max;
+    float sigma_thrust, sigma_rate, lambda;
+    float w_col, d_safe, w_u;
+    float gate_inner_half, gate_outer_half, gate_half_depth;
+    float softplus_beta;
+    uint64_t seed;
+    uint32_t drone_id;
+    uint32_t reserved;
+} mppi_config;
+
+typedef struct mppi_ctx mppi_ctx;
+
+/* Fill *cfg with the defaults listed above. */
+void mppi_config_default(mppi_config* cfg);
+
+/*
+ * Create a controller.  cuda_stream is a cudaStream_t (NULL: the library
+ * creates and owns a non-blocking stream).  Allocates every device buffer the
+ * step needs for (K, H, max_gates); later calls allocate nothing on the
+ * device.  Initial state: hovering at the origin, nominal = H copies of
+ * u_hover = (mass * gravity, 0, 0, 0), step counter 0, no gates, no weights.
+ * Errors: MPPI_E_INVALID (cfg), MPPI_E_UNSUPPORTED (device), MPPI_E_OOM, MPPI_E_CUDA.
+ * On error *out is NULL (the message is in the thread's last-error slot,
+ * readable with mppi_last_error(NULL)).
+ */
+int mppi_create(const mppi_config* cfg, void* cuda_stream, mppi_ctx** out);
+
+/* Free the context and its device buffers.  NULL is ignored. */
+void mppi_destroy(mppi_ctx* ctx);
+
+/* Last error message of ctx (or of the calling thread's last failed create when ctx is NULL). */
+const char* mppi_last_error(const mppi_ctx* ctx);
+
+/*
+ * Set the gates in view (host pointers).  poses: n_gates x 7; latents:
+ * n_gates x MPPI_LATENT_DIM (the per-gate latent code z of the Gate-SDF
+ * decoder, Sec. III-B; may be NULL in MPPI_SDF_ANALYTIC mode).  0 <= n_gates
+ * <= max_gates.  With no gates the collision and progress costs are zero.
+ * Synchronous.
+ */
+int mppi_set_gates(mppi_ctx* ctx, int n_gates, const float* poses, const float* latents);
+
+/*
+ * Set the Gate-SDF MLP weights (host pointers, FP32): layers[2*i] is W_i
+ * [out_i x in_i] row-major and layers[2*i+1] its bias [out_i], for the five
+ * affine maps 67 -> 128 -> 128 -> 128 -> 128 -> 1 (n_layers = 10 pointers).
+ * The library keeps FP32 copies and the BF16 copies the tensor-core path
+ * uses, and precomputes the per-gate first-layer bias W1[:, 3:] z_g + b1.
+ * fp8_scales must be NULL (reserved).  Synchronous.
+ */
+int mppi_set_sdf_weights(mppi_ctx* ctx, const float* const* layers, int n_layers, const float* fp8_scales);
+
+/*
+ * One control step, host buffers, synchronous.
+ *   state        13 floats, or NULL to continue from the device-resident state
+ *                (advanced by the previous step's plant update)
+ *   gate_poses   n_gates x 7, or NULL to keep the current gates
+ *   latents      n_gates x 64, or NULL to keep the current latents
+ *   nominal      H x 4 initial sequence U*, or NULL for the device-resident
+ *                warm start (previous step's U* shifted by one)
+ *   new_controls H x 4 out: the updated sequence U*_new of Eq. 5 (required)
+ *   weights      K out: w_m of Eq. 5 (nullable)
+ *   costs        K out: J_m (nullable)
+ * After the update the library applies U*_new[0] to its device-resident
+ * state with one RK4 step, stores U*_new shifted left by one (u_hover
+ * appended) as the next warm start and increments the step counter that
+ * keys the noise.
+ * Errors: MPPI_E_INVALID (NaN/Inf in state, NULL new_controls),
+ * MPPI_E_NOT_READY, MPPI_E_TIMEOUT, MPPI_E_CUDA.
+ */
+int mppi_step(mppi_ctx* ctx, const float* state, const float* gate_poses, const float* latents,
+              const float* nominal, float* new_controls, float* weights, float* costs);
+
+/*
+ * Same as mppi_step with DEVICE pointers (same shapes, same NULL rules),
+ * enqueued on the context's stream and returned without synchronising; the
+ * outputs are valid once the stream has reached this point.  No host-side
+ * NaN check.  Device-side timeouts are reported by the next synchronous call
+ * (mppi_sync, mppi_step, mppi_get_*).
+ */
+int mppi_step_async(mppi_ctx* ctx, const float* d_state, const float* d_gate_poses, const float* d_latents,
+                    const float* d_nominal, float* d_new_controls, float* d_weights, float* d_costs);
+
+/* Wait for the context's stream and report any device-side error. */
+int mppi_sync(mppi_ctx* ctx);
+
+/* Read back the device-resident warm-start sequence (H x 4) / true state (13). Synchronous. */
+int mppi_get_nominal(mppi_ctx* ctx, float* out);
+int mppi_get_state(mppi_ctx* ctx, float* out);
+
+/* Overwrite the step counter that keys the Philox noise (the counter's 3rd word is its low 32 bits). */
+int mppi_set_step_counter(mppi_ctx* ctx, uint64_t step);
+uint64_t mppi_get_step_counter(const mppi_ctx* ctx);
+
+/*
+ * Copy one of the last step's intermediate buffers to host memory (tests and
+ * diagnostics).  n is the number of floats the caller's buffer holds; it must
+ * be at least the buffer's size.  Synchronous.
+ *   MPPI_BUF_NOISE      H x K x 4  delta u, layout [h][k][4]
+ *   MPPI_BUF_POSITIONS  H x K x 4  rollout positions p_1..p_H, [h][k][x,y,z,0]
+ *   MPPI_BUF_COST_PARTS 3 x K      [J_col; J_prog; J_ctl]
+ *   MPPI_BUF_SDF        H x K      s(p_h) = min over gates of the SDF at every rollout state (MLP modes)
+ *   MPPI_BUF_WEIGHTS    K
+ *   MPPI_BUF_COSTS      K
+ */
+#define MPPI_BUF_NOISE       0
+#define MPPI_BUF_POSITIONS   1
+#define MPPI_BUF_COST_PARTS  2
+#define MPPI_BUF_SDF         3
+#define MPPI_BUF_WEIGHTS     4
+#define MPPI_BUF_COSTS       5
+int mppi_read_buffer(mppi_ctx* ctx, int which, float* host_out, size_t n);
+
+/*
+ * Raw Philox4x32-10 words of the noise kernel for the current step counter
+ * (H x K x 4 uint32, [h][k][word]), produced by the same device function the
+ * noise kernel uses.  For bit-exact tests.  Synchronous.
+ */
+int mppi_read_noise_words(mppi_ctx* ctx, uint32_t* host_out, size_t n);
+
+/*
+ * Per-kernel timing of the last step run with timing enabled (milliseconds,
+ * CUDA events on the context's stream).  mppi_set_timing(ctx, 1) makes each
+ * following step record events around its kernels (this adds event records
+ * to the stream); names[i] are static strings.  Returns the number of
+ * entries written (<= cap) or a negative error.
+ */
+int mppi_set_timing(mppi_ctx* ctx, int enable);
+int mppi_get_kernel_times(mppi_ctx* ctx, const char** names, float* ms, int cap);
+
+/* Number of kernel launches one step makes in the context's current mode. */
+int mppi_kernels_per_step(const mppi_ctx* ctx);
+
+/*
+ * Self-test of the tensor-core path: D = A * B^T for one 128 x 128 x 128
+ * tile through the same shared-memory layout, tcgen05.mma and TMEM read-back
+ * the BF16 SDF kernel uses.  d_A: 128 x 128 BF16 (row-major, rows = M),
+ * d_B: 128 x 128 BF16 (row-major, rows = N, columns = K), d_D: 128 x 128 FP32
+ * row-major; device pointers.  stream may be NULL (default stream).
+ * Synchronous.  Returns MPPI_E_UNSUPPORTED off sm_103.
+ */
+int mppi_selftest_tc_gemm(const uint16_t* d_A, const uint16_t* d_B, float* d_D, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPPI_GB300_H */

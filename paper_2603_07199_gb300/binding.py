@@ -1,0 +1,216 @@
+"""Thin ctypes binding of the C ABI in include/mppi.h (argument marshalling only).
+
+Array arguments may be numpy arrays (host pointers, must be C-contiguous
+float32 / uint32 / uint16), torch tensors (their data_ptr(), host or device),
+raw integer addresses, or None for a NULL pointer.  Every call that returns
+a negative status raises MppiError with the library's message.
+"""
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmppi_gb300.so")
+
+MPPI_OK = 0
+MPPI_E_INVALID = -1
+MPPI_E_OOM = -2
+MPPI_E_CUDA = -3
+MPPI_E_TIMEOUT = -4
+MPPI_E_NOT_READY = -5
+MPPI_E_UNSUPPORTED = -6
+
+MPPI_SDF_ANALYTIC = 0
+MPPI_SDF_MLP_FP32 = 1
+MPPI_SDF_MLP_BF16 = 2
+
+MPPI_BUF_NOISE = 0
+MPPI_BUF_POSITIONS = 1
+MPPI_BUF_COST_PARTS = 2
+MPPI_BUF_SDF = 3
+MPPI_BUF_WEIGHTS = 4
+MPPI_BUF_COSTS = 5
+
+LATENT_DIM = 64
+HIDDEN = 128
+
+# every symbol include/mppi.h declares
+EXPORTS = [
+    "mppi_config_default", "mppi_create", "mppi_destroy", "mppi_last_error", "mppi_set_gates",
+    "mppi_set_sdf_weights", "mppi_step", "mppi_step_async", "mppi_sync", "mppi_get_nominal",
+    "mppi_get_state", "mppi_set_step_counter", "mppi_get_step_counter", "mppi_read_buffer",
+    "mppi_read_noise_words", "mppi_set_timing", "mppi_get_kernel_times", "mppi_kernels_per_step",
+    "mppi_selftest_tc_gemm",
+]
+
+
+class MppiError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mppi error {code}: {msg}")
+        self.code = code
+
+
+class MppiConfig(ctypes.Structure):
+    _fields_ = [
+        ("K", ctypes.c_int32), ("H", ctypes.c_int32), ("max_gates", ctypes.c_int32), ("sdf_mode", ctypes.c_int32),
+        ("dt", ctypes.c_float), ("mass", ctypes.c_float), ("gravity", ctypes.c_float),
+        ("thrust_min", ctypes.c_float), ("thrust_max", ctypes.c_float), ("rate_max", ctypes.c_float),
+        ("sigma_thrust", ctypes.c_float), ("sigma_rate", ctypes.c_float), ("lam", ctypes.c_float),
+        ("w_col", ctypes.c_float), ("d_safe", ctypes.c_float), ("w_u", ctypes.c_float),
+        ("gate_inner_half", ctypes.c_float), ("gate_outer_half", ctypes.c_float), ("gate_half_depth", ctypes.c_float),
+        ("softplus_beta", ctypes.c_float),
+        ("seed", ctypes.c_uint64), ("drone_id", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+    ]
+
+
+_vp = ctypes.c_void_p
+_SIGS = {
+    "mppi_config_default": (None, [ctypes.POINTER(MppiConfig)]),
+    "mppi_create": (ctypes.c_int, [ctypes.POINTER(MppiConfig), _vp, ctypes.POINTER(_vp)]),
+    "mppi_destroy": (None, [_vp]),
+    "mppi_last_error": (ctypes.c_char_p, [_vp]),
+    "mppi_set_gates": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "mppi_set_sdf_weights": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.c_int, _vp]),
+    "mppi_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "mppi_step_async": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "mppi_sync": (ctypes.c_int, [_vp]),
+    "mppi_get_nominal": (ctypes.c_int, [_vp, _vp]),
+    "mppi_get_state": (ctypes.c_int, [_vp, _vp]),
+    "mppi_set_step_counter": (ctypes.c_int, [_vp, ctypes.c_uint64]),
+    "mppi_get_step_counter": (ctypes.c_uint64, [_vp]),
+    "mppi_read_buffer": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_size_t]),
+    "mppi_read_noise_words": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+    "mppi_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "mppi_get_kernel_times": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float),
+                                             ctypes.c_int]),
+    "mppi_kernels_per_step": (ctypes.c_int, [_vp]),
+    "mppi_selftest_tc_gemm": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+}
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load the CUDA library (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with paper_2603_07199_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _check(rc, ctx=None):
+    if rc < 0:
+        msg = load().mppi_last_error(ctx)
+        raise MppiError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def mppi_config_default():
+    cfg = MppiConfig()
+    load().mppi_config_default(ctypes.byref(cfg))
+    return cfg
+
+
+def mppi_create(cfg, stream=None):
+    ctx = _vp()
+    _check(load().mppi_create(ctypes.byref(cfg), stream, ctypes.byref(ctx)))
+    return ctx
+
+
+def mppi_destroy(ctx):
+    load().mppi_destroy(ctx)
+
+
+def mppi_last_error(ctx=None):
+    m = load().mppi_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def mppi_set_gates(ctx, n_gates, poses, latents=None):
+    return _check(load().mppi_set_gates(ctx, n_gates, _ptr(poses), _ptr(latents)), ctx)
+
+
+def mppi_set_sdf_weights(ctx, layers, fp8_scales=None):
+    """layers: [W1, b1, W2, b2, W3, b3, W4, b4, W5, b5] as float32 arrays (kept alive by the caller)."""
+    arr = (_vp * len(layers))(*[_ptr(a) for a in layers])
+    return _check(load().mppi_set_sdf_weights(ctx, arr, len(layers), _ptr(fp8_scales)), ctx)
+
+
+def mppi_step(ctx, state, gate_poses, latents, nominal, new_controls, weights=None, costs=None):
+    return _check(load().mppi_step(ctx, _ptr(state), _ptr(gate_poses), _ptr(latents), _ptr(nominal),
+                                   _ptr(new_controls), _ptr(weights), _ptr(costs)), ctx)
+
+
+def mppi_step_async(ctx, d_state, d_gate_poses, d_latents, d_nominal, d_new_controls, d_weights=None, d_costs=None):
+    return _check(load().mppi_step_async(ctx, _ptr(d_state), _ptr(d_gate_poses), _ptr(d_latents), _ptr(d_nominal),
+                                         _ptr(d_new_controls), _ptr(d_weights), _ptr(d_costs)), ctx)
+
+
+def mppi_sync(ctx):
+    return _check(load().mppi_sync(ctx), ctx)
+
+
+def mppi_get_nominal(ctx, out):
+    return _check(load().mppi_get_nominal(ctx, _ptr(out)), ctx)
+
+
+def mppi_get_state(ctx, out):
+    return _check(load().mppi_get_state(ctx, _ptr(out)), ctx)
+
+
+def mppi_set_step_counter(ctx, step):
+    return _check(load().mppi_set_step_counter(ctx, step), ctx)
+
+
+def mppi_get_step_counter(ctx):
+    return load().mppi_get_step_counter(ctx)
+
+
+def mppi_read_buffer(ctx, which, out):
+    return _check(load().mppi_read_buffer(ctx, which, _ptr(out), out.size if hasattr(out, "size") and
+                                          not callable(out.size) else out.numel()), ctx)
+
+
+def mppi_read_noise_words(ctx, out):
+    return _check(load().mppi_read_noise_words(ctx, _ptr(out), out.size), ctx)
+
+
+def mppi_set_timing(ctx, enable):
+    return _check(load().mppi_set_timing(ctx, 1 if enable else 0), ctx)
+
+
+def mppi_get_kernel_times(ctx, cap=16):
+    names = (ctypes.c_char_p * cap)()
+    ms = (ctypes.c_float * cap)()
+    n = _check(load().mppi_get_kernel_times(ctx, names, ms, cap), ctx)
+    return [(names[i].decode(), ms[i]) for i in range(n)]
+
+
+def mppi_kernels_per_step(ctx):
+    return load().mppi_kernels_per_step(ctx)
+
+
+def mppi_selftest_tc_gemm(d_A, d_B, d_D, stream=None):
+    return _check(load().mppi_selftest_tc_gemm(_ptr(d_A), _ptr(d_B), _ptr(d_D), stream))

@@ -1,0 +1,175 @@
+// (c) Gate-SDF MLP at every rollout state, FP32 on the CUDA cores: the plain
+// FP32 path.  One CTA takes a tile of 128 rollouts at one horizon step, runs
+// the whole MLP for every gate with register-blocked FP32 GEMMs through
+// shared memory, keeps the minimum over gates and writes the per-state
+// minimum over gates s(p) of every rollout state.
+#include "kernels.h"
+
+namespace mppi {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kLdA = kTileRows + 4;     // activations stored feature-major: act[feature][row]
+
+// sp(x) = max(x, 0) + log1p(exp(-beta |x|)) / beta, accurate FP32 library calls
+__device__ __forceinline__ float softplus_acc(float x, float beta, float inv_beta) {
+    return fmaxf(x, 0.f) + log1pf(expf(-beta * fabsf(x))) * inv_beta;
+}
+
+// rows / columns of the 8 x 8 register tile of thread (tr, tn): two 4-wide
+// strips 64 apart, so 16 threads read 256 contiguous bytes per shared load
+__device__ __forceinline__ int strip(int t, int i) { return (i < 4) ? t * 4 + i : 64 + t * 4 + (i - 4); }
+
+__global__ void __launch_bounds__(kThreads, 1) sdf_mlp_fp32_kernel(StepParams P, StepBuffers B, MlpWeights W) {
+    extern __shared__ __align__(16) float smem[];
+    float* act = smem;                              // [128][kLdA]
+    float* wt = act + kHidden * kLdA;               // [128 in][128 out]
+    float* sW1 = wt + kHidden * kHidden;            // [3][128]   W1[:, 0:3] transposed
+    float* sB1 = sW1 + 3 * kHidden;                 // [G][128]   per-gate first-layer bias
+    float* sBias = sB1 + kMaxGates * kHidden;       // [3][128]   b2, b3, b4
+    float* sW5 = sBias + 3 * kHidden;               // [128]
+    float* sPg = sW5 + kHidden;                     // [3][128]   gate-frame points of the tile
+    float* sMin = sPg + 3 * kTileRows;              // [128]      min over gates
+    float* sPose = sMin + kTileRows;                // [G][8]
+
+    const int tid = threadIdx.x;
+    const int K = P.K, G = P.G;
+    for (int i = tid; i < 3 * kHidden; i += kThreads) {
+        const int j = i / kHidden, n = i - j * kHidden;
+        sW1[i] = W.W1[n * (3 + kLatent) + j];
+        sBias[i] = W.b[j][n];
+    }
+    for (int i = tid; i < G * kHidden; i += kThreads) sB1[i] = B.b1p[i];
+    for (int i = tid; i < kHidden; i += kThreads) sW5[i] = W.w5[i];
+    for (int i = tid; i < G * 8; i += kThreads) sPose[i] = B.poses[i];
+    __syncthreads();
+
+    const float beta = P.beta, inv_beta = 1.0f / P.beta;
+    const int tn = tid & 15, tr = tid >> 4;
+    const int n_kb = (K + kTileRows - 1) / kTileRows;
+    const int n_items = P.H * n_kb;
+
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int h = item / n_kb, kb = item - h * n_kb;
+        if (tid < kTileRows) sMin[tid] = __int_as_float(0x7f800000);
+        for (int g = 0; g < G; ++g) {
+            if (tid < kTileRows) {
+                const int k = min(kb * kTileRows + tid, K - 1);
+                const float4 p = B.pos[h * K + k];
+                const Vec3 pg = to_gate(sPose + 8 * g, v3(p.x, p.y, p.z));
+                sPg[tid] = pg.x;
+                sPg[kTileRows + tid] = pg.y;
+                sPg[2 * kTileRows + tid] = pg.z;
+            }
+            __syncthreads();
+            // layer 1: [p, z] -> 128, with the latent part folded into the per-gate bias
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int r = strip(tr, i);
+                const float x0 = sPg[r], x1 = sPg[kTileRows + r], x2 = sPg[2 * kTileRows + r];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int n = strip(tn, j);
+                    const float a = sB1[g * kHidden + n] + sW1[n] * x0 + sW1[kHidden + n] * x1 +
+                                    sW1[2 * kHidden + n] * x2;
+                    act[n * kLdA + r] = softplus_acc(a, beta, inv_beta);
+                }
+            }
+            // layers 2..4: 128 x 128 GEMMs; the last one is followed by the output dot
+            for (int l = 0; l < 3; ++l) {
+                const float4* src = reinterpret_cast<const float4*>(W.Wt[l]);
+                float4* dst = reinterpret_cast<float4*>(wt);
+                __syncthreads();
+                for (int i = tid; i < kHidden * kHidden / 4; i += kThreads) dst[i] = __ldg(src + i);
+                __syncthreads();
+                float acc[8][8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+#pragma unroll 4
+                for (int kk = 0; kk < kHidden; ++kk) {
+                    const float4 a0 = *reinterpret_cast<const float4*>(act + kk * kLdA + tr * 4);
+                    const float4 a1 = *reinterpret_cast<const float4*>(act + kk * kLdA + 64 + tr * 4);
+                    const float4 b0 = *reinterpret_cast<const float4*>(wt + kk * kHidden + tn * 4);
+                    const float4 b1 = *reinterpret_cast<const float4*>(wt + kk * kHidden + 64 + tn * 4);
+                    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+                }
+                __syncthreads();
+                if (l < 2) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int n = strip(tn, j);
+                        const float bn = sBias[l * kHidden + n];
+                        float4 lo, hi;
+                        lo.x = softplus_acc(acc[0][j] + bn, beta, inv_beta);
+                        lo.y = softplus_acc(acc[1][j] + bn, beta, inv_beta);
+                        lo.z = softplus_acc(acc[2][j] + bn, beta, inv_beta);
+                        lo.w = softplus_acc(acc[3][j] + bn, beta, inv_beta);
+                        hi.x = softplus_acc(acc[4][j] + bn, beta, inv_beta);
+                        hi.y = softplus_acc(acc[5][j] + bn, beta, inv_beta);
+                        hi.z = softplus_acc(acc[6][j] + bn, beta, inv_beta);
+                        hi.w = softplus_acc(acc[7][j] + bn, beta, inv_beta);
+                        *reinterpret_cast<float4*>(act + n * kLdA + tr * 4) = lo;
+                        *reinterpret_cast<float4*>(act + n * kLdA + 64 + tr * 4) = hi;
+                    }
+                } else {
+                    // s_r = w5 . sp(h4_r + b4) + b5, reduced over the 16 column threads
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        float part = 0.f;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int n = strip(tn, j);
+                            part = fmaf(sW5[n], softplus_acc(acc[i][j] + sBias[2 * kHidden + n], beta, inv_beta),
+                                        part);
+                        }
+                        part += __shfl_xor_sync(0xffffffffu, part, 1);
+                        part += __shfl_xor_sync(0xffffffffu, part, 2);
+                        part += __shfl_xor_sync(0xffffffffu, part, 4);
+                        part += __shfl_xor_sync(0xffffffffu, part, 8);
+                        if (tn == 0) {
+                            const int r = strip(tr, i);
+                            sMin[r] = fminf(sMin[r], part + W.b5);
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (tid < kTileRows) {
+            const int k = kb * kTileRows + tid;
+            if (k < K) B.sdf[h * K + k] = sMin[tid];
+        }
+        __syncthreads();
+    }
+}
+
+constexpr size_t kSmemBytes = sizeof(float) * (kHidden * kLdA + kHidden * kHidden + 3 * kHidden +
+                                                kMaxGates * kHidden + 3 * kHidden + kHidden + 3 * kTileRows +
+                                                kTileRows + kMaxGates * 8);
+
+}  // namespace
+
+cudaError_t launch_sdf_mlp_fp32(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
+                                cudaStream_t s) {
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(sdf_mlp_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(kSmemBytes));
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int n_items = P.H * ((P.K + kTileRows - 1) / kTileRows);
+    const int grid = n_items < num_sms ? n_items : num_sms;
+    sdf_mlp_fp32_kernel<<<grid, kThreads, kSmemBytes, s>>>(P, B, W);
+    return cudaGetLastError();
+}
+
+}  // namespace mppi

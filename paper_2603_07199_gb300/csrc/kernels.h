@@ -1,0 +1,45 @@
+// Launchers of the step kernels (host side, internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace mppi {
+
+// (a) noise: delta u for every (h, k) -> B.noise
+cudaError_t launch_noise(const StepParams& P, const StepBuffers& B, cudaStream_t s);
+// raw Philox words for every (h, k) (tests)
+cudaError_t launch_noise_words(const StepParams& P, const StepBuffers& B, uint4* out, cudaStream_t s);
+// (b) rollouts; with analytic != 0 the frame SDF cost is fused in
+cudaError_t launch_rollout(const StepParams& P, const StepBuffers& B, int analytic, cudaStream_t s);
+// (c) Gate-SDF MLP at every rollout state -> B.sdf (min over gates)
+struct MlpWeights {
+    const float* W1;        // [128][67]
+    const float* Wt[3];     // W2..W4 transposed: [in][out], FP32
+    const float* b[3];      // b2..b4
+    const float* w5;        // [128]
+    float b5;
+    const uint16_t* Wbf[3]; // W2..W4 as BF16 in the tensor-core operand layout
+};
+cudaError_t launch_sdf_mlp_fp32(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
+                                cudaStream_t s);
+cudaError_t launch_sdf_mlp_bf16(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
+                                cudaStream_t s);
+// (d) costs -> weights; weighted update + plant step + shift
+cudaError_t launch_cost_weights(const StepParams& P, const StepBuffers& B, int mlp, cudaStream_t s);
+cudaError_t launch_update_plant(const StepParams& P, const StepBuffers& B, cudaStream_t s);
+// per-gate first-layer bias b1'_g = W1[:, 3:67] z_g + b1
+cudaError_t launch_first_layer_bias(const float* W1, const float* b1, const float* latents, int G, float* b1p,
+                                    cudaStream_t s);
+// tensor-core self-test (one 128x128x128 tile)
+cudaError_t launch_tc_selftest(const uint16_t* A, const uint16_t* B, float* D, int* err, cudaStream_t s);
+
+// Host helper: BF16 (round to nearest even) of a float.
+uint16_t float_to_bf16(float f);
+// Host helper: offset (in elements) of (row, col) in the 128 x 128 tensor-core operand layout.
+inline int tc_operand_offset(int row, int col) {
+    return ((row >> 3) * 16 + (col >> 3)) * 64 + (row & 7) * 8 + (col & 7);
+}
+
+}  // namespace mppi

@@ -1,0 +1,652 @@
+// C ABI of the control-step library: context, device buffers, the step's
+// launch sequence, host <-> device staging and diagnostics.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.h"
+#include "mppi.h"
+
+using namespace mppi;
+
+namespace {
+thread_local char g_thread_err[512] = "";
+}
+
+struct mppi_ctx {
+    mppi_config cfg{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int num_sms = 0;
+    int n_gates = 0;
+    bool have_weights = false;
+    bool have_latents = false;
+    bool timing = false;
+    uint64_t step_count = 0;
+    char err[512] = "";
+
+    StepBuffers B{};
+    float* d_latents = nullptr;   // [maxG][64]
+    // MLP weights
+    float* d_W1 = nullptr;        // [128][67]
+    float* d_b1 = nullptr;        // [128]
+    float* d_Wt[3] = {nullptr, nullptr, nullptr};
+    float* d_bias[3] = {nullptr, nullptr, nullptr};
+    float* d_w5 = nullptr;
+    uint16_t* d_Wbf[3] = {nullptr, nullptr, nullptr};
+    float b5 = 0.f;
+    // pinned staging
+    float* h_in = nullptr;        // state(16) | nominal(H*4) | poses(maxG*8) | latents(maxG*64)
+    float* h_out = nullptr;       // unew(H*4) | w(K) | J(K) | err(1)
+    // timing
+    cudaEvent_t ev[8] = {};
+    int n_ev = 0;
+    const char* ev_names[8] = {};
+    std::vector<void*> allocations;
+};
+
+namespace {
+
+int fail(mppi_ctx* c, int code, const char* fmt, ...) {
+    char* dst = c ? c->err : g_thread_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CUDA_TRY(ctx, expr)                                                                        \
+    do {                                                                                           \
+        cudaError_t e_ = (expr);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail((ctx), MPPI_E_CUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));      \
+    } while (0)
+
+template <typename T>
+int dev_alloc(mppi_ctx* c, T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, MPPI_E_OOM, "cudaMalloc(%zu bytes) failed: %s", count * sizeof(T), cudaGetErrorString(e));
+    }
+    c->allocations.push_back(q);
+    *p = static_cast<T*>(q);
+    return MPPI_OK;
+}
+
+StepParams make_params(const mppi_ctx* c) {
+    const mppi_config& g = c->cfg;
+    StepParams P{};
+    P.K = g.K;
+    P.H = g.H;
+    P.G = c->n_gates;
+    P.dt = g.dt;
+    P.mass = g.mass;
+    P.gravity = g.gravity;
+    P.tmin = g.thrust_min;
+    P.tmax = g.thrust_max;
+    P.rmax = g.rate_max;
+    P.sig_t = g.sigma_thrust;
+    P.sig_r = g.sigma_rate;
+    P.lam = g.lambda;
+    P.w_col = g.w_col;
+    P.d_safe = g.d_safe;
+    P.w_u = g.w_u;
+    P.a_in = g.gate_inner_half;
+    P.a_out = g.gate_outer_half;
+    P.half_depth = g.gate_half_depth;
+    P.beta = g.softplus_beta;
+    P.key0 = static_cast<uint32_t>(g.seed & 0xFFFFFFFFull);
+    P.key1 = static_cast<uint32_t>(g.seed >> 32);
+    P.drone = g.drone_id;
+    return P;
+}
+
+bool finite_all(const float* x, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(x[i])) return false;
+    return true;
+}
+
+int check_config(const mppi_config* g) {
+    if (!g) return fail(nullptr, MPPI_E_INVALID, "cfg is NULL");
+    if (g->K < 1 || g->K > MPPI_MAX_K) return fail(nullptr, MPPI_E_INVALID, "K=%d out of [1, %d]", g->K, MPPI_MAX_K);
+    if (g->H < 1 || g->H > MPPI_MAX_H) return fail(nullptr, MPPI_E_INVALID, "H=%d out of [1, %d]", g->H, MPPI_MAX_H);
+    if (static_cast<long long>(g->K) * g->H > (1ll << 28))
+        return fail(nullptr, MPPI_E_INVALID, "K*H=%lld exceeds 2^28", static_cast<long long>(g->K) * g->H);
+    if (g->max_gates < 1 || g->max_gates > MPPI_MAX_GATES)
+        return fail(nullptr, MPPI_E_INVALID, "max_gates=%d out of [1, %d]", g->max_gates, MPPI_MAX_GATES);
+    if (g->sdf_mode < MPPI_SDF_ANALYTIC || g->sdf_mode > MPPI_SDF_MLP_BF16)
+        return fail(nullptr, MPPI_E_UNSUPPORTED, "sdf_mode=%d is not built", g->sdf_mode);
+    const float f[] = {g->dt, g->mass, g->gravity, g->thrust_min, g->thrust_max, g->rate_max, g->sigma_thrust,
+                       g->sigma_rate, g->lambda, g->w_col, g->d_safe, g->w_u, g->gate_inner_half,
+                       g->gate_outer_half, g->gate_half_depth, g->softplus_beta};
+    if (!finite_all(f, sizeof(f) / sizeof(f[0]))) return fail(nullptr, MPPI_E_INVALID, "non-finite parameter");
+    if (!(g->dt > 0.f) || !(g->mass > 0.f) || !(g->lambda > 0.f) || !(g->softplus_beta > 0.f))
+        return fail(nullptr, MPPI_E_INVALID, "dt, mass, lambda and softplus_beta must be > 0");
+    if (!(g->thrust_min <= g->thrust_max) || !(g->rate_max >= 0.f) || g->sigma_thrust < 0.f || g->sigma_rate < 0.f)
+        return fail(nullptr, MPPI_E_INVALID, "inconsistent control bounds or negative sigma");
+    if (!(g->gate_inner_half < g->gate_outer_half) || !(g->gate_half_depth > 0.f))
+        return fail(nullptr, MPPI_E_INVALID, "gate geometry");
+    return MPPI_OK;
+}
+
+int recompute_b1p(mppi_ctx* c) {
+    if (!c->have_weights || !c->have_latents || c->n_gates == 0) return MPPI_OK;
+    CUDA_TRY(c, launch_first_layer_bias(c->d_W1, c->d_b1, c->d_latents, c->n_gates, c->B.b1p, c->stream));
+    return MPPI_OK;
+}
+
+bool is_mlp(const mppi_ctx* c) { return c->cfg.sdf_mode == MPPI_SDF_MLP_FP32 || c->cfg.sdf_mode == MPPI_SDF_MLP_BF16; }
+
+MlpWeights make_weights(const mppi_ctx* c) {
+    MlpWeights W{};
+    W.W1 = c->d_W1;
+    for (int l = 0; l < 3; ++l) {
+        W.Wt[l] = c->d_Wt[l];
+        W.b[l] = c->d_bias[l];
+        W.Wbf[l] = c->d_Wbf[l];
+    }
+    W.w5 = c->d_w5;
+    W.b5 = c->b5;
+    return W;
+}
+
+void record(mppi_ctx* c, const char* name) {
+    if (!c->timing || c->n_ev >= 8) return;
+    cudaEventRecord(c->ev[c->n_ev], c->stream);
+    c->ev_names[c->n_ev] = name;
+    ++c->n_ev;
+}
+
+// The kernels of one step, enqueued on the context's stream.
+int enqueue_kernels(mppi_ctx* c) {
+    const StepParams P = make_params(c);
+    const bool mlp = is_mlp(c);
+    c->n_ev = 0;
+    record(c, "start");
+    CUDA_TRY(c, launch_noise(P, c->B, c->stream));
+    record(c, "noise");
+    CUDA_TRY(c, launch_rollout(P, c->B, mlp ? 0 : 1, c->stream));
+    record(c, "rollout");
+    if (mlp) {
+        const MlpWeights W = make_weights(c);
+        if (c->cfg.sdf_mode == MPPI_SDF_MLP_FP32) {
+            CUDA_TRY(c, launch_sdf_mlp_fp32(P, c->B, W, c->num_sms, c->stream));
+            record(c, "sdf_mlp_fp32");
+        } else {
+            CUDA_TRY(c, launch_sdf_mlp_bf16(P, c->B, W, c->num_sms, c->stream));
+            record(c, "sdf_mlp_bf16");
+        }
+    }
+    CUDA_TRY(c, launch_cost_weights(P, c->B, mlp ? 1 : 0, c->stream));
+    record(c, "cost_weights");
+    CUDA_TRY(c, launch_update_plant(P, c->B, c->stream));
+    record(c, "update_plant");
+    return MPPI_OK;
+}
+
+int check_ready(mppi_ctx* c) {
+    if (is_mlp(c)) {
+        if (!c->have_weights) return fail(c, MPPI_E_NOT_READY, "MLP SDF mode but no weights set");
+        if (c->n_gates > 0 && !c->have_latents) return fail(c, MPPI_E_NOT_READY, "MLP SDF mode but no latents set");
+    }
+    return MPPI_OK;
+}
+
+int read_err_word(mppi_ctx* c) {
+    int e = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&e, c->B.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (e != 0) {
+        CUDA_TRY(c, cudaMemsetAsync(c->B.err, 0, sizeof(int), c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        return fail(c, MPPI_E_TIMEOUT, "a device-side wait timed out (error word %d)", e);
+    }
+    return MPPI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mppi_config_default(mppi_config* g) {
+    if (!g) return;
+    std::memset(g, 0, sizeof(*g));
+    g->K = 256;
+    g->H = 20;
+    g->max_gates = 1;
+    g->sdf_mode = MPPI_SDF_ANALYTIC;
+    g->dt = 0.02f;
+    g->mass = 0.8f;
+    g->gravity = 9.81f;
+    g->thrust_min = 0.f;
+    g->thrust_max = 30.f;
+    g->rate_max = 8.f;
+    g->sigma_thrust = 2.f;
+    g->sigma_rate = 1.5f;
+    g->lambda = 0.1f;
+    g->w_col = 100.f;
+    g->d_safe = 0.3f;
+    g->w_u = 1e-3f;
+    g->gate_inner_half = 0.5f;
+    g->gate_outer_half = 0.75f;
+    g->gate_half_depth = 0.1f;
+    g->softplus_beta = 100.f;
+    g->seed = 0;
+    g->drone_id = 0;
+}
+
+const char* mppi_last_error(const mppi_ctx* c) { return c ? c->err : g_thread_err; }
+
+void mppi_destroy(mppi_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (void* p : c->allocations) cudaFree(p);
+    if (c->h_in) cudaFreeHost(c->h_in);
+    if (c->h_out) cudaFreeHost(c->h_out);
+    for (auto& e : c->ev)
+        if (e) cudaEventDestroy(e);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int mppi_create(const mppi_config* cfg, void* cuda_stream, mppi_ctx** out) {
+    if (!out) return fail(nullptr, MPPI_E_INVALID, "out is NULL");
+    *out = nullptr;
+    int rc = check_config(cfg);
+    if (rc != MPPI_OK) return rc;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, MPPI_E_UNSUPPORTED, "no CUDA device");
+    }
+    int major = 0, minor = 0, sms = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (major != 10 || minor != 3)
+        return fail(nullptr, MPPI_E_UNSUPPORTED, "device is sm_%d%d; this library is built for sm_103a only", major,
+                    minor);
+
+    mppi_ctx* c = new (std::nothrow) mppi_ctx();
+    if (!c) return fail(nullptr, MPPI_E_OOM, "host allocation failed");
+    c->cfg = *cfg;
+    c->device = dev;
+    c->num_sms = sms;
+    if (cuda_stream) {
+        c->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return fail(nullptr, MPPI_E_CUDA, "cudaStreamCreate failed");
+        }
+        c->own_stream = true;
+    }
+    const int K = cfg->K, H = cfg->H, MG = cfg->max_gates;
+    const size_t KH = static_cast<size_t>(K) * H;
+    const int nred = (K + 255) / 256;
+    StepBuffers& B = c->B;
+    rc = MPPI_OK;
+    rc = rc ? rc : dev_alloc(c, &B.state, 16);
+    rc = rc ? rc : dev_alloc(c, &B.nominal, H);
+    rc = rc ? rc : dev_alloc(c, &B.step, 2);
+    rc = rc ? rc : dev_alloc(c, &B.poses, static_cast<size_t>(MG) * 8);
+    rc = rc ? rc : dev_alloc(c, &B.b1p, static_cast<size_t>(MG) * kHidden);
+    rc = rc ? rc : dev_alloc(c, &B.noise, KH);
+    rc = rc ? rc : dev_alloc(c, &B.pos, KH);
+    rc = rc ? rc : dev_alloc(c, &B.parts, 3 * static_cast<size_t>(K));
+    rc = rc ? rc : dev_alloc(c, &B.sdf, KH);
+    rc = rc ? rc : dev_alloc(c, &B.J, K);
+    rc = rc ? rc : dev_alloc(c, &B.w, K);
+    rc = rc ? rc : dev_alloc(c, &B.unew, H);
+    rc = rc ? rc : dev_alloc(c, &B.red, nred);
+    rc = rc ? rc : dev_alloc(c, &B.stats, 4);
+    rc = rc ? rc : dev_alloc(c, &B.tickets, 4);
+    rc = rc ? rc : dev_alloc(c, &B.err, 1);
+    rc = rc ? rc : dev_alloc(c, &c->d_latents, static_cast<size_t>(MG) * kLatent);
+    rc = rc ? rc : dev_alloc(c, &c->d_W1, kHidden * (3 + kLatent));
+    rc = rc ? rc : dev_alloc(c, &c->d_b1, kHidden);
+    for (int l = 0; l < 3; ++l) {
+        rc = rc ? rc : dev_alloc(c, &c->d_Wt[l], kHidden * kHidden);
+        rc = rc ? rc : dev_alloc(c, &c->d_bias[l], kHidden);
+        rc = rc ? rc : dev_alloc(c, &c->d_Wbf[l], kHidden * kHidden);
+    }
+    rc = rc ? rc : dev_alloc(c, &c->d_w5, kHidden);
+    if (rc != MPPI_OK) {
+        std::snprintf(g_thread_err, sizeof(g_thread_err), "%s", c->err);
+        mppi_destroy(c);
+        return rc;
+    }
+    const size_t in_floats = 16 + static_cast<size_t>(H) * 4 + MG * 8 + MG * kLatent;
+    const size_t out_floats = static_cast<size_t>(H) * 4 + 2 * static_cast<size_t>(K) + 4;
+    if (cudaMallocHost(&c->h_in, in_floats * sizeof(float)) != cudaSuccess ||
+        cudaMallocHost(&c->h_out, out_floats * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        std::snprintf(g_thread_err, sizeof(g_thread_err), "pinned host allocation failed");
+        mppi_destroy(c);
+        return MPPI_E_OOM;
+    }
+    for (auto& e : c->ev) {
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            std::snprintf(g_thread_err, sizeof(g_thread_err), "cudaEventCreate failed");
+            mppi_destroy(c);
+            return MPPI_E_CUDA;
+        }
+    }
+    // initial state: hover at the origin; nominal: H copies of u_hover; counter 0
+    float* st = c->h_in;
+    std::memset(st, 0, 16 * sizeof(float));
+    st[6] = 1.f;
+    float* nom = c->h_in + 16;
+    for (int h = 0; h < H; ++h) {
+        nom[4 * h + 0] = cfg->mass * cfg->gravity;
+        nom[4 * h + 1] = nom[4 * h + 2] = nom[4 * h + 3] = 0.f;
+    }
+    bool ok = cudaMemcpyAsync(B.state, st, 16 * sizeof(float), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
+              cudaMemcpyAsync(B.nominal, nom, H * sizeof(float4), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
+              cudaMemsetAsync(B.step, 0, 2 * sizeof(uint32_t), c->stream) == cudaSuccess &&
+              cudaMemsetAsync(B.tickets, 0, 4 * sizeof(unsigned), c->stream) == cudaSuccess &&
+              cudaMemsetAsync(B.err, 0, sizeof(int), c->stream) == cudaSuccess &&
+              cudaMemsetAsync(B.poses, 0, MG * 8 * sizeof(float), c->stream) == cudaSuccess &&
+              cudaStreamSynchronize(c->stream) == cudaSuccess;
+    if (!ok) {
+        std::snprintf(g_thread_err, sizeof(g_thread_err), "initialisation copies failed: %s",
+                      cudaGetErrorString(cudaGetLastError()));
+        mppi_destroy(c);
+        return MPPI_E_CUDA;
+    }
+    *out = c;
+    return MPPI_OK;
+}
+
+int mppi_set_gates(mppi_ctx* c, int n_gates, const float* poses, const float* latents) {
+    if (!c) return fail(nullptr, MPPI_E_INVALID, "ctx is NULL");
+    if (n_gates < 0 || n_gates > c->cfg.max_gates)
+        return fail(c, MPPI_E_INVALID, "n_gates=%d out of [0, %d]", n_gates, c->cfg.max_gates);
+    if (n_gates > 0 && !poses) return fail(c, MPPI_E_INVALID, "poses is NULL");
+    if (n_gates > 0 && !finite_all(poses, static_cast<size_t>(n_gates) * 7))
+        return fail(c, MPPI_E_INVALID, "non-finite gate pose");
+    if (latents && !finite_all(latents, static_cast<size_t>(n_gates) * kLatent))
+        return fail(c, MPPI_E_INVALID, "non-finite latent");
+    float* hp = c->h_in + 16 + c->cfg.H * 4;
+    float* hl = hp + c->cfg.max_gates * 8;
+    for (int g = 0; g < n_gates; ++g) {
+        for (int i = 0; i < 7; ++i) hp[8 * g + i] = poses[7 * g + i];
+        hp[8 * g + 7] = 0.f;
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->n_gates = n_gates;
+    if (n_gates > 0)
+        CUDA_TRY(c, cudaMemcpyAsync(c->B.poses, hp, n_gates * 8 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    if (latents && n_gates > 0) {
+        std::memcpy(hl, latents, static_cast<size_t>(n_gates) * kLatent * sizeof(float));
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_latents, hl, n_gates * kLatent * sizeof(float), cudaMemcpyHostToDevice,
+                                    c->stream));
+        c->have_latents = true;
+    } else if (!latents) {
+        c->have_latents = (n_gates == 0);
+    }
+    int rc = recompute_b1p(c);
+    if (rc != MPPI_OK) return rc;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return MPPI_OK;
+}
+
+int mppi_set_sdf_weights(mppi_ctx* c, const float* const* layers, int n_layers, const float* fp8_scales) {
+    if (!c) return fail(nullptr, MPPI_E_INVALID, "ctx is NULL");
+    if (!layers || n_layers != 2 * MPPI_MLP_LAYERS)
+        return fail(c, MPPI_E_INVALID, "expected %d layer pointers (W, b for 5 affine maps)", 2 * MPPI_MLP_LAYERS);
+    if (fp8_scales) return fail(c, MPPI_E_UNSUPPORTED, "fp8_scales is reserved and must be NULL");
+    for (int i = 0; i < n_layers; ++i)
+        if (!layers[i]) return fail(c, MPPI_E_INVALID, "layer pointer %d is NULL", i);
+    const int in1 = 3 + kLatent;
+    const size_t sizes[10] = {static_cast<size_t>(kHidden) * in1, kHidden, kHidden * kHidden, kHidden,
+                              kHidden * kHidden, kHidden, kHidden * kHidden, kHidden, kHidden, 1};
+    for (int i = 0; i < 10; ++i)
+        if (!finite_all(layers[i], sizes[i])) return fail(c, MPPI_E_INVALID, "non-finite value in layer array %d", i);
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    CUDA_TRY(c, cudaMemcpy(c->d_W1, layers[0], sizes[0] * sizeof(float), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->d_b1, layers[1], sizes[1] * sizeof(float), cudaMemcpyHostToDevice));
+    std::vector<float> t(kHidden * kHidden);
+    std::vector<uint16_t> bf(kHidden * kHidden);
+    for (int l = 0; l < 3; ++l) {
+        const float* Wl = layers[2 + 2 * l];
+        for (int n = 0; n < kHidden; ++n)
+            for (int k = 0; k < kHidden; ++k) {
+                t[k * kHidden + n] = Wl[n * kHidden + k];
+                bf[tc_operand_offset(n, k)] = float_to_bf16(Wl[n * kHidden + k]);
+            }
+        CUDA_TRY(c, cudaMemcpy(c->d_Wt[l], t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(c->d_Wbf[l], bf.data(), bf.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(c->d_bias[l], layers[3 + 2 * l], kHidden * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    CUDA_TRY(c, cudaMemcpy(c->d_w5, layers[8], kHidden * sizeof(float), cudaMemcpyHostToDevice));
+    c->b5 = layers[9][0];
+    c->have_weights = true;
+    int rc = recompute_b1p(c);
+    if (rc != MPPI_OK) return rc;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return MPPI_OK;
+}
+
+int mppi_step(mppi_ctx* c, const float* state, const float* gate_poses, const float* latents, const float* nominal,
+              float* new_controls, float* weights, float* costs) {
+    if (!c) return fail(nullptr, MPPI_E_INVALID, "ctx is NULL");
+    if (!new_controls) return fail(c, MPPI_E_INVALID, "new_controls is NULL");
+    const int K = c->cfg.K, H = c->cfg.H;
+    if (state && !finite_all(state, 13)) return fail(c, MPPI_E_INVALID, "non-finite state");
+    if (nominal && !finite_all(nominal, static_cast<size_t>(H) * 4))
+        return fail(c, MPPI_E_INVALID, "non-finite nominal");
+    if (gate_poses || latents) {
+        // gates change: same path as mppi_set_gates with the current count
+        if (gate_poses) {
+            int rc = mppi_set_gates(c, c->n_gates, gate_poses, latents);
+            if (rc != MPPI_OK) return rc;
+        } else {
+            if (!finite_all(latents, static_cast<size_t>(c->n_gates) * kLatent))
+                return fail(c, MPPI_E_INVALID, "non-finite latent");
+            float* hl = c->h_in + 16 + H * 4 + c->cfg.max_gates * 8;
+            CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+            std::memcpy(hl, latents, static_cast<size_t>(c->n_gates) * kLatent * sizeof(float));
+            if (c->n_gates > 0)
+                CUDA_TRY(c, cudaMemcpyAsync(c->d_latents, hl, c->n_gates * kLatent * sizeof(float),
+                                            cudaMemcpyHostToDevice, c->stream));
+            c->have_latents = true;
+            int rc = recompute_b1p(c);
+            if (rc != MPPI_OK) return rc;
+        }
+    }
+    int rc = check_ready(c);
+    if (rc != MPPI_OK) return rc;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // staging buffers are free
+    if (state) {
+        std::memcpy(c->h_in, state, 13 * sizeof(float));
+        CUDA_TRY(c, cudaMemcpyAsync(c->B.state, c->h_in, 13 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    }
+    if (nominal) {
+        std::memcpy(c->h_in + 16, nominal, static_cast<size_t>(H) * 4 * sizeof(float));
+        CUDA_TRY(c, cudaMemcpyAsync(c->B.nominal, c->h_in + 16, H * sizeof(float4), cudaMemcpyHostToDevice,
+                                    c->stream));
+    }
+    rc = enqueue_kernels(c);
+    if (rc != MPPI_OK) return rc;
+    float* ho = c->h_out;
+    CUDA_TRY(c, cudaMemcpyAsync(ho, c->B.unew, H * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+    if (weights)
+        CUDA_TRY(c, cudaMemcpyAsync(ho + H * 4, c->B.w, K * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    if (costs)
+        CUDA_TRY(c, cudaMemcpyAsync(ho + H * 4 + K, c->B.J, K * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    int* herr = reinterpret_cast<int*>(ho + H * 4 + 2 * K);
+    CUDA_TRY(c, cudaMemcpyAsync(herr, c->B.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    ++c->step_count;
+    if (*herr != 0) {
+        CUDA_TRY(c, cudaMemsetAsync(c->B.err, 0, sizeof(int), c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        return fail(c, MPPI_E_TIMEOUT, "a device-side wait timed out (error word %d)", *herr);
+    }
+    std::memcpy(new_controls, ho, static_cast<size_t>(H) * 4 * sizeof(float));
+    if (weights) std::memcpy(weights, ho + H * 4, static_cast<size_t>(K) * sizeof(float));
+    if (costs) std::memcpy(costs, ho + H * 4 + K, static_cast<size_t>(K) * sizeof(float));
+    return MPPI_OK;
+}
+
+int mppi_step_async(mppi_ctx* c, const float* d_state, const float* d_gate_poses, const float* d_latents,
+                    const float* d_nominal, float* d_new_controls, float* d_weights, float* d_costs) {
+    if (!c) return fail(nullptr, MPPI_E_INVALID, "ctx is NULL");
+    const int K = c->cfg.K, H = c->cfg.H, G = c->n_gates;
+    if (d_state) CUDA_TRY(c, cudaMemcpyAsync(c->B.state, d_state, 13 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    if (d_gate_poses && G > 0)
+        CUDA_TRY(c, cudaMemcpy2DAsync(c->B.poses, 8 * sizeof(float), d_gate_poses, 7 * sizeof(float),
+                                      7 * sizeof(float), G, cudaMemcpyDeviceToDevice, c->stream));
+    if (d_latents && G > 0) {
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_latents, d_latents, G * kLatent * sizeof(float), cudaMemcpyDeviceToDevice,
+                                    c->stream));
+        c->have_latents = true;
+        int rc = recompute_b1p(c);
+        if (rc != MPPI_OK) return rc;
+    }
+    int rc = check_ready(c);
+    if (rc != MPPI_OK) return rc;
+    if (d_nominal)
+        CUDA_TRY(c, cudaMemcpyAsync(c->B.nominal, d_nominal, H * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream));
+    rc = enqueue_kernels(c);
+    if (rc != MPPI_OK) return rc;
+    if (d_new_controls)
+        CUDA_TRY(c, cudaMemcpyAsync(d_new_controls, c->B.unew, H * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream));
+    if (d_weights)
+        CUDA_TRY(c, cudaMemcpyAsync(d_weights, c->B.w, K * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    if (d_costs) CUDA_TRY(c, cudaMemcpyAsync(d_costs, c->B.J, K * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    ++c->step_count;
+    return MPPI_OK;
+}
+
+int mppi_sync(mppi_ctx* c) {
+    if (!c) return fail(nullptr, MPPI_E_INVALID, "ctx is NULL");
+    return read_err_word(c);
+}
+
+int mppi_get_nominal(mppi_ctx* c, float* out) {
+    if (!c || !out) return fail(c, MPPI_E_INVALID, "NULL argument");
+    CUDA_TRY(c, cudaMemcpyAsync(out, c->B.nominal, c->cfg.H * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+    return read_err_word(c);
+}
+
+int mppi_get_state(mppi_ctx* c, float* out) {
+    if (!c || !out) return fail(c, MPPI_E_INVALID, "NULL argument");
+    CUDA_TRY(c, cudaMemcpyAsync(out, c->B.state, 13 * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    return read_err_word(c);
+}
+
+int mppi_set_step_counter(mppi_ctx* c, uint64_t step) {
+    if (!c) return fail(nullptr, MPPI_E_INVALID, "ctx is NULL");
+    uint32_t* w = reinterpret_cast<uint32_t*>(c->h_in);
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    w[0] = static_cast<uint32_t>(step & 0xFFFFFFFFull);
+    w[1] = static_cast<uint32_t>(step >> 32);
+    CUDA_TRY(c, cudaMemcpyAsync(c->B.step, w, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->step_count = step;
+    return MPPI_OK;
+}
+
+uint64_t mppi_get_step_counter(const mppi_ctx* c) { return c ? c->step_count : 0; }
+
+int mppi_read_buffer(mppi_ctx* c, int which, float* host_out, size_t n) {
+    if (!c || !host_out) return fail(c, MPPI_E_INVALID, "NULL argument");
+    const size_t K = c->cfg.K, H = c->cfg.H;
+    const void* src = nullptr;
+    size_t count = 0;
+    switch (which) {
+        case MPPI_BUF_NOISE: src = c->B.noise; count = H * K * 4; break;
+        case MPPI_BUF_POSITIONS: src = c->B.pos; count = H * K * 4; break;
+        case MPPI_BUF_COST_PARTS: src = c->B.parts; count = 3 * K; break;
+        case MPPI_BUF_SDF: src = c->B.sdf; count = H * K; break;
+        case MPPI_BUF_WEIGHTS: src = c->B.w; count = K; break;
+        case MPPI_BUF_COSTS: src = c->B.J; count = K; break;
+        default: return fail(c, MPPI_E_INVALID, "unknown buffer %d", which);
+    }
+    if (n < count) return fail(c, MPPI_E_INVALID, "buffer %d needs %zu floats, got %zu", which, count, n);
+    CUDA_TRY(c, cudaMemcpyAsync(host_out, src, count * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    return read_err_word(c);
+}
+
+int mppi_read_noise_words(mppi_ctx* c, uint32_t* host_out, size_t n) {
+    if (!c || !host_out) return fail(c, MPPI_E_INVALID, "NULL argument");
+    const size_t count = static_cast<size_t>(c->cfg.K) * c->cfg.H * 4;
+    if (n < count) return fail(c, MPPI_E_INVALID, "needs %zu words, got %zu", count, n);
+    uint4* tmp = nullptr;
+    CUDA_TRY(c, cudaMalloc(&tmp, count * sizeof(uint32_t)));
+    const StepParams P = make_params(c);
+    cudaError_t e = launch_noise_words(P, c->B, tmp, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host_out, tmp, count * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return fail(c, MPPI_E_CUDA, "noise words: %s", cudaGetErrorString(e));
+    return MPPI_OK;
+}
+
+int mppi_set_timing(mppi_ctx* c, int enable) {
+    if (!c) return fail(nullptr, MPPI_E_INVALID, "ctx is NULL");
+    c->timing = enable != 0;
+    return MPPI_OK;
+}
+
+int mppi_get_kernel_times(mppi_ctx* c, const char** names, float* ms, int cap) {
+    if (!c) return fail(nullptr, MPPI_E_INVALID, "ctx is NULL");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    int n = 0;
+    for (int i = 1; i < c->n_ev && n < cap; ++i, ++n) {
+        float t = 0.f;
+        CUDA_TRY(c, cudaEventElapsedTime(&t, c->ev[i - 1], c->ev[i]));
+        if (names) names[n] = c->ev_names[i];
+        if (ms) ms[n] = t;
+    }
+    return n;
+}
+
+int mppi_kernels_per_step(const mppi_ctx* c) {
+    if (!c) return 0;
+    return is_mlp(c) ? 5 : 4;
+}
+
+int mppi_selftest_tc_gemm(const uint16_t* d_A, const uint16_t* d_B, float* d_D, void* stream) {
+    int dev = 0, major = 0, minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, MPPI_E_UNSUPPORTED, "no CUDA device");
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10 || minor != 3) return fail(nullptr, MPPI_E_UNSUPPORTED, "device is sm_%d%d", major, minor);
+    if (!d_A || !d_B || !d_D) return fail(nullptr, MPPI_E_INVALID, "NULL argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int* derr = nullptr;
+    if (cudaMalloc(&derr, sizeof(int)) != cudaSuccess) return fail(nullptr, MPPI_E_OOM, "cudaMalloc failed");
+    cudaError_t e = cudaMemsetAsync(derr, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = launch_tc_selftest(d_A, d_B, d_D, derr, s);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(derr);
+    if (e != cudaSuccess) return fail(nullptr, MPPI_E_CUDA, "self-test: %s", cudaGetErrorString(e));
+    if (herr != 0) return fail(nullptr, MPPI_E_TIMEOUT, "self-test wait timed out");
+    return MPPI_OK;
+}
+
+}  // extern "C"
+
+namespace mppi {
+uint16_t float_to_bf16(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u) return static_cast<uint16_t>(u >> 16);   // inf / nan (inputs are finite)
+    const uint32_t rounding = 0x7FFFu + ((u >> 16) & 1u);                           // round to nearest even
+    return static_cast<uint16_t>((u + rounding) >> 16);
+}
+}  // namespace mppi

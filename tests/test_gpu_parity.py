@@ -1,0 +1,337 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle.
+
+Tolerances (stated once, used throughout):
+* Philox words: bit-exact.
+* Normals: |delta_gpu - delta_oracle| <= 4e-6 * sigma * max(1, |n|) -- FP32 log/sqrt/sincospi
+  of exact uniforms are a few ulp (ulp(6) = 4.8e-7).
+* Positions: 5e-5 m after up to 50 RK4 steps in FP32 (|p| <= ~20 m).
+* Costs (FP32 paths): |J_gpu - J| <= 1e-4 * (|J_col| + |J_prog| + |J_ctl|) per rollout,
+  i.e. 1e-4 relative to the magnitude of the summed terms.
+* Updated controls (FP32 paths): |U*_gpu - U*| <= 1e-4 absolute (N, rad/s).
+* BF16 path: SDF error (mm), cost and control errors are reported; the test
+  only bounds them loosely (a layout or descriptor bug gives errors of 100s of mm).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import mppi as O
+from oracle import noise as ON
+from paper_2603_07199_gb300 import binding as B
+
+from .gpu_helpers import GpuController, cost_scale
+
+pytestmark = pytest.mark.gpu
+
+COST_RTOL = 1e-4
+CTRL_ATOL = 1e-4
+POS_ATOL = 5e-5
+
+
+def _params(wl, **over):
+    d = dict(wl["params"])
+    d.update(over)
+    return d
+
+
+def _oracle(wl, prm, state, nominal, step, mlp):
+    return O.mppi_step(state, nominal, wl["poses"], O.Params(**prm), step,
+                       wl["latents"] if mlp else None, wl["layers"] if mlp else None)
+
+
+def _check_costs(gpu_J, ref, rtol=COST_RTOL):
+    err = np.abs(gpu_J.astype(np.float64) - ref["J"])
+    bound = rtol * cost_scale(ref) + 1e-7
+    assert np.all(err <= bound), f"max cost err {err.max():.3e}, worst ratio {np.max(err / bound):.2f}"
+
+
+def _report(name, data):
+    os.makedirs("gpurun_out", exist_ok=True)
+    with open(os.path.join("gpurun_out", "parity_report.jsonl"), "a") as f:
+        f.write(json.dumps(dict(test=name, **data)) + "\n")
+
+
+# ---------------------------------------------------------------- tensor-core building block
+def test_tc_selftest_gemm(lib):
+    import torch
+    g = torch.Generator().manual_seed(0)
+    A = torch.randn(128, 128, generator=g).to(torch.bfloat16)
+    Bm = torch.randn(128, 128, generator=g).to(torch.bfloat16)
+    dA, dB = A.cuda(), Bm.cuda()
+    dD = torch.zeros(128, 128, dtype=torch.float32, device="cuda")
+    B.mppi_selftest_tc_gemm(dA.view(torch.int16), dB.view(torch.int16), dD)
+    ref = A.double() @ Bm.double().T
+    scale = A.double().abs() @ Bm.double().abs().T
+    err = (dD.cpu().double() - ref).abs()
+    assert torch.all(err <= 1e-6 * scale + 1e-6), float(err.max())
+
+
+# ---------------------------------------------------------------- (a) noise
+@pytest.mark.parametrize("K,H,step,drone", [(300, 7, 123456789 + 3 * 2**32, 5), (1, 1, 0, 0), (129, 3, 7, 2**31 + 1)])
+def test_noise_words_bit_exact(lib, K, H, step, drone):
+    wl = W.hover_gate()
+    prm = _params(wl, K=K, H=H, seed=0x1234567890ABCDEF, drone_id=drone)
+    g = GpuController(wl, "analytic", prm)
+    B.mppi_set_step_counter(g.ctx, step)
+    words = g.noise_words()
+    ref = ON.philox_words(K, H, prm["seed"], step, drone)
+    np.testing.assert_array_equal(words, ref)
+    g.close()
+
+
+def test_noise_values(lib):
+    wl = W.hover_gate()
+    prm = _params(wl, K=1000, H=9, seed=99)
+    g = GpuController(wl, "analytic", prm)
+    B.mppi_set_step_counter(g.ctx, 41)
+    g.step(state=wl["state"], nominal=W.hover_nominal(9))
+    d = g.read(B.MPPI_BUF_NOISE).astype(np.float64)
+    n = ON.standard_normals(ON.philox_words(1000, 9, 99, 41, 0))
+    sig = np.array([prm["sigma_thrust"], prm["sigma_rate"], prm["sigma_rate"], prm["sigma_rate"]])
+    err = np.abs(d - n * sig)
+    assert np.all(err <= 4e-6 * sig * np.maximum(1.0, np.abs(n))), err.max()
+    g.close()
+
+
+# ---------------------------------------------------------------- whole step, analytic SDF
+def _compare_step(g, wl, prm, state, nominal, step, mlp, check_sdf_atol=None):
+    out = g.step(state=state, nominal=nominal)
+    ref = _oracle(wl, prm, state, nominal, step, mlp)
+    pos = g.read(B.MPPI_BUF_POSITIONS)[..., :3].astype(np.float64)
+    np.testing.assert_allclose(pos, ref["positions"], atol=POS_ATOL, rtol=0)
+    parts = g.read(B.MPPI_BUF_COST_PARTS).astype(np.float64)
+    scale = cost_scale(ref) + 1e-7
+    for i, key in enumerate(("J_col", "J_prog", "J_ctl")):
+        assert np.all(np.abs(parts[i] - ref[key]) <= COST_RTOL * scale), key
+    if check_sdf_atol is not None:
+        s = g.read(B.MPPI_BUF_SDF).astype(np.float64)
+        np.testing.assert_allclose(s, ref["sdf"], atol=check_sdf_atol, rtol=0)
+    _check_costs(out["J"], ref)
+    np.testing.assert_allclose(out["U_new"], ref["U_new"], atol=CTRL_ATOL, rtol=0)
+    assert abs(float(out["weights"].astype(np.float64).sum()) - 1.0) < 1e-5
+    return out, ref
+
+
+def test_step_hover_gate_analytic(lib):
+    wl = W.hover_gate()
+    g = GpuController(wl, "analytic")
+    out, ref = _compare_step(g, wl, wl["params"], wl["state"], wl["nominal"], 0, False)
+    np.testing.assert_allclose(out["weights"], ref["weights"], atol=1e-5)
+    g.close()
+
+
+def test_closed_loop_hover_gate_teacher_forced(lib):
+    """10 closed-loop steps; each step's oracle starts from the GPU's own state and warm start."""
+    wl = W.hover_gate()
+    prm = wl["params"]
+    g = GpuController(wl, "analytic")
+    state, nominal = wl["state"], wl["nominal"]
+    free = O.closed_loop(wl["state"], wl["nominal"], wl["poses"], O.Params(**prm), 10)[0]
+    worst = 0.0
+    for step in range(10):
+        s_gpu = g.state() if step > 0 else state
+        n_gpu = g.nominal() if step > 0 else nominal
+        out = g.step(state=None if step > 0 else state, nominal=None if step > 0 else nominal)
+        ref = _oracle(wl, prm, s_gpu, n_gpu, step, False)
+        _check_costs(out["J"], ref)
+        np.testing.assert_allclose(out["U_new"], ref["U_new"], atol=CTRL_ATOL, rtol=0)
+        worst = max(worst, float(np.max(np.abs(out["U_new"] - free[step]["U_new"]))))
+    _report("closed_loop_hover_gate_free_running", dict(max_abs_control_divergence=worst))
+    # the plant update on the device equals one oracle RK4 step of U*_new[0]
+    g.close()
+
+
+def test_plant_update_and_shift(lib):
+    wl = W.hover_gate()
+    g = GpuController(wl, "analytic")
+    out = g.step(state=wl["state"], nominal=wl["nominal"])
+    st = g.state().astype(np.float64)
+    from oracle import dynamics as D
+    prm = wl["params"]
+    ref = D.plant_step(wl["state"], out["U_new"][0].astype(np.float64), prm["dt"], prm["mass"], prm["gravity"])
+    np.testing.assert_allclose(st, ref, atol=2e-6)
+    nom = g.nominal()
+    np.testing.assert_array_equal(nom[:-1], out["U_new"][1:])
+    np.testing.assert_allclose(nom[-1], [np.float32(prm["mass"] * prm["gravity"]), 0, 0, 0])
+    assert B.mppi_get_step_counter(g.ctx) == 1
+    g.close()
+
+
+# ---------------------------------------------------------------- edge cases
+@pytest.mark.parametrize("K,H", [(1, 1), (2, 1), (129, 3), (257, 2)])
+def test_small_and_ragged_sizes_analytic(lib, K, H):
+    wl = W.hover_gate()
+    prm = _params(wl, K=K, H=H)
+    g = GpuController(wl, "analytic", prm)
+    out, ref = _compare_step(g, wl, prm, W.hover_state([-0.3, 0.1, 0.45]), W.hover_nominal(H), 0, False)
+    if K == 1:
+        assert out["weights"][0] == 1.0
+    g.close()
+
+
+def test_no_gates(lib):
+    wl = dict(W.hover_gate())
+    wl["poses"] = np.zeros((0, 7), dtype=np.float32)
+    wl["latents"] = np.zeros((0, 64), dtype=np.float32)
+    prm = _params(wl, K=200, H=4)
+    g = GpuController(wl, "analytic", prm)
+    out = g.step(state=W.hover_state([0, 0, 0]), nominal=W.hover_nominal(4))
+    parts = g.read(B.MPPI_BUF_COST_PARTS)
+    assert np.all(parts[0] == 0) and np.all(parts[1] == 0)
+    ref = _oracle(wl, prm, W.hover_state([0, 0, 0]), W.hover_nominal(4), 0, False)
+    np.testing.assert_allclose(out["U_new"], ref["U_new"], atol=CTRL_ATOL)
+    g.close()
+
+
+def test_zero_noise_and_tiny_lambda(lib):
+    wl = W.hover_gate()
+    prm = _params(wl, K=64, H=5, sigma_thrust=0.0, sigma_rate=0.0)
+    g = GpuController(wl, "analytic", prm)
+    out = g.step(state=wl["state"], nominal=W.hover_nominal(5))
+    np.testing.assert_allclose(out["weights"], 1.0 / 64, rtol=1e-6)
+    np.testing.assert_allclose(out["U_new"], W.hover_nominal(5), rtol=1e-6)
+    g.close()
+    prm = _params(wl, K=64, H=5, lam=1e-6)
+    g = GpuController(wl, "analytic", prm)
+    out = g.step(state=wl["state"], nominal=W.hover_nominal(5))
+    ref = _oracle(wl, prm, wl["state"], W.hover_nominal(5), 0, False)
+    k = int(np.argmin(ref["J"]))
+    assert int(np.argmax(out["weights"])) == k
+    np.testing.assert_allclose(out["U_new"], ref["U"][k], atol=CTRL_ATOL)
+    g.close()
+
+
+def test_errors_leave_context_usable(lib):
+    wl = W.hover_gate()
+    g = GpuController(wl, "analytic")
+    bad = wl["state"].copy()
+    bad[4] = np.nan
+    with pytest.raises(B.MppiError) as e:
+        g.step(state=bad, nominal=wl["nominal"])
+    assert e.value.code == B.MPPI_E_INVALID
+    with pytest.raises(B.MppiError) as e:
+        B.mppi_set_gates(g.ctx, 5, np.zeros((5, 7), np.float32), None)
+    assert e.value.code == B.MPPI_E_INVALID
+    _compare_step(g, wl, wl["params"], wl["state"], wl["nominal"], 0, False)
+    g.close()
+    cfg = B.mppi_config_default()
+    cfg.K = 0
+    with pytest.raises(B.MppiError):
+        B.mppi_create(cfg)
+    cfg = B.mppi_config_default()
+    cfg.sdf_mode = B.MPPI_SDF_MLP_FP32
+    ctx = B.mppi_create(cfg)
+    with pytest.raises(B.MppiError) as e:
+        B.mppi_step(ctx, None, None, None, None, np.zeros((20, 4), np.float32))
+    assert e.value.code == B.MPPI_E_NOT_READY
+    B.mppi_destroy(ctx)
+
+
+def test_reruns_are_bit_identical(lib):
+    wl = W.two_gate_mlp()
+    prm = _params(wl, K=512, H=8)
+    outs = []
+    for mode in ("bf16", "bf16", "fp32", "fp32"):
+        g = GpuController(wl, mode, prm)
+        outs.append(g.step(state=wl["state"], nominal=W.hover_nominal(8)))
+        g.close()
+    for a, b in ((0, 1), (2, 3)):
+        for key in ("U_new", "weights", "J"):
+            np.testing.assert_array_equal(outs[a][key], outs[b][key])
+
+
+def test_async_device_path_matches_host_path(lib):
+    import torch
+    wl = W.two_gate_mlp()
+    prm = _params(wl, K=300, H=6)
+    g1 = GpuController(wl, "bf16", prm)
+    ref = g1.step(state=wl["state"], nominal=W.hover_nominal(6))
+    g1.close()
+    g2 = GpuController(wl, "bf16", prm)
+    dev = torch.device("cuda")
+    st = torch.from_numpy(wl["state"]).to(dev)
+    nom = torch.from_numpy(W.hover_nominal(6)).to(dev)
+    U = torch.zeros(6, 4, device=dev)
+    w = torch.zeros(300, device=dev)
+    J = torch.zeros(300, device=dev)
+    B.mppi_step_async(g2.ctx, st, None, None, nom, U, w, J)
+    B.mppi_sync(g2.ctx)
+    np.testing.assert_array_equal(U.cpu().numpy(), ref["U_new"])
+    np.testing.assert_array_equal(w.cpu().numpy(), ref["weights"])
+    np.testing.assert_array_equal(J.cpu().numpy(), ref["J"])
+    g2.close()
+
+
+# ---------------------------------------------------------------- Gate-SDF MLP, FP32 path
+@pytest.mark.parametrize("K,H", [(300, 6), (129, 2), (1, 3)])
+def test_step_mlp_fp32_small(lib, K, H):
+    wl = W.two_gate_mlp()
+    prm = _params(wl, K=K, H=H)
+    g = GpuController(wl, "fp32", prm)
+    _compare_step(g, wl, prm, wl["state"], W.hover_nominal(H), 0, True, check_sdf_atol=2e-5)
+    g.close()
+
+
+def test_step_mlp_fp32_full_size_two_gates(lib):
+    """K=4096, H=50, G=2: every rollout's cost and the controls against the oracle."""
+    wl = W.two_gate_mlp()
+    g = GpuController(wl, "fp32")
+    out, ref = _compare_step(g, wl, wl["params"], wl["state"], wl["nominal"], 0, True, check_sdf_atol=2e-5)
+    _report("fp32_full_size", dict(max_abs_control_err=float(np.max(np.abs(out["U_new"] - ref["U_new"]))),
+                                   max_rel_cost_err=float(np.max(np.abs(out["J"] - ref["J"]) / cost_scale(ref)))))
+    g.close()
+
+
+def test_closed_loop_mlp_fp32_teacher_forced(lib):
+    wl = W.two_gate_mlp()
+    prm = _params(wl, K=1024, H=20)
+    g = GpuController(wl, "fp32", prm)
+    state, nominal = wl["state"], W.hover_nominal(20)
+    for step in range(4):
+        s_gpu = g.state() if step > 0 else state
+        n_gpu = g.nominal() if step > 0 else nominal
+        out = g.step(state=None if step > 0 else state, nominal=None if step > 0 else nominal)
+        ref = _oracle(wl, prm, s_gpu, n_gpu, step, True)
+        _check_costs(out["J"], ref)
+        np.testing.assert_allclose(out["U_new"], ref["U_new"], atol=CTRL_ATOL, rtol=0)
+    g.close()
+
+
+# ---------------------------------------------------------------- Gate-SDF MLP, BF16 tensor-core path
+def _bf16_errors(g, ref, out):
+    s = g.read(B.MPPI_BUF_SDF).astype(np.float64)
+    e = np.abs(s - ref["sdf"]) * 1000.0
+    return dict(sdf_mae_mm=float(e.mean()), sdf_p99_mm=float(np.percentile(e, 99)), sdf_max_mm=float(e.max()),
+                cost_rel_max=float(np.max(np.abs(out["J"] - ref["J"]) / (cost_scale(ref) + 1e-7))),
+                control_abs_max=float(np.max(np.abs(out["U_new"] - ref["U_new"]))))
+
+
+@pytest.mark.parametrize("K,H", [(300, 6), (129, 2)])
+def test_step_mlp_bf16_small(lib, K, H):
+    wl = W.two_gate_mlp()
+    prm = _params(wl, K=K, H=H)
+    g = GpuController(wl, "bf16", prm)
+    out = g.step(state=wl["state"], nominal=W.hover_nominal(H))
+    ref = _oracle(wl, prm, wl["state"], W.hover_nominal(H), 0, True)
+    pos = g.read(B.MPPI_BUF_POSITIONS)[..., :3].astype(np.float64)
+    np.testing.assert_allclose(pos, ref["positions"], atol=POS_ATOL, rtol=0)
+    err = _bf16_errors(g, ref, out)
+    _report(f"bf16_K{K}_H{H}", err)
+    assert err["sdf_mae_mm"] < 10.0 and err["sdf_max_mm"] < 60.0, err
+    g.close()
+
+
+def test_step_mlp_bf16_full_size_two_gates(lib):
+    """The bench configuration (K=4096, H=50, G=2, BF16): errors against the FP64 oracle."""
+    wl = W.two_gate_mlp()
+    g = GpuController(wl, "bf16")
+    out = g.step(state=wl["state"], nominal=wl["nominal"])
+    ref = _oracle(wl, wl["params"], wl["state"], wl["nominal"], 0, True)
+    err = _bf16_errors(g, ref, out)
+    _report("bf16_full_size", err)
+    assert err["sdf_mae_mm"] < 10.0, err
+    assert abs(float(out["weights"].astype(np.float64).sum()) - 1.0) < 1e-5
+    g.close()
