@@ -236,7 +236,10 @@ def run_ours(args):
 
     wl = workload()
     K, H, G = wl["params"]["K"], wl["params"]["H"], wl["poses"].shape[0]
+    # a dedicated stream shared by torch (flush, events) and the library (its kernels)
+    torch.cuda.set_stream(torch.cuda.Stream(device=dev))
     stream = torch.cuda.current_stream().cuda_stream
+    assert stream != 0
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     ctx = make_ctx(B, wl, "bf16", stream, drone_id=rank)

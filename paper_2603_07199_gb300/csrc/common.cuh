@@ -41,8 +41,8 @@ struct StepBuffers {
     float* J;              // [K]
     float* w;              // [K]
     float4* unew;          // [H] updated sequence U*_new
-    float* red;            // [>= nblocks] per-block minima
-    float* stats;          // [4] rho, eta
+    float* red;            // [2 * cost blocks] per-block (min J, sum exp) partials
+    float* stats;          // [4] rho, eta of the last step
     unsigned* tickets;     // [4] last-block counters
     int* err;              // [1] device error word
 };

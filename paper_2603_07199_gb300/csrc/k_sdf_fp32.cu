@@ -157,15 +157,13 @@ constexpr size_t kSmemBytes = sizeof(float) * (kHidden * kLdA + kHidden * kHidde
 
 }  // namespace
 
+cudaError_t configure_sdf_mlp_fp32() {
+    return cudaFuncSetAttribute(sdf_mlp_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kSmemBytes));
+}
+
 cudaError_t launch_sdf_mlp_fp32(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
                                 cudaStream_t s) {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(sdf_mlp_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(kSmemBytes));
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
     const int n_items = P.H * ((P.K + kTileRows - 1) / kTileRows);
     const int grid = n_items < num_sms ? n_items : num_sms;
     sdf_mlp_fp32_kernel<<<grid, kThreads, kSmemBytes, s>>>(P, B, W);

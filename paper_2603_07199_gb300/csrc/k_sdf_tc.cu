@@ -8,10 +8,17 @@
 // and keeps the running minimum over gates in a register; the item ends by
 // storing that minimum s(p) for the 128 states of the tile.
 //
-// CTA = 2 epilogue warpgroups (one tile chain each, own A tile and own
+// CTA = 3 epilogue warpgroups (one tile chain each, own A tile and own
 // 128-column TMEM accumulator) + 1 MMA warp whose lane 0 issues the MMAs of
 // whichever warpgroup has its A tile ready.  W2..W4 (BF16, 96 KB) stay in
 // shared memory for the life of the persistent CTA.  Every wait is bounded.
+//
+// Activations are carried in log2 units: with c = beta log2(e) and y = c x,
+//   sp_beta(x) = (ln 2 / beta) h(y),   h(y) = log2(1 + 2^y) = max(y, 0) + log2(1 + 2^-|y|),
+// and c (ln 2 / beta) = 1, so the hidden weights are used unchanged while the
+// first layer and the hidden biases are scaled by c and the output weights by
+// ln 2 / beta.  h is evaluated with one hardware exp2 and a quartic in
+// e = 2^-|y| (see log2_1p_poly), in packed f32x2 arithmetic.
 #include "kernels.h"
 #include "tc.cuh"
 
@@ -19,11 +26,11 @@ namespace mppi {
 
 namespace {
 
-constexpr int kEpiWarpgroups = 2;
+constexpr int kEpiWarpgroups = 3;
 constexpr int kThreads = kEpiWarpgroups * 128 + 32;
 constexpr int kMmaWarp = kEpiWarpgroups * 4;
 constexpr uint32_t kTileBytes = kHidden * kHidden * 2;     // one 128 x 128 BF16 operand
-constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kIdesc = tc::idesc_bf16_f32(128, 128);
 
 struct __align__(16) TcShared {
@@ -40,11 +47,56 @@ struct __align__(16) TcShared {
     int abort_flag;
 };
 
-// Fast softplus for the BF16 chain: sp(x) = max(x, 0) + log2(1 + 2^(-beta log2(e) |x|)) ln(2) / beta,
-// with the hardware base-2 exponential and logarithm.
-__device__ __forceinline__ float softplus_fast(float x, float nbl2e, float ln2_beta) {
-    const float t = tc::ex2_approx(nbl2e * fabsf(x));
-    return fmaxf(x, 0.f) + tc::lg2_approx(1.f + t) * ln2_beta;
+// ---------------------------------------------------------------- packed f32x2 helpers
+__device__ __forceinline__ uint64_t pk(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 upk(uint64_t v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+// log2(1 + e) for e in [0, 1] as e (c1 + e (c2 + e (c3 + e c4))) with c1 = 1 / ln 2
+// exact and c2..c4 a weighted least-squares (near-minimax) fit made for this
+// kernel: max abs error 2.1e-4, relative error 1.4e-4 as e -> 0 (below the
+// BF16 rounding of the activations it feeds).
+constexpr float kL1 = 1.4426950408889634f;
+constexpr float kL2 = -0.69991479f;
+constexpr float kL3 = 0.35777588f;
+constexpr float kL4 = -0.10076641f;
+
+// Two activations at once: h(y) = max(y, 0) + log2(1 + 2^-|y|) for y = acc + bias.
+__device__ __forceinline__ uint32_t softplus2_log2_bf16(float a0, float a1, uint64_t bias2) {
+    const float2 y = upk(add2(pk(a0, a1), bias2));
+    const uint64_t e = pk(tc::ex2_approx(-fabsf(y.x)), tc::ex2_approx(-fabsf(y.y)));
+    uint64_t p = fma2(e, pk(kL4, kL4), pk(kL3, kL3));
+    p = fma2(e, p, pk(kL2, kL2));
+    p = fma2(e, p, pk(kL1, kL1));
+    const uint64_t g = mul2(e, p);
+    const float2 h = upk(add2(pk(fmaxf(y.x, 0.f), fmaxf(y.y, 0.f)), g));
+    return tc::pack_bf16x2(h.x, h.y);
+}
+__device__ __forceinline__ float softplus_log2(float y) {
+    const float e = tc::ex2_approx(-fabsf(y));
+    return fmaxf(y, 0.f) + e * fmaf(e, fmaf(e, fmaf(e, kL4, kL3), kL2), kL1);
 }
 
 __device__ __forceinline__ int items_of_slot(int slot, int nslots, int n_items) {
@@ -76,13 +128,14 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_bf16_kernel(StepParams P,
         uint4* dst = reinterpret_cast<uint4*>(S.w[l]);
         for (int i = tid; i < int(kTileBytes / 16); i += kThreads) dst[i] = __ldg(src + i);
     }
+    const float cl2 = P.beta * 1.4426950408889634f;          // beta log2(e)
     for (int i = tid; i < 3 * kHidden; i += kThreads) {
         const int j = i / kHidden, n = i - j * kHidden;
-        S.w1[j][n] = W.W1[n * (3 + kLatent) + j];
-        S.bias[j][n] = W.b[j][n];
+        S.w1[j][n] = cl2 * W.W1[n * (3 + kLatent) + j];
+        S.bias[j][n] = cl2 * W.b[j][n];
     }
-    for (int i = tid; i < G * kHidden; i += kThreads) S.b1[i / kHidden][i % kHidden] = B.b1p[i];
-    for (int i = tid; i < kHidden; i += kThreads) S.w5[i] = W.w5[i];
+    for (int i = tid; i < G * kHidden; i += kThreads) S.b1[i / kHidden][i % kHidden] = cl2 * B.b1p[i];
+    for (int i = tid; i < kHidden; i += kThreads) S.w5[i] = (0.69314718055994531f / P.beta) * W.w5[i];
     for (int i = tid; i < G * 8; i += kThreads) S.pose[i / 8][i % 8] = B.poses[i];
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
@@ -161,8 +214,6 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_bf16_kernel(StepParams P,
                                static_cast<uint32_t>(wg * kHidden);
         const uint32_t act_bar = tc::smem_u32(&S.act_full[wg]);
         const uint32_t acc_bar = tc::smem_u32(&S.acc_full[wg]);
-        const float nbl2e = -P.beta * 1.4426950408889634f;
-        const float ln2_beta = 0.69314718055994531f / P.beta;
         uint32_t acc_phase = 0;
         bool ok = true;
 
@@ -174,18 +225,21 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_bf16_kernel(StepParams P,
             for (int g = 0; g < G && ok; ++g) {
                 // layer 1: a_c = b1'_g[c] + W1[c, 0:3] . p_g  -> softplus -> BF16 row of the A tile
                 const Vec3 pg = to_gate(S.pose[g], v3(p.x, p.y, p.z));
+                const uint64_t px = pk(pg.x, pg.x), py = pk(pg.y, pg.y), pz = pk(pg.z, pg.z);
 #pragma unroll 2
                 for (int c = 0; c < kHidden; c += 8) {
-                    float y[8];
+                    uint32_t o[4];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int n = c + j;
-                        const float a = S.b1[g][n] + S.w1[0][n] * pg.x + S.w1[1][n] * pg.y + S.w1[2][n] * pg.z;
-                        y[j] = softplus_fast(a, nbl2e, ln2_beta);
+                    for (int j = 0; j < 4; ++j) {
+                        const int n = c + 2 * j;
+                        uint64_t a = fma2(pk(S.w1[0][n], S.w1[0][n + 1]), px,
+                                          pk(S.b1[g][n], S.b1[g][n + 1]));
+                        a = fma2(pk(S.w1[1][n], S.w1[1][n + 1]), py, a);
+                        a = fma2(pk(S.w1[2][n], S.w1[2][n + 1]), pz, a);
+                        const float2 af = upk(a);
+                        o[j] = softplus2_log2_bf16(af.x, af.y, pk(0.f, 0.f));
                     }
-                    tc::st_shared_v4(a_base + tc::operand_offset_bytes(row, c), tc::pack_bf16x2(y[0], y[1]),
-                                     tc::pack_bf16x2(y[2], y[3]), tc::pack_bf16x2(y[4], y[5]),
-                                     tc::pack_bf16x2(y[6], y[7]));
+                    tc::st_shared_v4(a_base + tc::operand_offset_bytes(row, c), o[0], o[1], o[2], o[3]);
                 }
                 tc::fence_proxy_async_smem();
                 tc::named_barrier(1 + wg, 128);
@@ -209,20 +263,19 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_bf16_kernel(StepParams P,
                         if (l < 2) {
 #pragma unroll
                             for (int j = 0; j < 32; j += 8) {
-                                float y[8];
-#pragma unroll
-                                for (int e = 0; e < 8; ++e)
-                                    y[e] = softplus_fast(__uint_as_float(v[j + e]) + S.bias[l][ch + j + e], nbl2e,
-                                                         ln2_beta);
-                                tc::st_shared_v4(a_base + tc::operand_offset_bytes(row, ch + j),
-                                                 tc::pack_bf16x2(y[0], y[1]), tc::pack_bf16x2(y[2], y[3]),
-                                                 tc::pack_bf16x2(y[4], y[5]), tc::pack_bf16x2(y[6], y[7]));
+                                const float4 b0 = *reinterpret_cast<const float4*>(&S.bias[l][ch + j]);
+                                const float4 b1 = *reinterpret_cast<const float4*>(&S.bias[l][ch + j + 4]);
+                                tc::st_shared_v4(
+                                    a_base + tc::operand_offset_bytes(row, ch + j),
+                                    softplus2_log2_bf16(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), pk(b0.x, b0.y)),
+                                    softplus2_log2_bf16(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]), pk(b0.z, b0.w)),
+                                    softplus2_log2_bf16(__uint_as_float(v[j + 4]), __uint_as_float(v[j + 5]), pk(b1.x, b1.y)),
+                                    softplus2_log2_bf16(__uint_as_float(v[j + 6]), __uint_as_float(v[j + 7]), pk(b1.z, b1.w)));
                             }
                         } else {
 #pragma unroll
                             for (int j = 0; j < 32; ++j)
-                                s = fmaf(S.w5[ch + j],
-                                         softplus_fast(__uint_as_float(v[j]) + S.bias[2][ch + j], nbl2e, ln2_beta), s);
+                                s = fmaf(S.w5[ch + j], softplus_log2(__uint_as_float(v[j]) + S.bias[2][ch + j]), s);
                         }
                     }
                     tc::fence_before_sync();
@@ -316,15 +369,13 @@ constexpr size_t kSmemBytes = sizeof(TcShared) + 1024;
 
 }  // namespace
 
+cudaError_t configure_sdf_mlp_bf16() {
+    return cudaFuncSetAttribute(sdf_mlp_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kSmemBytes));
+}
+
 cudaError_t launch_sdf_mlp_bf16(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
                                 cudaStream_t s) {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(sdf_mlp_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(kSmemBytes));
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
     const int n_items = P.H * ((P.K + kTileRows - 1) / kTileRows);
     const int want = (n_items + kEpiWarpgroups - 1) / kEpiWarpgroups;
     const int grid = want < num_sms ? want : num_sms;

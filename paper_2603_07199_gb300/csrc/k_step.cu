@@ -35,6 +35,8 @@ __global__ void noise_words_kernel(StepParams P, const uint32_t* __restrict__ st
 // step clips U*_h + delta, accumulates the control cost, integrates RK4 and
 // stores the position as one float4 (coalesced across k).  In analytic mode
 // the frame SDF of every gate and the collision hinge are evaluated here too.
+constexpr int kPrefetch = 8;
+
 __global__ void __launch_bounds__(64) rollout_kernel(StepParams P, StepBuffers B, int analytic) {
     extern __shared__ float4 sU[];                 // [H]
     __shared__ float sPose[kMaxGates * 8];
@@ -62,23 +64,41 @@ __global__ void __launch_bounds__(64) rollout_kernel(StepParams P, StepBuffers B
 
     const float uh = P.mass * P.gravity;
     float jctl = 0.f, jcol = 0.f;
-    const int K = P.K;
-    for (int h = 0; h < P.H; ++h) {
-        const float4 d = B.noise[h * K + k];
-        const float4 un = sU[h];
-        const float4 u = clip_control(P, make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w));
-        const float e0 = u.x - uh;
-        jctl += e0 * e0 + u.y * u.y + u.z * u.z + u.w * u.w;
-        rk4_step(P, p, v, q, u.x, v3(u.y, u.z, u.w));
-        B.pos[h * K + k] = make_float4(p.x, p.y, p.z, 0.f);
-        if (analytic) {
-            float smin = __int_as_float(0x7f800000);
-            for (int g = 0; g < P.G; ++g) {
-                const Vec3 pg = to_gate(sPose + 8 * g, p);
-                smin = fminf(smin, frame_sdf(pg.x, pg.y, pg.z, P.a_in, P.a_out, P.half_depth));
-            }
-            jcol += hinge_sq(smin, P.d_safe);
+    const int K = P.K, H = P.H;
+    // The noise of the next kPrefetch steps is loaded while the current ones are
+    // integrated, so the load latency is not on the serial RK4 chain.
+    float4 cur[kPrefetch], nxt[kPrefetch];
+#pragma unroll
+    for (int j = 0; j < kPrefetch; ++j) cur[j] = (j < H) ? __ldcs(B.noise + j * K + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int h0 = 0; h0 < H; h0 += kPrefetch) {
+#pragma unroll
+        for (int j = 0; j < kPrefetch; ++j) {
+            const int hn = h0 + kPrefetch + j;
+            nxt[j] = (hn < H) ? __ldcs(B.noise + hn * K + k) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+#pragma unroll
+        for (int j = 0; j < kPrefetch; ++j) {
+            const int h = h0 + j;
+            if (h < H) {
+                const float4 d = cur[j];
+                const float4 un = sU[h];
+                const float4 u = clip_control(P, make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w));
+                const float e0 = u.x - uh;
+                jctl += e0 * e0 + u.y * u.y + u.z * u.z + u.w * u.w;
+                rk4_step(P, p, v, q, u.x, v3(u.y, u.z, u.w));
+                B.pos[h * K + k] = make_float4(p.x, p.y, p.z, 0.f);
+                if (analytic) {
+                    float smin = __int_as_float(0x7f800000);
+                    for (int g = 0; g < P.G; ++g) {
+                        const Vec3 pg = to_gate(sPose + 8 * g, p);
+                        smin = fminf(smin, frame_sdf(pg.x, pg.y, pg.z, P.a_in, P.a_out, P.half_depth));
+                    }
+                    jcol += hinge_sq(smin, P.d_safe);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kPrefetch; ++j) cur[j] = nxt[j];
     }
     const float jprog = (tgt >= 0) ? -(n_tgt.x * (p.x - p0.x) + n_tgt.y * (p.y - p0.y) + n_tgt.z * (p.z - p0.z))
                                    : 0.f;
@@ -87,48 +107,37 @@ __global__ void __launch_bounds__(64) rollout_kernel(StepParams P, StepBuffers B
     B.parts[2 * K + k] = P.w_u * jctl;
 }
 
-// ------------------------------------------------------------------ (d1) costs -> weights
+// ------------------------------------------------------------------ (d1) costs
 // J_k = J_col + J_prog + J_ctl (MLP modes: J_col = w_col sum_h max(0, d_safe - s_h)^2
-// over the stored SDF values, in order of h).  rho = min J, w~ = exp(-(J - rho) / lambda), eta = sum w~,
-// w = w~ / eta (Eq. 5).  The last block to finish computes rho, eta and w, so
-// the reduction order is fixed and reruns are bit-identical.
-constexpr int kRedThreads = 256;
+// over the stored SDF values, in order of h).  Each block also leaves the
+// partial (m_b, s_b) = (min_{k in b} J_k, sum_{k in b} exp(-(J_k - m_b) / lambda)),
+// from which rho = min J and eta = sum exp(-(J - rho) / lambda) of Eq. 5 follow
+// without another pass (online softmax).  Fixed reduction order: reruns are
+// bit-identical.
+constexpr int kCostThreads = 128;
 
-__device__ __forceinline__ float block_min(float x, float* sh) {
-    sh[threadIdx.x] = x;
-    __syncthreads();
-    for (int s = kRedThreads / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) sh[threadIdx.x] = fminf(sh[threadIdx.x], sh[threadIdx.x + s]);
-        __syncthreads();
-    }
-    const float r = sh[0];
-    __syncthreads();
-    return r;
+__device__ __forceinline__ float warp_min(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
 }
 
-__device__ __forceinline__ float block_sum(float x, float* sh) {
-    sh[threadIdx.x] = x;
-    __syncthreads();
-    for (int s = kRedThreads / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-        __syncthreads();
-    }
-    const float r = sh[0];
-    __syncthreads();
-    return r;
-}
-
-__global__ void __launch_bounds__(kRedThreads) cost_weights_kernel(StepParams P, StepBuffers B, int mlp) {
-    __shared__ float sh[kRedThreads];
-    __shared__ int is_last;
+__global__ void __launch_bounds__(kCostThreads) cost_kernel(StepParams P, StepBuffers B, int mlp) {
+    __shared__ float sh[kCostThreads / 32];
     const int K = P.K;
-    const int k = blockIdx.x * kRedThreads + threadIdx.x;
+    const int k = blockIdx.x * kCostThreads + threadIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float J = __int_as_float(0x7f800000);
     if (k < K) {
         float jcol;
         if (mlp) {
             float acc = 0.f;
-            for (int h = 0; h < P.H; ++h) acc += hinge_sq(B.sdf[h * K + k], P.d_safe);
+            for (int h = 0; h < P.H; ++h) acc += hinge_sq(__ldcs(B.sdf + h * K + k), P.d_safe);
             jcol = P.w_col * acc;
             B.parts[k] = jcol;
         } else {
@@ -137,52 +146,63 @@ __global__ void __launch_bounds__(kRedThreads) cost_weights_kernel(StepParams P,
         J = jcol + B.parts[K + k] + B.parts[2 * K + k];
         B.J[k] = J;
     }
-    const float bmin = block_min(J, sh);
-    if (threadIdx.x == 0) {
-        B.red[blockIdx.x] = bmin;
-        __threadfence();
-        const unsigned t = atomicAdd(&B.tickets[0], 1u);
-        is_last = (t == gridDim.x - 1);
-    }
+    float m = warp_min(J);
+    if (lane == 0) sh[wid] = m;
     __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-
-    float m = __int_as_float(0x7f800000);
-    for (int b = threadIdx.x; b < gridDim.x; b += kRedThreads) m = fminf(m, __ldcg(&B.red[b]));
-    const float rho = block_min(m, sh);
-    const float inv_lam = 1.0f / P.lam;
-    float acc = 0.f;
-    for (int i = threadIdx.x; i < K; i += kRedThreads) {
-        const float wt = expf(-(__ldcg(&B.J[i]) - rho) * inv_lam);
-        B.w[i] = wt;
-        acc += wt;
-    }
-    const float eta = block_sum(acc, sh);
-    for (int i = threadIdx.x; i < K; i += kRedThreads) B.w[i] = B.w[i] / eta;
+    m = sh[0];
+#pragma unroll
+    for (int i = 1; i < kCostThreads / 32; ++i) m = fminf(m, sh[i]);
+    __syncthreads();
+    const float e = (k < K) ? expf(-(J - m) / P.lam) : 0.f;
+    float s = warp_sum(e);
+    if (lane == 0) sh[wid] = s;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        B.stats[0] = rho;
-        B.stats[1] = eta;
-        B.tickets[0] = 0u;
+        float t = sh[0];
+#pragma unroll
+        for (int i = 1; i < kCostThreads / 32; ++i) t += sh[i];
+        B.red[2 * blockIdx.x] = m;
+        B.red[2 * blockIdx.x + 1] = t;
     }
 }
 
-// ------------------------------------------------------------------ (d2) update + receding horizon
-// Block h: U*_new[h] = sum_k w_k clip(U*_h + delta_{k,h}) (Eq. 5), fixed-order
-// tree.  The last block applies U*_new[0] to the device-resident state with
-// one RK4 step, writes the shifted warm start and bumps the step counter.
+// ------------------------------------------------------------------ (d2) weights, update, receding horizon
+// Every block first combines the cost blocks' partials into rho and eta (same
+// fixed order in every block), then block h forms w_k = exp(-(J_k - rho) / lambda) / eta
+// and U*_new[h] = sum_k w_k clip(U*_h + delta_{k,h}) (Eq. 5) with a fixed-order
+// tree; block 0 also stores w.  The last block to finish applies U*_new[0] to
+// the device-resident state with one RK4 step, writes the shifted warm start
+// and bumps the step counter.
 constexpr int kUpdThreads = 256;
 
 __global__ void __launch_bounds__(kUpdThreads) update_plant_kernel(StepParams P, StepBuffers B) {
     __shared__ float4 sh[kUpdThreads];
+    __shared__ float s_rho, s_eta;
     __shared__ int is_last;
     const int h = blockIdx.x;
     const int K = P.K;
+    const int nb = (K + kCostThreads - 1) / kCostThreads;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        float m = __int_as_float(0x7f800000);
+        for (int b = lane; b < nb; b += 32) m = fminf(m, B.red[2 * b]);
+        const float rho = warp_min(m);
+        float s = 0.f;
+        for (int b = lane; b < nb; b += 32) s += B.red[2 * b + 1] * expf(-(B.red[2 * b] - rho) / P.lam);
+        const float eta = warp_sum(s);
+        if (lane == 0) {
+            s_rho = rho;
+            s_eta = eta;
+        }
+    }
+    __syncthreads();
+    const float rho = s_rho, eta = s_eta;
     const float4 un = B.nominal[h];
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int k = threadIdx.x; k < K; k += kUpdThreads) {
-        const float w = B.w[k];
-        const float4 d = B.noise[h * K + k];
+        const float w = expf(-(B.J[k] - rho) / P.lam) / eta;
+        if (h == 0) B.w[k] = w;
+        const float4 d = __ldcs(B.noise + h * K + k);
         const float4 u = clip_control(P, make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w));
         acc.x = fmaf(w, u.x, acc.x);
         acc.y = fmaf(w, u.y, acc.y);
@@ -202,6 +222,10 @@ __global__ void __launch_bounds__(kUpdThreads) update_plant_kernel(StepParams P,
     }
     if (threadIdx.x == 0) {
         B.unew[h] = sh[0];
+        if (h == 0) {
+            B.stats[0] = rho;
+            B.stats[1] = eta;
+        }
         __threadfence();
         const unsigned t = atomicAdd(&B.tickets[1], 1u);
         is_last = (t == gridDim.x - 1);
@@ -269,7 +293,7 @@ cudaError_t launch_rollout(const StepParams& P, const StepBuffers& B, int analyt
 }
 
 cudaError_t launch_cost_weights(const StepParams& P, const StepBuffers& B, int mlp, cudaStream_t s) {
-    cost_weights_kernel<<<(P.K + kRedThreads - 1) / kRedThreads, kRedThreads, 0, s>>>(P, B, mlp);
+    cost_kernel<<<(P.K + kCostThreads - 1) / kCostThreads, kCostThreads, 0, s>>>(P, B, mlp);
     return cudaGetLastError();
 }
 

@@ -22,6 +22,9 @@ struct MlpWeights {
     float b5;
     const uint16_t* Wbf[3]; // W2..W4 as BF16 in the tensor-core operand layout
 };
+// set the dynamic shared-memory limits (once per context, outside any stream capture)
+cudaError_t configure_sdf_mlp_fp32();
+cudaError_t configure_sdf_mlp_bf16();
 cudaError_t launch_sdf_mlp_fp32(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
                                 cudaStream_t s);
 cudaError_t launch_sdf_mlp_bf16(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,

@@ -42,6 +42,9 @@ struct mppi_ctx {
     // pinned staging
     float* h_in = nullptr;        // state(16) | nominal(H*4) | poses(maxG*8) | latents(maxG*64)
     float* h_out = nullptr;       // unew(H*4) | w(K) | J(K) | err(1)
+    // the step's kernels as one CUDA graph, re-captured when a launch argument changes
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_dirty = true;
     // timing
     cudaEvent_t ev[8] = {};
     int n_ev = 0;
@@ -160,7 +163,11 @@ MlpWeights make_weights(const mppi_ctx* c) {
 
 void record(mppi_ctx* c, const char* name) {
     if (!c->timing || c->n_ev >= 8) return;
-    cudaEventRecord(c->ev[c->n_ev], c->stream);
+    // while the step is being captured, an external event node is what records the event at replay
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(c->stream, &cs);
+    cudaEventRecordWithFlags(c->ev[c->n_ev], c->stream,
+                             cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault);
     c->ev_names[c->n_ev] = name;
     ++c->n_ev;
 }
@@ -189,6 +196,39 @@ int enqueue_kernels(mppi_ctx* c) {
     record(c, "cost_weights");
     CUDA_TRY(c, launch_update_plant(P, c->B, c->stream));
     record(c, "update_plant");
+    return MPPI_OK;
+}
+
+// Launch the step: replay the captured graph, capturing it first when the
+// launch arguments changed.  When the caller's stream is itself being
+// captured, the kernels are enqueued directly into the caller's capture.
+int launch_step(mppi_ctx* c) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CUDA_TRY(c, cudaStreamIsCapturing(c->stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return enqueue_kernels(c);
+    if (c->gexec == nullptr || c->graph_dirty) {
+        if (c->gexec) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        const int rc = enqueue_kernels(c);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (rc != MPPI_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(c, MPPI_E_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
+        const cudaError_t ei = cudaGraphInstantiate(&c->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            c->gexec = nullptr;
+            return fail(c, MPPI_E_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+        }
+        c->graph_dirty = false;
+    }
+    CUDA_TRY(c, cudaGraphLaunch(c->gexec, c->stream));
     return MPPI_OK;
 }
 
@@ -248,6 +288,7 @@ const char* mppi_last_error(const mppi_ctx* c) { return c ? c->err : g_thread_er
 void mppi_destroy(mppi_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
     for (void* p : c->allocations) cudaFree(p);
     if (c->h_in) cudaFreeHost(c->h_in);
     if (c->h_out) cudaFreeHost(c->h_out);
@@ -280,6 +321,10 @@ int mppi_create(const mppi_config* cfg, void* cuda_stream, mppi_ctx** out) {
     c->cfg = *cfg;
     c->device = dev;
     c->num_sms = sms;
+    if (configure_sdf_mlp_fp32() != cudaSuccess || configure_sdf_mlp_bf16() != cudaSuccess) {
+        delete c;
+        return fail(nullptr, MPPI_E_CUDA, "kernel attribute set-up failed: %s", cudaGetErrorString(cudaGetLastError()));
+    }
     if (cuda_stream) {
         c->stream = static_cast<cudaStream_t>(cuda_stream);
     } else {
@@ -291,7 +336,7 @@ int mppi_create(const mppi_config* cfg, void* cuda_stream, mppi_ctx** out) {
     }
     const int K = cfg->K, H = cfg->H, MG = cfg->max_gates;
     const size_t KH = static_cast<size_t>(K) * H;
-    const int nred = (K + 255) / 256;
+    const int nred = 2 * ((K + 127) / 128);
     StepBuffers& B = c->B;
     rc = MPPI_OK;
     rc = rc ? rc : dev_alloc(c, &B.state, 16);
@@ -382,6 +427,7 @@ int mppi_set_gates(mppi_ctx* c, int n_gates, const float* poses, const float* la
         hp[8 * g + 7] = 0.f;
     }
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (c->n_gates != n_gates) c->graph_dirty = true;
     c->n_gates = n_gates;
     if (n_gates > 0)
         CUDA_TRY(c, cudaMemcpyAsync(c->B.poses, hp, n_gates * 8 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
@@ -429,6 +475,7 @@ int mppi_set_sdf_weights(mppi_ctx* c, const float* const* layers, int n_layers, 
     }
     CUDA_TRY(c, cudaMemcpy(c->d_w5, layers[8], kHidden * sizeof(float), cudaMemcpyHostToDevice));
     c->b5 = layers[9][0];
+    c->graph_dirty = true;
     c->have_weights = true;
     int rc = recompute_b1p(c);
     if (rc != MPPI_OK) return rc;
@@ -475,7 +522,7 @@ int mppi_step(mppi_ctx* c, const float* state, const float* gate_poses, const fl
         CUDA_TRY(c, cudaMemcpyAsync(c->B.nominal, c->h_in + 16, H * sizeof(float4), cudaMemcpyHostToDevice,
                                     c->stream));
     }
-    rc = enqueue_kernels(c);
+    rc = launch_step(c);
     if (rc != MPPI_OK) return rc;
     float* ho = c->h_out;
     CUDA_TRY(c, cudaMemcpyAsync(ho, c->B.unew, H * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
@@ -517,7 +564,7 @@ int mppi_step_async(mppi_ctx* c, const float* d_state, const float* d_gate_poses
     if (rc != MPPI_OK) return rc;
     if (d_nominal)
         CUDA_TRY(c, cudaMemcpyAsync(c->B.nominal, d_nominal, H * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream));
-    rc = enqueue_kernels(c);
+    rc = launch_step(c);
     if (rc != MPPI_OK) return rc;
     if (d_new_controls)
         CUDA_TRY(c, cudaMemcpyAsync(d_new_controls, c->B.unew, H * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream));
@@ -596,6 +643,7 @@ int mppi_read_noise_words(mppi_ctx* c, uint32_t* host_out, size_t n) {
 
 int mppi_set_timing(mppi_ctx* c, int enable) {
     if (!c) return fail(nullptr, MPPI_E_INVALID, "ctx is NULL");
+    if (c->timing != (enable != 0)) c->graph_dirty = true;
     c->timing = enable != 0;
     return MPPI_OK;
 }
