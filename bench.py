@@ -128,7 +128,7 @@ def make_ctx(B, wl, mode, stream, drone_id):
     cfg.lam = prm["lam"]
     cfg.drone_id = drone_id
     cfg.max_gates = wl["poses"].shape[0]
-    cfg.sdf_mode = {"bf16": B.MPPI_SDF_MLP_BF16, "fp32": B.MPPI_SDF_MLP_FP32}[mode]
+    cfg.sdf_mode = {"bf16": B.MPPI_SDF_MLP_BF16, "fp32": B.MPPI_SDF_MLP_FP32, "fp16": B.MPPI_SDF_MLP_FP16}[mode]
     ctx = B.mppi_create(cfg, stream)
     keep = []
     for Wm, b in wl["layers"]:
@@ -267,6 +267,11 @@ def run_ours(args):
     e2e_ms, h2d, d2h = e2e_loop(torch, B, ctx, wl, args.e2e_steps, flush)
     B.mppi_destroy(ctx)
 
+    ctx16 = make_ctx(B, wl, "fp16", stream, drone_id=rank)
+    ms16 = device_loop(torch, B, ctx16, wl, args.steps, 3, flush, dev)
+    kt16 = kernel_times(torch, B, ctx16, 20, flush, wl, dev)
+    B.mppi_destroy(ctx16)
+
     ctx32 = make_ctx(B, wl, "fp32", stream, drone_id=rank)
     ms32 = device_loop(torch, B, ctx32, wl, args.fp32_steps, 3, flush, dev)
     kt32 = kernel_times(torch, B, ctx32, 5, flush, wl, dev)
@@ -299,6 +304,9 @@ def run_ours(args):
                        "mean": float(ms.mean()), "min": float(ms.min())},
         "fp32": {"value": K * H / (ms32.mean() * 1e-3), "p50_ms": float(np.percentile(ms32, 50)),
                  "p99_ms": float(np.percentile(ms32, 99)), "steps": args.fp32_steps, "kernel_ms": kt32},
+        "fp16": {"value": K * H / (ms16.mean() * 1e-3), "p50_ms": float(np.percentile(ms16, 50)),
+                 "p99_ms": float(np.percentile(ms16, 99)), "kernel_ms": kt16,
+                 "speedup_vs_fp32": float(ms32.mean() / ms16.mean())},
         "speedup_vs_fp32": float(ms32.mean() / ms.mean()),
         "p99_speedup_vs_fp32": float(np.percentile(ms32, 99) / np.percentile(ms, 99)),
         "sdf_queries_per_s": K * H * G / (t_sdf * 1e-3) if t_sdf else None,

@@ -53,6 +53,8 @@ extern "C" {
 #define MPPI_SDF_ANALYTIC  0    /* exact signed distance to the rectangular gate frame */
 #define MPPI_SDF_MLP_FP32  1    /* Gate-SDF MLP, FP32 on the CUDA cores (plain FP32 path) */
 #define MPPI_SDF_MLP_BF16  2    /* Gate-SDF MLP, hidden GEMMs in BF16 on tcgen05, FP32 accumulate */
+#define MPPI_SDF_MLP_FP16  3    /* Gate-SDF MLP, hidden GEMMs in FP16 on tcgen05, FP32 accumulate,
+                                   activations packed f16x2 between layers */
 
 /* Gate-SDF MLP shape: [p(3), z(MPPI_LATENT_DIM)] -> 4 x MPPI_HIDDEN softplus -> 1. */
 #define MPPI_LATENT_DIM 64

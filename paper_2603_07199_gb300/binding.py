@@ -22,6 +22,7 @@ MPPI_E_UNSUPPORTED = -6
 MPPI_SDF_ANALYTIC = 0
 MPPI_SDF_MLP_FP32 = 1
 MPPI_SDF_MLP_BF16 = 2
+MPPI_SDF_MLP_FP16 = 3
 
 MPPI_BUF_NOISE = 0
 MPPI_BUF_POSITIONS = 1

@@ -8,17 +8,21 @@
 // and keeps the running minimum over gates in a register; the item ends by
 // storing that minimum s(p) for the 128 states of the tile.
 //
-// CTA = 3 epilogue warpgroups (one tile chain each, own A tile and own
-// 128-column TMEM accumulator) + 1 MMA warp whose lane 0 issues the MMAs of
-// whichever warpgroup has its A tile ready.  W2..W4 (BF16, 96 KB) stay in
-// shared memory for the life of the persistent CTA.  Every wait is bounded.
+// CTA = 3 tile groups of 8 warps + 1 MMA warp.  A tile group owns one A tile
+// (smem) and one 128-column FP32 accumulator (TMEM); its warps w and w + 4
+// share TMEM lane quadrant w % 4 (rows 32 (w % 4) .. + 31) and split the 128
+// columns into halves.  Lane 0 of the MMA warp serves whichever group has its
+// A tile ready; each layer's GEMM is issued as two N = 64 halves with their
+// own completion barriers, so the first half's epilogue overlaps the second
+// half's MMAs.  W2..W4 (BF16, 96 KB) stay in shared memory for the life of the
+// persistent CTA.  Every wait is bounded.
 //
 // Activations are carried in log2 units: with c = beta log2(e) and y = c x,
 //   sp_beta(x) = (ln 2 / beta) h(y),   h(y) = log2(1 + 2^y) = max(y, 0) + log2(1 + 2^-|y|),
 // and c (ln 2 / beta) = 1, so the hidden weights are used unchanged while the
 // first layer and the hidden biases are scaled by c and the output weights by
 // ln 2 / beta.  h is evaluated with one hardware exp2 and a quartic in
-// e = 2^-|y| (see log2_1p_poly), in packed f32x2 arithmetic.
+// e = 2^-|y| (see kL1..kL4), in packed f32x2 arithmetic.
 #include "kernels.h"
 #include "tc.cuh"
 
@@ -26,23 +30,29 @@ namespace mppi {
 
 namespace {
 
-constexpr int kEpiWarpgroups = 3;
-constexpr int kThreads = kEpiWarpgroups * 128 + 32;
-constexpr int kMmaWarp = kEpiWarpgroups * 4;
+constexpr int kGroups = 3;                          // tile groups (tiles in flight per CTA)
+constexpr int kGroupWarps = 8;
+constexpr int kGroupThreads = kGroupWarps * 32;
+constexpr int kThreads = kGroups * kGroupThreads + 32;
+constexpr int kMmaWarp = kGroups * kGroupWarps;
+constexpr int kHalf = kHidden / 2;
 constexpr uint32_t kTileBytes = kHidden * kHidden * 2;     // one 128 x 128 BF16 operand
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kIdesc = tc::idesc_bf16_f32(128, 128);
+constexpr uint32_t kIdescHalf = tc::idesc_bf16_f32(128, kHalf);
+constexpr uint32_t kIdescFull = tc::idesc_bf16_f32(128, 128);
+constexpr uint32_t kIdescHalfF16 = tc::idesc_f16_f32(128, kHalf);
 
 struct __align__(16) TcShared {
     uint8_t w[3][kTileBytes];                 // W2, W3, W4 (B operands, N = out, K = in)
-    uint8_t a[kEpiWarpgroups][kTileBytes];    // activation tiles (A operands, M = rows, K = features)
-    float w1[3][kHidden];                     // W1[:, 0:3] transposed
-    float b1[kMaxGates][kHidden];             // per-gate first-layer bias
-    float bias[3][kHidden];                   // b2, b3, b4
-    float w5[kHidden];
+    uint8_t a[kGroups][kTileBytes];           // activation tiles (A operands, M = rows, K = features)
+    float w1[3][kHidden];                     // c W1[:, 0:3] transposed
+    float b1[kMaxGates][kHidden];             // c (per-gate first-layer bias)
+    float bias[3][kHidden];                   // c b2, c b3, c b4
+    float w5[kHidden];                        // (ln 2 / beta) w5
+    float part[kGroups][kTileRows];           // output-layer partial sums of the upper column half
     float pose[kMaxGates][8];
-    uint64_t act_full[kEpiWarpgroups];        // epilogue -> MMA: A tile written
-    uint64_t acc_full[kEpiWarpgroups];        // MMA -> epilogue: accumulator ready
+    uint64_t act_full[kGroups];               // epilogue -> MMA: A tile written
+    uint64_t acc_full[kGroups][2];            // MMA -> epilogue: accumulator half ready
     uint32_t tmem_base;
     int abort_flag;
 };
@@ -68,11 +78,6 @@ __device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
-__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
-    uint64_t r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
 
 // log2(1 + e) for e in [0, 1] as e (c1 + e (c2 + e (c3 + e c4))) with c1 = 1 / ln 2
 // exact and c2..c4 a weighted least-squares (near-minimax) fit made for this
@@ -84,28 +89,96 @@ constexpr float kL3 = 0.35777588f;
 constexpr float kL4 = -0.10076641f;
 
 // Two activations at once: h(y) = max(y, 0) + log2(1 + 2^-|y|) for y = acc + bias.
-__device__ __forceinline__ uint32_t softplus2_log2_bf16(float a0, float a1, uint64_t bias2) {
+__device__ __forceinline__ uint64_t softplus2_log2(float a0, float a1, uint64_t bias2) {
     const float2 y = upk(add2(pk(a0, a1), bias2));
     const uint64_t e = pk(tc::ex2_approx(-fabsf(y.x)), tc::ex2_approx(-fabsf(y.y)));
     uint64_t p = fma2(e, pk(kL4, kL4), pk(kL3, kL3));
     p = fma2(e, p, pk(kL2, kL2));
     p = fma2(e, p, pk(kL1, kL1));
-    const uint64_t g = mul2(e, p);
-    const float2 h = upk(add2(pk(fmaxf(y.x, 0.f), fmaxf(y.y, 0.f)), g));
+    return fma2(e, p, pk(fmaxf(y.x, 0.f), fmaxf(y.y, 0.f)));
+}
+__device__ __forceinline__ uint32_t softplus2_log2_bf16(float a0, float a1, uint64_t bias2) {
+    const float2 h = upk(softplus2_log2(a0, a1, bias2));
     return tc::pack_bf16x2(h.x, h.y);
 }
-__device__ __forceinline__ float softplus_log2(float y) {
-    const float e = tc::ex2_approx(-fabsf(y));
-    return fmaxf(y, 0.f) + e * fmaf(e, fmaf(e, fmaf(e, kL4, kL3), kL2), kL1);
+
+// ---------------------------------------------------------------- packed f16x2 epilogue (FP16 operand path)
+// The same h(y) with every step after the FP32 bias add in f16x2: one hardware
+// exp2 per two activations, the quartic as f16x2 FMAs (coefficients rounded to
+// f16), and the result is directly the FP16 A operand of the next layer.
+constexpr uint32_t kH1 = 0x3dc53dc5u;   // f16x2 of kL1
+constexpr uint32_t kH2 = 0xb999b999u;   // f16x2 of kL2
+constexpr uint32_t kH3 = 0x35b935b9u;   // f16x2 of kL3
+constexpr uint32_t kH4 = 0xae73ae73u;   // f16x2 of kL4
+
+__device__ __forceinline__ uint32_t hfma2(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t r;
+    asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+    return r;
+}
+__device__ __forceinline__ uint32_t hmax2_zero(uint32_t a) {
+    uint32_t r;
+    asm("max.f16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(0u));
+    return r;
+}
+__device__ __forceinline__ uint32_t hex2(uint32_t a) {
+    uint32_t r;
+    asm("ex2.approx.f16x2 %0, %1;" : "=r"(r) : "r"(a));
+    return r;
+}
+__device__ __forceinline__ uint32_t f32x2_to_f16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+__device__ __forceinline__ float2 f16x2_to_f32x2(uint32_t v) {
+    float2 r;
+    asm("{\n\t.reg .f16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\tcvt.f32.f16 %0, lo;\n\tcvt.f32.f16 %1, hi;\n\t}"
+        : "=f"(r.x), "=f"(r.y) : "r"(v));
+    return r;
+}
+__device__ __forceinline__ uint32_t softplus2_log2_f16(float y0, float y1) {
+    const uint32_t h = f32x2_to_f16x2(y0, y1);
+    const uint32_t e = hex2(h | 0x80008000u);              // 2^-|y|
+    uint32_t p = hfma2(e, kH4, kH3);
+    p = hfma2(e, p, kH2);
+    p = hfma2(e, p, kH1);
+    return hfma2(e, p, hmax2_zero(h));
+}
+
+// One 16-bit activation pair of the requested operand type.
+template <bool kF16>
+__device__ __forceinline__ uint32_t act_pair(float a0, float a1, uint64_t bias2) {
+    if constexpr (kF16) {
+        const float2 y = upk(add2(pk(a0, a1), bias2));
+        return softplus2_log2_f16(y.x, y.y);
+    } else {
+        return softplus2_log2_bf16(a0, a1, bias2);
+    }
+}
+// Output-layer contribution w5 . h for one activation pair (FP32 accumulate).
+template <bool kF16>
+__device__ __forceinline__ uint64_t out_pair(float a0, float a1, uint64_t bias2, uint64_t w2, uint64_t acc) {
+    if constexpr (kF16) {
+        const float2 y = upk(add2(pk(a0, a1), bias2));
+        const float2 h = f16x2_to_f32x2(softplus2_log2_f16(y.x, y.y));
+        return fma2(w2, pk(h.x, h.y), acc);
+    } else {
+        return fma2(w2, softplus2_log2(a0, a1, bias2), acc);
+    }
 }
 
 __device__ __forceinline__ int items_of_slot(int slot, int nslots, int n_items) {
     return slot < n_items ? (n_items - slot + nslots - 1) / nslots : 0;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) sdf_mlp_bf16_kernel(StepParams P, StepBuffers B, MlpWeights W) {
-    extern __shared__ uint8_t smem_raw[];
-    TcShared& S = *reinterpret_cast<TcShared*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+template <bool kF16>
+__global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, StepBuffers B, MlpWeights W) {
+    // the kernel has no static shared memory, so the dynamic block starts at the
+    // (1024-byte aligned) base of the CTA's window; indexing it directly keeps the
+    // shared address space visible to the compiler (no generic loads)
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    TcShared& S = *reinterpret_cast<TcShared*>(smem_raw);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int K = P.K, G = P.G;
@@ -116,15 +189,16 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_bf16_kernel(StepParams P,
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        for (int i = 0; i < kEpiWarpgroups; ++i) {
+        for (int i = 0; i < kGroups; ++i) {
             tc::mbar_init(tc::smem_u32(&S.act_full[i]), 1);
-            tc::mbar_init(tc::smem_u32(&S.acc_full[i]), 1);
+            tc::mbar_init(tc::smem_u32(&S.acc_full[i][0]), 1);
+            tc::mbar_init(tc::smem_u32(&S.acc_full[i][1]), 1);
         }
         S.abort_flag = 0;
         tc::mbar_fence_init();
     }
     for (int l = 0; l < 3; ++l) {
-        const uint4* src = reinterpret_cast<const uint4*>(W.Wbf[l]);
+        const uint4* src = reinterpret_cast<const uint4*>(kF16 ? W.Wh[l] : W.Wbf[l]);
         uint4* dst = reinterpret_cast<uint4*>(S.w[l]);
         for (int i = tid; i < int(kTileBytes / 16); i += kThreads) dst[i] = __ldg(src + i);
     }
@@ -145,48 +219,55 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_bf16_kernel(StepParams P,
 
     const int n_kb = (K + kTileRows - 1) / kTileRows;
     const int n_items = P.H * n_kb;
-    const int nslots = gridDim.x * kEpiWarpgroups;
+    const int nslots = gridDim.x * kGroups;
     volatile int* abort_flag = &S.abort_flag;
 
     if (warp == kMmaWarp) {
         // ---------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            int nreq[kEpiWarpgroups], issued[kEpiWarpgroups];
-            uint32_t phase[kEpiWarpgroups];
-            uint64_t adesc[kEpiWarpgroups], bdesc[3];
-            for (int i = 0; i < kEpiWarpgroups; ++i) {
-                nreq[i] = items_of_slot(blockIdx.x * kEpiWarpgroups + i, nslots, n_items) * G * 3;
+            int nreq[kGroups], issued[kGroups];
+            uint32_t phase[kGroups];
+#pragma unroll
+            for (int i = 0; i < kGroups; ++i) {
+                nreq[i] = items_of_slot(blockIdx.x * kGroups + i, nslots, n_items) * G * 3;
                 issued[i] = 0;
                 phase[i] = 0;
-                adesc[i] = tc::smem_desc(tc::smem_u32(S.a[i]), 128, 2048);
             }
-            for (int l = 0; l < 3; ++l) bdesc[l] = tc::smem_desc(tc::smem_u32(S.w[l]), 128, 2048);
             uint64_t t0 = tc::global_timer();
-            int spins = 0;
+            int idle = 0;
             while (true) {
                 bool pending = false, progressed = false;
-                for (int i = 0; i < kEpiWarpgroups; ++i) {
+#pragma unroll
+                for (int i = 0; i < kGroups; ++i) {
                     if (issued[i] >= nreq[i]) continue;
                     pending = true;
-                    if (!tc::mbar_try_wait(tc::smem_u32(&S.act_full[i]), phase[i])) continue;
+                    // non-blocking: a suspended try_wait on one group would delay the others
+                    if (!tc::mbar_test_wait(tc::smem_u32(&S.act_full[i]), phase[i])) continue;
                     phase[i] ^= 1u;
                     tc::fence_after_sync();
                     const int l = issued[i] % 3;
-                    const uint32_t d = tmem_base + static_cast<uint32_t>(i * kHidden);
+                    const uint64_t ad = tc::smem_desc(tc::smem_u32(S.a[i]), 128, 2048);
+                    const uint64_t bd = tc::smem_desc(tc::smem_u32(S.w[l]), 128, 2048);
 #pragma unroll
-                    for (int s = 0; s < kHidden / 16; ++s)   // K = 16 per instruction: 256 B along K
-                        tc::mma_bf16(d, adesc[i] + static_cast<uint64_t>(s * 16), bdesc[l] + static_cast<uint64_t>(s * 16),
-                                     kIdesc, s > 0 ? 1u : 0u);
-                    tc::mma_commit(tc::smem_u32(&S.acc_full[i]));
+                    for (int hf = 0; hf < 2; ++hf) {
+                        // N half hf: accumulator columns [64 hf, 64 hf + 64), B rows 64 hf.. (+16 KB)
+                        const uint32_t d = tmem_base + static_cast<uint32_t>(i * kHidden + hf * kHalf);
+                        const uint64_t bh = bd + static_cast<uint64_t>(hf * (kHalf / 8) * (2048 >> 4));
+#pragma unroll
+                        for (int s = 0; s < kHidden / 16; ++s)   // K = 16 per instruction: 256 B along K
+                            tc::mma_bf16(d, ad + static_cast<uint64_t>(s * 16), bh + static_cast<uint64_t>(s * 16),
+                                         kF16 ? kIdescHalfF16 : kIdescHalf, s > 0 ? 1u : 0u);
+                        tc::mma_commit(tc::smem_u32(&S.acc_full[i][hf]));
+                    }
                     ++issued[i];
                     progressed = true;
                 }
                 if (!pending) break;
                 if (progressed) {
                     t0 = tc::global_timer();
-                    spins = 0;
-                } else if (++spins >= 64) {
-                    spins = 0;
+                    idle = 0;
+                } else if (++idle >= 64) {
+                    idle = 0;
                     if (*abort_flag) break;
                     if (tc::global_timer() - t0 > tc::kWaitLimitNs) {
                         *abort_flag = 1;
@@ -196,102 +277,120 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_bf16_kernel(StepParams P,
                 }
             }
             // on abort: let the MMAs already issued finish before TMEM is released
-            for (int i = 0; i < kEpiWarpgroups; ++i) {
+#pragma unroll
+            for (int i = 0; i < kGroups; ++i) {
                 if (issued[i] > 0) {
                     int dummy = 0;
-                    tc::mbar_wait_bounded(tc::smem_u32(&S.acc_full[i]), static_cast<uint32_t>((issued[i] - 1) & 1),
-                                          &dummy, B.err, kDevErrTimeout);
+                    for (int hf = 0; hf < 2; ++hf)
+                        tc::mbar_wait_bounded(tc::smem_u32(&S.acc_full[i][hf]),
+                                              static_cast<uint32_t>((issued[i] - 1) & 1), &dummy, B.err,
+                                              kDevErrTimeout);
                 }
             }
         }
         __syncwarp();
     } else {
-        // ---------------------------------------------------------- epilogue warpgroups
-        const int wg = warp >> 2;
-        const int row = (warp & 3) * 32 + lane;                       // TMEM lane == tile row
-        const uint32_t a_base = tc::smem_u32(S.a[wg]);
-        const uint32_t t_row = tmem_base + (static_cast<uint32_t>((warp & 3) * 32) << 16) +
-                               static_cast<uint32_t>(wg * kHidden);
-        const uint32_t act_bar = tc::smem_u32(&S.act_full[wg]);
-        const uint32_t acc_bar = tc::smem_u32(&S.acc_full[wg]);
+        // ---------------------------------------------------------- epilogue tile groups
+        const int grp = warp / kGroupWarps;
+        const int quad = warp & 3;                                    // TMEM lane quadrant (= warp % 4)
+        const int half = (warp % kGroupWarps) >> 2;                   // column half
+        const int row = quad * 32 + lane;                             // TMEM lane == tile row
+        const int col0 = half * kHalf;
+        const uint32_t a_base = tc::smem_u32(S.a[grp]);
+        const uint32_t t_row = tmem_base + (static_cast<uint32_t>(quad * 32) << 16) +
+                               static_cast<uint32_t>(grp * kHidden + col0);
+        const uint32_t act_bar = tc::smem_u32(&S.act_full[grp]);
+        const uint32_t acc_bar = tc::smem_u32(&S.acc_full[grp][half]);
+        const uint32_t bar_id = 1 + grp;
+        const bool leader = (warp % kGroupWarps) == 0 && lane == 0;
         uint32_t acc_phase = 0;
         bool ok = true;
 
-        for (int item = blockIdx.x * kEpiWarpgroups + wg; item < n_items && ok; item += nslots) {
+        for (int item = blockIdx.x * kGroups + grp; item < n_items && ok; item += nslots) {
             const int h = item / n_kb, kb = item - h * n_kb;
             const int k = kb * kTileRows + row;
             const float4 p = B.pos[h * K + min(k, K - 1)];
             float smin = __int_as_float(0x7f800000);
             for (int g = 0; g < G && ok; ++g) {
-                // layer 1: a_c = b1'_g[c] + W1[c, 0:3] . p_g  -> softplus -> BF16 row of the A tile
+                // layer 1: a_c = b1'_g[c] + W1[c, 0:3] . p_g  -> softplus -> this half of the BF16 A-tile row
                 const Vec3 pg = to_gate(S.pose[g], v3(p.x, p.y, p.z));
                 const uint64_t px = pk(pg.x, pg.x), py = pk(pg.y, pg.y), pz = pk(pg.z, pg.z);
 #pragma unroll 2
-                for (int c = 0; c < kHidden; c += 8) {
+                for (int c = col0; c < col0 + kHalf; c += 8) {
                     uint32_t o[4];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const int n = c + 2 * j;
-                        uint64_t a = fma2(pk(S.w1[0][n], S.w1[0][n + 1]), px,
-                                          pk(S.b1[g][n], S.b1[g][n + 1]));
+                        uint64_t a = fma2(pk(S.w1[0][n], S.w1[0][n + 1]), px, pk(S.b1[g][n], S.b1[g][n + 1]));
                         a = fma2(pk(S.w1[1][n], S.w1[1][n + 1]), py, a);
                         a = fma2(pk(S.w1[2][n], S.w1[2][n + 1]), pz, a);
                         const float2 af = upk(a);
-                        o[j] = softplus2_log2_bf16(af.x, af.y, pk(0.f, 0.f));
+                        o[j] = kF16 ? softplus2_log2_f16(af.x, af.y) : softplus2_log2_bf16(af.x, af.y, pk(0.f, 0.f));
                     }
                     tc::st_shared_v4(a_base + tc::operand_offset_bytes(row, c), o[0], o[1], o[2], o[3]);
                 }
                 tc::fence_proxy_async_smem();
-                tc::named_barrier(1 + wg, 128);
-                if ((warp & 3) == 0 && lane == 0) tc::mbar_arrive(act_bar);
+                tc::named_barrier(bar_id, kGroupThreads);
+                if (leader) tc::mbar_arrive(act_bar);
 
-                float s = W.b5;
+                float s = 0.f;
                 for (int l = 0; l < 3; ++l) {
-                    // every thread of the warpgroup agrees on the outcome before going on, so a
+                    // every thread of the group agrees on the outcome before going on, so a
                     // timeout seen by one thread cannot strand the others at a named barrier
                     const bool got = tc::mbar_wait_bounded(acc_bar, acc_phase, abort_flag, B.err, kDevErrTimeout);
-                    if (!tc::named_barrier_and(1 + wg, 128, got)) {
+                    if (!tc::named_barrier_and(bar_id, kGroupThreads, got)) {
                         ok = false;
                         break;
                     }
                     acc_phase ^= 1u;
                     tc::fence_after_sync();
-                    for (int ch = 0; ch < kHidden; ch += 32) {
+                    uint64_t s2 = pk(0.f, 0.f);
+#pragma unroll 1
+                    for (int ch = 0; ch < kHalf; ch += 32) {
                         uint32_t v[32];
                         tc::tmem_ld_32x32b_x32(t_row + static_cast<uint32_t>(ch), v);
                         tc::tmem_wait_ld();
+                        const int cc = col0 + ch;
                         if (l < 2) {
 #pragma unroll
                             for (int j = 0; j < 32; j += 8) {
-                                const float4 b0 = *reinterpret_cast<const float4*>(&S.bias[l][ch + j]);
-                                const float4 b1 = *reinterpret_cast<const float4*>(&S.bias[l][ch + j + 4]);
+                                const float4 b0 = *reinterpret_cast<const float4*>(&S.bias[l][cc + j]);
+                                const float4 b1 = *reinterpret_cast<const float4*>(&S.bias[l][cc + j + 4]);
                                 tc::st_shared_v4(
-                                    a_base + tc::operand_offset_bytes(row, ch + j),
-                                    softplus2_log2_bf16(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), pk(b0.x, b0.y)),
-                                    softplus2_log2_bf16(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]), pk(b0.z, b0.w)),
-                                    softplus2_log2_bf16(__uint_as_float(v[j + 4]), __uint_as_float(v[j + 5]), pk(b1.x, b1.y)),
-                                    softplus2_log2_bf16(__uint_as_float(v[j + 6]), __uint_as_float(v[j + 7]), pk(b1.z, b1.w)));
+                                    a_base + tc::operand_offset_bytes(row, cc + j),
+                                    act_pair<kF16>(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), pk(b0.x, b0.y)),
+                                    act_pair<kF16>(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]), pk(b0.z, b0.w)),
+                                    act_pair<kF16>(__uint_as_float(v[j + 4]), __uint_as_float(v[j + 5]), pk(b1.x, b1.y)),
+                                    act_pair<kF16>(__uint_as_float(v[j + 6]), __uint_as_float(v[j + 7]), pk(b1.z, b1.w)));
                             }
                         } else {
 #pragma unroll
-                            for (int j = 0; j < 32; ++j)
-                                s = fmaf(S.w5[ch + j], softplus_log2(__uint_as_float(v[j]) + S.bias[2][ch + j]), s);
+                            for (int j = 0; j < 32; j += 4) {
+                                const float4 b0 = *reinterpret_cast<const float4*>(&S.bias[2][cc + j]);
+                                const float4 w0 = *reinterpret_cast<const float4*>(&S.w5[cc + j]);
+                                s2 = out_pair<kF16>(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), pk(b0.x, b0.y),
+                                                    pk(w0.x, w0.y), s2);
+                                s2 = out_pair<kF16>(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]), pk(b0.z, b0.w),
+                                                    pk(w0.z, w0.w), s2);
+                            }
                         }
                     }
                     tc::fence_before_sync();
                     if (l < 2) {
                         tc::fence_proxy_async_smem();
-                        tc::named_barrier(1 + wg, 128);
-                        if ((warp & 3) == 0 && lane == 0) tc::mbar_arrive(act_bar);
+                        tc::named_barrier(bar_id, kGroupThreads);
+                        if (leader) tc::mbar_arrive(act_bar);
                     } else {
-                        // the accumulator is free again once every thread of the warpgroup has read it;
-                        // the next request (next gate or item) is only posted after the next A tile is
-                        // written and the warpgroup barrier has passed
+                        // the two column halves of a row meet through shared memory
+                        const float2 sp2 = upk(s2);
+                        s = sp2.x + sp2.y;
+                        if (half == 1) S.part[grp][row] = s;
+                        tc::named_barrier(bar_id, kGroupThreads);
+                        if (half == 0) smin = fminf(smin, s + S.part[grp][row] + W.b5);
                     }
                 }
-                smin = fminf(smin, s);
             }
-            if (ok && k < K) B.sdf[h * K + k] = smin;
+            if (ok && half == 0 && k < K) B.sdf[h * K + k] = smin;
         }
     }
 
@@ -341,7 +440,7 @@ __global__ void __launch_bounds__(128, 1) tc_selftest_kernel(const uint16_t* __r
         const uint64_t ad = tc::smem_desc(tc::smem_u32(sa), 128, 2048);
         const uint64_t bd = tc::smem_desc(tc::smem_u32(sb), 128, 2048);
         for (int s = 0; s < kHidden / 16; ++s)
-            tc::mma_bf16(t, ad + static_cast<uint64_t>(s * 16), bd + static_cast<uint64_t>(s * 16), kIdesc,
+            tc::mma_bf16(t, ad + static_cast<uint64_t>(s * 16), bd + static_cast<uint64_t>(s * 16), kIdescFull,
                          s > 0 ? 1u : 0u);
         tc::mma_commit(tc::smem_u32(&bar));
     }
@@ -365,21 +464,33 @@ __global__ void __launch_bounds__(128, 1) tc_selftest_kernel(const uint16_t* __r
     }
 }
 
-constexpr size_t kSmemBytes = sizeof(TcShared) + 1024;
+constexpr size_t kSmemBytes = sizeof(TcShared);
 
 }  // namespace
 
 cudaError_t configure_sdf_mlp_bf16() {
-    return cudaFuncSetAttribute(sdf_mlp_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(sdf_mlp_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kSmemBytes));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(sdf_mlp_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(kSmemBytes));
 }
 
 cudaError_t launch_sdf_mlp_bf16(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
                                 cudaStream_t s) {
     const int n_items = P.H * ((P.K + kTileRows - 1) / kTileRows);
-    const int want = (n_items + kEpiWarpgroups - 1) / kEpiWarpgroups;
+    const int want = (n_items + kGroups - 1) / kGroups;
     const int grid = want < num_sms ? want : num_sms;
-    sdf_mlp_bf16_kernel<<<grid, kThreads, kSmemBytes, s>>>(P, B, W);
+    sdf_mlp_tc_kernel<false><<<grid, kThreads, kSmemBytes, s>>>(P, B, W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sdf_mlp_fp16(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
+                                cudaStream_t s) {
+    const int n_items = P.H * ((P.K + kTileRows - 1) / kTileRows);
+    const int want = (n_items + kGroups - 1) / kGroups;
+    const int grid = want < num_sms ? want : num_sms;
+    sdf_mlp_tc_kernel<true><<<grid, kThreads, kSmemBytes, s>>>(P, B, W);
     return cudaGetLastError();
 }
 

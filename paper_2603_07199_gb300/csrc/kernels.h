@@ -21,6 +21,7 @@ struct MlpWeights {
     const float* w5;        // [128]
     float b5;
     const uint16_t* Wbf[3]; // W2..W4 as BF16 in the tensor-core operand layout
+    const uint16_t* Wh[3];  // W2..W4 as FP16 in the tensor-core operand layout
 };
 // set the dynamic shared-memory limits (once per context, outside any stream capture)
 cudaError_t configure_sdf_mlp_fp32();
@@ -28,6 +29,8 @@ cudaError_t configure_sdf_mlp_bf16();
 cudaError_t launch_sdf_mlp_fp32(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
                                 cudaStream_t s);
 cudaError_t launch_sdf_mlp_bf16(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
+                                cudaStream_t s);
+cudaError_t launch_sdf_mlp_fp16(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
                                 cudaStream_t s);
 // (d) costs -> weights; weighted update + plant step + shift
 cudaError_t launch_cost_weights(const StepParams& P, const StepBuffers& B, int mlp, cudaStream_t s);
@@ -38,8 +41,9 @@ cudaError_t launch_first_layer_bias(const float* W1, const float* b1, const floa
 // tensor-core self-test (one 128x128x128 tile)
 cudaError_t launch_tc_selftest(const uint16_t* A, const uint16_t* B, float* D, int* err, cudaStream_t s);
 
-// Host helper: BF16 (round to nearest even) of a float.
+// Host helpers: BF16 / FP16 (round to nearest even) of a float.
 uint16_t float_to_bf16(float f);
+uint16_t float_to_f16(float f);
 // Host helper: offset (in elements) of (row, col) in the 128 x 128 tensor-core operand layout.
 inline int tc_operand_offset(int row, int col) {
     return ((row >> 3) * 16 + (col >> 3)) * 64 + (row & 7) * 8 + (col & 7);

@@ -7,6 +7,8 @@
 #include <new>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "kernels.h"
 #include "mppi.h"
 
@@ -38,6 +40,7 @@ struct mppi_ctx {
     float* d_bias[3] = {nullptr, nullptr, nullptr};
     float* d_w5 = nullptr;
     uint16_t* d_Wbf[3] = {nullptr, nullptr, nullptr};
+    uint16_t* d_Wh[3] = {nullptr, nullptr, nullptr};
     float b5 = 0.f;
     // pinned staging
     float* h_in = nullptr;        // state(16) | nominal(H*4) | poses(maxG*8) | latents(maxG*64)
@@ -125,7 +128,7 @@ int check_config(const mppi_config* g) {
         return fail(nullptr, MPPI_E_INVALID, "K*H=%lld exceeds 2^28", static_cast<long long>(g->K) * g->H);
     if (g->max_gates < 1 || g->max_gates > MPPI_MAX_GATES)
         return fail(nullptr, MPPI_E_INVALID, "max_gates=%d out of [1, %d]", g->max_gates, MPPI_MAX_GATES);
-    if (g->sdf_mode < MPPI_SDF_ANALYTIC || g->sdf_mode > MPPI_SDF_MLP_BF16)
+    if (g->sdf_mode < MPPI_SDF_ANALYTIC || g->sdf_mode > MPPI_SDF_MLP_FP16)
         return fail(nullptr, MPPI_E_UNSUPPORTED, "sdf_mode=%d is not built", g->sdf_mode);
     const float f[] = {g->dt, g->mass, g->gravity, g->thrust_min, g->thrust_max, g->rate_max, g->sigma_thrust,
                        g->sigma_rate, g->lambda, g->w_col, g->d_safe, g->w_u, g->gate_inner_half,
@@ -146,7 +149,7 @@ int recompute_b1p(mppi_ctx* c) {
     return MPPI_OK;
 }
 
-bool is_mlp(const mppi_ctx* c) { return c->cfg.sdf_mode == MPPI_SDF_MLP_FP32 || c->cfg.sdf_mode == MPPI_SDF_MLP_BF16; }
+bool is_mlp(const mppi_ctx* c) { return c->cfg.sdf_mode != MPPI_SDF_ANALYTIC; }
 
 MlpWeights make_weights(const mppi_ctx* c) {
     MlpWeights W{};
@@ -155,6 +158,7 @@ MlpWeights make_weights(const mppi_ctx* c) {
         W.Wt[l] = c->d_Wt[l];
         W.b[l] = c->d_bias[l];
         W.Wbf[l] = c->d_Wbf[l];
+        W.Wh[l] = c->d_Wh[l];
     }
     W.w5 = c->d_w5;
     W.b5 = c->b5;
@@ -187,9 +191,12 @@ int enqueue_kernels(mppi_ctx* c) {
         if (c->cfg.sdf_mode == MPPI_SDF_MLP_FP32) {
             CUDA_TRY(c, launch_sdf_mlp_fp32(P, c->B, W, c->num_sms, c->stream));
             record(c, "sdf_mlp_fp32");
-        } else {
+        } else if (c->cfg.sdf_mode == MPPI_SDF_MLP_BF16) {
             CUDA_TRY(c, launch_sdf_mlp_bf16(P, c->B, W, c->num_sms, c->stream));
             record(c, "sdf_mlp_bf16");
+        } else {
+            CUDA_TRY(c, launch_sdf_mlp_fp16(P, c->B, W, c->num_sms, c->stream));
+            record(c, "sdf_mlp_fp16");
         }
     }
     CUDA_TRY(c, launch_cost_weights(P, c->B, mlp ? 1 : 0, c->stream));
@@ -362,6 +369,7 @@ int mppi_create(const mppi_config* cfg, void* cuda_stream, mppi_ctx** out) {
         rc = rc ? rc : dev_alloc(c, &c->d_Wt[l], kHidden * kHidden);
         rc = rc ? rc : dev_alloc(c, &c->d_bias[l], kHidden);
         rc = rc ? rc : dev_alloc(c, &c->d_Wbf[l], kHidden * kHidden);
+        rc = rc ? rc : dev_alloc(c, &c->d_Wh[l], kHidden * kHidden);
     }
     rc = rc ? rc : dev_alloc(c, &c->d_w5, kHidden);
     if (rc != MPPI_OK) {
@@ -461,16 +469,18 @@ int mppi_set_sdf_weights(mppi_ctx* c, const float* const* layers, int n_layers, 
     CUDA_TRY(c, cudaMemcpy(c->d_W1, layers[0], sizes[0] * sizeof(float), cudaMemcpyHostToDevice));
     CUDA_TRY(c, cudaMemcpy(c->d_b1, layers[1], sizes[1] * sizeof(float), cudaMemcpyHostToDevice));
     std::vector<float> t(kHidden * kHidden);
-    std::vector<uint16_t> bf(kHidden * kHidden);
+    std::vector<uint16_t> bf(kHidden * kHidden), hf(kHidden * kHidden);
     for (int l = 0; l < 3; ++l) {
         const float* Wl = layers[2 + 2 * l];
         for (int n = 0; n < kHidden; ++n)
             for (int k = 0; k < kHidden; ++k) {
                 t[k * kHidden + n] = Wl[n * kHidden + k];
                 bf[tc_operand_offset(n, k)] = float_to_bf16(Wl[n * kHidden + k]);
+                hf[tc_operand_offset(n, k)] = float_to_f16(Wl[n * kHidden + k]);
             }
         CUDA_TRY(c, cudaMemcpy(c->d_Wt[l], t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice));
         CUDA_TRY(c, cudaMemcpy(c->d_Wbf[l], bf.data(), bf.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(c->d_Wh[l], hf.data(), hf.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
         CUDA_TRY(c, cudaMemcpy(c->d_bias[l], layers[3 + 2 * l], kHidden * sizeof(float), cudaMemcpyHostToDevice));
     }
     CUDA_TRY(c, cudaMemcpy(c->d_w5, layers[8], kHidden * sizeof(float), cudaMemcpyHostToDevice));
@@ -697,4 +707,5 @@ uint16_t float_to_bf16(float f) {
     const uint32_t rounding = 0x7FFFu + ((u >> 16) & 1u);                           // round to nearest even
     return static_cast<uint16_t>((u + rounding) >> 16);
 }
+uint16_t float_to_f16(float f) { return __half_as_ushort(__float2half_rn(f)); }
 }  // namespace mppi

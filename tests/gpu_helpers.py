@@ -4,7 +4,8 @@ import numpy as np
 
 from paper_2603_07199_gb300 import binding as B
 
-MODES = {"analytic": B.MPPI_SDF_ANALYTIC, "fp32": B.MPPI_SDF_MLP_FP32, "bf16": B.MPPI_SDF_MLP_BF16}
+MODES = {"analytic": B.MPPI_SDF_ANALYTIC, "fp32": B.MPPI_SDF_MLP_FP32, "bf16": B.MPPI_SDF_MLP_BF16,
+         "fp16": B.MPPI_SDF_MLP_FP16}
 _KEYS = ("K", "H", "dt", "mass", "gravity", "thrust_min", "thrust_max", "rate_max", "sigma_thrust",
          "sigma_rate", "w_col", "d_safe", "w_u", "seed", "drone_id")
 

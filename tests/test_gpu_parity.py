@@ -10,6 +10,7 @@ Tolerances (stated once, used throughout):
 * Updated controls (FP32 paths): |U*_gpu - U*| <= 1e-4 absolute (N, rad/s).
 * BF16 path: SDF error (mm), cost and control errors are reported; the test
   only bounds them loosely (a layout or descriptor bug gives errors of 100s of mm).
+* FP16 path: SDF error within 2 mm at p99 (and MAE < 1 mm) at the full size.
 """
 import json
 import os
@@ -234,11 +235,11 @@ def test_reruns_are_bit_identical(lib):
     wl = W.two_gate_mlp()
     prm = _params(wl, K=512, H=8)
     outs = []
-    for mode in ("bf16", "bf16", "fp32", "fp32"):
+    for mode in ("bf16", "bf16", "fp32", "fp32", "fp16", "fp16"):
         g = GpuController(wl, mode, prm)
         outs.append(g.step(state=wl["state"], nominal=W.hover_nominal(8)))
         g.close()
-    for a, b in ((0, 1), (2, 3)):
+    for a, b in ((0, 1), (2, 3), (4, 5)):
         for key in ("U_new", "weights", "J"):
             np.testing.assert_array_equal(outs[a][key], outs[b][key])
 
@@ -334,4 +335,32 @@ def test_step_mlp_bf16_full_size_two_gates(lib):
     _report("bf16_full_size", err)
     assert err["sdf_mae_mm"] < 10.0, err
     assert abs(float(out["weights"].astype(np.float64).sum()) - 1.0) < 1e-5
+    g.close()
+
+
+# ---------------------------------------------------------------- Gate-SDF MLP, FP16 tensor-core path
+@pytest.mark.parametrize("K,H", [(300, 6), (129, 2)])
+def test_step_mlp_fp16_small(lib, K, H):
+    wl = W.two_gate_mlp()
+    prm = _params(wl, K=K, H=H)
+    g = GpuController(wl, "fp16", prm)
+    out = g.step(state=wl["state"], nominal=W.hover_nominal(H))
+    ref = _oracle(wl, prm, wl["state"], W.hover_nominal(H), 0, True)
+    pos = g.read(B.MPPI_BUF_POSITIONS)[..., :3].astype(np.float64)
+    np.testing.assert_allclose(pos, ref["positions"], atol=POS_ATOL, rtol=0)
+    err = _bf16_errors(g, ref, out)
+    _report(f"fp16_K{K}_H{H}", err)
+    assert err["sdf_mae_mm"] < 1.0 and err["sdf_max_mm"] < 5.0, err
+    g.close()
+
+
+def test_step_mlp_fp16_full_size_two_gates(lib):
+    """K=4096, H=50, G=2 with FP16 operands: SDF error against the FP64 oracle within 2 mm."""
+    wl = W.two_gate_mlp()
+    g = GpuController(wl, "fp16")
+    out = g.step(state=wl["state"], nominal=wl["nominal"])
+    ref = _oracle(wl, wl["params"], wl["state"], wl["nominal"], 0, True)
+    err = _bf16_errors(g, ref, out)
+    _report("fp16_full_size", err)
+    assert err["sdf_mae_mm"] < 1.0 and err["sdf_p99_mm"] < 2.0, err
     g.close()
