@@ -25,6 +25,7 @@ struct StepParams {
     float a_in, a_out, half_depth;
     float beta;
     uint32_t key0, key1, drone;
+    int pdl;               // host side: launch kernels as programmatic dependents
 };
 
 // Device buffers of one controller.
@@ -125,61 +126,61 @@ __device__ __forceinline__ Vec3 quat_x_axis(const Quat& q) {
 
 // One RK4 step of dp = v, dv = (T/m) R(q) e_z - g e_z, dq = q (x) (0, w) / 2,
 // then renormalise q.  T, w held over the step.
+//
+// With w constant, q -> q (x) (0, w) is linear and squares to -|w|^2, so every
+// RK4 stage quaternion is a q + b Wq (Wq = q (x) (0, w)) with a, b polynomials in
+// |w|^2 dt^2, and the stage sums collapse (same RK4 polynomial as the four-stage
+// form, written out):
+//   q2 = q + dt/4 Wq,   q3 = (1 - dt^2 w2/16) q + dt/4 Wq,
+//   q4 = (1 - dt^2 w2/8) q + (dt/2 - dt^3 w2/32) Wq,
+//   q' = (1 - dt^2 w2/8 + dt^4 w2^2/384) q + (dt/2 - dt^3 w2/48) Wq,
+//   p' = p + dt v + dt^2/6 (a1 + a2 + a3),  v' = v + dt/6 (a1 + 2 a2 + 2 a3 + a4),
+// where a_s = (T/m) z(q_s) - g e_z and z(q) = R(q) e_z in the unit-quaternion form.
+__device__ __forceinline__ Vec3 body_z(const Quat& a) {
+    return v3(2.f * (a.x * a.z + a.w * a.y), 2.f * (a.y * a.z - a.w * a.x), 1.f - 2.f * (a.x * a.x + a.y * a.y));
+}
+
 __device__ __forceinline__ void rk4_step(const StepParams& P, Vec3& p, Vec3& v, Quat& q, float T, Vec3 w) {
+    const float dt = P.dt;
     const float tm = T / P.mass;
-    const float g = P.gravity;
-    const float dt = P.dt, hdt = 0.5f * P.dt;
-    // stage derivative helpers
-    auto acc = [&](const Quat& a) -> Vec3 {
-        return v3(tm * 2.f * (a.x * a.z + a.w * a.y),
-                  tm * 2.f * (a.y * a.z - a.w * a.x),
-                  tm * (1.f - 2.f * (a.x * a.x + a.y * a.y)) - g);
-    };
-    auto qdot = [&](const Quat& a) -> Quat {
-        return Quat{0.5f * (-a.x * w.x - a.y * w.y - a.z * w.z),
-                    0.5f * (a.w * w.x + a.y * w.z - a.z * w.y),
-                    0.5f * (a.w * w.y - a.x * w.z + a.z * w.x),
-                    0.5f * (a.w * w.z + a.x * w.y - a.y * w.x)};
-    };
-    auto qadd = [](const Quat& a, float s, const Quat& d) -> Quat {
-        return Quat{a.w + s * d.w, a.x + s * d.x, a.y + s * d.y, a.z + s * d.z};
-    };
-    // k1
-    const Vec3 dp1 = v;
-    const Vec3 dv1 = acc(q);
-    const Quat dq1 = qdot(q);
-    // k2
-    const Vec3 v2 = v3(v.x + hdt * dv1.x, v.y + hdt * dv1.y, v.z + hdt * dv1.z);
-    const Quat q2 = qadd(q, hdt, dq1);
-    const Vec3 dp2 = v2;
-    const Vec3 dv2 = acc(q2);
-    const Quat dq2 = qdot(q2);
-    // k3
-    const Vec3 v3s = v3(v.x + hdt * dv2.x, v.y + hdt * dv2.y, v.z + hdt * dv2.z);
-    const Quat q3 = qadd(q, hdt, dq2);
-    const Vec3 dp3 = v3s;
-    const Vec3 dv3 = acc(q3);
-    const Quat dq3 = qdot(q3);
-    // k4
-    const Vec3 v4 = v3(v.x + dt * dv3.x, v.y + dt * dv3.y, v.z + dt * dv3.z);
-    const Quat q4 = qadd(q, dt, dq3);
-    const Vec3 dp4 = v4;
-    const Vec3 dv4 = acc(q4);
-    const Quat dq4 = qdot(q4);
-    const float s6 = dt / 6.f;
-    p.x += s6 * (dp1.x + 2.f * dp2.x + 2.f * dp3.x + dp4.x);
-    p.y += s6 * (dp1.y + 2.f * dp2.y + 2.f * dp3.y + dp4.y);
-    p.z += s6 * (dp1.z + 2.f * dp2.z + 2.f * dp3.z + dp4.z);
-    v.x += s6 * (dv1.x + 2.f * dv2.x + 2.f * dv3.x + dv4.x);
-    v.y += s6 * (dv1.y + 2.f * dv2.y + 2.f * dv3.y + dv4.y);
-    v.z += s6 * (dv1.z + 2.f * dv2.z + 2.f * dv3.z + dv4.z);
-    Quat qn{q.w + s6 * (dq1.w + 2.f * dq2.w + 2.f * dq3.w + dq4.w),
-            q.x + s6 * (dq1.x + 2.f * dq2.x + 2.f * dq3.x + dq4.x),
-            q.y + s6 * (dq1.y + 2.f * dq2.y + 2.f * dq3.y + dq4.y),
-            q.z + s6 * (dq1.z + 2.f * dq2.z + 2.f * dq3.z + dq4.z)};
-    const float inv = 1.0f / sqrtf(qn.w * qn.w + qn.x * qn.x + qn.y * qn.y + qn.z * qn.z);
+    const Quat wq{-q.x * w.x - q.y * w.y - q.z * w.z,
+                  q.w * w.x + q.y * w.z - q.z * w.y,
+                  q.w * w.y - q.x * w.z + q.z * w.x,
+                  q.w * w.z + q.x * w.y - q.y * w.x};
+    const float w2 = w.x * w.x + w.y * w.y + w.z * w.z;
+    const float d2 = dt * dt * w2;                       // (|w| dt)^2
+    const float b2 = 0.25f * dt;
+    const float a3 = 1.f - d2 * (1.f / 16.f);
+    const float a4 = 1.f - d2 * 0.125f;
+    const float b4 = dt * (0.5f - d2 * (1.f / 32.f));
+    const float an = 1.f - d2 * 0.125f + d2 * d2 * (1.f / 384.f);
+    const float bn = dt * (0.5f - d2 * (1.f / 48.f));
+    const Quat q2{q.w + b2 * wq.w, q.x + b2 * wq.x, q.y + b2 * wq.y, q.z + b2 * wq.z};
+    const Quat q3{a3 * q.w + b2 * wq.w, a3 * q.x + b2 * wq.x, a3 * q.y + b2 * wq.y, a3 * q.z + b2 * wq.z};
+    const Quat q4{a4 * q.w + b4 * wq.w, a4 * q.x + b4 * wq.x, a4 * q.y + b4 * wq.y, a4 * q.z + b4 * wq.z};
+    const Vec3 z1 = body_z(q), z2 = body_z(q2), z3 = body_z(q3), z4 = body_z(q4);
+    const Vec3 s3 = v3(z1.x + z2.x + z3.x, z1.y + z2.y + z3.y, z1.z + z2.z + z3.z);
+    const Vec3 s6 = v3(z1.x + 2.f * (z2.x + z3.x) + z4.x, z1.y + 2.f * (z2.y + z3.y) + z4.y,
+                       z1.z + 2.f * (z2.z + z3.z) + z4.z);
+    const float c3 = dt * dt * (1.f / 6.f);
+    const float c6 = dt * (1.f / 6.f);
+    p.x += dt * v.x + c3 * (tm * s3.x);
+    p.y += dt * v.y + c3 * (tm * s3.y);
+    p.z += dt * v.z + c3 * (tm * s3.z - 3.f * P.gravity);
+    v.x += c6 * (tm * s6.x);
+    v.y += c6 * (tm * s6.y);
+    v.z += c6 * (tm * s6.z) - dt * P.gravity;
+    Quat qn{an * q.w + bn * wq.w, an * q.x + bn * wq.x, an * q.y + bn * wq.y, an * q.z + bn * wq.z};
+    const float inv = rsqrtf(qn.w * qn.w + qn.x * qn.x + qn.y * qn.y + qn.z * qn.z);
     q = Quat{qn.w * inv, qn.x * inv, qn.y * inv, qn.z * inv};
 }
+
+// ---------------------------------------------------------------- programmatic dependent launch
+// Wait until the preceding kernel in the stream has completed and its writes are
+// visible (returns at once when the kernel was not launched as a dependent).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Allow the next kernel in the stream to start launching (its prologue overlaps this kernel).
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // ---------------------------------------------------------------- gate frame SDF
 // Exact signed distance to the square frame {|x| <= d, a_in <= max(|y|,|z|) <= a_out}.

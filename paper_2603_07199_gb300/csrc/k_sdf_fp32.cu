@@ -44,6 +44,8 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_fp32_kernel(StepParams P,
     for (int i = tid; i < kHidden; i += kThreads) sW5[i] = W.w5[i];
     for (int i = tid; i < G * 8; i += kThreads) sPose[i] = B.poses[i];
     __syncthreads();
+    pdl_trigger();
+    pdl_wait();
 
     const float beta = P.beta, inv_beta = 1.0f / P.beta;
     const int tn = tid & 15, tr = tid >> 4;
@@ -166,8 +168,7 @@ cudaError_t launch_sdf_mlp_fp32(const StepParams& P, const StepBuffers& B, const
                                 cudaStream_t s) {
     const int n_items = P.H * ((P.K + kTileRows - 1) / kTileRows);
     const int grid = n_items < num_sms ? n_items : num_sms;
-    sdf_mlp_fp32_kernel<<<grid, kThreads, kSmemBytes, s>>>(P, B, W);
-    return cudaGetLastError();
+    return launch_dependent(P.pdl != 0, sdf_mlp_fp32_kernel, dim3(grid), dim3(kThreads), kSmemBytes, s, P, B, W);
 }
 
 }  // namespace mppi

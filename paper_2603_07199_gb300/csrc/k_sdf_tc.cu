@@ -216,6 +216,10 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem_base = S.tmem_base;
+    // everything above only reads weights and gate data set before the step; the
+    // rollout positions are read only after the preceding kernel has completed
+    pdl_trigger();
+    pdl_wait();
 
     const int n_kb = (K + kTileRows - 1) / kTileRows;
     const int n_items = P.H * n_kb;
@@ -481,8 +485,7 @@ cudaError_t launch_sdf_mlp_bf16(const StepParams& P, const StepBuffers& B, const
     const int n_items = P.H * ((P.K + kTileRows - 1) / kTileRows);
     const int want = (n_items + kGroups - 1) / kGroups;
     const int grid = want < num_sms ? want : num_sms;
-    sdf_mlp_tc_kernel<false><<<grid, kThreads, kSmemBytes, s>>>(P, B, W);
-    return cudaGetLastError();
+    return launch_dependent(P.pdl != 0, sdf_mlp_tc_kernel<false>, dim3(grid), dim3(kThreads), kSmemBytes, s, P, B, W);
 }
 
 cudaError_t launch_sdf_mlp_fp16(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
@@ -490,8 +493,7 @@ cudaError_t launch_sdf_mlp_fp16(const StepParams& P, const StepBuffers& B, const
     const int n_items = P.H * ((P.K + kTileRows - 1) / kTileRows);
     const int want = (n_items + kGroups - 1) / kGroups;
     const int grid = want < num_sms ? want : num_sms;
-    sdf_mlp_tc_kernel<true><<<grid, kThreads, kSmemBytes, s>>>(P, B, W);
-    return cudaGetLastError();
+    return launch_dependent(P.pdl != 0, sdf_mlp_tc_kernel<true>, dim3(grid), dim3(kThreads), kSmemBytes, s, P, B, W);
 }
 
 cudaError_t launch_tc_selftest(const uint16_t* A, const uint16_t* Bm, float* D, int* err, cudaStream_t s) {

@@ -11,6 +11,7 @@ namespace {
 // Layout [h][k] so the rollout kernel's per-h reads are coalesced across k.
 __global__ void __launch_bounds__(256) noise_kernel(StepParams P, const uint32_t* __restrict__ step,
                                                     float4* __restrict__ noise) {
+    pdl_trigger();
     const int n = P.K * P.H;
     const uint32_t st = __ldg(step);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -40,6 +41,8 @@ constexpr int kPrefetch = 8;
 __global__ void __launch_bounds__(64) rollout_kernel(StepParams P, StepBuffers B, int analytic) {
     extern __shared__ float4 sU[];                 // [H]
     __shared__ float sPose[kMaxGates * 8];
+    pdl_trigger();
+    pdl_wait();
     for (int i = threadIdx.x; i < P.H; i += blockDim.x) sU[i] = B.nominal[i];
     for (int i = threadIdx.x; i < P.G * 8; i += blockDim.x) sPose[i] = B.poses[i];
     __syncthreads();
@@ -132,11 +135,14 @@ __global__ void __launch_bounds__(kCostThreads) cost_kernel(StepParams P, StepBu
     const int K = P.K;
     const int k = blockIdx.x * kCostThreads + threadIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    pdl_trigger();
+    pdl_wait();
     float J = __int_as_float(0x7f800000);
     if (k < K) {
         float jcol;
         if (mlp) {
             float acc = 0.f;
+#pragma unroll 10
             for (int h = 0; h < P.H; ++h) acc += hinge_sq(__ldcs(B.sdf + h * K + k), P.d_safe);
             jcol = P.w_col * acc;
             B.parts[k] = jcol;
@@ -173,17 +179,18 @@ __global__ void __launch_bounds__(kCostThreads) cost_kernel(StepParams P, StepBu
 // tree; block 0 also stores w.  The last block to finish applies U*_new[0] to
 // the device-resident state with one RK4 step, writes the shifted warm start
 // and bumps the step counter.
-constexpr int kUpdThreads = 256;
+constexpr int kUpdThreads = 512;
 
 __global__ void __launch_bounds__(kUpdThreads) update_plant_kernel(StepParams P, StepBuffers B) {
-    __shared__ float4 sh[kUpdThreads];
+    __shared__ float4 sh[kUpdThreads / 32];
     __shared__ float s_rho, s_eta;
     __shared__ int is_last;
+    pdl_wait();
     const int h = blockIdx.x;
     const int K = P.K;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nb = (K + kCostThreads - 1) / kCostThreads;
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
+    if (wid == 0) {
         float m = __int_as_float(0x7f800000);
         for (int b = lane; b < nb; b += 32) m = fminf(m, B.red[2 * b]);
         const float rho = warp_min(m);
@@ -199,6 +206,7 @@ __global__ void __launch_bounds__(kUpdThreads) update_plant_kernel(StepParams P,
     const float rho = s_rho, eta = s_eta;
     const float4 un = B.nominal[h];
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
     for (int k = threadIdx.x; k < K; k += kUpdThreads) {
         const float w = expf(-(B.J[k] - rho) / P.lam) / eta;
         if (h == 0) B.w[k] = w;
@@ -209,26 +217,25 @@ __global__ void __launch_bounds__(kUpdThreads) update_plant_kernel(StepParams P,
         acc.z = fmaf(w, u.z, acc.z);
         acc.w = fmaf(w, u.w, acc.w);
     }
-    sh[threadIdx.x] = acc;
+    acc.x = warp_sum(acc.x);
+    acc.y = warp_sum(acc.y);
+    acc.z = warp_sum(acc.z);
+    acc.w = warp_sum(acc.w);
+    if (lane == 0) sh[wid] = acc;
     __syncthreads();
-    for (int s = kUpdThreads / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            float4 a = sh[threadIdx.x];
-            const float4 b = sh[threadIdx.x + s];
-            a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
-            sh[threadIdx.x] = a;
-        }
-        __syncthreads();
-    }
     if (threadIdx.x == 0) {
-        B.unew[h] = sh[0];
+        float4 t = sh[0];
+        for (int i = 1; i < kUpdThreads / 32; ++i) {
+            t.x += sh[i].x; t.y += sh[i].y; t.z += sh[i].z; t.w += sh[i].w;
+        }
+        B.unew[h] = t;
         if (h == 0) {
             B.stats[0] = rho;
             B.stats[1] = eta;
         }
         __threadfence();
-        const unsigned t = atomicAdd(&B.tickets[1], 1u);
-        is_last = (t == gridDim.x - 1);
+        const unsigned tk = atomicAdd(&B.tickets[1], 1u);
+        is_last = (tk == gridDim.x - 1);
     }
     __syncthreads();
     if (!is_last) return;
@@ -288,18 +295,17 @@ cudaError_t launch_noise_words(const StepParams& P, const StepBuffers& B, uint4*
 
 cudaError_t launch_rollout(const StepParams& P, const StepBuffers& B, int analytic, cudaStream_t s) {
     const int threads = 64;
-    rollout_kernel<<<(P.K + threads - 1) / threads, threads, P.H * sizeof(float4), s>>>(P, B, analytic);
-    return cudaGetLastError();
+    return launch_dependent(P.pdl != 0, rollout_kernel, dim3((P.K + threads - 1) / threads), dim3(threads),
+                            P.H * sizeof(float4), s, P, B, analytic);
 }
 
 cudaError_t launch_cost_weights(const StepParams& P, const StepBuffers& B, int mlp, cudaStream_t s) {
-    cost_kernel<<<(P.K + kCostThreads - 1) / kCostThreads, kCostThreads, 0, s>>>(P, B, mlp);
-    return cudaGetLastError();
+    return launch_dependent(P.pdl != 0, cost_kernel, dim3((P.K + kCostThreads - 1) / kCostThreads), dim3(kCostThreads), 0, s,
+                            P, B, mlp);
 }
 
 cudaError_t launch_update_plant(const StepParams& P, const StepBuffers& B, cudaStream_t s) {
-    update_plant_kernel<<<P.H, kUpdThreads, 0, s>>>(P, B);
-    return cudaGetLastError();
+    return launch_dependent(P.pdl != 0, update_plant_kernel, dim3(P.H), dim3(kUpdThreads), 0, s, P, B);
 }
 
 cudaError_t launch_first_layer_bias(const float* W1, const float* b1, const float* latents, int G, float* b1p,

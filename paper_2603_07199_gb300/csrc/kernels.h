@@ -3,9 +3,30 @@
 
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include "common.cuh"
 
 namespace mppi {
+
+// Launch a kernel as a programmatic dependent of the preceding kernel in the
+// stream: it may start while that kernel finishes; its griddepcontrol.wait
+// (pdl_wait) orders its dependent reads.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                             Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // (a) noise: delta u for every (h, k) -> B.noise
 cudaError_t launch_noise(const StepParams& P, const StepBuffers& B, cudaStream_t s);

@@ -111,6 +111,8 @@ StepParams make_params(const mppi_ctx* c) {
     P.key0 = static_cast<uint32_t>(g.seed & 0xFFFFFFFFull);
     P.key1 = static_cast<uint32_t>(g.seed >> 32);
     P.drone = g.drone_id;
+    // per-kernel event timing measures kernels one after the other
+    P.pdl = c->timing ? 0 : 1;
     return P;
 }
 
