@@ -2,9 +2,11 @@
 //
 // Work item = one tile of 128 rollouts at one horizon step; for every gate the
 // tile runs the chain
-//   layer 1 (3 inputs + per-gate bias, FMA)  -> softplus -> BF16 A tile (smem)
-//   3 x [tcgen05.mma 128x128x128 BF16 -> FP32 in TMEM] -> TMEM load -> bias,
-//        softplus -> BF16 A tile (layers 2, 3) or the FP32 output dot (layer 4)
+//   layer 1: one tcgen05.mma 128x128x16 (BF16 hi/lo split of the gate-frame
+//        point and of the first-layer weights, FP32 accumulate)
+//   3 x [tcgen05.mma 128x128x128 BF16/FP16 -> FP32 in TMEM]
+//   each followed by TMEM load -> bias, softplus -> 16-bit A tile (layers 1-3)
+//        or the FP32 output dot (layer 4)
 // and keeps the running minimum over gates in a register; the item ends by
 // storing that minimum s(p) for the 128 states of the tile.
 //
@@ -38,14 +40,13 @@ constexpr int kMmaWarp = kGroups * kGroupWarps;
 constexpr int kHalf = kHidden / 2;
 constexpr uint32_t kTileBytes = kHidden * kHidden * 2;     // one 128 x 128 BF16 operand
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kIdescHalf = tc::idesc_bf16_f32(128, kHalf);
 constexpr uint32_t kIdescFull = tc::idesc_bf16_f32(128, 128);
-constexpr uint32_t kIdescHalfF16 = tc::idesc_f16_f32(128, kHalf);
+constexpr uint32_t kIdescFullF16 = tc::idesc_f16_f32(128, 128);
 
 struct __align__(16) TcShared {
     uint8_t w[3][kTileBytes];                 // W2, W3, W4 (B operands, N = out, K = in)
     uint8_t a[kGroups][kTileBytes];           // activation tiles (A operands, M = rows, K = features)
-    float w1[3][kHidden];                     // c W1[:, 0:3] transposed
+    uint8_t w1[kHidden * 16 * 2];             // layer-1 B operand: c W1[:, 0:3] split hi/lo (BF16, K = 16)
     float b1[kMaxGates][kHidden];             // c (per-gate first-layer bias)
     float bias[3][kHidden];                   // c b2, c b3, c b4
     float w5[kHidden];                        // (ln 2 / beta) w5
@@ -168,6 +169,11 @@ __device__ __forceinline__ uint64_t out_pair(float a0, float a1, uint64_t bias2,
     }
 }
 
+// x rounded to the nearest BF16, as a float
+__device__ __forceinline__ float bf16_round(float x) {
+    return __uint_as_float(tc::pack_bf16x2(x, 0.f) << 16);
+}
+
 __device__ __forceinline__ int items_of_slot(int slot, int nslots, int n_items) {
     return slot < n_items ? (n_items - slot + nslots - 1) / nslots : 0;
 }
@@ -203,9 +209,10 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
         for (int i = tid; i < int(kTileBytes / 16); i += kThreads) dst[i] = __ldg(src + i);
     }
     const float cl2 = P.beta * 1.4426950408889634f;          // beta log2(e)
+    for (int i = tid; i < int(sizeof(S.w1) / 16); i += kThreads)
+        reinterpret_cast<uint4*>(S.w1)[i] = __ldg(reinterpret_cast<const uint4*>(W.W1tc) + i);
     for (int i = tid; i < 3 * kHidden; i += kThreads) {
         const int j = i / kHidden, n = i - j * kHidden;
-        S.w1[j][n] = cl2 * W.W1[n * (3 + kLatent) + j];
         S.bias[j][n] = cl2 * W.b[j][n];
     }
     for (int i = tid; i < G * kHidden; i += kThreads) S.b1[i / kHidden][i % kHidden] = cl2 * B.b1p[i];
@@ -233,7 +240,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
             uint32_t phase[kGroups];
 #pragma unroll
             for (int i = 0; i < kGroups; ++i) {
-                nreq[i] = items_of_slot(blockIdx.x * kGroups + i, nslots, n_items) * G * 3;
+                nreq[i] = items_of_slot(blockIdx.x * kGroups + i, nslots, n_items) * G * 4;
                 issued[i] = 0;
                 phase[i] = 0;
             }
@@ -249,20 +256,22 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                     if (!tc::mbar_test_wait(tc::smem_u32(&S.act_full[i]), phase[i])) continue;
                     phase[i] ^= 1u;
                     tc::fence_after_sync();
-                    const int l = issued[i] % 3;
+                    const int l = issued[i] & 3;
                     const uint64_t ad = tc::smem_desc(tc::smem_u32(S.a[i]), 128, 2048);
-                    const uint64_t bd = tc::smem_desc(tc::smem_u32(S.w[l]), 128, 2048);
-#pragma unroll
-                    for (int hf = 0; hf < 2; ++hf) {
-                        // N half hf: accumulator columns [64 hf, 64 hf + 64), B rows 64 hf.. (+16 KB)
-                        const uint32_t d = tmem_base + static_cast<uint32_t>(i * kHidden + hf * kHalf);
-                        const uint64_t bh = bd + static_cast<uint64_t>(hf * (kHalf / 8) * (2048 >> 4));
+                    const uint32_t d = tmem_base + static_cast<uint32_t>(i * kHidden);
+                    if (l == 0) {
+                        // layer 1: K = 16 (hi/lo split point x weights), always BF16
+                        tc::mma_bf16(d, ad, tc::smem_desc(tc::smem_u32(S.w1), 128, 256), kIdescFull, 0u);
+                    } else {
+                        // one N = 128 GEMM: the A tile is read once (an N = 64 split reads it twice and
+                        // makes the MMA shared-memory bound)
+                        const uint64_t bd = tc::smem_desc(tc::smem_u32(S.w[l - 1]), 128, 2048);
 #pragma unroll
                         for (int s = 0; s < kHidden / 16; ++s)   // K = 16 per instruction: 256 B along K
-                            tc::mma_bf16(d, ad + static_cast<uint64_t>(s * 16), bh + static_cast<uint64_t>(s * 16),
-                                         kF16 ? kIdescHalfF16 : kIdescHalf, s > 0 ? 1u : 0u);
-                        tc::mma_commit(tc::smem_u32(&S.acc_full[i][hf]));
+                            tc::mma_bf16(d, ad + static_cast<uint64_t>(s * 16), bd + static_cast<uint64_t>(s * 16),
+                                         kF16 ? kIdescFullF16 : kIdescFull, s > 0 ? 1u : 0u);
                     }
+                    tc::mma_commit(tc::smem_u32(&S.acc_full[i][0]));
                     ++issued[i];
                     progressed = true;
                 }
@@ -285,10 +294,8 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
             for (int i = 0; i < kGroups; ++i) {
                 if (issued[i] > 0) {
                     int dummy = 0;
-                    for (int hf = 0; hf < 2; ++hf)
-                        tc::mbar_wait_bounded(tc::smem_u32(&S.acc_full[i][hf]),
-                                              static_cast<uint32_t>((issued[i] - 1) & 1), &dummy, B.err,
-                                              kDevErrTimeout);
+                    tc::mbar_wait_bounded(tc::smem_u32(&S.acc_full[i][0]), static_cast<uint32_t>((issued[i] - 1) & 1),
+                                          &dummy, B.err, kDevErrTimeout);
                 }
             }
         }
@@ -304,7 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
         const uint32_t t_row = tmem_base + (static_cast<uint32_t>(quad * 32) << 16) +
                                static_cast<uint32_t>(grp * kHidden + col0);
         const uint32_t act_bar = tc::smem_u32(&S.act_full[grp]);
-        const uint32_t acc_bar = tc::smem_u32(&S.acc_full[grp][half]);
+        const uint32_t acc_bar = tc::smem_u32(&S.acc_full[grp][0]);
         const uint32_t bar_id = 1 + grp;
         const bool leader = (warp % kGroupWarps) == 0 && lane == 0;
         uint32_t acc_phase = 0;
@@ -316,29 +323,24 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
             const float4 p = B.pos[h * K + min(k, K - 1)];
             float smin = __int_as_float(0x7f800000);
             for (int g = 0; g < G && ok; ++g) {
-                // layer 1: a_c = b1'_g[c] + W1[c, 0:3] . p_g  -> softplus -> this half of the BF16 A-tile row
-                const Vec3 pg = to_gate(S.pose[g], v3(p.x, p.y, p.z));
-                const uint64_t px = pk(pg.x, pg.x), py = pk(pg.y, pg.y), pz = pk(pg.z, pg.z);
-#pragma unroll 2
-                for (int c = col0; c < col0 + kHalf; c += 8) {
-                    uint32_t o[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int n = c + 2 * j;
-                        uint64_t a = fma2(pk(S.w1[0][n], S.w1[0][n + 1]), px, pk(S.b1[g][n], S.b1[g][n + 1]));
-                        a = fma2(pk(S.w1[1][n], S.w1[1][n + 1]), py, a);
-                        a = fma2(pk(S.w1[2][n], S.w1[2][n + 1]), pz, a);
-                        const float2 af = upk(a);
-                        o[j] = kF16 ? softplus2_log2_f16(af.x, af.y) : softplus2_log2_bf16(af.x, af.y, pk(0.f, 0.f));
-                    }
-                    tc::st_shared_v4(a_base + tc::operand_offset_bytes(row, c), o[0], o[1], o[2], o[3]);
+                // layer-1 A operand (K = 16): the gate-frame point split p = hi + lo in BF16,
+                // laid out against the weight split [W_hi, W_hi, W_lo] so the MMA sums
+                // hi.W_hi + lo.W_hi + hi.W_lo (relative error ~2^-16); the latent's part
+                // of the first layer is the per-gate bias of the epilogue
+                if (half == 0) {
+                    const Vec3 pg = to_gate(S.pose[g], v3(p.x, p.y, p.z));
+                    const float hx = bf16_round(pg.x), hy = bf16_round(pg.y), hz = bf16_round(pg.z);
+                    const float lx = pg.x - hx, ly = pg.y - hy, lz = pg.z - hz;
+                    tc::st_shared_v4(a_base + tc::operand_offset_bytes(row, 0), tc::pack_bf16x2(hx, hy),
+                                     tc::pack_bf16x2(hz, lx), tc::pack_bf16x2(ly, lz), tc::pack_bf16x2(hx, hy));
+                    tc::st_shared_v4(a_base + tc::operand_offset_bytes(row, 8), tc::pack_bf16x2(hz, 0.f), 0u, 0u, 0u);
                 }
                 tc::fence_proxy_async_smem();
                 tc::named_barrier(bar_id, kGroupThreads);
                 if (leader) tc::mbar_arrive(act_bar);
 
                 float s = 0.f;
-                for (int l = 0; l < 3; ++l) {
+                for (int l = 0; l < 4; ++l) {
                     // every thread of the group agrees on the outcome before going on, so a
                     // timeout seen by one thread cannot strand the others at a named barrier
                     const bool got = tc::mbar_wait_bounded(acc_bar, acc_phase, abort_flag, B.err, kDevErrTimeout);
@@ -355,11 +357,12 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                         tc::tmem_ld_32x32b_x32(t_row + static_cast<uint32_t>(ch), v);
                         tc::tmem_wait_ld();
                         const int cc = col0 + ch;
-                        if (l < 2) {
+                        if (l < 3) {
+                            const float* bias = (l == 0) ? S.b1[g] : S.bias[l - 1];
 #pragma unroll
                             for (int j = 0; j < 32; j += 8) {
-                                const float4 b0 = *reinterpret_cast<const float4*>(&S.bias[l][cc + j]);
-                                const float4 b1 = *reinterpret_cast<const float4*>(&S.bias[l][cc + j + 4]);
+                                const float4 b0 = *reinterpret_cast<const float4*>(bias + cc + j);
+                                const float4 b1 = *reinterpret_cast<const float4*>(bias + cc + j + 4);
                                 tc::st_shared_v4(
                                     a_base + tc::operand_offset_bytes(row, cc + j),
                                     act_pair<kF16>(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), pk(b0.x, b0.y)),
@@ -380,7 +383,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                         }
                     }
                     tc::fence_before_sync();
-                    if (l < 2) {
+                    if (l < 3) {
                         tc::fence_proxy_async_smem();
                         tc::named_barrier(bar_id, kGroupThreads);
                         if (leader) tc::mbar_arrive(act_bar);

@@ -43,6 +43,7 @@ struct MlpWeights {
     float b5;
     const uint16_t* Wbf[3]; // W2..W4 as BF16 in the tensor-core operand layout
     const uint16_t* Wh[3];  // W2..W4 as FP16 in the tensor-core operand layout
+    const uint16_t* W1tc;   // layer-1 B operand [128][16] BF16: beta log2(e) W1[:, 0:3] as [hi, hi, lo, 0..]
 };
 // set the dynamic shared-memory limits (once per context, outside any stream capture)
 cudaError_t configure_sdf_mlp_fp32();
@@ -65,6 +66,8 @@ cudaError_t launch_tc_selftest(const uint16_t* A, const uint16_t* B, float* D, i
 // Host helpers: BF16 / FP16 (round to nearest even) of a float.
 uint16_t float_to_bf16(float f);
 uint16_t float_to_f16(float f);
+// Host helper: offset (in elements) of (row, k) in the 128 x 16 layer-1 operand (LBO 128 B, SBO 256 B).
+inline int tc_operand16_offset(int row, int k) { return (row >> 3) * 128 + (k >> 3) * 64 + (row & 7) * 8 + (k & 7); }
 // Host helper: offset (in elements) of (row, col) in the 128 x 128 tensor-core operand layout.
 inline int tc_operand_offset(int row, int col) {
     return ((row >> 3) * 16 + (col >> 3)) * 64 + (row & 7) * 8 + (col & 7);

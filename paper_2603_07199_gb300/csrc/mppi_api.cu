@@ -41,6 +41,7 @@ struct mppi_ctx {
     float* d_w5 = nullptr;
     uint16_t* d_Wbf[3] = {nullptr, nullptr, nullptr};
     uint16_t* d_Wh[3] = {nullptr, nullptr, nullptr};
+    uint16_t* d_W1tc = nullptr;
     float b5 = 0.f;
     // pinned staging
     float* h_in = nullptr;        // state(16) | nominal(H*4) | poses(maxG*8) | latents(maxG*64)
@@ -164,6 +165,7 @@ MlpWeights make_weights(const mppi_ctx* c) {
     }
     W.w5 = c->d_w5;
     W.b5 = c->b5;
+    W.W1tc = c->d_W1tc;
     return W;
 }
 
@@ -374,6 +376,7 @@ int mppi_create(const mppi_config* cfg, void* cuda_stream, mppi_ctx** out) {
         rc = rc ? rc : dev_alloc(c, &c->d_Wh[l], kHidden * kHidden);
     }
     rc = rc ? rc : dev_alloc(c, &c->d_w5, kHidden);
+    rc = rc ? rc : dev_alloc(c, &c->d_W1tc, kHidden * 16);
     if (rc != MPPI_OK) {
         std::snprintf(g_thread_err, sizeof(g_thread_err), "%s", c->err);
         mppi_destroy(c);
@@ -486,6 +489,24 @@ int mppi_set_sdf_weights(mppi_ctx* c, const float* const* layers, int n_layers, 
         CUDA_TRY(c, cudaMemcpy(c->d_bias[l], layers[3 + 2 * l], kHidden * sizeof(float), cudaMemcpyHostToDevice));
     }
     CUDA_TRY(c, cudaMemcpy(c->d_w5, layers[8], kHidden * sizeof(float), cudaMemcpyHostToDevice));
+    // layer-1 tensor-core operand: row n = [hi(0..2), hi(0..2), lo(0..2), 0 x 7] of beta log2(e) W1[n, 0:3]
+    {
+        const float cl2 = c->cfg.softplus_beta * 1.4426950408889634f;
+        std::vector<uint16_t> w1(kHidden * 16, 0);
+        for (int n = 0; n < kHidden; ++n)
+            for (int j = 0; j < 3; ++j) {
+                const float ws = cl2 * layers[0][n * (3 + kLatent) + j];
+                const uint16_t hi = float_to_bf16(ws);
+                uint32_t hb = static_cast<uint32_t>(hi) << 16;
+                float hf;
+                std::memcpy(&hf, &hb, 4);
+                const uint16_t lo = float_to_bf16(ws - hf);
+                w1[tc_operand16_offset(n, j)] = hi;
+                w1[tc_operand16_offset(n, 3 + j)] = hi;
+                w1[tc_operand16_offset(n, 6 + j)] = lo;
+            }
+        CUDA_TRY(c, cudaMemcpy(c->d_W1tc, w1.data(), w1.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    }
     c->b5 = layers[9][0];
     c->graph_dirty = true;
     c->have_weights = true;
