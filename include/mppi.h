@@ -229,6 +229,42 @@ int mppi_kernels_per_step(const mppi_ctx* ctx);
  */
 int mppi_selftest_tc_gemm(const uint16_t* d_A, const uint16_t* d_B, float* d_D, void* stream);
 
+/*
+ * Allocation-free softmax weights and weighted control update, for costs the
+ * caller computed elsewhere.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory -- code that runs
+ * inside a CUDA stream capture, real-time control loops that forbid allocation
+ * after start-up (cudaMalloc can synchronise the device and take unbounded
+ * time), and hosts whose device memory belongs to another allocator.  It
+ * needs no context and calls no cudaMalloc, cudaFree or other allocating
+ * routine.
+ *   d_costs         K floats, the rollout costs J_m (device)
+ *   d_noise         H x K x 4 floats, delta u in the [h][k][4] layout of MPPI_BUF_NOISE (device)
+ *   d_nominal       H x 4 floats, the nominal sequence U* (device)
+ *   K, H            1 <= K <= MPPI_NOALLOC_MAX_K, 1 <= H <= MPPI_MAX_H
+ *   lambda          temperature (> 0); thrust_min <= thrust_max, rate_max >= 0:
+ *                   the control box applied to U*_h + delta before weighting
+ *   d_new_controls  H x 4 out: U*_new[h] = sum_k w_k clip(U*_h + delta_{k,h}) (device)
+ *   d_weights       K out: w_k = exp(-(J_k - min J) / lambda) / sum (device, nullable)
+ *   stream          cudaStream_t (NULL: the legacy default stream)
+ * Enqueues two kernels and returns; the outputs are valid once the stream
+ * has reached them.  Scratch: a file-scope device array of 2 * 1024 floats
+ * (8 KB) that every GPU which loads this library holds until the process
+ * exits; it caps K at MPPI_NOALLOC_MAX_K.  The first call on each device looks
+ * up the array's device address with that device current (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Every call on a device
+ * shares the array and each call overwrites what it uses (nothing needs to
+ * start at zero), so calls whose kernels overlap on the GPU -- on different
+ * streams, or from several host threads -- race and must not be issued.
+ * Errors: MPPI_E_INVALID (NULL pointer, K or H out of range, bad lambda or
+ * bounds; nothing is enqueued), MPPI_E_CUDA; the message is read with
+ * mppi_last_error(NULL).
+ */
+#define MPPI_NOALLOC_MAX_K 131072
+int mppi_softmax_update_noalloc(const float* d_costs, const float* d_noise, const float* d_nominal, int K, int H,
+                                float lambda, float thrust_min, float thrust_max, float rate_max,
+                                float* d_new_controls, float* d_weights, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,7 +40,7 @@ EXPORTS = [
     "mppi_set_sdf_weights", "mppi_step", "mppi_step_async", "mppi_sync", "mppi_get_nominal",
     "mppi_get_state", "mppi_set_step_counter", "mppi_get_step_counter", "mppi_read_buffer",
     "mppi_read_noise_words", "mppi_set_timing", "mppi_get_kernel_times", "mppi_kernels_per_step",
-    "mppi_selftest_tc_gemm",
+    "mppi_selftest_tc_gemm", "mppi_softmax_update_noalloc",
 ]
 
 
@@ -85,6 +85,8 @@ _SIGS = {
                                              ctypes.c_int]),
     "mppi_kernels_per_step": (ctypes.c_int, [_vp]),
     "mppi_selftest_tc_gemm": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "mppi_softmax_update_noalloc": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                                   ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -211,6 +213,17 @@ def mppi_get_kernel_times(ctx, cap=16):
 
 def mppi_kernels_per_step(ctx):
     return load().mppi_kernels_per_step(ctx)
+
+
+MPPI_NOALLOC_MAX_K = 131072
+
+
+def mppi_softmax_update_noalloc(d_costs, d_noise, d_nominal, K, H, lam, thrust_min, thrust_max, rate_max,
+                                d_new_controls, d_weights=None, stream=None):
+    """Allocation-free weights + update on caller-owned device buffers (see include/mppi.h)."""
+    return _check(load().mppi_softmax_update_noalloc(_ptr(d_costs), _ptr(d_noise), _ptr(d_nominal), K, H, lam,
+                                                     thrust_min, thrust_max, rate_max, _ptr(d_new_controls),
+                                                     _ptr(d_weights), stream))
 
 
 def mppi_selftest_tc_gemm(d_A, d_B, d_D, stream=None):

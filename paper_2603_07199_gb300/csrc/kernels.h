@@ -63,6 +63,8 @@ cudaError_t launch_first_layer_bias(const float* W1, const float* b1, const floa
 // tensor-core self-test (one 128x128x128 tile)
 cudaError_t launch_tc_selftest(const uint16_t* A, const uint16_t* B, float* D, int* err, cudaStream_t s);
 
+// Store a message in the calling thread's error slot (read by mppi_last_error(NULL)).
+void set_thread_error(const char* msg);
 // Host helpers: BF16 / FP16 (round to nearest even) of a float.
 uint16_t float_to_bf16(float f);
 uint16_t float_to_f16(float f);

@@ -723,6 +723,8 @@ int mppi_selftest_tc_gemm(const uint16_t* d_A, const uint16_t* d_B, float* d_D, 
 }  // extern "C"
 
 namespace mppi {
+void set_thread_error(const char* msg) { std::snprintf(g_thread_err, sizeof(g_thread_err), "%s", msg); }
+
 uint16_t float_to_bf16(float f) {
     uint32_t u;
     std::memcpy(&u, &f, 4);
