@@ -130,7 +130,8 @@ def make_ctx(B, wl, mode, stream, drone_id):
     cfg.lam = prm["lam"]
     cfg.drone_id = drone_id
     cfg.max_gates = wl["poses"].shape[0]
-    cfg.sdf_mode = {"bf16": B.MPPI_SDF_MLP_BF16, "fp32": B.MPPI_SDF_MLP_FP32, "fp16": B.MPPI_SDF_MLP_FP16}[mode]
+    cfg.sdf_mode = {"bf16": B.MPPI_SDF_MLP_BF16, "fp32": B.MPPI_SDF_MLP_FP32, "fp16": B.MPPI_SDF_MLP_FP16,
+                    "fp8": B.MPPI_SDF_MLP_FP8}[mode]
     ctx = B.mppi_create(cfg, stream)
     keep = []
     for Wm, b in wl["layers"]:
@@ -274,6 +275,11 @@ def run_ours(args):
     kt16 = kernel_times(torch, B, ctx16, 20, flush, wl, dev)
     B.mppi_destroy(ctx16)
 
+    ctx8 = make_ctx(B, wl, "fp8", stream, drone_id=rank)
+    ms8 = device_loop(torch, B, ctx8, wl, args.steps, 3, flush, dev)
+    kt8 = kernel_times(torch, B, ctx8, 20, flush, wl, dev)
+    B.mppi_destroy(ctx8)
+
     ctx32 = make_ctx(B, wl, "fp32", stream, drone_id=rank)
     ms32 = device_loop(torch, B, ctx32, wl, args.fp32_steps, 3, flush, dev)
     kt32 = kernel_times(torch, B, ctx32, 5, flush, wl, dev)
@@ -309,6 +315,9 @@ def run_ours(args):
         "fp16": {"value": K * H / (ms16.mean() * 1e-3), "p50_ms": float(np.percentile(ms16, 50)),
                  "p99_ms": float(np.percentile(ms16, 99)), "kernel_ms": kt16,
                  "speedup_vs_fp32": float(ms32.mean() / ms16.mean())},
+        "fp8": {"value": K * H / (ms8.mean() * 1e-3), "p50_ms": float(np.percentile(ms8, 50)),
+                "p99_ms": float(np.percentile(ms8, 99)), "kernel_ms": kt8,
+                "speedup_vs_fp32": float(ms32.mean() / ms8.mean())},
         "speedup_vs_fp32": float(ms32.mean() / ms.mean()),
         "p99_speedup_vs_fp32": float(np.percentile(ms32, 99) / np.percentile(ms, 99)),
         "sdf_queries_per_s": K * H * G / (t_sdf * 1e-3) if t_sdf else None,

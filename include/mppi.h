@@ -55,6 +55,8 @@ extern "C" {
 #define MPPI_SDF_MLP_BF16  2    /* Gate-SDF MLP, hidden GEMMs in BF16 on tcgen05, FP32 accumulate */
 #define MPPI_SDF_MLP_FP16  3    /* Gate-SDF MLP, hidden GEMMs in FP16 on tcgen05, FP32 accumulate,
                                    activations packed f16x2 between layers */
+#define MPPI_SDF_MLP_FP8   4    /* Gate-SDF MLP, hidden GEMMs in FP8 E4M3 on tcgen05 (per-tensor scales),
+                                   FP32 accumulate */
 
 /* Gate-SDF MLP shape: [p(3), z(MPPI_LATENT_DIM)] -> 4 x MPPI_HIDDEN softplus -> 1. */
 #define MPPI_LATENT_DIM 64
@@ -132,9 +134,13 @@ int mppi_set_gates(mppi_ctx* ctx, int n_gates, const float* poses, const float* 
  * Set the Gate-SDF MLP weights (host pointers, FP32): layers[2*i] is W_i
  * [out_i x in_i] row-major and layers[2*i+1] its bias [out_i], for the five
  * affine maps 67 -> 128 -> 128 -> 128 -> 128 -> 1 (n_layers = 10 pointers).
- * The library keeps FP32 copies and the BF16 copies the tensor-core path
- * uses, and precomputes the per-gate first-layer bias W1[:, 3:] z_g + b1.
- * fp8_scales must be NULL (reserved).  Synchronous.
+ * The library keeps FP32 copies and the BF16 / FP16 / E4M3 copies the
+ * tensor-core paths use, and precomputes the per-gate first-layer bias
+ * W1[:, 3:] z_g + b1.  fp8_scales (MPPI_SDF_MLP_FP8 only; nullable): 3
+ * per-tensor scales of the E4M3 activations entering the three hidden
+ * 128 x 128 layers, in softplus-output units (an activation a is stored as
+ * E4M3(a / scale), saturating at 448 scale); NULL selects 1/64.  The E4M3
+ * weight scales are max|W| / 448 per tensor.  Synchronous.
  */
 int mppi_set_sdf_weights(mppi_ctx* ctx, const float* const* layers, int n_layers, const float* fp8_scales);
 

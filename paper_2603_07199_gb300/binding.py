@@ -23,6 +23,7 @@ MPPI_SDF_ANALYTIC = 0
 MPPI_SDF_MLP_FP32 = 1
 MPPI_SDF_MLP_BF16 = 2
 MPPI_SDF_MLP_FP16 = 3
+MPPI_SDF_MLP_FP8 = 4
 
 MPPI_BUF_NOISE = 0
 MPPI_BUF_POSITIONS = 1
@@ -156,7 +157,8 @@ def mppi_set_gates(ctx, n_gates, poses, latents=None):
 
 
 def mppi_set_sdf_weights(ctx, layers, fp8_scales=None):
-    """layers: [W1, b1, W2, b2, W3, b3, W4, b4, W5, b5] as float32 arrays (kept alive by the caller)."""
+    """layers: [W1, b1, W2, b2, W3, b3, W4, b4, W5, b5] as float32 arrays (kept alive by the caller);
+    fp8_scales: None or 3 float32 activation scales for MPPI_SDF_MLP_FP8."""
     arr = (_vp * len(layers))(*[_ptr(a) for a in layers])
     return _check(load().mppi_set_sdf_weights(ctx, arr, len(layers), _ptr(fp8_scales)), ctx)
 

@@ -42,6 +42,7 @@ constexpr uint32_t kTileBytes = kHidden * kHidden * 2;     // one 128 x 128 BF16
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kIdescFull = tc::idesc_bf16_f32(128, 128);
 constexpr uint32_t kIdescFullF16 = tc::idesc_f16_f32(128, 128);
+constexpr uint32_t kIdescE4M3 = tc::idesc_e4m3_f32(128, 128);
 
 struct __align__(16) TcShared {
     uint8_t w[3][kTileBytes];                 // W2, W3, W4 (B operands, N = out, K = in)
@@ -147,26 +148,53 @@ __device__ __forceinline__ uint32_t softplus2_log2_f16(float y0, float y1) {
     return hfma2(e, p, hmax2_zero(h));
 }
 
+// Operand formats of the hidden 128 x 128 GEMMs.
+constexpr int kFmtBF16 = 0;
+constexpr int kFmtFP16 = 1;
+constexpr int kFmtE4M3 = 2;
+
+__device__ __forceinline__ uint32_t hmul2(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("mul.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+// Four activations (two f16x2) -> four E4M3 bytes, saturating at +-448.
+__device__ __forceinline__ uint32_t f16x2x2_to_e4m3x4(uint32_t h01, uint32_t h23) {
+    uint32_t r;
+    asm("{\n\t.reg .b16 lo, hi;\n\t"
+        "cvt.rn.satfinite.e4m3x2.f16x2 lo, %1;\n\t"
+        "cvt.rn.satfinite.e4m3x2.f16x2 hi, %2;\n\t"
+        "mov.b32 %0, {lo, hi};\n\t}"
+        : "=r"(r) : "r"(h01), "r"(h23));
+    return r;
+}
+
 // One 16-bit activation pair of the requested operand type.
-template <bool kF16>
+template <int kFmt>
 __device__ __forceinline__ uint32_t act_pair(float a0, float a1, uint64_t bias2) {
-    if constexpr (kF16) {
+    if constexpr (kFmt == kFmtBF16) {
+        return softplus2_log2_bf16(a0, a1, bias2);
+    } else {
         const float2 y = upk(add2(pk(a0, a1), bias2));
         return softplus2_log2_f16(y.x, y.y);
-    } else {
-        return softplus2_log2_bf16(a0, a1, bias2);
     }
 }
 // Output-layer contribution w5 . h for one activation pair (FP32 accumulate).
-template <bool kF16>
+template <int kFmt>
 __device__ __forceinline__ uint64_t out_pair(float a0, float a1, uint64_t bias2, uint64_t w2, uint64_t acc) {
-    if constexpr (kF16) {
+    if constexpr (kFmt == kFmtBF16) {
+        return fma2(w2, softplus2_log2(a0, a1, bias2), acc);
+    } else {
         const float2 y = upk(add2(pk(a0, a1), bias2));
         const float2 h = f16x2_to_f32x2(softplus2_log2_f16(y.x, y.y));
         return fma2(w2, pk(h.x, h.y), acc);
-    } else {
-        return fma2(w2, softplus2_log2(a0, a1, bias2), acc);
     }
+}
+
+// Byte offset of (row, k) in a 128 x 128 E4M3 operand tile: 8 x 16-byte core
+// matrices (8 rows x 16 elements), LBO 128 B along K, SBO 1024 B along rows.
+__device__ __forceinline__ uint32_t operand8_offset_bytes(int row, int k) {
+    return static_cast<uint32_t>((row >> 3) * 1024 + (k >> 4) * 128 + (row & 7) * 16 + (k & 15));
 }
 
 // x rounded to the nearest BF16, as a float
@@ -178,8 +206,10 @@ __device__ __forceinline__ int items_of_slot(int slot, int nslots, int n_items) 
     return slot < n_items ? (n_items - slot + nslots - 1) / nslots : 0;
 }
 
-template <bool kF16>
+template <int kFmt>
 __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, StepBuffers B, MlpWeights W) {
+    constexpr bool kF16 = (kFmt == kFmtFP16);
+    constexpr bool kF8 = (kFmt == kFmtE4M3);
     // the kernel has no static shared memory, so the dynamic block starts at the
     // (1024-byte aligned) base of the CTA's window; indexing it directly keeps the
     // shared address space visible to the compiler (no generic loads)
@@ -204,9 +234,12 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
         tc::mbar_fence_init();
     }
     for (int l = 0; l < 3; ++l) {
-        const uint4* src = reinterpret_cast<const uint4*>(kF16 ? W.Wh[l] : W.Wbf[l]);
+        const uint4* src = reinterpret_cast<const uint4*>(kF8 ? static_cast<const void*>(W.W8[l])
+                                                          : kF16 ? static_cast<const void*>(W.Wh[l])
+                                                                 : static_cast<const void*>(W.Wbf[l]));
         uint4* dst = reinterpret_cast<uint4*>(S.w[l]);
-        for (int i = tid; i < int(kTileBytes / 16); i += kThreads) dst[i] = __ldg(src + i);
+        const int n16 = int((kF8 ? kTileBytes / 2 : kTileBytes) / 16);
+        for (int i = tid; i < n16; i += kThreads) dst[i] = __ldg(src + i);
     }
     const float cl2 = P.beta * 1.4426950408889634f;          // beta log2(e)
     for (int i = tid; i < int(sizeof(S.w1) / 16); i += kThreads)
@@ -262,6 +295,14 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                     if (l == 0) {
                         // layer 1: K = 16 (hi/lo split point x weights), always BF16
                         tc::mma_bf16(d, ad, tc::smem_desc(tc::smem_u32(S.w1), 128, 256), kIdescFull, 0u);
+                    } else if constexpr (kF8) {
+                        // E4M3 x E4M3 -> FP32, K = 32 per instruction (256 B along K), SBO 1024 B
+                        const uint64_t a8 = tc::smem_desc(tc::smem_u32(S.a[i]), 128, 1024);
+                        const uint64_t bd = tc::smem_desc(tc::smem_u32(S.w[l - 1]), 128, 1024);
+#pragma unroll
+                        for (int s = 0; s < kHidden / 32; ++s)
+                            tc::mma_e4m3(d, a8 + static_cast<uint64_t>(s * 16), bd + static_cast<uint64_t>(s * 16),
+                                         kIdescE4M3, s > 0 ? 1u : 0u);
                     } else {
                         // one N = 128 GEMM: the A tile is read once (an N = 64 split reads it twice and
                         // makes the MMA shared-memory bound)
@@ -357,7 +398,29 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                         tc::tmem_ld_32x32b_x32(t_row + static_cast<uint32_t>(ch), v);
                         tc::tmem_wait_ld();
                         const int cc = col0 + ch;
-                        if (l < 3) {
+                        if (kF8 && l < 3) {
+                            // y = D dequant + bias -> softplus (f16x2) -> / activation scale -> E4M3
+                            const float* bias = (l == 0) ? S.b1[g] : S.bias[l - 1];
+                            const float dq = (l == 0) ? 1.f : W.f8_dequant[l - 1];
+                            const uint64_t dq2 = pk(dq, dq);
+                            const uint32_t isa = f32x2_to_f16x2(W.f8_inv_act[l], W.f8_inv_act[l]);
+#pragma unroll
+                            for (int j = 0; j < 32; j += 16) {
+                                uint32_t q[4];
+#pragma unroll
+                                for (int t = 0; t < 4; ++t) {
+                                    const int e = j + 4 * t;
+                                    const float4 bb = *reinterpret_cast<const float4*>(bias + cc + e);
+                                    const float2 y0 = upk(fma2(pk(__uint_as_float(v[e]), __uint_as_float(v[e + 1])),
+                                                               dq2, pk(bb.x, bb.y)));
+                                    const float2 y1 = upk(fma2(pk(__uint_as_float(v[e + 2]), __uint_as_float(v[e + 3])),
+                                                               dq2, pk(bb.z, bb.w)));
+                                    q[t] = f16x2x2_to_e4m3x4(hmul2(softplus2_log2_f16(y0.x, y0.y), isa),
+                                                             hmul2(softplus2_log2_f16(y1.x, y1.y), isa));
+                                }
+                                tc::st_shared_v4(a_base + operand8_offset_bytes(row, cc + j), q[0], q[1], q[2], q[3]);
+                            }
+                        } else if (l < 3) {
                             const float* bias = (l == 0) ? S.b1[g] : S.bias[l - 1];
 #pragma unroll
                             for (int j = 0; j < 32; j += 8) {
@@ -365,19 +428,24 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                                 const float4 b1 = *reinterpret_cast<const float4*>(bias + cc + j + 4);
                                 tc::st_shared_v4(
                                     a_base + tc::operand_offset_bytes(row, cc + j),
-                                    act_pair<kF16>(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), pk(b0.x, b0.y)),
-                                    act_pair<kF16>(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]), pk(b0.z, b0.w)),
-                                    act_pair<kF16>(__uint_as_float(v[j + 4]), __uint_as_float(v[j + 5]), pk(b1.x, b1.y)),
-                                    act_pair<kF16>(__uint_as_float(v[j + 6]), __uint_as_float(v[j + 7]), pk(b1.z, b1.w)));
+                                    act_pair<kFmt>(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), pk(b0.x, b0.y)),
+                                    act_pair<kFmt>(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]), pk(b0.z, b0.w)),
+                                    act_pair<kFmt>(__uint_as_float(v[j + 4]), __uint_as_float(v[j + 5]), pk(b1.x, b1.y)),
+                                    act_pair<kFmt>(__uint_as_float(v[j + 6]), __uint_as_float(v[j + 7]), pk(b1.z, b1.w)));
                             }
                         } else {
+                            if constexpr (kF8) {
+#pragma unroll
+                                for (int j = 0; j < 32; ++j)
+                                    v[j] = __float_as_uint(__uint_as_float(v[j]) * W.f8_dequant[2]);
+                            }
 #pragma unroll
                             for (int j = 0; j < 32; j += 4) {
                                 const float4 b0 = *reinterpret_cast<const float4*>(&S.bias[2][cc + j]);
                                 const float4 w0 = *reinterpret_cast<const float4*>(&S.w5[cc + j]);
-                                s2 = out_pair<kF16>(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), pk(b0.x, b0.y),
+                                s2 = out_pair<kFmt>(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), pk(b0.x, b0.y),
                                                     pk(w0.x, w0.y), s2);
-                                s2 = out_pair<kF16>(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]), pk(b0.z, b0.w),
+                                s2 = out_pair<kFmt>(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]), pk(b0.z, b0.w),
                                                     pk(w0.z, w0.w), s2);
                             }
                         }
@@ -476,10 +544,13 @@ constexpr size_t kSmemBytes = sizeof(TcShared);
 }  // namespace
 
 cudaError_t configure_sdf_mlp_bf16() {
-    cudaError_t e = cudaFuncSetAttribute(sdf_mlp_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(sdf_mlp_tc_kernel<kFmtBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(kSmemBytes));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(sdf_mlp_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(sdf_mlp_tc_kernel<kFmtFP16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kSmemBytes));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(sdf_mlp_tc_kernel<kFmtE4M3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(kSmemBytes));
 }
 
@@ -488,7 +559,7 @@ cudaError_t launch_sdf_mlp_bf16(const StepParams& P, const StepBuffers& B, const
     const int n_items = P.H * ((P.K + kTileRows - 1) / kTileRows);
     const int want = (n_items + kGroups - 1) / kGroups;
     const int grid = want < num_sms ? want : num_sms;
-    return launch_dependent(P.pdl != 0, sdf_mlp_tc_kernel<false>, dim3(grid), dim3(kThreads), kSmemBytes, s, P, B, W);
+    return launch_dependent(P.pdl != 0, sdf_mlp_tc_kernel<kFmtBF16>, dim3(grid), dim3(kThreads), kSmemBytes, s, P, B, W);
 }
 
 cudaError_t launch_sdf_mlp_fp16(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
@@ -496,7 +567,15 @@ cudaError_t launch_sdf_mlp_fp16(const StepParams& P, const StepBuffers& B, const
     const int n_items = P.H * ((P.K + kTileRows - 1) / kTileRows);
     const int want = (n_items + kGroups - 1) / kGroups;
     const int grid = want < num_sms ? want : num_sms;
-    return launch_dependent(P.pdl != 0, sdf_mlp_tc_kernel<true>, dim3(grid), dim3(kThreads), kSmemBytes, s, P, B, W);
+    return launch_dependent(P.pdl != 0, sdf_mlp_tc_kernel<kFmtFP16>, dim3(grid), dim3(kThreads), kSmemBytes, s, P, B, W);
+}
+
+cudaError_t launch_sdf_mlp_fp8(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
+                               cudaStream_t s) {
+    const int n_items = P.H * ((P.K + kTileRows - 1) / kTileRows);
+    const int want = (n_items + kGroups - 1) / kGroups;
+    const int grid = want < num_sms ? want : num_sms;
+    return launch_dependent(P.pdl != 0, sdf_mlp_tc_kernel<kFmtE4M3>, dim3(grid), dim3(kThreads), kSmemBytes, s, P, B, W);
 }
 
 cudaError_t launch_tc_selftest(const uint16_t* A, const uint16_t* Bm, float* D, int* err, cudaStream_t s) {

@@ -44,6 +44,9 @@ struct MlpWeights {
     const uint16_t* Wbf[3]; // W2..W4 as BF16 in the tensor-core operand layout
     const uint16_t* Wh[3];  // W2..W4 as FP16 in the tensor-core operand layout
     const uint16_t* W1tc;   // layer-1 B operand [128][16] BF16: beta log2(e) W1[:, 0:3] as [hi, hi, lo, 0..]
+    const uint8_t* W8[3];   // W2..W4 / (per-tensor weight scale) as E4M3 in the 8-bit operand layout
+    float f8_dequant[3];    // weight scale x activation scale of each hidden GEMM (log2 units)
+    float f8_inv_act[3];    // 1 / activation scale of the E4M3 inputs of the hidden GEMMs (log2 units)
 };
 // set the dynamic shared-memory limits (once per context, outside any stream capture)
 cudaError_t configure_sdf_mlp_fp32();
@@ -54,6 +57,8 @@ cudaError_t launch_sdf_mlp_bf16(const StepParams& P, const StepBuffers& B, const
                                 cudaStream_t s);
 cudaError_t launch_sdf_mlp_fp16(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
                                 cudaStream_t s);
+cudaError_t launch_sdf_mlp_fp8(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
+                               cudaStream_t s);
 // (d) costs -> weights; weighted update + plant step + shift
 cudaError_t launch_cost_weights(const StepParams& P, const StepBuffers& B, int mlp, cudaStream_t s);
 cudaError_t launch_update_plant(const StepParams& P, const StepBuffers& B, cudaStream_t s);
@@ -70,6 +75,8 @@ uint16_t float_to_bf16(float f);
 uint16_t float_to_f16(float f);
 // Host helper: offset (in elements) of (row, k) in the 128 x 16 layer-1 operand (LBO 128 B, SBO 256 B).
 inline int tc_operand16_offset(int row, int k) { return (row >> 3) * 128 + (k >> 3) * 64 + (row & 7) * 8 + (k & 7); }
+// Host helper: byte offset of (row, k) in the 128 x 128 E4M3 operand layout (LBO 128 B, SBO 1024 B).
+inline int tc_operand8_offset(int row, int k) { return (row >> 3) * 1024 + (k >> 4) * 128 + (row & 7) * 16 + (k & 15); }
 // Host helper: offset (in elements) of (row, col) in the 128 x 128 tensor-core operand layout.
 inline int tc_operand_offset(int row, int col) {
     return ((row >> 3) * 16 + (col >> 3)) * 64 + (row & 7) * 8 + (col & 7);

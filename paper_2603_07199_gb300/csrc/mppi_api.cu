@@ -8,6 +8,7 @@
 #include <vector>
 
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "kernels.h"
 #include "mppi.h"
@@ -42,6 +43,9 @@ struct mppi_ctx {
     uint16_t* d_Wbf[3] = {nullptr, nullptr, nullptr};
     uint16_t* d_Wh[3] = {nullptr, nullptr, nullptr};
     uint16_t* d_W1tc = nullptr;
+    uint8_t* d_W8[3] = {nullptr, nullptr, nullptr};
+    float f8_dequant[3] = {1.f, 1.f, 1.f};
+    float f8_inv_act[3] = {1.f, 1.f, 1.f};
     float b5 = 0.f;
     // pinned staging
     float* h_in = nullptr;        // state(16) | nominal(H*4) | poses(maxG*8) | latents(maxG*64)
@@ -131,7 +135,7 @@ int check_config(const mppi_config* g) {
         return fail(nullptr, MPPI_E_INVALID, "K*H=%lld exceeds 2^28", static_cast<long long>(g->K) * g->H);
     if (g->max_gates < 1 || g->max_gates > MPPI_MAX_GATES)
         return fail(nullptr, MPPI_E_INVALID, "max_gates=%d out of [1, %d]", g->max_gates, MPPI_MAX_GATES);
-    if (g->sdf_mode < MPPI_SDF_ANALYTIC || g->sdf_mode > MPPI_SDF_MLP_FP16)
+    if (g->sdf_mode < MPPI_SDF_ANALYTIC || g->sdf_mode > MPPI_SDF_MLP_FP8)
         return fail(nullptr, MPPI_E_UNSUPPORTED, "sdf_mode=%d is not built", g->sdf_mode);
     const float f[] = {g->dt, g->mass, g->gravity, g->thrust_min, g->thrust_max, g->rate_max, g->sigma_thrust,
                        g->sigma_rate, g->lambda, g->w_col, g->d_safe, g->w_u, g->gate_inner_half,
@@ -166,6 +170,11 @@ MlpWeights make_weights(const mppi_ctx* c) {
     W.w5 = c->d_w5;
     W.b5 = c->b5;
     W.W1tc = c->d_W1tc;
+    for (int l = 0; l < 3; ++l) {
+        W.W8[l] = c->d_W8[l];
+        W.f8_dequant[l] = c->f8_dequant[l];
+        W.f8_inv_act[l] = c->f8_inv_act[l];
+    }
     return W;
 }
 
@@ -198,9 +207,12 @@ int enqueue_kernels(mppi_ctx* c) {
         } else if (c->cfg.sdf_mode == MPPI_SDF_MLP_BF16) {
             CUDA_TRY(c, launch_sdf_mlp_bf16(P, c->B, W, c->num_sms, c->stream));
             record(c, "sdf_mlp_bf16");
-        } else {
+        } else if (c->cfg.sdf_mode == MPPI_SDF_MLP_FP16) {
             CUDA_TRY(c, launch_sdf_mlp_fp16(P, c->B, W, c->num_sms, c->stream));
             record(c, "sdf_mlp_fp16");
+        } else {
+            CUDA_TRY(c, launch_sdf_mlp_fp8(P, c->B, W, c->num_sms, c->stream));
+            record(c, "sdf_mlp_fp8");
         }
     }
     CUDA_TRY(c, launch_cost_weights(P, c->B, mlp ? 1 : 0, c->stream));
@@ -374,6 +386,7 @@ int mppi_create(const mppi_config* cfg, void* cuda_stream, mppi_ctx** out) {
         rc = rc ? rc : dev_alloc(c, &c->d_bias[l], kHidden);
         rc = rc ? rc : dev_alloc(c, &c->d_Wbf[l], kHidden * kHidden);
         rc = rc ? rc : dev_alloc(c, &c->d_Wh[l], kHidden * kHidden);
+        rc = rc ? rc : dev_alloc(c, &c->d_W8[l], kHidden * kHidden);
     }
     rc = rc ? rc : dev_alloc(c, &c->d_w5, kHidden);
     rc = rc ? rc : dev_alloc(c, &c->d_W1tc, kHidden * 16);
@@ -462,7 +475,11 @@ int mppi_set_sdf_weights(mppi_ctx* c, const float* const* layers, int n_layers, 
     if (!c) return fail(nullptr, MPPI_E_INVALID, "ctx is NULL");
     if (!layers || n_layers != 2 * MPPI_MLP_LAYERS)
         return fail(c, MPPI_E_INVALID, "expected %d layer pointers (W, b for 5 affine maps)", 2 * MPPI_MLP_LAYERS);
-    if (fp8_scales) return fail(c, MPPI_E_UNSUPPORTED, "fp8_scales is reserved and must be NULL");
+    if (fp8_scales) {
+        for (int i = 0; i < 3; ++i)
+            if (!std::isfinite(fp8_scales[i]) || !(fp8_scales[i] > 0.f))
+                return fail(c, MPPI_E_INVALID, "fp8_scales[%d] must be finite and > 0", i);
+    }
     for (int i = 0; i < n_layers; ++i)
         if (!layers[i]) return fail(c, MPPI_E_INVALID, "layer pointer %d is NULL", i);
     const int in1 = 3 + kLatent;
@@ -475,8 +492,22 @@ int mppi_set_sdf_weights(mppi_ctx* c, const float* const* layers, int n_layers, 
     CUDA_TRY(c, cudaMemcpy(c->d_b1, layers[1], sizes[1] * sizeof(float), cudaMemcpyHostToDevice));
     std::vector<float> t(kHidden * kHidden);
     std::vector<uint16_t> bf(kHidden * kHidden), hf(kHidden * kHidden);
+    std::vector<uint8_t> f8(kHidden * kHidden);
+    const float cl2 = c->cfg.softplus_beta * 1.4426950408889634f;
     for (int l = 0; l < 3; ++l) {
         const float* Wl = layers[2 + 2 * l];
+        // FP8: per-tensor weight scale max|W| / 448 (the E4M3 range); activation scale from
+        // fp8_scales (softplus-output units, default 1/64), carried here in log2 units
+        float wmax = 0.f;
+        for (int i = 0; i < kHidden * kHidden; ++i) wmax = std::fmax(wmax, std::fabs(Wl[i]));
+        const float sw = wmax > 0.f ? wmax / 448.f : 1.f;
+        const float sa = cl2 * (fp8_scales ? fp8_scales[l] : (1.f / 64.f));
+        c->f8_dequant[l] = sw * sa;
+        c->f8_inv_act[l] = 1.f / sa;
+        for (int n = 0; n < kHidden; ++n)
+            for (int k = 0; k < kHidden; ++k)
+                f8[tc_operand8_offset(n, k)] =
+                    static_cast<uint8_t>(__nv_cvt_float_to_fp8(Wl[n * kHidden + k] / sw, __NV_SATFINITE, __NV_E4M3));
         for (int n = 0; n < kHidden; ++n)
             for (int k = 0; k < kHidden; ++k) {
                 t[k * kHidden + n] = Wl[n * kHidden + k];
@@ -486,12 +517,12 @@ int mppi_set_sdf_weights(mppi_ctx* c, const float* const* layers, int n_layers, 
         CUDA_TRY(c, cudaMemcpy(c->d_Wt[l], t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice));
         CUDA_TRY(c, cudaMemcpy(c->d_Wbf[l], bf.data(), bf.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
         CUDA_TRY(c, cudaMemcpy(c->d_Wh[l], hf.data(), hf.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(c->d_W8[l], f8.data(), f8.size(), cudaMemcpyHostToDevice));
         CUDA_TRY(c, cudaMemcpy(c->d_bias[l], layers[3 + 2 * l], kHidden * sizeof(float), cudaMemcpyHostToDevice));
     }
     CUDA_TRY(c, cudaMemcpy(c->d_w5, layers[8], kHidden * sizeof(float), cudaMemcpyHostToDevice));
     // layer-1 tensor-core operand: row n = [hi(0..2), hi(0..2), lo(0..2), 0 x 7] of beta log2(e) W1[n, 0:3]
     {
-        const float cl2 = c->cfg.softplus_beta * 1.4426950408889634f;
         std::vector<uint16_t> w1(kHidden * 16, 0);
         for (int n = 0; n < kHidden; ++n)
             for (int j = 0; j < 3; ++j) {

@@ -5,7 +5,7 @@ import numpy as np
 from paper_2603_07199_gb300 import binding as B
 
 MODES = {"analytic": B.MPPI_SDF_ANALYTIC, "fp32": B.MPPI_SDF_MLP_FP32, "bf16": B.MPPI_SDF_MLP_BF16,
-         "fp16": B.MPPI_SDF_MLP_FP16}
+         "fp16": B.MPPI_SDF_MLP_FP16, "fp8": B.MPPI_SDF_MLP_FP8}
 _KEYS = ("K", "H", "dt", "mass", "gravity", "thrust_min", "thrust_max", "rate_max", "sigma_thrust",
          "sigma_rate", "w_col", "d_safe", "w_u", "seed", "drone_id")
 
@@ -30,7 +30,7 @@ def flat_layers(layers):
 class GpuController:
     """One library context set up from a workload dict (see ``workloads``)."""
 
-    def __init__(self, wl, mode, prm=None, stream=None, max_gates=None):
+    def __init__(self, wl, mode, prm=None, stream=None, max_gates=None, fp8_scales=None):
         self.prm = dict(prm if prm is not None else wl["params"])
         poses = np.ascontiguousarray(wl["poses"], dtype=np.float32).reshape(-1, 7)
         self.G = poses.shape[0]
@@ -40,7 +40,8 @@ class GpuController:
         lat = np.ascontiguousarray(wl["latents"], dtype=np.float32).reshape(-1, 64)[: self.G]
         if mode != "analytic":
             self._keep = flat_layers(wl["layers"])
-            B.mppi_set_sdf_weights(self.ctx, self._keep)
+            self._scales = None if fp8_scales is None else np.ascontiguousarray(fp8_scales, dtype=np.float32)
+            B.mppi_set_sdf_weights(self.ctx, self._keep, self._scales)
         B.mppi_set_gates(self.ctx, self.G, poses if self.G else None, lat if self.G else None)
         self.K, self.H = self.prm["K"], self.prm["H"]
 

@@ -364,3 +364,23 @@ def test_step_mlp_fp16_full_size_two_gates(lib):
     _report("fp16_full_size", err)
     assert err["sdf_mae_mm"] < 1.0 and err["sdf_p99_mm"] < 2.0, err
     g.close()
+
+
+# ---------------------------------------------------------------- Gate-SDF MLP, FP8 E4M3 tensor-core path
+@pytest.mark.parametrize("K,H", [(300, 6), (4096, 50)])
+def test_step_mlp_fp8_errors(lib, K, H):
+    """E4M3 weights and activations (per-tensor scales): errors against the FP64 oracle are reported.
+
+    A numpy E4M3 emulation of this network predicts SDF MAE ~21 mm (p99 ~80 mm); the bound
+    only catches layout or scale mistakes, which give errors of metres.
+    """
+    wl = W.two_gate_mlp()
+    prm = _params(wl, K=K, H=H)
+    g = GpuController(wl, "fp8", prm)
+    out = g.step(state=wl["state"], nominal=W.hover_nominal(H))
+    ref = _oracle(wl, prm, wl["state"], W.hover_nominal(H), 0, True)
+    err = _bf16_errors(g, ref, out)
+    _report(f"fp8_K{K}_H{H}", err)
+    assert err["sdf_mae_mm"] < 60.0, err
+    assert abs(float(out["weights"].astype(np.float64).sum()) - 1.0) < 1e-5
+    g.close()
