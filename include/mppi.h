@@ -48,6 +48,8 @@ extern "C" {
 #define MPPI_E_TIMEOUT     -4   /* a device-side bounded wait gave up; the context stays usable */
 #define MPPI_E_NOT_READY   -5   /* weights or gates required by the SDF mode are not set */
 #define MPPI_E_UNSUPPORTED -6   /* the device is not an sm_103 GPU or the mode is not built */
+#define MPPI_E_ADMISSION   -7   /* a serving request can never fit in the device-memory budget */
+#define MPPI_PENDING        1   /* mppi_server_poll: the request is queued or running */
 
 /* ---- SDF evaluation modes (mppi_config.sdf_mode) ---- */
 #define MPPI_SDF_ANALYTIC  0    /* exact signed distance to the rectangular gate frame */
@@ -270,6 +272,63 @@ int mppi_selftest_tc_gemm(const uint16_t* d_A, const uint16_t* d_B, float* d_D, 
 int mppi_softmax_update_noalloc(const float* d_costs, const float* d_noise, const float* d_nominal, int K, int H,
                                 float lambda, float thrust_min, float thrust_max, float rate_max,
                                 float* d_new_controls, float* d_weights, void* stream);
+
+/* ======================================================================== serving
+ * Continuous batching of control steps from many drones (one request = one
+ * control step of one drone).  Each drone keeps a context on the device: its
+ * warm-started nominal sequence, true state and Philox step counter persist
+ * between its requests (the same chain as mppi_step), so a drone's results do
+ * not depend on which other drones share the GPU.  Requests are admitted in
+ * arrival order as soon as the drone has no request in flight, fewer than
+ * max_inflight requests run and the drone's context fits in the device-memory
+ * budget; the least recently used idle drone is evicted to host memory (its
+ * warm start, state and counter are restored on its next request) when it does
+ * not.  Requests of different drones run concurrently, each on its drone's own
+ * stream.  All functions are thread-safe; a worker thread owned by the server
+ * issues the GPU work.
+ */
+typedef struct mppi_server mppi_server;
+
+typedef struct mppi_server_config {
+    size_t hbm_budget_bytes;   /* device bytes the drone contexts may hold together; 0 = no limit */
+    int32_t max_inflight;      /* requests on the device at once (1 .. 1024) */
+    int32_t sdf_mode;          /* MPPI_SDF_* used by every drone */
+} mppi_server_config;
+
+typedef struct mppi_server_stats {
+    uint64_t submitted, completed, queued, inflight;
+    uint64_t evictions, restores;      /* drone contexts moved to host memory / brought back */
+    size_t device_bytes, peak_device_bytes;
+} mppi_server_stats;
+
+/* Defaults: no budget, 16 requests in flight, BF16 tensor-core SDF. */
+void mppi_server_config_default(mppi_server_config* cfg);
+/* Create a server on the current device (starts its worker thread).  *out is NULL on error. */
+int mppi_server_create(const mppi_server_config* cfg, mppi_server** out);
+/* Drain in-flight work, stop the worker and free every drone context.  NULL is ignored. */
+void mppi_server_destroy(mppi_server* server);
+/* Message of the server's last error (server NULL: the calling thread's last failed create). */
+const char* mppi_server_last_error(const mppi_server* server);
+/* Gate-SDF MLP weights for every drone (same arrays as mppi_set_sdf_weights); call before the first request. */
+int mppi_server_set_sdf_weights(mppi_server* server, const float* const* layers, int n_layers,
+                                const float* fp8_scales);
+/*
+ * Queue one control step of drone drone_id (host buffers, copied before the
+ * call returns): cfg gives the drone's controller parameters (K, H and
+ * max_gates must stay the same for a drone; the server's sdf_mode applies),
+ * state 13 floats, n_gates gate poses (n x 7) and latents (n x 64; NULL in
+ * analytic mode).  *ticket identifies the request.  Returns at once.
+ */
+int mppi_server_submit(mppi_server* server, int drone_id, const mppi_config* cfg, const float* state, int n_gates,
+                       const float* poses, const float* latents, uint64_t* ticket);
+/*
+ * Non-blocking: MPPI_PENDING while the request is queued or running; once it
+ * is done, its status (MPPI_OK with new_controls = U*_new, H x 4, filled; or
+ * the error of that request) and latency_us = submit-to-completion time in
+ * microseconds (nullable).  A finished ticket is reported once.
+ */
+int mppi_server_poll(mppi_server* server, uint64_t ticket, float* new_controls, double* latency_us);
+int mppi_server_get_stats(mppi_server* server, mppi_server_stats* out);
 
 #ifdef __cplusplus
 }

@@ -18,6 +18,8 @@ MPPI_E_CUDA = -3
 MPPI_E_TIMEOUT = -4
 MPPI_E_NOT_READY = -5
 MPPI_E_UNSUPPORTED = -6
+MPPI_E_ADMISSION = -7
+MPPI_PENDING = 1
 
 MPPI_SDF_ANALYTIC = 0
 MPPI_SDF_MLP_FP32 = 1
@@ -42,6 +44,8 @@ EXPORTS = [
     "mppi_get_state", "mppi_set_step_counter", "mppi_get_step_counter", "mppi_read_buffer",
     "mppi_read_noise_words", "mppi_set_timing", "mppi_get_kernel_times", "mppi_kernels_per_step",
     "mppi_selftest_tc_gemm", "mppi_softmax_update_noalloc",
+    "mppi_server_config_default", "mppi_server_create", "mppi_server_destroy", "mppi_server_last_error",
+    "mppi_server_set_sdf_weights", "mppi_server_submit", "mppi_server_poll", "mppi_server_get_stats",
 ]
 
 
@@ -62,6 +66,16 @@ class MppiConfig(ctypes.Structure):
         ("softplus_beta", ctypes.c_float),
         ("seed", ctypes.c_uint64), ("drone_id", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
     ]
+
+
+class MppiServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32), ("sdf_mode", ctypes.c_int32)]
+
+
+class MppiServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("queued", ctypes.c_uint64),
+                ("inflight", ctypes.c_uint64), ("evictions", ctypes.c_uint64), ("restores", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_size_t), ("peak_device_bytes", ctypes.c_size_t)]
 
 
 _vp = ctypes.c_void_p
@@ -88,6 +102,15 @@ _SIGS = {
     "mppi_selftest_tc_gemm": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "mppi_softmax_update_noalloc": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_float,
                                                    ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp]),
+    "mppi_server_config_default": (None, [ctypes.POINTER(MppiServerConfig)]),
+    "mppi_server_create": (ctypes.c_int, [ctypes.POINTER(MppiServerConfig), ctypes.POINTER(_vp)]),
+    "mppi_server_destroy": (None, [_vp]),
+    "mppi_server_last_error": (ctypes.c_char_p, [_vp]),
+    "mppi_server_set_sdf_weights": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.c_int, _vp]),
+    "mppi_server_submit": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(MppiConfig), _vp, ctypes.c_int, _vp, _vp,
+                                          ctypes.POINTER(ctypes.c_uint64)]),
+    "mppi_server_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, ctypes.POINTER(ctypes.c_double)]),
+    "mppi_server_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(MppiServerStats)]),
 }
 
 _lib = None
@@ -230,3 +253,58 @@ def mppi_softmax_update_noalloc(d_costs, d_noise, d_nominal, K, H, lam, thrust_m
 
 def mppi_selftest_tc_gemm(d_A, d_B, d_D, stream=None):
     return _check(load().mppi_selftest_tc_gemm(_ptr(d_A), _ptr(d_B), _ptr(d_D), stream))
+
+
+# ------------------------------------------------------------------ serving
+def _scheck(rc, server=None):
+    if rc < 0:
+        msg = load().mppi_server_last_error(server)
+        raise MppiError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def mppi_server_config_default():
+    cfg = MppiServerConfig()
+    load().mppi_server_config_default(ctypes.byref(cfg))
+    return cfg
+
+
+def mppi_server_create(cfg):
+    srv = _vp()
+    _scheck(load().mppi_server_create(ctypes.byref(cfg), ctypes.byref(srv)))
+    return srv
+
+
+def mppi_server_destroy(server):
+    load().mppi_server_destroy(server)
+
+
+def mppi_server_last_error(server=None):
+    m = load().mppi_server_last_error(server)
+    return m.decode() if m else ""
+
+
+def mppi_server_set_sdf_weights(server, layers, fp8_scales=None):
+    arr = (_vp * len(layers))(*[_ptr(a) for a in layers])
+    return _scheck(load().mppi_server_set_sdf_weights(server, arr, len(layers), _ptr(fp8_scales)), server)
+
+
+def mppi_server_submit(server, drone_id, cfg, state, n_gates, poses, latents):
+    """Queue one control step; returns its ticket."""
+    t = ctypes.c_uint64()
+    _scheck(load().mppi_server_submit(server, drone_id, ctypes.byref(cfg), _ptr(state), n_gates, _ptr(poses),
+                                      _ptr(latents), ctypes.byref(t)), server)
+    return t.value
+
+
+def mppi_server_poll(server, ticket, new_controls):
+    """Returns (status, latency_us): status MPPI_PENDING while queued or running; raises on a request error."""
+    lat = ctypes.c_double()
+    rc = _scheck(load().mppi_server_poll(server, ticket, _ptr(new_controls), ctypes.byref(lat)), server)
+    return rc, lat.value
+
+
+def mppi_server_get_stats(server):
+    st = MppiServerStats()
+    _scheck(load().mppi_server_get_stats(server, ctypes.byref(st)), server)
+    return {f: getattr(st, f) for f, _ in MppiServerStats._fields_}

@@ -10,6 +10,7 @@
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
+#include "ctx_internal.h"
 #include "kernels.h"
 #include "mppi.h"
 
@@ -50,6 +51,8 @@ struct mppi_ctx {
     // pinned staging
     float* h_in = nullptr;        // state(16) | nominal(H*4) | poses(maxG*8) | latents(maxG*64)
     float* h_out = nullptr;       // unew(H*4) | w(K) | J(K) | err(1)
+    // completion of the last step enqueued by the serving path
+    cudaEvent_t done = nullptr;
     // the step's kernels as one CUDA graph, re-captured when a launch argument changes
     cudaGraphExec_t gexec = nullptr;
     bool graph_dirty = true;
@@ -317,6 +320,7 @@ void mppi_destroy(mppi_ctx* c) {
     if (c->h_out) cudaFreeHost(c->h_out);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
+    if (c->done) cudaEventDestroy(c->done);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -403,6 +407,11 @@ int mppi_create(const mppi_config* cfg, void* cuda_stream, mppi_ctx** out) {
         std::snprintf(g_thread_err, sizeof(g_thread_err), "pinned host allocation failed");
         mppi_destroy(c);
         return MPPI_E_OOM;
+    }
+    if (cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming) != cudaSuccess) {
+        std::snprintf(g_thread_err, sizeof(g_thread_err), "cudaEventCreate failed");
+        mppi_destroy(c);
+        return MPPI_E_CUDA;
     }
     for (auto& e : c->ev) {
         if (cudaEventCreate(&e) != cudaSuccess) {
@@ -755,6 +764,93 @@ int mppi_selftest_tc_gemm(const uint16_t* d_A, const uint16_t* d_B, float* d_D, 
 
 namespace mppi {
 void set_thread_error(const char* msg) { std::snprintf(g_thread_err, sizeof(g_thread_err), "%s", msg); }
+
+// ---------------------------------------------------------------- serving hooks
+int ctx_enqueue_host_step(mppi_ctx* c, const float* state, int n_gates, const float* poses, const float* latents) {
+    const int H = c->cfg.H;
+    if (n_gates < 0 || n_gates > c->cfg.max_gates) return fail(c, MPPI_E_INVALID, "n_gates out of range");
+    if (!finite_all(state, 13)) return fail(c, MPPI_E_INVALID, "non-finite state");
+    if (n_gates > 0 && (!poses || !finite_all(poses, static_cast<size_t>(n_gates) * 7)))
+        return fail(c, MPPI_E_INVALID, "bad gate poses");
+    if (n_gates > 0 && is_mlp(c) && (!latents || !finite_all(latents, static_cast<size_t>(n_gates) * kLatent)))
+        return fail(c, MPPI_E_INVALID, "bad latents");
+    // the staging buffers are free: the caller has one request per context in flight
+    float* hs = c->h_in;
+    float* hp = c->h_in + 16 + H * 4;
+    float* hl = hp + c->cfg.max_gates * 8;
+    std::memcpy(hs, state, 13 * sizeof(float));
+    for (int g = 0; g < n_gates; ++g) {
+        for (int i = 0; i < 7; ++i) hp[8 * g + i] = poses[7 * g + i];
+        hp[8 * g + 7] = 0.f;
+    }
+    if (c->n_gates != n_gates) c->graph_dirty = true;
+    c->n_gates = n_gates;
+    CUDA_TRY(c, cudaMemcpyAsync(c->B.state, hs, 13 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    if (n_gates > 0) {
+        CUDA_TRY(c, cudaMemcpyAsync(c->B.poses, hp, n_gates * 8 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        if (latents) {
+            std::memcpy(hl, latents, static_cast<size_t>(n_gates) * kLatent * sizeof(float));
+            CUDA_TRY(c, cudaMemcpyAsync(c->d_latents, hl, n_gates * kLatent * sizeof(float), cudaMemcpyHostToDevice,
+                                        c->stream));
+            c->have_latents = true;
+            int rc = recompute_b1p(c);
+            if (rc != MPPI_OK) return rc;
+        }
+    }
+    int rc = check_ready(c);
+    if (rc != MPPI_OK) return rc;
+    rc = launch_step(c);
+    if (rc != MPPI_OK) return rc;
+    float* ho = c->h_out;
+    CUDA_TRY(c, cudaMemcpyAsync(ho, c->B.unew, H * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(ho + H * 4 + 2 * c->cfg.K, c->B.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaEventRecord(c->done, c->stream));
+    ++c->step_count;
+    return MPPI_OK;
+}
+
+int ctx_poll_host_step(mppi_ctx* c, float* new_controls) {
+    const cudaError_t q = cudaEventQuery(c->done);
+    if (q == cudaErrorNotReady) return 1;
+    if (q != cudaSuccess) return fail(c, MPPI_E_CUDA, "step failed: %s", cudaGetErrorString(q));
+    const int H = c->cfg.H;
+    const int* herr = reinterpret_cast<const int*>(c->h_out + H * 4 + 2 * c->cfg.K);
+    if (*herr != 0) {
+        CUDA_TRY(c, cudaMemsetAsync(c->B.err, 0, sizeof(int), c->stream));
+        return fail(c, MPPI_E_TIMEOUT, "a device-side wait timed out (error word %d)", *herr);
+    }
+    std::memcpy(new_controls, c->h_out, static_cast<size_t>(H) * 4 * sizeof(float));
+    return MPPI_OK;
+}
+
+int ctx_save(mppi_ctx* c, float* nominal, float* state, uint64_t* step) {
+    int rc = mppi_get_nominal(c, nominal);
+    if (rc != MPPI_OK) return rc;
+    rc = mppi_get_state(c, state);
+    if (rc != MPPI_OK) return rc;
+    *step = c->step_count;
+    return MPPI_OK;
+}
+
+int ctx_restore(mppi_ctx* c, const float* nominal, const float* state, uint64_t step) {
+    const int H = c->cfg.H;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    std::memcpy(c->h_in, state, 13 * sizeof(float));
+    std::memcpy(c->h_in + 16, nominal, static_cast<size_t>(H) * 4 * sizeof(float));
+    CUDA_TRY(c, cudaMemcpyAsync(c->B.state, c->h_in, 13 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->B.nominal, c->h_in + 16, H * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return mppi_set_step_counter(c, step);
+}
+
+size_t ctx_device_bytes(const mppi_config& g) {
+    const size_t K = g.K, H = g.H, MG = g.max_gates;
+    const size_t floats = 16 + 4 * H + 2 + MG * 8 + MG * kHidden + 4 * K * H * 2 + 3 * K + K * H + 2 * K + 4 * H +
+                          2 * ((K + 127) / 128) + 4 + 4 + 1 + MG * kLatent;
+    const size_t weights = sizeof(float) * (kHidden * (3 + kLatent) + kHidden + 3 * (kHidden * kHidden + kHidden) + kHidden) +
+                           3 * kHidden * kHidden * (2 + 2 + 1) + kHidden * 16 * 2;
+    return floats * sizeof(float) + weights;
+}
 
 uint16_t float_to_bf16(float f) {
     uint32_t u;

@@ -1,0 +1,372 @@
+// Serving engine: continuous batching of MPPI control steps from many drones.
+//
+// Each drone owns a controller context (device-resident warm start, true state
+// and Philox step counter, its own stream and captured step graph), created on
+// the drone's first request when the device-memory budget allows.  A worker
+// thread admits queued requests in arrival order as soon as the drone is idle,
+// an in-flight slot is free and the drone's context fits in the budget; when it
+// does not fit, the least recently used idle drone is evicted (its warm start,
+// state and counter go to host memory and come back on its next request).
+// Requests of different drones run concurrently on their own streams, so work
+// that arrives while other solves are on the GPU overlaps with them.  Results
+// are collected per ticket with their submit-to-completion latency.
+#include <chrono>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "ctx_internal.h"
+#include "kernels.h"
+#include "mppi.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Drone {
+    mppi_config cfg{};
+    mppi_ctx* ctx = nullptr;
+    size_t bytes = 0;
+    bool busy = false;
+    uint64_t last_use = 0;
+    bool saved = false;               // warm start held in host memory after an eviction
+    std::vector<float> nominal;
+    float state[13] = {};
+    uint64_t step = 0;
+};
+
+struct Request {
+    uint64_t ticket = 0;
+    int drone = 0;
+    float state[13] = {};
+    int n_gates = 0;
+    std::vector<float> poses, latents;
+    Clock::time_point t_submit;
+};
+
+struct Inflight {
+    uint64_t ticket;
+    int drone;
+    Clock::time_point t_submit;
+};
+
+struct Result {
+    int status = MPPI_OK;
+    std::vector<float> controls;
+    double latency_us = 0.0;
+};
+
+}  // namespace
+
+struct mppi_server {
+    mppi_server_config cfg{};
+    int device = 0;
+    std::vector<std::vector<float>> layers;
+    std::vector<float> fp8;
+    bool have_weights = false;
+    std::mutex mu;
+    std::thread worker;
+    bool stop = false;
+    std::deque<Request> queue;
+    std::unordered_map<int, Drone> drones;
+    std::vector<Inflight> inflight;
+    std::unordered_map<uint64_t, Result> results;
+    uint64_t next_ticket = 1;
+    uint64_t lru_clock = 0;
+    size_t used_bytes = 0, peak_bytes = 0;
+    uint64_t completed = 0, evictions = 0, restores = 0, admitted = 0;
+    char err[512] = "";
+};
+
+namespace {
+
+thread_local char g_server_err[512] = "";
+
+int sfail(mppi_server* s, int code, const char* fmt, ...) {
+    char* dst = s ? s->err : g_server_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+// Make room for `need` bytes by evicting least recently used idle drones.
+bool make_room(mppi_server* s, size_t need, int keep) {
+    const size_t budget = s->cfg.hbm_budget_bytes;
+    while (budget != 0 && s->used_bytes + need > budget) {
+        Drone* victim = nullptr;
+        for (auto& kv : s->drones) {
+            Drone& d = kv.second;
+            if (kv.first == keep || d.ctx == nullptr || d.busy) continue;
+            if (victim == nullptr || d.last_use < victim->last_use) victim = &d;
+        }
+        if (victim == nullptr) return false;
+        victim->nominal.assign(static_cast<size_t>(victim->cfg.H) * 4, 0.f);
+        if (mppi::ctx_save(victim->ctx, victim->nominal.data(), victim->state, &victim->step) != MPPI_OK) return false;
+        victim->saved = true;
+        mppi_destroy(victim->ctx);
+        victim->ctx = nullptr;
+        s->used_bytes -= victim->bytes;
+        ++s->evictions;
+    }
+    return true;
+}
+
+// Create (or restore) the drone's context.  Returns MPPI_OK, 1 when the budget
+// cannot hold it right now, or an error.
+int ensure_context(mppi_server* s, int id, Drone& d) {
+    if (d.ctx) return MPPI_OK;
+    const size_t need = mppi::ctx_device_bytes(d.cfg);
+    if (s->cfg.hbm_budget_bytes != 0 && need > s->cfg.hbm_budget_bytes)
+        return sfail(s, MPPI_E_ADMISSION, "drone %d needs %zu bytes, more than the whole budget", id, need);
+    if (!make_room(s, need, id)) return 1;
+    mppi_ctx* c = nullptr;
+    int rc = mppi_create(&d.cfg, nullptr, &c);
+    if (rc != MPPI_OK) return sfail(s, rc, "drone %d: %s", id, mppi_last_error(nullptr));
+    if (s->have_weights && d.cfg.sdf_mode != MPPI_SDF_ANALYTIC) {
+        const float* ptrs[2 * MPPI_MLP_LAYERS];
+        for (int i = 0; i < 2 * MPPI_MLP_LAYERS; ++i) ptrs[i] = s->layers[i].data();
+        rc = mppi_set_sdf_weights(c, ptrs, 2 * MPPI_MLP_LAYERS, s->fp8.empty() ? nullptr : s->fp8.data());
+        if (rc != MPPI_OK) {
+            sfail(s, rc, "drone %d: %s", id, mppi_last_error(c));
+            mppi_destroy(c);
+            return rc;
+        }
+    }
+    if (d.saved) {
+        rc = mppi::ctx_restore(c, d.nominal.data(), d.state, d.step);
+        if (rc != MPPI_OK) {
+            sfail(s, rc, "drone %d restore: %s", id, mppi_last_error(c));
+            mppi_destroy(c);
+            return rc;
+        }
+        d.saved = false;
+        ++s->restores;
+    }
+    d.ctx = c;
+    d.bytes = need;
+    s->used_bytes += need;
+    if (s->used_bytes > s->peak_bytes) s->peak_bytes = s->used_bytes;
+    return MPPI_OK;
+}
+
+void finish(mppi_server* s, const Inflight& f, int status, std::vector<float>&& controls) {
+    Result r;
+    r.status = status;
+    r.controls = std::move(controls);
+    r.latency_us = std::chrono::duration<double, std::micro>(Clock::now() - f.t_submit).count();
+    s->results[f.ticket] = std::move(r);
+    ++s->completed;
+}
+
+void worker_loop(mppi_server* s) {
+    cudaSetDevice(s->device);
+    std::vector<float> scratch;
+    while (true) {
+        bool progress = false, idle = false;
+        {
+            std::lock_guard<std::mutex> lock(s->mu);
+            // completions
+            for (size_t i = 0; i < s->inflight.size();) {
+                const Inflight f = s->inflight[i];
+                Drone& d = s->drones[f.drone];
+                scratch.resize(static_cast<size_t>(d.cfg.H) * 4);
+                const int rc = mppi::ctx_poll_host_step(d.ctx, scratch.data());
+                if (rc == 1) {
+                    ++i;
+                    continue;
+                }
+                std::vector<float> ctrl(scratch.begin(), scratch.end());
+                if (rc != MPPI_OK) sfail(s, rc, "drone %d: %s", f.drone, mppi_last_error(d.ctx));
+                finish(s, f, rc, std::move(ctrl));
+                d.busy = false;
+                s->inflight.erase(s->inflight.begin() + static_cast<long>(i));
+                progress = true;
+            }
+            // admissions, in arrival order; a drone with a request in flight keeps its later ones queued
+            for (auto it = s->queue.begin(); it != s->queue.end();) {
+                if (static_cast<int>(s->inflight.size()) >= s->cfg.max_inflight) break;
+                Drone& d = s->drones[it->drone];
+                if (d.busy) {
+                    ++it;
+                    continue;
+                }
+                const int rc = ensure_context(s, it->drone, d);
+                if (rc == 1) break;                       // wait for memory to free up
+                Inflight f{it->ticket, it->drone, it->t_submit};
+                if (rc != MPPI_OK) {
+                    finish(s, f, rc, {});
+                    it = s->queue.erase(it);
+                    continue;
+                }
+                const int e = mppi::ctx_enqueue_host_step(d.ctx, it->state, it->n_gates,
+                                                          it->poses.empty() ? nullptr : it->poses.data(),
+                                                          it->latents.empty() ? nullptr : it->latents.data());
+                if (e != MPPI_OK) {
+                    sfail(s, e, "drone %d: %s", it->drone, mppi_last_error(d.ctx));
+                    finish(s, f, e, {});
+                    it = s->queue.erase(it);
+                    continue;
+                }
+                d.busy = true;
+                d.last_use = ++s->lru_clock;
+                ++s->admitted;
+                s->inflight.push_back(f);
+                it = s->queue.erase(it);
+                progress = true;
+            }
+            idle = s->queue.empty() && s->inflight.empty();
+            if (idle && s->stop) break;
+        }
+        if (idle)
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        else if (!progress)
+            std::this_thread::yield();
+    }
+}
+
+bool finite(const float* x, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!(x[i] == x[i]) || x[i] > 3.0e38f || x[i] < -3.0e38f) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mppi_server_config_default(mppi_server_config* c) {
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->hbm_budget_bytes = 0;
+    c->max_inflight = 16;
+    c->sdf_mode = MPPI_SDF_MLP_BF16;
+}
+
+int mppi_server_create(const mppi_server_config* cfg, mppi_server** out) {
+    if (!out || !cfg) return sfail(nullptr, MPPI_E_INVALID, "NULL argument");
+    *out = nullptr;
+    if (cfg->max_inflight < 1 || cfg->max_inflight > 1024)
+        return sfail(nullptr, MPPI_E_INVALID, "max_inflight=%d out of [1, 1024]", cfg->max_inflight);
+    if (cfg->sdf_mode < MPPI_SDF_ANALYTIC || cfg->sdf_mode > MPPI_SDF_MLP_FP8)
+        return sfail(nullptr, MPPI_E_INVALID, "sdf_mode=%d", cfg->sdf_mode);
+    mppi_server* s = new (std::nothrow) mppi_server();
+    if (!s) return sfail(nullptr, MPPI_E_OOM, "host allocation failed");
+    s->cfg = *cfg;
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        delete s;
+        return sfail(nullptr, MPPI_E_UNSUPPORTED, "no CUDA device");
+    }
+    s->worker = std::thread(worker_loop, s);
+    *out = s;
+    return MPPI_OK;
+}
+
+void mppi_server_destroy(mppi_server* s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->stop = true;
+    }
+    if (s->worker.joinable()) s->worker.join();
+    for (auto& kv : s->drones)
+        if (kv.second.ctx) mppi_destroy(kv.second.ctx);
+    delete s;
+}
+
+const char* mppi_server_last_error(const mppi_server* s) { return s ? s->err : g_server_err; }
+
+int mppi_server_set_sdf_weights(mppi_server* s, const float* const* layers, int n_layers, const float* fp8_scales) {
+    if (!s) return sfail(nullptr, MPPI_E_INVALID, "server is NULL");
+    if (!layers || n_layers != 2 * MPPI_MLP_LAYERS) return sfail(s, MPPI_E_INVALID, "expected 10 layer pointers");
+    const size_t sizes[10] = {MPPI_HIDDEN * (3 + MPPI_LATENT_DIM), MPPI_HIDDEN, MPPI_HIDDEN * MPPI_HIDDEN, MPPI_HIDDEN,
+                              MPPI_HIDDEN * MPPI_HIDDEN, MPPI_HIDDEN, MPPI_HIDDEN * MPPI_HIDDEN, MPPI_HIDDEN,
+                              MPPI_HIDDEN, 1};
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (!s->drones.empty()) return sfail(s, MPPI_E_INVALID, "set the weights before the first request");
+    s->layers.clear();
+    for (int i = 0; i < n_layers; ++i) {
+        if (!layers[i] || !finite(layers[i], sizes[i])) return sfail(s, MPPI_E_INVALID, "layer array %d", i);
+        s->layers.emplace_back(layers[i], layers[i] + sizes[i]);
+    }
+    s->fp8.clear();
+    if (fp8_scales) s->fp8.assign(fp8_scales, fp8_scales + 3);
+    s->have_weights = true;
+    return MPPI_OK;
+}
+
+int mppi_server_submit(mppi_server* s, int drone_id, const mppi_config* cfg, const float* state, int n_gates,
+                       const float* poses, const float* latents, uint64_t* ticket) {
+    if (!s || !cfg || !state || !ticket) return sfail(s, MPPI_E_INVALID, "NULL argument");
+    if (n_gates < 0 || n_gates > cfg->max_gates) return sfail(s, MPPI_E_INVALID, "n_gates=%d", n_gates);
+    if (n_gates > 0 && !poses) return sfail(s, MPPI_E_INVALID, "poses is NULL");
+    if (s->cfg.sdf_mode != MPPI_SDF_ANALYTIC && n_gates > 0 && !latents)
+        return sfail(s, MPPI_E_INVALID, "latents are required by the MLP SDF");
+    if (!finite(state, 13)) return sfail(s, MPPI_E_INVALID, "non-finite state");
+    Request r;
+    r.drone = drone_id;
+    std::memcpy(r.state, state, sizeof(r.state));
+    r.n_gates = n_gates;
+    if (n_gates > 0) r.poses.assign(poses, poses + 7 * n_gates);
+    if (n_gates > 0 && latents) r.latents.assign(latents, latents + MPPI_LATENT_DIM * n_gates);
+    r.t_submit = Clock::now();
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->cfg.sdf_mode != MPPI_SDF_ANALYTIC && !s->have_weights)
+        return sfail(s, MPPI_E_NOT_READY, "no SDF weights set");
+    auto it = s->drones.find(drone_id);
+    if (it == s->drones.end()) {
+        Drone d;
+        d.cfg = *cfg;
+        d.cfg.sdf_mode = s->cfg.sdf_mode;
+        s->drones.emplace(drone_id, d);
+    } else {
+        const mppi_config& c0 = it->second.cfg;
+        if (c0.K != cfg->K || c0.H != cfg->H || c0.max_gates != cfg->max_gates)
+            return sfail(s, MPPI_E_INVALID, "drone %d: K, H or max_gates differ from its first request", drone_id);
+    }
+    r.ticket = s->next_ticket++;
+    *ticket = r.ticket;
+    s->queue.push_back(std::move(r));
+    return MPPI_OK;
+}
+
+int mppi_server_poll(mppi_server* s, uint64_t ticket, float* new_controls, double* latency_us) {
+    if (!s) return sfail(nullptr, MPPI_E_INVALID, "server is NULL");
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->results.find(ticket);
+    if (it == s->results.end()) {
+        if (ticket == 0 || ticket >= s->next_ticket) return sfail(s, MPPI_E_INVALID, "unknown ticket %llu",
+                                                                  static_cast<unsigned long long>(ticket));
+        return MPPI_PENDING;
+    }
+    const int status = it->second.status;
+    if (status == MPPI_OK && new_controls)
+        std::memcpy(new_controls, it->second.controls.data(), it->second.controls.size() * sizeof(float));
+    if (latency_us) *latency_us = it->second.latency_us;
+    s->results.erase(it);
+    return status;
+}
+
+int mppi_server_get_stats(mppi_server* s, mppi_server_stats* out) {
+    if (!s || !out) return sfail(s, MPPI_E_INVALID, "NULL argument");
+    std::lock_guard<std::mutex> lock(s->mu);
+    out->submitted = s->next_ticket - 1;
+    out->completed = s->completed;
+    out->queued = s->queue.size();
+    out->inflight = s->inflight.size();
+    out->evictions = s->evictions;
+    out->restores = s->restores;
+    out->device_bytes = s->used_bytes;
+    out->peak_device_bytes = s->peak_bytes;
+    return MPPI_OK;
+}
+
+}  // extern "C"

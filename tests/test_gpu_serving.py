@@ -1,0 +1,134 @@
+"""Serving engine: continuous batching of many drones' control steps (GPU).
+
+The bar: every drone's results are the same alone and in the mix (bit-identical:
+each drone's warm start and Philox counter live on the device, and every kernel
+reduces in a fixed order), also when a small device-memory budget forces its
+context to be evicted to host memory and restored between requests.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+from paper_2603_07199_gb300 import binding as B
+
+from .gpu_helpers import flat_layers, make_config
+
+pytestmark = pytest.mark.gpu
+
+
+def _drone_cfg(d, mode="bf16"):
+    return make_config(d["params"], mode, d["G"])
+
+
+def _run(fleet, requests, budget=0, max_inflight=16, mode="bf16", layers=None):
+    """Submit (drone index, state) requests in order without waiting; return controls per request."""
+    cfg = B.mppi_server_config_default()
+    cfg.hbm_budget_bytes = budget
+    cfg.max_inflight = max_inflight
+    cfg.sdf_mode = {"bf16": B.MPPI_SDF_MLP_BF16, "fp32": B.MPPI_SDF_MLP_FP32, "analytic": B.MPPI_SDF_ANALYTIC}[mode]
+    srv = B.mppi_server_create(cfg)
+    keep = flat_layers(layers) if layers is not None else None
+    if keep is not None:
+        B.mppi_server_set_sdf_weights(srv, keep)
+    tickets = []
+    for di, state in requests:
+        d = fleet[di]
+        tickets.append((di, B.mppi_server_submit(srv, d["drone_id"], _drone_cfg(d, mode), np.ascontiguousarray(state, np.float32),
+                                                 d["G"], np.ascontiguousarray(d["poses"]), np.ascontiguousarray(d["latents"]))))
+    outs, lats = [None] * len(tickets), [0.0] * len(tickets)
+    t0 = time.time()
+    pending = set(range(len(tickets)))
+    while pending and time.time() - t0 < 120:
+        for i in list(pending):
+            di, t = tickets[i]
+            U = np.zeros((fleet[di]["params"]["H"], 4), np.float32)
+            st, lat = B.mppi_server_poll(srv, t, U)
+            if st == B.MPPI_OK:
+                outs[i], lats[i] = U, lat
+                pending.discard(i)
+        time.sleep(0.0005)
+    stats = B.mppi_server_get_stats(srv)
+    B.mppi_server_destroy(srv)
+    assert not pending, "requests did not finish"
+    return outs, lats, stats
+
+
+def _states(fleet, n_steps, seed=7):
+    rng = np.random.default_rng(seed)
+    return {i: [np.asarray(d["state"], np.float32) + np.float32(0.05) * rng.standard_normal(13).astype(np.float32) * np.array(
+        [1, 1, 1, 1, 1, 1, 0, 0, 0, 0, 1, 1, 1], np.float32) for _ in range(n_steps)] for i, d in enumerate(fleet)}
+
+
+def test_results_are_the_same_alone_and_in_the_mix(lib):
+    fleet = W.serving_fleet(8, seed=4, Ks=(256, 512, 1024), Hs=(10, 20, 30))
+    layers = W.xavier_mlp(1)
+    n_steps = 4
+    states = _states(fleet, n_steps)
+    target = 3
+    alone, _, _ = _run(fleet, [(target, states[target][s]) for s in range(n_steps)], layers=layers)
+    mix_reqs = [(i, states[i][s]) for s in range(n_steps) for i in range(len(fleet))]
+    mix, lats, stats = _run(fleet, mix_reqs, layers=layers)
+    got = [mix[j] for j, (i, _) in enumerate(mix_reqs) if i == target]
+    for a, b in zip(alone, got):
+        np.testing.assert_array_equal(a, b)
+    assert stats["completed"] == len(mix_reqs) and stats["evictions"] == 0
+    assert all(l > 0 for l in lats)
+
+
+def test_small_budget_evicts_and_restores_without_changing_results(lib):
+    fleet = W.serving_fleet(4, seed=9, Ks=(512,), Hs=(20,))
+    layers = W.xavier_mlp(1)
+    n_steps = 3
+    states = _states(fleet, n_steps, seed=8)
+    reqs = [(i, states[i][s]) for s in range(n_steps) for i in range(len(fleet))]
+    free, _, st_free = _run(fleet, reqs, layers=layers)
+    one = st_free["peak_device_bytes"] // len(fleet)
+    tight, _, st_tight = _run(fleet, reqs, budget=int(2.5 * one), max_inflight=2, layers=layers)
+    assert st_tight["evictions"] > 0 and st_tight["restores"] > 0
+    assert st_tight["peak_device_bytes"] <= int(2.5 * one)
+    for a, b in zip(free, tight):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_serving_matches_a_plain_context(lib):
+    """One drone through the server equals the same steps through mppi_step."""
+    fleet = W.serving_fleet(1, seed=11, Ks=(700,), Hs=(12,))
+    layers = W.xavier_mlp(1)
+    d = fleet[0]
+    states = _states(fleet, 3, seed=12)[0]
+    served, _, _ = _run(fleet, [(0, s) for s in states], layers=layers)
+    ctx = B.mppi_create(_drone_cfg(d))
+    keep = flat_layers(layers)
+    B.mppi_set_sdf_weights(ctx, keep)
+    B.mppi_set_gates(ctx, d["G"], np.ascontiguousarray(d["poses"]), np.ascontiguousarray(d["latents"]))
+    for s, u in zip(states, served):
+        U = np.zeros((12, 4), np.float32)
+        B.mppi_step(ctx, np.ascontiguousarray(s, np.float32), None, None, None, U)
+        np.testing.assert_array_equal(U, u)
+    B.mppi_destroy(ctx)
+
+
+def test_serving_errors(lib):
+    fleet = W.serving_fleet(1, seed=13, Ks=(256,), Hs=(10,))
+    d = fleet[0]
+    cfg = B.mppi_server_config_default()
+    cfg.sdf_mode = B.MPPI_SDF_ANALYTIC
+    cfg.hbm_budget_bytes = 1024          # smaller than any context
+    srv = B.mppi_server_create(cfg)
+    dc = _drone_cfg(d, "analytic")
+    with pytest.raises(B.MppiError):
+        B.mppi_server_submit(srv, 0, dc, np.ascontiguousarray(d["state"]), dc.max_gates + 1,
+                             np.zeros((dc.max_gates + 1, 7), np.float32), None)
+    t = B.mppi_server_submit(srv, 0, dc, np.ascontiguousarray(d["state"]), d["G"], np.ascontiguousarray(d["poses"]), None)
+    U = np.zeros((10, 4), np.float32)
+    t0 = time.time()
+    with pytest.raises(B.MppiError) as e:
+        while time.time() - t0 < 30:
+            st, _ = B.mppi_server_poll(srv, t, U)
+            time.sleep(0.001)
+    assert e.value.code == B.MPPI_E_ADMISSION
+    with pytest.raises(B.MppiError):
+        B.mppi_server_poll(srv, 10 ** 9, U)
+    B.mppi_server_destroy(srv)

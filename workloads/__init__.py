@@ -136,3 +136,33 @@ def four_gate_mlp():
     return dict(name="four_gate_mlp_K16384_H64_G4", params=prm, poses=gate_track(4),
                 latents=latents(4), layers=xavier_mlp(1),
                 state=hover_state([0.0, 0.0, 0.0]), nominal=hover_nominal(64), steps=3)
+
+
+def serving_fleet(n_drones, seed=4, Ks=(1024, 2048, 4096, 8192), Hs=(30, 50, 80), max_gates=4):
+    """Drones of the serving workload: per drone K, H and the number of gates in view
+    (1..max_gates) drawn uniformly, its own seeded gate poses and latents, and a start
+    state near the origin.  Returns a list of dicts (params, poses, latents, state, drone_id)."""
+    rng = np.random.default_rng(seed)
+    fleet = []
+    for d in range(n_drones):
+        K = int(rng.choice(Ks))
+        H = int(rng.choice(Hs))
+        G = int(rng.integers(1, max_gates + 1))
+        prm = params(K, H, drone_id=d)
+        fleet.append(dict(drone_id=d, params=prm, G=G, poses=gate_track(G, seed=1000 + d),
+                          latents=latents(G, seed=2000 + d), state=perturbed_states(1, 3000 + d, hover_state([0, 0, 0]))[0]))
+    return fleet
+
+
+def poisson_arrivals(n_drones, rate_hz, duration_s, seed=5):
+    """Request times of n_drones independent Poisson processes (exponential gaps):
+    a time-sorted list of (t, drone_id)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for d in range(n_drones):
+        t = rng.exponential(1.0 / rate_hz)
+        while t < duration_s:
+            out.append((t, d))
+            t += rng.exponential(1.0 / rate_hz)
+    out.sort()
+    return out
