@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-seconds", type=float, default=1.0)
     return ap.parse_args()
 
 
@@ -196,6 +197,97 @@ def e2e_loop(torch, B, ctx, wl, steps, flush):
     return np.array(out), 13 * 4, H * 4 * 4 + 4
 
 
+def serving_leg(torch, B, dev, duration_s, n_drones=64, rate_hz=100.0):
+    """64 drones, each a Poisson request stream at rate_hz, per-drone K in {1024..8192},
+    H in {30, 50, 80}, 1-4 gates, BF16 SDF, through the serving engine; plus the same
+    requests' solve time alone in the plain FP32 path (a sample of drone configurations)."""
+    import workloads as W
+    fleet = W.serving_fleet(n_drones)
+    keep = []
+    for Wm, b in W.xavier_mlp(1):
+        keep += [np.ascontiguousarray(Wm, np.float32), np.ascontiguousarray(b, np.float32)]
+    cfgs = []
+    for d in fleet:
+        c = B.mppi_config_default()
+        for key in ("K", "H", "dt", "mass", "gravity", "thrust_min", "thrust_max", "rate_max", "sigma_thrust",
+                    "sigma_rate", "w_col", "d_safe", "w_u", "seed", "drone_id"):
+            setattr(c, key, d["params"][key])
+        c.lam = d["params"]["lam"]
+        c.max_gates = d["G"]
+        cfgs.append(c)
+    scfg = B.mppi_server_config_default()
+    scfg.max_inflight = 32
+    scfg.sdf_mode = B.MPPI_SDF_MLP_BF16
+    srv = B.mppi_server_create(scfg)
+    B.mppi_server_set_sdf_weights(srv, keep)
+    inputs = [(np.ascontiguousarray(d["state"], np.float32), np.ascontiguousarray(d["poses"]),
+               np.ascontiguousarray(d["latents"])) for d in fleet]
+    out = np.zeros(80 * 4, np.float32)
+
+    def submit(i):
+        st, po, la = inputs[i]
+        return B.mppi_server_submit(srv, fleet[i]["drone_id"], cfgs[i], st, fleet[i]["G"], po, la)
+
+    # warm-up: one request per drone creates its context and captures its step graph
+    for i in range(n_drones):
+        submit(i)
+    got = 0
+    while got < n_drones:
+        rc, _, _ = B.mppi_server_next_result(srv, out)
+        got += rc == B.MPPI_OK
+    arrivals = W.poisson_arrivals(n_drones, rate_hz, duration_s)
+    owner, lat, kh = {}, [], 0
+    i, done = 0, 0
+    t0 = time.perf_counter()
+    while done < len(arrivals):
+        now = time.perf_counter() - t0
+        while i < len(arrivals) and arrivals[i][0] <= now:
+            owner[submit(arrivals[i][1])] = arrivals[i][1]
+            i += 1
+        rc, t, l = B.mppi_server_next_result(srv, out)
+        if rc == B.MPPI_OK:
+            done += 1
+            lat.append(l)
+            p = fleet[owner.pop(t)]["params"]
+            kh += p["K"] * p["H"]
+    wall = time.perf_counter() - t0
+    stats = B.mppi_server_get_stats(srv)
+    B.mppi_server_destroy(srv)
+    offered = sum(fleet[d]["params"]["K"] * fleet[d]["params"]["H"] for _, d in arrivals) / duration_s
+    # the same solves alone, one at a time, in the plain FP32 path (device time per configuration)
+    t32 = {}
+    for d, c in list(zip(fleet, cfgs))[:8]:
+        c32 = B.mppi_config_default()
+        ctypes_copy = [f for f, _ in B.MppiConfig._fields_]
+        for f in ctypes_copy:
+            setattr(c32, f, getattr(c, f))
+        c32.sdf_mode = B.MPPI_SDF_MLP_FP32
+        ctx = B.mppi_create(c32, torch.cuda.current_stream().cuda_stream)
+        B.mppi_set_sdf_weights(ctx, keep)
+        B.mppi_set_gates(ctx, d["G"], np.ascontiguousarray(d["poses"]), np.ascontiguousarray(d["latents"]))
+        U = torch.zeros(d["params"]["H"], 4, device=dev)
+        st = torch.from_numpy(np.ascontiguousarray(d["state"], np.float32)).to(dev)
+        for _ in range(2):
+            B.mppi_step_async(ctx, st, None, None, None, U, None, None)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(3):
+            B.mppi_step_async(ctx, st, None, None, None, U, None, None)
+        ev[1].record()
+        torch.cuda.synchronize()
+        t32[(d["params"]["K"], d["params"]["H"], d["G"])] = ev[0].elapsed_time(ev[1]) / 3
+        B.mppi_destroy(ctx)
+    fp32_kh_per_ms = np.mean([k * h / t for (k, h, g), t in t32.items()])
+    lat = np.array(lat)
+    return {"drones": n_drones, "rate_hz_per_drone": rate_hz, "requests": len(arrivals), "duration_s": duration_s,
+            "offered_rollout_steps_per_s": offered, "value": kh / wall, "unit": UNIT,
+            "p50_ms": float(np.percentile(lat, 50) / 1e3), "p99_ms": float(np.percentile(lat, 99) / 1e3),
+            "max_inflight": scfg.max_inflight, "sdf": "bf16", "evictions": stats["evictions"],
+            "peak_device_bytes": stats["peak_device_bytes"],
+            "fp32_alone": {"rollout_steps_per_s": fp32_kh_per_ms * 1e3,
+                           "solve_ms_by_config": {f"K{k}_H{h}_G{g}": t for (k, h, g), t in t32.items()}}}
+
+
 def cpu_baseline(wl, seconds):
     """The FP64 oracle, as it stands, on the host cores: whole control steps until `seconds` pass."""
     from oracle import mppi as O
@@ -285,6 +377,8 @@ def run_ours(args):
     kt32 = kernel_times(torch, B, ctx32, 5, flush, wl, dev)
     B.mppi_destroy(ctx32)
 
+    serving = serving_leg(torch, B, dev, args.serving_seconds) if args.serving_seconds > 0 else None
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -329,6 +423,7 @@ def run_ours(args):
         "e2e": {"value": K * H / (e2e_ms.mean() * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "p50_ms": float(np.percentile(e2e_ms, 50)),
                 "p99_ms": float(np.percentile(e2e_ms, 99))},
+        "serving": serving,
         "gpu_launches": per_launch * args.steps,
         "clocks": clocks,
         "wall_s_timed_region": t_wall,

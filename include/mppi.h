@@ -328,6 +328,14 @@ int mppi_server_submit(mppi_server* server, int drone_id, const mppi_config* cfg
  * microseconds (nullable).  A finished ticket is reported once.
  */
 int mppi_server_poll(mppi_server* server, uint64_t ticket, float* new_controls, double* latency_us);
+/*
+ * Non-blocking: take any one finished request: MPPI_PENDING when none is
+ * finished; otherwise *ticket, its status (as mppi_server_poll) and, for
+ * MPPI_OK, new_controls (cap_floats floats available; H x 4 are written).
+ */
+int mppi_server_next_result(mppi_server* server, uint64_t* ticket, float* new_controls, size_t cap_floats,
+                            double* latency_us);
+/* Counters of the server (submitted, completed, queued, in flight, evictions, restores, device bytes). */
 int mppi_server_get_stats(mppi_server* server, mppi_server_stats* out);
 
 #ifdef __cplusplus

@@ -45,7 +45,8 @@ EXPORTS = [
     "mppi_read_noise_words", "mppi_set_timing", "mppi_get_kernel_times", "mppi_kernels_per_step",
     "mppi_selftest_tc_gemm", "mppi_softmax_update_noalloc",
     "mppi_server_config_default", "mppi_server_create", "mppi_server_destroy", "mppi_server_last_error",
-    "mppi_server_set_sdf_weights", "mppi_server_submit", "mppi_server_poll", "mppi_server_get_stats",
+    "mppi_server_set_sdf_weights", "mppi_server_submit", "mppi_server_poll", "mppi_server_next_result",
+    "mppi_server_get_stats",
 ]
 
 
@@ -110,6 +111,8 @@ _SIGS = {
     "mppi_server_submit": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(MppiConfig), _vp, ctypes.c_int, _vp, _vp,
                                           ctypes.POINTER(ctypes.c_uint64)]),
     "mppi_server_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, ctypes.POINTER(ctypes.c_double)]),
+    "mppi_server_next_result": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64), _vp, ctypes.c_size_t,
+                                               ctypes.POINTER(ctypes.c_double)]),
     "mppi_server_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(MppiServerStats)]),
 }
 
@@ -302,6 +305,16 @@ def mppi_server_poll(server, ticket, new_controls):
     lat = ctypes.c_double()
     rc = _scheck(load().mppi_server_poll(server, ticket, _ptr(new_controls), ctypes.byref(lat)), server)
     return rc, lat.value
+
+
+def mppi_server_next_result(server, new_controls):
+    """Returns (status, ticket, latency_us) of any finished request, or (MPPI_PENDING, 0, 0.0)."""
+    t = ctypes.c_uint64()
+    lat = ctypes.c_double()
+    cap = 0 if new_controls is None else new_controls.size
+    rc = _scheck(load().mppi_server_next_result(server, ctypes.byref(t), _ptr(new_controls), cap,
+                                                ctypes.byref(lat)), server)
+    return rc, t.value, lat.value
 
 
 def mppi_server_get_stats(server):

@@ -355,6 +355,25 @@ int mppi_server_poll(mppi_server* s, uint64_t ticket, float* new_controls, doubl
     return status;
 }
 
+int mppi_server_next_result(mppi_server* s, uint64_t* ticket, float* new_controls, size_t cap_floats,
+                            double* latency_us) {
+    if (!s || !ticket) return sfail(s, MPPI_E_INVALID, "NULL argument");
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->results.empty()) return MPPI_PENDING;
+    auto it = s->results.begin();
+    *ticket = it->first;
+    const int status = it->second.status;
+    if (status == MPPI_OK && new_controls) {
+        if (it->second.controls.size() > cap_floats)
+            return sfail(s, MPPI_E_INVALID, "new_controls holds %zu floats, the result has %zu", cap_floats,
+                         it->second.controls.size());
+        std::memcpy(new_controls, it->second.controls.data(), it->second.controls.size() * sizeof(float));
+    }
+    if (latency_us) *latency_us = it->second.latency_us;
+    s->results.erase(it);
+    return status;
+}
+
 int mppi_server_get_stats(mppi_server* s, mppi_server_stats* out) {
     if (!s || !out) return sfail(s, MPPI_E_INVALID, "NULL argument");
     std::lock_guard<std::mutex> lock(s->mu);
