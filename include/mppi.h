@@ -273,6 +273,63 @@ int mppi_softmax_update_noalloc(const float* d_costs, const float* d_noise, cons
                                 float lambda, float thrust_min, float thrust_max, float rate_max,
                                 float* d_new_controls, float* d_weights, void* stream);
 
+/* ======================================================================== learned part
+ * Distillation of the exact gate-frame SDF (the frame of mppi_config's gate
+ * geometry) into the Gate-SDF MLP (Sec. III-B trains the decoder with an L1
+ * loss on the SDF; here the target is the exact frame SDF and an Eikonal
+ * term regularises the input gradient):
+ *     L = mean |s - s*| + eikonal_weight mean (|grad_p s| - 1)^2,
+ * at one fixed latent z0, with Adam on FP32 master weights.  Training and
+ * held-out points are sampled on the GPU from Philox: near_surface_fraction
+ * of them a uniform point of the frame surface plus N(0, near_surface_sigma^2 I),
+ * the rest uniform in [-cube_half, cube_half]^3 (gate frame).  The forward
+ * pass carries the three input tangents next to the values; the backward pass
+ * differentiates both (FP32, deterministic reductions).
+ */
+typedef struct mppi_trainer mppi_trainer;
+
+typedef struct mppi_train_config {
+    int32_t batch;                  /* points per step, a multiple of 128 (<= 2^20) */
+    int32_t n_points;               /* training-set size, a multiple of batch (<= 2^26) */
+    int32_t n_holdout;              /* held-out check points, a multiple of 128 (<= 2^22) */
+    float lr, beta1, beta2, eps;    /* Adam */
+    float eikonal_weight;
+    float softplus_beta;
+    float near_surface_fraction, near_surface_sigma, cube_half;
+    float gate_inner_half, gate_outer_half, gate_half_depth;
+    uint64_t seed;                  /* Philox key of the training set (the held-out set uses a derived key) */
+} mppi_train_config;
+
+/* Defaults: batch 65536, 2^21 points, 2^18 held out, lr 1e-3, (0.9, 0.999, 1e-8), Eikonal 0.1,
+ * beta 100, 70 % near-surface with sigma 0.05 m, cube half-width 4 m, the 1.0 / 1.5 / 0.2 m gate. */
+void mppi_train_config_default(mppi_train_config* cfg);
+/*
+ * Create a trainer from initial weights (10 host arrays as in
+ * mppi_set_sdf_weights) and the latent z0 (64 floats); samples the training
+ * and held-out sets on the device.  Synchronous.
+ */
+int mppi_train_create(const mppi_train_config* cfg, const float* const* init_layers, const float* latent,
+                      mppi_trainer** out);
+void mppi_train_destroy(mppi_trainer* trainer);
+const char* mppi_train_last_error(const mppi_trainer* trainer);
+/* Run n_steps Adam steps over consecutive batches of the training set; *last_loss (nullable) = last batch's loss. */
+int mppi_train_step(mppi_trainer* trainer, int n_steps, float* last_loss);
+/*
+ * Loss and gradient of one explicit batch without updating (for checks):
+ * points n x 4 host floats (x, y, z, target), n a multiple of 128 and <= batch;
+ * grads receives mppi_train_num_params() floats in the order W1, b1, W2, b2,
+ * W3, b3, W4, b4, w5, b5 (row-major).  Synchronous.
+ */
+int mppi_train_loss_grads(mppi_trainer* trainer, const float* points, int n, float* loss, float* grads);
+/* Current weights into 10 host arrays (shapes of mppi_set_sdf_weights). */
+int mppi_train_get_weights(mppi_trainer* trainer, float* const* layers_out);
+/* Held-out error against the exact SDF, in metres: mean, p99, max, and p99 over points with |SDF| < 0.3 m. */
+int mppi_train_evaluate(mppi_trainer* trainer, float* mae, float* p99, float* max_err, float* near_p99);
+/* Copy the training (which = 0) or held-out (1) points, n x 4 floats (x, y, z, target). */
+int mppi_train_read_points(mppi_trainer* trainer, int which, float* out, size_t n_floats);
+/* Number of trainable parameters (the length of the gradient vector). */
+int mppi_train_num_params(void);
+
 /* ======================================================================== serving
  * Continuous batching of control steps from many drones (one request = one
  * control step of one drone).  Each drone keeps a context on the device: its

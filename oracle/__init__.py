@@ -19,6 +19,7 @@ The oracle restates the paper's method step by step in float64 with numpy:
                    distance to the rectangular gate frame.
 * ``mlp``       -- the Gate-SDF decoder g_phi(z, p) (Sec. III-B), softplus MLP,
                    and its input gradient (for the Eikonal term).
+* ``distill``   -- the distillation loss (L1 + Eikonal), its gradients and Adam.
 * ``mppi``      -- per-rollout costs (Eq. 8-10 in the configured form),
                    softmax weights and the weighted update (Eq. 5), the
                    receding-horizon shift, one whole control step and a
@@ -30,4 +31,4 @@ states) are passed in by the caller from the seeded generators in
 ``workloads``.
 """
 
-from . import philox, noise, dynamics, gate_sdf, mlp, mppi  # noqa: F401
+from . import philox, noise, dynamics, gate_sdf, mlp, mppi, distill  # noqa: F401

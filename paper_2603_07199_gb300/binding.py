@@ -47,6 +47,9 @@ EXPORTS = [
     "mppi_server_config_default", "mppi_server_create", "mppi_server_destroy", "mppi_server_last_error",
     "mppi_server_set_sdf_weights", "mppi_server_submit", "mppi_server_poll", "mppi_server_next_result",
     "mppi_server_get_stats",
+    "mppi_train_config_default", "mppi_train_create", "mppi_train_destroy", "mppi_train_last_error",
+    "mppi_train_step", "mppi_train_loss_grads", "mppi_train_get_weights", "mppi_train_evaluate",
+    "mppi_train_read_points", "mppi_train_num_params",
 ]
 
 
@@ -77,6 +80,15 @@ class MppiServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("queued", ctypes.c_uint64),
                 ("inflight", ctypes.c_uint64), ("evictions", ctypes.c_uint64), ("restores", ctypes.c_uint64),
                 ("device_bytes", ctypes.c_size_t), ("peak_device_bytes", ctypes.c_size_t)]
+
+
+class MppiTrainConfig(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int32), ("n_points", ctypes.c_int32), ("n_holdout", ctypes.c_int32),
+                ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("eikonal_weight", ctypes.c_float), ("softplus_beta", ctypes.c_float),
+                ("near_surface_fraction", ctypes.c_float), ("near_surface_sigma", ctypes.c_float),
+                ("cube_half", ctypes.c_float), ("gate_inner_half", ctypes.c_float),
+                ("gate_outer_half", ctypes.c_float), ("gate_half_depth", ctypes.c_float), ("seed", ctypes.c_uint64)]
 
 
 _vp = ctypes.c_void_p
@@ -114,6 +126,17 @@ _SIGS = {
     "mppi_server_next_result": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64), _vp, ctypes.c_size_t,
                                                ctypes.POINTER(ctypes.c_double)]),
     "mppi_server_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(MppiServerStats)]),
+    "mppi_train_config_default": (None, [ctypes.POINTER(MppiTrainConfig)]),
+    "mppi_train_create": (ctypes.c_int, [ctypes.POINTER(MppiTrainConfig), ctypes.POINTER(_vp), _vp,
+                                         ctypes.POINTER(_vp)]),
+    "mppi_train_destroy": (None, [_vp]),
+    "mppi_train_last_error": (ctypes.c_char_p, [_vp]),
+    "mppi_train_step": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
+    "mppi_train_loss_grads": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float), _vp]),
+    "mppi_train_get_weights": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
+    "mppi_train_evaluate": (ctypes.c_int, [_vp] + [ctypes.POINTER(ctypes.c_float)] * 4),
+    "mppi_train_read_points": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_size_t]),
+    "mppi_train_num_params": (ctypes.c_int, []),
 }
 
 _lib = None
@@ -321,3 +344,62 @@ def mppi_server_get_stats(server):
     st = MppiServerStats()
     _scheck(load().mppi_server_get_stats(server, ctypes.byref(st)), server)
     return {f: getattr(st, f) for f, _ in MppiServerStats._fields_}
+
+
+# ------------------------------------------------------------------ learned part (distillation)
+def _tcheck(rc, trainer=None):
+    if rc < 0:
+        msg = load().mppi_train_last_error(trainer)
+        raise MppiError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def mppi_train_config_default():
+    cfg = MppiTrainConfig()
+    load().mppi_train_config_default(ctypes.byref(cfg))
+    return cfg
+
+
+def mppi_train_create(cfg, init_layers, latent):
+    """init_layers: [W1, b1, ..., w5, b5] float32 arrays; latent: 64 float32."""
+    arr = (_vp * len(init_layers))(*[_ptr(a) for a in init_layers])
+    tr = _vp()
+    _tcheck(load().mppi_train_create(ctypes.byref(cfg), arr, _ptr(latent), ctypes.byref(tr)))
+    return tr
+
+
+def mppi_train_destroy(trainer):
+    load().mppi_train_destroy(trainer)
+
+
+def mppi_train_step(trainer, n_steps):
+    loss = ctypes.c_float()
+    _tcheck(load().mppi_train_step(trainer, n_steps, ctypes.byref(loss)), trainer)
+    return loss.value
+
+
+def mppi_train_num_params():
+    return load().mppi_train_num_params()
+
+
+def mppi_train_loss_grads(trainer, points, grads):
+    loss = ctypes.c_float()
+    _tcheck(load().mppi_train_loss_grads(trainer, _ptr(points), points.shape[0], ctypes.byref(loss), _ptr(grads)),
+            trainer)
+    return loss.value
+
+
+def mppi_train_get_weights(trainer, layers_out):
+    arr = (_vp * len(layers_out))(*[_ptr(a) for a in layers_out])
+    return _tcheck(load().mppi_train_get_weights(trainer, arr), trainer)
+
+
+def mppi_train_evaluate(trainer):
+    """Held-out error against the exact SDF (metres): dict of mae, p99, max, near_p99."""
+    v = [ctypes.c_float() for _ in range(4)]
+    _tcheck(load().mppi_train_evaluate(trainer, *[ctypes.byref(x) for x in v]), trainer)
+    return dict(mae=v[0].value, p99=v[1].value, max=v[2].value, near_p99=v[3].value)
+
+
+def mppi_train_read_points(trainer, which, out):
+    return _tcheck(load().mppi_train_read_points(trainer, which, _ptr(out), out.size), trainer)

@@ -1,0 +1,107 @@
+"""Learned part on the GPU: sampled training points, gradients of the L1 +
+Eikonal loss against the FP64 oracle, Adam, and what training buys.
+
+Tolerances: targets 1e-6 m (the exact frame SDF in FP32); loss 1e-5 relative;
+gradients within 2e-3 of each tensor's largest entry (FP32 sums over the batch
+against FP64); Adam 1e-6 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import distill as OD
+from oracle import gate_sdf
+from paper_2603_07199_gb300 import binding as B
+
+from .gpu_helpers import flat_layers
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ["W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4", "w5", "b5"]
+
+
+def _trainer(batch=512, n_points=1024, n_holdout=1024, seed=7, **over):
+    cfg = B.mppi_train_config_default()
+    cfg.batch, cfg.n_points, cfg.n_holdout, cfg.seed = batch, n_points, n_holdout, seed
+    for k, v in over.items():
+        setattr(cfg, k, v)
+    layers = flat_layers(W.xavier_mlp(1))
+    z0 = W.latents(1, seed=2)[0]
+    return B.mppi_train_create(cfg, layers, z0), layers, z0, cfg
+
+
+def _split(vec, layers):
+    out, o = [], 0
+    for a in layers:
+        out.append(vec[o:o + a.size].reshape(a.shape))
+        o += a.size
+    return out
+
+
+def test_training_points_and_targets(lib):
+    tr, _, _, cfg = _trainer(batch=1024, n_points=1 << 15, n_holdout=1024)
+    pts = np.zeros(4 * cfg.n_points, np.float32)
+    B.mppi_train_read_points(tr, 0, pts)
+    B.mppi_train_destroy(tr)
+    pts = pts.reshape(-1, 4).astype(np.float64)
+    np.testing.assert_allclose(pts[:, 3], gate_sdf.frame_sdf(pts[:, :3]), atol=1e-6)
+    near = np.abs(pts[:, 3]) < 0.25
+    frac = near.mean()
+    assert abs(frac - 0.7) < 0.02, frac                     # 70 % near-surface (+ a few cube points)
+    cube = ~near
+    assert np.all(np.abs(pts[cube, :3]) <= 4.0 + 1e-6)
+    # near-surface offsets are |N(0, 0.05^2)| along the normal: median distance 0.05 * 0.674 (to ~10 %)
+    med = np.median(np.abs(pts[near, 3]))
+    assert 0.025 < med < 0.045, med
+
+
+def test_gradients_match_the_oracle(lib):
+    tr, layers, z0, cfg = _trainer(batch=512)
+    n = 512
+    rng = np.random.default_rng(3)
+    P = np.concatenate([rng.normal(0, 0.6, (n // 2, 3)), rng.uniform(-3, 3, (n // 2, 3))]).astype(np.float32)
+    tgt = gate_sdf.frame_sdf(P.astype(np.float64)).astype(np.float32)
+    pts = np.ascontiguousarray(np.concatenate([P, tgt[:, None]], axis=1), dtype=np.float32)
+    grads = np.zeros(B.mppi_train_num_params(), np.float32)
+    loss = B.mppi_train_loss_grads(tr, pts, grads)
+    B.mppi_train_destroy(tr)
+    pairs = [(layers[2 * i], layers[2 * i + 1]) for i in range(5)]
+    ref_loss, ref = OD.loss_and_grads(pairs, P.astype(np.float64), z0.astype(np.float64),
+                                      tgt.astype(np.float64), lam_e=0.1)
+    assert abs(loss - ref_loss) <= 1e-5 * abs(ref_loss)
+    got = _split(grads.astype(np.float64), layers)
+    for i, (name, g) in enumerate(zip(NAMES, got)):
+        r = ref[i // 2][i % 2].reshape(g.shape)
+        scale = np.max(np.abs(r))
+        assert np.max(np.abs(g - r)) <= 2e-3 * scale + 1e-9, (name, np.max(np.abs(g - r)), scale)
+
+
+def test_adam_step_matches_the_oracle(lib):
+    tr, layers, z0, cfg = _trainer(batch=512, n_points=512)
+    pts = np.zeros(4 * 512, np.float32)
+    B.mppi_train_read_points(tr, 0, pts)
+    grads = np.zeros(B.mppi_train_num_params(), np.float32)
+    B.mppi_train_loss_grads(tr, pts.reshape(-1, 4), grads)
+    B.mppi_train_step(tr, 1)                                 # the same batch: the whole training set
+    after = [np.zeros_like(a) for a in layers]
+    B.mppi_train_get_weights(tr, after)
+    B.mppi_train_destroy(tr)
+    theta0 = np.concatenate([a.ravel() for a in layers]).astype(np.float64)
+    want, _, _ = OD.adam_update(theta0, grads.astype(np.float64), 0.0, 0.0, t=1, lr=cfg.lr, b1=cfg.beta1,
+                                b2=cfg.beta2, eps=cfg.eps)
+    got = np.concatenate([a.ravel() for a in after]).astype(np.float64)
+    np.testing.assert_allclose(got, want, rtol=1e-6, atol=1e-9)
+
+
+def test_training_reduces_the_sdf_error(lib):
+    """A few hundred Adam steps already cut the held-out error of the random network by a large factor."""
+    tr, layers, z0, cfg = _trainer(batch=4096, n_points=1 << 16, n_holdout=8192, seed=11)
+    before = B.mppi_train_evaluate(tr)
+    l0 = B.mppi_train_step(tr, 1)
+    l1 = B.mppi_train_step(tr, 299)
+    after = B.mppi_train_evaluate(tr)
+    B.mppi_train_destroy(tr)
+    assert l1 < 0.5 * l0, (l0, l1)
+    assert after["mae"] < 0.25 * before["mae"], (before, after)
