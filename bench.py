@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-seconds", type=float, default=1.0)
+    ap.add_argument("--distill-steps", type=int, default=0)
     return ap.parse_args()
 
 
@@ -288,6 +289,72 @@ def serving_leg(torch, B, dev, duration_s, n_drones=64, rate_hz=100.0):
                            "solve_ms_by_config": {f"K{k}_H{h}_G{g}": t for (k, h, g), t in t32.items()}}}
 
 
+def distill_leg(torch, B, dev, steps):
+    """Distil the exact frame SDF into the Gate-SDF MLP (2^21 points, batch 65536, Adam 1e-3,
+    L1 + 0.1 Eikonal), then run the two-gate workload with the learned, the exact and the
+    untrained SDF.  The learned SDF is used only when its held-out error stays within 5 mm
+    (mean, and p99 of the points within 0.3 m of the frame); otherwise the exact SDF is kept."""
+    import workloads as W
+    cfg = B.mppi_train_config_default()
+    init = []
+    for Wm, b in W.xavier_mlp(1):
+        init += [np.ascontiguousarray(Wm, np.float32), np.ascontiguousarray(b, np.float32)]
+    z0 = W.latents(1, seed=2)[0]
+    tr = B.mppi_train_create(cfg, init, z0)
+    before = B.mppi_train_evaluate(tr)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = B.mppi_train_step(tr, steps)
+    train_s = time.perf_counter() - t0
+    after = B.mppi_train_evaluate(tr)
+    learned = [np.zeros_like(a) for a in init]
+    B.mppi_train_get_weights(tr, learned)
+    B.mppi_train_destroy(tr)
+    use_learned = after["mae"] <= 5e-3 and after["near_p99"] <= 5e-3
+    # closed-loop comparison on the two-gate workload (every gate with latent z0), starting
+    # hovering 1.5 m in front of the first gate's centre, so the rollouts reach the frame
+    wl = dict(workload())
+    K, H, G = wl["params"]["K"], wl["params"]["H"], wl["poses"].shape[0]
+    lat = np.ascontiguousarray(np.tile(z0, (G, 1)), np.float32)
+    qg = wl["poses"][0, 3:7].astype(np.float64)
+    normal = np.array([qg[0] ** 2 + qg[1] ** 2 - qg[2] ** 2 - qg[3] ** 2, 2 * (qg[1] * qg[2] + qg[0] * qg[3]),
+                       2 * (qg[1] * qg[3] - qg[0] * qg[2])])
+    wl["state"] = W.hover_state(wl["poses"][0, 0:3] - 1.5 * normal + np.array([0.0, 0.0, 0.3]))
+    outs = {}
+    for name, mode, ls in (("exact", "analytic", None), ("learned", "fp32", learned), ("untrained", "fp32", init)):
+        c = B.mppi_config_default()
+        for key in ("K", "H", "dt", "mass", "gravity", "thrust_min", "thrust_max", "rate_max", "sigma_thrust",
+                    "sigma_rate", "w_col", "d_safe", "w_u", "seed"):
+            setattr(c, key, wl["params"][key])
+        c.lam = wl["params"]["lam"]
+        c.max_gates = G
+        c.sdf_mode = B.MPPI_SDF_ANALYTIC if mode == "analytic" else B.MPPI_SDF_MLP_FP32
+        ctx = B.mppi_create(c)
+        if ls is not None:
+            B.mppi_set_sdf_weights(ctx, ls)
+        B.mppi_set_gates(ctx, G, np.ascontiguousarray(wl["poses"]), lat)
+        U = np.zeros((H, 4), np.float32)
+        Us = []
+        B.mppi_step(ctx, np.ascontiguousarray(wl["state"]), None, None, np.ascontiguousarray(wl["nominal"]), U)
+        Us.append(U.copy())
+        for _ in range(9):
+            B.mppi_step(ctx, None, None, None, None, U)
+            Us.append(U.copy())
+        st = np.zeros(13, np.float32)
+        B.mppi_get_state(ctx, st)
+        outs[name] = (np.array(Us), st)
+        B.mppi_destroy(ctx)
+    div = {n: float(np.max(np.abs(outs[n][0] - outs["exact"][0]))) for n in ("learned", "untrained")}
+    pos_div = {n: float(np.linalg.norm(outs[n][1][:3] - outs["exact"][1][:3])) for n in ("learned", "untrained")}
+    return {"steps": steps, "batch": cfg.batch, "points": cfg.n_points, "train_s": train_s,
+            "steps_per_s": steps / train_s if train_s > 0 else None, "final_loss": loss,
+            "holdout_before_mm": {k: v * 1e3 for k, v in before.items()},
+            "holdout_after_mm": {k: v * 1e3 for k, v in after.items()},
+            "fallback_to_exact_sdf": not use_learned,
+            "closed_loop_10_steps": {"max_control_divergence_vs_exact": div,
+                                     "final_position_divergence_m_vs_exact": pos_div}}
+
+
 def cpu_baseline(wl, seconds):
     """The FP64 oracle, as it stands, on the host cores: whole control steps until `seconds` pass."""
     from oracle import mppi as O
@@ -378,6 +445,7 @@ def run_ours(args):
     B.mppi_destroy(ctx32)
 
     serving = serving_leg(torch, B, dev, args.serving_seconds) if args.serving_seconds > 0 else None
+    distill = distill_leg(torch, B, dev, args.distill_steps) if args.distill_steps > 0 else None
 
     if rank != 0:
         if world > 1:
@@ -424,6 +492,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": d2h, "p50_ms": float(np.percentile(e2e_ms, 50)),
                 "p99_ms": float(np.percentile(e2e_ms, 99))},
         "serving": serving,
+        "distill": distill,
         "gpu_launches": per_launch * args.steps,
         "clocks": clocks,
         "wall_s_timed_region": t_wall,

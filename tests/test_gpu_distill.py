@@ -105,3 +105,45 @@ def test_training_reduces_the_sdf_error(lib):
     B.mppi_train_destroy(tr)
     assert l1 < 0.5 * l0, (l0, l1)
     assert after["mae"] < 0.25 * before["mae"], (before, after)
+
+
+def _mppi_step(mode, layers, z0, state, prm, gate):
+    """One MPPI step near a gate with the exact SDF or an MLP (every gate uses latent z0)."""
+    from .gpu_helpers import GpuController
+    wl = dict(params=prm, poses=gate, latents=np.tile(z0, (gate.shape[0], 1)),
+              layers=[(layers[2 * i], layers[2 * i + 1]) for i in range(5)])
+    g = GpuController(wl, mode, prm)
+    out = g.step(state=state, nominal=W.hover_nominal(prm["H"]))
+    pos = g.read(B.MPPI_BUF_POSITIONS)[..., :3]
+    sdf = g.read(B.MPPI_BUF_SDF) if mode != "analytic" else None
+    g.close()
+    return out, pos, sdf
+
+
+def test_learned_sdf_steers_mppi_like_the_exact_one(lib):
+    """What the trained network gains over the untrained one inside the controller: near a gate,
+    its SDF at the rollout states, its rollout costs and its controls are close to the exact SDF's."""
+    tr, layers, z0, cfg = _trainer(batch=8192, n_points=1 << 17, n_holdout=8192, seed=21)
+    B.mppi_train_step(tr, 1500)
+    learned = [np.zeros_like(a) for a in layers]
+    B.mppi_train_get_weights(tr, learned)
+    B.mppi_train_destroy(tr)
+    prm = dict(W.params(2048, 20), lam=1.0)
+    gate = W.origin_gate()
+    res = {"learned": [], "untrained": []}
+    for k, pos0 in enumerate([[-1.0, 0.0, 0.55], [-0.8, 0.5, 0.1], [-1.2, -0.4, -0.45]]):
+        state = W.hover_state(pos0)
+        exact, pos, _ = _mppi_step("analytic", layers, z0, state, prm, gate)
+        s_exact = gate_sdf.frame_sdf(pos.reshape(-1, 3).astype(np.float64))
+        for name, ls in (("learned", learned), ("untrained", layers)):
+            out, pos2, sdf = _mppi_step("fp32", ls, z0, state, prm, gate)
+            np.testing.assert_array_equal(pos2, pos)        # same noise, same rollouts
+            res[name].append(dict(
+                sdf_mae=float(np.mean(np.abs(sdf.reshape(-1) - s_exact))),
+                cost_corr=float(np.corrcoef(out["J"], exact["J"])[0, 1]),
+                ctrl=float(np.max(np.abs(out["U_new"] - exact["U_new"])))))
+    L, U = res["learned"], res["untrained"]
+    for l, u in zip(L, U):
+        assert l["sdf_mae"] < 0.2 * u["sdf_mae"], (l, u)
+        assert l["cost_corr"] > u["cost_corr"] and l["cost_corr"] > 0.9, (l, u)
+    assert np.mean([l["ctrl"] for l in L]) < np.mean([u["ctrl"] for u in U]), (L, U)
