@@ -42,7 +42,7 @@ FMA_FLOPS_PER_QUERY = 2 * 3 * 128 + 2 * 128           # layer 1 (point part) + o
 # dram__bytes_read.sum + dram__bytes_write.sum of one sdf_mlp_bf16 launch at this workload, from
 # the ncu capture summarised in profiles/sdf_mlp_tc_bf16_two_gate_K4096_H50_G2.md (None once the
 # kernel changes)
-SDF_BF16_DRAM_BYTES = 3431168
+SDF_BF16_DRAM_BYTES = None
 
 
 def parse():
@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-seconds", type=float, default=1.0)
     ap.add_argument("--distill-steps", type=int, default=0)
+    ap.add_argument("--four-gate-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -133,13 +134,15 @@ def make_ctx(B, wl, mode, stream, drone_id):
     cfg.drone_id = drone_id
     cfg.max_gates = wl["poses"].shape[0]
     cfg.sdf_mode = {"bf16": B.MPPI_SDF_MLP_BF16, "fp32": B.MPPI_SDF_MLP_FP32, "fp16": B.MPPI_SDF_MLP_FP16,
-                    "fp8": B.MPPI_SDF_MLP_FP8}[mode]
+                    "fp8": B.MPPI_SDF_MLP_FP8, "analytic": B.MPPI_SDF_ANALYTIC}[mode]
     ctx = B.mppi_create(cfg, stream)
-    keep = []
-    for Wm, b in wl["layers"]:
-        keep += [np.ascontiguousarray(Wm, np.float32), np.ascontiguousarray(b, np.float32)]
-    B.mppi_set_sdf_weights(ctx, keep)
-    B.mppi_set_gates(ctx, wl["poses"].shape[0], np.ascontiguousarray(wl["poses"]), np.ascontiguousarray(wl["latents"]))
+    if mode != "analytic":
+        keep = []
+        for Wm, b in wl["layers"]:
+            keep += [np.ascontiguousarray(Wm, np.float32), np.ascontiguousarray(b, np.float32)]
+        B.mppi_set_sdf_weights(ctx, keep)
+    B.mppi_set_gates(ctx, wl["poses"].shape[0], np.ascontiguousarray(wl["poses"], np.float32),
+                     np.ascontiguousarray(wl["latents"], np.float32))
     return ctx
 
 
@@ -382,6 +385,45 @@ def blas_threads():
     return int(env) if env else (os.cpu_count() or 1)
 
 
+def mode_leg(torch, B, wl, mode, stream, flush, dev, steps, drone_id):
+    """Device-resident closed loop of one SDF mode on a workload: rate, latency, per-kernel ms."""
+    K, H, G = wl["params"]["K"], wl["params"]["H"], wl["poses"].shape[0]
+    ctx = make_ctx(B, wl, mode, stream, drone_id)
+    ms = device_loop(torch, B, ctx, wl, steps, 3, flush, dev)
+    kt = kernel_times(torch, B, ctx, min(steps, 10), flush, wl, dev)
+    B.mppi_destroy(ctx)
+    t_sdf = next((v for k, v in kt.items() if k.startswith("sdf_")), None)
+    return {"value": K * H / (ms.mean() * 1e-3), "p50_ms": float(np.percentile(ms, 50)),
+            "p99_ms": float(np.percentile(ms, 99)), "steps": steps, "kernel_ms": kt,
+            "sdf_queries_per_s": K * H * G / (t_sdf * 1e-3) if t_sdf else None}
+
+
+def four_gate_leg(torch, B, stream, flush, dev, steps, drone_id):
+    """The scaled-up precision workload (K=16384, H=64, four gates) in every MLP mode."""
+    import workloads as W
+    wl = W.four_gate_mlp()
+    out = {"workload": wl["name"]}
+    for mode in ("fp32", "bf16", "fp16", "fp8"):
+        out[mode] = mode_leg(torch, B, wl, mode, stream, flush, dev, max(3, steps // 4) if mode == "fp32" else steps,
+                             drone_id)
+    for mode in ("bf16", "fp16", "fp8"):
+        out[mode]["speedup_vs_fp32"] = out["fp32"]["p50_ms"] / out[mode]["p50_ms"]
+        out[mode]["p99_speedup_vs_fp32"] = out["fp32"]["p99_ms"] / out[mode]["p99_ms"]
+    return out
+
+
+def hover_gate_leg(torch, B, stream, flush, dev, steps, drone_id):
+    """The small single-gate workload (K=256, H=20, analytic frame SDF)."""
+    import workloads as W
+    wl = W.hover_gate()
+    K, H = wl["params"]["K"], wl["params"]["H"]
+    ctx = make_ctx(B, wl, "analytic", stream, drone_id)
+    ms = device_loop(torch, B, ctx, wl, steps, 3, flush, dev)
+    B.mppi_destroy(ctx)
+    return {"workload": wl["name"], "value": K * H / (ms.mean() * 1e-3), "p50_ms": float(np.percentile(ms, 50)),
+            "p99_ms": float(np.percentile(ms, 99)), "steps": steps}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -444,6 +486,9 @@ def run_ours(args):
     kt32 = kernel_times(torch, B, ctx32, 5, flush, wl, dev)
     B.mppi_destroy(ctx32)
 
+    four = (four_gate_leg(torch, B, stream, flush, dev, args.four_gate_steps, rank)
+            if args.four_gate_steps > 0 else None)
+    hover = hover_gate_leg(torch, B, stream, flush, dev, args.steps, rank)
     serving = serving_leg(torch, B, dev, args.serving_seconds) if args.serving_seconds > 0 else None
     distill = distill_leg(torch, B, dev, args.distill_steps) if args.distill_steps > 0 else None
 
@@ -491,6 +536,8 @@ def run_ours(args):
         "e2e": {"value": K * H / (e2e_ms.mean() * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "p50_ms": float(np.percentile(e2e_ms, 50)),
                 "p99_ms": float(np.percentile(e2e_ms, 99))},
+        "four_gates": four,
+        "hover_gate_analytic": hover,
         "serving": serving,
         "distill": distill,
         "gpu_launches": per_launch * args.steps,

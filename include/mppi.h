@@ -192,10 +192,10 @@ uint64_t mppi_get_step_counter(const mppi_ctx* ctx);
  * Copy one of the last step's intermediate buffers to host memory (tests and
  * diagnostics).  n is the number of floats the caller's buffer holds; it must
  * be at least the buffer's size.  Synchronous.
- *   MPPI_BUF_NOISE      H x K x 4  delta u, layout [h][k][4]
- *   MPPI_BUF_POSITIONS  H x K x 4  rollout positions p_1..p_H, [h][k][x,y,z,0]
+ *   MPPI_BUF_NOISE      K x H x 4  delta u, layout [k][h][4] (h fastest)
+ *   MPPI_BUF_POSITIONS  K x H x 4  rollout positions p_1..p_H, [k][h][x,y,z,0]
  *   MPPI_BUF_COST_PARTS 3 x K      [J_col; J_prog; J_ctl]
- *   MPPI_BUF_SDF        H x K      s(p_h) = min over gates of the SDF at every rollout state (MLP modes)
+ *   MPPI_BUF_SDF        K x H      s(p_h) = min over gates of the SDF at every rollout state, [k][h] (MLP modes)
  *   MPPI_BUF_WEIGHTS    K
  *   MPPI_BUF_COSTS      K
  */
@@ -208,9 +208,9 @@ uint64_t mppi_get_step_counter(const mppi_ctx* ctx);
 int mppi_read_buffer(mppi_ctx* ctx, int which, float* host_out, size_t n);
 
 /*
- * Raw Philox4x32-10 words of the noise kernel for the current step counter
- * (H x K x 4 uint32, [h][k][word]), produced by the same device function the
- * noise kernel uses.  For bit-exact tests.  Synchronous.
+ * Raw Philox4x32-10 words of the step's noise for the current step counter
+ * (K x H x 4 uint32, [k][h][word]), produced by the same device function the
+ * rollout kernel draws its noise with.  For bit-exact tests.  Synchronous.
  */
 int mppi_read_noise_words(mppi_ctx* ctx, uint32_t* host_out, size_t n);
 
@@ -247,7 +247,7 @@ int mppi_selftest_tc_gemm(const uint16_t* d_A, const uint16_t* d_B, float* d_D, 
  * needs no context and calls no cudaMalloc, cudaFree or other allocating
  * routine.
  *   d_costs         K floats, the rollout costs J_m (device)
- *   d_noise         H x K x 4 floats, delta u in the [h][k][4] layout of MPPI_BUF_NOISE (device)
+ *   d_noise         H x K x 4 floats, delta u in the layout [h][k][4] (the transpose of MPPI_BUF_NOISE) (device)
  *   d_nominal       H x 4 floats, the nominal sequence U* (device)
  *   K, H            1 <= K <= MPPI_NOALLOC_MAX_K, 1 <= H <= MPPI_MAX_H
  *   lambda          temperature (> 0); thrust_min <= thrust_max, rate_max >= 0:

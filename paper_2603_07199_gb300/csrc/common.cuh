@@ -10,7 +10,8 @@ namespace mppi {
 constexpr int kHidden = 128;
 constexpr int kLatent = 64;
 constexpr int kMaxGates = 8;
-constexpr int kTileRows = 128;       // SDF rows (rollouts) per tile
+constexpr int kTileRows = 128;       // SDF rows (rollout states) per tile
+constexpr int kMaxRollouts = 1 << 20;
 
 // device error word values
 constexpr int kDevErrTimeout = 1;
@@ -35,16 +36,23 @@ struct StepBuffers {
     uint32_t* step;        // [2] step counter (lo, hi)
     float* poses;          // [maxG][8] (t, q, pad)
     float* b1p;            // [maxG][128] per-gate first-layer bias W1[:,3:] z_g + b1
-    float4* noise;         // [H][K] delta u
-    float4* pos;           // [H][K] rollout positions (x, y, z, 0)
+    float4* noise;         // [K][H] delta u (h fastest)
+    float4* pos;           // [K][H] rollout positions p_1..p_H (x, y, z, 0)
     float* parts;          // [3][K] J_col, J_prog, J_ctl
-    float* sdf;            // [H][K] min-over-gates SDF at every rollout state (MLP modes)
+    float* sdf;            // [K][H] min-over-gates SDF at every rollout state (MLP modes)
     float* J;              // [K]
     float* w;              // [K]
     float4* unew;          // [H] updated sequence U*_new
-    float* red;            // [2 * cost blocks] per-block (min J, sum exp) partials
+    float4* upart;         // [update blocks][H] per-block sums of e_k U^k_h
+    float2* bstat;         // [update blocks] per-block (min J, sum e_k)
+    float* bfac;           // [update blocks] block factor within its group exp(-(rho_b - rho_g) / lambda)
+    float4* gpart;         // [update groups][H] per-group sums
+    float2* gstat;         // [update groups] per-group (min J, sum)
+    float4* out_U;         // optional caller device buffers written by the step (H x 4, K, K)
+    float* out_w;
+    float* out_J;
     float* stats;          // [4] rho, eta of the last step
-    unsigned* tickets;     // [4] last-block counters
+    unsigned* tickets;     // [32] last-block counters: [1] all groups, [2 + g] blocks of group g
     int* err;              // [1] device error word
 };
 
@@ -102,6 +110,18 @@ struct Quat { float w, x, y, z; };
 struct Vec3 { float x, y, z; };
 
 __device__ __forceinline__ Vec3 v3(float x, float y, float z) { return Vec3{x, y, z}; }
+
+// Hamilton product a (x) b.
+__device__ __forceinline__ Quat qmul(const Quat& a, const Quat& b) {
+    return Quat{a.w * b.w - a.x * b.x - a.y * b.y - a.z * b.z,
+                a.w * b.x + a.x * b.w + a.y * b.z - a.z * b.y,
+                a.w * b.y - a.x * b.z + a.y * b.w + a.z * b.x,
+                a.w * b.z + a.x * b.y - a.y * b.x + a.z * b.w};
+}
+__device__ __forceinline__ Quat qnormalize(const Quat& q) {
+    const float inv = rsqrtf(q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z);
+    return Quat{q.w * inv, q.x * inv, q.y * inv, q.z * inv};
+}
 
 // Rotate v by the conjugate of unit q (world -> body/gate frame): R(q)^T v.
 __device__ __forceinline__ Vec3 rotate_inv(const Quat& q, const Vec3& v) {

@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_fp32_kernel(StepParams P,
     float* sPose = sMin + kTileRows;                // [G][8]
 
     const int tid = threadIdx.x;
-    const int K = P.K, G = P.G;
+    const int G = P.G;
     for (int i = tid; i < 3 * kHidden; i += kThreads) {
         const int j = i / kHidden, n = i - j * kHidden;
         sW1[i] = W.W1[n * (3 + kLatent) + j];
@@ -49,16 +49,15 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_fp32_kernel(StepParams P,
 
     const float beta = P.beta, inv_beta = 1.0f / P.beta;
     const int tn = tid & 15, tr = tid >> 4;
-    const int n_kb = (K + kTileRows - 1) / kTileRows;
-    const int n_items = P.H * n_kb;
+    // tile = 128 consecutive rollout states of the [K][H] position array
+    const int n_rows = P.K * P.H;
+    const int n_items = (n_rows + kTileRows - 1) / kTileRows;
 
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int h = item / n_kb, kb = item - h * n_kb;
         if (tid < kTileRows) sMin[tid] = __int_as_float(0x7f800000);
         for (int g = 0; g < G; ++g) {
             if (tid < kTileRows) {
-                const int k = min(kb * kTileRows + tid, K - 1);
-                const float4 p = B.pos[h * K + k];
+                const float4 p = B.pos[min(item * kTileRows + tid, n_rows - 1)];
                 const Vec3 pg = to_gate(sPose + 8 * g, v3(p.x, p.y, p.z));
                 sPg[tid] = pg.x;
                 sPg[kTileRows + tid] = pg.y;
@@ -146,8 +145,8 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_fp32_kernel(StepParams P,
         }
         __syncthreads();
         if (tid < kTileRows) {
-            const int k = kb * kTileRows + tid;
-            if (k < K) B.sdf[h * K + k] = sMin[tid];
+            const int r = item * kTileRows + tid;
+            if (r < n_rows) B.sdf[r] = sMin[tid];
         }
         __syncthreads();
     }
@@ -166,7 +165,7 @@ cudaError_t configure_sdf_mlp_fp32() {
 
 cudaError_t launch_sdf_mlp_fp32(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
                                 cudaStream_t s) {
-    const int n_items = P.H * ((P.K + kTileRows - 1) / kTileRows);
+    const int n_items = (P.K * P.H + kTileRows - 1) / kTileRows;
     const int grid = n_items < num_sms ? n_items : num_sms;
     return launch_dependent(P.pdl != 0, sdf_mlp_fp32_kernel, dim3(grid), dim3(kThreads), kSmemBytes, s, P, B, W);
 }

@@ -1,30 +1,30 @@
 // (c) Gate-SDF MLP at every rollout state on the Blackwell tensor cores.
 //
-// Work item = one tile of 128 rollouts at one horizon step; for every gate the
-// tile runs the chain
+// Work item = one tile of 128 consecutive rollout states of the [K][H]
+// position array; for every gate the tile runs the chain
 //   layer 1: one tcgen05.mma 128x128x16 (BF16 hi/lo split of the gate-frame
 //        point and of the first-layer weights, FP32 accumulate)
-//   3 x [tcgen05.mma 128x128x128 BF16/FP16 -> FP32 in TMEM]
-//   each followed by TMEM load -> bias, softplus -> 16-bit A tile (layers 1-3)
+//   3 x [tcgen05.mma 128x128x128 BF16/FP16 (+ one 128x128x16 MMA that adds the
+//        layer's bias: ones against its hi/lo split) or E4M3 -> FP32 in TMEM]
+//   each followed by TMEM load -> (bias,) softplus -> 16-bit A tile (layers 1-3)
 //        or the FP32 output dot (layer 4)
 // and keeps the running minimum over gates in a register; the item ends by
 // storing that minimum s(p) for the 128 states of the tile.
 //
-// CTA = 3 tile groups of 8 warps + 1 MMA warp.  A tile group owns one A tile
-// (smem) and one 128-column FP32 accumulator (TMEM); its warps w and w + 4
-// share TMEM lane quadrant w % 4 (rows 32 (w % 4) .. + 31) and split the 128
-// columns into halves.  Lane 0 of the MMA warp serves whichever group has its
-// A tile ready; each layer's GEMM is issued as two N = 64 halves with their
-// own completion barriers, so the first half's epilogue overlaps the second
-// half's MMAs.  W2..W4 (BF16, 96 KB) stay in shared memory for the life of the
-// persistent CTA.  Every wait is bounded.
+// CTA = 3 tile groups of 8 warps.  A tile group owns one A tile (smem) and one
+// 128-column FP32 accumulator (TMEM); its warps w and w + 4 share TMEM lane
+// quadrant w % 4 (rows 32 (w % 4) .. + 31) and split the 128 columns into
+// halves.  Once all 256 threads of a group have written its A tile (named
+// barrier), the group's leader thread issues that layer's MMAs and commits them
+// to the group's mbarrier, on which the group's warps wait (bounded).  W2..W4
+// (96 KB in BF16/FP16) stay in shared memory for the life of the persistent CTA.
 //
 // Activations are carried in log2 units: with c = beta log2(e) and y = c x,
 //   sp_beta(x) = (ln 2 / beta) h(y),   h(y) = log2(1 + 2^y) = max(y, 0) + log2(1 + 2^-|y|),
 // and c (ln 2 / beta) = 1, so the hidden weights are used unchanged while the
 // first layer and the hidden biases are scaled by c and the output weights by
 // ln 2 / beta.  h is evaluated with one hardware exp2 and a quartic in
-// e = 2^-|y| (see kL1..kL4), in packed f32x2 arithmetic.
+// e = 2^-|y| (see kL1..kL4), in packed f32x2 (BF16) or f16x2 (FP16, E4M3) arithmetic.
 #include "kernels.h"
 #include "tc.cuh"
 
@@ -35,8 +35,7 @@ namespace {
 constexpr int kGroups = 3;                          // tile groups (tiles in flight per CTA)
 constexpr int kGroupWarps = 8;
 constexpr int kGroupThreads = kGroupWarps * 32;
-constexpr int kThreads = kGroups * kGroupThreads + 32;
-constexpr int kMmaWarp = kGroups * kGroupWarps;
+constexpr int kThreads = kGroups * kGroupThreads;
 constexpr int kHalf = kHidden / 2;
 constexpr uint32_t kTileBytes = kHidden * kHidden * 2;     // one 128 x 128 BF16 operand
 constexpr uint32_t kTmemCols = 512;
@@ -48,13 +47,14 @@ struct __align__(16) TcShared {
     uint8_t w[3][kTileBytes];                 // W2, W3, W4 (B operands, N = out, K = in)
     uint8_t a[kGroups][kTileBytes];           // activation tiles (A operands, M = rows, K = features)
     uint8_t w1[kHidden * 16 * 2];             // layer-1 B operand: c W1[:, 0:3] split hi/lo (BF16, K = 16)
+    uint8_t ones[kHidden * 16 * 2];           // K = 16 A operand with columns 0, 1 = 1 (16-bit hidden paths)
+    uint8_t bslab[3][kHidden * 16 * 2];       // K = 16 B operands: columns 0, 1 = hi, lo of c b2, c b3, c b4
     float b1[kMaxGates][kHidden];             // c (per-gate first-layer bias)
-    float bias[3][kHidden];                   // c b2, c b3, c b4
+    float bias[3][kHidden];                   // c b2, c b3, c b4 (E4M3 path: added in the epilogue)
     float w5[kHidden];                        // (ln 2 / beta) w5
     float part[kGroups][kTileRows];           // output-layer partial sums of the upper column half
     float pose[kMaxGates][8];
-    uint64_t act_full[kGroups];               // epilogue -> MMA: A tile written
-    uint64_t acc_full[kGroups][2];            // MMA -> epilogue: accumulator half ready
+    uint64_t acc_full[kGroups];               // MMA -> epilogue: accumulator ready
     uint32_t tmem_base;
     int abort_flag;
 };
@@ -89,20 +89,6 @@ constexpr float kL1 = 1.4426950408889634f;
 constexpr float kL2 = -0.69991479f;
 constexpr float kL3 = 0.35777588f;
 constexpr float kL4 = -0.10076641f;
-
-// Two activations at once: h(y) = max(y, 0) + log2(1 + 2^-|y|) for y = acc + bias.
-__device__ __forceinline__ uint64_t softplus2_log2(float a0, float a1, uint64_t bias2) {
-    const float2 y = upk(add2(pk(a0, a1), bias2));
-    const uint64_t e = pk(tc::ex2_approx(-fabsf(y.x)), tc::ex2_approx(-fabsf(y.y)));
-    uint64_t p = fma2(e, pk(kL4, kL4), pk(kL3, kL3));
-    p = fma2(e, p, pk(kL2, kL2));
-    p = fma2(e, p, pk(kL1, kL1));
-    return fma2(e, p, pk(fmaxf(y.x, 0.f), fmaxf(y.y, 0.f)));
-}
-__device__ __forceinline__ uint32_t softplus2_log2_bf16(float a0, float a1, uint64_t bias2) {
-    const float2 h = upk(softplus2_log2(a0, a1, bias2));
-    return tc::pack_bf16x2(h.x, h.y);
-}
 
 // ---------------------------------------------------------------- packed f16x2 epilogue (FP16 operand path)
 // The same h(y) with every step after the FP32 bias add in f16x2: one hardware
@@ -169,23 +155,34 @@ __device__ __forceinline__ uint32_t f16x2x2_to_e4m3x4(uint32_t h01, uint32_t h23
     return r;
 }
 
-// One 16-bit activation pair of the requested operand type.
+// One 16-bit activation pair of the requested operand type from y = (y0, y1) (log2 units).
 template <int kFmt>
-__device__ __forceinline__ uint32_t act_pair(float a0, float a1, uint64_t bias2) {
+__device__ __forceinline__ uint32_t act_pair(uint64_t y2) {
     if constexpr (kFmt == kFmtBF16) {
-        return softplus2_log2_bf16(a0, a1, bias2);
+        const float2 y = upk(y2);
+        const uint64_t e = pk(tc::ex2_approx(-fabsf(y.x)), tc::ex2_approx(-fabsf(y.y)));
+        uint64_t p = fma2(e, pk(kL4, kL4), pk(kL3, kL3));
+        p = fma2(e, p, pk(kL2, kL2));
+        p = fma2(e, p, pk(kL1, kL1));
+        const float2 h = upk(fma2(e, p, pk(fmaxf(y.x, 0.f), fmaxf(y.y, 0.f))));
+        return tc::pack_bf16x2(h.x, h.y);
     } else {
-        const float2 y = upk(add2(pk(a0, a1), bias2));
+        const float2 y = upk(y2);
         return softplus2_log2_f16(y.x, y.y);
     }
 }
-// Output-layer contribution w5 . h for one activation pair (FP32 accumulate).
+// Output-layer contribution w5 . h(y) for one pair (FP32 accumulate).
 template <int kFmt>
-__device__ __forceinline__ uint64_t out_pair(float a0, float a1, uint64_t bias2, uint64_t w2, uint64_t acc) {
+__device__ __forceinline__ uint64_t out_pair(uint64_t y2, uint64_t w2, uint64_t acc) {
     if constexpr (kFmt == kFmtBF16) {
-        return fma2(w2, softplus2_log2(a0, a1, bias2), acc);
+        const float2 y = upk(y2);
+        const uint64_t e = pk(tc::ex2_approx(-fabsf(y.x)), tc::ex2_approx(-fabsf(y.y)));
+        uint64_t p = fma2(e, pk(kL4, kL4), pk(kL3, kL3));
+        p = fma2(e, p, pk(kL2, kL2));
+        p = fma2(e, p, pk(kL1, kL1));
+        return fma2(w2, fma2(e, p, pk(fmaxf(y.x, 0.f), fmaxf(y.y, 0.f))), acc);
     } else {
-        const float2 y = upk(add2(pk(a0, a1), bias2));
+        const float2 y = upk(y2);
         const float2 h = f16x2_to_f32x2(softplus2_log2_f16(y.x, y.y));
         return fma2(w2, pk(h.x, h.y), acc);
     }
@@ -206,6 +203,24 @@ __device__ __forceinline__ int items_of_slot(int slot, int nslots, int n_items) 
     return slot < n_items ? (n_items - slot + nslots - 1) / nslots : 0;
 }
 
+// 16-bit pattern of x in the operand type of the hidden GEMMs (round to nearest even).
+template <int kFmt>
+__device__ __forceinline__ uint16_t to_operand16(float x) {
+    if constexpr (kFmt == kFmtFP16) {
+        return static_cast<uint16_t>(f32x2_to_f16x2(x, 0.f) & 0xFFFFu);
+    } else {
+        return static_cast<uint16_t>(tc::pack_bf16x2(x, 0.f) & 0xFFFFu);
+    }
+}
+template <int kFmt>
+__device__ __forceinline__ float from_operand16(uint16_t v) {
+    if constexpr (kFmt == kFmtFP16) {
+        return f16x2_to_f32x2(v).x;
+    } else {
+        return __uint_as_float(static_cast<uint32_t>(v) << 16);
+    }
+}
+
 template <int kFmt>
 __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, StepBuffers B, MlpWeights W) {
     constexpr bool kF16 = (kFmt == kFmtFP16);
@@ -217,19 +232,15 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
     TcShared& S = *reinterpret_cast<TcShared*>(smem_raw);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int K = P.K, G = P.G;
+    const int G = P.G;
 
     // ---- set-up: TMEM, barriers, resident weights
-    if (warp == kMmaWarp) {
+    if (warp == 0) {
         tc::tmem_alloc(tc::smem_u32(&S.tmem_base), kTmemCols);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        for (int i = 0; i < kGroups; ++i) {
-            tc::mbar_init(tc::smem_u32(&S.act_full[i]), 1);
-            tc::mbar_init(tc::smem_u32(&S.acc_full[i][0]), 1);
-            tc::mbar_init(tc::smem_u32(&S.acc_full[i][1]), 1);
-        }
+        for (int i = 0; i < kGroups; ++i) tc::mbar_init(tc::smem_u32(&S.acc_full[i]), 1);
         S.abort_flag = 0;
         tc::mbar_fence_init();
     }
@@ -246,7 +257,24 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
         reinterpret_cast<uint4*>(S.w1)[i] = __ldg(reinterpret_cast<const uint4*>(W.W1tc) + i);
     for (int i = tid; i < 3 * kHidden; i += kThreads) {
         const int j = i / kHidden, n = i - j * kHidden;
-        S.bias[j][n] = cl2 * W.b[j][n];
+        const float b = cl2 * W.b[j][n];
+        S.bias[j][n] = b;
+        if constexpr (!kF8) {
+            // bias row n of layer j as the K = 16 operand row [hi, lo, 0, ..., 0]
+            const uint16_t hi = to_operand16<kFmt>(b);
+            const uint16_t lo = to_operand16<kFmt>(b - from_operand16<kFmt>(hi));
+            const uint32_t off = static_cast<uint32_t>((n >> 3) * 256 + (n & 7) * 16);
+            *reinterpret_cast<uint4*>(S.bslab[j] + off) = make_uint4(static_cast<uint32_t>(hi) | (static_cast<uint32_t>(lo) << 16), 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(S.bslab[j] + off + 128) = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+    if constexpr (!kF8) {
+        const uint32_t one = kF16 ? 0x3C003C00u : 0x3F803F80u;   // (1, 1) in the operand type
+        for (int r = tid; r < kTileRows; r += kThreads) {
+            const uint32_t off = static_cast<uint32_t>((r >> 3) * 256 + (r & 7) * 16);
+            *reinterpret_cast<uint4*>(S.ones + off) = make_uint4(one, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(S.ones + off + 128) = make_uint4(0u, 0u, 0u, 0u);
+        }
     }
     for (int i = tid; i < G * kHidden; i += kThreads) S.b1[i / kHidden][i % kHidden] = cl2 * B.b1p[i];
     for (int i = tid; i < kHidden; i += kThreads) S.w5[i] = (0.69314718055994531f / P.beta) * W.w5[i];
@@ -261,137 +289,98 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
     pdl_trigger();
     pdl_wait();
 
-    const int n_kb = (K + kTileRows - 1) / kTileRows;
-    const int n_items = P.H * n_kb;
+    // tile i (128 consecutive rows of the [K][H] state array) goes to group slot i mod (3 gridDim)
+    const int n_rows = P.K * P.H;
+    const int n_tiles = (n_rows + kTileRows - 1) / kTileRows;
     const int nslots = gridDim.x * kGroups;
+    const int slot = blockIdx.x * kGroups + (warp / kGroupWarps);
     volatile int* abort_flag = &S.abort_flag;
 
-    if (warp == kMmaWarp) {
-        // ---------------------------------------------------------- MMA issuer
-        if (lane == 0) {
-            int nreq[kGroups], issued[kGroups];
-            uint32_t phase[kGroups];
+    const int grp = warp / kGroupWarps;
+    const int quad = warp & 3;                                    // TMEM lane quadrant (= warp % 4)
+    const int half = (warp % kGroupWarps) >> 2;                   // column half
+    const int row = quad * 32 + lane;                             // TMEM lane == tile row
+    const int col0 = half * kHalf;
+    const uint32_t a_base = tc::smem_u32(S.a[grp]);
+    const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(grp * kHidden);
+    const uint32_t t_row = tmem_base + (static_cast<uint32_t>(quad * 32) << 16) +
+                           static_cast<uint32_t>(grp * kHidden + col0);
+    const uint32_t acc_bar = tc::smem_u32(&S.acc_full[grp]);
+    const uint32_t bar_id = 1 + grp;
+    const bool leader = (warp % kGroupWarps) == 0 && lane == 0;
+    uint32_t acc_phase = 0;
+    int outstanding = 0;                                          // leader: commits not yet waited for
+    bool ok = true;
+
+    // The group's leader issues GEMM l (0: layer 1, 1..3: layers 2..4) once the whole
+    // group has written its A tile (named barrier + proxy fences on every writer).
+    auto issue = [&](int l) {
+        tc::fence_after_sync();
+        const uint64_t ad = tc::smem_desc(a_base, 128, 2048);
+        if (l == 0) {
+            // layer 1: K = 16 (hi/lo split point x weights), always BF16
+            tc::mma_bf16(d_tmem, ad, tc::smem_desc(tc::smem_u32(S.w1), 128, 256), kIdescFull, 0u);
+        } else if constexpr (kF8) {
+            // E4M3 x E4M3 -> FP32, K = 32 per instruction (256 B along K), SBO 1024 B
+            const uint64_t a8 = tc::smem_desc(a_base, 128, 1024);
+            const uint64_t bd = tc::smem_desc(tc::smem_u32(S.w[l - 1]), 128, 1024);
 #pragma unroll
-            for (int i = 0; i < kGroups; ++i) {
-                nreq[i] = items_of_slot(blockIdx.x * kGroups + i, nslots, n_items) * G * 4;
-                issued[i] = 0;
-                phase[i] = 0;
-            }
-            uint64_t t0 = tc::global_timer();
-            int idle = 0;
-            while (true) {
-                bool pending = false, progressed = false;
+            for (int s = 0; s < kHidden / 32; ++s)
+                tc::mma_e4m3(d_tmem, a8 + static_cast<uint64_t>(s * 16), bd + static_cast<uint64_t>(s * 16), kIdescE4M3,
+                             s > 0 ? 1u : 0u);
+        } else {
+            const uint32_t idesc = kF16 ? kIdescFullF16 : kIdescFull;
+            const uint64_t bd = tc::smem_desc(tc::smem_u32(S.w[l - 1]), 128, 2048);
 #pragma unroll
-                for (int i = 0; i < kGroups; ++i) {
-                    if (issued[i] >= nreq[i]) continue;
-                    pending = true;
-                    // non-blocking: a suspended try_wait on one group would delay the others
-                    if (!tc::mbar_test_wait(tc::smem_u32(&S.act_full[i]), phase[i])) continue;
-                    phase[i] ^= 1u;
-                    tc::fence_after_sync();
-                    const int l = issued[i] & 3;
-                    const uint64_t ad = tc::smem_desc(tc::smem_u32(S.a[i]), 128, 2048);
-                    const uint32_t d = tmem_base + static_cast<uint32_t>(i * kHidden);
-                    if (l == 0) {
-                        // layer 1: K = 16 (hi/lo split point x weights), always BF16
-                        tc::mma_bf16(d, ad, tc::smem_desc(tc::smem_u32(S.w1), 128, 256), kIdescFull, 0u);
-                    } else if constexpr (kF8) {
-                        // E4M3 x E4M3 -> FP32, K = 32 per instruction (256 B along K), SBO 1024 B
-                        const uint64_t a8 = tc::smem_desc(tc::smem_u32(S.a[i]), 128, 1024);
-                        const uint64_t bd = tc::smem_desc(tc::smem_u32(S.w[l - 1]), 128, 1024);
-#pragma unroll
-                        for (int s = 0; s < kHidden / 32; ++s)
-                            tc::mma_e4m3(d, a8 + static_cast<uint64_t>(s * 16), bd + static_cast<uint64_t>(s * 16),
-                                         kIdescE4M3, s > 0 ? 1u : 0u);
-                    } else {
-                        // one N = 128 GEMM: the A tile is read once (an N = 64 split reads it twice and
-                        // makes the MMA shared-memory bound)
-                        const uint64_t bd = tc::smem_desc(tc::smem_u32(S.w[l - 1]), 128, 2048);
-#pragma unroll
-                        for (int s = 0; s < kHidden / 16; ++s)   // K = 16 per instruction: 256 B along K
-                            tc::mma_bf16(d, ad + static_cast<uint64_t>(s * 16), bd + static_cast<uint64_t>(s * 16),
-                                         kF16 ? kIdescFullF16 : kIdescFull, s > 0 ? 1u : 0u);
-                    }
-                    tc::mma_commit(tc::smem_u32(&S.acc_full[i][0]));
-                    ++issued[i];
-                    progressed = true;
-                }
-                if (!pending) break;
-                if (progressed) {
-                    t0 = tc::global_timer();
-                    idle = 0;
-                } else if (++idle >= 64) {
-                    idle = 0;
-                    if (*abort_flag) break;
-                    if (tc::global_timer() - t0 > tc::kWaitLimitNs) {
-                        *abort_flag = 1;
-                        atomicExch(B.err, kDevErrTimeout);
-                        break;
-                    }
-                }
-            }
-            // on abort: let the MMAs already issued finish before TMEM is released
-#pragma unroll
-            for (int i = 0; i < kGroups; ++i) {
-                if (issued[i] > 0) {
-                    int dummy = 0;
-                    tc::mbar_wait_bounded(tc::smem_u32(&S.acc_full[i][0]), static_cast<uint32_t>((issued[i] - 1) & 1),
-                                          &dummy, B.err, kDevErrTimeout);
-                }
-            }
+            for (int s = 0; s < kHidden / 16; ++s)   // K = 16 per instruction: 256 B along K
+                tc::mma_bf16(d_tmem, ad + static_cast<uint64_t>(s * 16), bd + static_cast<uint64_t>(s * 16), idesc,
+                             s > 0 ? 1u : 0u);
+            // + bias: ones (M x 16) against [hi, lo, 0..] (N x 16)
+            tc::mma_bf16(d_tmem, tc::smem_desc(tc::smem_u32(S.ones), 128, 256),
+                         tc::smem_desc(tc::smem_u32(S.bslab[l - 1]), 128, 256), idesc, 1u);
         }
-        __syncwarp();
-    } else {
-        // ---------------------------------------------------------- epilogue tile groups
-        const int grp = warp / kGroupWarps;
-        const int quad = warp & 3;                                    // TMEM lane quadrant (= warp % 4)
-        const int half = (warp % kGroupWarps) >> 2;                   // column half
-        const int row = quad * 32 + lane;                             // TMEM lane == tile row
-        const int col0 = half * kHalf;
-        const uint32_t a_base = tc::smem_u32(S.a[grp]);
-        const uint32_t t_row = tmem_base + (static_cast<uint32_t>(quad * 32) << 16) +
-                               static_cast<uint32_t>(grp * kHidden + col0);
-        const uint32_t act_bar = tc::smem_u32(&S.act_full[grp]);
-        const uint32_t acc_bar = tc::smem_u32(&S.acc_full[grp][0]);
-        const uint32_t bar_id = 1 + grp;
-        const bool leader = (warp % kGroupWarps) == 0 && lane == 0;
-        uint32_t acc_phase = 0;
-        bool ok = true;
+        tc::mma_commit(acc_bar);
+        ++outstanding;
+    };
 
-        for (int item = blockIdx.x * kGroups + grp; item < n_items && ok; item += nslots) {
-            const int h = item / n_kb, kb = item - h * n_kb;
-            const int k = kb * kTileRows + row;
-            const float4 p = B.pos[h * K + min(k, K - 1)];
-            float smin = __int_as_float(0x7f800000);
-            for (int g = 0; g < G && ok; ++g) {
-                // layer-1 A operand (K = 16): the gate-frame point split p = hi + lo in BF16,
-                // laid out against the weight split [W_hi, W_hi, W_lo] so the MMA sums
-                // hi.W_hi + lo.W_hi + hi.W_lo (relative error ~2^-16); the latent's part
-                // of the first layer is the per-gate bias of the epilogue
-                if (half == 0) {
-                    const Vec3 pg = to_gate(S.pose[g], v3(p.x, p.y, p.z));
-                    const float hx = bf16_round(pg.x), hy = bf16_round(pg.y), hz = bf16_round(pg.z);
-                    const float lx = pg.x - hx, ly = pg.y - hy, lz = pg.z - hz;
-                    tc::st_shared_v4(a_base + tc::operand_offset_bytes(row, 0), tc::pack_bf16x2(hx, hy),
-                                     tc::pack_bf16x2(hz, lx), tc::pack_bf16x2(ly, lz), tc::pack_bf16x2(hx, hy));
-                    tc::st_shared_v4(a_base + tc::operand_offset_bytes(row, 8), tc::pack_bf16x2(hz, 0.f), 0u, 0u, 0u);
+    for (int tile = slot; tile < n_tiles && ok; tile += nslots) {
+        const int row0 = tile * kTileRows;
+        const int nvalid = min(kTileRows, n_rows - row0);          // the last tile may be ragged
+        const bool active = quad * 32 < nvalid;                   // this warp's quadrant has rows
+        const int r = row0 + row;
+        const float4 p = B.pos[min(r, n_rows - 1)];
+        float smin = __int_as_float(0x7f800000);
+        for (int g = 0; g < G && ok; ++g) {
+            // layer-1 A operand (K = 16): the gate-frame point split p = hi + lo in BF16,
+            // laid out against the weight split [W_hi, W_hi, W_lo] so the MMA sums
+            // hi.W_hi + lo.W_hi + hi.W_lo (relative error ~2^-16); the latent's part
+            // of the first layer is the per-gate bias of the epilogue
+            if (half == 0 && active) {
+                const Vec3 pg = to_gate(S.pose[g], v3(p.x, p.y, p.z));
+                const float hx = bf16_round(pg.x), hy = bf16_round(pg.y), hz = bf16_round(pg.z);
+                const float lx = pg.x - hx, ly = pg.y - hy, lz = pg.z - hz;
+                tc::st_shared_v4(a_base + tc::operand_offset_bytes(row, 0), tc::pack_bf16x2(hx, hy),
+                                 tc::pack_bf16x2(hz, lx), tc::pack_bf16x2(ly, lz), tc::pack_bf16x2(hx, hy));
+                tc::st_shared_v4(a_base + tc::operand_offset_bytes(row, 8), tc::pack_bf16x2(hz, 0.f), 0u, 0u, 0u);
+            }
+            tc::fence_proxy_async_smem();
+            tc::fence_before_sync();
+            tc::named_barrier(bar_id, kGroupThreads);
+            if (leader) issue(0);
+
+            for (int l = 0; l < 4; ++l) {
+                // every thread of the group agrees on the outcome before going on, so a
+                // timeout seen by one thread cannot strand the others at a named barrier
+                const bool got = tc::mbar_wait_bounded(acc_bar, acc_phase, abort_flag, B.err, kDevErrTimeout);
+                if (!tc::named_barrier_and(bar_id, kGroupThreads, got)) {
+                    ok = false;
+                    break;
                 }
-                tc::fence_proxy_async_smem();
-                tc::named_barrier(bar_id, kGroupThreads);
-                if (leader) tc::mbar_arrive(act_bar);
-
-                float s = 0.f;
-                for (int l = 0; l < 4; ++l) {
-                    // every thread of the group agrees on the outcome before going on, so a
-                    // timeout seen by one thread cannot strand the others at a named barrier
-                    const bool got = tc::mbar_wait_bounded(acc_bar, acc_phase, abort_flag, B.err, kDevErrTimeout);
-                    if (!tc::named_barrier_and(bar_id, kGroupThreads, got)) {
-                        ok = false;
-                        break;
-                    }
-                    acc_phase ^= 1u;
-                    tc::fence_after_sync();
-                    uint64_t s2 = pk(0.f, 0.f);
+                acc_phase ^= 1u;
+                if (leader) --outstanding;
+                tc::fence_after_sync();
+                uint64_t s2 = pk(0.f, 0.f);
+                if (active) {
 #pragma unroll 1
                     for (int ch = 0; ch < kHalf; ch += 32) {
                         uint32_t v[32];
@@ -420,58 +409,78 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                                 }
                                 tc::st_shared_v4(a_base + operand8_offset_bytes(row, cc + j), q[0], q[1], q[2], q[3]);
                             }
-                        } else if (l < 3) {
-                            const float* bias = (l == 0) ? S.b1[g] : S.bias[l - 1];
+                        } else if (l == 0) {
+                            // layer 1: + the gate's first-layer bias
+                            const float* bias = S.b1[g];
 #pragma unroll
                             for (int j = 0; j < 32; j += 8) {
                                 const float4 b0 = *reinterpret_cast<const float4*>(bias + cc + j);
                                 const float4 b1 = *reinterpret_cast<const float4*>(bias + cc + j + 4);
                                 tc::st_shared_v4(
                                     a_base + tc::operand_offset_bytes(row, cc + j),
-                                    act_pair<kFmt>(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), pk(b0.x, b0.y)),
-                                    act_pair<kFmt>(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]), pk(b0.z, b0.w)),
-                                    act_pair<kFmt>(__uint_as_float(v[j + 4]), __uint_as_float(v[j + 5]), pk(b1.x, b1.y)),
-                                    act_pair<kFmt>(__uint_as_float(v[j + 6]), __uint_as_float(v[j + 7]), pk(b1.z, b1.w)));
+                                    act_pair<kFmt>(add2(pk(__uint_as_float(v[j]), __uint_as_float(v[j + 1])), pk(b0.x, b0.y))),
+                                    act_pair<kFmt>(add2(pk(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3])), pk(b0.z, b0.w))),
+                                    act_pair<kFmt>(add2(pk(__uint_as_float(v[j + 4]), __uint_as_float(v[j + 5])), pk(b1.x, b1.y))),
+                                    act_pair<kFmt>(add2(pk(__uint_as_float(v[j + 6]), __uint_as_float(v[j + 7])), pk(b1.z, b1.w))));
                             }
-                        } else {
-                            if constexpr (kF8) {
+                        } else if (l < 3) {
+                            // hidden layers 2, 3: the bias is already in the accumulator
 #pragma unroll
-                                for (int j = 0; j < 32; ++j)
-                                    v[j] = __float_as_uint(__uint_as_float(v[j]) * W.f8_dequant[2]);
+                            for (int j = 0; j < 32; j += 8) {
+                                tc::st_shared_v4(a_base + tc::operand_offset_bytes(row, cc + j),
+                                                 act_pair<kFmt>(pk(__uint_as_float(v[j]), __uint_as_float(v[j + 1]))),
+                                                 act_pair<kFmt>(pk(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]))),
+                                                 act_pair<kFmt>(pk(__uint_as_float(v[j + 4]), __uint_as_float(v[j + 5]))),
+                                                 act_pair<kFmt>(pk(__uint_as_float(v[j + 6]), __uint_as_float(v[j + 7]))));
                             }
+                        } else if constexpr (kF8) {
 #pragma unroll
                             for (int j = 0; j < 32; j += 4) {
                                 const float4 b0 = *reinterpret_cast<const float4*>(&S.bias[2][cc + j]);
                                 const float4 w0 = *reinterpret_cast<const float4*>(&S.w5[cc + j]);
-                                s2 = out_pair<kFmt>(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), pk(b0.x, b0.y),
-                                                    pk(w0.x, w0.y), s2);
-                                s2 = out_pair<kFmt>(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]), pk(b0.z, b0.w),
-                                                    pk(w0.z, w0.w), s2);
+                                const uint64_t dq2 = pk(W.f8_dequant[2], W.f8_dequant[2]);
+                                s2 = out_pair<kFmt>(fma2(pk(__uint_as_float(v[j]), __uint_as_float(v[j + 1])), dq2,
+                                                         pk(b0.x, b0.y)), pk(w0.x, w0.y), s2);
+                                s2 = out_pair<kFmt>(fma2(pk(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3])), dq2,
+                                                         pk(b0.z, b0.w)), pk(w0.z, w0.w), s2);
+                            }
+                        } else {
+                            // output layer: the bias b4 is already in the accumulator
+#pragma unroll
+                            for (int j = 0; j < 32; j += 4) {
+                                const float4 w0 = *reinterpret_cast<const float4*>(&S.w5[cc + j]);
+                                s2 = out_pair<kFmt>(pk(__uint_as_float(v[j]), __uint_as_float(v[j + 1])), pk(w0.x, w0.y), s2);
+                                s2 = out_pair<kFmt>(pk(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3])), pk(w0.z, w0.w), s2);
                             }
                         }
                     }
-                    tc::fence_before_sync();
-                    if (l < 3) {
-                        tc::fence_proxy_async_smem();
-                        tc::named_barrier(bar_id, kGroupThreads);
-                        if (leader) tc::mbar_arrive(act_bar);
-                    } else {
-                        // the two column halves of a row meet through shared memory
-                        const float2 sp2 = upk(s2);
-                        s = sp2.x + sp2.y;
-                        if (half == 1) S.part[grp][row] = s;
-                        tc::named_barrier(bar_id, kGroupThreads);
-                        if (half == 0) smin = fminf(smin, s + S.part[grp][row] + W.b5);
-                    }
+                }
+                tc::fence_before_sync();
+                if (l < 3) {
+                    tc::fence_proxy_async_smem();
+                    tc::named_barrier(bar_id, kGroupThreads);
+                    if (leader) issue(l + 1);
+                } else {
+                    // the two column halves of a row meet through shared memory
+                    const float2 sp2 = upk(s2);
+                    const float sh = sp2.x + sp2.y;
+                    if (half == 1) S.part[grp][row] = sh;
+                    tc::named_barrier(bar_id, kGroupThreads);
+                    if (half == 0) smin = fminf(smin, sh + S.part[grp][row] + W.b5);
                 }
             }
-            if (ok && half == 0 && k < K) B.sdf[h * K + k] = smin;
         }
+        if (ok && half == 0 && row < nvalid && r < n_rows) B.sdf[r] = smin;
     }
 
+    // on abort: let the MMAs this group's leader issued finish before TMEM is released
+    if (leader && outstanding > 0) {
+        int dummy = 0;
+        tc::mbar_wait_bounded(acc_bar, acc_phase, &dummy, B.err, kDevErrTimeout);
+    }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == kMmaWarp) {
+    if (warp == 0) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem_base, kTmemCols);
     }
@@ -556,7 +565,7 @@ cudaError_t configure_sdf_mlp_bf16() {
 
 cudaError_t launch_sdf_mlp_bf16(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
                                 cudaStream_t s) {
-    const int n_items = P.H * ((P.K + kTileRows - 1) / kTileRows);
+    const int n_items = (P.K * P.H + kTileRows - 1) / kTileRows;
     const int want = (n_items + kGroups - 1) / kGroups;
     const int grid = want < num_sms ? want : num_sms;
     return launch_dependent(P.pdl != 0, sdf_mlp_tc_kernel<kFmtBF16>, dim3(grid), dim3(kThreads), kSmemBytes, s, P, B, W);
@@ -564,7 +573,7 @@ cudaError_t launch_sdf_mlp_bf16(const StepParams& P, const StepBuffers& B, const
 
 cudaError_t launch_sdf_mlp_fp16(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
                                 cudaStream_t s) {
-    const int n_items = P.H * ((P.K + kTileRows - 1) / kTileRows);
+    const int n_items = (P.K * P.H + kTileRows - 1) / kTileRows;
     const int want = (n_items + kGroups - 1) / kGroups;
     const int grid = want < num_sms ? want : num_sms;
     return launch_dependent(P.pdl != 0, sdf_mlp_tc_kernel<kFmtFP16>, dim3(grid), dim3(kThreads), kSmemBytes, s, P, B, W);
@@ -572,7 +581,7 @@ cudaError_t launch_sdf_mlp_fp16(const StepParams& P, const StepBuffers& B, const
 
 cudaError_t launch_sdf_mlp_fp8(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
                                cudaStream_t s) {
-    const int n_items = P.H * ((P.K + kTileRows - 1) / kTileRows);
+    const int n_items = (P.K * P.H + kTileRows - 1) / kTileRows;
     const int want = (n_items + kGroups - 1) / kGroups;
     const int grid = want < num_sms ? want : num_sms;
     return launch_dependent(P.pdl != 0, sdf_mlp_tc_kernel<kFmtE4M3>, dim3(grid), dim3(kThreads), kSmemBytes, s, P, B, W);

@@ -1,44 +1,92 @@
-// Step kernels around the SDF query: (a) noise, (b) rollouts, (d) cost ->
-// weights -> update, receding-horizon plant step, per-gate first-layer bias.
+// Step kernels around the SDF query: (a) + (b) noise and rollouts, (d) costs ->
+// softmax weights -> update -> receding-horizon plant step, and the per-gate
+// first-layer bias.
 #include "kernels.h"
 
 namespace mppi {
 
 namespace {
 
-// ------------------------------------------------------------------ (a) noise
-// One Philox4x32-10 block per (h, k) -> four normals -> delta u (Sec. IV-A, Eq. 5).
-// Layout [h][k] so the rollout kernel's per-h reads are coalesced across k.
-__global__ void __launch_bounds__(256) noise_kernel(StepParams P, const uint32_t* __restrict__ step,
-                                                    float4* __restrict__ noise) {
-    pdl_trigger();
-    const int n = P.K * P.H;
-    const uint32_t st = __ldg(step);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int h = i / P.K;
-        const int k = i - h * P.K;
-        noise[i] = noise_from_block(P, noise_block(P, k, h, st));
+__device__ __forceinline__ float warp_min(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+__device__ __forceinline__ Quat shfl_up(const Quat& q, int d) {
+    return Quat{__shfl_up_sync(0xffffffffu, q.w, d), __shfl_up_sync(0xffffffffu, q.x, d),
+                __shfl_up_sync(0xffffffffu, q.y, d), __shfl_up_sync(0xffffffffu, q.z, d)};
+}
+__device__ __forceinline__ Vec3 shfl_up(const Vec3& v, int d) {
+    return v3(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d),
+              __shfl_up_sync(0xffffffffu, v.z, d));
+}
+__device__ __forceinline__ Quat shfl_idx(const Quat& q, int src) {
+    return Quat{__shfl_sync(0xffffffffu, q.w, src), __shfl_sync(0xffffffffu, q.x, src),
+                __shfl_sync(0xffffffffu, q.y, src), __shfl_sync(0xffffffffu, q.z, src)};
+}
+__device__ __forceinline__ Vec3 shfl_idx(const Vec3& v, int src) {
+    return v3(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+              __shfl_sync(0xffffffffu, v.z, src));
+}
+// Inclusive prefix sum over the lanes (Hillis-Steele).
+__device__ __forceinline__ Vec3 warp_scan_add(Vec3 x, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const Vec3 t = shfl_up(x, d);
+        if (lane >= d) x = v3(t.x + x.x, t.y + x.y, t.z + x.z);
     }
+    return x;
+}
+// Inclusive ordered product x_0 (x) x_1 (x) ... (x) x_lane: at every round the
+// partial product of the earlier lanes multiplies from the left.
+__device__ __forceinline__ Quat warp_scan_qmul(Quat x, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const Quat t = shfl_up(x, d);
+        if (lane >= d) x = qmul(t, x);
+    }
+    return x;
 }
 
 __global__ void noise_words_kernel(StepParams P, const uint32_t* __restrict__ step, uint4* __restrict__ out) {
     const int n = P.K * P.H;
     const uint32_t st = __ldg(step);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int h = i / P.K;
-        const int k = i - h * P.K;
+        const int k = i / P.H;
+        const int h = i - k * P.H;
         out[i] = noise_block(P, k, h, st);
     }
 }
 
-// ------------------------------------------------------------------ (b) rollouts
-// One rollout per thread, state in registers, serial over the horizon.  Each
-// step clips U*_h + delta, accumulates the control cost, integrates RK4 and
-// stores the position as one float4 (coalesced across k).  In analytic mode
-// the frame SDF of every gate and the collision hinge are evaluated here too.
-constexpr int kPrefetch = 8;
+// ------------------------------------------------------------------ (a) + (b) noise and rollouts
+// One warp per rollout; the horizon runs across the lanes in chunks of
+// 32 x kSteps steps, lane l owning the kSteps consecutive steps
+// h = c0 + kSteps l + j.  For each of its steps a lane draws the noise
+// (Philox4x32-10 block (k, h, step, drone) -> four normals -> delta u,
+// Sec. IV-A, Eq. 5), stores it, clips U*_h + delta and adds the control cost.
+// With the body rate held over a step (dw/dt = 0) the RK4 attitude update is
+// q_{h+1} = normalise(q_h (x) M_h), M_h = (a_n, b_n w_h) with a_n, b_n the
+// polynomials in |w_h| dt of rk4_step, so q_{h+1} = q_h (x) N_h with the unit
+// N_h = M_h / |M_h|: the attitude at the start of every lane's segment is an
+// ordered prefix product of state-independent factors (a warp scan).  Each lane
+// then walks its segment: stage accelerations of every step, the velocity
+// offsets V_j = sum_{i<j} dv_i and position offsets L_j relative to the
+// segment's start, with
+//   v_{h+1} = v_h + dt/6 (a1 + 2 a2 + 2 a3 + a4),  p_{h+1} = p_h + dt v_h + dt^2/6 (a1 + a2 + a3),
+// so p after j + 1 steps of the segment = p_s + (j + 1) dt v_s + L_j.  Two more
+// scans give every segment's v_s and p_s.  The serial chain of H dependent RK4
+// steps becomes 5 shuffle rounds per chunk.  Stores: one float4 per step,
+// contiguous across the warp in the [K][H] arrays.  In analytic mode the frame
+// SDF of every gate and the collision hinge are evaluated at every p_{h+1}.
+constexpr int kRollWarps = 4;
+constexpr int kSteps = 2;                      // consecutive horizon steps per lane
 
-__global__ void __launch_bounds__(64) rollout_kernel(StepParams P, StepBuffers B, int analytic) {
+__global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, StepBuffers B, int analytic) {
     extern __shared__ float4 sU[];                 // [H]
     __shared__ float sPose[kMaxGates * 8];
     pdl_trigger();
@@ -46,13 +94,16 @@ __global__ void __launch_bounds__(64) rollout_kernel(StepParams P, StepBuffers B
     for (int i = threadIdx.x; i < P.H; i += blockDim.x) sU[i] = B.nominal[i];
     for (int i = threadIdx.x; i < P.G * 8; i += blockDim.x) sPose[i] = B.poses[i];
     __syncthreads();
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= P.K) return;
+    const int lane = threadIdx.x & 31;
+    const int k = blockIdx.x * kRollWarps + (threadIdx.x >> 5);
+    if (k >= P.K) return;                          // whole warps only
+    const int K = P.K, H = P.H;
+    const uint32_t st = B.step[0];
 
     const Vec3 p0 = v3(B.state[0], B.state[1], B.state[2]);
-    Vec3 p = p0;
-    Vec3 v = v3(B.state[3], B.state[4], B.state[5]);
-    Quat q{B.state[6], B.state[7], B.state[8], B.state[9]};
+    Vec3 pc = p0;                                  // p, v, q at the start of the chunk
+    Vec3 vc = v3(B.state[3], B.state[4], B.state[5]);
+    Quat qc{B.state[6], B.state[7], B.state[8], B.state[9]};
 
     // target gate: the first gate whose plane the current position has not crossed
     int tgt = -1;
@@ -66,30 +117,98 @@ __global__ void __launch_bounds__(64) rollout_kernel(StepParams P, StepBuffers B
     }
 
     const float uh = P.mass * P.gravity;
+    const float dt = P.dt;
+    const float c3 = dt * dt * (1.f / 6.f), c6 = dt * (1.f / 6.f);
+    const float b2 = 0.25f * dt;
+    const float inv_m = 1.f / P.mass;
     float jctl = 0.f, jcol = 0.f;
-    const int K = P.K, H = P.H;
-    // The noise of the next kPrefetch steps is loaded while the current ones are
-    // integrated, so the load latency is not on the serial RK4 chain.
-    float4 cur[kPrefetch], nxt[kPrefetch];
+    float4* noise_k = B.noise + static_cast<size_t>(k) * H;
+    float4* pos_k = B.pos + static_cast<size_t>(k) * H;
+    for (int c0 = 0; c0 < H; c0 += 32 * kSteps) {
+        const int h0 = c0 + kSteps * lane;
+        // pass A: noise, clipped controls, control cost, the segment's attitude increment
+        float4 u[kSteps];
+        Quat N[kSteps];
+        Quat seg{1.f, 0.f, 0.f, 0.f};
+        int nact = 0;
 #pragma unroll
-    for (int j = 0; j < kPrefetch; ++j) cur[j] = (j < H) ? __ldcs(B.noise + j * K + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int h0 = 0; h0 < H; h0 += kPrefetch) {
-#pragma unroll
-        for (int j = 0; j < kPrefetch; ++j) {
-            const int hn = h0 + kPrefetch + j;
-            nxt[j] = (hn < H) ? __ldcs(B.noise + hn * K + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int j = 0; j < kSteps; ++j) {
+            const int h = h0 + j;
+            u[j] = make_float4(uh, 0.f, 0.f, 0.f);       // steps past H: no rotation, no increments
+            if (h < H) {
+                const float4 d = noise_from_block(P, noise_block(P, k, h, st));
+                noise_k[h] = d;
+                const float4 un = sU[h];
+                u[j] = clip_control(P, make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w));
+                const float e0 = u[j].x - uh;
+                jctl += e0 * e0 + u[j].y * u[j].y + u[j].z * u[j].z + u[j].w * u[j].w;
+                ++nact;
+            }
+            const float d2 = dt * dt * (u[j].y * u[j].y + u[j].z * u[j].z + u[j].w * u[j].w);
+            const float an = 1.f - d2 * 0.125f + d2 * d2 * (1.f / 384.f);
+            const float bn = dt * (0.5f - d2 * (1.f / 48.f));
+            N[j] = qnormalize(Quat{an, bn * u[j].y, bn * u[j].z, bn * u[j].w});
+            seg = (j == 0) ? N[0] : qmul(seg, N[j]);
         }
+        const Quat S = warp_scan_qmul(seg, lane);
+        Quat E = shfl_up(S, 1);
+        if (lane == 0) E = Quat{1.f, 0.f, 0.f, 0.f};
+        // attitude at the segment's start (the first step uses the state's attitude as given,
+        // as the sequential form does)
+        Quat q = (h0 == 0) ? qc : qnormalize(qmul(qc, E));
+
+        // pass B: stage accelerations; velocity and position offsets within the segment
+        Vec3 L[kSteps];
+        Vec3 V = v3(0.f, 0.f, 0.f);
+        Vec3 Lacc = v3(0.f, 0.f, 0.f);
 #pragma unroll
-        for (int j = 0; j < kPrefetch; ++j) {
+        for (int j = 0; j < kSteps; ++j) {
+            const bool act = h0 + j < H;
+            const float tm = u[j].x * inv_m;
+            const float d2 = dt * dt * (u[j].y * u[j].y + u[j].z * u[j].z + u[j].w * u[j].w);
+            const Quat wq{-q.x * u[j].y - q.y * u[j].z - q.z * u[j].w,
+                          q.w * u[j].y + q.y * u[j].w - q.z * u[j].z,
+                          q.w * u[j].z - q.x * u[j].w + q.z * u[j].y,
+                          q.w * u[j].w + q.x * u[j].z - q.y * u[j].y};
+            const float a3 = 1.f - d2 * (1.f / 16.f);
+            const float a4 = 1.f - d2 * 0.125f;
+            const float b4 = dt * (0.5f - d2 * (1.f / 32.f));
+            const Quat q2{q.w + b2 * wq.w, q.x + b2 * wq.x, q.y + b2 * wq.y, q.z + b2 * wq.z};
+            const Quat q3{a3 * q.w + b2 * wq.w, a3 * q.x + b2 * wq.x, a3 * q.y + b2 * wq.y, a3 * q.z + b2 * wq.z};
+            const Quat q4{a4 * q.w + b4 * wq.w, a4 * q.x + b4 * wq.x, a4 * q.y + b4 * wq.y, a4 * q.z + b4 * wq.z};
+            const Vec3 z1 = body_z(q), z2 = body_z(q2), z3 = body_z(q3), z4 = body_z(q4);
+            const Vec3 s3 = v3(z1.x + z2.x + z3.x, z1.y + z2.y + z3.y, z1.z + z2.z + z3.z);
+            const Vec3 s6 = v3(z1.x + 2.f * (z2.x + z3.x) + z4.x, z1.y + 2.f * (z2.y + z3.y) + z4.y,
+                               z1.z + 2.f * (z2.z + z3.z) + z4.z);
+            if (act) {
+                // p offset after this step: previous offset + dt V_j + dt^2/6 (a1 + a2 + a3)
+                Lacc = v3(Lacc.x + dt * V.x + c3 * (tm * s3.x), Lacc.y + dt * V.y + c3 * (tm * s3.y),
+                          Lacc.z + dt * V.z + c3 * (tm * s3.z - 3.f * P.gravity));
+                V = v3(V.x + c6 * (tm * s6.x), V.y + c6 * (tm * s6.y), V.z + (c6 * (tm * s6.z) - dt * P.gravity));
+            }
+            L[j] = Lacc;
+            if (j + 1 < kSteps) q = qnormalize(qmul(q, N[j]));
+        }
+        // segment start velocities and positions: exclusive scans of the segments' totals
+        const Vec3 Sv = warp_scan_add(V, lane);
+        Vec3 ev = shfl_up(Sv, 1);
+        if (lane == 0) ev = v3(0.f, 0.f, 0.f);
+        const Vec3 vs = v3(vc.x + ev.x, vc.y + ev.y, vc.z + ev.z);
+        const float tn = dt * static_cast<float>(nact);
+        const Vec3 dP = v3(tn * vs.x + Lacc.x, tn * vs.y + Lacc.y, tn * vs.z + Lacc.z);
+        const Vec3 Sp = warp_scan_add(dP, lane);
+        Vec3 ep = shfl_up(Sp, 1);
+        if (lane == 0) ep = v3(0.f, 0.f, 0.f);
+        const Vec3 ps = v3(pc.x + ep.x, pc.y + ep.y, pc.z + ep.z);
+
+        // pass C: positions p_{h+1} = p_s + (j + 1) dt v_s + L_j
+#pragma unroll
+        for (int j = 0; j < kSteps; ++j) {
             const int h = h0 + j;
             if (h < H) {
-                const float4 d = cur[j];
-                const float4 un = sU[h];
-                const float4 u = clip_control(P, make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w));
-                const float e0 = u.x - uh;
-                jctl += e0 * e0 + u.y * u.y + u.z * u.z + u.w * u.w;
-                rk4_step(P, p, v, q, u.x, v3(u.y, u.z, u.w));
-                B.pos[h * K + k] = make_float4(p.x, p.y, p.z, 0.f);
+                const float tj = dt * static_cast<float>(j + 1);
+                const Vec3 p = v3(ps.x + tj * vs.x + L[j].x, ps.y + tj * vs.y + L[j].y, ps.z + tj * vs.z + L[j].z);
+                pos_k[h] = make_float4(p.x, p.y, p.z, 0.f);
                 if (analytic) {
                     float smin = __int_as_float(0x7f800000);
                     for (int g = 0; g < P.G; ++g) {
@@ -100,168 +219,344 @@ __global__ void __launch_bounds__(64) rollout_kernel(StepParams P, StepBuffers B
                 }
             }
         }
-#pragma unroll
-        for (int j = 0; j < kPrefetch; ++j) cur[j] = nxt[j];
+        // state at the end of the chunk
+        const Vec3 pe = shfl_idx(Sp, 31);
+        pc = v3(pc.x + pe.x, pc.y + pe.y, pc.z + pe.z);
+        const Vec3 sv = shfl_idx(Sv, 31);
+        vc = v3(vc.x + sv.x, vc.y + sv.y, vc.z + sv.z);
+        qc = qnormalize(qmul(qc, shfl_idx(S, 31)));
     }
-    const float jprog = (tgt >= 0) ? -(n_tgt.x * (p.x - p0.x) + n_tgt.y * (p.y - p0.y) + n_tgt.z * (p.z - p0.z))
-                                   : 0.f;
-    B.parts[k] = analytic ? P.w_col * jcol : 0.f;
-    B.parts[K + k] = jprog;
-    B.parts[2 * K + k] = P.w_u * jctl;
-}
-
-// ------------------------------------------------------------------ (d1) costs
-// J_k = J_col + J_prog + J_ctl (MLP modes: J_col = w_col sum_h max(0, d_safe - s_h)^2
-// over the stored SDF values, in order of h).  Each block also leaves the
-// partial (m_b, s_b) = (min_{k in b} J_k, sum_{k in b} exp(-(J_k - m_b) / lambda)),
-// from which rho = min J and eta = sum exp(-(J - rho) / lambda) of Eq. 5 follow
-// without another pass (online softmax).  Fixed reduction order: reruns are
-// bit-identical.
-constexpr int kCostThreads = 128;
-
-__device__ __forceinline__ float warp_min(float x) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
-    return x;
-}
-__device__ __forceinline__ float warp_sum(float x) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-}
-
-__global__ void __launch_bounds__(kCostThreads) cost_kernel(StepParams P, StepBuffers B, int mlp) {
-    __shared__ float sh[kCostThreads / 32];
-    const int K = P.K;
-    const int k = blockIdx.x * kCostThreads + threadIdx.x;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    pdl_trigger();
-    pdl_wait();
-    float J = __int_as_float(0x7f800000);
-    if (k < K) {
-        float jcol;
-        if (mlp) {
-            float acc = 0.f;
-#pragma unroll 10
-            for (int h = 0; h < P.H; ++h) acc += hinge_sq(__ldcs(B.sdf + h * K + k), P.d_safe);
-            jcol = P.w_col * acc;
-            B.parts[k] = jcol;
-        } else {
-            jcol = B.parts[k];
-        }
-        J = jcol + B.parts[K + k] + B.parts[2 * K + k];
-        B.J[k] = J;
-    }
-    float m = warp_min(J);
-    if (lane == 0) sh[wid] = m;
-    __syncthreads();
-    m = sh[0];
-#pragma unroll
-    for (int i = 1; i < kCostThreads / 32; ++i) m = fminf(m, sh[i]);
-    __syncthreads();
-    const float e = (k < K) ? expf(-(J - m) / P.lam) : 0.f;
-    float s = warp_sum(e);
-    if (lane == 0) sh[wid] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = sh[0];
-#pragma unroll
-        for (int i = 1; i < kCostThreads / 32; ++i) t += sh[i];
-        B.red[2 * blockIdx.x] = m;
-        B.red[2 * blockIdx.x + 1] = t;
+    jctl = warp_sum(jctl);
+    jcol = warp_sum(jcol);
+    if (lane == 0) {
+        const float jprog =
+            (tgt >= 0) ? -(n_tgt.x * (pc.x - p0.x) + n_tgt.y * (pc.y - p0.y) + n_tgt.z * (pc.z - p0.z)) : 0.f;
+        B.parts[k] = analytic ? P.w_col * jcol : 0.f;
+        B.parts[K + k] = jprog;
+        B.parts[2 * K + k] = P.w_u * jctl;
     }
 }
 
-// ------------------------------------------------------------------ (d2) weights, update, receding horizon
-// Every block first combines the cost blocks' partials into rho and eta (same
-// fixed order in every block), then block h forms w_k = exp(-(J_k - rho) / lambda) / eta
-// and U*_new[h] = sum_k w_k clip(U*_h + delta_{k,h}) (Eq. 5) with a fixed-order
-// tree; block 0 also stores w.  The last block to finish applies U*_new[0] to
-// the device-resident state with one RK4 step, writes the shifted warm start
-// and bumps the step counter.
-constexpr int kUpdThreads = 512;
+// ------------------------------------------------------------------ (d) costs, weights, update, receding horizon
+// Block b owns R consecutive rollouts (R a multiple of 32, at most kCuMaxBlocks blocks):
+//  1. J_k = J_col + J_prog + J_ctl (MLP modes: J_col = w_col sum_h max(0, d_safe - s_h)^2
+//     over rollout k's row of the SDF array), rho_b = min of the block's J_k,
+//     e_k = exp(-(J_k - rho_b) / lambda), eta_b = sum of the block's e_k;
+//  2. S_b[h] = sum_{k in b} e_k clip(U*_h + delta_{k,h});
+//  3. the last block of every group of kCuGroup blocks combines the group (softmax
+//     with max subtraction: rho_g = min rho_b, f_b = exp(-(rho_b - rho_g) / lambda),
+//     eta_g = sum f_b eta_b, S_g = sum f_b S_b);
+//  4. the last group combiner combines the groups the same way (rho, F_g, eta):
+//     U*_new[h] = sum_g (F_g / eta) S_g[h] and w_k = e_k f_b F_g / eta (Eq. 5), then
+//     applies U*_new[0] to the device-resident state with one RK4 step, writes the
+//     shifted warm start and bumps the step counter.
+// Every reduction runs in a fixed order (group membership and summation order do
+// not depend on which block finishes last): reruns are bit-identical.  Loads are
+// issued in explicit batches so each phase waits for memory about once.  When the
+// caller passed device buffers for U*_new, w and J, the kernel writes them too.
+constexpr int kCuThreads = 256;
+constexpr int kCuWarps = kCuThreads / 32;
+constexpr int kCuMaxBlocks = 128;
+constexpr int kCuGroup = 8;                        // blocks per first-level combine
+constexpr int kCuMaxGroups = kCuMaxBlocks / kCuGroup;
+constexpr int kCuHChunk = 64;                      // horizon steps per pass of the weighted sums
+constexpr int kCuBatch = 4;                        // rollouts per warp whose loads are in flight together
 
-__global__ void __launch_bounds__(kUpdThreads) update_plant_kernel(StepParams P, StepBuffers B) {
-    __shared__ float4 sh[kUpdThreads / 32];
+__device__ __forceinline__ float4 f4_fma(float a, float4 x, float4 y) {
+    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+
+__global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, StepBuffers B, int mlp, int R) {
+    extern __shared__ float sE[];                  // [R] J_k, then e_k
+    __shared__ float4 sRed[kCuWarps][kCuHChunk];
+    __shared__ float sWarp[kCuWarps];
+    __shared__ float sF[kCuMaxBlocks];
     __shared__ float s_rho, s_eta;
     __shared__ int is_last;
+    const float* __restrict__ sdf = B.sdf;
+    const float4* __restrict__ noise = B.noise;
+    const float* __restrict__ parts_in = B.parts;
     pdl_wait();
-    const int h = blockIdx.x;
-    const int K = P.K;
+    const int K = P.K, H = P.H;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nb = (K + kCostThreads - 1) / kCostThreads;
-    if (wid == 0) {
-        float m = __int_as_float(0x7f800000);
-        for (int b = lane; b < nb; b += 32) m = fminf(m, B.red[2 * b]);
-        const float rho = warp_min(m);
-        float s = 0.f;
-        for (int b = lane; b < nb; b += 32) s += B.red[2 * b + 1] * expf(-(B.red[2 * b] - rho) / P.lam);
-        const float eta = warp_sum(s);
-        if (lane == 0) {
-            s_rho = rho;
-            s_eta = eta;
+    const int k0 = blockIdx.x * R;
+    const int nk = min(K, k0 + R) - k0;
+    const float inv_lam = 1.f / P.lam;
+    const float inf = __int_as_float(0x7f800000);
+
+    // the noise rows of this warp's first kCuBatch rollouts (first kCuHChunk steps) are
+    // loaded now; their latency overlaps the cost phase
+    float4 pre_a[kCuBatch], pre_b[kCuBatch];
+#pragma unroll
+    for (int u = 0; u < kCuBatch; ++u) {
+        const int i = wid + u * kCuWarps;
+        const float4* nrow = noise + static_cast<size_t>(k0 + (i < nk ? i : 0)) * H;
+        pre_a[u] = (i < nk && lane < H) ? __ldcs(nrow + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+        pre_b[u] = (i < nk && lane + 32 < H) ? __ldcs(nrow + 32 + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+
+    // 1. costs: one warp per rollout (the horizon across the lanes), kCuBatch rollouts at a time
+    float mloc = inf;
+    for (int i0 = wid; i0 < nk; i0 += kCuWarps * kCuBatch) {
+        float acc[kCuBatch], pj[kCuBatch], pc[kCuBatch], pcol[kCuBatch];
+#pragma unroll
+        for (int u = 0; u < kCuBatch; ++u) {
+            const int i = i0 + u * kCuWarps;
+            const int k = k0 + (i < nk ? i : 0);
+            acc[u] = 0.f;
+            pcol[u] = 0.f;
+            if (mlp) {
+                const float* srow = sdf + static_cast<size_t>(k) * H;
+                const float s0 = (lane < H) ? __ldcs(srow + lane) : inf;
+                const float s1 = (lane + 32 < H) ? __ldcs(srow + lane + 32) : inf;
+                acc[u] = hinge_sq(s0, P.d_safe) + hinge_sq(s1, P.d_safe);
+                for (int h = lane + 64; h < H; h += 32) acc[u] += hinge_sq(__ldcs(srow + h), P.d_safe);
+            } else {
+                pcol[u] = parts_in[k];
+            }
+            pj[u] = parts_in[K + k];
+            pc[u] = parts_in[2 * K + k];
+        }
+#pragma unroll
+        for (int u = 0; u < kCuBatch; ++u) {
+            const int i = i0 + u * kCuWarps;
+            const float jcol = mlp ? P.w_col * warp_sum(acc[u]) : pcol[u];
+            if (i < nk) {
+                const float J = jcol + pj[u] + pc[u];
+                if (lane == 0) sE[i] = J;
+                if (mlp && lane == 1) B.parts[k0 + i] = jcol;
+                mloc = fminf(mloc, J);
+            }
         }
     }
-    __syncthreads();
-    const float rho = s_rho, eta = s_eta;
-    const float4 un = B.nominal[h];
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 4
-    for (int k = threadIdx.x; k < K; k += kUpdThreads) {
-        const float w = expf(-(B.J[k] - rho) / P.lam) / eta;
-        if (h == 0) B.w[k] = w;
-        const float4 d = __ldcs(B.noise + h * K + k);
-        const float4 u = clip_control(P, make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w));
-        acc.x = fmaf(w, u.x, acc.x);
-        acc.y = fmaf(w, u.y, acc.y);
-        acc.z = fmaf(w, u.z, acc.z);
-        acc.w = fmaf(w, u.w, acc.w);
-    }
-    acc.x = warp_sum(acc.x);
-    acc.y = warp_sum(acc.y);
-    acc.z = warp_sum(acc.z);
-    acc.w = warp_sum(acc.w);
-    if (lane == 0) sh[wid] = acc;
+    if (lane == 0) sWarp[wid] = mloc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        float4 t = sh[0];
-        for (int i = 1; i < kUpdThreads / 32; ++i) {
-            t.x += sh[i].x; t.y += sh[i].y; t.z += sh[i].z; t.w += sh[i].w;
+        float m = sWarp[0];
+#pragma unroll
+        for (int i = 1; i < kCuWarps; ++i) m = fminf(m, sWarp[i]);
+        s_rho = m;
+    }
+    __syncthreads();
+    const float rho_b = s_rho;
+    float eloc = 0.f;
+    for (int i = threadIdx.x; i < nk; i += kCuThreads) {
+        const float J = sE[i];
+        const float e = expf(-(J - rho_b) * inv_lam);
+        B.J[k0 + i] = J;
+        if (B.out_J) B.out_J[k0 + i] = J;
+        B.w[k0 + i] = e;                           // scaled to w_k by the last combiner
+        sE[i] = e;
+        eloc += e;
+    }
+    eloc = warp_sum(eloc);
+    if (lane == 0) sWarp[wid] = eloc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float e = sWarp[0];
+#pragma unroll
+        for (int i = 1; i < kCuWarps; ++i) e += sWarp[i];
+        B.bstat[blockIdx.x] = make_float2(rho_b, e);
+    }
+
+    // 2. e-weighted sums of the rolled-out (clipped) controls, kCuHChunk horizon steps per pass
+    for (int c0 = 0; c0 < H; c0 += kCuHChunk) {
+        const int ha = c0 + lane, hb = c0 + 32 + lane;
+        const bool va = ha < H, vb = hb < H;
+        const float4 una = B.nominal[min(ha, H - 1)];
+        const float4 unb = B.nominal[min(hb, H - 1)];
+        float4 aa = make_float4(0.f, 0.f, 0.f, 0.f), ab = aa;
+        for (int i0 = wid; i0 < nk; i0 += kCuWarps * kCuBatch) {
+            float4 da[kCuBatch], db[kCuBatch];
+            float e[kCuBatch];
+            const bool first = (c0 == 0 && i0 == wid);
+#pragma unroll
+            for (int u = 0; u < kCuBatch; ++u) {
+                const int i = i0 + u * kCuWarps;
+                const bool v = i < nk;
+                const float4* nrow = noise + static_cast<size_t>(k0 + (v ? i : 0)) * H;
+                e[u] = v ? sE[i] : 0.f;
+                if (first) {
+                    da[u] = pre_a[u];
+                    db[u] = pre_b[u];
+                } else {
+                    da[u] = (v && va) ? __ldcs(nrow + ha) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    db[u] = (v && vb) ? __ldcs(nrow + hb) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kCuBatch; ++u) {
+                aa = f4_fma(e[u], clip_control(P, make_float4(una.x + da[u].x, una.y + da[u].y, una.z + da[u].z,
+                                                             una.w + da[u].w)), aa);
+                ab = f4_fma(e[u], clip_control(P, make_float4(unb.x + db[u].x, unb.y + db[u].y, unb.z + db[u].z,
+                                                             unb.w + db[u].w)), ab);
+            }
         }
-        B.unew[h] = t;
-        if (h == 0) {
-            B.stats[0] = rho;
-            B.stats[1] = eta;
+        sRed[wid][lane] = aa;
+        sRed[wid][32 + lane] = ab;
+        __syncthreads();
+        if (threadIdx.x < kCuHChunk && c0 + threadIdx.x < H) {
+            float4 t = sRed[0][threadIdx.x];
+#pragma unroll
+            for (int i = 1; i < kCuWarps; ++i) {
+                const float4 o = sRed[i][threadIdx.x];
+                t.x += o.x; t.y += o.y; t.z += o.z; t.w += o.w;
+            }
+            B.upart[static_cast<size_t>(blockIdx.x) * H + c0 + threadIdx.x] = t;
         }
+        __syncthreads();
+    }
+
+    // 3. the last block of the group combines the group's blocks (the block's writes are
+    //    ordered before its ticket by the barrier and thread 0's fence)
+    const int nb = gridDim.x;
+    const int grp = blockIdx.x / kCuGroup;
+    const int gb0 = grp * kCuGroup;
+    const int gn = min(nb - gb0, kCuGroup);
+    __syncthreads();
+    if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned tk = atomicAdd(&B.tickets[1], 1u);
-        is_last = (tk == gridDim.x - 1);
+        const unsigned tk = atomicAdd(&B.tickets[2 + grp], 1u);
+        is_last = (tk == static_cast<unsigned>(gn - 1));
     }
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-
-    const float uh = P.mass * P.gravity;
-    for (int i = threadIdx.x; i < P.H; i += kUpdThreads) {
-        B.nominal[i] = (i + 1 < P.H) ? __ldcg(&B.unew[i + 1]) : make_float4(uh, 0.f, 0.f, 0.f);
-    }
     if (threadIdx.x == 0) {
-        const float4 u0 = __ldcg(&B.unew[0]);
-        float* s = B.state;
-        Vec3 p = v3(s[0], s[1], s[2]);
-        Vec3 v = v3(s[3], s[4], s[5]);
-        Quat q{s[6], s[7], s[8], s[9]};
-        rk4_step(P, p, v, q, u0.x, v3(u0.y, u0.z, u0.w));
-        s[0] = p.x; s[1] = p.y; s[2] = p.z;
-        s[3] = v.x; s[4] = v.y; s[5] = v.z;
-        s[6] = q.w; s[7] = q.x; s[8] = q.y; s[9] = q.z;
-        s[10] = u0.y; s[11] = u0.z; s[12] = u0.w;
-        const uint32_t lo = B.step[0] + 1u;
-        B.step[0] = lo;
-        if (lo == 0u) B.step[1] += 1u;
-        B.tickets[1] = 0u;
+        float2 bs[kCuGroup];
+        float m = inf;
+#pragma unroll
+        for (int j = 0; j < kCuGroup; ++j) {
+            bs[j] = (j < gn) ? __ldcg(&B.bstat[gb0 + j]) : make_float2(inf, 0.f);
+            m = fminf(m, bs[j].x);
+        }
+        float e = 0.f;
+#pragma unroll
+        for (int j = 0; j < kCuGroup; ++j) {
+            const float f = (j < gn) ? expf(-(bs[j].x - m) * inv_lam) : 0.f;
+            sF[j] = f;
+            e += f * bs[j].y;
+            if (j < gn) B.bfac[gb0 + j] = f;
+        }
+        B.gstat[grp] = make_float2(m, e);
+        B.tickets[2 + grp] = 0u;
+    }
+    __syncthreads();
+    for (int h = threadIdx.x; h < H; h += kCuThreads) {
+        float4 sb[kCuGroup];
+#pragma unroll
+        for (int j = 0; j < kCuGroup; ++j)
+            sb[j] = (j < gn) ? __ldcg(B.upart + static_cast<size_t>(gb0 + j) * H + h) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < kCuGroup; ++j) t = f4_fma(sF[j], sb[j], t);
+        B.gpart[static_cast<size_t>(grp) * H + h] = t;
+    }
+
+    // 4. the last group combiner combines the groups and advances the controller
+    __syncthreads();
+    const int ng = (nb + kCuGroup - 1) / kCuGroup;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned tk = atomicAdd(&B.tickets[1], 1u);
+        is_last = (tk == static_cast<unsigned>(ng - 1));
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        float2 gs[kCuMaxGroups];
+        float m = inf;
+#pragma unroll
+        for (int j = 0; j < kCuMaxGroups; ++j) {
+            gs[j] = (j < ng) ? __ldcg(&B.gstat[j]) : make_float2(inf, 0.f);
+            m = fminf(m, gs[j].x);
+        }
+        float e = 0.f;
+#pragma unroll
+        for (int j = 0; j < kCuMaxGroups; ++j) {
+            const float f = (j < ng) ? expf(-(gs[j].x - m) * inv_lam) : 0.f;
+            sF[j] = f;
+            e += f * gs[j].y;
+        }
+        s_rho = m;
+        s_eta = e;
+    }
+    __syncthreads();
+    if (threadIdx.x < kCuMaxGroups) sF[threadIdx.x] = sF[threadIdx.x] / s_eta;
+    __syncthreads();
+    for (int h = threadIdx.x; h < H; h += kCuThreads) {
+        float4 sg[kCuMaxGroups];
+#pragma unroll
+        for (int j = 0; j < kCuMaxGroups; ++j)
+            sg[j] = (j < ng) ? __ldcg(B.gpart + static_cast<size_t>(j) * H + h) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < kCuMaxGroups; ++j) t = f4_fma(sF[j], sg[j], t);
+        B.unew[h] = t;
+        if (B.out_U) B.out_U[h] = t;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        // warp 0: shift the warm start, apply U*_new[0] to the device-resident state
+        const float uh = P.mass * P.gravity;
+        for (int i = lane; i < H; i += 32)
+            B.nominal[i] = (i + 1 < H) ? B.unew[i + 1] : make_float4(uh, 0.f, 0.f, 0.f);
+        if (lane == 0) {
+            B.stats[0] = s_rho;
+            B.stats[1] = s_eta;
+            const float4 u0 = B.unew[0];
+            float* s = B.state;
+            Vec3 p = v3(s[0], s[1], s[2]);
+            Vec3 v = v3(s[3], s[4], s[5]);
+            Quat q{s[6], s[7], s[8], s[9]};
+            rk4_step(P, p, v, q, u0.x, v3(u0.y, u0.z, u0.w));
+            s[0] = p.x; s[1] = p.y; s[2] = p.z;
+            s[3] = v.x; s[4] = v.y; s[5] = v.z;
+            s[6] = q.w; s[7] = q.x; s[8] = q.y; s[9] = q.z;
+            s[10] = u0.y; s[11] = u0.z; s[12] = u0.w;
+            const uint32_t lo = B.step[0] + 1u;
+            B.step[0] = lo;
+            if (lo == 0u) B.step[1] += 1u;
+            B.tickets[1] = 0u;
+        }
+    } else {
+        // warps 1..: w_k = e_k f_b F_g / eta, one update block (R rollouts) per warp pass
+        for (int b0 = wid - 1; b0 < nb; b0 += (kCuWarps - 1) * 4) {
+            float fb[4], wv[4][8];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int b = b0 + u * (kCuWarps - 1);
+                fb[u] = (b < nb) ? __ldcg(B.bfac + b) * sF[b / kCuGroup] : 0.f;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int kk = b * R + t * 32 + lane;
+                    wv[u][t] = (b < nb && t * 32 < R && kk < K) ? __ldcg(B.w + kk) : 0.f;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int b = b0 + u * (kCuWarps - 1);
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int kk = b * R + t * 32 + lane;
+                    if (b < nb && t * 32 < R && kk < K) {
+                        const float wk = wv[u][t] * fb[u];
+                        B.w[kk] = wk;
+                        if (B.out_w) B.out_w[kk] = wk;
+                    }
+                }
+                // blocks of more than 256 rollouts (K > 32768)
+                for (int kk = b * R + 256 + lane; b < nb && kk < min(K, (b + 1) * R); kk += 32) {
+                    const float wk = __ldcg(B.w + kk) * fb[u];
+                    B.w[kk] = wk;
+                    if (B.out_w) B.out_w[kk] = wk;
+                }
+            }
+        }
     }
 }
+
 
 // ------------------------------------------------------------------ per-gate first-layer bias
 // The Gate-SDF decoder's first layer sees [p, z]; z is fixed per gate, so its
@@ -280,13 +575,6 @@ __global__ void first_layer_bias_kernel(const float* __restrict__ W1, const floa
 
 }  // namespace
 
-cudaError_t launch_noise(const StepParams& P, const StepBuffers& B, cudaStream_t s) {
-    const int n = P.K * P.H;
-    const int blocks = (n + 255) / 256;
-    noise_kernel<<<blocks, 256, 0, s>>>(P, B.step, B.noise);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_noise_words(const StepParams& P, const StepBuffers& B, uint4* out, cudaStream_t s) {
     const int n = P.K * P.H;
     noise_words_kernel<<<(n + 255) / 256, 256, 0, s>>>(P, B.step, out);
@@ -294,18 +582,34 @@ cudaError_t launch_noise_words(const StepParams& P, const StepBuffers& B, uint4*
 }
 
 cudaError_t launch_rollout(const StepParams& P, const StepBuffers& B, int analytic, cudaStream_t s) {
-    const int threads = 64;
-    return launch_dependent(P.pdl != 0, rollout_kernel, dim3((P.K + threads - 1) / threads), dim3(threads),
+    // first kernel of the step: ordered after the previous step's last kernel by the stream
+    return launch_dependent(false, rollout_kernel, dim3((P.K + kRollWarps - 1) / kRollWarps), dim3(kRollWarps * 32),
                             P.H * sizeof(float4), s, P, B, analytic);
 }
 
-cudaError_t launch_cost_weights(const StepParams& P, const StepBuffers& B, int mlp, cudaStream_t s) {
-    return launch_dependent(P.pdl != 0, cost_kernel, dim3((P.K + kCostThreads - 1) / kCostThreads), dim3(kCostThreads), 0, s,
-                            P, B, mlp);
+int update_rollouts_per_block(int K) {
+    const int r = (K + kCuMaxBlocks - 1) / kCuMaxBlocks;
+    const int r32 = ((r + 31) / 32) * 32;
+    return r32 < 32 ? 32 : r32;
 }
 
-cudaError_t launch_update_plant(const StepParams& P, const StepBuffers& B, cudaStream_t s) {
-    return launch_dependent(P.pdl != 0, update_plant_kernel, dim3(P.H), dim3(kUpdThreads), 0, s, P, B);
+int update_blocks(int K) {
+    const int R = update_rollouts_per_block(K);
+    return (K + R - 1) / R;
+}
+
+int update_groups(int K) { return (update_blocks(K) + kCuGroup - 1) / kCuGroup; }
+
+cudaError_t configure_cost_update() {
+    // R floats of dynamic shared memory: up to MPPI_MAX_K / kCuMaxBlocks
+    return cudaFuncSetAttribute(cost_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(sizeof(float) * update_rollouts_per_block(kMaxRollouts)));
+}
+
+cudaError_t launch_cost_update(const StepParams& P, const StepBuffers& B, int mlp, cudaStream_t s) {
+    const int R = update_rollouts_per_block(P.K);
+    return launch_dependent(P.pdl != 0, cost_update_kernel, dim3((P.K + R - 1) / R), dim3(kCuThreads),
+                            sizeof(float) * R, s, P, B, mlp, R);
 }
 
 cudaError_t launch_first_layer_bias(const float* W1, const float* b1, const float* latents, int G, float* b1p,

@@ -28,11 +28,10 @@ cudaError_t launch_dependent(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-// (a) noise: delta u for every (h, k) -> B.noise
-cudaError_t launch_noise(const StepParams& P, const StepBuffers& B, cudaStream_t s);
-// raw Philox words for every (h, k) (tests)
+// raw Philox words for every (k, h), [K][H] (tests)
 cudaError_t launch_noise_words(const StepParams& P, const StepBuffers& B, uint4* out, cudaStream_t s);
-// (b) rollouts; with analytic != 0 the frame SDF cost is fused in
+// (a) + (b) noise -> B.noise and rollouts -> B.pos, control / progress costs; with
+// analytic != 0 the frame SDF cost is fused in
 cudaError_t launch_rollout(const StepParams& P, const StepBuffers& B, int analytic, cudaStream_t s);
 // (c) Gate-SDF MLP at every rollout state -> B.sdf (min over gates)
 struct MlpWeights {
@@ -59,9 +58,13 @@ cudaError_t launch_sdf_mlp_fp16(const StepParams& P, const StepBuffers& B, const
                                 cudaStream_t s);
 cudaError_t launch_sdf_mlp_fp8(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
                                cudaStream_t s);
-// (d) costs -> weights; weighted update + plant step + shift
-cudaError_t launch_cost_weights(const StepParams& P, const StepBuffers& B, int mlp, cudaStream_t s);
-cudaError_t launch_update_plant(const StepParams& P, const StepBuffers& B, cudaStream_t s);
+// (d) costs -> weights -> weighted update -> plant step + shift (one kernel)
+cudaError_t launch_cost_update(const StepParams& P, const StepBuffers& B, int mlp, cudaStream_t s);
+cudaError_t configure_cost_update();
+// blocks of the update kernel for K rollouts (sizes B.upart and B.bstat)
+int update_blocks(int K);
+// groups of the update kernel's two-level combine (sizes B.gpart and B.gstat)
+int update_groups(int K);
 // per-gate first-layer bias b1'_g = W1[:, 3:67] z_g + b1
 cudaError_t launch_first_layer_bias(const float* W1, const float* b1, const float* latents, int G, float* b1p,
                                     cudaStream_t s);

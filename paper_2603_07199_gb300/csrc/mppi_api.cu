@@ -51,6 +51,7 @@ struct mppi_ctx {
     // pinned staging
     float* h_in = nullptr;        // state(16) | nominal(H*4) | poses(maxG*8) | latents(maxG*64)
     float* h_out = nullptr;       // unew(H*4) | w(K) | J(K) | err(1)
+    float* d_hout = nullptr;      // device address of h_out (the step writes its outputs there directly)
     // completion of the last step enqueued by the serving path
     cudaEvent_t done = nullptr;
     // the step's kernels as one CUDA graph, re-captured when a launch argument changes
@@ -161,6 +162,16 @@ int recompute_b1p(mppi_ctx* c) {
 
 bool is_mlp(const mppi_ctx* c) { return c->cfg.sdf_mode != MPPI_SDF_ANALYTIC; }
 
+// Caller device buffers the step's last kernel writes U*_new, w and J into (NULL: none).
+void set_outputs(mppi_ctx* c, float4* U, float* w, float* J) {
+    if (c->B.out_U != U || c->B.out_w != w || c->B.out_J != J) {
+        c->B.out_U = U;
+        c->B.out_w = w;
+        c->B.out_J = J;
+        c->graph_dirty = true;
+    }
+}
+
 MlpWeights make_weights(const mppi_ctx* c) {
     MlpWeights W{};
     W.W1 = c->d_W1;
@@ -198,8 +209,6 @@ int enqueue_kernels(mppi_ctx* c) {
     const bool mlp = is_mlp(c);
     c->n_ev = 0;
     record(c, "start");
-    CUDA_TRY(c, launch_noise(P, c->B, c->stream));
-    record(c, "noise");
     CUDA_TRY(c, launch_rollout(P, c->B, mlp ? 0 : 1, c->stream));
     record(c, "rollout");
     if (mlp) {
@@ -218,10 +227,8 @@ int enqueue_kernels(mppi_ctx* c) {
             record(c, "sdf_mlp_fp8");
         }
     }
-    CUDA_TRY(c, launch_cost_weights(P, c->B, mlp ? 1 : 0, c->stream));
-    record(c, "cost_weights");
-    CUDA_TRY(c, launch_update_plant(P, c->B, c->stream));
-    record(c, "update_plant");
+    CUDA_TRY(c, launch_cost_update(P, c->B, mlp ? 1 : 0, c->stream));
+    record(c, "cost_update");
     return MPPI_OK;
 }
 
@@ -348,7 +355,8 @@ int mppi_create(const mppi_config* cfg, void* cuda_stream, mppi_ctx** out) {
     c->cfg = *cfg;
     c->device = dev;
     c->num_sms = sms;
-    if (configure_sdf_mlp_fp32() != cudaSuccess || configure_sdf_mlp_bf16() != cudaSuccess) {
+    if (configure_sdf_mlp_fp32() != cudaSuccess || configure_sdf_mlp_bf16() != cudaSuccess ||
+        configure_cost_update() != cudaSuccess) {
         delete c;
         return fail(nullptr, MPPI_E_CUDA, "kernel attribute set-up failed: %s", cudaGetErrorString(cudaGetLastError()));
     }
@@ -363,7 +371,7 @@ int mppi_create(const mppi_config* cfg, void* cuda_stream, mppi_ctx** out) {
     }
     const int K = cfg->K, H = cfg->H, MG = cfg->max_gates;
     const size_t KH = static_cast<size_t>(K) * H;
-    const int nred = 2 * ((K + 127) / 128);
+    const int nub = update_blocks(K);
     StepBuffers& B = c->B;
     rc = MPPI_OK;
     rc = rc ? rc : dev_alloc(c, &B.state, 16);
@@ -378,9 +386,13 @@ int mppi_create(const mppi_config* cfg, void* cuda_stream, mppi_ctx** out) {
     rc = rc ? rc : dev_alloc(c, &B.J, K);
     rc = rc ? rc : dev_alloc(c, &B.w, K);
     rc = rc ? rc : dev_alloc(c, &B.unew, H);
-    rc = rc ? rc : dev_alloc(c, &B.red, nred);
+    rc = rc ? rc : dev_alloc(c, &B.upart, static_cast<size_t>(nub) * H);
+    rc = rc ? rc : dev_alloc(c, &B.bstat, nub);
+    rc = rc ? rc : dev_alloc(c, &B.bfac, nub);
+    rc = rc ? rc : dev_alloc(c, &B.gpart, static_cast<size_t>(update_groups(K)) * H);
+    rc = rc ? rc : dev_alloc(c, &B.gstat, update_groups(K));
     rc = rc ? rc : dev_alloc(c, &B.stats, 4);
-    rc = rc ? rc : dev_alloc(c, &B.tickets, 4);
+    rc = rc ? rc : dev_alloc(c, &B.tickets, 32);
     rc = rc ? rc : dev_alloc(c, &B.err, 1);
     rc = rc ? rc : dev_alloc(c, &c->d_latents, static_cast<size_t>(MG) * kLatent);
     rc = rc ? rc : dev_alloc(c, &c->d_W1, kHidden * (3 + kLatent));
@@ -402,7 +414,8 @@ int mppi_create(const mppi_config* cfg, void* cuda_stream, mppi_ctx** out) {
     const size_t in_floats = 16 + static_cast<size_t>(H) * 4 + MG * 8 + MG * kLatent;
     const size_t out_floats = static_cast<size_t>(H) * 4 + 2 * static_cast<size_t>(K) + 4;
     if (cudaMallocHost(&c->h_in, in_floats * sizeof(float)) != cudaSuccess ||
-        cudaMallocHost(&c->h_out, out_floats * sizeof(float)) != cudaSuccess) {
+        cudaMallocHost(&c->h_out, out_floats * sizeof(float)) != cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->d_hout), c->h_out, 0) != cudaSuccess) {
         cudaGetLastError();
         std::snprintf(g_thread_err, sizeof(g_thread_err), "pinned host allocation failed");
         mppi_destroy(c);
@@ -432,7 +445,7 @@ int mppi_create(const mppi_config* cfg, void* cuda_stream, mppi_ctx** out) {
     bool ok = cudaMemcpyAsync(B.state, st, 16 * sizeof(float), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
               cudaMemcpyAsync(B.nominal, nom, H * sizeof(float4), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
               cudaMemsetAsync(B.step, 0, 2 * sizeof(uint32_t), c->stream) == cudaSuccess &&
-              cudaMemsetAsync(B.tickets, 0, 4 * sizeof(unsigned), c->stream) == cudaSuccess &&
+              cudaMemsetAsync(B.tickets, 0, 32 * sizeof(unsigned), c->stream) == cudaSuccess &&
               cudaMemsetAsync(B.err, 0, sizeof(int), c->stream) == cudaSuccess &&
               cudaMemsetAsync(B.poses, 0, MG * 8 * sizeof(float), c->stream) == cudaSuccess &&
               cudaStreamSynchronize(c->stream) == cudaSuccess;
@@ -595,14 +608,13 @@ int mppi_step(mppi_ctx* c, const float* state, const float* gate_poses, const fl
         CUDA_TRY(c, cudaMemcpyAsync(c->B.nominal, c->h_in + 16, H * sizeof(float4), cudaMemcpyHostToDevice,
                                     c->stream));
     }
+    // the step's last kernel writes U*_new (and w, J when asked for) straight into the
+    // pinned staging buffer
+    float* ho = c->h_out;
+    float* dho = c->d_hout;
+    set_outputs(c, reinterpret_cast<float4*>(dho), weights ? dho + H * 4 : nullptr, costs ? dho + H * 4 + K : nullptr);
     rc = launch_step(c);
     if (rc != MPPI_OK) return rc;
-    float* ho = c->h_out;
-    CUDA_TRY(c, cudaMemcpyAsync(ho, c->B.unew, H * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
-    if (weights)
-        CUDA_TRY(c, cudaMemcpyAsync(ho + H * 4, c->B.w, K * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
-    if (costs)
-        CUDA_TRY(c, cudaMemcpyAsync(ho + H * 4 + K, c->B.J, K * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     int* herr = reinterpret_cast<int*>(ho + H * 4 + 2 * K);
     CUDA_TRY(c, cudaMemcpyAsync(herr, c->B.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -637,13 +649,11 @@ int mppi_step_async(mppi_ctx* c, const float* d_state, const float* d_gate_poses
     if (rc != MPPI_OK) return rc;
     if (d_nominal)
         CUDA_TRY(c, cudaMemcpyAsync(c->B.nominal, d_nominal, H * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream));
+    // the step's last kernel writes the caller's buffers itself; a change of buffers is a
+    // change of launch arguments (the step graph is captured again)
+    set_outputs(c, reinterpret_cast<float4*>(d_new_controls), d_weights, d_costs);
     rc = launch_step(c);
     if (rc != MPPI_OK) return rc;
-    if (d_new_controls)
-        CUDA_TRY(c, cudaMemcpyAsync(d_new_controls, c->B.unew, H * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream));
-    if (d_weights)
-        CUDA_TRY(c, cudaMemcpyAsync(d_weights, c->B.w, K * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
-    if (d_costs) CUDA_TRY(c, cudaMemcpyAsync(d_costs, c->B.J, K * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
     ++c->step_count;
     return MPPI_OK;
 }
@@ -736,7 +746,7 @@ int mppi_get_kernel_times(mppi_ctx* c, const char** names, float* ms, int cap) {
 
 int mppi_kernels_per_step(const mppi_ctx* c) {
     if (!c) return 0;
-    return is_mlp(c) ? 5 : 4;
+    return is_mlp(c) ? 3 : 2;
 }
 
 int mppi_selftest_tc_gemm(const uint16_t* d_A, const uint16_t* d_B, float* d_D, void* stream) {
@@ -799,10 +809,10 @@ int ctx_enqueue_host_step(mppi_ctx* c, const float* state, int n_gates, const fl
     }
     int rc = check_ready(c);
     if (rc != MPPI_OK) return rc;
+    set_outputs(c, reinterpret_cast<float4*>(c->d_hout), nullptr, nullptr);   // U*_new straight into pinned staging
     rc = launch_step(c);
     if (rc != MPPI_OK) return rc;
     float* ho = c->h_out;
-    CUDA_TRY(c, cudaMemcpyAsync(ho, c->B.unew, H * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(ho + H * 4 + 2 * c->cfg.K, c->B.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaEventRecord(c->done, c->stream));
     ++c->step_count;
@@ -845,8 +855,10 @@ int ctx_restore(mppi_ctx* c, const float* nominal, const float* state, uint64_t 
 
 size_t ctx_device_bytes(const mppi_config& g) {
     const size_t K = g.K, H = g.H, MG = g.max_gates;
+    const size_t nub = static_cast<size_t>(update_blocks(g.K));
+    const size_t nug = static_cast<size_t>(update_groups(g.K));
     const size_t floats = 16 + 4 * H + 2 + MG * 8 + MG * kHidden + 4 * K * H * 2 + 3 * K + K * H + 2 * K + 4 * H +
-                          2 * ((K + 127) / 128) + 4 + 4 + 1 + MG * kLatent;
+                          nub * (4 * H + 3) + nug * (4 * H + 2) + 4 + 32 + 1 + MG * kLatent;
     const size_t weights = sizeof(float) * (kHidden * (3 + kLatent) + kHidden + 3 * (kHidden * kHidden + kHidden) + kHidden) +
                            3 * kHidden * kHidden * (2 + 2 + 1) + kHidden * 16 * 2;
     return floats * sizeof(float) + weights;

@@ -67,7 +67,7 @@ class GpuController:
         if which in (B.MPPI_BUF_NOISE, B.MPPI_BUF_POSITIONS):
             out = np.zeros(H * K * 4, dtype=np.float32)
             B.mppi_read_buffer(self.ctx, which, out)
-            return out.reshape(H, K, 4).transpose(1, 0, 2)          # -> [K, H, 4] like the oracle
+            return out.reshape(K, H, 4)                              # [K, H, 4] like the oracle
         if which == B.MPPI_BUF_COST_PARTS:
             out = np.zeros(3 * K, dtype=np.float32)
             B.mppi_read_buffer(self.ctx, which, out)
@@ -75,7 +75,7 @@ class GpuController:
         if which == B.MPPI_BUF_SDF:
             out = np.zeros(H * K, dtype=np.float32)
             B.mppi_read_buffer(self.ctx, which, out)
-            return out.reshape(H, K).T
+            return out.reshape(K, H)
         out = np.zeros(K, dtype=np.float32)
         B.mppi_read_buffer(self.ctx, which, out)
         return out
@@ -93,7 +93,7 @@ class GpuController:
     def noise_words(self):
         out = np.zeros(self.H * self.K * 4, dtype=np.uint32)
         B.mppi_read_noise_words(self.ctx, out)
-        return out.reshape(self.H, self.K, 4).transpose(1, 0, 2)
+        return out.reshape(self.K, self.H, 4)
 
 
 def cost_scale(ref):

@@ -1,0 +1,54 @@
+"""The scaled-up precision workload: K=16384 rollouts, H=64, four gates, one step.
+
+All four MLP paths run the same step from hover at the origin with the hover
+warm start; the FP64 oracle computes that step once for every rollout.  The
+FP32 path must meet the FP32 tolerances of the parity tests (per-rollout cost
+1e-4 relative, controls 1e-4 absolute, SDF 2e-5 m); the BF16, FP16 and E4M3
+tensor-core paths report SDF error (mm), cost relative error and control
+absolute error, bounded loosely (a layout or scale mistake gives errors of
+metres).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import mppi as O
+from paper_2603_07199_gb300 import binding as B
+
+from .gpu_helpers import GpuController, cost_scale
+from .test_gpu_parity import COST_RTOL, CTRL_ATOL, _bf16_errors, _report
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def four_gates():
+    wl = W.four_gate_mlp()
+    ref = O.mppi_step(wl["state"], wl["nominal"], wl["poses"], O.Params(**wl["params"]), 0, wl["latents"],
+                      wl["layers"])
+    return wl, ref
+
+
+BOUNDS = {"fp32": None, "fp16": (1.0, 5.0), "bf16": (10.0, 60.0), "fp8": (60.0, 400.0)}
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fp16", "bf16", "fp8"])
+def test_four_gates_K16384_H64(lib, four_gates, mode):
+    wl, ref = four_gates
+    g = GpuController(wl, mode)
+    try:
+        out = g.step(state=wl["state"], nominal=wl["nominal"])
+        err = _bf16_errors(g, ref, out)
+        _report(f"{mode}_K16384_H64_G4", err)
+        assert abs(float(out["weights"].astype(np.float64).sum()) - 1.0) < 1e-5
+        if mode == "fp32":
+            s = g.read(B.MPPI_BUF_SDF).astype(np.float64)
+            np.testing.assert_allclose(s, ref["sdf"], atol=2e-5, rtol=0)
+            cerr = np.abs(out["J"].astype(np.float64) - ref["J"])
+            assert np.all(cerr <= COST_RTOL * cost_scale(ref) + 1e-7), cerr.max()
+            np.testing.assert_allclose(out["U_new"], ref["U_new"], atol=CTRL_ATOL, rtol=0)
+        else:
+            mae, mx = BOUNDS[mode]
+            assert err["sdf_mae_mm"] < mae and err["sdf_max_mm"] < mx, err
+    finally:
+        g.close()

@@ -35,8 +35,8 @@ def test_noalloc_update_matches_mppi_step_on_two_calls(lib):
             nominal = W.hover_nominal(H) if call == 0 else g.nominal()
             out = g.step(state=wl["state"] if call == 0 else None, nominal=nominal if call == 0 else None)
             J = g.read(B.MPPI_BUF_COSTS)
-            noise = np.zeros(H * K * 4, dtype=np.float32)          # [h][k][4], as the step used it
-            B.mppi_read_buffer(g.ctx, B.MPPI_BUF_NOISE, noise)
+            # the step's noise ([k][h][4]) in the [h][k][4] layout the entry point takes
+            noise = np.ascontiguousarray(g.read(B.MPPI_BUF_NOISE).transpose(1, 0, 2))
             dJ = torch.from_numpy(J).to(dev)
             dnoise = torch.from_numpy(noise).to(dev)
             dnom = torch.from_numpy(np.ascontiguousarray(nominal, dtype=np.float32)).to(dev)
