@@ -45,14 +45,11 @@ struct StepBuffers {
     float4* unew;          // [H] updated sequence U*_new
     float4* upart;         // [update blocks][H] per-block sums of e_k U^k_h
     float2* bstat;         // [update blocks] per-block (min J, sum e_k)
-    float* bfac;           // [update blocks] block factor within its group exp(-(rho_b - rho_g) / lambda)
-    float4* gpart;         // [update groups][H] per-group sums
-    float2* gstat;         // [update groups] per-group (min J, sum)
     float4* out_U;         // optional caller device buffers written by the step (H x 4, K, K)
     float* out_w;
     float* out_J;
     float* stats;          // [4] rho, eta of the last step
-    unsigned* tickets;     // [32] last-block counters: [1] all groups, [2 + g] blocks of group g
+    unsigned* tickets;     // [32] [9] grid-barrier arrivals, [10] grid-barrier generation
     int* err;              // [1] device error word
 };
 

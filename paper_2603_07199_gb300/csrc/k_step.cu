@@ -243,22 +243,26 @@ __global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, 
 //     over rollout k's row of the SDF array), rho_b = min of the block's J_k,
 //     e_k = exp(-(J_k - rho_b) / lambda), eta_b = sum of the block's e_k;
 //  2. S_b[h] = sum_{k in b} e_k clip(U*_h + delta_{k,h});
-//  3. the last block of every group of kCuGroup blocks combines the group (softmax
-//     with max subtraction: rho_g = min rho_b, f_b = exp(-(rho_b - rho_g) / lambda),
-//     eta_g = sum f_b eta_b, S_g = sum f_b S_b);
-//  4. the last group combiner combines the groups the same way (rho, F_g, eta):
-//     U*_new[h] = sum_g (F_g / eta) S_g[h] and w_k = e_k f_b F_g / eta (Eq. 5), then
-//     applies U*_new[0] to the device-resident state with one RK4 step, writes the
-//     shifted warm start and bumps the step counter.
-// Every reduction runs in a fixed order (group membership and summation order do
-// not depend on which block finishes last): reruns are bit-identical.  Loads are
-// issued in explicit batches so each phase waits for memory about once.  When the
-// caller passed device buffers for U*_new, w and J, the kernel writes them too.
+//  3. grid barrier (the kernel is a cooperative launch, so all its blocks are resident);
+//  4. every block forms rho = min_b rho_b, F_b = exp(-(rho_b - rho) / lambda) and
+//     eta = sum_b F_b eta_b from the same data in the same order (bit-identical in every
+//     block), writes its own weights w_k = e_k F_b / eta (Eq. 5 with max subtraction) and
+//     U*_new[h] = sum_b (F_b / eta) S_b[h] for its share of the horizon, written in place
+//     as the shifted warm start; the block owning h = 0 applies U*_new[0] to the
+//     device-resident state with one RK4 step and bumps the step counter.
+// Every reduction runs in a fixed order: reruns are bit-identical.  Loads are issued in
+// explicit batches so each phase waits for memory about once.  When the caller passed
+// device buffers for U*_new, w and J, the kernel writes them too.
 constexpr int kCuThreads = 256;
 constexpr int kCuWarps = kCuThreads / 32;
 constexpr int kCuMaxBlocks = 128;
-constexpr int kCuGroup = 8;                        // blocks per first-level combine
-constexpr int kCuMaxGroups = kCuMaxBlocks / kCuGroup;
+constexpr uint64_t kGridWaitLimitNs = 2000000000ull;  // bound of the grid barrier's wait
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
 constexpr int kCuHChunk = 64;                      // horizon steps per pass of the weighted sums
 constexpr int kCuBatch = 4;                        // rollouts per warp whose loads are in flight together
 
@@ -407,156 +411,117 @@ __global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, S
         __syncthreads();
     }
 
-    // 3. the last block of the group combines the group's blocks (the block's writes are
-    //    ordered before its ticket by the barrier and thread 0's fence)
-    const int nb = gridDim.x;
-    const int grp = blockIdx.x / kCuGroup;
-    const int gb0 = grp * kCuGroup;
-    const int gn = min(nb - gb0, kCuGroup);
-    __syncthreads();
+    // 3. grid barrier (cooperative launch: every block is resident; the wait is bounded)
     if (threadIdx.x == 0) {
+        volatile unsigned* gen_p = B.tickets + 10;
+        const unsigned gen = *gen_p;
         __threadfence();
-        const unsigned tk = atomicAdd(&B.tickets[2 + grp], 1u);
-        is_last = (tk == static_cast<unsigned>(gn - 1));
+        const unsigned tk = atomicAdd(&B.tickets[9], 1u);
+        bool ok = true;
+        if (tk == gridDim.x - 1) {
+            B.tickets[9] = 0u;
+            __threadfence();
+            atomicAdd(&B.tickets[10], 1u);
+        } else {
+            const uint64_t t0 = global_timer_ns();
+            while (*gen_p == gen) {
+                if (global_timer_ns() - t0 > kGridWaitLimitNs) {
+                    atomicExch(B.err, kDevErrTimeout);
+                    ok = false;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        is_last = ok ? 1 : 0;
     }
     __syncthreads();
     if (!is_last) return;
-    __threadfence();
-    if (threadIdx.x == 0) {
-        float2 bs[kCuGroup];
+
+    // 4. every block combines the blocks' statistics the same way (same data, same order):
+    //    rho = min_b rho_b, F_b = exp(-(rho_b - rho) / lambda), eta = sum_b F_b eta_b
+    const int nb = gridDim.x;
+    if (wid == 0) {
+        float2 bs[kCuMaxBlocks / 32];
         float m = inf;
 #pragma unroll
-        for (int j = 0; j < kCuGroup; ++j) {
-            bs[j] = (j < gn) ? __ldcg(&B.bstat[gb0 + j]) : make_float2(inf, 0.f);
+        for (int j = 0; j < kCuMaxBlocks / 32; ++j) {
+            const int b = lane + 32 * j;
+            bs[j] = (b < nb) ? __ldcg(&B.bstat[b]) : make_float2(inf, 0.f);
             m = fminf(m, bs[j].x);
         }
+        const float rho = warp_min(m);
         float e = 0.f;
 #pragma unroll
-        for (int j = 0; j < kCuGroup; ++j) {
-            const float f = (j < gn) ? expf(-(bs[j].x - m) * inv_lam) : 0.f;
-            sF[j] = f;
+        for (int j = 0; j < kCuMaxBlocks / 32; ++j) {
+            const int b = lane + 32 * j;
+            const float f = (b < nb) ? expf(-(bs[j].x - rho) * inv_lam) : 0.f;
+            if (b < nb) sF[b] = f;
             e += f * bs[j].y;
-            if (j < gn) B.bfac[gb0 + j] = f;
         }
-        B.gstat[grp] = make_float2(m, e);
-        B.tickets[2 + grp] = 0u;
-    }
-    __syncthreads();
-    for (int h = threadIdx.x; h < H; h += kCuThreads) {
-        float4 sb[kCuGroup];
-#pragma unroll
-        for (int j = 0; j < kCuGroup; ++j)
-            sb[j] = (j < gn) ? __ldcg(B.upart + static_cast<size_t>(gb0 + j) * H + h) : make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int j = 0; j < kCuGroup; ++j) t = f4_fma(sF[j], sb[j], t);
-        B.gpart[static_cast<size_t>(grp) * H + h] = t;
-    }
-
-    // 4. the last group combiner combines the groups and advances the controller
-    __syncthreads();
-    const int ng = (nb + kCuGroup - 1) / kCuGroup;
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned tk = atomicAdd(&B.tickets[1], 1u);
-        is_last = (tk == static_cast<unsigned>(ng - 1));
-    }
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    if (threadIdx.x == 0) {
-        float2 gs[kCuMaxGroups];
-        float m = inf;
-#pragma unroll
-        for (int j = 0; j < kCuMaxGroups; ++j) {
-            gs[j] = (j < ng) ? __ldcg(&B.gstat[j]) : make_float2(inf, 0.f);
-            m = fminf(m, gs[j].x);
-        }
-        float e = 0.f;
-#pragma unroll
-        for (int j = 0; j < kCuMaxGroups; ++j) {
-            const float f = (j < ng) ? expf(-(gs[j].x - m) * inv_lam) : 0.f;
-            sF[j] = f;
-            e += f * gs[j].y;
-        }
-        s_rho = m;
-        s_eta = e;
-    }
-    __syncthreads();
-    if (threadIdx.x < kCuMaxGroups) sF[threadIdx.x] = sF[threadIdx.x] / s_eta;
-    __syncthreads();
-    for (int h = threadIdx.x; h < H; h += kCuThreads) {
-        float4 sg[kCuMaxGroups];
-#pragma unroll
-        for (int j = 0; j < kCuMaxGroups; ++j)
-            sg[j] = (j < ng) ? __ldcg(B.gpart + static_cast<size_t>(j) * H + h) : make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int j = 0; j < kCuMaxGroups; ++j) t = f4_fma(sF[j], sg[j], t);
-        B.unew[h] = t;
-        if (B.out_U) B.out_U[h] = t;
-    }
-    __syncthreads();
-    if (wid == 0) {
-        // warp 0: shift the warm start, apply U*_new[0] to the device-resident state
-        const float uh = P.mass * P.gravity;
-        for (int i = lane; i < H; i += 32)
-            B.nominal[i] = (i + 1 < H) ? B.unew[i + 1] : make_float4(uh, 0.f, 0.f, 0.f);
+        const float eta = warp_sum(e);
         if (lane == 0) {
-            B.stats[0] = s_rho;
-            B.stats[1] = s_eta;
-            const float4 u0 = B.unew[0];
-            float* s = B.state;
-            Vec3 p = v3(s[0], s[1], s[2]);
-            Vec3 v = v3(s[3], s[4], s[5]);
-            Quat q{s[6], s[7], s[8], s[9]};
-            rk4_step(P, p, v, q, u0.x, v3(u0.y, u0.z, u0.w));
-            s[0] = p.x; s[1] = p.y; s[2] = p.z;
-            s[3] = v.x; s[4] = v.y; s[5] = v.z;
-            s[6] = q.w; s[7] = q.x; s[8] = q.y; s[9] = q.z;
-            s[10] = u0.y; s[11] = u0.z; s[12] = u0.w;
-            const uint32_t lo = B.step[0] + 1u;
-            B.step[0] = lo;
-            if (lo == 0u) B.step[1] += 1u;
-            B.tickets[1] = 0u;
+            s_rho = rho;
+            s_eta = eta;
         }
-    } else {
-        // warps 1..: w_k = e_k f_b F_g / eta, one update block (R rollouts) per warp pass
-        for (int b0 = wid - 1; b0 < nb; b0 += (kCuWarps - 1) * 4) {
-            float fb[4], wv[4][8];
+    }
+    __syncthreads();
+    const float eta = s_eta;
+    // this block's weights: w_k = e_k F_b / eta
+    const float fw = sF[blockIdx.x] / eta;
+    for (int i = threadIdx.x; i < nk; i += kCuThreads) {
+        const float wk = sE[i] * fw;
+        B.w[k0 + i] = wk;
+        if (B.out_w) B.out_w[k0 + i] = wk;
+    }
+    // U*_new[h] for h = blockIdx.x, blockIdx.x + nb, ...: thread t < nb loads block t's partial,
+    // then a fixed-order tree in shared memory
+    float4* sU = reinterpret_cast<float4*>(sRed);
+    const float uh = P.mass * P.gravity;
+    for (int h = blockIdx.x; h < H; h += nb) {
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (threadIdx.x < nb) {
+            const float4 sb = __ldcg(B.upart + static_cast<size_t>(threadIdx.x) * H + h);
+            const float f = sF[threadIdx.x] / eta;
+            t = make_float4(f * sb.x, f * sb.y, f * sb.z, f * sb.w);
+        }
+        sU[threadIdx.x] = t;
+        __syncthreads();
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int b = b0 + u * (kCuWarps - 1);
-                fb[u] = (b < nb) ? __ldcg(B.bfac + b) * sF[b / kCuGroup] : 0.f;
-#pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const int kk = b * R + t * 32 + lane;
-                    wv[u][t] = (b < nb && t * 32 < R && kk < K) ? __ldcg(B.w + kk) : 0.f;
-                }
+        for (int o = kCuThreads / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) {
+                const float4 a = sU[threadIdx.x], c = sU[threadIdx.x + o];
+                sU[threadIdx.x] = make_float4(a.x + c.x, a.y + c.y, a.z + c.z, a.w + c.w);
             }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int b = b0 + u * (kCuWarps - 1);
-#pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const int kk = b * R + t * 32 + lane;
-                    if (b < nb && t * 32 < R && kk < K) {
-                        const float wk = wv[u][t] * fb[u];
-                        B.w[kk] = wk;
-                        if (B.out_w) B.out_w[kk] = wk;
-                    }
-                }
-                // blocks of more than 256 rollouts (K > 32768)
-                for (int kk = b * R + 256 + lane; b < nb && kk < min(K, (b + 1) * R); kk += 32) {
-                    const float wk = __ldcg(B.w + kk) * fb[u];
-                    B.w[kk] = wk;
-                    if (B.out_w) B.out_w[kk] = wk;
-                }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const float4 u = sU[0];
+            B.unew[h] = u;
+            if (B.out_U) B.out_U[h] = u;
+            if (h >= 1) B.nominal[h - 1] = u;                     // the warm start, shifted by one
+            if (h == H - 1) B.nominal[H - 1] = make_float4(uh, 0.f, 0.f, 0.f);
+            if (h == 0) {
+                // apply U*_new[0] to the device-resident state
+                B.stats[0] = s_rho;
+                B.stats[1] = eta;
+                float* st = B.state;
+                Vec3 p = v3(st[0], st[1], st[2]);
+                Vec3 v = v3(st[3], st[4], st[5]);
+                Quat q{st[6], st[7], st[8], st[9]};
+                rk4_step(P, p, v, q, u.x, v3(u.y, u.z, u.w));
+                st[0] = p.x; st[1] = p.y; st[2] = p.z;
+                st[3] = v.x; st[4] = v.y; st[5] = v.z;
+                st[6] = q.w; st[7] = q.x; st[8] = q.y; st[9] = q.z;
+                st[10] = u.y; st[11] = u.z; st[12] = u.w;
+                const uint32_t lo = B.step[0] + 1u;
+                B.step[0] = lo;
+                if (lo == 0u) B.step[1] += 1u;
             }
         }
+        __syncthreads();
     }
 }
-
 
 // ------------------------------------------------------------------ per-gate first-layer bias
 // The Gate-SDF decoder's first layer sees [p, z]; z is fixed per gate, so its
@@ -598,7 +563,7 @@ int update_blocks(int K) {
     return (K + R - 1) / R;
 }
 
-int update_groups(int K) { return (update_blocks(K) + kCuGroup - 1) / kCuGroup; }
+
 
 cudaError_t configure_cost_update() {
     // R floats of dynamic shared memory: up to MPPI_MAX_K / kCuMaxBlocks
@@ -607,9 +572,19 @@ cudaError_t configure_cost_update() {
 }
 
 cudaError_t launch_cost_update(const StepParams& P, const StepBuffers& B, int mlp, cudaStream_t s) {
+    // a cooperative launch: the blocks meet at a grid barrier, so all of them must be resident
     const int R = update_rollouts_per_block(P.K);
-    return launch_dependent(P.pdl != 0, cost_update_kernel, dim3((P.K + R - 1) / R), dim3(kCuThreads),
-                            sizeof(float) * R, s, P, B, mlp, R);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((P.K + R - 1) / R);
+    cfg.blockDim = dim3(kCuThreads);
+    cfg.dynamicSmemBytes = sizeof(float) * R;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, cost_update_kernel, P, B, mlp, R);
 }
 
 cudaError_t launch_first_layer_bias(const float* W1, const float* b1, const float* latents, int G, float* b1p,

@@ -63,8 +63,6 @@ cudaError_t launch_cost_update(const StepParams& P, const StepBuffers& B, int ml
 cudaError_t configure_cost_update();
 // blocks of the update kernel for K rollouts (sizes B.upart and B.bstat)
 int update_blocks(int K);
-// groups of the update kernel's two-level combine (sizes B.gpart and B.gstat)
-int update_groups(int K);
 // per-gate first-layer bias b1'_g = W1[:, 3:67] z_g + b1
 cudaError_t launch_first_layer_bias(const float* W1, const float* b1, const float* latents, int G, float* b1p,
                                     cudaStream_t s);

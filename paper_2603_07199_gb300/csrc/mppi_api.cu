@@ -273,12 +273,20 @@ int check_ready(mppi_ctx* c) {
     return MPPI_OK;
 }
 
+// After a device-side timeout: clear the error word and the barrier counters (a timed-out
+// grid barrier leaves its arrival count behind).
+cudaError_t clear_device_error(mppi_ctx* c) {
+    cudaError_t e = cudaMemsetAsync(c->B.err, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->B.tickets, 0, 32 * sizeof(unsigned), c->stream);
+    return e;
+}
+
 int read_err_word(mppi_ctx* c) {
     int e = 0;
     CUDA_TRY(c, cudaMemcpyAsync(&e, c->B.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     if (e != 0) {
-        CUDA_TRY(c, cudaMemsetAsync(c->B.err, 0, sizeof(int), c->stream));
+        CUDA_TRY(c, clear_device_error(c));
         CUDA_TRY(c, cudaStreamSynchronize(c->stream));
         return fail(c, MPPI_E_TIMEOUT, "a device-side wait timed out (error word %d)", e);
     }
@@ -388,9 +396,6 @@ int mppi_create(const mppi_config* cfg, void* cuda_stream, mppi_ctx** out) {
     rc = rc ? rc : dev_alloc(c, &B.unew, H);
     rc = rc ? rc : dev_alloc(c, &B.upart, static_cast<size_t>(nub) * H);
     rc = rc ? rc : dev_alloc(c, &B.bstat, nub);
-    rc = rc ? rc : dev_alloc(c, &B.bfac, nub);
-    rc = rc ? rc : dev_alloc(c, &B.gpart, static_cast<size_t>(update_groups(K)) * H);
-    rc = rc ? rc : dev_alloc(c, &B.gstat, update_groups(K));
     rc = rc ? rc : dev_alloc(c, &B.stats, 4);
     rc = rc ? rc : dev_alloc(c, &B.tickets, 32);
     rc = rc ? rc : dev_alloc(c, &B.err, 1);
@@ -620,7 +625,7 @@ int mppi_step(mppi_ctx* c, const float* state, const float* gate_poses, const fl
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     ++c->step_count;
     if (*herr != 0) {
-        CUDA_TRY(c, cudaMemsetAsync(c->B.err, 0, sizeof(int), c->stream));
+        CUDA_TRY(c, clear_device_error(c));
         CUDA_TRY(c, cudaStreamSynchronize(c->stream));
         return fail(c, MPPI_E_TIMEOUT, "a device-side wait timed out (error word %d)", *herr);
     }
@@ -826,7 +831,7 @@ int ctx_poll_host_step(mppi_ctx* c, float* new_controls) {
     const int H = c->cfg.H;
     const int* herr = reinterpret_cast<const int*>(c->h_out + H * 4 + 2 * c->cfg.K);
     if (*herr != 0) {
-        CUDA_TRY(c, cudaMemsetAsync(c->B.err, 0, sizeof(int), c->stream));
+        CUDA_TRY(c, clear_device_error(c));
         return fail(c, MPPI_E_TIMEOUT, "a device-side wait timed out (error word %d)", *herr);
     }
     std::memcpy(new_controls, c->h_out, static_cast<size_t>(H) * 4 * sizeof(float));
@@ -856,9 +861,8 @@ int ctx_restore(mppi_ctx* c, const float* nominal, const float* state, uint64_t 
 size_t ctx_device_bytes(const mppi_config& g) {
     const size_t K = g.K, H = g.H, MG = g.max_gates;
     const size_t nub = static_cast<size_t>(update_blocks(g.K));
-    const size_t nug = static_cast<size_t>(update_groups(g.K));
     const size_t floats = 16 + 4 * H + 2 + MG * 8 + MG * kHidden + 4 * K * H * 2 + 3 * K + K * H + 2 * K + 4 * H +
-                          nub * (4 * H + 3) + nug * (4 * H + 2) + 4 + 32 + 1 + MG * kLatent;
+                          nub * (4 * H + 2) + 4 + 32 + 1 + MG * kLatent;
     const size_t weights = sizeof(float) * (kHidden * (3 + kLatent) + kHidden + 3 * (kHidden * kHidden + kHidden) + kHidden) +
                            3 * kHidden * kHidden * (2 + 2 + 1) + kHidden * 16 * 2;
     return floats * sizeof(float) + weights;
