@@ -83,6 +83,13 @@ extern "C" {
  *   gate_inner_half, gate_outer_half, gate_half_depth   frame geometry (m)
  *   softplus_beta                     sharpness of the MLP's softplus
  *   seed, drone_id                    Philox key and the counter's 4th word
+ *   cost_mode                         MPPI_COST_CONFIGURED (w_col, w_u and the progress
+ *                                     along the target gate's normal) or MPPI_COST_PAPER
+ *   q_gate, q_vis, q_sdf              weights of Eq. 9 (MPPI_COST_PAPER): waypoint progress
+ *                                     (Eq. 6), perception alignment (Eq. 7) and the linear SDF
+ *                                     hinge max(0, d_safe - s) (Eq. 8) on the target gate
+ *   guide_tan_alpha                   tan of the cone angle of the guidance SDF (Eq. 2), the
+ *                                     analytic SDF of MPPI_COST_PAPER
  */
 typedef struct mppi_config {
     int32_t K;
@@ -97,8 +104,15 @@ typedef struct mppi_config {
     float softplus_beta;
     uint64_t seed;
     uint32_t drone_id;
-    uint32_t reserved;
+    int32_t cost_mode;
+    float q_gate, q_vis, q_sdf;
+    float guide_tan_alpha;
 } mppi_config;
+
+/* Cost forms (mppi_config.cost_mode). */
+#define MPPI_COST_CONFIGURED 0  /* w_col max(0, d_safe - s)^2 + progress along the target gate's normal
+                                   + w_u |u - u_hover|^2; s = min over gates */
+#define MPPI_COST_PAPER      1  /* Q_gate J_gate + Q_vis J_vis + Q_sdf J_sdf (Eq. 6-9) on the target gate */
 
 typedef struct mppi_ctx mppi_ctx;
 
@@ -194,7 +208,7 @@ uint64_t mppi_get_step_counter(const mppi_ctx* ctx);
  * be at least the buffer's size.  Synchronous.
  *   MPPI_BUF_NOISE      K x H x 4  delta u, layout [k][h][4] (h fastest)
  *   MPPI_BUF_POSITIONS  K x H x 4  rollout positions p_1..p_H, [k][h][x,y,z,0]
- *   MPPI_BUF_COST_PARTS 3 x K      [J_col; J_prog; J_ctl]
+ *   MPPI_BUF_COST_PARTS 3 x K      [J_col; J_prog; J_ctl] (MPPI_COST_PAPER: [Q_sdf J_sdf; Q_gate J_gate; Q_vis J_vis])
  *   MPPI_BUF_SDF        K x H      s(p_h) = min over gates of the SDF at every rollout state, [k][h] (MLP modes)
  *   MPPI_BUF_WEIGHTS    K
  *   MPPI_BUF_COSTS      K

@@ -93,10 +93,10 @@ def pack_state(p, v, q, w):
     return np.concatenate([p, v, q, w], axis=-1)
 
 
-def rollout(state, U, dt, mass, gravity):
+def rollout_states(state, U, dt, mass, gravity):
     """Roll out command sequences U [K, H, 4] from one state [13].
 
-    Returns positions [K, H, 3] of the post-step states p_1 .. p_H.
+    Returns (positions [K, H, 3], attitudes [K, H, 4]) of the post-step states 1 .. H.
     """
     K, H, _ = U.shape
     p0, v0, q0, _ = unpack_state(state)
@@ -104,10 +104,25 @@ def rollout(state, U, dt, mass, gravity):
     v = np.broadcast_to(v0, (K, 3)).copy()
     q = np.broadcast_to(q0, (K, 4)).copy()
     pos = np.empty((K, H, 3))
+    att = np.empty((K, H, 4))
     for h in range(H):
         p, v, q, _ = rk4_step(p, v, q, U[:, h, :], dt, mass, gravity)
         pos[:, h, :] = p
-    return pos
+        att[:, h, :] = q
+    return pos, att
+
+
+def rollout(state, U, dt, mass, gravity):
+    """Positions [K, H, 3] of the post-step states p_1 .. p_H (see rollout_states)."""
+    return rollout_states(state, U, dt, mass, gravity)[0]
+
+
+def yaw_angle(q):
+    """Heading of the body x axis about world z: atan2 of the first column of R(q)
+    projected on the horizontal plane, (2 (xy + wz), 1 - 2 (y^2 + z^2))."""
+    q = np.asarray(q, dtype=np.float64)
+    w, x, y, z = q[..., 0], q[..., 1], q[..., 2], q[..., 3]
+    return np.arctan2(2.0 * (x * y + w * z), 1.0 - 2.0 * (y * y + z * z))
 
 
 def plant_step(state, u, dt, mass, gravity):

@@ -20,6 +20,9 @@ Per control step (Sec. IV-A, Eq. 5):
        J_ctl  = w_u * sum_{h=0..H-1} |U^m_h - u_hover|^2,  u_hover = (m g, 0, 0, 0);
 4. weights w_m = exp(-J_m / lambda) / sum_i exp(-J_i / lambda), evaluated as
    exp(-(J_m - rho) / lambda) / eta with rho = min J (Eq. 5);
+   or, with ``cost_mode = "paper"``, the paper's own terms (``paper_costs``, Eq. 6-9:
+   waypoint progress, perception alignment, linear SDF hinge on the target gate's
+   guidance SDF of Eq. 2 or its network);
 5. U*_new = sum_m w_m U^m (Eq. 5; U^m the clipped sequences that were rolled out);
 6. receding horizon: apply U*_new[0] to the plant for one step and start the
    next cycle from U*_new shifted left by one with u_hover appended.
@@ -53,6 +56,14 @@ class Params:
     w_u: float = 1e-3
     seed: int = 0
     drone_id: int = 0
+    # "configured": w_col max(0, d_safe - s)^2 + progress along the gate normal + control cost;
+    # "paper": Q_gate J_gate + Q_vis J_vis + Q_sdf J_sdf (Eq. 6-9) on the target gate's
+    # guidance SDF (Eq. 2, analytic) or its Gate-SDF network
+    cost_mode: str = "configured"
+    q_gate: float = 1.0
+    q_vis: float = 1.0
+    q_sdf: float = 10.0
+    guide_tan_alpha: float = 0.5773502691896257      # tan(30 deg), the cone angle of Eq. 2
 
     def u_hover(self):
         return np.array([self.mass * self.gravity, 0.0, 0.0, 0.0])
@@ -116,6 +127,45 @@ def rollout_costs(state, U, positions, poses, prm, latents=None, layers=None):
     return dict(sdf=s, J_col=J_col, J_prog=J_prog, J_ctl=J_ctl, J=J_col + J_prog + J_ctl)
 
 
+def paper_costs(state, positions, attitudes, poses, prm, latents=None, layers=None):
+    """The paper's task costs (Sec. IV-B) for every rollout, at the post-step states 1 .. H:
+
+    J_gate = sum_k (|p_{k+1} - p_wp|^2 - |p_k - p_wp|^2)            (Eq. 6)
+    J_vis  = sum_k (1 - cos(psi_k - psi_gate,k))                      (Eq. 7)
+    J_sdf  = sum_k max(0, d_safe - s_k)                                (Eq. 8)
+    J      = Q_gate J_gate + Q_vis J_vis + Q_sdf J_sdf                 (Eq. 9)
+
+    The waypoint p_wp is the target gate's centre; psi_k is the yaw of the rollout's
+    attitude, psi_gate,k the bearing from p_k to p_wp in the horizontal plane; s_k is the
+    guidance SDF of Eq. 2 of the target gate (c = the opening's half-width, cone angle
+    atan(guide_tan_alpha)) or, with ``layers``, the Gate-SDF network at the target gate.
+    Returns the three weighted terms, their sum and s [K, H].
+    """
+    K, H, _ = positions.shape
+    poses = np.asarray(poses, dtype=np.float64).reshape(-1, 7)
+    g = target_gate(state, poses)
+    if g < 0:
+        z = np.zeros(K)
+        return dict(sdf=np.full((K, H), np.inf), J_col=z, J_prog=z.copy(), J_ctl=z.copy(), J=z.copy())
+    wp = poses[g, 0:3]
+    p0 = np.asarray(state, dtype=np.float64)[0:3]
+    p_all = np.concatenate([np.broadcast_to(p0, (K, 1, 3)), positions], axis=1)      # p_0 .. p_H
+    d2 = np.sum((p_all - wp) ** 2, axis=-1)
+    J_gate = np.sum(d2[:, 1:] - d2[:, :-1], axis=1)
+    psi = dynamics.yaw_angle(attitudes)
+    psi_gate = np.arctan2(wp[1] - positions[..., 1], wp[0] - positions[..., 0])
+    J_vis = np.sum(1.0 - np.cos(psi - psi_gate), axis=1)
+    pg = gate_sdf.to_gate_frame(positions.reshape(-1, 3), poses[g])
+    if layers is None:
+        s = gate_sdf.guide_sdf(pg, c=gate_sdf.GATE_INNER_HALF, alpha=np.arctan(prm.guide_tan_alpha))
+    else:
+        s = mlp.sdf(layers, pg, latents[g])
+    s = s.reshape(K, H)
+    J_sdf = np.sum(np.maximum(0.0, prm.d_safe - s), axis=1)
+    parts = dict(J_col=prm.q_sdf * J_sdf, J_prog=prm.q_gate * J_gate, J_ctl=prm.q_vis * J_vis)
+    return dict(sdf=s, J=parts["J_col"] + parts["J_prog"] + parts["J_ctl"], **parts)
+
+
 def softmax_weights(J, lam):
     """Eq. 5 weights with max-subtraction: rho = min J."""
     J = np.asarray(J, dtype=np.float64)
@@ -141,8 +191,11 @@ def mppi_step(state, nominal, poses, prm, step, latents=None, layers=None):
     delta = noise.control_noise(prm.K, prm.H, prm.seed, step, prm.drone_id,
                                 prm.sigma_thrust, prm.sigma_rate)
     U = clip_controls(nominal[None, :, :] + delta, prm)
-    positions = dynamics.rollout(state, U, prm.dt, prm.mass, prm.gravity)
-    costs = rollout_costs(state, U, positions, poses, prm, latents, layers)
+    positions, attitudes = dynamics.rollout_states(state, U, prm.dt, prm.mass, prm.gravity)
+    if prm.cost_mode == "paper":
+        costs = paper_costs(state, positions, attitudes, poses, prm, latents, layers)
+    else:
+        costs = rollout_costs(state, U, positions, poses, prm, latents, layers)
     w = softmax_weights(costs["J"], prm.lam)
     U_new = weighted_update(w, U)
     out = dict(delta=delta, U=U, positions=positions, weights=w, U_new=U_new)

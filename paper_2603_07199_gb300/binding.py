@@ -27,6 +27,9 @@ MPPI_SDF_MLP_BF16 = 2
 MPPI_SDF_MLP_FP16 = 3
 MPPI_SDF_MLP_FP8 = 4
 
+MPPI_COST_CONFIGURED = 0
+MPPI_COST_PAPER = 1
+
 MPPI_BUF_NOISE = 0
 MPPI_BUF_POSITIONS = 1
 MPPI_BUF_COST_PARTS = 2
@@ -68,7 +71,9 @@ class MppiConfig(ctypes.Structure):
         ("w_col", ctypes.c_float), ("d_safe", ctypes.c_float), ("w_u", ctypes.c_float),
         ("gate_inner_half", ctypes.c_float), ("gate_outer_half", ctypes.c_float), ("gate_half_depth", ctypes.c_float),
         ("softplus_beta", ctypes.c_float),
-        ("seed", ctypes.c_uint64), ("drone_id", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+        ("seed", ctypes.c_uint64), ("drone_id", ctypes.c_uint32), ("cost_mode", ctypes.c_int32),
+        ("q_gate", ctypes.c_float), ("q_vis", ctypes.c_float), ("q_sdf", ctypes.c_float),
+        ("guide_tan_alpha", ctypes.c_float),
     ]
 
 

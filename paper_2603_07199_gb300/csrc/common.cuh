@@ -27,6 +27,8 @@ struct StepParams {
     float beta;
     uint32_t key0, key1, drone;
     int pdl;               // host side: launch kernels as programmatic dependents
+    int paper;             // cost form of Eq. 6-9 on the target gate (else the configured form)
+    float q_gate, q_vis, q_sdf, tan_alpha;
 };
 
 // Device buffers of one controller.
@@ -233,6 +235,46 @@ __device__ __forceinline__ Vec3 to_gate(const float* pose, Vec3 p) {
 __device__ __forceinline__ float hinge_sq(float s, float d_safe) {
     const float e = fmaxf(d_safe - s, 0.f);
     return e * e;
+}
+
+// The collision / safety stage cost of one state: configured w_col-free form max(0, d - s)^2,
+// or the paper's linear hinge max(0, d - s) (Eq. 8).
+__device__ __forceinline__ float stage_hinge(float s, float d_safe, int paper) {
+    const float e = fmaxf(d_safe - s, 0.f);
+    return paper ? e : e * e;
+}
+
+// Index of the first gate whose plane the position p has not crossed (n_g . (p - t_g) < 0),
+// else the last gate; -1 without gates.  poses: [G][8] = (t, q, pad); n_out: its normal.
+__device__ __forceinline__ int target_gate(const float* poses, int G, Vec3 p, Vec3* n_out) {
+    for (int g = 0; g < G; ++g) {
+        const float* ps = poses + 8 * g;
+        const Vec3 n = quat_x_axis(Quat{ps[3], ps[4], ps[5], ps[6]});
+        const float side = n.x * (p.x - ps[0]) + n.y * (p.y - ps[1]) + n.z * (p.z - ps[2]);
+        if (side < 0.f || g == G - 1) {
+            *n_out = n;
+            return g;
+        }
+    }
+    *n_out = v3(0.f, 0.f, 0.f);
+    return -1;
+}
+
+// Eq. 2: guidance SDF c + |x| tan(alpha) - max(|y|, |z|) of a gate-frame point.
+__device__ __forceinline__ float guide_sdf(Vec3 pg, float c, float tan_alpha) {
+    return c + fabsf(pg.x) * tan_alpha - fmaxf(fabsf(pg.y), fabsf(pg.z));
+}
+
+// 1 - cos(psi - psi_gate) of Eq. 7 for attitude q at position p and waypoint wp: psi is the
+// heading of the body x axis, (1 - 2 (y^2 + z^2), 2 (xy + wz)), psi_gate the bearing of
+// wp - p in the horizontal plane; a zero vector has heading 0 (the atan2(0, 0) convention).
+__device__ __forceinline__ float misalignment(const Quat& q, Vec3 p, Vec3 wp) {
+    float hx = 1.f - 2.f * (q.y * q.y + q.z * q.z), hy = 2.f * (q.x * q.y + q.w * q.z);
+    float lx = wp.x - p.x, ly = wp.y - p.y;
+    float hn = hx * hx + hy * hy, ln = lx * lx + ly * ly;
+    if (hn == 0.f) { hx = 1.f; hy = 0.f; hn = 1.f; }
+    if (ln == 0.f) { lx = 1.f; ly = 0.f; ln = 1.f; }
+    return 1.f - (hx * lx + hy * ly) * rsqrtf(hn * ln);
 }
 
 }  // namespace mppi

@@ -49,13 +49,21 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_fp32_kernel(StepParams P,
 
     const float beta = P.beta, inv_beta = 1.0f / P.beta;
     const int tn = tid & 15, tr = tid >> 4;
+    // gates queried: all (min over gates), or the target gate only (the paper's form)
+    int g_lo = 0, g_hi = G;
+    if (P.paper) {
+        Vec3 n;
+        const int t = target_gate(sPose, G, v3(B.state[0], B.state[1], B.state[2]), &n);
+        g_lo = t < 0 ? 0 : t;
+        g_hi = t < 0 ? 0 : t + 1;
+    }
     // tile = 128 consecutive rollout states of the [K][H] position array
     const int n_rows = P.K * P.H;
     const int n_items = (n_rows + kTileRows - 1) / kTileRows;
 
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         if (tid < kTileRows) sMin[tid] = __int_as_float(0x7f800000);
-        for (int g = 0; g < G; ++g) {
+        for (int g = g_lo; g < g_hi; ++g) {
             if (tid < kTileRows) {
                 const float4 p = B.pos[min(item * kTileRows + tid, n_rows - 1)];
                 const Vec3 pg = to_gate(sPose + 8 * g, v3(p.x, p.y, p.z));

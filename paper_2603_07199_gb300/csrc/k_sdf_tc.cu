@@ -33,10 +33,11 @@ namespace mppi {
 namespace {
 
 constexpr int kGroups = 3;                          // tile groups (tiles in flight per CTA)
-constexpr int kGroupWarps = 8;
+constexpr int kGroupWarps = 8;                      // 4 (one warp per TMEM lane quadrant) or 8 (two)
 constexpr int kGroupThreads = kGroupWarps * 32;
+constexpr int kHalves = kGroupWarps / 4;            // column slices per row
 constexpr int kThreads = kGroups * kGroupThreads;
-constexpr int kHalf = kHidden / 2;
+constexpr int kHalf = kHidden / kHalves;            // accumulator columns per thread
 constexpr uint32_t kTileBytes = kHidden * kHidden * 2;     // one 128 x 128 BF16 operand
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kIdescFull = tc::idesc_bf16_f32(128, 128);
@@ -290,6 +291,14 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
     pdl_wait();
 
     // tile i (128 consecutive rows of the [K][H] state array) goes to group slot i mod (3 gridDim)
+    // gates queried: all (min over gates), or the target gate only (the paper's form)
+    int g_lo = 0, g_hi = G;
+    if (P.paper) {
+        Vec3 n;
+        const int t = target_gate(&S.pose[0][0], G, v3(B.state[0], B.state[1], B.state[2]), &n);
+        g_lo = t < 0 ? 0 : t;
+        g_hi = t < 0 ? 0 : t + 1;
+    }
     const int n_rows = P.K * P.H;
     const int n_tiles = (n_rows + kTileRows - 1) / kTileRows;
     const int nslots = gridDim.x * kGroups;
@@ -350,7 +359,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
         const int r = row0 + row;
         const float4 p = B.pos[min(r, n_rows - 1)];
         float smin = __int_as_float(0x7f800000);
-        for (int g = 0; g < G && ok; ++g) {
+        for (int g = g_lo; g < g_hi && ok; ++g) {
             // layer-1 A operand (K = 16): the gate-frame point split p = hi + lo in BF16,
             // laid out against the weight split [W_hi, W_hi, W_lo] so the MMA sums
             // hi.W_hi + lo.W_hi + hi.W_lo (relative error ~2^-16); the latent's part
@@ -461,12 +470,16 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                     tc::named_barrier(bar_id, kGroupThreads);
                     if (leader) issue(l + 1);
                 } else {
-                    // the two column halves of a row meet through shared memory
                     const float2 sp2 = upk(s2);
                     const float sh = sp2.x + sp2.y;
-                    if (half == 1) S.part[grp][row] = sh;
-                    tc::named_barrier(bar_id, kGroupThreads);
-                    if (half == 0) smin = fminf(smin, sh + S.part[grp][row] + W.b5);
+                    if constexpr (kHalves == 2) {
+                        // the two column halves of a row meet through shared memory
+                        if (half == 1) S.part[grp][row] = sh;
+                        tc::named_barrier(bar_id, kGroupThreads);
+                        if (half == 0) smin = fminf(smin, sh + S.part[grp][row] + W.b5);
+                    } else {
+                        smin = fminf(smin, sh + W.b5);
+                    }
                 }
             }
         }

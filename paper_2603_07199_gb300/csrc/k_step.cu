@@ -105,23 +105,19 @@ __global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, 
     Vec3 vc = v3(B.state[3], B.state[4], B.state[5]);
     Quat qc{B.state[6], B.state[7], B.state[8], B.state[9]};
 
-    // target gate: the first gate whose plane the current position has not crossed
-    int tgt = -1;
-    Vec3 n_tgt = v3(0.f, 0.f, 0.f);
-    for (int g = 0; g < P.G; ++g) {
-        const float* ps = sPose + 8 * g;
-        const Vec3 n = quat_x_axis(Quat{ps[3], ps[4], ps[5], ps[6]});
-        const float side = n.x * (p0.x - ps[0]) + n.y * (p0.y - ps[1]) + n.z * (p0.z - ps[2]);
-        if (tgt < 0 && side < 0.f) { tgt = g; n_tgt = n; }
-        if (tgt < 0 && g == P.G - 1) { tgt = g; n_tgt = n; }
-    }
+    // target gate: the first gate whose plane the current position has not crossed; its
+    // centre is the waypoint of the paper's cost form
+    Vec3 n_tgt;
+    const int tgt = target_gate(sPose, P.G, p0, &n_tgt);
+    const float* pose_t = sPose + 8 * (tgt < 0 ? 0 : tgt);
+    const Vec3 wp = v3(pose_t[0], pose_t[1], pose_t[2]);
 
     const float uh = P.mass * P.gravity;
     const float dt = P.dt;
     const float c3 = dt * dt * (1.f / 6.f), c6 = dt * (1.f / 6.f);
     const float b2 = 0.25f * dt;
     const float inv_m = 1.f / P.mass;
-    float jctl = 0.f, jcol = 0.f;
+    float jctl = 0.f, jcol = 0.f, jvis = 0.f;
     float4* noise_k = B.noise + static_cast<size_t>(k) * H;
     float4* pos_k = B.pos + static_cast<size_t>(k) * H;
     for (int c0 = 0; c0 < H; c0 += 32 * kSteps) {
@@ -159,6 +155,7 @@ __global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, 
 
         // pass B: stage accelerations; velocity and position offsets within the segment
         Vec3 L[kSteps];
+        Quat Qa[kSteps];                                 // attitude after each step (paper form)
         Vec3 V = v3(0.f, 0.f, 0.f);
         Vec3 Lacc = v3(0.f, 0.f, 0.f);
 #pragma unroll
@@ -187,7 +184,8 @@ __global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, 
                 V = v3(V.x + c6 * (tm * s6.x), V.y + c6 * (tm * s6.y), V.z + (c6 * (tm * s6.z) - dt * P.gravity));
             }
             L[j] = Lacc;
-            if (j + 1 < kSteps) q = qnormalize(qmul(q, N[j]));
+            if (P.paper || j + 1 < kSteps) q = qnormalize(qmul(q, N[j]));
+            Qa[j] = q;
         }
         // segment start velocities and positions: exclusive scans of the segments' totals
         const Vec3 Sv = warp_scan_add(V, lane);
@@ -209,7 +207,12 @@ __global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, 
                 const float tj = dt * static_cast<float>(j + 1);
                 const Vec3 p = v3(ps.x + tj * vs.x + L[j].x, ps.y + tj * vs.y + L[j].y, ps.z + tj * vs.z + L[j].z);
                 pos_k[h] = make_float4(p.x, p.y, p.z, 0.f);
-                if (analytic) {
+                if (P.paper) {
+                    if (tgt >= 0) {
+                        jvis += misalignment(Qa[j], p, wp);
+                        if (analytic) jcol += fmaxf(P.d_safe - guide_sdf(to_gate(pose_t, p), P.a_in, P.tan_alpha), 0.f);
+                    }
+                } else if (analytic) {
                     float smin = __int_as_float(0x7f800000);
                     for (int g = 0; g < P.G; ++g) {
                         const Vec3 pg = to_gate(sPose + 8 * g, p);
@@ -228,19 +231,32 @@ __global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, 
     }
     jctl = warp_sum(jctl);
     jcol = warp_sum(jcol);
+    jvis = warp_sum(jvis);
     if (lane == 0) {
-        const float jprog =
-            (tgt >= 0) ? -(n_tgt.x * (pc.x - p0.x) + n_tgt.y * (pc.y - p0.y) + n_tgt.z * (pc.z - p0.z)) : 0.f;
-        B.parts[k] = analytic ? P.w_col * jcol : 0.f;
-        B.parts[K + k] = jprog;
-        B.parts[2 * K + k] = P.w_u * jctl;
+        if (P.paper) {
+            // Eq. 6 telescoped: sum_k |p_{k+1} - wp|^2 - |p_k - wp|^2 = |p_H - wp|^2 - |p_0 - wp|^2
+            const float dHx = pc.x - wp.x, dHy = pc.y - wp.y, dHz = pc.z - wp.z;
+            const float d0x = p0.x - wp.x, d0y = p0.y - wp.y, d0z = p0.z - wp.z;
+            const float jgate = (tgt >= 0) ? (dHx * dHx + dHy * dHy + dHz * dHz) - (d0x * d0x + d0y * d0y + d0z * d0z)
+                                           : 0.f;
+            B.parts[k] = analytic ? P.q_sdf * jcol : 0.f;
+            B.parts[K + k] = P.q_gate * jgate;
+            B.parts[2 * K + k] = P.q_vis * jvis;
+        } else {
+            const float jprog =
+                (tgt >= 0) ? -(n_tgt.x * (pc.x - p0.x) + n_tgt.y * (pc.y - p0.y) + n_tgt.z * (pc.z - p0.z)) : 0.f;
+            B.parts[k] = analytic ? P.w_col * jcol : 0.f;
+            B.parts[K + k] = jprog;
+            B.parts[2 * K + k] = P.w_u * jctl;
+        }
     }
 }
 
 // ------------------------------------------------------------------ (d) costs, weights, update, receding horizon
 // Block b owns R consecutive rollouts (R a multiple of 32, at most kCuMaxBlocks blocks):
 //  1. J_k = J_col + J_prog + J_ctl (MLP modes: J_col = w_col sum_h max(0, d_safe - s_h)^2
-//     over rollout k's row of the SDF array), rho_b = min of the block's J_k,
+//     over rollout k's row of the SDF array, or Q_sdf sum_h max(0, d_safe - s_h) in the
+//     paper's form), rho_b = min of the block's J_k,
 //     e_k = exp(-(J_k - rho_b) / lambda), eta_b = sum of the block's e_k;
 //  2. S_b[h] = sum_{k in b} e_k clip(U*_h + delta_{k,h});
 //  3. grid barrier (the kernel is a cooperative launch, so all its blocks are resident);
@@ -313,8 +329,8 @@ __global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, S
                 const float* srow = sdf + static_cast<size_t>(k) * H;
                 const float s0 = (lane < H) ? __ldcs(srow + lane) : inf;
                 const float s1 = (lane + 32 < H) ? __ldcs(srow + lane + 32) : inf;
-                acc[u] = hinge_sq(s0, P.d_safe) + hinge_sq(s1, P.d_safe);
-                for (int h = lane + 64; h < H; h += 32) acc[u] += hinge_sq(__ldcs(srow + h), P.d_safe);
+                acc[u] = stage_hinge(s0, P.d_safe, P.paper) + stage_hinge(s1, P.d_safe, P.paper);
+                for (int h = lane + 64; h < H; h += 32) acc[u] += stage_hinge(__ldcs(srow + h), P.d_safe, P.paper);
             } else {
                 pcol[u] = parts_in[k];
             }
@@ -324,7 +340,7 @@ __global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, S
 #pragma unroll
         for (int u = 0; u < kCuBatch; ++u) {
             const int i = i0 + u * kCuWarps;
-            const float jcol = mlp ? P.w_col * warp_sum(acc[u]) : pcol[u];
+            const float jcol = mlp ? (P.paper ? P.q_sdf : P.w_col) * warp_sum(acc[u]) : pcol[u];
             if (i < nk) {
                 const float J = jcol + pj[u] + pc[u];
                 if (lane == 0) sE[i] = J;

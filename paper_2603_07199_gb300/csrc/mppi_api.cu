@@ -120,6 +120,11 @@ StepParams make_params(const mppi_ctx* c) {
     P.key0 = static_cast<uint32_t>(g.seed & 0xFFFFFFFFull);
     P.key1 = static_cast<uint32_t>(g.seed >> 32);
     P.drone = g.drone_id;
+    P.paper = g.cost_mode == MPPI_COST_PAPER ? 1 : 0;
+    P.q_gate = g.q_gate;
+    P.q_vis = g.q_vis;
+    P.q_sdf = g.q_sdf;
+    P.tan_alpha = g.guide_tan_alpha;
     // per-kernel event timing measures kernels one after the other
     P.pdl = c->timing ? 0 : 1;
     return P;
@@ -141,9 +146,12 @@ int check_config(const mppi_config* g) {
         return fail(nullptr, MPPI_E_INVALID, "max_gates=%d out of [1, %d]", g->max_gates, MPPI_MAX_GATES);
     if (g->sdf_mode < MPPI_SDF_ANALYTIC || g->sdf_mode > MPPI_SDF_MLP_FP8)
         return fail(nullptr, MPPI_E_UNSUPPORTED, "sdf_mode=%d is not built", g->sdf_mode);
+    if (g->cost_mode != MPPI_COST_CONFIGURED && g->cost_mode != MPPI_COST_PAPER)
+        return fail(nullptr, MPPI_E_INVALID, "cost_mode=%d is not one of MPPI_COST_*", g->cost_mode);
     const float f[] = {g->dt, g->mass, g->gravity, g->thrust_min, g->thrust_max, g->rate_max, g->sigma_thrust,
                        g->sigma_rate, g->lambda, g->w_col, g->d_safe, g->w_u, g->gate_inner_half,
-                       g->gate_outer_half, g->gate_half_depth, g->softplus_beta};
+                       g->gate_outer_half, g->gate_half_depth, g->softplus_beta, g->q_gate, g->q_vis, g->q_sdf,
+                       g->guide_tan_alpha};
     if (!finite_all(f, sizeof(f) / sizeof(f[0]))) return fail(nullptr, MPPI_E_INVALID, "non-finite parameter");
     if (!(g->dt > 0.f) || !(g->mass > 0.f) || !(g->lambda > 0.f) || !(g->softplus_beta > 0.f))
         return fail(nullptr, MPPI_E_INVALID, "dt, mass, lambda and softplus_beta must be > 0");
@@ -322,6 +330,11 @@ void mppi_config_default(mppi_config* g) {
     g->softplus_beta = 100.f;
     g->seed = 0;
     g->drone_id = 0;
+    g->cost_mode = MPPI_COST_CONFIGURED;
+    g->q_gate = 1.f;
+    g->q_vis = 1.f;
+    g->q_sdf = 10.f;
+    g->guide_tan_alpha = 0.57735027f;   // tan(30 deg)
 }
 
 const char* mppi_last_error(const mppi_ctx* c) { return c ? c->err : g_thread_err; }

@@ -17,6 +17,10 @@ def make_config(prm, mode, max_gates):
     cfg.lam = prm["lam"]
     cfg.max_gates = max(1, int(max_gates))
     cfg.sdf_mode = MODES[mode]
+    cfg.cost_mode = {"configured": B.MPPI_COST_CONFIGURED, "paper": B.MPPI_COST_PAPER}[prm.get("cost_mode", "configured")]
+    for key in ("q_gate", "q_vis", "q_sdf", "guide_tan_alpha"):
+        if key in prm:
+            setattr(cfg, key, prm[key])
     return cfg
 
 

@@ -40,6 +40,15 @@ def params(K, H, **over):
     return d
 
 
+def paper_params(K, H, **over):
+    """Parameters of the paper's cost form (Eq. 6-9): d_safe = 1.0 m (its table of MPPI
+    parameters), weights Q_gate = 1, Q_vis = 1, Q_sdf = 10 and a 30 degree guidance cone."""
+    d = params(K, H, cost_mode="paper", d_safe=1.0, q_gate=1.0, q_vis=1.0, q_sdf=10.0,
+               guide_tan_alpha=math.tan(math.radians(30.0)))
+    d.update(over)
+    return d
+
+
 def yaw_pitch_quat(yaw, pitch):
     """Unit quaternion (w, x, y, z) of a yaw about world z followed by a pitch about the
     yawed y axis, written out in closed form from the half-angle sines and cosines."""
