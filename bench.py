@@ -424,6 +424,19 @@ def hover_gate_leg(torch, B, stream, flush, dev, steps, drone_id):
             "p99_ms": float(np.percentile(ms, 99)), "steps": steps}
 
 
+def max_over_ranks(torch, dist, x, device):
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_replicas(total_ms, units_per_rank, world, reduce_max):
+    """Whole-job throughput of `world` independent replicas: every rank's units over the
+    slowest rank's timed total (reduce_max: the maximum over ranks).  Returns (value, slowest ms)."""
+    slowest = reduce_max(total_ms)
+    return world * units_per_rank / (slowest * 1e-3), slowest
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -460,12 +473,8 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    total = float(ms.sum())
-    if world > 1:
-        t = torch.tensor([total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
-    value = world * K * H * args.steps / (total * 1e-3)
+    value, total = aggregate_replicas(float(ms.sum()), K * H * args.steps, world,
+                                      lambda x: max_over_ranks(torch, dist, x, dev) if world > 1 else x)
 
     ktimes = kernel_times(torch, B, ctx, 20, flush, wl, dev)
     e2e_ms, h2d, d2h = e2e_loop(torch, B, ctx, wl, args.e2e_steps, flush)

@@ -50,6 +50,7 @@ struct StepBuffers {
     float4* out_U;         // optional caller device buffers written by the step (H x 4, K, K)
     float* out_w;
     float* out_J;
+    int* err_out;          // optional: the step's last kernel copies *err here when it is done
     float* stats;          // [4] rho, eta of the last step
     unsigned* tickets;     // [32] [9] grid-barrier arrivals, [10] grid-barrier generation
     int* err;              // [1] device error word

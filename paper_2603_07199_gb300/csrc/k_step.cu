@@ -533,6 +533,8 @@ __global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, S
                 const uint32_t lo = B.step[0] + 1u;
                 B.step[0] = lo;
                 if (lo == 0u) B.step[1] += 1u;
+                // every earlier wait of this step has ended (this block passed the grid barrier)
+                if (B.err_out) *B.err_out = *reinterpret_cast<volatile int*>(B.err);
             }
         }
         __syncthreads();

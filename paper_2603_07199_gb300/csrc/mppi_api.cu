@@ -170,12 +170,14 @@ int recompute_b1p(mppi_ctx* c) {
 
 bool is_mlp(const mppi_ctx* c) { return c->cfg.sdf_mode != MPPI_SDF_ANALYTIC; }
 
-// Caller device buffers the step's last kernel writes U*_new, w and J into (NULL: none).
-void set_outputs(mppi_ctx* c, float4* U, float* w, float* J) {
-    if (c->B.out_U != U || c->B.out_w != w || c->B.out_J != J) {
+// Caller device buffers the step's last kernel writes U*_new, w and J into, and the slot
+// it copies the device error word to (NULL: none).
+void set_outputs(mppi_ctx* c, float4* U, float* w, float* J, int* err) {
+    if (c->B.out_U != U || c->B.out_w != w || c->B.out_J != J || c->B.err_out != err) {
         c->B.out_U = U;
         c->B.out_w = w;
         c->B.out_J = J;
+        c->B.err_out = err;
         c->graph_dirty = true;
     }
 }
@@ -630,11 +632,13 @@ int mppi_step(mppi_ctx* c, const float* state, const float* gate_poses, const fl
     // pinned staging buffer
     float* ho = c->h_out;
     float* dho = c->d_hout;
-    set_outputs(c, reinterpret_cast<float4*>(dho), weights ? dho + H * 4 : nullptr, costs ? dho + H * 4 + K : nullptr);
+    // and the error word too: -1 stays if the step's last kernel did not finish its work
+    volatile int* herr = reinterpret_cast<volatile int*>(ho + H * 4 + 2 * K);
+    *herr = -1;
+    set_outputs(c, reinterpret_cast<float4*>(dho), weights ? dho + H * 4 : nullptr, costs ? dho + H * 4 + K : nullptr,
+                reinterpret_cast<int*>(dho + H * 4 + 2 * K));
     rc = launch_step(c);
     if (rc != MPPI_OK) return rc;
-    int* herr = reinterpret_cast<int*>(ho + H * 4 + 2 * K);
-    CUDA_TRY(c, cudaMemcpyAsync(herr, c->B.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     ++c->step_count;
     if (*herr != 0) {
@@ -669,7 +673,7 @@ int mppi_step_async(mppi_ctx* c, const float* d_state, const float* d_gate_poses
         CUDA_TRY(c, cudaMemcpyAsync(c->B.nominal, d_nominal, H * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream));
     // the step's last kernel writes the caller's buffers itself; a change of buffers is a
     // change of launch arguments (the step graph is captured again)
-    set_outputs(c, reinterpret_cast<float4*>(d_new_controls), d_weights, d_costs);
+    set_outputs(c, reinterpret_cast<float4*>(d_new_controls), d_weights, d_costs, nullptr);
     rc = launch_step(c);
     if (rc != MPPI_OK) return rc;
     ++c->step_count;
@@ -827,11 +831,13 @@ int ctx_enqueue_host_step(mppi_ctx* c, const float* state, int n_gates, const fl
     }
     int rc = check_ready(c);
     if (rc != MPPI_OK) return rc;
-    set_outputs(c, reinterpret_cast<float4*>(c->d_hout), nullptr, nullptr);   // U*_new straight into pinned staging
+    // U*_new and the error word straight into pinned staging (-1 stays if the step's last
+    // kernel did not finish its work)
+    *reinterpret_cast<volatile int*>(c->h_out + H * 4 + 2 * c->cfg.K) = -1;
+    set_outputs(c, reinterpret_cast<float4*>(c->d_hout), nullptr, nullptr,
+                reinterpret_cast<int*>(c->d_hout + H * 4 + 2 * c->cfg.K));
     rc = launch_step(c);
     if (rc != MPPI_OK) return rc;
-    float* ho = c->h_out;
-    CUDA_TRY(c, cudaMemcpyAsync(ho + H * 4 + 2 * c->cfg.K, c->B.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaEventRecord(c->done, c->stream));
     ++c->step_count;
     return MPPI_OK;
@@ -842,7 +848,7 @@ int ctx_poll_host_step(mppi_ctx* c, float* new_controls) {
     if (q == cudaErrorNotReady) return 1;
     if (q != cudaSuccess) return fail(c, MPPI_E_CUDA, "step failed: %s", cudaGetErrorString(q));
     const int H = c->cfg.H;
-    const int* herr = reinterpret_cast<const int*>(c->h_out + H * 4 + 2 * c->cfg.K);
+    const volatile int* herr = reinterpret_cast<const volatile int*>(c->h_out + H * 4 + 2 * c->cfg.K);
     if (*herr != 0) {
         CUDA_TRY(c, clear_device_error(c));
         return fail(c, MPPI_E_TIMEOUT, "a device-side wait timed out (error word %d)", *herr);
