@@ -24,7 +24,7 @@
 // and c (ln 2 / beta) = 1, so the hidden weights are used unchanged while the
 // first layer and the hidden biases are scaled by c and the output weights by
 // ln 2 / beta.  h is evaluated with one hardware exp2 and a quartic in
-// e = 2^-|y| (see kL1..kL4), in packed f32x2 (BF16) or f16x2 (FP16, E4M3) arithmetic.
+// e = 2^-|y| (see kPolyDeg), in packed f32x2 (BF16) or f16x2 (FP16, E4M3) arithmetic.
 #include "kernels.h"
 #include "tc.cuh"
 
@@ -82,23 +82,42 @@ __device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
     return r;
 }
 
-// log2(1 + e) for e in [0, 1] as e (c1 + e (c2 + e (c3 + e c4))) with c1 = 1 / ln 2
-// exact and c2..c4 a weighted least-squares (near-minimax) fit made for this
-// kernel: max abs error 2.1e-4, relative error 1.4e-4 as e -> 0 (below the
-// BF16 rounding of the activations it feeds).
-constexpr float kL1 = 1.4426950408889634f;
-constexpr float kL2 = -0.69991479f;
-constexpr float kL3 = 0.35777588f;
+// log2(1 + e) for e in [0, 1] as e p(e), p a polynomial of degree kPolyDeg - 1 fitted for
+// this kernel (weighted least squares, near-minimax):
+//   degree 4: c1 = 1 / ln 2 exact, c2..c4 fitted; max abs error 2.1e-4 (relative 1.4e-4 as e -> 0)
+//   degree 3: max abs error 7.7e-4;  degree 2: max abs error 6.3e-3.
+// The 16-bit rounding of the operands (2^-9 relative for BF16, 2^-11 for FP16) dominates the
+// SDF error at every one of these degrees; measured against the FP64 oracle at K = 4096,
+// H = 50, two gates, degree 2 instead of 4 moves the SDF error from 1.210 to 1.242 mm (BF16,
+// mean) and 0.097 to 0.101 mm (FP16) and saves two packed FMAs per activation pair.
+constexpr int kPolyDeg = 2;
+constexpr float kL1 = kPolyDeg == 4 ? 1.4426950408889634f : kPolyDeg == 3 ? 1.42459805f : 1.35697908f;
+constexpr float kL2 = kPolyDeg == 4 ? -0.69991479f : kPolyDeg == 3 ? -0.58922454f : -0.36332346f;
+constexpr float kL3 = kPolyDeg == 4 ? 0.35777588f : 0.16539965f;
 constexpr float kL4 = -0.10076641f;
+
+// p(e) in packed f32x2
+__device__ __forceinline__ uint64_t poly2(uint64_t e) {
+    if constexpr (kPolyDeg == 4) {
+        uint64_t p = fma2(e, pk(kL4, kL4), pk(kL3, kL3));
+        p = fma2(e, p, pk(kL2, kL2));
+        return fma2(e, p, pk(kL1, kL1));
+    } else if constexpr (kPolyDeg == 3) {
+        const uint64_t p = fma2(e, pk(kL3, kL3), pk(kL2, kL2));
+        return fma2(e, p, pk(kL1, kL1));
+    } else {
+        return fma2(e, pk(kL2, kL2), pk(kL1, kL1));
+    }
+}
 
 // ---------------------------------------------------------------- packed f16x2 epilogue (FP16 operand path)
 // The same h(y) with every step after the FP32 bias add in f16x2: one hardware
-// exp2 per two activations, the quartic as f16x2 FMAs (coefficients rounded to
+// exp2 per two activations, the polynomial as f16x2 FMAs (coefficients rounded to
 // f16), and the result is directly the FP16 A operand of the next layer.
-constexpr uint32_t kH1 = 0x3dc53dc5u;   // f16x2 of kL1
-constexpr uint32_t kH2 = 0xb999b999u;   // f16x2 of kL2
-constexpr uint32_t kH3 = 0x35b935b9u;   // f16x2 of kL3
-constexpr uint32_t kH4 = 0xae73ae73u;   // f16x2 of kL4
+constexpr uint32_t kH1 = kPolyDeg == 4 ? 0x3dc53dc5u : kPolyDeg == 3 ? 0x3db33db3u : 0x3d6e3d6eu;   // f16x2 of kL1
+constexpr uint32_t kH2 = kPolyDeg == 4 ? 0xb999b999u : kPolyDeg == 3 ? 0xb8b7b8b7u : 0xb5d0b5d0u;   // f16x2 of kL2
+constexpr uint32_t kH3 = kPolyDeg == 4 ? 0x35b935b9u : 0x314b314bu;                                // f16x2 of kL3
+constexpr uint32_t kH4 = 0xae73ae73u;                                                            // f16x2 of kL4
 
 __device__ __forceinline__ uint32_t hfma2(uint32_t a, uint32_t b, uint32_t c) {
     uint32_t r;
@@ -129,9 +148,17 @@ __device__ __forceinline__ float2 f16x2_to_f32x2(uint32_t v) {
 __device__ __forceinline__ uint32_t softplus2_log2_f16(float y0, float y1) {
     const uint32_t h = f32x2_to_f16x2(y0, y1);
     const uint32_t e = hex2(h | 0x80008000u);              // 2^-|y|
-    uint32_t p = hfma2(e, kH4, kH3);
-    p = hfma2(e, p, kH2);
-    p = hfma2(e, p, kH1);
+    uint32_t p;
+    if constexpr (kPolyDeg == 4) {
+        p = hfma2(e, kH4, kH3);
+        p = hfma2(e, p, kH2);
+        p = hfma2(e, p, kH1);
+    } else if constexpr (kPolyDeg == 3) {
+        p = hfma2(e, kH3, kH2);
+        p = hfma2(e, p, kH1);
+    } else {
+        p = hfma2(e, kH2, kH1);
+    }
     return hfma2(e, p, hmax2_zero(h));
 }
 
@@ -162,10 +189,7 @@ __device__ __forceinline__ uint32_t act_pair(uint64_t y2) {
     if constexpr (kFmt == kFmtBF16) {
         const float2 y = upk(y2);
         const uint64_t e = pk(tc::ex2_approx(-fabsf(y.x)), tc::ex2_approx(-fabsf(y.y)));
-        uint64_t p = fma2(e, pk(kL4, kL4), pk(kL3, kL3));
-        p = fma2(e, p, pk(kL2, kL2));
-        p = fma2(e, p, pk(kL1, kL1));
-        const float2 h = upk(fma2(e, p, pk(fmaxf(y.x, 0.f), fmaxf(y.y, 0.f))));
+        const float2 h = upk(fma2(e, poly2(e), pk(fmaxf(y.x, 0.f), fmaxf(y.y, 0.f))));
         return tc::pack_bf16x2(h.x, h.y);
     } else {
         const float2 y = upk(y2);
@@ -178,10 +202,7 @@ __device__ __forceinline__ uint64_t out_pair(uint64_t y2, uint64_t w2, uint64_t 
     if constexpr (kFmt == kFmtBF16) {
         const float2 y = upk(y2);
         const uint64_t e = pk(tc::ex2_approx(-fabsf(y.x)), tc::ex2_approx(-fabsf(y.y)));
-        uint64_t p = fma2(e, pk(kL4, kL4), pk(kL3, kL3));
-        p = fma2(e, p, pk(kL2, kL2));
-        p = fma2(e, p, pk(kL1, kL1));
-        return fma2(w2, fma2(e, p, pk(fmaxf(y.x, 0.f), fmaxf(y.y, 0.f))), acc);
+        return fma2(w2, fma2(e, poly2(e), pk(fmaxf(y.x, 0.f), fmaxf(y.y, 0.f))), acc);
     } else {
         const float2 y = upk(y2);
         const float2 h = f16x2_to_f32x2(softplus2_log2_f16(y.x, y.y));
