@@ -42,7 +42,7 @@ FMA_FLOPS_PER_QUERY = 2 * 3 * 128 + 2 * 128           # layer 1 (point part) + o
 # dram__bytes_read.sum + dram__bytes_write.sum of one sdf_mlp_bf16 launch at this workload, from
 # the ncu capture summarised in profiles/sdf_mlp_tc_bf16_two_gate_K4096_H50_G2.md (None once the
 # kernel changes)
-SDF_BF16_DRAM_BYTES = 3415552
+SDF_BF16_DRAM_BYTES = 3414784
 
 
 def parse():
