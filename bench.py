@@ -135,6 +135,11 @@ def make_ctx(B, wl, mode, stream, drone_id):
     cfg.max_gates = wl["poses"].shape[0]
     cfg.sdf_mode = {"bf16": B.MPPI_SDF_MLP_BF16, "fp32": B.MPPI_SDF_MLP_FP32, "fp16": B.MPPI_SDF_MLP_FP16,
                     "fp8": B.MPPI_SDF_MLP_FP8, "analytic": B.MPPI_SDF_ANALYTIC}[mode]
+    if prm.get("dynamics") == "rotor":
+        cfg.dynamics_mode = B.MPPI_DYN_ROTOR
+        cfg.tdot_max, cfg.rotor_thrust_max, cfg.sigma_tdot = prm["tdot_max"], prm["rotor_thrust_max"], prm["sigma_tdot"]
+        cfg.arm_length, cfg.torque_coeff = prm["arm_length"], prm["kappa"]
+        cfg.inertia_x, cfg.inertia_y, cfg.inertia_z = prm["inertia"]
     ctx = B.mppi_create(cfg, stream)
     if mode != "analytic":
         keep = []
@@ -412,6 +417,18 @@ def four_gate_leg(torch, B, stream, flush, dev, steps, drone_id):
     return out
 
 
+def rotor_leg(torch, B, stream, flush, dev, steps, drone_id):
+    """The paper's rotor-thrust-rate model on the K=4096, H=50, two-gate workload (BF16 SDF)."""
+    import workloads as W
+    wl = dict(W.two_gate_mlp())
+    wl["params"] = W.rotor_params(4096, 50)
+    wl["state"] = W.rotor_state([0.0, 0.0, 0.0])
+    wl["nominal"] = np.zeros((50, 4), np.float32)
+    out = mode_leg(torch, B, wl, "bf16", stream, flush, dev, steps, drone_id)
+    out["workload"] = "rotor_two_gate_mlp_K4096_H50_G2"
+    return out
+
+
 def hover_gate_leg(torch, B, stream, flush, dev, steps, drone_id):
     """The small single-gate workload (K=256, H=20, analytic frame SDF)."""
     import workloads as W
@@ -498,6 +515,7 @@ def run_ours(args):
     four = (four_gate_leg(torch, B, stream, flush, dev, args.four_gate_steps, rank)
             if args.four_gate_steps > 0 else None)
     hover = hover_gate_leg(torch, B, stream, flush, dev, args.steps, rank)
+    rotor_dyn = rotor_leg(torch, B, stream, flush, dev, args.steps, rank)
     serving = serving_leg(torch, B, dev, args.serving_seconds) if args.serving_seconds > 0 else None
     distill = distill_leg(torch, B, dev, args.distill_steps) if args.distill_steps > 0 else None
 
@@ -547,6 +565,7 @@ def run_ours(args):
                 "p99_ms": float(np.percentile(e2e_ms, 99))},
         "four_gates": four,
         "hover_gate_analytic": hover,
+        "rotor_dynamics": rotor_dyn,
         "serving": serving,
         "distill": distill,
         "gpu_launches": per_launch * args.steps,

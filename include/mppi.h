@@ -17,8 +17,9 @@
  *
  * Conventions for every call:
  *   - All floats are IEEE binary32, row-major, SI units.  A state is 13
- *     floats [p(3), v(3), q(4) = (w, x, y, z), w_body(3)]; a control is 4
- *     floats [collective thrust T (N), body rates wx, wy, wz (rad/s)]; a gate
+ *     floats [p(3), v(3), q(4) = (w, x, y, z), w_body(3)] (MPPI_DYN_ROTOR: 17, the
+ *     rotor thrusts T1..T4 appended); a control is 4 floats [collective thrust T (N),
+ *     body rates wx, wy, wz (rad/s)] (MPPI_DYN_ROTOR: the rotor-thrust rates); a gate
  *     pose is 7 floats [t(3), q(4) (w, x, y, z) rotating gate -> world]; the
  *     gate plane is x = 0 of the gate frame and its normal is R(q) e_x.
  *   - The caller owns every pointer it passes.  The library never keeps a
@@ -90,6 +91,15 @@ extern "C" {
  *                                     hinge max(0, d_safe - s) (Eq. 8) on the target gate
  *   guide_tan_alpha                   tan of the cone angle of the guidance SDF (Eq. 2), the
  *                                     analytic SDF of MPPI_COST_PAPER
+ *   dynamics_mode                     MPPI_DYN_CTBR (u = collective thrust + body rates, the
+ *                                     body rate tracked ideally) or MPPI_DYN_ROTOR (u = the
+ *                                     four rotor-thrust rates, Sec. IV-A; the state adds the
+ *                                     rotor thrusts)
+ *   tdot_max, rotor_thrust_max        MPPI_DYN_ROTOR bounds: |u_i| <= tdot_max (N/s), each rotor
+ *                                     thrust clamped to [0, rotor_thrust_max] (N) after a step
+ *   sigma_tdot                        MPPI_DYN_ROTOR noise standard deviation (N/s)
+ *   arm_length, torque_coeff          X layout arm (m) and rotor reaction torque per newton (m)
+ *   inertia_x, inertia_y, inertia_z   diagonal inertia (kg m^2)
  */
 typedef struct mppi_config {
     int32_t K;
@@ -107,7 +117,20 @@ typedef struct mppi_config {
     int32_t cost_mode;
     float q_gate, q_vis, q_sdf;
     float guide_tan_alpha;
+    int32_t dynamics_mode;
+    float tdot_max, rotor_thrust_max, sigma_tdot;
+    float arm_length, torque_coeff;
+    float inertia_x, inertia_y, inertia_z;
 } mppi_config;
+
+/* Dynamics models (mppi_config.dynamics_mode). */
+#define MPPI_DYN_CTBR   0       /* state [p, v, q, w] (13); u = [T, wx, wy, wz], ideal body-rate tracking */
+#define MPPI_DYN_ROTOR  1       /* state [p, v, q, w, T1..T4] (17); u = [dT1/dt .. dT4/dt], rigid body with
+                                   the rotors' torques (X layout) */
+#define MPPI_STATE_MAX  17
+
+/* Number of floats of a state under cfg: 13 (MPPI_DYN_CTBR) or 17 (MPPI_DYN_ROTOR). */
+int mppi_state_dim(const mppi_config* cfg);
 
 /* Cost forms (mppi_config.cost_mode). */
 #define MPPI_COST_CONFIGURED 0  /* w_col max(0, d_safe - s)^2 + progress along the target gate's normal
@@ -162,7 +185,7 @@ int mppi_set_sdf_weights(mppi_ctx* ctx, const float* const* layers, int n_layers
 
 /*
  * One control step, host buffers, synchronous.
- *   state        13 floats, or NULL to continue from the device-resident state
+ *   state        mppi_state_dim(cfg) floats, or NULL to continue from the device-resident state
  *                (advanced by the previous step's plant update)
  *   gate_poses   n_gates x 7, or NULL to keep the current gates
  *   latents      n_gates x 64, or NULL to keep the current latents
@@ -194,7 +217,7 @@ int mppi_step_async(mppi_ctx* ctx, const float* d_state, const float* d_gate_pos
 /* Wait for the context's stream and report any device-side error. */
 int mppi_sync(mppi_ctx* ctx);
 
-/* Read back the device-resident warm-start sequence (H x 4) / true state (13). Synchronous. */
+/* Read back the device-resident warm-start sequence (H x 4) / true state (mppi_state_dim). Synchronous. */
 int mppi_get_nominal(mppi_ctx* ctx, float* out);
 int mppi_get_state(mppi_ctx* ctx, float* out);
 
@@ -387,7 +410,7 @@ int mppi_server_set_sdf_weights(mppi_server* server, const float* const* layers,
  * Queue one control step of drone drone_id (host buffers, copied before the
  * call returns): cfg gives the drone's controller parameters (K, H and
  * max_gates must stay the same for a drone; the server's sdf_mode applies),
- * state 13 floats, n_gates gate poses (n x 7) and latents (n x 64; NULL in
+ * state mppi_state_dim(cfg) floats, n_gates gate poses (n x 7) and latents (n x 64; NULL in
  * analytic mode).  *ticket identifies the request.  Returns at once.
  */
 int mppi_server_submit(mppi_server* server, int drone_id, const mppi_config* cfg, const float* state, int n_gates,

@@ -14,6 +14,8 @@ The oracle restates the paper's method step by step in float64 with numpy:
                    perturbations delta u ~ N(0, Sigma) of Sec. IV-A (Eq. 5).
 * ``dynamics``  -- quadrotor model x_dot = f(x, u) with state [p, v, q, w]
                    (Sec. IV-A) in collective-thrust + body-rate form, RK4.
+* ``rotor``     -- the paper's rotor-thrust-rate model (state + four rotor thrusts,
+                   command = thrust rates) and its RK4 step, with stated airframe readings.
 * ``gate_sdf``  -- gate-frame transform, the l-infinity radial metric (Eq. 1),
                    the hourglass guide SDF (Eq. 2) and the exact signed
                    distance to the rectangular gate frame.
@@ -31,4 +33,4 @@ states) are passed in by the caller from the seeded generators in
 ``workloads``.
 """
 
-from . import philox, noise, dynamics, gate_sdf, mlp, mppi, distill  # noqa: F401
+from . import philox, noise, dynamics, rotor, gate_sdf, mlp, mppi, distill  # noqa: F401

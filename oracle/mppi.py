@@ -35,7 +35,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import dynamics, gate_sdf, mlp, noise
+from . import dynamics, gate_sdf, mlp, noise, rotor
 
 
 @dataclass
@@ -64,12 +64,25 @@ class Params:
     q_vis: float = 1.0
     q_sdf: float = 10.0
     guide_tan_alpha: float = 0.5773502691896257      # tan(30 deg), the cone angle of Eq. 2
+    # "ctbr": collective thrust + body rates; "rotor": the paper's rotor-thrust rates
+    # (``oracle.rotor``) with the bounds of its Table I and the airframe readings below
+    dynamics: str = "ctbr"
+    tdot_max: float = 10.0
+    rotor_thrust_max: float = 10.0
+    sigma_tdot: float = 5.0
+    arm_length: float = 0.15
+    kappa: float = 0.016
+    inertia: tuple = (0.003, 0.003, 0.005)
 
     def u_hover(self):
+        if self.dynamics == "rotor":
+            return np.zeros(4)
         return np.array([self.mass * self.gravity, 0.0, 0.0, 0.0])
 
 
 def clip_controls(U, prm):
+    if prm.dynamics == "rotor":
+        return np.clip(U, -prm.tdot_max, prm.tdot_max)
     lo = np.array([prm.thrust_min, -prm.rate_max, -prm.rate_max, -prm.rate_max])
     hi = np.array([prm.thrust_max, prm.rate_max, prm.rate_max, prm.rate_max])
     return np.minimum(np.maximum(U, lo), hi)
@@ -188,10 +201,14 @@ def mppi_step(state, nominal, poses, prm, step, latents=None, layers=None):
     """One control step from state [13] and nominal U* [H, 4]; returns every intermediate."""
     state = np.asarray(state, dtype=np.float64)
     nominal = np.asarray(nominal, dtype=np.float64)
+    rot = prm.dynamics == "rotor"
     delta = noise.control_noise(prm.K, prm.H, prm.seed, step, prm.drone_id,
-                                prm.sigma_thrust, prm.sigma_rate)
+                                prm.sigma_tdot if rot else prm.sigma_thrust, prm.sigma_tdot if rot else prm.sigma_rate)
     U = clip_controls(nominal[None, :, :] + delta, prm)
-    positions, attitudes = dynamics.rollout_states(state, U, prm.dt, prm.mass, prm.gravity)
+    if rot:
+        positions, attitudes = rotor.rollout(state, U, prm)
+    else:
+        positions, attitudes = dynamics.rollout_states(state, U, prm.dt, prm.mass, prm.gravity)
     if prm.cost_mode == "paper":
         costs = paper_costs(state, positions, attitudes, poses, prm, latents, layers)
     else:
@@ -205,7 +222,10 @@ def mppi_step(state, nominal, poses, prm, step, latents=None, layers=None):
 
 def receding_horizon(state, U_new, prm):
     """Apply U*_new[0] to the plant; return (next state, next nominal)."""
-    nxt = dynamics.plant_step(state, U_new[0], prm.dt, prm.mass, prm.gravity)
+    if prm.dynamics == "rotor":
+        nxt = rotor.plant_step(state, U_new[0], prm)
+    else:
+        nxt = dynamics.plant_step(state, U_new[0], prm.dt, prm.mass, prm.gravity)
     return nxt, shift_nominal(U_new, prm)
 
 

@@ -29,6 +29,9 @@ MPPI_SDF_MLP_FP8 = 4
 
 MPPI_COST_CONFIGURED = 0
 MPPI_COST_PAPER = 1
+MPPI_DYN_CTBR = 0
+MPPI_DYN_ROTOR = 1
+MPPI_STATE_MAX = 17
 
 MPPI_BUF_NOISE = 0
 MPPI_BUF_POSITIONS = 1
@@ -42,7 +45,7 @@ HIDDEN = 128
 
 # every symbol include/mppi.h declares
 EXPORTS = [
-    "mppi_config_default", "mppi_create", "mppi_destroy", "mppi_last_error", "mppi_set_gates",
+    "mppi_config_default", "mppi_state_dim", "mppi_create", "mppi_destroy", "mppi_last_error", "mppi_set_gates",
     "mppi_set_sdf_weights", "mppi_step", "mppi_step_async", "mppi_sync", "mppi_get_nominal",
     "mppi_get_state", "mppi_set_step_counter", "mppi_get_step_counter", "mppi_read_buffer",
     "mppi_read_noise_words", "mppi_set_timing", "mppi_get_kernel_times", "mppi_kernels_per_step",
@@ -74,6 +77,9 @@ class MppiConfig(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("drone_id", ctypes.c_uint32), ("cost_mode", ctypes.c_int32),
         ("q_gate", ctypes.c_float), ("q_vis", ctypes.c_float), ("q_sdf", ctypes.c_float),
         ("guide_tan_alpha", ctypes.c_float),
+        ("dynamics_mode", ctypes.c_int32), ("tdot_max", ctypes.c_float), ("rotor_thrust_max", ctypes.c_float),
+        ("sigma_tdot", ctypes.c_float), ("arm_length", ctypes.c_float), ("torque_coeff", ctypes.c_float),
+        ("inertia_x", ctypes.c_float), ("inertia_y", ctypes.c_float), ("inertia_z", ctypes.c_float),
     ]
 
 
@@ -99,6 +105,7 @@ class MppiTrainConfig(ctypes.Structure):
 _vp = ctypes.c_void_p
 _SIGS = {
     "mppi_config_default": (None, [ctypes.POINTER(MppiConfig)]),
+    "mppi_state_dim": (ctypes.c_int, [ctypes.POINTER(MppiConfig)]),
     "mppi_create": (ctypes.c_int, [ctypes.POINTER(MppiConfig), _vp, ctypes.POINTER(_vp)]),
     "mppi_destroy": (None, [_vp]),
     "mppi_last_error": (ctypes.c_char_p, [_vp]),
@@ -189,6 +196,10 @@ def mppi_config_default():
     cfg = MppiConfig()
     load().mppi_config_default(ctypes.byref(cfg))
     return cfg
+
+
+def mppi_state_dim(cfg):
+    return load().mppi_state_dim(ctypes.byref(cfg))
 
 
 def mppi_create(cfg, stream=None):

@@ -29,6 +29,10 @@ struct StepParams {
     int pdl;               // host side: launch kernels as programmatic dependents
     int paper;             // cost form of Eq. 6-9 on the target gate (else the configured form)
     float q_gate, q_vis, q_sdf, tan_alpha;
+    int rotor;             // rotor-thrust-rate model (17-number state) instead of thrust + body rates
+    float u_hover;         // first control channel of the hover command (m g, or 0 for thrust rates)
+    float arm_d, kappa, t_rotor_max;  // rotor offset l / sqrt(2), reaction torque per newton, thrust bound
+    float3 J, inv_J;       // diagonal inertia and its reciprocal
 };
 
 // Device buffers of one controller.
@@ -193,6 +197,71 @@ __device__ __forceinline__ void rk4_step(const StepParams& P, Vec3& p, Vec3& v, 
     Quat qn{an * q.w + bn * wq.w, an * q.x + bn * wq.x, an * q.y + bn * wq.y, an * q.z + bn * wq.z};
     const float inv = rsqrtf(qn.w * qn.w + qn.x * qn.x + qn.y * qn.y + qn.z * qn.z);
     q = Quat{qn.w * inv, qn.x * inv, qn.y * inv, qn.z * inv};
+}
+
+// ---------------------------------------------------------------- rotor-thrust-rate model
+// State [p, v, q, w, T1..T4], command u = dT/dt (Sec. IV-A).  Rotor i sits at body
+// d (1, -1), (-1, -1), (-1, 1), (1, 1) (X layout, d = arm / sqrt(2)) with reaction torque
+// kappa (+1, -1, +1, -1) T_i about body z, so tau = (d (T3 + T4 - T1 - T2),
+// d (T2 + T3 - T1 - T4), kappa (T1 + T3 - T2 - T4)) in 1-based rotor numbers, and
+//   dv = (sum T / m) R(q) e_z - g e_z,  dq = q (x) (0, w) / 2,  dw = J^-1 (tau - w x J w),  dT = u.
+struct RotorDeriv {
+    Vec3 dv;
+    Quat dq;
+    Vec3 dw;
+};
+
+__device__ __forceinline__ RotorDeriv rotor_deriv(const StepParams& P, const Quat& q, const Vec3& w, float t0, float t1,
+                                                  float t2, float t3) {
+    RotorDeriv d;
+    const float a = (t0 + t1 + t2 + t3) / P.mass;
+    const Vec3 z = body_z(q);
+    d.dv = v3(a * z.x, a * z.y, a * z.z - P.gravity);
+    d.dq = Quat{-0.5f * (q.x * w.x + q.y * w.y + q.z * w.z), 0.5f * (q.w * w.x + q.y * w.z - q.z * w.y),
+                0.5f * (q.w * w.y - q.x * w.z + q.z * w.x), 0.5f * (q.w * w.z + q.x * w.y - q.y * w.x)};
+    const float tx = P.arm_d * ((t2 + t3) - (t0 + t1));
+    const float ty = P.arm_d * ((t1 + t2) - (t0 + t3));
+    const float tz = P.kappa * ((t0 + t2) - (t1 + t3));
+    const Vec3 Jw = v3(P.J.x * w.x, P.J.y * w.y, P.J.z * w.z);
+    d.dw = v3((tx - (w.y * Jw.z - w.z * Jw.y)) * P.inv_J.x, (ty - (w.z * Jw.x - w.x * Jw.z)) * P.inv_J.y,
+              (tz - (w.x * Jw.y - w.y * Jw.x)) * P.inv_J.z);
+    return d;
+}
+
+__device__ __forceinline__ Vec3 axpy(float a, const Vec3& x, const Vec3& y) {
+    return v3(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z));
+}
+__device__ __forceinline__ Quat axpy(float a, const Quat& x, const Quat& y) {
+    return Quat{fmaf(a, x.w, y.w), fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z)};
+}
+
+// One classical RK4 step of the rotor model with u held; q renormalised, thrusts clamped to
+// [0, t_rotor_max].  T: the four rotor thrusts, updated in place.
+__device__ __forceinline__ void rk4_rotor(const StepParams& P, Vec3& p, Vec3& v, Quat& q, Vec3& w, float* T, float4 u) {
+    const float dt = P.dt, h2 = 0.5f * dt;
+    const float a0 = T[0] + h2 * u.x, a1 = T[1] + h2 * u.y, a2 = T[2] + h2 * u.z, a3 = T[3] + h2 * u.w;
+    const RotorDeriv k1 = rotor_deriv(P, q, w, T[0], T[1], T[2], T[3]);
+    const Vec3 v2 = axpy(h2, k1.dv, v);
+    const RotorDeriv k2 = rotor_deriv(P, axpy(h2, k1.dq, q), axpy(h2, k1.dw, w), a0, a1, a2, a3);
+    const Vec3 v3s = axpy(h2, k2.dv, v);
+    const RotorDeriv k3 = rotor_deriv(P, axpy(h2, k2.dq, q), axpy(h2, k2.dw, w), a0, a1, a2, a3);
+    const Vec3 v4 = axpy(dt, k3.dv, v);
+    const RotorDeriv k4 = rotor_deriv(P, axpy(dt, k3.dq, q), axpy(dt, k3.dw, w), T[0] + dt * u.x, T[1] + dt * u.y,
+                                      T[2] + dt * u.z, T[3] + dt * u.w);
+    const float c = dt * (1.f / 6.f);
+    p = v3(p.x + c * (v.x + 2.f * (v2.x + v3s.x) + v4.x), p.y + c * (v.y + 2.f * (v2.y + v3s.y) + v4.y),
+           p.z + c * (v.z + 2.f * (v2.z + v3s.z) + v4.z));
+    v = v3(v.x + c * (k1.dv.x + 2.f * (k2.dv.x + k3.dv.x) + k4.dv.x), v.y + c * (k1.dv.y + 2.f * (k2.dv.y + k3.dv.y) + k4.dv.y),
+           v.z + c * (k1.dv.z + 2.f * (k2.dv.z + k3.dv.z) + k4.dv.z));
+    const Quat qn{q.w + c * (k1.dq.w + 2.f * (k2.dq.w + k3.dq.w) + k4.dq.w), q.x + c * (k1.dq.x + 2.f * (k2.dq.x + k3.dq.x) + k4.dq.x),
+                  q.y + c * (k1.dq.y + 2.f * (k2.dq.y + k3.dq.y) + k4.dq.y), q.z + c * (k1.dq.z + 2.f * (k2.dq.z + k3.dq.z) + k4.dq.z)};
+    q = qnormalize(qn);
+    w = v3(w.x + c * (k1.dw.x + 2.f * (k2.dw.x + k3.dw.x) + k4.dw.x), w.y + c * (k1.dw.y + 2.f * (k2.dw.y + k3.dw.y) + k4.dw.y),
+           w.z + c * (k1.dw.z + 2.f * (k2.dw.z + k3.dw.z) + k4.dw.z));
+    T[0] = fminf(fmaxf(T[0] + dt * u.x, 0.f), P.t_rotor_max);
+    T[1] = fminf(fmaxf(T[1] + dt * u.y, 0.f), P.t_rotor_max);
+    T[2] = fminf(fmaxf(T[2] + dt * u.z, 0.f), P.t_rotor_max);
+    T[3] = fminf(fmaxf(T[3] + dt * u.w, 0.f), P.t_rotor_max);
 }
 
 // ---------------------------------------------------------------- programmatic dependent launch

@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, 
     const float* pose_t = sPose + 8 * (tgt < 0 ? 0 : tgt);
     const Vec3 wp = v3(pose_t[0], pose_t[1], pose_t[2]);
 
-    const float uh = P.mass * P.gravity;
+    const float uh = P.u_hover;
     const float dt = P.dt;
     const float c3 = dt * dt * (1.f / 6.f), c6 = dt * (1.f / 6.f);
     const float b2 = 0.25f * dt;
@@ -249,6 +249,77 @@ __global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, 
             B.parts[K + k] = jprog;
             B.parts[2 * K + k] = P.w_u * jctl;
         }
+    }
+}
+
+// ------------------------------------------------------------------ (a) + (b) rotor-thrust-rate model
+// The paper's command (Sec. IV-A): the four rotor-thrust rates, the body rate following from
+// the rotors' torques (rk4_rotor).  The body rate now has dynamics of its own, so the attitude
+// is no longer a product of state-independent factors: one rollout per thread, sequential
+// over the horizon, drawing its noise (the same Philox blocks as the thrust / body-rate
+// model, scaled by sigma_tdot), storing noise and positions in the [K][H] arrays.
+constexpr int kRotorThreads = 64;
+
+__global__ void __launch_bounds__(kRotorThreads) rollout_rotor_kernel(StepParams P, StepBuffers B, int analytic) {
+    extern __shared__ float4 sU[];                 // [H]
+    __shared__ float sPose[kMaxGates * 8];
+    pdl_trigger();
+    pdl_wait();
+    for (int i = threadIdx.x; i < P.H; i += blockDim.x) sU[i] = B.nominal[i];
+    for (int i = threadIdx.x; i < P.G * 8; i += blockDim.x) sPose[i] = B.poses[i];
+    __syncthreads();
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P.K) return;
+    const int K = P.K, H = P.H;
+    const uint32_t st = B.step[0];
+    const float* s0 = B.state;
+    const Vec3 p0 = v3(s0[0], s0[1], s0[2]);
+    Vec3 p = p0, v = v3(s0[3], s0[4], s0[5]), w = v3(s0[10], s0[11], s0[12]);
+    Quat q{s0[6], s0[7], s0[8], s0[9]};
+    float T[4] = {s0[13], s0[14], s0[15], s0[16]};
+    Vec3 n_tgt;
+    const int tgt = target_gate(sPose, P.G, p0, &n_tgt);
+    const float* pose_t = sPose + 8 * (tgt < 0 ? 0 : tgt);
+    const Vec3 wp = v3(pose_t[0], pose_t[1], pose_t[2]);
+    float jctl = 0.f, jcol = 0.f, jvis = 0.f;
+    float4* noise_k = B.noise + static_cast<size_t>(k) * H;
+    float4* pos_k = B.pos + static_cast<size_t>(k) * H;
+    for (int h = 0; h < H; ++h) {
+        const float4 d = noise_from_block(P, noise_block(P, k, h, st));
+        noise_k[h] = d;
+        const float4 un = sU[h];
+        const float4 u = clip_control(P, make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w));
+        const float e0 = u.x - P.u_hover;
+        jctl += e0 * e0 + u.y * u.y + u.z * u.z + u.w * u.w;
+        rk4_rotor(P, p, v, q, w, T, u);
+        pos_k[h] = make_float4(p.x, p.y, p.z, 0.f);
+        if (P.paper) {
+            if (tgt >= 0) {
+                jvis += misalignment(q, p, wp);
+                if (analytic) jcol += fmaxf(P.d_safe - guide_sdf(to_gate(pose_t, p), P.a_in, P.tan_alpha), 0.f);
+            }
+        } else if (analytic) {
+            float smin = __int_as_float(0x7f800000);
+            for (int g = 0; g < P.G; ++g) {
+                const Vec3 pg = to_gate(sPose + 8 * g, p);
+                smin = fminf(smin, frame_sdf(pg.x, pg.y, pg.z, P.a_in, P.a_out, P.half_depth));
+            }
+            jcol += hinge_sq(smin, P.d_safe);
+        }
+    }
+    if (P.paper) {
+        const float dHx = p.x - wp.x, dHy = p.y - wp.y, dHz = p.z - wp.z;
+        const float d0x = p0.x - wp.x, d0y = p0.y - wp.y, d0z = p0.z - wp.z;
+        const float jgate = (tgt >= 0) ? (dHx * dHx + dHy * dHy + dHz * dHz) - (d0x * d0x + d0y * d0y + d0z * d0z) : 0.f;
+        B.parts[k] = analytic ? P.q_sdf * jcol : 0.f;
+        B.parts[K + k] = P.q_gate * jgate;
+        B.parts[2 * K + k] = P.q_vis * jvis;
+    } else {
+        const float jprog =
+            (tgt >= 0) ? -(n_tgt.x * (p.x - p0.x) + n_tgt.y * (p.y - p0.y) + n_tgt.z * (p.z - p0.z)) : 0.f;
+        B.parts[k] = analytic ? P.w_col * jcol : 0.f;
+        B.parts[K + k] = jprog;
+        B.parts[2 * K + k] = P.w_u * jctl;
     }
 }
 
@@ -493,7 +564,7 @@ __global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, S
     // U*_new[h] for h = blockIdx.x, blockIdx.x + nb, ...: thread t < nb loads block t's partial,
     // then a fixed-order tree in shared memory
     float4* sU = reinterpret_cast<float4*>(sRed);
-    const float uh = P.mass * P.gravity;
+    const float uh = P.u_hover;
     for (int h = blockIdx.x; h < H; h += nb) {
         float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
         if (threadIdx.x < nb) {
@@ -525,11 +596,19 @@ __global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, S
                 Vec3 p = v3(st[0], st[1], st[2]);
                 Vec3 v = v3(st[3], st[4], st[5]);
                 Quat q{st[6], st[7], st[8], st[9]};
-                rk4_step(P, p, v, q, u.x, v3(u.y, u.z, u.w));
+                if (P.rotor) {
+                    Vec3 w = v3(st[10], st[11], st[12]);
+                    float T[4] = {st[13], st[14], st[15], st[16]};
+                    rk4_rotor(P, p, v, q, w, T, u);
+                    st[10] = w.x; st[11] = w.y; st[12] = w.z;
+                    st[13] = T[0]; st[14] = T[1]; st[15] = T[2]; st[16] = T[3];
+                } else {
+                    rk4_step(P, p, v, q, u.x, v3(u.y, u.z, u.w));
+                    st[10] = u.y; st[11] = u.z; st[12] = u.w;
+                }
                 st[0] = p.x; st[1] = p.y; st[2] = p.z;
                 st[3] = v.x; st[4] = v.y; st[5] = v.z;
                 st[6] = q.w; st[7] = q.x; st[8] = q.y; st[9] = q.z;
-                st[10] = u.y; st[11] = u.z; st[12] = u.w;
                 const uint32_t lo = B.step[0] + 1u;
                 B.step[0] = lo;
                 if (lo == 0u) B.step[1] += 1u;
@@ -566,6 +645,9 @@ cudaError_t launch_noise_words(const StepParams& P, const StepBuffers& B, uint4*
 
 cudaError_t launch_rollout(const StepParams& P, const StepBuffers& B, int analytic, cudaStream_t s) {
     // first kernel of the step: ordered after the previous step's last kernel by the stream
+    if (P.rotor)
+        return launch_dependent(false, rollout_rotor_kernel, dim3((P.K + kRotorThreads - 1) / kRotorThreads),
+                                dim3(kRotorThreads), P.H * sizeof(float4), s, P, B, analytic);
     return launch_dependent(false, rollout_kernel, dim3((P.K + kRollWarps - 1) / kRollWarps), dim3(kRollWarps * 32),
                             P.H * sizeof(float4), s, P, B, analytic);
 }

@@ -18,6 +18,8 @@ using namespace mppi;
 
 namespace {
 thread_local char g_thread_err[512] = "";
+// floats reserved for the state in the device buffer and the host staging (>= MPPI_STATE_MAX)
+constexpr int kStateSlot = 24;
 }
 
 struct mppi_ctx {
@@ -125,10 +127,27 @@ StepParams make_params(const mppi_ctx* c) {
     P.q_vis = g.q_vis;
     P.q_sdf = g.q_sdf;
     P.tan_alpha = g.guide_tan_alpha;
+    P.rotor = g.dynamics_mode == MPPI_DYN_ROTOR ? 1 : 0;
+    P.u_hover = P.rotor ? 0.f : g.mass * g.gravity;
+    if (P.rotor) {
+        // the thrust-rate command: every channel in [-tdot_max, tdot_max], noise sigma_tdot
+        P.tmin = -g.tdot_max;
+        P.tmax = g.tdot_max;
+        P.rmax = g.tdot_max;
+        P.sig_t = g.sigma_tdot;
+        P.sig_r = g.sigma_tdot;
+    }
+    P.arm_d = g.arm_length * 0.70710678f;
+    P.kappa = g.torque_coeff;
+    P.inv_J = make_float3(1.f / g.inertia_x, 1.f / g.inertia_y, 1.f / g.inertia_z);
+    P.J = make_float3(g.inertia_x, g.inertia_y, g.inertia_z);
+    P.t_rotor_max = g.rotor_thrust_max;
     // per-kernel event timing measures kernels one after the other
     P.pdl = c->timing ? 0 : 1;
     return P;
 }
+
+int state_dim(const mppi_config& g) { return g.dynamics_mode == MPPI_DYN_ROTOR ? 17 : 13; }
 
 bool finite_all(const float* x, size_t n) {
     for (size_t i = 0; i < n; ++i)
@@ -148,6 +167,15 @@ int check_config(const mppi_config* g) {
         return fail(nullptr, MPPI_E_UNSUPPORTED, "sdf_mode=%d is not built", g->sdf_mode);
     if (g->cost_mode != MPPI_COST_CONFIGURED && g->cost_mode != MPPI_COST_PAPER)
         return fail(nullptr, MPPI_E_INVALID, "cost_mode=%d is not one of MPPI_COST_*", g->cost_mode);
+    if (g->dynamics_mode != MPPI_DYN_CTBR && g->dynamics_mode != MPPI_DYN_ROTOR)
+        return fail(nullptr, MPPI_E_INVALID, "dynamics_mode=%d is not one of MPPI_DYN_*", g->dynamics_mode);
+    if (g->dynamics_mode == MPPI_DYN_ROTOR) {
+        const float r[] = {g->tdot_max, g->rotor_thrust_max, g->sigma_tdot, g->arm_length, g->torque_coeff,
+                           g->inertia_x, g->inertia_y, g->inertia_z};
+        if (!finite_all(r, 8) || !(g->tdot_max >= 0.f) || !(g->rotor_thrust_max > 0.f) || g->sigma_tdot < 0.f ||
+            !(g->arm_length > 0.f) || !(g->inertia_x > 0.f) || !(g->inertia_y > 0.f) || !(g->inertia_z > 0.f))
+            return fail(nullptr, MPPI_E_INVALID, "rotor-model parameters");
+    }
     const float f[] = {g->dt, g->mass, g->gravity, g->thrust_min, g->thrust_max, g->rate_max, g->sigma_thrust,
                        g->sigma_rate, g->lambda, g->w_col, g->d_safe, g->w_u, g->gate_inner_half,
                        g->gate_outer_half, g->gate_half_depth, g->softplus_beta, g->q_gate, g->q_vis, g->q_sdf,
@@ -337,7 +365,18 @@ void mppi_config_default(mppi_config* g) {
     g->q_vis = 1.f;
     g->q_sdf = 10.f;
     g->guide_tan_alpha = 0.57735027f;   // tan(30 deg)
+    g->dynamics_mode = MPPI_DYN_CTBR;
+    g->tdot_max = 10.f;
+    g->rotor_thrust_max = 10.f;
+    g->sigma_tdot = 5.f;
+    g->arm_length = 0.15f;
+    g->torque_coeff = 0.016f;
+    g->inertia_x = 0.003f;
+    g->inertia_y = 0.003f;
+    g->inertia_z = 0.005f;
 }
+
+int mppi_state_dim(const mppi_config* g) { return g && g->dynamics_mode == MPPI_DYN_ROTOR ? 17 : 13; }
 
 const char* mppi_last_error(const mppi_ctx* c) { return c ? c->err : g_thread_err; }
 
@@ -397,7 +436,7 @@ int mppi_create(const mppi_config* cfg, void* cuda_stream, mppi_ctx** out) {
     const int nub = update_blocks(K);
     StepBuffers& B = c->B;
     rc = MPPI_OK;
-    rc = rc ? rc : dev_alloc(c, &B.state, 16);
+    rc = rc ? rc : dev_alloc(c, &B.state, kStateSlot);
     rc = rc ? rc : dev_alloc(c, &B.nominal, H);
     rc = rc ? rc : dev_alloc(c, &B.step, 2);
     rc = rc ? rc : dev_alloc(c, &B.poses, static_cast<size_t>(MG) * 8);
@@ -431,7 +470,7 @@ int mppi_create(const mppi_config* cfg, void* cuda_stream, mppi_ctx** out) {
         mppi_destroy(c);
         return rc;
     }
-    const size_t in_floats = 16 + static_cast<size_t>(H) * 4 + MG * 8 + MG * kLatent;
+    const size_t in_floats = kStateSlot + static_cast<size_t>(H) * 4 + MG * 8 + MG * kLatent;
     const size_t out_floats = static_cast<size_t>(H) * 4 + 2 * static_cast<size_t>(K) + 4;
     if (cudaMallocHost(&c->h_in, in_floats * sizeof(float)) != cudaSuccess ||
         cudaMallocHost(&c->h_out, out_floats * sizeof(float)) != cudaSuccess ||
@@ -454,15 +493,19 @@ int mppi_create(const mppi_config* cfg, void* cuda_stream, mppi_ctx** out) {
         }
     }
     // initial state: hover at the origin; nominal: H copies of u_hover; counter 0
+    // (rotor model: every rotor carrying m g / 4; nominal: zero thrust rates)
     float* st = c->h_in;
-    std::memset(st, 0, 16 * sizeof(float));
+    std::memset(st, 0, kStateSlot * sizeof(float));
     st[6] = 1.f;
-    float* nom = c->h_in + 16;
+    const bool rotor = cfg->dynamics_mode == MPPI_DYN_ROTOR;
+    if (rotor)
+        for (int i = 0; i < 4; ++i) st[13 + i] = 0.25f * cfg->mass * cfg->gravity;
+    float* nom = c->h_in + kStateSlot;
     for (int h = 0; h < H; ++h) {
-        nom[4 * h + 0] = cfg->mass * cfg->gravity;
+        nom[4 * h + 0] = rotor ? 0.f : cfg->mass * cfg->gravity;
         nom[4 * h + 1] = nom[4 * h + 2] = nom[4 * h + 3] = 0.f;
     }
-    bool ok = cudaMemcpyAsync(B.state, st, 16 * sizeof(float), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
+    bool ok = cudaMemcpyAsync(B.state, st, kStateSlot * sizeof(float), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
               cudaMemcpyAsync(B.nominal, nom, H * sizeof(float4), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
               cudaMemsetAsync(B.step, 0, 2 * sizeof(uint32_t), c->stream) == cudaSuccess &&
               cudaMemsetAsync(B.tickets, 0, 32 * sizeof(unsigned), c->stream) == cudaSuccess &&
@@ -488,7 +531,7 @@ int mppi_set_gates(mppi_ctx* c, int n_gates, const float* poses, const float* la
         return fail(c, MPPI_E_INVALID, "non-finite gate pose");
     if (latents && !finite_all(latents, static_cast<size_t>(n_gates) * kLatent))
         return fail(c, MPPI_E_INVALID, "non-finite latent");
-    float* hp = c->h_in + 16 + c->cfg.H * 4;
+    float* hp = c->h_in + kStateSlot + c->cfg.H * 4;
     float* hl = hp + c->cfg.max_gates * 8;
     for (int g = 0; g < n_gates; ++g) {
         for (int i = 0; i < 7; ++i) hp[8 * g + i] = poses[7 * g + i];
@@ -594,7 +637,7 @@ int mppi_step(mppi_ctx* c, const float* state, const float* gate_poses, const fl
     if (!c) return fail(nullptr, MPPI_E_INVALID, "ctx is NULL");
     if (!new_controls) return fail(c, MPPI_E_INVALID, "new_controls is NULL");
     const int K = c->cfg.K, H = c->cfg.H;
-    if (state && !finite_all(state, 13)) return fail(c, MPPI_E_INVALID, "non-finite state");
+    if (state && !finite_all(state, state_dim(c->cfg))) return fail(c, MPPI_E_INVALID, "non-finite state");
     if (nominal && !finite_all(nominal, static_cast<size_t>(H) * 4))
         return fail(c, MPPI_E_INVALID, "non-finite nominal");
     if (gate_poses || latents) {
@@ -605,7 +648,7 @@ int mppi_step(mppi_ctx* c, const float* state, const float* gate_poses, const fl
         } else {
             if (!finite_all(latents, static_cast<size_t>(c->n_gates) * kLatent))
                 return fail(c, MPPI_E_INVALID, "non-finite latent");
-            float* hl = c->h_in + 16 + H * 4 + c->cfg.max_gates * 8;
+            float* hl = c->h_in + kStateSlot + H * 4 + c->cfg.max_gates * 8;
             CUDA_TRY(c, cudaStreamSynchronize(c->stream));
             std::memcpy(hl, latents, static_cast<size_t>(c->n_gates) * kLatent * sizeof(float));
             if (c->n_gates > 0)
@@ -620,12 +663,13 @@ int mppi_step(mppi_ctx* c, const float* state, const float* gate_poses, const fl
     if (rc != MPPI_OK) return rc;
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // staging buffers are free
     if (state) {
-        std::memcpy(c->h_in, state, 13 * sizeof(float));
-        CUDA_TRY(c, cudaMemcpyAsync(c->B.state, c->h_in, 13 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        std::memcpy(c->h_in, state, state_dim(c->cfg) * sizeof(float));
+        CUDA_TRY(c, cudaMemcpyAsync(c->B.state, c->h_in, state_dim(c->cfg) * sizeof(float), cudaMemcpyHostToDevice,
+                                    c->stream));
     }
     if (nominal) {
-        std::memcpy(c->h_in + 16, nominal, static_cast<size_t>(H) * 4 * sizeof(float));
-        CUDA_TRY(c, cudaMemcpyAsync(c->B.nominal, c->h_in + 16, H * sizeof(float4), cudaMemcpyHostToDevice,
+        std::memcpy(c->h_in + kStateSlot, nominal, static_cast<size_t>(H) * 4 * sizeof(float));
+        CUDA_TRY(c, cudaMemcpyAsync(c->B.nominal, c->h_in + kStateSlot, H * sizeof(float4), cudaMemcpyHostToDevice,
                                     c->stream));
     }
     // the step's last kernel writes U*_new (and w, J when asked for) straight into the
@@ -656,7 +700,9 @@ int mppi_step_async(mppi_ctx* c, const float* d_state, const float* d_gate_poses
                     const float* d_nominal, float* d_new_controls, float* d_weights, float* d_costs) {
     if (!c) return fail(nullptr, MPPI_E_INVALID, "ctx is NULL");
     const int K = c->cfg.K, H = c->cfg.H, G = c->n_gates;
-    if (d_state) CUDA_TRY(c, cudaMemcpyAsync(c->B.state, d_state, 13 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    if (d_state)
+        CUDA_TRY(c, cudaMemcpyAsync(c->B.state, d_state, state_dim(c->cfg) * sizeof(float), cudaMemcpyDeviceToDevice,
+                                    c->stream));
     if (d_gate_poses && G > 0)
         CUDA_TRY(c, cudaMemcpy2DAsync(c->B.poses, 8 * sizeof(float), d_gate_poses, 7 * sizeof(float),
                                       7 * sizeof(float), G, cudaMemcpyDeviceToDevice, c->stream));
@@ -693,7 +739,7 @@ int mppi_get_nominal(mppi_ctx* c, float* out) {
 
 int mppi_get_state(mppi_ctx* c, float* out) {
     if (!c || !out) return fail(c, MPPI_E_INVALID, "NULL argument");
-    CUDA_TRY(c, cudaMemcpyAsync(out, c->B.state, 13 * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(out, c->B.state, state_dim(c->cfg) * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     return read_err_word(c);
 }
 
@@ -801,23 +847,23 @@ void set_thread_error(const char* msg) { std::snprintf(g_thread_err, sizeof(g_th
 int ctx_enqueue_host_step(mppi_ctx* c, const float* state, int n_gates, const float* poses, const float* latents) {
     const int H = c->cfg.H;
     if (n_gates < 0 || n_gates > c->cfg.max_gates) return fail(c, MPPI_E_INVALID, "n_gates out of range");
-    if (!finite_all(state, 13)) return fail(c, MPPI_E_INVALID, "non-finite state");
+    if (!finite_all(state, state_dim(c->cfg))) return fail(c, MPPI_E_INVALID, "non-finite state");
     if (n_gates > 0 && (!poses || !finite_all(poses, static_cast<size_t>(n_gates) * 7)))
         return fail(c, MPPI_E_INVALID, "bad gate poses");
     if (n_gates > 0 && is_mlp(c) && (!latents || !finite_all(latents, static_cast<size_t>(n_gates) * kLatent)))
         return fail(c, MPPI_E_INVALID, "bad latents");
     // the staging buffers are free: the caller has one request per context in flight
     float* hs = c->h_in;
-    float* hp = c->h_in + 16 + H * 4;
+    float* hp = c->h_in + kStateSlot + H * 4;
     float* hl = hp + c->cfg.max_gates * 8;
-    std::memcpy(hs, state, 13 * sizeof(float));
+    std::memcpy(hs, state, state_dim(c->cfg) * sizeof(float));
     for (int g = 0; g < n_gates; ++g) {
         for (int i = 0; i < 7; ++i) hp[8 * g + i] = poses[7 * g + i];
         hp[8 * g + 7] = 0.f;
     }
     if (c->n_gates != n_gates) c->graph_dirty = true;
     c->n_gates = n_gates;
-    CUDA_TRY(c, cudaMemcpyAsync(c->B.state, hs, 13 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->B.state, hs, state_dim(c->cfg) * sizeof(float), cudaMemcpyHostToDevice, c->stream));
     if (n_gates > 0) {
         CUDA_TRY(c, cudaMemcpyAsync(c->B.poses, hp, n_gates * 8 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
         if (latents) {
@@ -869,10 +915,11 @@ int ctx_save(mppi_ctx* c, float* nominal, float* state, uint64_t* step) {
 int ctx_restore(mppi_ctx* c, const float* nominal, const float* state, uint64_t step) {
     const int H = c->cfg.H;
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    std::memcpy(c->h_in, state, 13 * sizeof(float));
-    std::memcpy(c->h_in + 16, nominal, static_cast<size_t>(H) * 4 * sizeof(float));
-    CUDA_TRY(c, cudaMemcpyAsync(c->B.state, c->h_in, 13 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-    CUDA_TRY(c, cudaMemcpyAsync(c->B.nominal, c->h_in + 16, H * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
+    std::memcpy(c->h_in, state, state_dim(c->cfg) * sizeof(float));
+    std::memcpy(c->h_in + kStateSlot, nominal, static_cast<size_t>(H) * 4 * sizeof(float));
+    CUDA_TRY(c, cudaMemcpyAsync(c->B.state, c->h_in, state_dim(c->cfg) * sizeof(float), cudaMemcpyHostToDevice,
+                                c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->B.nominal, c->h_in + kStateSlot, H * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return mppi_set_step_counter(c, step);
 }

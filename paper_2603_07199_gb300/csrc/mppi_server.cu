@@ -38,14 +38,14 @@ struct Drone {
     uint64_t last_use = 0;
     bool saved = false;               // warm start held in host memory after an eviction
     std::vector<float> nominal;
-    float state[13] = {};
+    float state[MPPI_STATE_MAX] = {};
     uint64_t step = 0;
 };
 
 struct Request {
     uint64_t ticket = 0;
     int drone = 0;
-    float state[13] = {};
+    float state[MPPI_STATE_MAX] = {};
     int n_gates = 0;
     std::vector<float> poses, latents;
     Clock::time_point t_submit;
@@ -310,10 +310,10 @@ int mppi_server_submit(mppi_server* s, int drone_id, const mppi_config* cfg, con
     if (n_gates > 0 && !poses) return sfail(s, MPPI_E_INVALID, "poses is NULL");
     if (s->cfg.sdf_mode != MPPI_SDF_ANALYTIC && n_gates > 0 && !latents)
         return sfail(s, MPPI_E_INVALID, "latents are required by the MLP SDF");
-    if (!finite(state, 13)) return sfail(s, MPPI_E_INVALID, "non-finite state");
+    if (!finite(state, mppi_state_dim(cfg))) return sfail(s, MPPI_E_INVALID, "non-finite state");
     Request r;
     r.drone = drone_id;
-    std::memcpy(r.state, state, sizeof(r.state));
+    std::memcpy(r.state, state, sizeof(float) * mppi_state_dim(cfg));
     r.n_gates = n_gates;
     if (n_gates > 0) r.poses.assign(poses, poses + 7 * n_gates);
     if (n_gates > 0 && latents) r.latents.assign(latents, latents + MPPI_LATENT_DIM * n_gates);

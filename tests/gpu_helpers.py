@@ -21,6 +21,14 @@ def make_config(prm, mode, max_gates):
     for key in ("q_gate", "q_vis", "q_sdf", "guide_tan_alpha"):
         if key in prm:
             setattr(cfg, key, prm[key])
+    cfg.dynamics_mode = {"ctbr": B.MPPI_DYN_CTBR, "rotor": B.MPPI_DYN_ROTOR}[prm.get("dynamics", "ctbr")]
+    for key in ("tdot_max", "rotor_thrust_max", "sigma_tdot", "arm_length"):
+        if key in prm:
+            setattr(cfg, key, prm[key])
+    if "kappa" in prm:
+        cfg.torque_coeff = prm["kappa"]
+    if "inertia" in prm:
+        cfg.inertia_x, cfg.inertia_y, cfg.inertia_z = prm["inertia"]
     return cfg
 
 
@@ -85,7 +93,7 @@ class GpuController:
         return out
 
     def state(self):
-        s = np.zeros(13, dtype=np.float32)
+        s = np.zeros(B.mppi_state_dim(self.cfg), dtype=np.float32)
         B.mppi_get_state(self.ctx, s)
         return s
 

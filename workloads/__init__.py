@@ -49,6 +49,27 @@ def paper_params(K, H, **over):
     return d
 
 
+def rotor_params(K, H, **over):
+    """Parameters of the paper's rotor-thrust-rate model: its Table I bounds (thrust rates in
+    [-10, 10] N/s, rotor thrusts in [0, 10] N) and the airframe readings (arm 0.15 m, reaction
+    torque 0.016 m per newton, inertia diag(0.003, 0.003, 0.005) kg m^2), noise 5 N/s."""
+    d = params(K, H, dynamics="rotor", tdot_max=10.0, rotor_thrust_max=10.0, sigma_tdot=5.0,
+               arm_length=0.15, kappa=0.016, inertia=(0.003, 0.003, 0.005))
+    d.update(over)
+    return d
+
+
+def rotor_state(position, mass=0.8, gravity=9.81, yaw=0.0, rates=(0.0, 0.0, 0.0), thrust_offsets=(0.0, 0.0, 0.0, 0.0)):
+    """A 17-number rotor-model state: at rest at `position` with heading `yaw`, body rates
+    `rates`, every rotor carrying m g / 4 plus its offset (float32)."""
+    s = np.zeros(17, dtype=np.float32)
+    s[0:3] = position
+    s[6], s[9] = math.cos(0.5 * yaw), math.sin(0.5 * yaw)
+    s[10:13] = rates
+    s[13:17] = 0.25 * mass * gravity + np.asarray(thrust_offsets, dtype=np.float32)
+    return s
+
+
 def yaw_pitch_quat(yaw, pitch):
     """Unit quaternion (w, x, y, z) of a yaw about world z followed by a pitch about the
     yawed y axis, written out in closed form from the half-angle sines and cosines."""
