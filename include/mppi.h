@@ -100,6 +100,10 @@ extern "C" {
  *   sigma_tdot                        MPPI_DYN_ROTOR noise standard deviation (N/s)
  *   arm_length, torque_coeff          X layout arm (m) and rotor reaction torque per newton (m)
  *   inertia_x, inertia_y, inertia_z   diagonal inertia (kg m^2)
+ *   pe_levels                         positional-encoding levels L of the decoder's query point
+ *                                     (Sec. III-B): the MLP sees [PE(p), z] with PE(p) = [p, then
+ *                                     sin(2^l pi p), cos(2^l pi p) for l < L] (3 + 6 L numbers);
+ *                                     0 .. MPPI_MAX_PE_LEVELS, 0 = the raw point
  */
 typedef struct mppi_config {
     int32_t K;
@@ -121,7 +125,10 @@ typedef struct mppi_config {
     float tdot_max, rotor_thrust_max, sigma_tdot;
     float arm_length, torque_coeff;
     float inertia_x, inertia_y, inertia_z;
+    int32_t pe_levels;
 } mppi_config;
+
+#define MPPI_MAX_PE_LEVELS 6
 
 /* Dynamics models (mppi_config.dynamics_mode). */
 #define MPPI_DYN_CTBR   0       /* state [p, v, q, w] (13); u = [T, wx, wy, wz], ideal body-rate tracking */
@@ -172,10 +179,10 @@ int mppi_set_gates(mppi_ctx* ctx, int n_gates, const float* poses, const float* 
 /*
  * Set the Gate-SDF MLP weights (host pointers, FP32): layers[2*i] is W_i
  * [out_i x in_i] row-major and layers[2*i+1] its bias [out_i], for the five
- * affine maps 67 -> 128 -> 128 -> 128 -> 128 -> 1 (n_layers = 10 pointers).
- * The library keeps FP32 copies and the BF16 / FP16 / E4M3 copies the
- * tensor-core paths use, and precomputes the per-gate first-layer bias
- * W1[:, 3:] z_g + b1.  fp8_scales (MPPI_SDF_MLP_FP8 only; nullable): 3
+ * affine maps (3 + 6 pe_levels + 64) -> 128 -> 128 -> 128 -> 128 -> 1 (67 -> ... without
+ * positional encoding; n_layers = 10 pointers).  The library keeps FP32 copies and the
+ * BF16 / FP16 / E4M3 copies the tensor-core paths use, and precomputes the per-gate
+ * first-layer bias W1[:, P:] z_g + b1 (P = 3 + 6 pe_levels).  fp8_scales (MPPI_SDF_MLP_FP8 only; nullable): 3
  * per-tensor scales of the E4M3 activations entering the three hidden
  * 128 x 128 layers, in softplus-output units (an activation a is stored as
  * E4M3(a / scale), saturating at 448 scale); NULL selects 1/64.  The E4M3

@@ -45,11 +45,23 @@ def forward(layers, x, beta=BETA):
     return (h @ W.T + b)[:, 0]
 
 
-def sdf(layers, pg, z, beta=BETA):
-    """g_phi(z, p) for gate-frame points pg [N, 3] and one latent z [Z]."""
+def positional_encoding(p, levels):
+    """PE(p) of Sec. III-B (applied to the query coordinates before concatenation with z):
+    [p, then for l = 0 .. levels-1: sin(2^l pi p), cos(2^l pi p)] -> [N, 3 + 6 levels];
+    levels = 0 is the point itself."""
+    p = np.asarray(p, dtype=np.float64)
+    feats = [p]
+    for l in range(levels):
+        a = (2.0 ** l) * np.pi * p
+        feats += [np.sin(a), np.cos(a)]
+    return np.concatenate(feats, axis=-1)
+
+
+def sdf(layers, pg, z, beta=BETA, pe_levels=0):
+    """g_phi(z, PE(p)) for query points pg [N, 3] in the latent's frame and one latent z [Z]."""
     pg = np.asarray(pg, dtype=np.float64)
     z = np.asarray(z, dtype=np.float64)
-    x = np.concatenate([pg, np.broadcast_to(z, (pg.shape[0], z.shape[0]))], axis=1)
+    x = np.concatenate([positional_encoding(pg, pe_levels), np.broadcast_to(z, (pg.shape[0], z.shape[0]))], axis=1)
     return forward(layers, x, beta)
 
 

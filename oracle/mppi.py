@@ -73,6 +73,8 @@ class Params:
     arm_length: float = 0.15
     kappa: float = 0.016
     inertia: tuple = (0.003, 0.003, 0.005)
+    # positional-encoding levels of the Gate-SDF decoder's query point (0: the raw point)
+    pe_levels: int = 0
 
     def u_hover(self):
         if self.dynamics == "rotor":
@@ -104,7 +106,7 @@ def target_gate(state, poses):
     return poses.shape[0] - 1
 
 
-def min_gate_sdf(positions, poses, latents=None, layers=None):
+def min_gate_sdf(positions, poses, latents=None, layers=None, pe_levels=0):
     """s(p) = min over gates of the gate SDF at world points positions [..., 3].
 
     With ``layers`` the Gate-SDF MLP is queried at the gate-frame point with
@@ -119,7 +121,7 @@ def min_gate_sdf(positions, poses, latents=None, layers=None):
         if layers is None:
             s = gate_sdf.frame_sdf(pg)
         else:
-            s = mlp.sdf(layers, pg, latents[g])
+            s = mlp.sdf(layers, pg, latents[g], pe_levels=pe_levels)
         best = np.minimum(best, s.reshape(shape))
     return best
 
@@ -127,7 +129,7 @@ def min_gate_sdf(positions, poses, latents=None, layers=None):
 def rollout_costs(state, U, positions, poses, prm, latents=None, layers=None):
     """Cost terms of every rollout: dict of J_col, J_prog, J_ctl, J (each [K]) and sdf [K, H]."""
     p0 = np.asarray(state, dtype=np.float64)[0:3]
-    s = min_gate_sdf(positions, poses, latents, layers)
+    s = min_gate_sdf(positions, poses, latents, layers, prm.pe_levels)
     J_col = prm.w_col * np.sum(np.maximum(0.0, prm.d_safe - s) ** 2, axis=1)
     g = target_gate(state, poses)
     if g < 0:
@@ -172,7 +174,7 @@ def paper_costs(state, positions, attitudes, poses, prm, latents=None, layers=No
     if layers is None:
         s = gate_sdf.guide_sdf(pg, c=gate_sdf.GATE_INNER_HALF, alpha=np.arctan(prm.guide_tan_alpha))
     else:
-        s = mlp.sdf(layers, pg, latents[g])
+        s = mlp.sdf(layers, pg, latents[g], pe_levels=prm.pe_levels)
     s = s.reshape(K, H)
     J_sdf = np.sum(np.maximum(0.0, prm.d_safe - s), axis=1)
     parts = dict(J_col=prm.q_sdf * J_sdf, J_prog=prm.q_gate * J_gate, J_ctl=prm.q_vis * J_vis)

@@ -32,6 +32,7 @@ MPPI_COST_PAPER = 1
 MPPI_DYN_CTBR = 0
 MPPI_DYN_ROTOR = 1
 MPPI_STATE_MAX = 17
+MPPI_MAX_PE_LEVELS = 6
 
 MPPI_BUF_NOISE = 0
 MPPI_BUF_POSITIONS = 1
@@ -80,6 +81,7 @@ class MppiConfig(ctypes.Structure):
         ("dynamics_mode", ctypes.c_int32), ("tdot_max", ctypes.c_float), ("rotor_thrust_max", ctypes.c_float),
         ("sigma_tdot", ctypes.c_float), ("arm_length", ctypes.c_float), ("torque_coeff", ctypes.c_float),
         ("inertia_x", ctypes.c_float), ("inertia_y", ctypes.c_float), ("inertia_z", ctypes.c_float),
+        ("pe_levels", ctypes.c_int32),
     ]
 
 

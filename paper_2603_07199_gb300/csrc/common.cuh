@@ -16,6 +16,15 @@ constexpr int kMaxRollouts = 1 << 20;
 // device error word values
 constexpr int kDevErrTimeout = 1;
 
+// Columns of the layer-1 tensor-core GEMM: 0..8 the query point split [hi, lo, hi] (against
+// [W_hi, W_hi, W_lo]), 9..15 zero, then one 8-column core-matrix chunk per positional-encoding
+// level l: columns 16 + 8 l + (0..5) = sin(2^l pi p) (x, y, z), cos(2^l pi p) (x, y, z).
+// K = 16 + 8 L rounded up to a multiple of 16 (16 .. 64).
+__host__ __device__ inline int layer1_gemm_k(int pe_levels) {
+    return pe_levels == 0 ? 16 : ((16 + 8 * pe_levels + 15) / 16) * 16;
+}
+__host__ __device__ inline int pe_column(int level, int t) { return 16 + 8 * level + t; }
+
 // Scalars every step kernel needs, passed by value.
 struct StepParams {
     int K, H, G;
@@ -33,6 +42,7 @@ struct StepParams {
     float u_hover;         // first control channel of the hover command (m g, or 0 for thrust rates)
     float arm_d, kappa, t_rotor_max;  // rotor offset l / sqrt(2), reaction torque per newton, thrust bound
     float3 J, inv_J;       // diagonal inertia and its reciprocal
+    int pe;                // positional-encoding levels of the decoder's query point
 };
 
 // Device buffers of one controller.

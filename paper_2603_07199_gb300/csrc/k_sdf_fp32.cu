@@ -11,6 +11,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kLdA = kTileRows + 4;     // activations stored feature-major: act[feature][row]
+constexpr int kMaxPoint = 3 + 6 * 6;    // point features with the most positional-encoding levels
 
 // sp(x) = max(x, 0) + log1p(exp(-beta |x|)) / beta, accurate FP32 library calls
 __device__ __forceinline__ float softplus_acc(float x, float beta, float inv_beta) {
@@ -25,19 +26,23 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_fp32_kernel(StepParams P,
     extern __shared__ __align__(16) float smem[];
     float* act = smem;                              // [128][kLdA]
     float* wt = act + kHidden * kLdA;               // [128 in][128 out]
-    float* sW1 = wt + kHidden * kHidden;            // [3][128]   W1[:, 0:3] transposed
-    float* sB1 = sW1 + 3 * kHidden;                 // [G][128]   per-gate first-layer bias
+    float* sW1 = wt + kHidden * kHidden;            // [NP][128]  W1[:, 0:NP] transposed (NP point features)
+    float* sB1 = sW1 + kMaxPoint * kHidden;         // [G][128]   per-gate first-layer bias
     float* sBias = sB1 + kMaxGates * kHidden;       // [3][128]   b2, b3, b4
     float* sW5 = sBias + 3 * kHidden;               // [128]
-    float* sPg = sW5 + kHidden;                     // [3][128]   gate-frame points of the tile
-    float* sMin = sPg + 3 * kTileRows;              // [128]      min over gates
+    float* sPg = sW5 + kHidden;                     // [NP][128]  point features of the tile's rows
+    float* sMin = sPg + kMaxPoint * kTileRows;      // [128]      min over gates
     float* sPose = sMin + kTileRows;                // [G][8]
 
     const int tid = threadIdx.x;
     const int G = P.G;
+    const int NP = 3 + 6 * P.pe;                    // point features: p and its positional encoding
+    for (int i = tid; i < NP * kHidden; i += kThreads) {
+        const int j = i / kHidden, n = i - j * kHidden;
+        sW1[i] = W.W1[n * (NP + kLatent) + j];
+    }
     for (int i = tid; i < 3 * kHidden; i += kThreads) {
         const int j = i / kHidden, n = i - j * kHidden;
-        sW1[i] = W.W1[n * (3 + kLatent) + j];
         sBias[i] = W.b[j][n];
     }
     for (int i = tid; i < G * kHidden; i += kThreads) sB1[i] = B.b1p[i];
@@ -70,18 +75,28 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_fp32_kernel(StepParams P,
                 sPg[tid] = pg.x;
                 sPg[kTileRows + tid] = pg.y;
                 sPg[2 * kTileRows + tid] = pg.z;
+                // positional encoding (Sec. III-B): sin, cos of 2^l pi p per level
+                for (int l = 0; l < P.pe; ++l) {
+                    const float sc = static_cast<float>(1 << l);
+                    float s0, c0, s1, c1, s2, c2;
+                    sincospif(sc * pg.x, &s0, &c0);
+                    sincospif(sc * pg.y, &s1, &c1);
+                    sincospif(sc * pg.z, &s2, &c2);
+                    float* f = sPg + (3 + 6 * l) * kTileRows + tid;
+                    f[0] = s0; f[kTileRows] = s1; f[2 * kTileRows] = s2;
+                    f[3 * kTileRows] = c0; f[4 * kTileRows] = c1; f[5 * kTileRows] = c2;
+                }
             }
             __syncthreads();
             // layer 1: [p, z] -> 128, with the latent part folded into the per-gate bias
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int r = strip(tr, i);
-                const float x0 = sPg[r], x1 = sPg[kTileRows + r], x2 = sPg[2 * kTileRows + r];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int n = strip(tn, j);
-                    const float a = sB1[g * kHidden + n] + sW1[n] * x0 + sW1[kHidden + n] * x1 +
-                                    sW1[2 * kHidden + n] * x2;
+                    float a = sB1[g * kHidden + n];
+                    for (int f = 0; f < NP; ++f) a += sW1[f * kHidden + n] * sPg[f * kTileRows + r];
                     act[n * kLdA + r] = softplus_acc(a, beta, inv_beta);
                 }
             }
@@ -160,8 +175,8 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_fp32_kernel(StepParams P,
     }
 }
 
-constexpr size_t kSmemBytes = sizeof(float) * (kHidden * kLdA + kHidden * kHidden + 3 * kHidden +
-                                                kMaxGates * kHidden + 3 * kHidden + kHidden + 3 * kTileRows +
+constexpr size_t kSmemBytes = sizeof(float) * (kHidden * kLdA + kHidden * kHidden + kMaxPoint * kHidden +
+                                                kMaxGates * kHidden + 3 * kHidden + kHidden + kMaxPoint * kTileRows +
                                                 kTileRows + kMaxGates * 8);
 
 }  // namespace

@@ -40,6 +40,10 @@ constexpr int kThreads = kGroups * kGroupThreads;
 constexpr int kHalf = kHidden / kHalves;            // accumulator columns per thread
 constexpr uint32_t kTileBytes = kHidden * kHidden * 2;     // one 128 x 128 BF16 operand
 constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kL1Bytes = 5 * kHidden * 16 * 2;            // 20 KB, see TcShared::l1
+constexpr uint32_t kOnesOff = kHidden * 16 * 2;
+constexpr uint32_t kSlabOff = 2 * kHidden * 16 * 2;
+constexpr uint32_t kSlabBytes = kHidden * 16 * 2;
 constexpr uint32_t kIdescFull = tc::idesc_bf16_f32(128, 128);
 constexpr uint32_t kIdescFullF16 = tc::idesc_f16_f32(128, 128);
 constexpr uint32_t kIdescE4M3 = tc::idesc_e4m3_f32(128, 128);
@@ -47,9 +51,12 @@ constexpr uint32_t kIdescE4M3 = tc::idesc_e4m3_f32(128, 128);
 struct __align__(16) TcShared {
     uint8_t w[3][kTileBytes];                 // W2, W3, W4 (B operands, N = out, K = in)
     uint8_t a[kGroups][kTileBytes];           // activation tiles (A operands, M = rows, K = features)
-    uint8_t w1[kHidden * 16 * 2];             // layer-1 B operand: c W1[:, 0:3] split hi/lo (BF16, K = 16)
-    uint8_t ones[kHidden * 16 * 2];           // K = 16 A operand with columns 0, 1 = 1 (16-bit hidden paths)
-    uint8_t bslab[3][kHidden * 16 * 2];       // K = 16 B operands: columns 0, 1 = hi, lo of c b2, c b3, c b4
+    // layer-1 B operand and, without positional encoding, the bias operands of the hidden GEMMs:
+    //   [0, 4 KB)   layer-1 B: c W1[:, 0:3] split hi/lo (BF16, K = 16)
+    //   [4, 8 KB)   K = 16 A operand with columns 0, 1 = 1 (16-bit hidden paths)
+    //   [8, 20 KB)  three K = 16 B operands: columns 0, 1 = hi, lo of c b2, c b3, c b4
+    // with positional encoding: [0, 16 KB) layer-1 B with K = 16 .. 64 (the PE columns in BF16)
+    uint8_t l1[kL1Bytes];
     float b1[kMaxGates][kHidden];             // c (per-gate first-layer bias)
     float bias[3][kHidden];                   // c b2, c b3, c b4 (E4M3 path: added in the epilogue)
     float w5[kHidden];                        // (ln 2 / beta) w5
@@ -243,10 +250,11 @@ __device__ __forceinline__ float from_operand16(uint16_t v) {
     }
 }
 
-template <int kFmt>
+template <int kFmt, bool kPE>
 __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, StepBuffers B, MlpWeights W) {
     constexpr bool kF16 = (kFmt == kFmtFP16);
     constexpr bool kF8 = (kFmt == kFmtE4M3);
+    constexpr bool kFold = !kF8 && !kPE;           // hidden biases ride in the GEMM (bias operands)
     // the kernel has no static shared memory, so the dynamic block starts at the
     // (1024-byte aligned) base of the CTA's window; indexing it directly keeps the
     // shared address space visible to the compiler (no generic loads)
@@ -275,27 +283,30 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
         for (int i = tid; i < n16; i += kThreads) dst[i] = __ldg(src + i);
     }
     const float cl2 = P.beta * 1.4426950408889634f;          // beta log2(e)
-    for (int i = tid; i < int(sizeof(S.w1) / 16); i += kThreads)
-        reinterpret_cast<uint4*>(S.w1)[i] = __ldg(reinterpret_cast<const uint4*>(W.W1tc) + i);
+    // layer-1 B operand: K = k1 columns (SBO k1 / 8 core matrices of 128 B)
+    const int k1 = kPE ? layer1_gemm_k(P.pe) : 16;
+    for (int i = tid; i < k1 * kHidden * 2 / 16; i += kThreads)
+        reinterpret_cast<uint4*>(S.l1)[i] = __ldg(reinterpret_cast<const uint4*>(W.W1tc) + i);
     for (int i = tid; i < 3 * kHidden; i += kThreads) {
         const int j = i / kHidden, n = i - j * kHidden;
         const float b = cl2 * W.b[j][n];
         S.bias[j][n] = b;
-        if constexpr (!kF8) {
+        if constexpr (kFold) {
             // bias row n of layer j as the K = 16 operand row [hi, lo, 0, ..., 0]
             const uint16_t hi = to_operand16<kFmt>(b);
             const uint16_t lo = to_operand16<kFmt>(b - from_operand16<kFmt>(hi));
+            uint8_t* slab = S.l1 + kSlabOff + j * kSlabBytes;
             const uint32_t off = static_cast<uint32_t>((n >> 3) * 256 + (n & 7) * 16);
-            *reinterpret_cast<uint4*>(S.bslab[j] + off) = make_uint4(static_cast<uint32_t>(hi) | (static_cast<uint32_t>(lo) << 16), 0u, 0u, 0u);
-            *reinterpret_cast<uint4*>(S.bslab[j] + off + 128) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(slab + off) = make_uint4(static_cast<uint32_t>(hi) | (static_cast<uint32_t>(lo) << 16), 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(slab + off + 128) = make_uint4(0u, 0u, 0u, 0u);
         }
     }
-    if constexpr (!kF8) {
+    if constexpr (kFold) {
         const uint32_t one = kF16 ? 0x3C003C00u : 0x3F803F80u;   // (1, 1) in the operand type
         for (int r = tid; r < kTileRows; r += kThreads) {
             const uint32_t off = static_cast<uint32_t>((r >> 3) * 256 + (r & 7) * 16);
-            *reinterpret_cast<uint4*>(S.ones + off) = make_uint4(one, 0u, 0u, 0u);
-            *reinterpret_cast<uint4*>(S.ones + off + 128) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(S.l1 + kOnesOff + off) = make_uint4(one, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(S.l1 + kOnesOff + off + 128) = make_uint4(0u, 0u, 0u, 0u);
         }
     }
     for (int i = tid; i < G * kHidden; i += kThreads) S.b1[i / kHidden][i % kHidden] = cl2 * B.b1p[i];
@@ -348,8 +359,11 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
         tc::fence_after_sync();
         const uint64_t ad = tc::smem_desc(a_base, 128, 2048);
         if (l == 0) {
-            // layer 1: K = 16 (hi/lo split point x weights), always BF16
-            tc::mma_bf16(d_tmem, ad, tc::smem_desc(tc::smem_u32(S.w1), 128, 256), kIdescFull, 0u);
+            // layer 1: K = k1 (hi/lo split point x weights, then the PE columns), always BF16
+            const uint64_t b1d = tc::smem_desc(tc::smem_u32(S.l1), 128, static_cast<uint32_t>(k1 / 8 * 128));
+            for (int s = 0; s < k1 / 16; ++s)
+                tc::mma_bf16(d_tmem, ad + static_cast<uint64_t>(s * 16), b1d + static_cast<uint64_t>(s * 16), kIdescFull,
+                             s > 0 ? 1u : 0u);
         } else if constexpr (kF8) {
             // E4M3 x E4M3 -> FP32, K = 32 per instruction (256 B along K), SBO 1024 B
             const uint64_t a8 = tc::smem_desc(a_base, 128, 1024);
@@ -365,9 +379,11 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
             for (int s = 0; s < kHidden / 16; ++s)   // K = 16 per instruction: 256 B along K
                 tc::mma_bf16(d_tmem, ad + static_cast<uint64_t>(s * 16), bd + static_cast<uint64_t>(s * 16), idesc,
                              s > 0 ? 1u : 0u);
-            // + bias: ones (M x 16) against [hi, lo, 0..] (N x 16)
-            tc::mma_bf16(d_tmem, tc::smem_desc(tc::smem_u32(S.ones), 128, 256),
-                         tc::smem_desc(tc::smem_u32(S.bslab[l - 1]), 128, 256), idesc, 1u);
+            if constexpr (kFold) {
+                // + bias: ones (M x 16) against [hi, lo, 0..] (N x 16)
+                tc::mma_bf16(d_tmem, tc::smem_desc(tc::smem_u32(S.l1 + kOnesOff), 128, 256),
+                             tc::smem_desc(tc::smem_u32(S.l1 + kSlabOff + (l - 1) * kSlabBytes), 128, 256), idesc, 1u);
+            }
         }
         tc::mma_commit(acc_bar);
         ++outstanding;
@@ -392,6 +408,31 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                 tc::st_shared_v4(a_base + tc::operand_offset_bytes(row, 0), tc::pack_bf16x2(hx, hy),
                                  tc::pack_bf16x2(hz, lx), tc::pack_bf16x2(ly, lz), tc::pack_bf16x2(hx, hy));
                 tc::st_shared_v4(a_base + tc::operand_offset_bytes(row, 8), tc::pack_bf16x2(hz, 0.f), 0u, 0u, 0u);
+                if constexpr (kPE) {
+                    // positional encoding (Sec. III-B): sin, cos of 2^l pi p, one 8-column chunk per
+                    // level; level 0 from the hardware sine / cosine, each next level by doubling the
+                    // angle (the features are rounded to BF16, 2^-9, far above the doubling's error)
+                    float sx, cx, sy, cy, sz, cz;
+                    __sincosf(3.14159265358979f * pg.x, &sx, &cx);
+                    __sincosf(3.14159265358979f * pg.y, &sy, &cy);
+                    __sincosf(3.14159265358979f * pg.z, &sz, &cz);
+                    for (int lv = 0; lv < P.pe; ++lv) {
+                        tc::st_shared_v4(a_base + tc::operand_offset_bytes(row, pe_column(lv, 0)), tc::pack_bf16x2(sx, sy),
+                                         tc::pack_bf16x2(sz, cx), tc::pack_bf16x2(cy, cz), 0u);
+                        const float nsx = 2.f * sx * cx, nsy = 2.f * sy * cy, nsz = 2.f * sz * cz;
+                        cx = (cx - sx) * (cx + sx);
+                        cy = (cy - sy) * (cy + sy);
+                        cz = (cz - sz) * (cz + sz);
+                        sx = nsx;
+                        sy = nsy;
+                        sz = nsz;
+                    }
+                    // chunks the GEMM's K (a multiple of 16) covers beyond the last level: zero (the
+                    // tile holds the previous layer's activations there, E4M3 bytes among them,
+                    // which read as BF16 could be Inf or NaN)
+                    for (int c8 = 2 + P.pe; c8 < k1 / 8; ++c8)
+                        tc::st_shared_v4(a_base + tc::operand_offset_bytes(row, 8 * c8), 0u, 0u, 0u, 0u);
+                }
             }
             tc::fence_proxy_async_smem();
             tc::fence_before_sync();
@@ -453,7 +494,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                                     act_pair<kFmt>(add2(pk(__uint_as_float(v[j + 4]), __uint_as_float(v[j + 5])), pk(b1.x, b1.y))),
                                     act_pair<kFmt>(add2(pk(__uint_as_float(v[j + 6]), __uint_as_float(v[j + 7])), pk(b1.z, b1.w))));
                             }
-                        } else if (l < 3) {
+                        } else if (l < 3 && kFold) {
                             // hidden layers 2, 3: the bias is already in the accumulator
 #pragma unroll
                             for (int j = 0; j < 32; j += 8) {
@@ -462,6 +503,20 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                                                  act_pair<kFmt>(pk(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]))),
                                                  act_pair<kFmt>(pk(__uint_as_float(v[j + 4]), __uint_as_float(v[j + 5]))),
                                                  act_pair<kFmt>(pk(__uint_as_float(v[j + 6]), __uint_as_float(v[j + 7]))));
+                            }
+                        } else if (l < 3) {
+                            // hidden layers 2, 3 (positional-encoding form): + the layer's bias
+                            const float* bias = S.bias[l - 1];
+#pragma unroll
+                            for (int j = 0; j < 32; j += 8) {
+                                const float4 b0 = *reinterpret_cast<const float4*>(bias + cc + j);
+                                const float4 b1 = *reinterpret_cast<const float4*>(bias + cc + j + 4);
+                                tc::st_shared_v4(
+                                    a_base + tc::operand_offset_bytes(row, cc + j),
+                                    act_pair<kFmt>(add2(pk(__uint_as_float(v[j]), __uint_as_float(v[j + 1])), pk(b0.x, b0.y))),
+                                    act_pair<kFmt>(add2(pk(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3])), pk(b0.z, b0.w))),
+                                    act_pair<kFmt>(add2(pk(__uint_as_float(v[j + 4]), __uint_as_float(v[j + 5])), pk(b1.x, b1.y))),
+                                    act_pair<kFmt>(add2(pk(__uint_as_float(v[j + 6]), __uint_as_float(v[j + 7])), pk(b1.z, b1.w))));
                             }
                         } else if constexpr (kF8) {
 #pragma unroll
@@ -474,13 +529,24 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                                 s2 = out_pair<kFmt>(fma2(pk(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3])), dq2,
                                                          pk(b0.z, b0.w)), pk(w0.z, w0.w), s2);
                             }
-                        } else {
+                        } else if constexpr (kFold) {
                             // output layer: the bias b4 is already in the accumulator
 #pragma unroll
                             for (int j = 0; j < 32; j += 4) {
                                 const float4 w0 = *reinterpret_cast<const float4*>(&S.w5[cc + j]);
                                 s2 = out_pair<kFmt>(pk(__uint_as_float(v[j]), __uint_as_float(v[j + 1])), pk(w0.x, w0.y), s2);
                                 s2 = out_pair<kFmt>(pk(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3])), pk(w0.z, w0.w), s2);
+                            }
+                        } else {
+                            // output layer (positional-encoding form): + b4
+#pragma unroll
+                            for (int j = 0; j < 32; j += 4) {
+                                const float4 b0 = *reinterpret_cast<const float4*>(&S.bias[2][cc + j]);
+                                const float4 w0 = *reinterpret_cast<const float4*>(&S.w5[cc + j]);
+                                s2 = out_pair<kFmt>(add2(pk(__uint_as_float(v[j]), __uint_as_float(v[j + 1])), pk(b0.x, b0.y)),
+                                                    pk(w0.x, w0.y), s2);
+                                s2 = out_pair<kFmt>(add2(pk(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3])), pk(b0.z, b0.w)),
+                                                    pk(w0.z, w0.w), s2);
                             }
                         }
                     }
@@ -586,39 +652,47 @@ constexpr size_t kSmemBytes = sizeof(TcShared);
 
 }  // namespace
 
-cudaError_t configure_sdf_mlp_bf16() {
-    cudaError_t e = cudaFuncSetAttribute(sdf_mlp_tc_kernel<kFmtBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(kSmemBytes));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(sdf_mlp_tc_kernel<kFmtFP16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kSmemBytes));
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(sdf_mlp_tc_kernel<kFmtE4M3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int kFmt, bool kPE>
+cudaError_t configure_one() {
+    return cudaFuncSetAttribute(sdf_mlp_tc_kernel<kFmt, kPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(kSmemBytes));
+}
+
+template <int kFmt>
+cudaError_t launch_tc(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms, cudaStream_t s) {
+    const int n_items = (P.K * P.H + kTileRows - 1) / kTileRows;
+    const int want = (n_items + kGroups - 1) / kGroups;
+    const int grid = want < num_sms ? want : num_sms;
+    if (P.pe > 0)
+        return launch_dependent(P.pdl != 0, sdf_mlp_tc_kernel<kFmt, true>, dim3(grid), dim3(kThreads), kSmemBytes, s, P,
+                                B, W);
+    return launch_dependent(P.pdl != 0, sdf_mlp_tc_kernel<kFmt, false>, dim3(grid), dim3(kThreads), kSmemBytes, s, P, B,
+                            W);
+}
+
+cudaError_t configure_sdf_mlp_bf16() {
+    cudaError_t e = configure_one<kFmtBF16, false>();
+    if (e == cudaSuccess) e = configure_one<kFmtFP16, false>();
+    if (e == cudaSuccess) e = configure_one<kFmtE4M3, false>();
+    if (e == cudaSuccess) e = configure_one<kFmtBF16, true>();
+    if (e == cudaSuccess) e = configure_one<kFmtFP16, true>();
+    if (e == cudaSuccess) e = configure_one<kFmtE4M3, true>();
+    return e;
 }
 
 cudaError_t launch_sdf_mlp_bf16(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
                                 cudaStream_t s) {
-    const int n_items = (P.K * P.H + kTileRows - 1) / kTileRows;
-    const int want = (n_items + kGroups - 1) / kGroups;
-    const int grid = want < num_sms ? want : num_sms;
-    return launch_dependent(P.pdl != 0, sdf_mlp_tc_kernel<kFmtBF16>, dim3(grid), dim3(kThreads), kSmemBytes, s, P, B, W);
+    return launch_tc<kFmtBF16>(P, B, W, num_sms, s);
 }
 
 cudaError_t launch_sdf_mlp_fp16(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
                                 cudaStream_t s) {
-    const int n_items = (P.K * P.H + kTileRows - 1) / kTileRows;
-    const int want = (n_items + kGroups - 1) / kGroups;
-    const int grid = want < num_sms ? want : num_sms;
-    return launch_dependent(P.pdl != 0, sdf_mlp_tc_kernel<kFmtFP16>, dim3(grid), dim3(kThreads), kSmemBytes, s, P, B, W);
+    return launch_tc<kFmtFP16>(P, B, W, num_sms, s);
 }
 
 cudaError_t launch_sdf_mlp_fp8(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
                                cudaStream_t s) {
-    const int n_items = (P.K * P.H + kTileRows - 1) / kTileRows;
-    const int want = (n_items + kGroups - 1) / kGroups;
-    const int grid = want < num_sms ? want : num_sms;
-    return launch_dependent(P.pdl != 0, sdf_mlp_tc_kernel<kFmtE4M3>, dim3(grid), dim3(kThreads), kSmemBytes, s, P, B, W);
+    return launch_tc<kFmtE4M3>(P, B, W, num_sms, s);
 }
 
 cudaError_t launch_tc_selftest(const uint16_t* A, const uint16_t* Bm, float* D, int* err, cudaStream_t s) {

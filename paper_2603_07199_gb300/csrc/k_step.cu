@@ -621,14 +621,14 @@ __global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, S
 }
 
 // ------------------------------------------------------------------ per-gate first-layer bias
-// The Gate-SDF decoder's first layer sees [p, z]; z is fixed per gate, so its
-// part W1[:, 3:] z + b1 is computed once per gate instead of once per query.
+// The Gate-SDF decoder's first layer sees [PE(p), z]; z is fixed per gate, so its
+// part W1[:, P:] z + b1 (P point features) is computed once per gate instead of once per query.
 __global__ void first_layer_bias_kernel(const float* __restrict__ W1, const float* __restrict__ b1,
-                                        const float* __restrict__ lat, int G, float* __restrict__ b1p) {
+                                        const float* __restrict__ lat, int G, int n_point, float* __restrict__ b1p) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= G * kHidden) return;
     const int g = i / kHidden, c = i - g * kHidden;
-    const float* wr = W1 + c * (3 + kLatent) + 3;
+    const float* wr = W1 + c * (n_point + kLatent) + n_point;
     const float* z = lat + g * kLatent;
     float acc = 0.f;
     for (int j = 0; j < kLatent; ++j) acc = fmaf(wr[j], z[j], acc);
@@ -687,11 +687,11 @@ cudaError_t launch_cost_update(const StepParams& P, const StepBuffers& B, int ml
     return cudaLaunchKernelEx(&cfg, cost_update_kernel, P, B, mlp, R);
 }
 
-cudaError_t launch_first_layer_bias(const float* W1, const float* b1, const float* latents, int G, float* b1p,
-                                    cudaStream_t s) {
+cudaError_t launch_first_layer_bias(const float* W1, const float* b1, const float* latents, int G, int n_point,
+                                    float* b1p, cudaStream_t s) {
     if (G <= 0) return cudaSuccess;
     const int n = G * kHidden;
-    first_layer_bias_kernel<<<(n + 127) / 128, 128, 0, s>>>(W1, b1, latents, G, b1p);
+    first_layer_bias_kernel<<<(n + 127) / 128, 128, 0, s>>>(W1, b1, latents, G, n_point, b1p);
     return cudaGetLastError();
 }
 

@@ -64,8 +64,8 @@ cudaError_t configure_cost_update();
 // blocks of the update kernel for K rollouts (sizes B.upart and B.bstat)
 int update_blocks(int K);
 // per-gate first-layer bias b1'_g = W1[:, 3:67] z_g + b1
-cudaError_t launch_first_layer_bias(const float* W1, const float* b1, const float* latents, int G, float* b1p,
-                                    cudaStream_t s);
+cudaError_t launch_first_layer_bias(const float* W1, const float* b1, const float* latents, int G, int n_point,
+                                    float* b1p, cudaStream_t s);
 // tensor-core self-test (one 128x128x128 tile)
 cudaError_t launch_tc_selftest(const uint16_t* A, const uint16_t* B, float* D, int* err, cudaStream_t s);
 
@@ -74,6 +74,9 @@ void set_thread_error(const char* msg);
 // Host helpers: BF16 / FP16 (round to nearest even) of a float.
 uint16_t float_to_bf16(float f);
 uint16_t float_to_f16(float f);
+// Host helper: offset (in elements) of (row, k) in a 128 x k1 16-bit operand of 8 x 16-byte core
+// matrices: LBO 128 B along K, SBO k1 / 8 x 128 B between 8-row groups.
+inline int tc_operand_k_offset(int row, int k, int k1) { return (row >> 3) * (k1 * 8) + (k >> 3) * 64 + (row & 7) * 8 + (k & 7); }
 // Host helper: offset (in elements) of (row, k) in the 128 x 16 layer-1 operand (LBO 128 B, SBO 256 B).
 inline int tc_operand16_offset(int row, int k) { return (row >> 3) * 128 + (k >> 3) * 64 + (row & 7) * 8 + (k & 7); }
 // Host helper: byte offset of (row, k) in the 128 x 128 E4M3 operand layout (LBO 128 B, SBO 1024 B).

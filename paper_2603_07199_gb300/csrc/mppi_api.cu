@@ -142,12 +142,16 @@ StepParams make_params(const mppi_ctx* c) {
     P.inv_J = make_float3(1.f / g.inertia_x, 1.f / g.inertia_y, 1.f / g.inertia_z);
     P.J = make_float3(g.inertia_x, g.inertia_y, g.inertia_z);
     P.t_rotor_max = g.rotor_thrust_max;
+    P.pe = g.pe_levels;
     // per-kernel event timing measures kernels one after the other
     P.pdl = c->timing ? 0 : 1;
     return P;
 }
 
 int state_dim(const mppi_config& g) { return g.dynamics_mode == MPPI_DYN_ROTOR ? 17 : 13; }
+// point features of the decoder's input (3 + 6 L) and the K of the layer-1 tensor-core GEMM
+int point_features(const mppi_config& g) { return 3 + 6 * g.pe_levels; }
+int layer1_k(const mppi_config& g) { return layer1_gemm_k(g.pe_levels); }
 
 bool finite_all(const float* x, size_t n) {
     for (size_t i = 0; i < n; ++i)
@@ -167,6 +171,8 @@ int check_config(const mppi_config* g) {
         return fail(nullptr, MPPI_E_UNSUPPORTED, "sdf_mode=%d is not built", g->sdf_mode);
     if (g->cost_mode != MPPI_COST_CONFIGURED && g->cost_mode != MPPI_COST_PAPER)
         return fail(nullptr, MPPI_E_INVALID, "cost_mode=%d is not one of MPPI_COST_*", g->cost_mode);
+    if (g->pe_levels < 0 || g->pe_levels > MPPI_MAX_PE_LEVELS)
+        return fail(nullptr, MPPI_E_INVALID, "pe_levels=%d out of [0, %d]", g->pe_levels, MPPI_MAX_PE_LEVELS);
     if (g->dynamics_mode != MPPI_DYN_CTBR && g->dynamics_mode != MPPI_DYN_ROTOR)
         return fail(nullptr, MPPI_E_INVALID, "dynamics_mode=%d is not one of MPPI_DYN_*", g->dynamics_mode);
     if (g->dynamics_mode == MPPI_DYN_ROTOR) {
@@ -192,7 +198,8 @@ int check_config(const mppi_config* g) {
 
 int recompute_b1p(mppi_ctx* c) {
     if (!c->have_weights || !c->have_latents || c->n_gates == 0) return MPPI_OK;
-    CUDA_TRY(c, launch_first_layer_bias(c->d_W1, c->d_b1, c->d_latents, c->n_gates, c->B.b1p, c->stream));
+    CUDA_TRY(c, launch_first_layer_bias(c->d_W1, c->d_b1, c->d_latents, c->n_gates, point_features(c->cfg), c->B.b1p,
+                                        c->stream));
     return MPPI_OK;
 }
 
@@ -454,7 +461,7 @@ int mppi_create(const mppi_config* cfg, void* cuda_stream, mppi_ctx** out) {
     rc = rc ? rc : dev_alloc(c, &B.tickets, 32);
     rc = rc ? rc : dev_alloc(c, &B.err, 1);
     rc = rc ? rc : dev_alloc(c, &c->d_latents, static_cast<size_t>(MG) * kLatent);
-    rc = rc ? rc : dev_alloc(c, &c->d_W1, kHidden * (3 + kLatent));
+    rc = rc ? rc : dev_alloc(c, &c->d_W1, kHidden * (point_features(*cfg) + kLatent));
     rc = rc ? rc : dev_alloc(c, &c->d_b1, kHidden);
     for (int l = 0; l < 3; ++l) {
         rc = rc ? rc : dev_alloc(c, &c->d_Wt[l], kHidden * kHidden);
@@ -464,7 +471,7 @@ int mppi_create(const mppi_config* cfg, void* cuda_stream, mppi_ctx** out) {
         rc = rc ? rc : dev_alloc(c, &c->d_W8[l], kHidden * kHidden);
     }
     rc = rc ? rc : dev_alloc(c, &c->d_w5, kHidden);
-    rc = rc ? rc : dev_alloc(c, &c->d_W1tc, kHidden * 16);
+    rc = rc ? rc : dev_alloc(c, &c->d_W1tc, kHidden * layer1_k(*cfg));
     if (rc != MPPI_OK) {
         std::snprintf(g_thread_err, sizeof(g_thread_err), "%s", c->err);
         mppi_destroy(c);
@@ -567,7 +574,8 @@ int mppi_set_sdf_weights(mppi_ctx* c, const float* const* layers, int n_layers, 
     }
     for (int i = 0; i < n_layers; ++i)
         if (!layers[i]) return fail(c, MPPI_E_INVALID, "layer pointer %d is NULL", i);
-    const int in1 = 3 + kLatent;
+    const int pf = point_features(c->cfg);
+    const int in1 = pf + kLatent;
     const size_t sizes[10] = {static_cast<size_t>(kHidden) * in1, kHidden, kHidden * kHidden, kHidden,
                               kHidden * kHidden, kHidden, kHidden * kHidden, kHidden, kHidden, 1};
     for (int i = 0; i < 10; ++i)
@@ -606,21 +614,28 @@ int mppi_set_sdf_weights(mppi_ctx* c, const float* const* layers, int n_layers, 
         CUDA_TRY(c, cudaMemcpy(c->d_bias[l], layers[3 + 2 * l], kHidden * sizeof(float), cudaMemcpyHostToDevice));
     }
     CUDA_TRY(c, cudaMemcpy(c->d_w5, layers[8], kHidden * sizeof(float), cudaMemcpyHostToDevice));
-    // layer-1 tensor-core operand: row n = [hi(0..2), hi(0..2), lo(0..2), 0 x 7] of beta log2(e) W1[n, 0:3]
+    // layer-1 tensor-core operand, K = layer1_k columns of beta log2(e) W1: row n =
+    // [hi(0..2), hi(0..2), lo(0..2) of the point columns, 0 x 7, then per PE level its six
+    // columns in BF16 and 0 x 2] (layer1_gemm_k, pe_column)
     {
-        std::vector<uint16_t> w1(kHidden * 16, 0);
-        for (int n = 0; n < kHidden; ++n)
+        const int k1 = layer1_k(c->cfg);
+        std::vector<uint16_t> w1(static_cast<size_t>(kHidden) * k1, 0);
+        for (int n = 0; n < kHidden; ++n) {
             for (int j = 0; j < 3; ++j) {
-                const float ws = cl2 * layers[0][n * (3 + kLatent) + j];
+                const float ws = cl2 * layers[0][n * in1 + j];
                 const uint16_t hi = float_to_bf16(ws);
                 uint32_t hb = static_cast<uint32_t>(hi) << 16;
                 float hf;
                 std::memcpy(&hf, &hb, 4);
                 const uint16_t lo = float_to_bf16(ws - hf);
-                w1[tc_operand16_offset(n, j)] = hi;
-                w1[tc_operand16_offset(n, 3 + j)] = hi;
-                w1[tc_operand16_offset(n, 6 + j)] = lo;
+                w1[tc_operand_k_offset(n, j, k1)] = hi;
+                w1[tc_operand_k_offset(n, 3 + j, k1)] = hi;
+                w1[tc_operand_k_offset(n, 6 + j, k1)] = lo;
             }
+            for (int j = 3; j < pf; ++j)
+                w1[tc_operand_k_offset(n, pe_column((j - 3) / 6, (j - 3) % 6), k1)] =
+                    float_to_bf16(cl2 * layers[0][n * in1 + j]);
+        }
         CUDA_TRY(c, cudaMemcpy(c->d_W1tc, w1.data(), w1.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
     }
     c->b5 = layers[9][0];
@@ -929,8 +944,9 @@ size_t ctx_device_bytes(const mppi_config& g) {
     const size_t nub = static_cast<size_t>(update_blocks(g.K));
     const size_t floats = 16 + 4 * H + 2 + MG * 8 + MG * kHidden + 4 * K * H * 2 + 3 * K + K * H + 2 * K + 4 * H +
                           nub * (4 * H + 2) + 4 + 32 + 1 + MG * kLatent;
-    const size_t weights = sizeof(float) * (kHidden * (3 + kLatent) + kHidden + 3 * (kHidden * kHidden + kHidden) + kHidden) +
-                           3 * kHidden * kHidden * (2 + 2 + 1) + kHidden * 16 * 2;
+    const size_t weights = sizeof(float) * (kHidden * (point_features(g) + kLatent) + kHidden +
+                                            3 * (kHidden * kHidden + kHidden) + kHidden) +
+                           3 * kHidden * kHidden * (2 + 2 + 1) + static_cast<size_t>(kHidden) * layer1_k(g) * 2;
     return floats * sizeof(float) + weights;
 }
 

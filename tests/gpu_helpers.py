@@ -29,6 +29,7 @@ def make_config(prm, mode, max_gates):
         cfg.torque_coeff = prm["kappa"]
     if "inertia" in prm:
         cfg.inertia_x, cfg.inertia_y, cfg.inertia_z = prm["inertia"]
+    cfg.pe_levels = int(prm.get("pe_levels", 0))
     return cfg
 
 

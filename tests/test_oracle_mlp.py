@@ -64,3 +64,26 @@ def test_input_gradient_central_differences():
     fd = np.stack([(mlp.forward(layers, x + e * np.eye(6)[i]) - mlp.forward(layers, x - e * np.eye(6)[i])) / (2 * e)
                    for i in range(6)], axis=1)
     np.testing.assert_allclose(g, fd, rtol=1e-5, atol=1e-7)
+
+
+def test_positional_encoding_closed_forms():
+    from oracle import mlp as M
+    p = np.array([[0.25, -0.5, 1.0]])
+    f = M.positional_encoding(p, 2)
+    assert f.shape == (1, 15)
+    np.testing.assert_allclose(f[0, 0:3], p[0])
+    np.testing.assert_allclose(f[0, 3:6], [np.sin(np.pi / 4), -1.0, 0.0], atol=1e-15)       # sin(pi p)
+    np.testing.assert_allclose(f[0, 6:9], [np.cos(np.pi / 4), 0.0, -1.0], atol=1e-15)       # cos(pi p)
+    np.testing.assert_allclose(f[0, 9:12], [1.0, 0.0, 0.0], atol=1e-15)                     # sin(2 pi p)
+    np.testing.assert_allclose(f[0, 12:15], [0.0, -1.0, 1.0], atol=1e-15)                   # cos(2 pi p)
+    np.testing.assert_array_equal(M.positional_encoding(p, 0), p)
+
+
+def test_sdf_with_positional_encoding_is_the_mlp_of_the_encoded_point():
+    import workloads as W
+    from oracle import mlp as M
+    layers = W.xavier_mlp(5, in_dim=3 + 6 * 3 + 64)
+    rng = np.random.default_rng(1)
+    pg, z = rng.normal(size=(7, 3)), rng.normal(size=64)
+    x = np.concatenate([M.positional_encoding(pg, 3), np.tile(z, (7, 1))], axis=1)
+    np.testing.assert_allclose(M.sdf(layers, pg, z, pe_levels=3), M.forward(layers, x), rtol=1e-15)
