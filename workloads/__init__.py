@@ -14,6 +14,10 @@ depth images and trained networks are not available):
                    yaw in [-60, 60] deg and pitch in [-30, 30] deg, Gate-SDF MLP
                    with Xavier-uniform weights and N(0, 1) latents (100 steps).
 * ``four_gate_mlp`` K=16384, H=64, four such gates.
+* ``depth_views``  64 camera poses approaching the two-gate track, rendered at
+                   640 x 480 by a pinhole camera of about 80 x 64 degrees (a stereo
+                   depth sensor's field of view; the paper's sensor and images are
+                   not available), with depth noise and dropout.
 """
 
 import math
@@ -196,3 +200,40 @@ def poisson_arrivals(n_drones, rate_hz, duration_s, seed=5):
             t += rng.exponential(1.0 / rate_hz)
     out.sort()
     return out
+
+
+def camera_views(n_views, gate_poses, seed=6, dist=(2.0, 9.0), lateral=1.5, vertical=0.8,
+                 yaw_jitter_deg=15.0, pitch_jitter_deg=10.0):
+    """Camera poses [n, 7] approaching the gates: each in front of a random gate (on the side
+    its normal points away from), at a distance ~ U(dist) along the normal, offset sideways
+    and vertically, heading towards the gate centre with yaw / pitch jitter.  The camera looks
+    along its +x axis (y left, z up)."""
+    rng = np.random.default_rng(seed)
+    gate_poses = np.asarray(gate_poses, dtype=np.float64).reshape(-1, 7)
+    out = np.zeros((n_views, 7), dtype=np.float32)
+    for i in range(n_views):
+        g = gate_poses[rng.integers(len(gate_poses))]
+        w, x, y, z = g[3:7] / np.linalg.norm(g[3:7])
+        normal = np.array([1 - 2 * (y * y + z * z), 2 * (x * y + w * z), 2 * (x * z - w * y)])
+        side = np.cross([0.0, 0.0, 1.0], normal)
+        side /= max(np.linalg.norm(side), 1e-9)
+        pos = (g[0:3] - rng.uniform(*dist) * normal + rng.uniform(-lateral, lateral) * side
+               + np.array([0.0, 0.0, rng.uniform(-vertical, vertical)]))
+        to_gate = g[0:3] - pos
+        yaw = math.atan2(to_gate[1], to_gate[0]) + math.radians(rng.uniform(-yaw_jitter_deg, yaw_jitter_deg))
+        elev = math.atan2(to_gate[2], math.hypot(to_gate[0], to_gate[1]))
+        pitch = -elev + math.radians(rng.uniform(-pitch_jitter_deg, pitch_jitter_deg))
+        out[i, 0:3] = pos
+        out[i, 3:7] = yaw_pitch_quat(yaw, pitch)
+    return out
+
+
+DEPTH_CAMERA = dict(width=640, height=480, fx=385.0, fy=385.0, cx=320.0, cy=240.0, max_range=10.0)
+
+
+def depth_views():
+    """64 views of the two-gate track at 640 x 480, with depth noise sigma = 0.005 z^2 and 2 %
+    dropout (readings of the paper's unspecified sensor noise)."""
+    gates = gate_track(2)
+    return dict(name="depth_views_N64_640x480_G2", camera=dict(DEPTH_CAMERA), gates=gates,
+                cams=camera_views(64, gates), noise_depth_coeff=0.005, dropout=0.02, seed=9, frame=0)
