@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--serving-seconds", type=float, default=1.0)
     ap.add_argument("--distill-steps", type=int, default=0)
     ap.add_argument("--four-gate-steps", type=int, default=20)
+    ap.add_argument("--render-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -441,6 +442,45 @@ def hover_gate_leg(torch, B, stream, flush, dev, steps, drone_id):
             "p99_ms": float(np.percentile(ms, 99)), "steps": steps}
 
 
+def render_leg(torch, B, stream, flush, dev, steps, peak_gbs):
+    """Depth images of the two-gate track (64 views at 640 x 480, clean and with sensor noise):
+    one mppi_render_depth launch per timed step, L2 flushed between steps.  Algorithmic bytes
+    per launch: the 4-byte depth of every pixel written plus the 28-byte camera and gate poses
+    read once."""
+    import workloads as W
+    wl = W.depth_views()
+    kw = wl["camera"]
+    n = wl["cams"].shape[0]
+    cams = torch.from_numpy(np.ascontiguousarray(wl["cams"], np.float32)).to(dev)
+    gates = torch.from_numpy(np.ascontiguousarray(wl["gates"], np.float32)).to(dev)
+    n_pix = n * kw["width"] * kw["height"]
+    out = torch.empty(n_pix, dtype=torch.float32, device=dev)
+    algo_bytes = 4 * n_pix + 28 * (n + gates.shape[0])
+    res = {"workload": wl["name"], "pixels_per_launch": n_pix, "algorithmic_bytes_per_launch": algo_bytes}
+    for name, noise, drop in (("clean", 0.0, 0.0), ("noisy", wl["noise_depth_coeff"], wl["dropout"])):
+        cam = B.mppi_depth_camera_default()
+        for k, v in kw.items():
+            setattr(cam, k, v)
+        cam.noise_depth_coeff, cam.dropout, cam.seed, cam.frame = noise, drop, wl["seed"], wl["frame"]
+        for _ in range(3):
+            B.mppi_render_depth(cam, n, cams, gates.shape[0], gates, out, stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record()
+            B.mppi_render_depth(cam, n, cams, gates.shape[0], gates, out, stream)
+            ev[i][1].record()
+        torch.cuda.synchronize()
+        ms = np.array([a.elapsed_time(b) for a, b in ev])
+        gbs = algo_bytes / (ms.mean() * 1e-3) / 1e9
+        res[name] = {"value": n_pix / (ms.mean() * 1e-3), "unit": "depth pixels/s", "mean_ms": float(ms.mean()),
+                     "p50_ms": float(np.percentile(ms, 50)), "achieved_gbs": gbs, "frac_of_hbm": gbs / peak_gbs,
+                     "steps": steps}
+    res["hit_fraction"] = float((out < kw["max_range"]).float().mean().item())
+    res["peak_gbs"] = peak_gbs
+    return res
+
+
 def max_over_ranks(torch, dist, x, device):
     t = torch.tensor([x], device=device, dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -516,6 +556,13 @@ def run_ours(args):
             if args.four_gate_steps > 0 else None)
     hover = hover_gate_leg(torch, B, stream, flush, dev, args.steps, rank)
     rotor_dyn = rotor_leg(torch, B, stream, flush, dev, args.steps, rank)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    render = (render_leg(torch, B, stream, flush, dev, args.render_steps, peaks.get("hbm_gbs") or 6800.0)
+              if args.render_steps > 0 else None)
     serving = serving_leg(torch, B, dev, args.serving_seconds) if args.serving_seconds > 0 else None
     distill = distill_leg(torch, B, dev, args.distill_steps) if args.distill_steps > 0 else None
 
@@ -523,12 +570,6 @@ def run_ours(args):
         if world > 1:
             dist.destroy_process_group()
         return
-    import json as _json
-    peaks = {}
-    try:
-        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
-        pass
     peak_tf = peaks.get("bf16_tflops")
     peak_src = "measured burst bf16 (MEASURED_PEAKS.json)" if peak_tf else "fallback 1900 TFLOP/s"
     peak_tf = peak_tf or 1900.0
@@ -566,6 +607,7 @@ def run_ours(args):
         "four_gates": four,
         "hover_gate_analytic": hover,
         "rotor_dynamics": rotor_dyn,
+        "depth_render": render,
         "serving": serving,
         "distill": distill,
         "gpu_launches": per_launch * args.steps,

@@ -317,6 +317,65 @@ int mppi_softmax_update_noalloc(const float* d_costs, const float* d_noise, cons
                                 float lambda, float thrust_min, float thrust_max, float rate_max,
                                 float* d_new_controls, float* d_weights, void* stream);
 
+/* ======================================================================== vision front end: depth images
+ * The onboard observation of Sec. III-B: a first-person depth image of the
+ * gates, which the paper renders with a simulator (Sec. III-A, V) and from
+ * which its encoder infers the latent z.  mppi_render_depth casts one ray per
+ * pixel through a pinhole camera and returns the depth of the first point of
+ * any gate frame on it (exact ray--frame intersection, no graphics API), for
+ * many camera poses at once; optionally it adds the synthetic sensor noise of
+ * the denoising pre-training stage (Sec. III-B, I_noisy).  Readings (the
+ * paper gives neither a camera model nor its noise model):
+ *   - camera frame x forward (optical axis), y left, z up; a camera pose is 7
+ *     floats [t(3), q(4) (w, x, y, z) rotating camera -> world];
+ *   - pixel (u, v), u to the right, v down, looks along
+ *     (1, -(u + 1/2 - cx) / fx, -(v + 1/2 - cy) / fy); its depth is the
+ *     optical-axis coordinate z of the first frame point on that ray (z >= 0),
+ *     or max_range when there is none at or before max_range;
+ *   - a gate frame is {|x| <= d, a_in <= max(|y|, |z|) <= a_out} in its gate
+ *     frame (the solid of the analytic SDF);
+ *   - noise: the pixel's Philox4x32-10 block with key = seed and counter
+ *     (v * width + u, view, frame, 0xDE9750); with n the first Box-Muller
+ *     normal of words 0, 1 and r the uniform of word 2 (both as in the control
+ *     noise), the pixel reads 0 when r < dropout, else max_range when its clean
+ *     depth is max_range, else clip(z + noise_depth_coeff z^2 n, 0, max_range).
+ */
+#define MPPI_MAX_IMAGE_SIDE   8192
+#define MPPI_MAX_RENDER_GATES 64
+
+typedef struct mppi_depth_camera {
+    int32_t width, height;          /* pixels, 1 .. MPPI_MAX_IMAGE_SIDE each */
+    float fx, fy, cx, cy;           /* pinhole intrinsics (pixels); fx, fy > 0 */
+    float max_range;                /* m, > 0: depth of a pixel that sees no frame */
+    float gate_inner_half, gate_outer_half, gate_half_depth;   /* frame geometry (m) */
+    float noise_depth_coeff;        /* c of the noise sigma = c z^2 (1/m), >= 0; 0 = no Gaussian noise */
+    float dropout;                  /* probability in [0, 1] that a pixel reads 0 */
+    uint64_t seed;                  /* Philox key of the noise */
+    uint32_t frame;                 /* Philox counter word 2 of the noise (e.g. an image index) */
+    uint32_t reserved;              /* must be 0 */
+} mppi_depth_camera;
+
+/* Defaults: 640 x 480, fx = fy = 385, cx = 320, cy = 240 (a 80 x 64 degree field of view),
+ * max_range 10 m, the 1.5 m / 1.0 m / 0.2 m frame, no noise, seed 0, frame 0. */
+void mppi_depth_camera_default(mppi_depth_camera* cam);
+/*
+ * Render n_views depth images (device pointers, enqueued on stream):
+ *   cam           camera intrinsics, range, frame geometry and noise (host struct)
+ *   n_views       0 .. 2^24 camera poses
+ *   d_cam_poses   n_views x 7 floats (device)
+ *   n_gates       0 .. MPPI_MAX_RENDER_GATES gate poses (0: every pixel reads max_range,
+ *                 or 0 where it drops out)
+ *   d_gate_poses  n_gates x 7 floats (device; NULL when n_gates = 0)
+ *   d_depth       n_views x height x width floats out (device), [view][v][u]
+ *   stream        cudaStream_t (NULL: the legacy default stream)
+ * Enqueues one kernel and returns.  Non-finite poses give unspecified (but
+ * finite) depths.  Errors: MPPI_E_INVALID (NULL pointer, a size or parameter
+ * out of range; nothing is enqueued), MPPI_E_CUDA; the message is read with
+ * mppi_last_error(NULL).
+ */
+int mppi_render_depth(const mppi_depth_camera* cam, int n_views, const float* d_cam_poses, int n_gates,
+                      const float* d_gate_poses, float* d_depth, void* stream);
+
 /* ======================================================================== learned part
  * Distillation of the exact gate-frame SDF (the frame of mppi_config's gate
  * geometry) into the Gate-SDF MLP (Sec. III-B trains the decoder with an L1

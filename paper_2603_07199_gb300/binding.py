@@ -57,6 +57,7 @@ EXPORTS = [
     "mppi_train_config_default", "mppi_train_create", "mppi_train_destroy", "mppi_train_last_error",
     "mppi_train_step", "mppi_train_loss_grads", "mppi_train_get_weights", "mppi_train_evaluate",
     "mppi_train_read_points", "mppi_train_num_params",
+    "mppi_depth_camera_default", "mppi_render_depth",
 ]
 
 
@@ -102,6 +103,17 @@ class MppiTrainConfig(ctypes.Structure):
                 ("near_surface_fraction", ctypes.c_float), ("near_surface_sigma", ctypes.c_float),
                 ("cube_half", ctypes.c_float), ("gate_inner_half", ctypes.c_float),
                 ("gate_outer_half", ctypes.c_float), ("gate_half_depth", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+class MppiDepthCamera(ctypes.Structure):
+    _fields_ = [
+        ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+        ("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+        ("max_range", ctypes.c_float),
+        ("gate_inner_half", ctypes.c_float), ("gate_outer_half", ctypes.c_float), ("gate_half_depth", ctypes.c_float),
+        ("noise_depth_coeff", ctypes.c_float), ("dropout", ctypes.c_float),
+        ("seed", ctypes.c_uint64), ("frame", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+    ]
 
 
 _vp = ctypes.c_void_p
@@ -151,6 +163,9 @@ _SIGS = {
     "mppi_train_evaluate": (ctypes.c_int, [_vp] + [ctypes.POINTER(ctypes.c_float)] * 4),
     "mppi_train_read_points": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_size_t]),
     "mppi_train_num_params": (ctypes.c_int, []),
+    "mppi_depth_camera_default": (None, [ctypes.POINTER(MppiDepthCamera)]),
+    "mppi_render_depth": (ctypes.c_int, [ctypes.POINTER(MppiDepthCamera), ctypes.c_int, _vp, ctypes.c_int, _vp, _vp,
+                                         _vp]),
 }
 
 _lib = None
@@ -421,3 +436,20 @@ def mppi_train_evaluate(trainer):
 
 def mppi_train_read_points(trainer, which, out):
     return _tcheck(load().mppi_train_read_points(trainer, which, _ptr(out), out.size), trainer)
+
+
+# ------------------------------------------------------------------ vision front end (depth images)
+MPPI_MAX_IMAGE_SIDE = 8192
+MPPI_MAX_RENDER_GATES = 64
+
+
+def mppi_depth_camera_default():
+    cam = MppiDepthCamera()
+    load().mppi_depth_camera_default(ctypes.byref(cam))
+    return cam
+
+
+def mppi_render_depth(cam, n_views, d_cam_poses, n_gates, d_gate_poses, d_depth, stream=None):
+    """Enqueue n_views depth images [n_views, height, width] into d_depth (device pointers)."""
+    return _check(load().mppi_render_depth(ctypes.byref(cam), n_views, _ptr(d_cam_poses), n_gates,
+                                           _ptr(d_gate_poses), _ptr(d_depth), _ptr(stream)))
