@@ -446,7 +446,8 @@ def render_leg(torch, B, stream, flush, dev, steps, peak_gbs):
     """Depth images of the two-gate track (64 views at 640 x 480, clean and with sensor noise):
     one mppi_render_depth launch per timed step, L2 flushed between steps.  Algorithmic bytes
     per launch: the 4-byte depth of every pixel written plus the 28-byte camera and gate poses
-    read once."""
+    read once.  The same launch with no gates (every pixel max_range) gives the kernel's store
+    floor."""
     import workloads as W
     wl = W.depth_views()
     kw = wl["camera"]
@@ -457,18 +458,20 @@ def render_leg(torch, B, stream, flush, dev, steps, peak_gbs):
     out = torch.empty(n_pix, dtype=torch.float32, device=dev)
     algo_bytes = 4 * n_pix + 28 * (n + gates.shape[0])
     res = {"workload": wl["name"], "pixels_per_launch": n_pix, "algorithmic_bytes_per_launch": algo_bytes}
-    for name, noise, drop in (("clean", 0.0, 0.0), ("noisy", wl["noise_depth_coeff"], wl["dropout"])):
+    for name, noise, drop, n_g in (("clean", 0.0, 0.0, gates.shape[0]),
+                                   ("noisy", wl["noise_depth_coeff"], wl["dropout"], gates.shape[0]),
+                                   ("no_gates_store_floor", 0.0, 0.0, 0)):
         cam = B.mppi_depth_camera_default()
         for k, v in kw.items():
             setattr(cam, k, v)
         cam.noise_depth_coeff, cam.dropout, cam.seed, cam.frame = noise, drop, wl["seed"], wl["frame"]
         for _ in range(3):
-            B.mppi_render_depth(cam, n, cams, gates.shape[0], gates, out, stream)
+            B.mppi_render_depth(cam, n, cams, n_g, gates, out, stream)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         for i in range(steps):
             flush.zero_()
             ev[i][0].record()
-            B.mppi_render_depth(cam, n, cams, gates.shape[0], gates, out, stream)
+            B.mppi_render_depth(cam, n, cams, n_g, gates, out, stream)
             ev[i][1].record()
         torch.cuda.synchronize()
         ms = np.array([a.elapsed_time(b) for a, b in ev])
@@ -476,6 +479,8 @@ def render_leg(torch, B, stream, flush, dev, steps, peak_gbs):
         res[name] = {"value": n_pix / (ms.mean() * 1e-3), "unit": "depth pixels/s", "mean_ms": float(ms.mean()),
                      "p50_ms": float(np.percentile(ms, 50)), "achieved_gbs": gbs, "frac_of_hbm": gbs / peak_gbs,
                      "steps": steps}
+    B.mppi_render_depth(cam, n, cams, gates.shape[0], gates, out, stream)
+    torch.cuda.synchronize()
     res["hit_fraction"] = float((out < kw["max_range"]).float().mean().item())
     res["peak_gbs"] = peak_gbs
     return res

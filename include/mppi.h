@@ -334,11 +334,14 @@ int mppi_softmax_update_noalloc(const float* d_costs, const float* d_noise, cons
  *     or max_range when there is none at or before max_range;
  *   - a gate frame is {|x| <= d, a_in <= max(|y|, |z|) <= a_out} in its gate
  *     frame (the solid of the analytic SDF);
- *   - noise: the pixel's Philox4x32-10 block with key = seed and counter
- *     (v * width + u, view, frame, 0xDE9750); with n the first Box-Muller
- *     normal of words 0, 1 and r the uniform of word 2 (both as in the control
- *     noise), the pixel reads 0 when r < dropout, else max_range when its clean
- *     depth is max_range, else clip(z + noise_depth_coeff z^2 n, 0, max_range).
+ *   - noise: with p = v * width + u, the pixel's dropout uniform r is word
+ *     (p mod 4) of the Philox4x32-10 block with key = seed and counter
+ *     (p / 4, view, frame, 0xDE9751), and its normal n is the cosine (p even)
+ *     or sine (p odd) Box-Muller normal of words 0, 1 of the block with
+ *     counter (p / 2, view, frame, 0xDE9750) (uniforms and Box-Muller as in the
+ *     control noise); the pixel reads 0 when r < dropout, else max_range when
+ *     its clean depth is max_range, else clip(z + noise_depth_coeff z^2 n, 0,
+ *     max_range).
  */
 #define MPPI_MAX_IMAGE_SIDE   8192
 #define MPPI_MAX_RENDER_GATES 64

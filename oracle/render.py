@@ -18,12 +18,14 @@ Readings (the paper gives neither a camera model nor its noise model):
 * a gate's frame is the union of four closed boxes in its gate frame
   (``gate_sdf.frame_boxes``); a ray enters a box where the slab intervals of the three
   axes first overlap;
-* noise: a pixel's Philox block has counter (pixel index v W + u, view, frame, 0xDE9750)
-  and key = the seed; its first Box-Muller normal n (words 0, 1) and the uniform of
-  word 2 give the noisy depth 0 when that uniform is below the dropout probability,
-  else max_range for a pixel whose clean depth is max_range, else
-  clip(z + c z^2 n, 0, max_range)
-  (a stereo sensor's depth error grows with the square of the depth).
+* noise: with p = v W + u the pixel's linear index, its dropout uniform r is word (p mod 4)
+  of the Philox block with counter (p div 4, view, frame, 0xDE9751), and its normal n is the
+  cosine (p even) or sine (p odd) Box-Muller normal of words 0, 1 of the block with counter
+  (p div 2, view, frame, 0xDE9750), both with key = the seed (one block serves four
+  pixels' dropout and two pixels' normals); the noisy depth is 0 when r is below the dropout
+  probability, else max_range for a pixel whose clean depth is max_range, else
+  clip(z + c z^2 n, 0, max_range) (a stereo sensor's depth error grows with the square of
+  the depth).
 """
 
 import numpy as np
@@ -33,7 +35,8 @@ from .dynamics import quat_conj, quat_rotate
 from .noise import box_muller, words_to_uniform
 from .philox import philox4x32_10, split_seed
 
-NOISE_STREAM_TAG = 0xDE9750
+NORMAL_STREAM_TAG = 0xDE9750
+DROPOUT_STREAM_TAG = 0xDE9751
 
 
 def _unit_pose(pose):
@@ -113,34 +116,44 @@ def depth_images(cam_poses, gate_poses, width, height, fx, fy, cx, cy, max_range
                      for c in cams]) if len(cams) else np.zeros((0, height, width))
 
 
-def pixel_noise_words(pix, view, seed, frame):
-    """Philox words [..., 4] of the noise blocks of pixels with linear index pix = v W + u
-    in views `view` (broadcast together)."""
-    pix, view = np.broadcast_arrays(np.asarray(pix, dtype=np.uint64), np.asarray(view, dtype=np.uint64))
-    ctr = np.empty(pix.shape + (4,), dtype=np.uint64)
-    ctr[..., 0] = pix
+def _blocks(index, view, seed, frame, tag):
+    index, view = np.broadcast_arrays(np.asarray(index, dtype=np.uint64), np.asarray(view, dtype=np.uint64))
+    ctr = np.empty(index.shape + (4,), dtype=np.uint64)
+    ctr[..., 0] = index
     ctr[..., 1] = view
     ctr[..., 2] = np.uint64(int(frame) & 0xFFFFFFFF)
-    ctr[..., 3] = np.uint64(NOISE_STREAM_TAG)
+    ctr[..., 3] = np.uint64(tag)
     return philox4x32_10(ctr, split_seed(seed))
 
 
-def noise_words(n_views, width, height, seed, frame):
-    """Philox words [N, H, W, 4] of every pixel's noise block."""
+def pixel_noise(pix, view, seed, frame):
+    """(normal n, dropout uniform r) of pixels with linear index pix = v W + u in views
+    `view` (broadcast together)."""
+    pix = np.asarray(pix, dtype=np.uint64)
+    nw = _blocks(pix >> np.uint64(1), view, seed, frame, NORMAL_STREAM_TAG)
+    un = words_to_uniform(nw)
+    c, s_ = box_muller(un[..., 0], un[..., 1])
+    n = np.where((pix & np.uint64(1)) == 0, c, s_)
+    dw = _blocks(pix >> np.uint64(2), view, seed, frame, DROPOUT_STREAM_TAG)
+    word = np.take_along_axis(dw, (pix & np.uint64(3)).astype(np.int64)[..., None], axis=-1)[..., 0]
+    return n, words_to_uniform(word)
+
+
+def image_noise(n_views, width, height, seed, frame):
+    """(normals, dropout uniforms), each [N, H, W], of every pixel."""
     pix = np.arange(width * height, dtype=np.uint64)[None, :]
     view = np.arange(n_views, dtype=np.uint64)[:, None]
-    return pixel_noise_words(pix, view, seed, frame).reshape(n_views, height, width, 4)
+    n, r = pixel_noise(pix, view, seed, frame)
+    return n.reshape(n_views, height, width), r.reshape(n_views, height, width)
 
 
-def noisy_depths(clean, words, max_range, depth_coeff, dropout):
-    """Noisy depths of pixels with clean depths `clean` [...] and noise words [..., 4]."""
+def noisy_depths(clean, n, r, max_range, depth_coeff, dropout):
+    """Noisy depths of pixels with clean depths `clean`, normals n and dropout uniforms r."""
     clean = np.asarray(clean, dtype=np.float64)
-    u = words_to_uniform(words)
-    n0, _ = box_muller(u[..., 0], u[..., 1])
     hit = clean < max_range
-    noisy = np.where(hit, np.clip(clean + depth_coeff * clean * clean * n0, 0.0, max_range), max_range)
+    noisy = np.where(hit, np.clip(clean + depth_coeff * clean * clean * n, 0.0, max_range), max_range)
     # the dropout test compares the 24-bit uniform with the probability rounded to float32
-    drop = u[..., 2] < float(np.float32(dropout))
+    drop = r < float(np.float32(dropout))
     return np.where(drop, 0.0, noisy)
 
 
@@ -148,4 +161,5 @@ def add_sensor_noise(clean, max_range, depth_coeff, dropout, seed, frame):
     """Noisy images [N, H, W] from clean ones [N, H, W] (see the module readings)."""
     clean = np.asarray(clean, dtype=np.float64)
     n_views, height, width = clean.shape
-    return noisy_depths(clean, noise_words(n_views, width, height, seed, frame), max_range, depth_coeff, dropout)
+    n, r = image_noise(n_views, width, height, seed, frame)
+    return noisy_depths(clean, n, r, max_range, depth_coeff, dropout)

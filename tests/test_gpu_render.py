@@ -120,7 +120,7 @@ def test_render_noise_parity(noise, dropout):
     got = _render(_camera(kw, noise, dropout, seed=77, frame=5), cams, gates)
     base, grown, shrunk = _oracle_triplet(cams, gates, kw)
     want = R.add_sensor_noise(base, kw["max_range"], noise, dropout, seed=77, frame=5)
-    u = R.words_to_uniform(R.noise_words(len(cams), kw["width"], kw["height"], 77, 5)[..., 2])
+    _, u = R.image_noise(len(cams), kw["width"], kw["height"], 77, 5)
     drop = u < np.float32(dropout)
     np.testing.assert_array_equal(got[drop], 0.0)
     good = ((shrunk - grown) <= COND) & ~drop
@@ -159,12 +159,12 @@ def test_render_full_size_sampled():
     assert n_checked == 4096
     # noise at the sampled pixels: dropout decisions exact, noisy depths within tolerance
     view, vs, us = pick[:, 0], pick[:, 1], pick[:, 2]
-    words = R.pixel_noise_words(vs * kw["width"] + us, view, wl["seed"], wl["frame"])
+    n, r = R.pixel_noise(vs * kw["width"] + us, view, wl["seed"], wl["frame"])
     base = np.concatenate([R.pixel_depths(cams[v], gates, us[view == v], vs[view == v], **geo) for v in range(64)])
     order = np.concatenate([np.nonzero(view == v)[0] for v in range(64)])
     want = np.empty(len(pick))
-    want[order] = R.noisy_depths(base, words[order], kw["max_range"], wl["noise_depth_coeff"], wl["dropout"])
-    drop = R.words_to_uniform(words[:, 2]) < np.float32(wl["dropout"])
+    want[order] = R.noisy_depths(base, n[order], r[order], kw["max_range"], wl["noise_depth_coeff"], wl["dropout"])
+    drop = r < np.float32(wl["dropout"])
     got = noisy[view, vs, us]
     np.testing.assert_array_equal(got[drop], 0.0)
     err = np.abs(got - want)

@@ -215,3 +215,19 @@ def test_noise_depends_on_view_and_frame():
     b = R.add_sensor_noise(clean, 10.0, 0.01, 0.0, seed=5, frame=1)
     assert not np.array_equal(a[0], a[1]) and not np.array_equal(a, b)
     np.testing.assert_array_equal(a, R.add_sensor_noise(clean, 10.0, 0.01, 0.0, seed=5, frame=0))
+
+
+def test_noise_pairs_share_a_box_muller_radius():
+    """The normals of pixels 2m and 2m + 1 are the cosine and sine branches of one Box-Muller
+    draw: n_2m^2 + n_2m+1^2 = -2 ln u of that draw's first uniform, whatever the angle."""
+    from oracle.noise import words_to_uniform
+    from oracle.philox import philox4x32_10, split_seed
+    pix = np.arange(0, 512, dtype=np.uint64)
+    n, r = R.pixel_noise(pix, 3, seed=99, frame=4)
+    ctr = np.stack([pix[0::2] >> np.uint64(1), np.full(256, 3, np.uint64), np.full(256, 4, np.uint64),
+                    np.full(256, R.NORMAL_STREAM_TAG, np.uint64)], -1)
+    u0 = words_to_uniform(philox4x32_10(ctr, split_seed(99))[:, 0])
+    np.testing.assert_allclose(n[0::2] ** 2 + n[1::2] ** 2, -2.0 * np.log(u0), rtol=1e-12)
+    # the angle differs between pairs and the dropout uniforms are all distinct
+    assert len(np.unique(np.round(np.arctan2(n[1::2], n[0::2]), 12))) == 256
+    assert len(np.unique(r)) > 500
