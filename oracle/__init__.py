@@ -23,6 +23,8 @@ The oracle restates the paper's method step by step in float64 with numpy:
                    and its input gradient (for the Eikonal term).
 * ``render``    -- depth images of the gate frames through a pinhole camera (exact ray
                    casting) and the synthetic sensor noise (Sec. III-B).
+* ``encoder``   -- the depth encoder E_theta (depth image -> latent z) in the stated
+                   convolutional reading (Sec. III-B).
 * ``distill``   -- the distillation loss (L1 + Eikonal), its gradients and Adam.
 * ``mppi``      -- per-rollout costs (Eq. 8-10 in the configured form),
                    softmax weights and the weighted update (Eq. 5), the
@@ -35,4 +37,4 @@ states) are passed in by the caller from the seeded generators in
 ``workloads``.
 """
 
-from . import philox, noise, dynamics, rotor, gate_sdf, mlp, mppi, distill, render  # noqa: F401
+from . import philox, noise, dynamics, rotor, gate_sdf, mlp, mppi, distill, render, encoder  # noqa: F401

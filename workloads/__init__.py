@@ -237,3 +237,23 @@ def depth_views():
     gates = gate_track(2)
     return dict(name="depth_views_N64_640x480_G2", camera=dict(DEPTH_CAMERA), gates=gates,
                 cams=camera_views(64, gates), noise_depth_coeff=0.005, dropout=0.02, seed=9, frame=0)
+
+
+ENCODER_CHANNELS = (16, 32, 64, 64)
+
+
+def encoder_weights(seed=7, channels=ENCODER_CHANNELS, latent=LATENT_DIM):
+    """Weights of the depth encoder: 4 convolutions 3x3 (He-uniform U(-a, a), a = sqrt(6 / fan_in),
+    biases U(-0.05, 0.05)) and the linear head (Xavier-uniform, zero bias).
+    Returns [(W [co, ci, 3, 3], b [co])] x 4 + [(W [64, 64], b [64])], float32."""
+    rng = np.random.default_rng(seed)
+    layers = []
+    ci = 1
+    for co in channels:
+        a = math.sqrt(6.0 / (9 * ci))
+        layers.append((rng.uniform(-a, a, size=(co, ci, 3, 3)).astype(np.float32),
+                       rng.uniform(-0.05, 0.05, size=co).astype(np.float32)))
+        ci = co
+    a = math.sqrt(6.0 / (ci + latent))
+    layers.append((rng.uniform(-a, a, size=(latent, ci)).astype(np.float32), np.zeros(latent, dtype=np.float32)))
+    return layers
