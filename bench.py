@@ -43,6 +43,9 @@ FMA_FLOPS_PER_QUERY = 2 * 3 * 128 + 2 * 128           # layer 1 (point part) + o
 # the ncu capture summarised in profiles/sdf_mlp_tc_bf16_two_gate_K4096_H50_G2.md (None once the
 # kernel changes)
 SDF_BF16_DRAM_BYTES = 3414784
+# multiply-adds x 2 of the depth encoder's convolutions and head for one 160 x 120 image
+ENCODER_FLOPS_PER_IMAGE_160x120 = 2 * (60 * 80 * 16 * 9 * 1 + 30 * 40 * 32 * 9 * 16 + 15 * 20 * 64 * 9 * 32
+                                       + 8 * 10 * 64 * 9 * 64 + 64 * 64)
 
 
 def parse():
@@ -59,6 +62,7 @@ def parse():
     ap.add_argument("--distill-steps", type=int, default=0)
     ap.add_argument("--four-gate-steps", type=int, default=20)
     ap.add_argument("--render-steps", type=int, default=20)
+    ap.add_argument("--vision-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -486,6 +490,81 @@ def render_leg(torch, B, stream, flush, dev, steps, peak_gbs):
     return res
 
 
+def vision_leg(torch, B, stream, flush, dev, steps, drone_id):
+    """The vision front end: (1) the 64 views of the two-gate track at 160 x 120 rendered with
+    sensor noise and encoded into 64 latents (one render + one encode per timed step); (2) one
+    control cycle of a drone -- render a view of each of the two gates, encode both, and run the
+    BF16 MPPI step (K=4096, H=50) on those latents -- per timed step, all on one stream."""
+    import workloads as W
+    wl = W.depth_views()
+    kw = dict(wl["camera"], width=160, height=120, fx=96.25, fy=96.25, cx=80.0, cy=60.0)
+    cam = B.mppi_depth_camera_default()
+    for k, v in kw.items():
+        setattr(cam, k, v)
+    cam.noise_depth_coeff, cam.dropout, cam.seed = wl["noise_depth_coeff"], wl["dropout"], wl["seed"]
+    n = wl["cams"].shape[0]
+    cams = torch.from_numpy(np.ascontiguousarray(wl["cams"], np.float32)).to(dev)
+    gates = torch.from_numpy(np.ascontiguousarray(wl["gates"], np.float32)).to(dev)
+    depth = torch.empty(n, kw["height"], kw["width"], device=dev)
+    z = torch.empty(n, 64, device=dev)
+    layers = []
+    for Wm, b in W.encoder_weights(7):
+        layers += [np.ascontiguousarray(Wm, np.float32), np.ascontiguousarray(b, np.float32)]
+    enc = B.mppi_encoder_create(kw["height"], kw["width"], n, layers, stream)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record()
+            fn()
+            ev[i][1].record()
+        torch.cuda.synchronize()
+        return np.array([a.elapsed_time(b) for a, b in ev])
+
+    def batch():
+        B.mppi_render_depth(cam, n, cams, gates.shape[0], gates, depth, stream)
+        B.mppi_encode_depth(enc, n, depth, kw["max_range"], z)
+
+    ms_batch = timed(batch)
+    ms_enc = timed(lambda: B.mppi_encode_depth(enc, n, depth, kw["max_range"], z))
+    # one drone's control cycle: a view of each gate (the first camera pose that faces it)
+    wl_mppi = W.two_gate_mlp()
+    ctx = make_ctx(B, wl_mppi, "bf16", stream, drone_id)
+    U = torch.zeros(50, 4, device=dev)
+    st = torch.from_numpy(wl_mppi["state"]).to(dev)
+    nom = torch.from_numpy(wl_mppi["nominal"]).to(dev)
+    cyc_cams = cams[:2].contiguous()
+    B.mppi_step_async(ctx, st, None, None, nom, U, None, None)
+
+    def cycle():
+        B.mppi_render_depth(cam, 2, cyc_cams, gates.shape[0], gates, depth, stream)
+        B.mppi_encode_depth(enc, 2, depth, kw["max_range"], z)
+        B.mppi_step_async(ctx, None, None, z, None, U, None, None)
+
+    ms_cycle = timed(cycle)
+    ms_r2 = timed(lambda: B.mppi_render_depth(cam, 2, cyc_cams, gates.shape[0], gates, depth, stream))
+    ms_e2 = timed(lambda: B.mppi_encode_depth(enc, 2, depth, kw["max_range"], z))
+    ms_s = timed(lambda: B.mppi_step_async(ctx, None, None, z, None, U, None, None))
+    B.mppi_sync(ctx)
+    B.mppi_destroy(ctx)
+    B.mppi_encoder_destroy(enc)
+    return {"workload": "depth_views_N64_160x120_G2 + two_gate_mlp_K4096_H50_G2",
+            "batch_render_encode": {"images": n, "mean_ms": float(ms_batch.mean()),
+                                    "images_per_s": n / (ms_batch.mean() * 1e-3)},
+            "encode_only": {"images": n, "mean_ms": float(ms_enc.mean()), "images_per_s": n / (ms_enc.mean() * 1e-3),
+                            "gflop_per_launch": n * ENCODER_FLOPS_PER_IMAGE_160x120 / 1e9,
+                            "achieved_tflops_fp32": n * ENCODER_FLOPS_PER_IMAGE_160x120 / (ms_enc.mean() * 1e-3) / 1e12},
+            "control_cycle": {"p50_ms": float(np.percentile(ms_cycle, 50)), "p99_ms": float(np.percentile(ms_cycle, 99)),
+                              "mean_ms": float(ms_cycle.mean()),
+                              "stages": "render 2 views + encode 2 + MPPI step (BF16)",
+                              "render_2_views_ms": float(ms_r2.mean()), "encode_2_ms": float(ms_e2.mean()),
+                              "mppi_step_with_new_latents_ms": float(ms_s.mean())},
+            "steps": steps}
+
+
 def max_over_ranks(torch, dist, x, device):
     t = torch.tensor([x], device=device, dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -568,6 +647,7 @@ def run_ours(args):
         pass
     render = (render_leg(torch, B, stream, flush, dev, args.render_steps, peaks.get("hbm_gbs") or 6800.0)
               if args.render_steps > 0 else None)
+    vision = vision_leg(torch, B, stream, flush, dev, args.vision_steps, rank) if args.vision_steps > 0 else None
     serving = serving_leg(torch, B, dev, args.serving_seconds) if args.serving_seconds > 0 else None
     distill = distill_leg(torch, B, dev, args.distill_steps) if args.distill_steps > 0 else None
 
@@ -613,6 +693,7 @@ def run_ours(args):
         "hover_gate_analytic": hover,
         "rotor_dynamics": rotor_dyn,
         "depth_render": render,
+        "vision_front_end": vision,
         "serving": serving,
         "distill": distill,
         "gpu_launches": per_launch * args.steps,

@@ -379,6 +379,48 @@ void mppi_depth_camera_default(mppi_depth_camera* cam);
 int mppi_render_depth(const mppi_depth_camera* cam, int n_views, const float* d_cam_poses, int n_gates,
                       const float* d_gate_poses, float* d_depth, void* stream);
 
+/* ======================================================================== vision front end: depth encoder
+ * The depth encoder E_theta of Sec. III-B, which maps the current depth image
+ * to the latent code z once per control cycle (Sec. IV-B).  The paper gives
+ * neither its architecture nor its weights; the reading built here is a small
+ * convolutional encoder of an H x W depth image:
+ *     x_0 = depth / max_range                               (1 channel)
+ *     x_l = relu(conv3x3, stride 2, zero padding 1 (x_{l-1}))  l = 1..4,
+ *           16, 32, 64, 64 channels, H_l = ceil(H_{l-1} / 2)
+ *     z   = W_5 mean_{pixels}(x_4) + b_5                    (64 -> 64)
+ * with out[co][i][j] = b[co] + sum_{ci,ky,kx} W[co][ci][ky][kx]
+ * x[ci][2i+ky-1][2j+kx-1].  The weights are inputs (e.g. of a trained
+ * encoder); the library does not train them.
+ */
+#define MPPI_ENCODER_LAYERS 5
+typedef struct mppi_encoder mppi_encoder;
+/*
+ * Create an encoder for depth images of height x width pixels (1 ..
+ * MPPI_MAX_IMAGE_SIDE) and batches of up to max_images (1 .. 65535) images:
+ *   layers     n_arrays = 10 host arrays W1, b1, W2, b2, W3, b3, W4, b4, W5, b5:
+ *              W_l [c_out][c_in][3][3] (c_in = 1, 16, 32, 64; c_out = 16, 32, 64, 64),
+ *              b_l [c_out], W5 [64][64] row-major, b5 [64]; copied before the call returns
+ *   stream     cudaStream_t the encoder's work goes to (NULL: the legacy default stream)
+ *   *out       the encoder (NULL on error); it holds the weights and the
+ *              activations of max_images images on the current device
+ * Errors: MPPI_E_INVALID, MPPI_E_OOM, MPPI_E_CUDA; message from mppi_encoder_last_error(NULL).
+ */
+int mppi_encoder_create(int height, int width, int max_images, const float* const* layers, int n_arrays,
+                        void* stream, mppi_encoder** out);
+/* Wait for the encoder's stream and free it.  NULL is ignored. */
+void mppi_encoder_destroy(mppi_encoder* enc);
+/* Message of the encoder's last error (enc NULL: the calling thread's last failed create). */
+const char* mppi_encoder_last_error(const mppi_encoder* enc);
+/*
+ * Enqueue the encoding of n_images (0 .. max_images) depth images:
+ *   d_depth    n_images x height x width floats (device), e.g. from mppi_render_depth
+ *   max_range  the depth scale (> 0): inputs are depth / max_range
+ *   d_latents  n_images x 64 floats out (device)
+ * Five kernels on the encoder's stream; calls on one encoder must not overlap.
+ * Errors: MPPI_E_INVALID (nothing enqueued), MPPI_E_CUDA.
+ */
+int mppi_encode_depth(mppi_encoder* enc, int n_images, const float* d_depth, float max_range, float* d_latents);
+
 /* ======================================================================== learned part
  * Distillation of the exact gate-frame SDF (the frame of mppi_config's gate
  * geometry) into the Gate-SDF MLP (Sec. III-B trains the decoder with an L1

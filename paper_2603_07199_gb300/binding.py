@@ -58,6 +58,7 @@ EXPORTS = [
     "mppi_train_step", "mppi_train_loss_grads", "mppi_train_get_weights", "mppi_train_evaluate",
     "mppi_train_read_points", "mppi_train_num_params",
     "mppi_depth_camera_default", "mppi_render_depth",
+    "mppi_encoder_create", "mppi_encoder_destroy", "mppi_encoder_last_error", "mppi_encode_depth",
 ]
 
 
@@ -164,6 +165,11 @@ _SIGS = {
     "mppi_train_read_points": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_size_t]),
     "mppi_train_num_params": (ctypes.c_int, []),
     "mppi_depth_camera_default": (None, [ctypes.POINTER(MppiDepthCamera)]),
+    "mppi_encoder_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp), ctypes.c_int,
+                                           _vp, ctypes.POINTER(_vp)]),
+    "mppi_encoder_destroy": (None, [_vp]),
+    "mppi_encoder_last_error": (ctypes.c_char_p, [_vp]),
+    "mppi_encode_depth": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_float, _vp]),
     "mppi_render_depth": (ctypes.c_int, [ctypes.POINTER(MppiDepthCamera), ctypes.c_int, _vp, ctypes.c_int, _vp, _vp,
                                          _vp]),
 }
@@ -453,3 +459,30 @@ def mppi_render_depth(cam, n_views, d_cam_poses, n_gates, d_gate_poses, d_depth,
     """Enqueue n_views depth images [n_views, height, width] into d_depth (device pointers)."""
     return _check(load().mppi_render_depth(ctypes.byref(cam), n_views, _ptr(d_cam_poses), n_gates,
                                            _ptr(d_gate_poses), _ptr(d_depth), _ptr(stream)))
+
+
+# ------------------------------------------------------------------ vision front end (depth encoder)
+MPPI_ENCODER_LAYERS = 5
+
+
+def _echeck(rc, enc=None):
+    if rc < 0:
+        msg = load().mppi_encoder_last_error(enc)
+        raise MppiError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def mppi_encoder_create(height, width, max_images, layers, stream=None):
+    """layers: [W1, b1, ..., W4, b4, W5, b5] float32 host arrays (see include/mppi.h)."""
+    arr = (_vp * len(layers))(*[_ptr(a) for a in layers])
+    enc = _vp()
+    _echeck(load().mppi_encoder_create(height, width, max_images, arr, len(layers), _ptr(stream), ctypes.byref(enc)))
+    return enc
+
+
+def mppi_encoder_destroy(enc):
+    load().mppi_encoder_destroy(enc)
+
+
+def mppi_encode_depth(enc, n_images, d_depth, max_range, d_latents):
+    return _echeck(load().mppi_encode_depth(enc, n_images, _ptr(d_depth), max_range, _ptr(d_latents)), enc)
