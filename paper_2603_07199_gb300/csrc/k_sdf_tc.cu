@@ -322,7 +322,10 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
     pdl_trigger();
     pdl_wait();
 
-    // tile i (128 consecutive rows of the [K][H] state array) goes to group slot i mod (3 gridDim)
+    // tile i (128 consecutive rows of the [K][H] state array) goes to group slot i mod (3 gridDim),
+    // slot = CTA + gridDim * group: consecutive tiles land on different CTAs, so every CTA gets
+    // floor or ceil of n_tiles / gridDim tiles (numbering the slots 3 CTA + group instead gives
+    // the first CTAs a tile more in every group when the last round is partial)
     // gates queried: all (min over gates), or the target gate only (the paper's form)
     int g_lo = 0, g_hi = G;
     if (P.paper) {
@@ -334,7 +337,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
     const int n_rows = P.K * P.H;
     const int n_tiles = (n_rows + kTileRows - 1) / kTileRows;
     const int nslots = gridDim.x * kGroups;
-    const int slot = blockIdx.x * kGroups + (warp / kGroupWarps);
+    const int slot = blockIdx.x + static_cast<int>(gridDim.x) * (warp / kGroupWarps);
     volatile int* abort_flag = &S.abort_flag;
 
     const int grp = warp / kGroupWarps;
