@@ -22,6 +22,7 @@ __device__ __forceinline__ float softplus_acc(float x, float beta, float inv_bet
 // strips 64 apart, so 16 threads read 256 contiguous bytes per shared load
 __device__ __forceinline__ int strip(int t, int i) { return (i < 4) ? t * 4 + i : 64 + t * 4 + (i - 4); }
 
+template <bool kPE>
 __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_fp32_kernel(StepParams P, StepBuffers B, MlpWeights W) {
     extern __shared__ __align__(16) float smem[];
     float* act = smem;                              // [128][kLdA]
@@ -36,7 +37,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_fp32_kernel(StepParams P,
 
     const int tid = threadIdx.x;
     const int G = P.G;
-    const int NP = 3 + 6 * P.pe;                    // point features: p and its positional encoding
+    const int NP = kPE ? 3 + 6 * P.pe : 3;          // point features: p and its positional encoding
     for (int i = tid; i < NP * kHidden; i += kThreads) {
         const int j = i / kHidden, n = i - j * kHidden;
         sW1[i] = W.W1[n * (NP + kLatent) + j];
@@ -76,7 +77,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_fp32_kernel(StepParams P,
                 sPg[kTileRows + tid] = pg.y;
                 sPg[2 * kTileRows + tid] = pg.z;
                 // positional encoding (Sec. III-B): sin, cos of 2^l pi p per level
-                for (int l = 0; l < P.pe; ++l) {
+                for (int l = 0; l < (kPE ? P.pe : 0); ++l) {
                     const float sc = static_cast<float>(1 << l);
                     float s0, c0, s1, c1, s2, c2;
                     sincospif(sc * pg.x, &s0, &c0);
@@ -92,11 +93,13 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_fp32_kernel(StepParams P,
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int r = strip(tr, i);
+                const float x0 = sPg[r], x1 = sPg[kTileRows + r], x2 = sPg[2 * kTileRows + r];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int n = strip(tn, j);
-                    float a = sB1[g * kHidden + n];
-                    for (int f = 0; f < NP; ++f) a += sW1[f * kHidden + n] * sPg[f * kTileRows + r];
+                    float a = sB1[g * kHidden + n] + sW1[n] * x0 + sW1[kHidden + n] * x1 + sW1[2 * kHidden + n] * x2;
+                    if (kPE)
+                        for (int f = 3; f < NP; ++f) a += sW1[f * kHidden + n] * sPg[f * kTileRows + r];
                     act[n * kLdA + r] = softplus_acc(a, beta, inv_beta);
                 }
             }
@@ -182,15 +185,22 @@ constexpr size_t kSmemBytes = sizeof(float) * (kHidden * kLdA + kHidden * kHidde
 }  // namespace
 
 cudaError_t configure_sdf_mlp_fp32() {
-    return cudaFuncSetAttribute(sdf_mlp_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(kSmemBytes));
+    cudaError_t e = cudaFuncSetAttribute(sdf_mlp_fp32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kSmemBytes));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sdf_mlp_fp32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(kSmemBytes));
+    return e;
 }
 
 cudaError_t launch_sdf_mlp_fp32(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
                                 cudaStream_t s) {
     const int n_items = (P.K * P.H + kTileRows - 1) / kTileRows;
     const int grid = n_items < num_sms ? n_items : num_sms;
-    return launch_dependent(P.pdl != 0, sdf_mlp_fp32_kernel, dim3(grid), dim3(kThreads), kSmemBytes, s, P, B, W);
+    if (P.pe > 0)
+        return launch_dependent(P.pdl != 0, sdf_mlp_fp32_kernel<true>, dim3(grid), dim3(kThreads), kSmemBytes, s, P, B,
+                                W);
+    return launch_dependent(P.pdl != 0, sdf_mlp_fp32_kernel<false>, dim3(grid), dim3(kThreads), kSmemBytes, s, P, B, W);
 }
 
 }  // namespace mppi
