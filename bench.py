@@ -42,7 +42,7 @@ FMA_FLOPS_PER_QUERY = 2 * 3 * 128 + 2 * 128           # layer 1 (point part) + o
 # dram__bytes_read.sum + dram__bytes_write.sum of one sdf_mlp_bf16 launch at this workload, from
 # the ncu capture summarised in profiles/sdf_mlp_tc_bf16_two_gate_K4096_H50_G2.md (None once the
 # kernel changes)
-SDF_BF16_DRAM_BYTES = 3414784
+SDF_BF16_DRAM_BYTES = 3415296
 # multiply-adds x 2 of the depth encoder's convolutions and head for one 160 x 120 image
 ENCODER_FLOPS_PER_IMAGE_160x120 = 2 * (60 * 80 * 16 * 9 * 1 + 30 * 40 * 32 * 9 * 16 + 15 * 20 * 64 * 9 * 32
                                        + 8 * 10 * 64 * 9 * 64 + 64 * 64)
