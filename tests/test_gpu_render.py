@@ -206,3 +206,34 @@ def test_render_edge_cases():
         B.mppi_render_depth(cam, 1, d_cam, B.MPPI_MAX_RENDER_GATES + 1, d_cam, buf)
     with pytest.raises(B.MppiError):
         B.mppi_render_depth(cam, 1, None, 0, None, buf)
+
+
+def test_render_many_gates_and_extreme_shapes():
+    """40 gates (the per-warp gate masks span two 32-lane ballots), an axis-aligned camera whose
+    rays run exactly parallel to slab planes, and images of 8192 x 2 and 3 x 8192 pixels."""
+    rng = np.random.default_rng(5)
+    gates = np.zeros((40, 7), np.float32)
+    gates[:, 0] = rng.uniform(3.0, 25.0, 40)
+    gates[:, 1] = rng.uniform(-6.0, 6.0, 40)
+    gates[:, 2] = rng.uniform(-3.0, 3.0, 40)
+    yaw = rng.uniform(-0.8, 0.8, 40)
+    gates[:, 3] = np.cos(yaw / 2)
+    gates[:, 6] = np.sin(yaw / 2)
+    kw = dict(width=160, height=96, fx=80.0, fy=80.0, cx=80.0, cy=48.0, max_range=30.0)
+    cams = np.array([[0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0], [1.0, -0.5, 0.3, 0.995, 0.0, 0.0, 0.0998]], np.float32)
+    got = _render(_camera(kw), cams, gates)
+    rep = _check_depth(got, *_oracle_triplet(cams, gates, kw), "40 gates")
+    assert np.mean(got < kw["max_range"]) > 0.05
+    # axis-aligned: a gate straight ahead, camera on its axis; pixel centres on the principal
+    # point's row and column give ray components exactly 0 in the gate frame
+    kw2 = dict(width=65, height=33, fx=20.0, fy=20.0, cx=32.5, cy=16.5, max_range=10.0)
+    ahead = np.array([[4.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0]], np.float32)
+    cam0 = np.array([[0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0]], np.float32)
+    got2 = _render(_camera(kw2), cam0, ahead)
+    _check_depth(got2, *_oracle_triplet(cam0, ahead, kw2), "axis-aligned")
+    for shape in [(8192, 2), (3, 8192)]:
+        kw3 = dict(width=shape[0], height=shape[1], fx=1200.0, fy=1200.0, cx=shape[0] / 2, cy=shape[1] / 2,
+                   max_range=12.0)
+        got3 = _render(_camera(kw3), cams[:1], gates)
+        _check_depth(got3, *_oracle_triplet(cams[:1], gates, kw3), f"{shape}")
+    print("many gates", rep)
