@@ -25,6 +25,8 @@ The oracle restates the paper's method step by step in float64 with numpy:
                    casting) and the synthetic sensor noise (Sec. III-B).
 * ``encoder``   -- the depth encoder E_theta (depth image -> latent z) in the stated
                    convolutional reading (Sec. III-B).
+* ``encoder_train`` -- denoising training of the encoder (L1 reconstruction of the pooled
+                   clean image through a linear depth decoder), its gradients and Adam.
 * ``distill``   -- the distillation loss (L1 + Eikonal), its gradients and Adam.
 * ``mppi``      -- per-rollout costs (Eq. 8-10 in the configured form),
                    softmax weights and the weighted update (Eq. 5), the
@@ -37,4 +39,4 @@ states) are passed in by the caller from the seeded generators in
 ``workloads``.
 """
 
-from . import philox, noise, dynamics, rotor, gate_sdf, mlp, mppi, distill, render, encoder  # noqa: F401
+from . import philox, noise, dynamics, rotor, gate_sdf, mlp, mppi, distill, render, encoder, encoder_train  # noqa: F401
