@@ -544,6 +544,19 @@ def vision_leg(torch, B, stream, flush, dev, steps, drone_id):
         B.mppi_encode_depth(enc, 2, depth, kw["max_range"], z)
         B.mppi_step_async(ctx, None, None, z, None, U, None, None)
 
+    # denoising training of the encoder on the batch (noisy input, clean reconstruction target)
+    clean = torch.empty_like(depth)
+    cam_clean = B.mppi_depth_camera_default()
+    for k, v in kw.items():
+        setattr(cam_clean, k, v)
+    B.mppi_render_depth(cam_clean, n, cams, gates.shape[0], gates, clean, stream)
+    B.mppi_render_depth(cam, n, cams, gates.shape[0], gates, depth, stream)
+    T = ((kw["height"] + 7) // 8) * ((kw["width"] + 7) // 8)
+    rng = np.random.default_rng(3)
+    tr = B.mppi_encoder_train_create(enc, n, 3e-3, rng.normal(0.0, 0.1, (T, 64)).astype(np.float32),
+                                     np.full(T, 0.9, np.float32))
+    ms_train = timed(lambda: B.mppi_encoder_train_step(tr, n, depth, clean, kw["max_range"], want_loss=False))
+    B.mppi_encoder_train_destroy(tr)
     ms_cycle = timed(cycle)
     ms_r2 = timed(lambda: B.mppi_render_depth(cam, 2, cyc_cams, gates.shape[0], gates, depth, stream))
     ms_e2 = timed(lambda: B.mppi_encode_depth(enc, 2, depth, kw["max_range"], z))
@@ -557,6 +570,9 @@ def vision_leg(torch, B, stream, flush, dev, steps, drone_id):
             "encode_only": {"images": n, "mean_ms": float(ms_enc.mean()), "images_per_s": n / (ms_enc.mean() * 1e-3),
                             "gflop_per_launch": n * ENCODER_FLOPS_PER_IMAGE_160x120 / 1e9,
                             "achieved_tflops_fp32": n * ENCODER_FLOPS_PER_IMAGE_160x120 / (ms_enc.mean() * 1e-3) / 1e12},
+            "encoder_training": {"images_per_step": n, "mean_ms": float(ms_train.mean()),
+                                 "steps_per_s": 1e3 / float(ms_train.mean()),
+                                 "images_per_s": n / (ms_train.mean() * 1e-3)},
             "control_cycle": {"p50_ms": float(np.percentile(ms_cycle, 50)), "p99_ms": float(np.percentile(ms_cycle, 99)),
                               "mean_ms": float(ms_cycle.mean()),
                               "stages": "render 2 views + encode 2 + MPPI step (BF16)",

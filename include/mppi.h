@@ -421,6 +421,57 @@ const char* mppi_encoder_last_error(const mppi_encoder* enc);
  */
 int mppi_encode_depth(mppi_encoder* enc, int n_images, const float* d_depth, float max_range, float* d_latents);
 
+/*
+ * Copy the encoder's current weights to host arrays (same 10 arrays and layouts as
+ * mppi_encoder_create; a NULL entry is skipped).  Synchronous.
+ */
+int mppi_encoder_get_weights(mppi_encoder* enc, float* const* layers_out);
+
+/* ======================================================================== vision front end: encoder training
+ * Denoising training of the depth encoder: the reconstruction term of the first
+ * (simulation) training stage of Sec. III-B.  The encoder reads noisy depth
+ * images (e.g. mppi_render_depth with sensor noise); a depth decoder D_psi maps
+ * each latent back to a coarse clean image; the L1 loss between the two is
+ * minimised with Adam.  Readings (the paper gives neither D_psi nor its
+ * resolution): the target is the clean image scaled by 1 / max_range and
+ * averaged over 8 x 8 pixel blocks (edge blocks average the pixels they hold),
+ * T = ceil(H / 8) x ceil(W / 8) values; D_psi is one affine map 64 -> T; the
+ * loss is mean |D_psi(E(noisy)) - target| with d|r|/dr = sign(r) (0 at 0);
+ * Adam beta1 = 0.9, beta2 = 0.999, eps = 1e-8, bias-corrected.  The paper's
+ * second term (the SDF decoder on query points) and its second stage are not
+ * built.  The trainer updates the encoder's weights in place, so
+ * mppi_encode_depth uses the trained encoder; it uses the encoder's stream and
+ * activations, so encoder calls must not overlap trainer calls.
+ */
+typedef struct mppi_encoder_trainer mppi_encoder_trainer;
+/*
+ * enc      the encoder to train (outlives the trainer); batch 1 .. its max_images
+ * lr       Adam step size (> 0)
+ * dec_W    T x 64 host floats (row-major), dec_b T host floats: D_psi's initial weights
+ * Errors: MPPI_E_INVALID, MPPI_E_OOM, MPPI_E_CUDA; message from mppi_encoder_train_last_error(NULL).
+ */
+int mppi_encoder_train_create(mppi_encoder* enc, int batch, float lr, const float* dec_W, const float* dec_b,
+                              mppi_encoder_trainer** out);
+void mppi_encoder_train_destroy(mppi_encoder_trainer* trainer);
+const char* mppi_encoder_train_last_error(const mppi_encoder_trainer* trainer);
+/*
+ * Loss and gradients of one batch without updating anything:
+ *   n                 1 .. batch images
+ *   d_noisy, d_clean  n x H x W floats each (device): encoder input and reconstruction source
+ *   max_range         depth scale (> 0)
+ *   loss              host float out (nullable): mean |r|
+ *   grads_out         12 host arrays (nullable; NULL entries skipped): dL/dW1, dL/db1, ..,
+ *                     dL/dW4, dL/db4, dL/dW5, dL/db5 (encoder layouts), dL/dW_D, dL/db_D
+ * Synchronous when loss or grads_out is given.
+ */
+int mppi_encoder_train_loss_grads(mppi_encoder_trainer* trainer, int n, const float* d_noisy, const float* d_clean,
+                                  float max_range, float* loss, float* const* grads_out);
+/* One training step (loss and gradients of the batch, then Adam on all 12 tensors); loss as above. */
+int mppi_encoder_train_step(mppi_encoder_trainer* trainer, int n, const float* d_noisy, const float* d_clean,
+                            float max_range, float* loss);
+/* D_psi's current weights (T x 64 and T host floats).  Synchronous. */
+int mppi_encoder_train_get_decoder(mppi_encoder_trainer* trainer, float* W, float* b);
+
 /* ======================================================================== learned part
  * Distillation of the exact gate-frame SDF (the frame of mppi_config's gate
  * geometry) into the Gate-SDF MLP (Sec. III-B trains the decoder with an L1

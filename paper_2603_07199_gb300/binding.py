@@ -59,6 +59,9 @@ EXPORTS = [
     "mppi_train_read_points", "mppi_train_num_params",
     "mppi_depth_camera_default", "mppi_render_depth",
     "mppi_encoder_create", "mppi_encoder_destroy", "mppi_encoder_last_error", "mppi_encode_depth",
+    "mppi_encoder_get_weights", "mppi_encoder_train_create", "mppi_encoder_train_destroy",
+    "mppi_encoder_train_last_error", "mppi_encoder_train_loss_grads", "mppi_encoder_train_step",
+    "mppi_encoder_train_get_decoder",
 ]
 
 
@@ -170,6 +173,15 @@ _SIGS = {
     "mppi_encoder_destroy": (None, [_vp]),
     "mppi_encoder_last_error": (ctypes.c_char_p, [_vp]),
     "mppi_encode_depth": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_float, _vp]),
+    "mppi_encoder_get_weights": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
+    "mppi_encoder_train_create": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_float, _vp, _vp, ctypes.POINTER(_vp)]),
+    "mppi_encoder_train_destroy": (None, [_vp]),
+    "mppi_encoder_train_last_error": (ctypes.c_char_p, [_vp]),
+    "mppi_encoder_train_loss_grads": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_float,
+                                                     ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_vp)]),
+    "mppi_encoder_train_step": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_float,
+                                               ctypes.POINTER(ctypes.c_float)]),
+    "mppi_encoder_train_get_decoder": (ctypes.c_int, [_vp, _vp, _vp]),
     "mppi_render_depth": (ctypes.c_int, [ctypes.POINTER(MppiDepthCamera), ctypes.c_int, _vp, ctypes.c_int, _vp, _vp,
                                          _vp]),
 }
@@ -486,3 +498,46 @@ def mppi_encoder_destroy(enc):
 
 def mppi_encode_depth(enc, n_images, d_depth, max_range, d_latents):
     return _echeck(load().mppi_encode_depth(enc, n_images, _ptr(d_depth), max_range, _ptr(d_latents)), enc)
+
+
+def mppi_encoder_get_weights(enc, layers_out):
+    arr = (_vp * len(layers_out))(*[_ptr(a) for a in layers_out])
+    return _echeck(load().mppi_encoder_get_weights(enc, arr), enc)
+
+
+# ------------------------------------------------------------------ vision front end (encoder training)
+def _etcheck(rc, trainer=None):
+    if rc < 0:
+        msg = load().mppi_encoder_train_last_error(trainer)
+        raise MppiError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def mppi_encoder_train_create(enc, batch, lr, dec_W, dec_b):
+    tr = _vp()
+    _etcheck(load().mppi_encoder_train_create(enc, batch, lr, _ptr(dec_W), _ptr(dec_b), ctypes.byref(tr)))
+    return tr
+
+
+def mppi_encoder_train_destroy(trainer):
+    load().mppi_encoder_train_destroy(trainer)
+
+
+def mppi_encoder_train_loss_grads(trainer, n, d_noisy, d_clean, max_range, grads_out=None):
+    """Returns the batch loss; fills the 12 host gradient arrays of grads_out when given."""
+    loss = ctypes.c_float()
+    arr = None if grads_out is None else (_vp * len(grads_out))(*[_ptr(a) for a in grads_out])
+    _etcheck(load().mppi_encoder_train_loss_grads(trainer, n, _ptr(d_noisy), _ptr(d_clean), max_range,
+                                                  ctypes.byref(loss), arr), trainer)
+    return loss.value
+
+
+def mppi_encoder_train_step(trainer, n, d_noisy, d_clean, max_range, want_loss=True):
+    loss = ctypes.c_float()
+    _etcheck(load().mppi_encoder_train_step(trainer, n, _ptr(d_noisy), _ptr(d_clean), max_range,
+                                            ctypes.byref(loss) if want_loss else None), trainer)
+    return loss.value if want_loss else None
+
+
+def mppi_encoder_train_get_decoder(trainer, W, b):
+    return _etcheck(load().mppi_encoder_train_get_decoder(trainer, _ptr(W), _ptr(b)), trainer)

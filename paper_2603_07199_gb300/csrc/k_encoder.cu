@@ -18,6 +18,7 @@
 
 #include <cooperative_groups.h>
 
+#include "encoder_internal.h"
 #include "kernels.h"
 #include "mppi.h"
 
@@ -248,19 +249,6 @@ thread_local char g_enc_err[512] = "";
 
 }  // namespace
 }  // namespace mppi
-
-struct mppi_encoder {
-    int H = 0, W = 0, max_images = 0;
-    int h[5] = {0, 0, 0, 0, 0}, w[5] = {0, 0, 0, 0, 0};   // sizes of x_0 .. x_4
-    cudaStream_t stream = nullptr;
-    float* wt[4] = {nullptr, nullptr, nullptr, nullptr};  // [co][ci][3][3] as given
-    float* bias[4] = {nullptr, nullptr, nullptr, nullptr};
-    float* W5 = nullptr;
-    float* b5 = nullptr;
-    float* act[4] = {nullptr, nullptr, nullptr, nullptr};  // x_1 .. x_4
-    int n_sms = 152;
-    char err[512] = "";
-};
 
 namespace {
 

@@ -1,0 +1,573 @@
+// Denoising training of the depth encoder (the reconstruction term of Sec. III-B's first
+// stage): encode noisy depth images, map each latent through a linear depth decoder D_psi to
+// the 8 x 8 block means of the clean image (scaled by 1 / max_range), take the L1 loss, back-
+// propagate through D_psi, the encoder head and the four stride-2 convolutions, and apply
+// Adam to every tensor.  FP32 on the CUDA cores; every reduction runs in a fixed order, so a
+// step is bit-reproducible.
+//
+// Kernels per step (after the encoder's own forward pass, whose activations it keeps):
+//   recon_kernel        per image: target, D_psi(z), residual, sign / (n T), dL/dz
+//   outer_sum_kernel    dL/dW_D, dL/db_D and dL/dW5, dL/db5 (sums over the batch)
+//   head_bwd_kernel     per image: the pooled mean, dL/dm = W5^T dL/dz, and the gradient at
+//                       conv 4's pre-activation (dL/dm / pixels where x4 > 0)
+//   conv_wgrad_kernel   per layer: dL/dW[co][k] = sum over pixels of delta x the gathered
+//                       input tap k (plus a ones column for the bias), split over blocks
+//   wgrad_reduce_kernel the split partial sums, in slice order
+//   conv_dgrad_kernel   per layer above the first: each input pixel gathers the output
+//                       gradients of the (1, 2 or 4 per axis pair) windows that read it,
+//                       times the weights, masked by the ReLU of that input
+//   adam_kernel         all 12 tensors
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <new>
+#include <vector>
+
+#include "encoder_internal.h"
+#include "kernels.h"
+#include "mppi.h"
+
+namespace mppi {
+namespace {
+
+constexpr int kLat = MPPI_LATENT_DIM;
+constexpr int kPool = 8;
+constexpr int kNumTensors = 12;        // W1, b1, .., W4, b4, W5, b5, W_D, b_D
+constexpr int kWgThreads = 256;
+constexpr int kWgK = 32;               // k columns per weight-gradient block
+constexpr int kWgP = 64;               // pixels per staged chunk
+constexpr int kDgThreads = 128;
+constexpr int kDgGroup = 16;           // input channels per data-gradient thread
+
+// ---------------------------------------------------------------- loss and head
+__global__ void __launch_bounds__(256) recon_kernel(const float* __restrict__ z, const float* __restrict__ clean,
+                                                    float inv_range, int H, int W, int th, int tw,
+                                                    const float* __restrict__ Wd, const float* __restrict__ bd,
+                                                    float inv_count, float* __restrict__ g, float* __restrict__ dz,
+                                                    float* __restrict__ loss_img) {
+    __shared__ float sz[kLat];
+    __shared__ float red[256];
+    const int n = blockIdx.x, T = th * tw;
+    if (threadIdx.x < kLat) sz[threadIdx.x] = z[n * kLat + threadIdx.x];
+    __syncthreads();
+    const float* img = clean + static_cast<size_t>(n) * H * W;
+    float l1 = 0.f;
+    for (int t = threadIdx.x; t < T; t += 256) {
+        const int a = t / tw, b = t - (t / tw) * tw;
+        const int y0 = a * kPool, x0 = b * kPool, y1 = min(y0 + kPool, H), x1 = min(x0 + kPool, W);
+        float s = 0.f;
+        for (int yy = y0; yy < y1; ++yy)
+            for (int xx = x0; xx < x1; ++xx) s += img[yy * W + xx];
+        const float target = s * inv_range / static_cast<float>((y1 - y0) * (x1 - x0));
+        float y = bd[t];
+        const float* wr = Wd + static_cast<size_t>(t) * kLat;
+#pragma unroll 8
+        for (int c = 0; c < kLat; ++c) y = fmaf(wr[c], sz[c], y);
+        const float r = y - target;
+        g[static_cast<size_t>(n) * T + t] = (r > 0.f ? inv_count : (r < 0.f ? -inv_count : 0.f));
+        l1 += fabsf(r);
+    }
+    red[threadIdx.x] = l1;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) loss_img[n] = red[0];
+    if (threadIdx.x < kLat) {
+        const int c = threadIdx.x;
+        const float* gn = g + static_cast<size_t>(n) * T;
+        float acc = 0.f;
+        for (int t = 0; t < T; ++t) acc = fmaf(Wd[static_cast<size_t>(t) * kLat + c], gn[t], acc);
+        dz[n * kLat + c] = acc;
+    }
+}
+
+// out[r][c] = sum_i A[i][r] Bm[i][c]; out_b[r] = sum_i A[i][r] (batch order)
+__global__ void __launch_bounds__(256) outer_sum_kernel(const float* __restrict__ A, const float* __restrict__ Bm,
+                                                        int n, int R, int C, float* __restrict__ out,
+                                                        float* __restrict__ out_b) {
+    const int e = blockIdx.x * 256 + threadIdx.x;
+    if (e < R * C) {
+        const int r = e / C, c = e - (e / C) * C;
+        float s = 0.f;
+        for (int i = 0; i < n; ++i) s = fmaf(A[static_cast<size_t>(i) * R + r], Bm[static_cast<size_t>(i) * C + c], s);
+        out[e] = s;
+    }
+    if (e < R) {
+        float s = 0.f;
+        for (int i = 0; i < n; ++i) s += A[static_cast<size_t>(i) * R + e];
+        out_b[e] = s;
+    }
+}
+
+__global__ void __launch_bounds__(kLat) head_bwd_kernel(const float* __restrict__ x4, int hw,
+                                                        const float* __restrict__ W5, const float* __restrict__ dz,
+                                                        float* __restrict__ m4, float* __restrict__ delta4) {
+    const int n = blockIdx.x, c = threadIdx.x;
+    const float* xc = x4 + (static_cast<size_t>(n) * kLat + c) * hw;
+    float s = 0.f;
+    for (int p = 0; p < hw; ++p) s += xc[p];
+    m4[n * kLat + c] = s / static_cast<float>(hw);
+    float dm = 0.f;
+    for (int o = 0; o < kLat; ++o) dm = fmaf(W5[o * kLat + c], dz[n * kLat + o], dm);
+    const float d = dm / static_cast<float>(hw);
+    float* dc = delta4 + (static_cast<size_t>(n) * kLat + c) * hw;
+    for (int p = 0; p < hw; ++p) dc[p] = xc[p] > 0.f ? d : 0.f;
+}
+
+// ---------------------------------------------------------------- convolution gradients
+// Partial sums over a slice of output pixels of dW[co][k] = sum_p delta[co][p] X[k][p], with
+// X[k][p] the layer input at tap k of output pixel p (k = ci 9 + ky 3 + kx, zero outside the
+// image) and X[9 CI][p] = 1 for the bias.  Block: kWgK columns x all CO rows; thread t holds
+// column t % 32 for rows t / 32 + 8 j.
+template <int CI, int CO, bool kScale>
+__global__ void __launch_bounds__(kWgThreads) conv_wgrad_kernel(const float* __restrict__ x,
+                                                                const float* __restrict__ delta, int n_img, int H,
+                                                                int W, int Ho, int Wo, float scale,
+                                                                int chunks_per_slice, float* __restrict__ ws) {
+    constexpr int K1 = 9 * CI + 1;
+    constexpr int kRows = CO / 8;
+    __shared__ float sd[CO][kWgP];
+    __shared__ float sx[kWgP][kWgK + 1];
+    const int hwo = Ho * Wo;
+    const long long P = static_cast<long long>(n_img) * hwo;
+    const long long n_chunks = (P + kWgP - 1) / kWgP;
+    const int k0 = blockIdx.x * kWgK;
+    const int kc = threadIdx.x % kWgK, rg = threadIdx.x / kWgK;
+    float acc[kRows];
+#pragma unroll
+    for (int j = 0; j < kRows; ++j) acc[j] = 0.f;
+    const long long c_begin = static_cast<long long>(blockIdx.y) * chunks_per_slice;
+    const long long c_end = min(c_begin + chunks_per_slice, n_chunks);
+    for (long long ch = c_begin; ch < c_end; ++ch) {
+        const long long p0 = ch * kWgP;
+        __syncthreads();
+        for (int e = threadIdx.x; e < CO * kWgP; e += kWgThreads) {
+            const int co = e / kWgP, pp = e - (e / kWgP) * kWgP;
+            const long long p = p0 + pp;
+            float v = 0.f;
+            if (p < P) {
+                const int n = static_cast<int>(p / hwo);
+                const int pix = static_cast<int>(p - static_cast<long long>(n) * hwo);
+                v = delta[(static_cast<size_t>(n) * CO + co) * hwo + pix];
+            }
+            sd[co][pp] = v;
+        }
+        for (int e = threadIdx.x; e < kWgK * kWgP; e += kWgThreads) {
+            const int pp = e / kWgK, kk = e - (e / kWgK) * kWgK;
+            const long long p = p0 + pp;
+            const int k = k0 + kk;
+            float v = 0.f;
+            if (p < P && k < K1) {
+                if (k == 9 * CI) {
+                    v = 1.f;
+                } else {
+                    const int n = static_cast<int>(p / hwo);
+                    const int pix = static_cast<int>(p - static_cast<long long>(n) * hwo);
+                    const int i = pix / Wo, j = pix - (pix / Wo) * Wo;
+                    const int ci = k / 9, t = k - 9 * (k / 9);
+                    const int yy = 2 * i + t / 3 - 1, xx = 2 * j + t % 3 - 1;
+                    if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+                        v = x[((static_cast<size_t>(n) * CI + ci) * H + yy) * W + xx];
+                        if (kScale) v *= scale;
+                    }
+                }
+            }
+            sx[pp][kk] = v;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int pp = 0; pp < kWgP; ++pp) {
+            const float xv = sx[pp][kc];
+#pragma unroll
+            for (int j = 0; j < kRows; ++j) acc[j] = fmaf(sd[rg + 8 * j][pp], xv, acc[j]);
+        }
+    }
+    const int k = k0 + kc;
+    if (k < K1) {
+#pragma unroll
+        for (int j = 0; j < kRows; ++j)
+            ws[(static_cast<size_t>(blockIdx.y) * CO + rg + 8 * j) * K1 + k] = acc[j];
+    }
+}
+
+// gW[co][k] (= the [co][ci][ky][kx] layout) and gb[co] from the slices' partial sums, in order.
+__global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float* __restrict__ ws, int n_slices, int CO, int K1,
+                                                           float* __restrict__ gW, float* __restrict__ gb) {
+    const int e = blockIdx.x * 256 + threadIdx.x;
+    if (e >= CO * K1) return;
+    const int co = e / K1, k = e - (e / K1) * K1;
+    float s = 0.f;
+    for (int q = 0; q < n_slices; ++q) s += ws[static_cast<size_t>(q) * CO * K1 + e];
+    if (k < K1 - 1)
+        gW[co * (K1 - 1) + k] = s;
+    else
+        gb[co] = s;
+}
+
+// delta_in[n][ci][y][x] = [x_in > 0] sum_{co, ky, kx} W[co][ci][ky][kx] delta[n][co][i][j] over the
+// windows (i, j) = ((y + 1 - ky) / 2, (x + 1 - kx) / 2) that read input pixel (y, x).
+template <int CI, int CO>
+__global__ void __launch_bounds__(kDgThreads) conv_dgrad_kernel(const float* __restrict__ delta,
+                                                                const float* __restrict__ Wt,
+                                                                const float* __restrict__ x_in, int n_img, int H,
+                                                                int W, int Ho, int Wo, float* __restrict__ delta_in) {
+    __shared__ __align__(16) float w_s[CO * 9 * kDgGroup];   // [co][tap][16 input channels]
+    const int c0 = blockIdx.y * kDgGroup;
+    for (int e = threadIdx.x; e < CO * 9 * kDgGroup; e += kDgThreads) {
+        const int co = e / (9 * kDgGroup), rem = e - co * 9 * kDgGroup;
+        const int t = rem / kDgGroup, c = rem - t * kDgGroup;
+        w_s[e] = Wt[(static_cast<size_t>(co) * CI + c0 + c) * 9 + t];
+    }
+    __syncthreads();
+    const int hw = H * W, hwo = Ho * Wo;
+    const long long p = static_cast<long long>(blockIdx.x) * kDgThreads + threadIdx.x;
+    if (p >= static_cast<long long>(n_img) * hw) return;
+    const int n = static_cast<int>(p / hw);
+    const int pix = static_cast<int>(p - static_cast<long long>(n) * hw);
+    const int y = pix / W, xq = pix - (pix / W) * W;
+    // taps along each axis: y odd -> ky in {0, 2}; y even -> ky = 1 (window index (y + 1 - ky) / 2)
+    int kys[2], iys[2], nky = 0, kxs[2], ixs[2], nkx = 0;
+    for (int k = 0; k < 3; ++k) {
+        const int a = y + 1 - k;
+        if ((a & 1) == 0 && a / 2 < Ho) { kys[nky] = k; iys[nky] = a / 2; ++nky; }
+        const int b = xq + 1 - k;
+        if ((b & 1) == 0 && b / 2 < Wo) { kxs[nkx] = k; ixs[nkx] = b / 2; ++nkx; }
+    }
+    float acc[kDgGroup];
+#pragma unroll
+    for (int c = 0; c < kDgGroup; ++c) acc[c] = 0.f;
+    const float* dn = delta + static_cast<size_t>(n) * CO * hwo;
+    const float4* w4 = reinterpret_cast<const float4*>(w_s);
+    for (int co = 0; co < CO; ++co) {
+        for (int a = 0; a < nky; ++a) {
+            for (int b = 0; b < nkx; ++b) {
+                const float d = dn[static_cast<size_t>(co) * hwo + iys[a] * Wo + ixs[b]];
+                const int t = kys[a] * 3 + kxs[b];
+#pragma unroll
+                for (int c4 = 0; c4 < kDgGroup / 4; ++c4) {
+                    const float4 w = w4[(co * 9 + t) * (kDgGroup / 4) + c4];
+                    acc[4 * c4 + 0] = fmaf(w.x, d, acc[4 * c4 + 0]);
+                    acc[4 * c4 + 1] = fmaf(w.y, d, acc[4 * c4 + 1]);
+                    acc[4 * c4 + 2] = fmaf(w.z, d, acc[4 * c4 + 2]);
+                    acc[4 * c4 + 3] = fmaf(w.w, d, acc[4 * c4 + 3]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < kDgGroup; ++c) {
+        const size_t o = (static_cast<size_t>(n) * CI + c0 + c) * hw + pix;
+        delta_in[o] = x_in[o] > 0.f ? acc[c] : 0.f;
+    }
+}
+
+// ---------------------------------------------------------------- Adam
+struct AdamTable {
+    float* p[kNumTensors];
+    const float* g[kNumTensors];
+    float* m[kNumTensors];
+    float* v[kNumTensors];
+    int size[kNumTensors];
+};
+
+__global__ void __launch_bounds__(256) adam_kernel(AdamTable tab, float lr, float c1, float c2) {
+    const int i = blockIdx.y;
+    const int e = blockIdx.x * 256 + threadIdx.x;
+    if (e >= tab.size[i]) return;
+    const float g = tab.g[i][e];
+    const float m = 0.9f * tab.m[i][e] + 0.1f * g;
+    const float v = 0.999f * tab.v[i][e] + 0.001f * g * g;
+    tab.m[i][e] = m;
+    tab.v[i][e] = v;
+    tab.p[i][e] -= lr * (m / c1) / (sqrtf(v / c2) + 1e-8f);
+}
+
+thread_local char g_etr_err[512] = "";
+
+}  // namespace
+}  // namespace mppi
+
+struct mppi_encoder_trainer {
+    mppi_encoder* enc = nullptr;
+    int batch = 0, th = 0, tw = 0, T = 0;
+    float lr = 1e-3f;
+    int step = 0;
+    float* param[mppi::kNumTensors] = {};
+    int size[mppi::kNumTensors] = {};
+    float* grad[mppi::kNumTensors] = {};
+    float* m[mppi::kNumTensors] = {};
+    float* v[mppi::kNumTensors] = {};
+    float* Wd = nullptr;
+    float* bd = nullptr;
+    float* z = nullptr;
+    float* g = nullptr;
+    float* dz = nullptr;
+    float* m4 = nullptr;
+    float* loss_img = nullptr;
+    float* delta[2] = {nullptr, nullptr};
+    float* ws = nullptr;
+    size_t ws_floats = 0;
+    std::vector<void*> allocs;
+    std::vector<float> h_loss;
+    char err[512] = "";
+};
+
+namespace {
+
+int tfail(mppi_encoder_trainer* t, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    std::snprintf(t ? t->err : mppi::g_etr_err, 512, "%s", buf);
+    return code;
+}
+
+bool talloc(mppi_encoder_trainer* t, float** p, size_t n) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(float)) != cudaSuccess) return false;
+    t->allocs.push_back(q);
+    *p = static_cast<float*>(q);
+    return true;
+}
+
+void trainer_free(mppi_encoder_trainer* t) {
+    for (void* p : t->allocs) cudaFree(p);
+    t->allocs.clear();
+}
+
+int wgrad_slices(const mppi_encoder* e, int k_tiles, long long chunks) {
+    const long long want = (2LL * e->n_sms + k_tiles - 1) / k_tiles;
+    return static_cast<int>(std::max(1LL, std::min(want, chunks)));
+}
+
+template <int CI, int CO, bool kScale>
+cudaError_t launch_wgrad(mppi_encoder_trainer* t, int l, int n, const float* x, float scale, const float* delta) {
+    const mppi_encoder* e = t->enc;
+    constexpr int K1 = 9 * CI + 1;
+    const int k_tiles = (K1 + mppi::kWgK - 1) / mppi::kWgK;
+    const long long P = static_cast<long long>(n) * e->h[l + 1] * e->w[l + 1];
+    const long long chunks = (P + mppi::kWgP - 1) / mppi::kWgP;
+    int S = wgrad_slices(e, k_tiles, chunks);
+    while (static_cast<size_t>(S) * CO * K1 > t->ws_floats && S > 1) --S;
+    const int cps = static_cast<int>((chunks + S - 1) / S);
+    S = static_cast<int>((chunks + cps - 1) / cps);
+    mppi::conv_wgrad_kernel<CI, CO, kScale><<<dim3(k_tiles, S), mppi::kWgThreads, 0, e->stream>>>(
+        x, delta, n, e->h[l], e->w[l], e->h[l + 1], e->w[l + 1], scale, cps, t->ws);
+    mppi::wgrad_reduce_kernel<<<(CO * K1 + 255) / 256, 256, 0, e->stream>>>(t->ws, S, CO, K1, t->grad[2 * l],
+                                                                           t->grad[2 * l + 1]);
+    return cudaGetLastError();
+}
+
+template <int CI, int CO>
+cudaError_t launch_dgrad(mppi_encoder_trainer* t, int l, int n, const float* delta, float* delta_in) {
+    const mppi_encoder* e = t->enc;
+    const long long pix = static_cast<long long>(n) * e->h[l] * e->w[l];
+    const dim3 grid(static_cast<unsigned>((pix + mppi::kDgThreads - 1) / mppi::kDgThreads), CI / mppi::kDgGroup);
+    mppi::conv_dgrad_kernel<CI, CO><<<grid, mppi::kDgThreads, 0, e->stream>>>(
+        delta, e->wt[l], e->act[l - 1], n, e->h[l], e->w[l], e->h[l + 1], e->w[l + 1], delta_in);
+    return cudaGetLastError();
+}
+
+// Forward, loss and every gradient of one batch; the loss (mean |r|) goes to *loss when non-NULL.
+int loss_grads(mppi_encoder_trainer* t, int n, const float* d_noisy, const float* d_clean, float max_range,
+               float* loss) {
+    mppi_encoder* e = t->enc;
+    int rc = mppi_encode_depth(e, n, d_noisy, max_range, t->z);
+    if (rc != MPPI_OK) return tfail(t, rc, "encoder forward failed: %s", mppi_encoder_last_error(e));
+    cudaStream_t s = e->stream;
+    const float inv_count = 1.f / (static_cast<float>(n) * static_cast<float>(t->T));
+    mppi::recon_kernel<<<n, 256, 0, s>>>(t->z, d_clean, 1.f / max_range, e->H, e->W, t->th, t->tw, t->Wd, t->bd,
+                                         inv_count, t->g, t->dz, t->loss_img);
+    mppi::outer_sum_kernel<<<(t->T * mppi::kLat + 255) / 256, 256, 0, s>>>(t->g, t->z, n, t->T, mppi::kLat,
+                                                                          t->grad[10], t->grad[11]);
+    const int hw4 = e->h[4] * e->w[4];
+    mppi::head_bwd_kernel<<<n, mppi::kLat, 0, s>>>(e->act[3], hw4, e->W5, t->dz, t->m4, t->delta[0]);
+    mppi::outer_sum_kernel<<<(mppi::kLat * mppi::kLat + 255) / 256, 256, 0, s>>>(t->dz, t->m4, n, mppi::kLat,
+                                                                                mppi::kLat, t->grad[8], t->grad[9]);
+    float* cur = t->delta[0];
+    float* nxt = t->delta[1];
+    cudaError_t ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = launch_wgrad<64, 64, false>(t, 3, n, e->act[2], 1.f, cur);
+    if (ce == cudaSuccess) ce = launch_dgrad<64, 64>(t, 3, n, cur, nxt);
+    std::swap(cur, nxt);
+    if (ce == cudaSuccess) ce = launch_wgrad<32, 64, false>(t, 2, n, e->act[1], 1.f, cur);
+    if (ce == cudaSuccess) ce = launch_dgrad<32, 64>(t, 2, n, cur, nxt);
+    std::swap(cur, nxt);
+    if (ce == cudaSuccess) ce = launch_wgrad<16, 32, false>(t, 1, n, e->act[0], 1.f, cur);
+    if (ce == cudaSuccess) ce = launch_dgrad<16, 32>(t, 1, n, cur, nxt);
+    std::swap(cur, nxt);
+    if (ce == cudaSuccess) ce = launch_wgrad<1, 16, true>(t, 0, n, d_noisy, 1.f / max_range, cur);
+    if (ce != cudaSuccess) return tfail(t, MPPI_E_CUDA, "launch failed: %s", cudaGetErrorString(ce));
+    if (loss) {
+        t->h_loss.resize(n);
+        ce = cudaMemcpyAsync(t->h_loss.data(), t->loss_img, n * sizeof(float), cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) return tfail(t, MPPI_E_CUDA, "loss read-back failed: %s", cudaGetErrorString(ce));
+        double sum = 0.0;
+        for (int i = 0; i < n; ++i) sum += t->h_loss[i];
+        *loss = static_cast<float>(sum * inv_count);
+    }
+    return MPPI_OK;
+}
+
+int check_batch(mppi_encoder_trainer* t, int n, const float* d_noisy, const float* d_clean, float max_range) {
+    if (n < 1 || n > t->batch) return tfail(t, MPPI_E_INVALID, "n out of [1, batch = %d]", t->batch);
+    if (!d_noisy || !d_clean) return tfail(t, MPPI_E_INVALID, "NULL image pointer");
+    if (!(max_range > 0.f && max_range <= 3.0e38f)) return tfail(t, MPPI_E_INVALID, "max_range must be > 0");
+    return MPPI_OK;
+}
+
+}  // namespace
+
+extern "C" int mppi_encoder_get_weights(mppi_encoder* e, float* const* layers_out) {
+    if (!e || !layers_out) return MPPI_E_INVALID;
+    cudaError_t ce = cudaStreamSynchronize(e->stream);
+    for (int l = 0; l < 4 && ce == cudaSuccess; ++l) {
+        const size_t nw = static_cast<size_t>(mppi::kEncCout[l]) * mppi::kEncCin[l] * 9;
+        if (layers_out[2 * l]) ce = cudaMemcpy(layers_out[2 * l], e->wt[l], nw * sizeof(float), cudaMemcpyDeviceToHost);
+        if (ce == cudaSuccess && layers_out[2 * l + 1])
+            ce = cudaMemcpy(layers_out[2 * l + 1], e->bias[l], mppi::kEncCout[l] * sizeof(float),
+                            cudaMemcpyDeviceToHost);
+    }
+    if (ce == cudaSuccess && layers_out[8])
+        ce = cudaMemcpy(layers_out[8], e->W5, MPPI_LATENT_DIM * MPPI_LATENT_DIM * sizeof(float), cudaMemcpyDeviceToHost);
+    if (ce == cudaSuccess && layers_out[9])
+        ce = cudaMemcpy(layers_out[9], e->b5, MPPI_LATENT_DIM * sizeof(float), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) {
+        std::snprintf(e->err, sizeof(e->err), "mppi_encoder_get_weights: %s", cudaGetErrorString(ce));
+        return MPPI_E_CUDA;
+    }
+    return MPPI_OK;
+}
+
+extern "C" int mppi_encoder_train_create(mppi_encoder* enc, int batch, float lr, const float* dec_W,
+                                         const float* dec_b, mppi_encoder_trainer** out) {
+    using namespace mppi;
+    if (!out) return tfail(nullptr, MPPI_E_INVALID, "mppi_encoder_train_create: NULL out");
+    *out = nullptr;
+    if (!enc || !dec_W || !dec_b) return tfail(nullptr, MPPI_E_INVALID, "mppi_encoder_train_create: NULL argument");
+    if (batch < 1 || batch > enc->max_images)
+        return tfail(nullptr, MPPI_E_INVALID, "mppi_encoder_train_create: batch out of [1, max_images = %d]",
+                     enc->max_images);
+    if (!(lr > 0.f && lr < 1e3f)) return tfail(nullptr, MPPI_E_INVALID, "mppi_encoder_train_create: lr must be > 0");
+    mppi_encoder_trainer* t = new (std::nothrow) mppi_encoder_trainer();
+    if (!t) return tfail(nullptr, MPPI_E_OOM, "mppi_encoder_train_create: host allocation failed");
+    t->enc = enc;
+    t->batch = batch;
+    t->lr = lr;
+    t->th = (enc->H + kPool - 1) / kPool;
+    t->tw = (enc->W + kPool - 1) / kPool;
+    t->T = t->th * t->tw;
+    bool ok = talloc(t, &t->Wd, static_cast<size_t>(t->T) * kLat) && talloc(t, &t->bd, t->T);
+    for (int l = 0; l < 4; ++l) {
+        t->param[2 * l] = enc->wt[l];
+        t->size[2 * l] = kEncCout[l] * kEncCin[l] * 9;
+        t->param[2 * l + 1] = enc->bias[l];
+        t->size[2 * l + 1] = kEncCout[l];
+    }
+    t->param[8] = enc->W5;
+    t->size[8] = kLat * kLat;
+    t->param[9] = enc->b5;
+    t->size[9] = kLat;
+    t->param[10] = t->Wd;
+    t->size[10] = t->T * kLat;
+    t->param[11] = t->bd;
+    t->size[11] = t->T;
+    for (int i = 0; i < kNumTensors && ok; ++i)
+        ok = talloc(t, &t->grad[i], t->size[i]) && talloc(t, &t->m[i], t->size[i]) && talloc(t, &t->v[i], t->size[i]);
+    size_t delta_floats = 0;
+    for (int l = 0; l < 4; ++l)
+        delta_floats = std::max(delta_floats, static_cast<size_t>(batch) * kEncCout[l] * enc->h[l + 1] * enc->w[l + 1]);
+    // a split layer has S <= ceil(2 SMs / k_tiles) slices of CO x K1 <= 64 x 32 k_tiles floats
+    t->ws_floats = static_cast<size_t>(64) * kWgK * (2 * enc->n_sms + 32);
+    ok = ok && talloc(t, &t->z, static_cast<size_t>(batch) * kLat) &&
+         talloc(t, &t->g, static_cast<size_t>(batch) * t->T) && talloc(t, &t->dz, static_cast<size_t>(batch) * kLat) &&
+         talloc(t, &t->m4, static_cast<size_t>(batch) * kLat) && talloc(t, &t->loss_img, batch) &&
+         talloc(t, &t->delta[0], delta_floats) && talloc(t, &t->delta[1], delta_floats) &&
+         talloc(t, &t->ws, t->ws_floats);
+    if (ok) {
+        ok = cudaMemcpy(t->Wd, dec_W, static_cast<size_t>(t->T) * kLat * sizeof(float), cudaMemcpyHostToDevice) ==
+                 cudaSuccess &&
+             cudaMemcpy(t->bd, dec_b, t->T * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
+        for (int i = 0; i < kNumTensors && ok; ++i)
+            ok = cudaMemset(t->m[i], 0, t->size[i] * sizeof(float)) == cudaSuccess &&
+                 cudaMemset(t->v[i], 0, t->size[i] * sizeof(float)) == cudaSuccess;
+    }
+    if (!ok) {
+        const cudaError_t ce = cudaGetLastError();
+        trainer_free(t);
+        delete t;
+        return tfail(nullptr, ce == cudaErrorMemoryAllocation ? MPPI_E_OOM : MPPI_E_CUDA,
+                     "mppi_encoder_train_create: device allocation or copy failed: %s", cudaGetErrorString(ce));
+    }
+    *out = t;
+    return MPPI_OK;
+}
+
+extern "C" void mppi_encoder_train_destroy(mppi_encoder_trainer* t) {
+    if (!t) return;
+    cudaStreamSynchronize(t->enc->stream);
+    trainer_free(t);
+    delete t;
+}
+
+extern "C" const char* mppi_encoder_train_last_error(const mppi_encoder_trainer* t) {
+    return t ? t->err : mppi::g_etr_err;
+}
+
+extern "C" int mppi_encoder_train_loss_grads(mppi_encoder_trainer* t, int n, const float* d_noisy,
+                                             const float* d_clean, float max_range, float* loss,
+                                             float* const* grads_out) {
+    if (!t) return tfail(nullptr, MPPI_E_INVALID, "mppi_encoder_train_loss_grads: NULL trainer");
+    int rc = check_batch(t, n, d_noisy, d_clean, max_range);
+    if (rc != MPPI_OK) return rc;
+    rc = loss_grads(t, n, d_noisy, d_clean, max_range, loss);
+    if (rc != MPPI_OK || !grads_out) return rc;
+    cudaError_t ce = cudaStreamSynchronize(t->enc->stream);
+    for (int i = 0; i < mppi::kNumTensors && ce == cudaSuccess; ++i)
+        if (grads_out[i])
+            ce = cudaMemcpy(grads_out[i], t->grad[i], t->size[i] * sizeof(float), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return tfail(t, MPPI_E_CUDA, "gradient read-back failed: %s", cudaGetErrorString(ce));
+    return MPPI_OK;
+}
+
+extern "C" int mppi_encoder_train_step(mppi_encoder_trainer* t, int n, const float* d_noisy, const float* d_clean,
+                                       float max_range, float* loss) {
+    if (!t) return tfail(nullptr, MPPI_E_INVALID, "mppi_encoder_train_step: NULL trainer");
+    int rc = check_batch(t, n, d_noisy, d_clean, max_range);
+    if (rc != MPPI_OK) return rc;
+    rc = loss_grads(t, n, d_noisy, d_clean, max_range, loss);
+    if (rc != MPPI_OK) return rc;
+    t->step += 1;
+    mppi::AdamTable tab{};
+    int max_size = 0;
+    for (int i = 0; i < mppi::kNumTensors; ++i) {
+        tab.p[i] = t->param[i];
+        tab.g[i] = t->grad[i];
+        tab.m[i] = t->m[i];
+        tab.v[i] = t->v[i];
+        tab.size[i] = t->size[i];
+        max_size = std::max(max_size, t->size[i]);
+    }
+    const float c1 = static_cast<float>(1.0 - std::pow(0.9, t->step));
+    const float c2 = static_cast<float>(1.0 - std::pow(0.999, t->step));
+    mppi::adam_kernel<<<dim3((max_size + 255) / 256, mppi::kNumTensors), 256, 0, t->enc->stream>>>(tab, t->lr, c1, c2);
+    const cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) return tfail(t, MPPI_E_CUDA, "Adam launch failed: %s", cudaGetErrorString(ce));
+    return MPPI_OK;
+}
+
+extern "C" int mppi_encoder_train_get_decoder(mppi_encoder_trainer* t, float* W, float* b) {
+    if (!t || !W || !b) return tfail(t, MPPI_E_INVALID, "mppi_encoder_train_get_decoder: NULL argument");
+    cudaError_t ce = cudaStreamSynchronize(t->enc->stream);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpy(W, t->Wd, static_cast<size_t>(t->T) * mppi::kLat * sizeof(float), cudaMemcpyDeviceToHost);
+    if (ce == cudaSuccess) ce = cudaMemcpy(b, t->bd, t->T * sizeof(float), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return tfail(t, MPPI_E_CUDA, "decoder read-back failed: %s", cudaGetErrorString(ce));
+    return MPPI_OK;
+}

@@ -1,0 +1,142 @@
+"""GPU parity of the depth encoder's denoising training (the reconstruction term of Sec. III-B's
+first stage) against the FP64 oracle, through the C ABI, and what training gains.
+
+Gradient bar: every tensor within 2e-3 of its largest oracle entry (FP32 sums of up to ~1e5
+products; a ReLU or an L1 sign decided differently by rounding moves one term).  One Adam step:
+the weights within 1e-6 + 1e-3 lr of the oracle's where the gradient is not within rounding of 0
+(the first Adam step is lr g / |g|)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import encoder_train as OT
+from oracle import render as R
+from paper_2603_07199_gb300 import binding as B
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _flat(layers):
+    out = []
+    for Wm, b in layers:
+        out += [np.ascontiguousarray(Wm, np.float32), np.ascontiguousarray(b, np.float32)]
+    return out
+
+
+def _data(n, h, w, seed):
+    gates = W.gate_track(2)
+    cams = W.camera_views(n, gates, seed=seed)
+    kw = dict(width=w, height=h, fx=w * 0.6, fy=w * 0.6, cx=w / 2, cy=h / 2, max_range=10.0)
+    clean = R.depth_images(cams, gates, **kw)
+    noisy = R.add_sensor_noise(clean, 10.0, 0.01, 0.03, seed=seed, frame=1)
+    return noisy.astype(np.float32), clean.astype(np.float32)
+
+
+def _decoder(T, seed=3):
+    rng = np.random.default_rng(seed)
+    return rng.normal(0.0, 0.1, (T, 64)).astype(np.float32), np.zeros(T, np.float32)
+
+
+def _setup(h, w, n, batch):
+    torch = _torch()
+    enc_layers = W.encoder_weights(7)
+    enc = B.mppi_encoder_create(h, w, batch, _flat(enc_layers))
+    T = -(-h // 8) * -(-w // 8)
+    Wd, bd = _decoder(T)
+    tr = B.mppi_encoder_train_create(enc, batch, 1e-3, Wd, bd)
+    noisy, clean = _data(n, h, w, seed=17)
+    return torch, enc, tr, enc_layers, (Wd, bd), noisy, clean
+
+
+def _shapes(enc_layers, dec):
+    return [a.shape for pair in enc_layers for a in pair] + [dec[0].shape, dec[1].shape]
+
+
+def test_gradients_match_oracle():
+    torch, enc, tr, enc_layers, dec, noisy, clean = _setup(37, 53, 3, 4)
+    try:
+        grads = [np.zeros(s, np.float32) for s in _shapes(enc_layers, dec)]
+        loss = B.mppi_encoder_train_loss_grads(tr, 3, torch.from_numpy(noisy).cuda(),
+                                               torch.from_numpy(clean).cuda(), 10.0, grads)
+    finally:
+        B.mppi_encoder_train_destroy(tr)
+        B.mppi_encoder_destroy(enc)
+    L, g_enc, g_dec = OT.gradients(noisy, clean, 10.0, enc_layers, dec)
+    assert abs(loss - L) <= 1e-5 * L
+    want = [g for pair in g_enc for g in pair] + list(g_dec)
+    for i, (got, ref) in enumerate(zip(grads, want)):
+        scale = np.max(np.abs(ref))
+        err = np.max(np.abs(got - ref))
+        assert scale > 0 and err <= 2e-3 * scale, (i, err, scale)
+
+
+def test_one_adam_step_matches_oracle():
+    torch, enc, tr, enc_layers, dec, noisy, clean = _setup(37, 53, 3, 4)
+    try:
+        B.mppi_encoder_train_step(tr, 3, torch.from_numpy(noisy).cuda(), torch.from_numpy(clean).cuda(), 10.0)
+        after = [np.zeros(s, np.float32) for s in _shapes(enc_layers, dec)]
+        B.mppi_encoder_get_weights(enc, after[:10])
+        B.mppi_encoder_train_get_decoder(tr, after[10], after[11])
+    finally:
+        B.mppi_encoder_train_destroy(tr)
+        B.mppi_encoder_destroy(enc)
+    _, g_enc, g_dec = OT.gradients(noisy, clean, 10.0, enc_layers, dec)
+    grads = [g for pair in g_enc for g in pair] + list(g_dec)
+    params = [np.asarray(a, np.float64) for pair in enc_layers for a in pair] + [np.asarray(a, np.float64) for a in dec]
+    want, _, _ = OT.adam_step(params, grads, [np.zeros_like(p) for p in params], [np.zeros_like(p) for p in params],
+                              1, 1e-3)
+    for i, (got, ref, g) in enumerate(zip(after, want, grads)):
+        sure = np.abs(g) > 1e-2 * np.max(np.abs(g))
+        err = np.abs(got - ref)[sure]
+        assert err.size and np.max(err) <= 1e-6 + 1e-6, (i, np.max(err))
+
+
+def test_training_reduces_heldout_reconstruction_error():
+    """1500 steps (batch 32, lr 3e-3, the decoder's bias started at 0.9, near the mean scaled
+    depth) on 2048 GPU-rendered noisy / clean pairs of the two-gate track (64 x 48): the held-out
+    L1 reconstruction error must fall below half its starting value and 15 % below that of the
+    best image-independent prediction, and the trained encoder must still encode."""
+    torch = _torch()
+    h, w, n_train, n_test, batch = 48, 64, 2048, 64, 32
+    gates = W.gate_track(2)
+    cam = B.mppi_depth_camera_default()
+    for k, v in dict(width=w, height=h, fx=38.5, fy=38.5, cx=32.0, cy=24.0, max_range=10.0).items():
+        setattr(cam, k, v)
+    cams = torch.from_numpy(np.ascontiguousarray(W.camera_views(n_train + n_test, gates, seed=44), np.float32)).cuda()
+    d_gates = torch.from_numpy(np.ascontiguousarray(gates, np.float32)).cuda()
+    clean = torch.empty(n_train + n_test, h, w, device="cuda")
+    noisy = torch.empty_like(clean)
+    B.mppi_render_depth(cam, n_train + n_test, cams, 2, d_gates, clean)
+    cam.noise_depth_coeff, cam.dropout, cam.seed = 0.01, 0.03, 5
+    B.mppi_render_depth(cam, n_train + n_test, cams, 2, d_gates, noisy)
+    enc = B.mppi_encoder_create(h, w, n_test, _flat(W.encoder_weights(7)))
+    Wd, bd = _decoder(6 * 8)
+    bd[:] = 0.9
+    tr = B.mppi_encoder_train_create(enc, n_test, 3e-3, Wd, bd)
+    try:
+        test_noisy, test_clean = noisy[n_train:], clean[n_train:]
+        before = B.mppi_encoder_train_loss_grads(tr, n_test, test_noisy, test_clean, 10.0)
+        rng = np.random.default_rng(0)
+        for _ in range(1500):
+            idx = torch.from_numpy(rng.choice(n_train, batch, replace=False)).cuda()
+            B.mppi_encoder_train_step(tr, batch, noisy[idx].contiguous(), clean[idx].contiguous(), 10.0,
+                                      want_loss=False)
+        after = B.mppi_encoder_train_loss_grads(tr, n_test, test_noisy, test_clean, 10.0)
+        z = torch.empty(n_test, 64, device="cuda")
+        B.mppi_encode_depth(enc, n_test, test_noisy, 10.0, z)
+        torch.cuda.synchronize()
+        assert np.isfinite(z.cpu().numpy()).all()
+    finally:
+        B.mppi_encoder_train_destroy(tr)
+        B.mppi_encoder_destroy(enc)
+    # the best image-independent prediction: the per-block median of the training targets
+    tgt = torch.nn.functional.avg_pool2d(clean[:, None] / 10.0, 8)[:, 0]
+    const_l1 = float((tgt[n_train:] - tgt[:n_train].median(dim=0).values).abs().mean())
+    print(f"held-out L1 reconstruction error {before:.4f} -> {after:.4f} (best constant {const_l1:.4f})")
+    assert after < 0.5 * before
+    assert after < 0.85 * const_l1   # the encoder's latent carries information about the image
