@@ -12,7 +12,8 @@
 //                       conv 4's pre-activation (dL/dm / pixels where x4 > 0)
 //   conv_wgrad_kernel   per layer: dL/dW[co][k] = sum over pixels of delta x the gathered
 //                       input tap k (plus a ones column for the bias), split over blocks
-//   wgrad_reduce_kernel the split partial sums, in slice order
+//   wgrad_reduce_kernel the split partial sums, in slice order (a block per element when
+//                       there are many slices)
 //   conv_dgrad_kernel   per layer above the first: each input pixel gathers the output
 //                       gradients of the (1, 2 or 4 per axis pair) windows that read it,
 //                       times the weights, masked by the ReLU of that input
@@ -120,25 +121,28 @@ __global__ void __launch_bounds__(kLat) head_bwd_kernel(const float* __restrict_
 // ---------------------------------------------------------------- convolution gradients
 // Partial sums over a slice of output pixels of dW[co][k] = sum_p delta[co][p] X[k][p], with
 // X[k][p] the layer input at tap k of output pixel p (k = ci 9 + ky 3 + kx, zero outside the
-// image) and X[9 CI][p] = 1 for the bias.  Block: kWgK columns x all CO rows; thread t holds
-// column t % 32 for rows t / 32 + 8 j.
+// image) and X[9 CI][p] = 1 for the bias.  Block: kWgK columns x all CO rows over 64-pixel
+// chunks staged in shared memory (both [row][pixel], padded); thread t holds columns
+// 2 (t % 16) + {0, 1} for rows (t / 16) CO / 16 + {0 .. CO / 16 - 1} and reads 4 pixels per
+// 16-byte load.
 template <int CI, int CO, bool kScale>
 __global__ void __launch_bounds__(kWgThreads) conv_wgrad_kernel(const float* __restrict__ x,
                                                                 const float* __restrict__ delta, int n_img, int H,
                                                                 int W, int Ho, int Wo, float scale,
                                                                 int chunks_per_slice, float* __restrict__ ws) {
     constexpr int K1 = 9 * CI + 1;
-    constexpr int kRows = CO / 8;
-    __shared__ float sd[CO][kWgP];
-    __shared__ float sx[kWgP][kWgK + 1];
+    constexpr int RT = CO / 16;                  // rows per thread
+    constexpr int kLd = kWgP + 4;
+    __shared__ __align__(16) float sd[CO][kLd];
+    __shared__ __align__(16) float sx[kWgK][kLd];
     const int hwo = Ho * Wo;
     const long long P = static_cast<long long>(n_img) * hwo;
     const long long n_chunks = (P + kWgP - 1) / kWgP;
     const int k0 = blockIdx.x * kWgK;
-    const int kc = threadIdx.x % kWgK, rg = threadIdx.x / kWgK;
-    float acc[kRows];
+    const int kp = threadIdx.x % 16, rg = threadIdx.x / 16;
+    float acc[RT][2];
 #pragma unroll
-    for (int j = 0; j < kRows; ++j) acc[j] = 0.f;
+    for (int j = 0; j < RT; ++j) acc[j][0] = acc[j][1] = 0.f;
     const long long c_begin = static_cast<long long>(blockIdx.y) * chunks_per_slice;
     const long long c_end = min(c_begin + chunks_per_slice, n_chunks);
     for (long long ch = c_begin; ch < c_end; ++ch) {
@@ -156,7 +160,7 @@ __global__ void __launch_bounds__(kWgThreads) conv_wgrad_kernel(const float* __r
             sd[co][pp] = v;
         }
         for (int e = threadIdx.x; e < kWgK * kWgP; e += kWgThreads) {
-            const int pp = e / kWgK, kk = e - (e / kWgK) * kWgK;
+            const int kk = e / kWgP, pp = e - (e / kWgP) * kWgP;
             const long long p = p0 + pp;
             const int k = k0 + kk;
             float v = 0.f;
@@ -175,25 +179,34 @@ __global__ void __launch_bounds__(kWgThreads) conv_wgrad_kernel(const float* __r
                     }
                 }
             }
-            sx[pp][kk] = v;
+            sx[kk][pp] = v;
         }
         __syncthreads();
 #pragma unroll 4
-        for (int pp = 0; pp < kWgP; ++pp) {
-            const float xv = sx[pp][kc];
+        for (int pp = 0; pp < kWgP; pp += 4) {
+            const float4 x0 = *reinterpret_cast<const float4*>(&sx[2 * kp][pp]);
+            const float4 x1 = *reinterpret_cast<const float4*>(&sx[2 * kp + 1][pp]);
 #pragma unroll
-            for (int j = 0; j < kRows; ++j) acc[j] = fmaf(sd[rg + 8 * j][pp], xv, acc[j]);
+            for (int j = 0; j < RT; ++j) {
+                const float4 d = *reinterpret_cast<const float4*>(&sd[rg * RT + j][pp]);
+                acc[j][0] = fmaf(d.x, x0.x, fmaf(d.y, x0.y, fmaf(d.z, x0.z, fmaf(d.w, x0.w, acc[j][0]))));
+                acc[j][1] = fmaf(d.x, x1.x, fmaf(d.y, x1.y, fmaf(d.z, x1.z, fmaf(d.w, x1.w, acc[j][1]))));
+            }
         }
     }
-    const int k = k0 + kc;
-    if (k < K1) {
 #pragma unroll
-        for (int j = 0; j < kRows; ++j)
-            ws[(static_cast<size_t>(blockIdx.y) * CO + rg + 8 * j) * K1 + k] = acc[j];
+    for (int c = 0; c < 2; ++c) {
+        const int k = k0 + 2 * kp + c;
+        if (k < K1) {
+#pragma unroll
+            for (int j = 0; j < RT; ++j)
+                ws[(static_cast<size_t>(blockIdx.y) * CO + rg * RT + j) * K1 + k] = acc[j][c];
+        }
     }
 }
 
-// gW[co][k] (= the [co][ci][ky][kx] layout) and gb[co] from the slices' partial sums, in order.
+// gW[co][k] (= the [co][ci][ky][kx] layout) and gb[co] from the slices' partial sums, in slice
+// order: one thread per element.
 __global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float* __restrict__ ws, int n_slices, int CO, int K1,
                                                            float* __restrict__ gW, float* __restrict__ gb) {
     const int e = blockIdx.x * 256 + threadIdx.x;
@@ -205,6 +218,29 @@ __global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float* __restri
         gW[co * (K1 - 1) + k] = s;
     else
         gb[co] = s;
+}
+
+// The same for many slices: one block per element, 128 strided partial sums, a fixed tree.
+__global__ void __launch_bounds__(128) wgrad_reduce_wide_kernel(const float* __restrict__ ws, int n_slices, int CO,
+                                                                int K1, float* __restrict__ gW,
+                                                                float* __restrict__ gb) {
+    __shared__ float red[128];
+    const int e = blockIdx.x;
+    const int co = e / K1, k = e - (e / K1) * K1;
+    float s = 0.f;
+    for (int q = threadIdx.x; q < n_slices; q += 128) s += ws[static_cast<size_t>(q) * CO * K1 + e];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 64; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (k < K1 - 1)
+            gW[co * (K1 - 1) + k] = red[0];
+        else
+            gb[co] = red[0];
+    }
 }
 
 // delta_in[n][ci][y][x] = [x_in > 0] sum_{co, ky, kx} W[co][ci][ky][kx] delta[n][co][i][j] over the
@@ -358,8 +394,12 @@ cudaError_t launch_wgrad(mppi_encoder_trainer* t, int l, int n, const float* x, 
     S = static_cast<int>((chunks + cps - 1) / cps);
     mppi::conv_wgrad_kernel<CI, CO, kScale><<<dim3(k_tiles, S), mppi::kWgThreads, 0, e->stream>>>(
         x, delta, n, e->h[l], e->w[l], e->h[l + 1], e->w[l + 1], scale, cps, t->ws);
-    mppi::wgrad_reduce_kernel<<<(CO * K1 + 255) / 256, 256, 0, e->stream>>>(t->ws, S, CO, K1, t->grad[2 * l],
-                                                                           t->grad[2 * l + 1]);
+    if (S > 32)
+        mppi::wgrad_reduce_wide_kernel<<<CO * K1, 128, 0, e->stream>>>(t->ws, S, CO, K1, t->grad[2 * l],
+                                                                       t->grad[2 * l + 1]);
+    else
+        mppi::wgrad_reduce_kernel<<<(CO * K1 + 255) / 256, 256, 0, e->stream>>>(t->ws, S, CO, K1, t->grad[2 * l],
+                                                                               t->grad[2 * l + 1]);
     return cudaGetLastError();
 }
 
