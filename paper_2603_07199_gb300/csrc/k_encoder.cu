@@ -6,7 +6,8 @@
 // (implicit im2col): all-channel x (4096 / CO)-pixel block tiles, 16-deep chunks staged
 // in shared memory, 4 x 4 outputs per thread, and the reduction split over the blocks of
 // a thread-block cluster, summed through distributed shared memory, when a layer has too
-// few tiles to fill the GPU (small batches, deep layers).
+// few tiles to fill the GPU (small batches, deep layers).  Layers are programmatic dependent
+// launches: a layer's grid launches while the previous one drains and waits for its output.
 // Activations are NCHW in device memory (L2-resident at these sizes); the first
 // layer scales the depths by 1 / max_range as it reads them.  The head (mean over
 // pixels, 64 x 64 matrix) is one block per image.
@@ -129,6 +130,10 @@ __global__ void __launch_bounds__(kConvThreads) conv3x3s2_gemm_kernel(const floa
             }
         }
     };
+    // programmatic dependent launch: let the next layer's grid start launching, and wait for
+    // the previous kernel's output (a no-op when launched without the attribute)
+    pdl_trigger();
+    pdl_wait();
     if (c_begin < c_end) load_chunk(c_begin);
     for (int ch = c_begin; ch < c_end; ++ch) {
         __syncthreads();
@@ -218,6 +223,7 @@ __global__ void __launch_bounds__(kHeadThreads) encoder_head_kernel(const float*
     __shared__ float m[kLatent];
     const int n = blockIdx.x, c = threadIdx.x % kLatent, q = threadIdx.x / kLatent;
     for (int e = threadIdx.x; e < kLatent * kLatent; e += kHeadThreads) w_s[e / kLatent][e % kLatent] = W5[e];
+    pdl_wait();
     const float* xc = x4 + (static_cast<size_t>(n) * kLatent + c) * hw;
     float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
     int k = q;
@@ -293,13 +299,15 @@ cudaError_t launch_conv(const mppi_encoder* e, int l, int n, const float* x, flo
     cfg.gridDim = dim3(static_cast<unsigned>(tiles), 1, split);
     cfg.blockDim = dim3(mppi::kConvThreads);
     cfg.stream = e->stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 1;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = split;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = 1;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = split;
     cfg.attrs = attr;
-    cfg.numAttrs = split > 1 ? 1 : 0;
+    cfg.numAttrs = split > 1 ? 2 : 1;
     return cudaLaunchKernelEx(&cfg, mppi::conv3x3s2_gemm_kernel<CI, CO, kScale>, x, n, e->h[l], e->w[l], e->h[l + 1],
                               e->w[l + 1], static_cast<const float*>(e->wt[l]), static_cast<const float*>(e->bias[l]),
                               scale, cps, y);
@@ -388,9 +396,9 @@ extern "C" int mppi_encode_depth(mppi_encoder* e, int n_images, const float* d_d
     if (ce == cudaSuccess) ce = launch_conv<32, 64, false>(e, 2, n_images, e->act[1], 1.f, e->act[2]);
     if (ce == cudaSuccess) ce = launch_conv<64, 64, false>(e, 3, n_images, e->act[2], 1.f, e->act[3]);
     if (ce == cudaSuccess) {
-        mppi::encoder_head_kernel<<<n_images, mppi::kHeadThreads, 0, e->stream>>>(e->act[3], e->h[4] * e->w[4], e->W5, e->b5,
-                                                                             d_latents);
-        ce = cudaGetLastError();
+        ce = mppi::launch_dependent(true, mppi::encoder_head_kernel, dim3(n_images), dim3(mppi::kHeadThreads), 0,
+                                    e->stream, static_cast<const float*>(e->act[3]), e->h[4] * e->w[4],
+                                    static_cast<const float*>(e->W5), static_cast<const float*>(e->b5), d_latents);
     }
     if (ce != cudaSuccess) return efail(e, MPPI_E_CUDA, "mppi_encode_depth: launch failed: %s", cudaGetErrorString(ce));
     return MPPI_OK;
