@@ -103,6 +103,9 @@ __global__ void __launch_bounds__(kRtThreads) render_depth_kernel(RenderParams P
     const int band = blockIdx.x - view * P.bands;
     const int v_begin = band * kRtBandRows;
     const int v_end = min(v_begin + kRtBandRows, P.H);
+    // a consumer launched as a programmatic dependent (the depth encoder) may start launching
+    // now; it waits for this grid to complete before it reads the depths
+    pdl_trigger();
 
     // ---- prologue: the per-view constants of every gate, 8 threads per gate (thread k of a
     // gate projects corner k of its outer box; the 8 reduce the bounds by shuffles)
