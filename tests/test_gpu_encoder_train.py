@@ -140,3 +140,27 @@ def test_training_reduces_heldout_reconstruction_error():
     print(f"held-out L1 reconstruction error {before:.4f} -> {after:.4f} (best constant {const_l1:.4f})")
     assert after < 0.5 * before
     assert after < 0.85 * const_l1   # the encoder's latent carries information about the image
+
+
+def test_training_steps_are_bit_reproducible():
+    """Fixed-order reductions: five steps from the same start give the same bits twice."""
+    torch = _torch()
+    noisy, clean = _data(6, 37, 53, seed=23)
+    d_noisy, d_clean = torch.from_numpy(noisy).cuda(), torch.from_numpy(clean).cuda()
+    runs = []
+    for _ in range(2):
+        enc = B.mppi_encoder_create(37, 53, 6, _flat(W.encoder_weights(7)))
+        Wd, bd = _decoder(35)
+        tr = B.mppi_encoder_train_create(enc, 6, 1e-3, Wd, bd)
+        try:
+            losses = [B.mppi_encoder_train_step(tr, 6, d_noisy, d_clean, 10.0) for _ in range(5)]
+            out = [np.zeros(a.shape, np.float32) for pair in W.encoder_weights(7) for a in pair]
+            B.mppi_encoder_get_weights(enc, out)
+        finally:
+            B.mppi_encoder_train_destroy(tr)
+            B.mppi_encoder_destroy(enc)
+        runs.append((losses, out))
+    assert runs[0][0] == runs[1][0]
+    for a, b in zip(runs[0][1], runs[1][1]):
+        np.testing.assert_array_equal(a, b)
+    assert runs[0][0][-1] < runs[0][0][0]
