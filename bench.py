@@ -562,6 +562,40 @@ def vision_leg(torch, B, stream, flush, dev, steps, drone_id):
     ms_e2 = timed(lambda: B.mppi_encode_depth(enc, 2, depth, kw["max_range"], z))
     ms_s = timed(lambda: B.mppi_step_async(ctx, None, None, z, None, U, None, None))
     B.mppi_sync(ctx)
+    # pipelined cycles (the paper runs its encoder beside the controller): views are rendered
+    # and encoded on a second stream while the MPPI step of the same cycle runs on the latents
+    # of the previous one; double-buffered latents, events order the hand-offs
+    side = torch.cuda.Stream(device=dev)
+    enc2 = B.mppi_encoder_create(kw["height"], kw["width"], 2, layers, side.cuda_stream)
+    depth2 = torch.empty(2, kw["height"], kw["width"], device=dev)
+    zb = [torch.zeros(2, 64, device=dev), torch.zeros(2, 64, device=dev)]
+    n_cyc = max(steps, 10)
+    enc_done = [torch.cuda.Event() for _ in range(n_cyc + 1)]
+    step_done = [torch.cuda.Event() for _ in range(n_cyc + 1)]
+    main = torch.cuda.current_stream()
+
+    def side_encode(i):
+        with torch.cuda.stream(side):
+            if i >= 2:
+                side.wait_event(step_done[i - 1])          # the step that read zb[i % 2] is done
+            B.mppi_render_depth(cam, 2, cyc_cams, gates.shape[0], gates, depth2, side.cuda_stream)
+            B.mppi_encode_depth(enc2, 2, depth2, kw["max_range"], zb[i % 2])
+            enc_done[i].record(side)
+
+    side_encode(0)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    main.wait_event(enc_done[0])
+    t0.record(main)
+    for i in range(1, n_cyc + 1):
+        side_encode(i)
+        main.wait_event(enc_done[i - 1])
+        B.mppi_step_async(ctx, None, None, zb[(i - 1) % 2], None, U, None, None)
+        step_done[i].record(main)
+    t1.record(main)
+    torch.cuda.synchronize()
+    ms_pipe = t0.elapsed_time(t1) / n_cyc
+    B.mppi_encoder_destroy(enc2)
     B.mppi_destroy(ctx)
     B.mppi_encoder_destroy(enc)
     return {"workload": "depth_views_N64_160x120_G2 + two_gate_mlp_K4096_H50_G2",
@@ -578,6 +612,9 @@ def vision_leg(torch, B, stream, flush, dev, steps, drone_id):
                               "stages": "render 2 views + encode 2 + MPPI step (BF16)",
                               "render_2_views_ms": float(ms_r2.mean()), "encode_2_ms": float(ms_e2.mean()),
                               "mppi_step_with_new_latents_ms": float(ms_s.mean())},
+            "control_cycle_pipelined": {"period_ms": ms_pipe, "cycles": n_cyc,
+                                        "stages": "render 2 views + encode 2 on a second stream, overlapped with "
+                                                  "the MPPI step on the previous cycle's latents"},
             "steps": steps}
 
 
