@@ -127,3 +127,121 @@ def adam_step(params, grads, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
         out_m.append(mi)
         out_v.append(vi)
     return out_p, out_m, out_v
+
+
+# ---------------------------------------------------------------- the SDF term (frozen decoder)
+# Sec. III-B supervises the latent through the SDF decoder: |g_phi(E(I_noisy), PE(p)) - s(p)| at
+# query points p of the camera frame whose exact SDF s is known from the rendered scene.  Here
+# the decoder is frozen (as in the paper's second stage) and only the encoder and D_psi learn.
+# Query points (a reading: the paper samples near-surface, interior, collision-prone and
+# frustum points, Sec. III-A): with Philox blocks A = (j, i, frame, 0x5DF0A) and
+# B = (j, i, frame, 0x5DF0B) of key = seed for point j of image i,
+#   * near a gate when the uniform of A's word 3 is below near_frac: gate g = ((A0 >> 8) G) >> 24,
+#     the gate-frame point ((2 uB0 - 1)(d + 0.3), (2 uB1 - 1)(a_out + 0.3), (2 uB2 - 1)(a_out + 0.3));
+#   * else in the view frustum: depth x = 0.2 + uA1 (max_range - 0.2) along the ray of the image
+#     position (W uA2, H uB3): y = -(W uA2 - cx) x / fx, z = -(H uB3 - cy) x / fy;
+# label = the exact frame SDF of the nearest gate (min over gates).
+
+QUERY_TAG_A = 0x5DF0A
+QUERY_TAG_B = 0x5DF0B
+
+
+def sample_queries(cam_poses, gate_poses, n_points, width, height, fx, fy, cx, cy, max_range, near_frac, seed, frame,
+                   a_in=0.5, a_out=0.75, d=0.1):
+    """Camera-frame query points [N, n_points, 3] and their exact SDF labels [N, n_points]."""
+    from . import gate_sdf
+    from .dynamics import quat_rotate, quat_conj
+    from .noise import words_to_uniform
+    from .philox import philox4x32_10, split_seed
+    cams = np.asarray(cam_poses, dtype=np.float64).reshape(-1, 7)
+    gates = np.asarray(gate_poses, dtype=np.float64).reshape(-1, 7)
+    n, G = len(cams), len(gates)
+    j = np.arange(n_points, dtype=np.uint64)[None, :]
+    i = np.arange(n, dtype=np.uint64)[:, None]
+
+    def block(tag):
+        j_b, i_b = np.broadcast_arrays(j, i)
+        ctr = np.stack([j_b, i_b, np.full(j_b.shape, int(frame) & 0xFFFFFFFF, np.uint64),
+                        np.full(j_b.shape, tag, np.uint64)], axis=-1)
+        return philox4x32_10(ctr, split_seed(seed))
+
+    A, Bw = block(QUERY_TAG_A), block(QUERY_TAG_B)
+    uA, uB = words_to_uniform(A), words_to_uniform(Bw)
+    near = uA[..., 3] < float(np.float32(near_frac))
+    gi = ((A[..., 0].astype(np.uint64) >> np.uint64(8)) * np.uint64(max(G, 1))) >> np.uint64(24)
+    cam_q = cams[:, 3:7] / np.linalg.norm(cams[:, 3:7], axis=1, keepdims=True)
+    pts = np.zeros((n, n_points, 3))
+    # frustum points
+    x = 0.2 + uA[..., 1] * (max_range - 0.2)
+    pts_f = np.stack([x, -(width * uA[..., 2] - cx) * x / fx, -(height * uB[..., 3] - cy) * x / fy], axis=-1)
+    pts[~near] = pts_f[~near]
+    if G > 0 and near.any():
+        half = np.array([d + 0.3, a_out + 0.3, a_out + 0.3])
+        pg = (2.0 * uB[..., 0:3] - 1.0) * half
+        gq = gates[gi.astype(np.int64), 3:7]
+        gq = gq / np.linalg.norm(gq, axis=-1, keepdims=True)
+        world = quat_rotate(gq, pg) + gates[gi.astype(np.int64), 0:3]
+        cq = np.broadcast_to(cam_q[:, None, :], world.shape[:-1] + (4,))
+        pc = quat_rotate(quat_conj(cq), world - cams[:, None, 0:3])
+        pts[near] = pc[near]
+    # labels: exact SDF of the nearest frame
+    cq = np.broadcast_to(cam_q[:, None, :], pts.shape[:-1] + (4,))
+    world = quat_rotate(cq, pts) + cams[:, None, 0:3]
+    lab = np.full((n, n_points), np.inf)
+    for gp in gates:
+        gp = np.array(gp, dtype=np.float64)
+        gp[3:7] /= np.linalg.norm(gp[3:7])
+        lab = np.minimum(lab, gate_sdf.frame_sdf(gate_sdf.to_gate_frame(world.reshape(-1, 3), gp).reshape(world.shape),
+                                                 a_in, a_out, d))
+    return pts, lab
+
+
+def sdf_term(z, points, labels, dec_layers, pe_levels):
+    """(mean |g(z_i, PE(p_ij)) - s_ij|, d/dz [N, 64]) with the decoder frozen."""
+    from .mlp import input_gradient, positional_encoding, sdf
+    z = np.asarray(z, dtype=np.float64)
+    n, m, _ = np.asarray(points).shape
+    L = 0.0
+    dz = np.zeros_like(z)
+    nf = 3 + 6 * pe_levels
+    for i in range(n):
+        s = sdf(dec_layers, points[i], z[i], pe_levels=pe_levels)
+        r = s - labels[i]
+        L += float(np.sum(np.abs(r)))
+        x = np.concatenate([positional_encoding(points[i], pe_levels), np.broadcast_to(z[i], (m, z.shape[1]))], axis=1)
+        gx = input_gradient(dec_layers, x)
+        dz[i] = (np.sign(r)[:, None] * gx[:, nf:]).sum(axis=0) / (n * m)
+    return L / (n * m), dz
+
+
+def gradients_joint(noisy, clean, max_range, enc_layers, dec, points, labels, sdf_layers, pe_levels, lam_recon,
+                    lam_sdf):
+    """Loss lam_recon L_recon + lam_sdf L_sdf and the gradients of the encoder's tensors and D_psi
+    (the SDF decoder frozen): (loss, L_recon, L_sdf, enc grads, dec grads)."""
+    enc = [(np.asarray(W, dtype=np.float64), np.asarray(b, dtype=np.float64)) for W, b in enc_layers]
+    Wd, bd = (np.asarray(a, dtype=np.float64) for a in dec)
+    xs, z = forward(noisy, max_range, enc)
+    n = len(z)
+    t = pooled_target(clean, max_range).reshape(n, -1)
+    r = z @ Wd.T + bd - t
+    L_rec = float(np.mean(np.abs(r)))
+    g = lam_recon * np.sign(r) / r.size
+    gWd, gbd = g.T @ z, g.sum(axis=0)
+    L_sdf, dz_sdf = sdf_term(z, points, labels, sdf_layers, pe_levels)
+    dz = g @ Wd + lam_sdf * dz_sdf
+    W5 = enc[4][0]
+    x4 = xs[4]
+    m = x4.mean(axis=(2, 3))
+    gW5, gb5 = dz.T @ m, dz.sum(axis=0)
+    dm = dz @ W5
+    hw = x4.shape[2] * x4.shape[3]
+    delta = (dm / hw)[:, :, None, None] * (x4 > 0.0)
+    grads = [None] * 4
+    for l in range(3, -1, -1):
+        x_in = xs[l]
+        grads[l] = (conv_weight_grad(x_in, delta), delta.sum(axis=(0, 2, 3)))
+        if l > 0:
+            dx = conv_input_grad(delta, enc[l][0], x_in.shape[2], x_in.shape[3])
+            delta = dx * (x_in > 0.0)
+    grads.append((gW5, gb5))
+    return lam_recon * L_rec + lam_sdf * L_sdf, L_rec, L_sdf, grads, (gWd, gbd)
