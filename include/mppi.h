@@ -379,6 +379,28 @@ void mppi_depth_camera_default(mppi_depth_camera* cam);
 int mppi_render_depth(const mppi_depth_camera* cam, int n_views, const float* d_cam_poses, int n_gates,
                       const float* d_gate_poses, float* d_depth, void* stream);
 
+/*
+ * Training queries for the SDF supervision of the encoder (Sec. III-A samples points in
+ * the camera frame and labels them with the analytic SDF): n_points camera-frame points per
+ * view and the exact signed distance of the nearest gate frame at each.  For point j of
+ * view i, Philox4x32-10 blocks A = (j, i, frame, 0x5DF0A) and B = (j, i, frame, 0x5DF0B)
+ * with key = cam->seed (uniforms as in the control noise) give: when uA3 < near_frac, a
+ * point near gate g = ((A0 >> 8) n_gates) >> 24, uniform in its frame's box grown by
+ * 0.3 m ((2 uB0 - 1)(d + 0.3), (2 uB1 - 1)(a_out + 0.3), (2 uB2 - 1)(a_out + 0.3)) in the
+ * gate frame; else a point of the view frustum at depth 0.2 + uA1 (max_range - 0.2) on
+ * the ray through image position (width uA2, height uB3) (R31's camera model).
+ *   cam           intrinsics, max_range (> 0.2), frame geometry, seed and frame
+ *   n_views       0 .. 2^24 camera poses (device, n_views x 7)
+ *   n_gates       1 .. MPPI_MAX_RENDER_GATES gate poses (device, n_gates x 7)
+ *   n_points      1 .. 2^20 points per view (n_views x n_points <= 2^31)
+ *   d_points      n_views x n_points x 3 floats out (device), camera frame
+ *   d_labels      n_views x n_points floats out (device)
+ * One kernel on stream.  Errors: MPPI_E_INVALID, MPPI_E_CUDA (mppi_last_error(NULL)).
+ */
+int mppi_sample_sdf_queries(const mppi_depth_camera* cam, int n_views, const float* d_cam_poses, int n_gates,
+                            const float* d_gate_poses, int n_points, float near_frac, float* d_points,
+                            float* d_labels, void* stream);
+
 /* ======================================================================== vision front end: depth encoder
  * The depth encoder E_theta of Sec. III-B, which maps the current depth image
  * to the latent code z once per control cycle (Sec. IV-B).  The paper gives
@@ -437,9 +459,8 @@ int mppi_encoder_get_weights(mppi_encoder* enc, float* const* layers_out);
  * averaged over 8 x 8 pixel blocks (edge blocks average the pixels they hold),
  * T = ceil(H / 8) x ceil(W / 8) values; D_psi is one affine map 64 -> T; the
  * loss is mean |D_psi(E(noisy)) - target| with d|r|/dr = sign(r) (0 at 0);
- * Adam beta1 = 0.9, beta2 = 0.999, eps = 1e-8, bias-corrected.  The paper's
- * second term (the SDF decoder on query points) and its second stage are not
- * built.  The trainer updates the encoder's weights in place, so
+ * Adam beta1 = 0.9, beta2 = 0.999, eps = 1e-8, bias-corrected.  The SDF term
+ * (below) runs through a frozen Gate-SDF decoder.  The trainer updates the encoder's weights in place, so
  * mppi_encode_depth uses the trained encoder; it uses the encoder's stream and
  * activations, so encoder calls must not overlap trainer calls.
  */
@@ -469,6 +490,31 @@ int mppi_encoder_train_loss_grads(mppi_encoder_trainer* trainer, int n, const fl
 /* One training step (loss and gradients of the batch, then Adam on all 12 tensors); loss as above. */
 int mppi_encoder_train_step(mppi_encoder_trainer* trainer, int n, const float* d_noisy, const float* d_clean,
                             float max_range, float* loss);
+/*
+ * The SDF term of the same stage with the Gate-SDF decoder g_phi frozen (the paper freezes it
+ * in its second stage): L = lambda_recon L_recon + lambda_sdf mean |g_phi(z_i, PE(p_ij)) - s_ij|
+ * over camera-frame query points p_ij of image i with exact SDF labels s_ij (e.g. from
+ * mppi_sample_sdf_queries); the decoder's input is [PE(p), z] as in mppi_set_sdf_weights with
+ * pe_levels, its activation softplus with softplus_beta.
+ *   layers                10 host arrays W1 [128][3 + 6 pe_levels + 64], b1, W2..W4 [128][128],
+ *                         b2..b4, w5 [1][128], b5 [1] (copied; the decoder is not trained)
+ *   max_points_per_image  32 .. 65536, a multiple of 32: the most query points a call may pass
+ * Errors: MPPI_E_INVALID (bad argument, or a decoder already set), MPPI_E_OOM, MPPI_E_CUDA.
+ */
+int mppi_encoder_train_set_sdf(mppi_encoder_trainer* trainer, const float* const* layers, int pe_levels,
+                               float softplus_beta, float lambda_recon, float lambda_sdf, int max_points_per_image);
+/*
+ * As mppi_encoder_train_loss_grads / _step with the SDF term: d_points n x n_points x 3 and
+ * d_labels n x n_points floats (device), n_points a multiple of 32 up to max_points_per_image;
+ * losses (nullable, host [3]): the weighted total, the reconstruction mean |r| and the SDF mean
+ * |r|.  MPPI_E_NOT_READY before mppi_encoder_train_set_sdf.
+ */
+int mppi_encoder_train_loss_grads_sdf(mppi_encoder_trainer* trainer, int n, const float* d_noisy, const float* d_clean,
+                                      float max_range, const float* d_points, const float* d_labels, int n_points,
+                                      float* losses, float* const* grads_out);
+int mppi_encoder_train_step_sdf(mppi_encoder_trainer* trainer, int n, const float* d_noisy, const float* d_clean,
+                                float max_range, const float* d_points, const float* d_labels, int n_points,
+                                float* losses);
 /* D_psi's current weights (T x 64 and T host floats).  Synchronous. */
 int mppi_encoder_train_get_decoder(mppi_encoder_trainer* trainer, float* W, float* b);
 

@@ -57,11 +57,12 @@ EXPORTS = [
     "mppi_train_config_default", "mppi_train_create", "mppi_train_destroy", "mppi_train_last_error",
     "mppi_train_step", "mppi_train_loss_grads", "mppi_train_get_weights", "mppi_train_evaluate",
     "mppi_train_read_points", "mppi_train_num_params",
-    "mppi_depth_camera_default", "mppi_render_depth",
+    "mppi_depth_camera_default", "mppi_render_depth", "mppi_sample_sdf_queries",
     "mppi_encoder_create", "mppi_encoder_destroy", "mppi_encoder_last_error", "mppi_encode_depth",
     "mppi_encoder_get_weights", "mppi_encoder_train_create", "mppi_encoder_train_destroy",
     "mppi_encoder_train_last_error", "mppi_encoder_train_loss_grads", "mppi_encoder_train_step",
-    "mppi_encoder_train_get_decoder",
+    "mppi_encoder_train_get_decoder", "mppi_encoder_train_set_sdf", "mppi_encoder_train_loss_grads_sdf",
+    "mppi_encoder_train_step_sdf",
 ]
 
 
@@ -168,6 +169,8 @@ _SIGS = {
     "mppi_train_read_points": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_size_t]),
     "mppi_train_num_params": (ctypes.c_int, []),
     "mppi_depth_camera_default": (None, [ctypes.POINTER(MppiDepthCamera)]),
+    "mppi_sample_sdf_queries": (ctypes.c_int, [ctypes.POINTER(MppiDepthCamera), ctypes.c_int, _vp, ctypes.c_int, _vp,
+                                               ctypes.c_int, ctypes.c_float, _vp, _vp, _vp]),
     "mppi_encoder_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp), ctypes.c_int,
                                            _vp, ctypes.POINTER(_vp)]),
     "mppi_encoder_destroy": (None, [_vp]),
@@ -182,6 +185,12 @@ _SIGS = {
     "mppi_encoder_train_step": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_float,
                                                ctypes.POINTER(ctypes.c_float)]),
     "mppi_encoder_train_get_decoder": (ctypes.c_int, [_vp, _vp, _vp]),
+    "mppi_encoder_train_set_sdf": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_float,
+                                                  ctypes.c_float, ctypes.c_float, ctypes.c_int]),
+    "mppi_encoder_train_loss_grads_sdf": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_float, _vp, _vp,
+                                                         ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+    "mppi_encoder_train_step_sdf": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_float, _vp, _vp,
+                                                   ctypes.c_int, _vp]),
     "mppi_render_depth": (ctypes.c_int, [ctypes.POINTER(MppiDepthCamera), ctypes.c_int, _vp, ctypes.c_int, _vp, _vp,
                                          _vp]),
 }
@@ -467,6 +476,14 @@ def mppi_depth_camera_default():
     return cam
 
 
+def mppi_sample_sdf_queries(cam, n_views, d_cam_poses, n_gates, d_gate_poses, n_points, near_frac, d_points,
+                            d_labels, stream=None):
+    """Enqueue camera-frame training queries and their exact SDF labels (device pointers)."""
+    return _check(load().mppi_sample_sdf_queries(ctypes.byref(cam), n_views, _ptr(d_cam_poses), n_gates,
+                                                 _ptr(d_gate_poses), n_points, near_frac, _ptr(d_points),
+                                                 _ptr(d_labels), _ptr(stream)))
+
+
 def mppi_render_depth(cam, n_views, d_cam_poses, n_gates, d_gate_poses, d_depth, stream=None):
     """Enqueue n_views depth images [n_views, height, width] into d_depth (device pointers)."""
     return _check(load().mppi_render_depth(ctypes.byref(cam), n_views, _ptr(d_cam_poses), n_gates,
@@ -541,3 +558,32 @@ def mppi_encoder_train_step(trainer, n, d_noisy, d_clean, max_range, want_loss=T
 
 def mppi_encoder_train_get_decoder(trainer, W, b):
     return _etcheck(load().mppi_encoder_train_get_decoder(trainer, _ptr(W), _ptr(b)), trainer)
+
+
+def mppi_encoder_train_set_sdf(trainer, layers, pe_levels, softplus_beta, lambda_recon, lambda_sdf,
+                               max_points_per_image):
+    arr = (_vp * len(layers))(*[_ptr(a) for a in layers])
+    return _etcheck(load().mppi_encoder_train_set_sdf(trainer, arr, pe_levels, softplus_beta, lambda_recon,
+                                                      lambda_sdf, max_points_per_image), trainer)
+
+
+def mppi_encoder_train_loss_grads_sdf(trainer, n, d_noisy, d_clean, max_range, d_points, d_labels, n_points,
+                                      grads_out=None):
+    """Returns (total, reconstruction, SDF) losses; fills the 12 host gradient arrays when given."""
+    import numpy as _np
+    losses = _np.zeros(3, _np.float32)
+    arr = None if grads_out is None else (_vp * len(grads_out))(*[_ptr(a) for a in grads_out])
+    _etcheck(load().mppi_encoder_train_loss_grads_sdf(trainer, n, _ptr(d_noisy), _ptr(d_clean), max_range,
+                                                      _ptr(d_points), _ptr(d_labels), n_points, _ptr(losses), arr),
+             trainer)
+    return tuple(float(x) for x in losses)
+
+
+def mppi_encoder_train_step_sdf(trainer, n, d_noisy, d_clean, max_range, d_points, d_labels, n_points,
+                                want_loss=True):
+    import numpy as _np
+    losses = _np.zeros(3, _np.float32)
+    _etcheck(load().mppi_encoder_train_step_sdf(trainer, n, _ptr(d_noisy), _ptr(d_clean), max_range, _ptr(d_points),
+                                                _ptr(d_labels), n_points, _ptr(losses) if want_loss else None),
+             trainer)
+    return tuple(float(x) for x in losses) if want_loss else None

@@ -18,6 +18,11 @@
 //                       gradients of the (1, 2 or 4 per axis pair) windows that read it,
 //                       times the weights, masked by the ReLU of that input
 //   adam_kernel         all 12 tensors
+// With the SDF term (a frozen Gate-SDF decoder g_phi and camera-frame query points with their
+// exact SDF), per step also: sdf_bias_kernel (per image b1 + W1_z z), sdf_dz_kernel (32
+// points per block: forward through the decoder keeping the softplus derivatives in shared
+// memory, the L1 residual's sign, backward to the first layer) and sdf_dz_reduce_kernel (the
+// per-image sum, W1_z^T of it added to dL/dz), before the encoder's backward pass.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -300,6 +305,196 @@ __global__ void __launch_bounds__(kDgThreads) conv_dgrad_kernel(const float* __r
     }
 }
 
+// ---------------------------------------------------------------- SDF term (frozen decoder)
+constexpr int kSdThreads = 256;
+constexpr int kSdPts = 32;                 // query points per block (all of one image)
+constexpr int kSdMaxFeat = 3 + 6 * MPPI_MAX_PE_LEVELS;
+constexpr int kSdHidden = MPPI_HIDDEN;
+
+struct SdfNet {
+    const float* W1;        // [128][NF + 64] as given
+    const float* b1;        // [128]
+    const float* WT[3];     // layers 2..4 transposed: [in][out]
+    const float* W[3];      // layers 2..4 as given: [out][in]
+    const float* b[3];      // [128]
+    const float* w5;        // [128]
+    float b5, beta;
+    int nf, pe;             // point features 3 + 6 pe
+};
+
+// per image: b1'_i = b1 + W1[:, NF:] z_i
+__global__ void __launch_bounds__(kSdHidden) sdf_bias_kernel(SdfNet N, const float* __restrict__ z,
+                                                              float* __restrict__ b1p) {
+    const int i = blockIdx.x, c = threadIdx.x;
+    const int ld = N.nf + kLat;
+    float acc = N.b1[c];
+    for (int j = 0; j < kLat; ++j) acc = fmaf(N.W1[c * ld + N.nf + j], z[i * kLat + j], acc);
+    b1p[i * kSdHidden + c] = acc;
+}
+
+__device__ __forceinline__ float sp_acc(float x, float beta) {
+    return fmaxf(x, 0.f) + log1pf(expf(-beta * fabsf(x))) / beta;
+}
+__device__ __forceinline__ float sp_grad(float x, float beta) {   // logistic(beta x)
+    const float e = expf(-beta * fabsf(x));
+    return x >= 0.f ? 1.f / (1.f + e) : e / (1.f + e);
+}
+
+// out[p][c] = sum_r in[p][r] M[r][c] for the block's 32 points: thread rows 4 (t / 32) .. + 3,
+// columns 4 (t % 32) .. + 3.
+__device__ __forceinline__ void sd_gemm(const float (*in)[kSdHidden], const float* M, float acc[4][4]) {
+    const int rp = threadIdx.x >> 5, cq = threadIdx.x & 31;
+#pragma unroll 4
+    for (int r = 0; r < kSdHidden; ++r) {
+        const float4 b = *reinterpret_cast<const float4*>(M + r * kSdHidden + cq * 4);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float a = in[rp * 4 + i][r];
+            acc[i][0] = fmaf(a, b.x, acc[i][0]);
+            acc[i][1] = fmaf(a, b.y, acc[i][1]);
+            acc[i][2] = fmaf(a, b.z, acc[i][2]);
+            acc[i][3] = fmaf(a, b.w, acc[i][3]);
+        }
+    }
+}
+
+// Forward through the frozen decoder at 32 query points of image blockIdx.x / (n_points / 32),
+// the signed L1 residual's coefficient, and the backward pass to the first layer's
+// pre-activation; writes the block's sum of that gradient over its points and its sum of |r|.
+__global__ void __launch_bounds__(kSdThreads) sdf_dz_kernel(SdfNet N, const float* __restrict__ points,
+                                                            const float* __restrict__ labels, int n_points,
+                                                            const float* __restrict__ b1p, float coef,
+                                                            float* __restrict__ part, float* __restrict__ loss_part) {
+    extern __shared__ __align__(16) float sm[];
+    float (*h)[kSdHidden] = reinterpret_cast<float (*)[kSdHidden]>(sm);                      // [32][128]
+    float (*spd)[kSdPts][kSdHidden] = reinterpret_cast<float (*)[kSdPts][kSdHidden]>(sm + kSdPts * kSdHidden);
+    float* Mst = sm + 5 * kSdPts * kSdHidden;                                                 // [128][128]
+    float* pe = Mst + kSdHidden * kSdHidden;                                                  // [NF][32]
+    float* sres = pe + kSdMaxFeat * kSdPts;                                                   // [32]
+    const int blocks_per_img = n_points / kSdPts;
+    const int img = blockIdx.x / blocks_per_img;
+    const long long q0 = static_cast<long long>(blockIdx.x) * kSdPts;   // first query of the block
+    const int rp = threadIdx.x >> 5, cq = threadIdx.x & 31;
+    if (threadIdx.x < kSdPts) {
+        const float* pt = points + (q0 + threadIdx.x) * 3;
+        const float px = pt[0], py = pt[1], pz = pt[2];
+        pe[0 * kSdPts + threadIdx.x] = px;
+        pe[1 * kSdPts + threadIdx.x] = py;
+        pe[2 * kSdPts + threadIdx.x] = pz;
+        for (int l = 0; l < N.pe; ++l) {
+            const float sc = static_cast<float>(1 << l);
+            float s0, c0, s1, c1, s2, c2;
+            sincospif(sc * px, &s0, &c0);
+            sincospif(sc * py, &s1, &c1);
+            sincospif(sc * pz, &s2, &c2);
+            float* f = pe + (3 + 6 * l) * kSdPts + threadIdx.x;
+            f[0] = s0; f[kSdPts] = s1; f[2 * kSdPts] = s2;
+            f[3 * kSdPts] = c0; f[4 * kSdPts] = c1; f[5 * kSdPts] = c2;
+        }
+    }
+    __syncthreads();
+    // layer 1: a1[p][c] = b1'_img[c] + W1[c][0:NF] pe[p]
+    const int ld1 = N.nf + kLat;
+    for (int e = threadIdx.x; e < kSdPts * kSdHidden; e += kSdThreads) {
+        const int pnt = e / kSdHidden, c = e - pnt * kSdHidden;
+        float a = b1p[img * kSdHidden + c];
+        for (int f = 0; f < N.nf; ++f) a = fmaf(N.W1[c * ld1 + f], pe[f * kSdPts + pnt], a);
+        h[pnt][c] = sp_acc(a, N.beta);
+        spd[0][pnt][c] = sp_grad(a, N.beta);
+    }
+    // layers 2..4
+    for (int l = 0; l < 3; ++l) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < kSdHidden * kSdHidden / 4; e += kSdThreads)
+            reinterpret_cast<float4*>(Mst)[e] = reinterpret_cast<const float4*>(N.WT[l])[e];
+        __syncthreads();
+        float acc[4][4] = {};
+        sd_gemm(h, Mst, acc);
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float a = acc[i][c] + N.b[l][cq * 4 + c];
+                h[rp * 4 + i][cq * 4 + c] = sp_acc(a, N.beta);
+                spd[l + 1][rp * 4 + i][cq * 4 + c] = sp_grad(a, N.beta);
+            }
+    }
+    __syncthreads();
+    // output, residual and its coefficient (one warp per 4 points, lanes over the hidden units)
+    {
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int pnt = w; pnt < kSdPts; pnt += kSdThreads / 32) {
+            float sacc = 0.f;
+            for (int c = lane; c < kSdHidden; c += 32) sacc = fmaf(N.w5[c], h[pnt][c], sacc);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+            if (lane == 0) sres[pnt] = sacc + N.b5 - labels[q0 + pnt];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float l1 = 0.f;
+        for (int pnt = 0; pnt < kSdPts; ++pnt) l1 += fabsf(sres[pnt]);
+        loss_part[blockIdx.x] = l1;
+    }
+    // backward: g4 = coef sign(r) w5 sp'(a4); g_{l-1} = (g_l W_l) sp'(a_{l-1})
+    for (int e = threadIdx.x; e < kSdPts * kSdHidden; e += kSdThreads) {
+        const int pnt = e / kSdHidden, c = e - pnt * kSdHidden;
+        const float r = sres[pnt];
+        const float sg = r > 0.f ? coef : (r < 0.f ? -coef : 0.f);
+        h[pnt][c] = sg * N.w5[c] * spd[3][pnt][c];
+    }
+    for (int l = 2; l >= 0; --l) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < kSdHidden * kSdHidden / 4; e += kSdThreads)
+            reinterpret_cast<float4*>(Mst)[e] = reinterpret_cast<const float4*>(N.W[l])[e];
+        __syncthreads();
+        float acc[4][4] = {};
+        sd_gemm(h, Mst, acc);
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                h[rp * 4 + i][cq * 4 + c] = acc[i][c] * spd[l][rp * 4 + i][cq * 4 + c];
+    }
+    __syncthreads();
+    if (threadIdx.x < kSdHidden) {
+        float acc = 0.f;
+        for (int pnt = 0; pnt < kSdPts; ++pnt) acc += h[pnt][threadIdx.x];
+        part[static_cast<size_t>(blockIdx.x) * kSdHidden + threadIdx.x] = acc;
+    }
+}
+
+// per image: G = sum over its blocks of the first-layer gradient sums (block order);
+// dz_i += W1[:, NF:]^T G; its SDF loss sum = sum of its blocks' |r| sums.
+__global__ void __launch_bounds__(kSdHidden) sdf_dz_reduce_kernel(SdfNet N, const float* __restrict__ part,
+                                                                   const float* __restrict__ loss_part,
+                                                                   int blocks_per_img, float* __restrict__ dz,
+                                                                   float* __restrict__ loss_img) {
+    __shared__ float G[kSdHidden];
+    const int i = blockIdx.x, c = threadIdx.x;
+    float acc = 0.f;
+    for (int q = 0; q < blocks_per_img; ++q) acc += part[(static_cast<size_t>(i) * blocks_per_img + q) * kSdHidden + c];
+    G[c] = acc;
+    __syncthreads();
+    if (c < kLat) {
+        const int ld = N.nf + kLat;
+        float d = 0.f;
+        for (int k = 0; k < kSdHidden; ++k) d = fmaf(N.W1[k * ld + N.nf + c], G[k], d);
+        dz[i * kLat + c] += d;
+    }
+    if (c == 0) {
+        float l1 = 0.f;
+        for (int q = 0; q < blocks_per_img; ++q) l1 += loss_part[i * blocks_per_img + q];
+        loss_img[i] = l1;
+    }
+}
+
+constexpr size_t kSdSmem = sizeof(float) * (5 * kSdPts * kSdHidden + kSdHidden * kSdHidden + kSdMaxFeat * kSdPts +
+                                            kSdPts);
+
 // ---------------------------------------------------------------- Adam
 struct AdamTable {
     float* p[kNumTensors];
@@ -346,8 +541,18 @@ struct mppi_encoder_trainer {
     float* delta[2] = {nullptr, nullptr};
     float* ws = nullptr;
     size_t ws_floats = 0;
+    // SDF term (frozen decoder), set by mppi_encoder_train_set_sdf
+    bool sdf = false;
+    float lam_recon = 1.f, lam_sdf = 0.f;
+    int max_points = 0;
+    mppi::SdfNet net{};
+    float* sdf_b1p = nullptr;
+    float* sdf_part = nullptr;
+    float* sdf_loss_part = nullptr;
+    float* sdf_loss_img = nullptr;
     std::vector<void*> allocs;
     std::vector<float> h_loss;
+    std::vector<float> h_loss2;
     char err[512] = "";
 };
 
@@ -413,16 +618,33 @@ cudaError_t launch_dgrad(mppi_encoder_trainer* t, int l, int n, const float* del
     return cudaGetLastError();
 }
 
-// Forward, loss and every gradient of one batch; the loss (mean |r|) goes to *loss when non-NULL.
+struct Queries {
+    const float* points;   // [n][n_points][3] camera frame (device)
+    const float* labels;   // [n][n_points] (device)
+    int n_points;
+};
+
+// Forward, loss and every gradient of one batch.  losses (nullable, host): total, reconstruction
+// mean |r|, SDF mean |r| (0 without queries).
 int loss_grads(mppi_encoder_trainer* t, int n, const float* d_noisy, const float* d_clean, float max_range,
-               float* loss) {
+               const Queries* q, float* losses) {
     mppi_encoder* e = t->enc;
     int rc = mppi_encode_depth(e, n, d_noisy, max_range, t->z);
     if (rc != MPPI_OK) return tfail(t, rc, "encoder forward failed: %s", mppi_encoder_last_error(e));
     cudaStream_t s = e->stream;
     const float inv_count = 1.f / (static_cast<float>(n) * static_cast<float>(t->T));
+    const float lam_r = q ? t->lam_recon : 1.f;
     mppi::recon_kernel<<<n, 256, 0, s>>>(t->z, d_clean, 1.f / max_range, e->H, e->W, t->th, t->tw, t->Wd, t->bd,
-                                         inv_count, t->g, t->dz, t->loss_img);
+                                         lam_r * inv_count, t->g, t->dz, t->loss_img);
+    const float inv_q = q ? 1.f / (static_cast<float>(n) * static_cast<float>(q->n_points)) : 0.f;
+    if (q) {
+        const int bpi = q->n_points / mppi::kSdPts;
+        mppi::sdf_bias_kernel<<<n, mppi::kSdHidden, 0, s>>>(t->net, t->z, t->sdf_b1p);
+        mppi::sdf_dz_kernel<<<n * bpi, mppi::kSdThreads, mppi::kSdSmem, s>>>(
+            t->net, q->points, q->labels, q->n_points, t->sdf_b1p, t->lam_sdf * inv_q, t->sdf_part, t->sdf_loss_part);
+        mppi::sdf_dz_reduce_kernel<<<n, mppi::kSdHidden, 0, s>>>(t->net, t->sdf_part, t->sdf_loss_part, bpi, t->dz,
+                                                                  t->sdf_loss_img);
+    }
     mppi::outer_sum_kernel<<<(t->T * mppi::kLat + 255) / 256, 256, 0, s>>>(t->g, t->z, n, t->T, mppi::kLat,
                                                                           t->grad[10], t->grad[11]);
     const int hw4 = e->h[4] * e->w[4];
@@ -443,15 +665,61 @@ int loss_grads(mppi_encoder_trainer* t, int n, const float* d_noisy, const float
     std::swap(cur, nxt);
     if (ce == cudaSuccess) ce = launch_wgrad<1, 16, true>(t, 0, n, d_noisy, 1.f / max_range, cur);
     if (ce != cudaSuccess) return tfail(t, MPPI_E_CUDA, "launch failed: %s", cudaGetErrorString(ce));
-    if (loss) {
+    if (losses) {
         t->h_loss.resize(n);
+        t->h_loss2.assign(n, 0.f);
         ce = cudaMemcpyAsync(t->h_loss.data(), t->loss_img, n * sizeof(float), cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess && q)
+            ce = cudaMemcpyAsync(t->h_loss2.data(), t->sdf_loss_img, n * sizeof(float), cudaMemcpyDeviceToHost, s);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
         if (ce != cudaSuccess) return tfail(t, MPPI_E_CUDA, "loss read-back failed: %s", cudaGetErrorString(ce));
-        double sum = 0.0;
-        for (int i = 0; i < n; ++i) sum += t->h_loss[i];
-        *loss = static_cast<float>(sum * inv_count);
+        double rsum = 0.0, ssum = 0.0;
+        for (int i = 0; i < n; ++i) {
+            rsum += t->h_loss[i];
+            ssum += t->h_loss2[i];
+        }
+        const double l_rec = rsum * inv_count, l_sdf = ssum * inv_q;
+        losses[0] = static_cast<float>(lam_r * l_rec + (q ? t->lam_sdf * l_sdf : 0.0));
+        losses[1] = static_cast<float>(l_rec);
+        losses[2] = static_cast<float>(l_sdf);
     }
+    return MPPI_OK;
+}
+
+int adam_all(mppi_encoder_trainer* t) {
+    t->step += 1;
+    mppi::AdamTable tab{};
+    int max_size = 0;
+    for (int i = 0; i < mppi::kNumTensors; ++i) {
+        tab.p[i] = t->param[i];
+        tab.g[i] = t->grad[i];
+        tab.m[i] = t->m[i];
+        tab.v[i] = t->v[i];
+        tab.size[i] = t->size[i];
+        max_size = std::max(max_size, t->size[i]);
+    }
+    const float c1 = static_cast<float>(1.0 - std::pow(0.9, t->step));
+    const float c2 = static_cast<float>(1.0 - std::pow(0.999, t->step));
+    mppi::adam_kernel<<<dim3((max_size + 255) / 256, mppi::kNumTensors), 256, 0, t->enc->stream>>>(tab, t->lr, c1, c2);
+    const cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) return tfail(t, MPPI_E_CUDA, "Adam launch failed: %s", cudaGetErrorString(ce));
+    return MPPI_OK;
+}
+
+int read_grads(mppi_encoder_trainer* t, float* const* grads_out) {
+    cudaError_t ce = cudaStreamSynchronize(t->enc->stream);
+    for (int i = 0; i < mppi::kNumTensors && ce == cudaSuccess; ++i)
+        if (grads_out[i])
+            ce = cudaMemcpy(grads_out[i], t->grad[i], t->size[i] * sizeof(float), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return tfail(t, MPPI_E_CUDA, "gradient read-back failed: %s", cudaGetErrorString(ce));
+    return MPPI_OK;
+}
+
+int check_queries(mppi_encoder_trainer* t, const float* d_points, const float* d_labels, int n_points) {
+    if (!t->sdf) return tfail(t, MPPI_E_NOT_READY, "no SDF decoder: call mppi_encoder_train_set_sdf first");
+    if (!d_points || !d_labels) return tfail(t, MPPI_E_INVALID, "NULL query pointer");
+    if (n_points < mppi::kSdPts || n_points % mppi::kSdPts != 0 || n_points > t->max_points)
+        return tfail(t, MPPI_E_INVALID, "n_points must be a multiple of 32 in [32, %d]", t->max_points);
     return MPPI_OK;
 }
 
@@ -566,14 +834,11 @@ extern "C" int mppi_encoder_train_loss_grads(mppi_encoder_trainer* t, int n, con
     if (!t) return tfail(nullptr, MPPI_E_INVALID, "mppi_encoder_train_loss_grads: NULL trainer");
     int rc = check_batch(t, n, d_noisy, d_clean, max_range);
     if (rc != MPPI_OK) return rc;
-    rc = loss_grads(t, n, d_noisy, d_clean, max_range, loss);
-    if (rc != MPPI_OK || !grads_out) return rc;
-    cudaError_t ce = cudaStreamSynchronize(t->enc->stream);
-    for (int i = 0; i < mppi::kNumTensors && ce == cudaSuccess; ++i)
-        if (grads_out[i])
-            ce = cudaMemcpy(grads_out[i], t->grad[i], t->size[i] * sizeof(float), cudaMemcpyDeviceToHost);
-    if (ce != cudaSuccess) return tfail(t, MPPI_E_CUDA, "gradient read-back failed: %s", cudaGetErrorString(ce));
-    return MPPI_OK;
+    float losses[3];
+    rc = loss_grads(t, n, d_noisy, d_clean, max_range, nullptr, loss ? losses : nullptr);
+    if (rc != MPPI_OK) return rc;
+    if (loss) *loss = losses[0];
+    return grads_out ? read_grads(t, grads_out) : MPPI_OK;
 }
 
 extern "C" int mppi_encoder_train_step(mppi_encoder_trainer* t, int n, const float* d_noisy, const float* d_clean,
@@ -581,25 +846,102 @@ extern "C" int mppi_encoder_train_step(mppi_encoder_trainer* t, int n, const flo
     if (!t) return tfail(nullptr, MPPI_E_INVALID, "mppi_encoder_train_step: NULL trainer");
     int rc = check_batch(t, n, d_noisy, d_clean, max_range);
     if (rc != MPPI_OK) return rc;
-    rc = loss_grads(t, n, d_noisy, d_clean, max_range, loss);
+    float losses[3];
+    rc = loss_grads(t, n, d_noisy, d_clean, max_range, nullptr, loss ? losses : nullptr);
     if (rc != MPPI_OK) return rc;
-    t->step += 1;
-    mppi::AdamTable tab{};
-    int max_size = 0;
-    for (int i = 0; i < mppi::kNumTensors; ++i) {
-        tab.p[i] = t->param[i];
-        tab.g[i] = t->grad[i];
-        tab.m[i] = t->m[i];
-        tab.v[i] = t->v[i];
-        tab.size[i] = t->size[i];
-        max_size = std::max(max_size, t->size[i]);
+    if (loss) *loss = losses[0];
+    return adam_all(t);
+}
+
+extern "C" int mppi_encoder_train_set_sdf(mppi_encoder_trainer* t, const float* const* layers, int pe_levels,
+                                          float softplus_beta, float lambda_recon, float lambda_sdf,
+                                          int max_points_per_image) {
+    using namespace mppi;
+    if (!t) return tfail(nullptr, MPPI_E_INVALID, "mppi_encoder_train_set_sdf: NULL trainer");
+    if (!layers) return tfail(t, MPPI_E_INVALID, "mppi_encoder_train_set_sdf: NULL layers");
+    for (int i = 0; i < 10; ++i)
+        if (!layers[i]) return tfail(t, MPPI_E_INVALID, "mppi_encoder_train_set_sdf: layer array %d is NULL", i);
+    if (pe_levels < 0 || pe_levels > MPPI_MAX_PE_LEVELS)
+        return tfail(t, MPPI_E_INVALID, "pe_levels out of [0, MPPI_MAX_PE_LEVELS]");
+    if (!(softplus_beta > 0.f && softplus_beta < 1e6f) || !(lambda_recon >= 0.f) || !(lambda_sdf >= 0.f))
+        return tfail(t, MPPI_E_INVALID, "softplus_beta must be > 0 and the lambdas >= 0");
+    if (max_points_per_image < kSdPts || max_points_per_image % kSdPts != 0 || max_points_per_image > (1 << 16))
+        return tfail(t, MPPI_E_INVALID, "max_points_per_image must be a multiple of 32 in [32, 65536]");
+    if (t->sdf) return tfail(t, MPPI_E_INVALID, "the SDF decoder is already set");
+    if (cudaFuncSetAttribute(sdf_dz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSdSmem)) !=
+        cudaSuccess)
+        return tfail(t, MPPI_E_CUDA, "shared-memory configuration of the SDF kernel failed");
+    const int nf = 3 + 6 * pe_levels, ld = nf + kLat;
+    float *W1, *b1, *WT[3], *Wl[3], *bl[3], *w5;
+    bool ok = talloc(t, &W1, static_cast<size_t>(kSdHidden) * ld) && talloc(t, &b1, kSdHidden) &&
+              talloc(t, &w5, kSdHidden);
+    for (int l = 0; l < 3 && ok; ++l)
+        ok = talloc(t, &WT[l], kSdHidden * kSdHidden) && talloc(t, &Wl[l], kSdHidden * kSdHidden) &&
+             talloc(t, &bl[l], kSdHidden);
+    const size_t per = static_cast<size_t>(t->batch) * (max_points_per_image / kSdPts);
+    ok = ok && talloc(t, &t->sdf_b1p, static_cast<size_t>(t->batch) * kSdHidden) &&
+         talloc(t, &t->sdf_part, per * kSdHidden) && talloc(t, &t->sdf_loss_part, per) &&
+         talloc(t, &t->sdf_loss_img, t->batch);
+    if (!ok) return tfail(t, MPPI_E_OOM, "device allocation failed");
+    std::vector<float> tr(kSdHidden * kSdHidden);
+    cudaError_t ce = cudaMemcpy(W1, layers[0], sizeof(float) * kSdHidden * ld, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(b1, layers[1], sizeof(float) * kSdHidden, cudaMemcpyHostToDevice);
+    for (int l = 0; l < 3 && ce == cudaSuccess; ++l) {
+        const float* Wsrc = layers[2 + 2 * l];
+        for (int o = 0; o < kSdHidden; ++o)
+            for (int k = 0; k < kSdHidden; ++k) tr[k * kSdHidden + o] = Wsrc[o * kSdHidden + k];
+        ce = cudaMemcpy(WT[l], tr.data(), sizeof(float) * kSdHidden * kSdHidden, cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpy(Wl[l], Wsrc, sizeof(float) * kSdHidden * kSdHidden, cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpy(bl[l], layers[3 + 2 * l], sizeof(float) * kSdHidden, cudaMemcpyHostToDevice);
     }
-    const float c1 = static_cast<float>(1.0 - std::pow(0.9, t->step));
-    const float c2 = static_cast<float>(1.0 - std::pow(0.999, t->step));
-    mppi::adam_kernel<<<dim3((max_size + 255) / 256, mppi::kNumTensors), 256, 0, t->enc->stream>>>(tab, t->lr, c1, c2);
-    const cudaError_t ce = cudaGetLastError();
-    if (ce != cudaSuccess) return tfail(t, MPPI_E_CUDA, "Adam launch failed: %s", cudaGetErrorString(ce));
+    if (ce == cudaSuccess) ce = cudaMemcpy(w5, layers[8], sizeof(float) * kSdHidden, cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) return tfail(t, MPPI_E_CUDA, "weight upload failed: %s", cudaGetErrorString(ce));
+    t->net.W1 = W1;
+    t->net.b1 = b1;
+    for (int l = 0; l < 3; ++l) {
+        t->net.WT[l] = WT[l];
+        t->net.W[l] = Wl[l];
+        t->net.b[l] = bl[l];
+    }
+    t->net.w5 = w5;
+    t->net.b5 = layers[9][0];
+    t->net.beta = softplus_beta;
+    t->net.nf = nf;
+    t->net.pe = pe_levels;
+    t->lam_recon = lambda_recon;
+    t->lam_sdf = lambda_sdf;
+    t->max_points = max_points_per_image;
+    t->sdf = true;
     return MPPI_OK;
+}
+
+extern "C" int mppi_encoder_train_loss_grads_sdf(mppi_encoder_trainer* t, int n, const float* d_noisy,
+                                                 const float* d_clean, float max_range, const float* d_points,
+                                                 const float* d_labels, int n_points, float* losses,
+                                                 float* const* grads_out) {
+    if (!t) return tfail(nullptr, MPPI_E_INVALID, "mppi_encoder_train_loss_grads_sdf: NULL trainer");
+    int rc = check_batch(t, n, d_noisy, d_clean, max_range);
+    if (rc == MPPI_OK) rc = check_queries(t, d_points, d_labels, n_points);
+    if (rc != MPPI_OK) return rc;
+    const Queries q{d_points, d_labels, n_points};
+    rc = loss_grads(t, n, d_noisy, d_clean, max_range, &q, losses);
+    if (rc != MPPI_OK) return rc;
+    return grads_out ? read_grads(t, grads_out) : MPPI_OK;
+}
+
+extern "C" int mppi_encoder_train_step_sdf(mppi_encoder_trainer* t, int n, const float* d_noisy, const float* d_clean,
+                                           float max_range, const float* d_points, const float* d_labels,
+                                           int n_points, float* losses) {
+    if (!t) return tfail(nullptr, MPPI_E_INVALID, "mppi_encoder_train_step_sdf: NULL trainer");
+    int rc = check_batch(t, n, d_noisy, d_clean, max_range);
+    if (rc == MPPI_OK) rc = check_queries(t, d_points, d_labels, n_points);
+    if (rc != MPPI_OK) return rc;
+    const Queries q{d_points, d_labels, n_points};
+    rc = loss_grads(t, n, d_noisy, d_clean, max_range, &q, losses);
+    if (rc != MPPI_OK) return rc;
+    return adam_all(t);
 }
 
 extern "C" int mppi_encoder_train_get_decoder(mppi_encoder_trainer* t, float* W, float* b) {

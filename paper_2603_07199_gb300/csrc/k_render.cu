@@ -271,6 +271,65 @@ __global__ void __launch_bounds__(kRtThreads) render_depth_kernel(RenderParams P
     }
 }
 
+// Training queries of the SDF supervision: camera-frame points of image i and the exact SDF
+// of the nearest frame there (Philox blocks A, B of (point, image, frame, tag); see the header).
+constexpr uint32_t kQueryTagA = 0x5DF0Au;
+constexpr uint32_t kQueryTagB = 0x5DF0Bu;
+
+__global__ void __launch_bounds__(128) sample_queries_kernel(RenderParams P, const float* __restrict__ cams,
+                                                             const float* __restrict__ gates, int n_points,
+                                                             float near_frac, float* __restrict__ points,
+                                                             float* __restrict__ labels) {
+    const long long e = static_cast<long long>(blockIdx.x) * 128 + threadIdx.x;
+    if (e >= static_cast<long long>(P.n_views) * n_points) return;
+    const int i = static_cast<int>(e / n_points), j = static_cast<int>(e - static_cast<long long>(i) * n_points);
+    const float* cp = cams + static_cast<size_t>(i) * 7;
+    const Mat3 Rc = quat_to_mat(cp[3], cp[4], cp[5], cp[6]);
+    const uint4 A = philox4x32_10(make_uint4(static_cast<uint32_t>(j), static_cast<uint32_t>(i), P.frame, kQueryTagA),
+                                  P.key0, P.key1);
+    const uint4 Bw = philox4x32_10(make_uint4(static_cast<uint32_t>(j), static_cast<uint32_t>(i), P.frame, kQueryTagB),
+                                   P.key0, P.key1);
+    float px, py, pz;                                  // camera frame
+    if (word_to_uniform(A.w) < near_frac && P.n_gates > 0) {
+        const int g = static_cast<int>((static_cast<unsigned long long>(A.x >> 8) * P.n_gates) >> 24);
+        const float* gp = gates + g * 7;
+        const Mat3 Rg = quat_to_mat(gp[3], gp[4], gp[5], gp[6]);
+        const float hx = P.hd + 0.3f, hy = P.a_out + 0.3f;
+        const float qx = (2.f * word_to_uniform(Bw.x) - 1.f) * hx;
+        const float qy = (2.f * word_to_uniform(Bw.y) - 1.f) * hy;
+        const float qz = (2.f * word_to_uniform(Bw.z) - 1.f) * hy;
+        // world = Rg q + t_g; camera = Rc^T (world - t_c)
+        const float wx = Rg.m[0][0] * qx + Rg.m[0][1] * qy + Rg.m[0][2] * qz + gp[0] - cp[0];
+        const float wy = Rg.m[1][0] * qx + Rg.m[1][1] * qy + Rg.m[1][2] * qz + gp[1] - cp[1];
+        const float wz = Rg.m[2][0] * qx + Rg.m[2][1] * qy + Rg.m[2][2] * qz + gp[2] - cp[2];
+        px = Rc.m[0][0] * wx + Rc.m[1][0] * wy + Rc.m[2][0] * wz;
+        py = Rc.m[0][1] * wx + Rc.m[1][1] * wy + Rc.m[2][1] * wz;
+        pz = Rc.m[0][2] * wx + Rc.m[1][2] * wy + Rc.m[2][2] * wz;
+    } else {
+        px = 0.2f + word_to_uniform(A.y) * (P.max_range - 0.2f);
+        py = -(static_cast<float>(P.W) * word_to_uniform(A.z) - P.cx) * px * P.inv_fx;
+        pz = -(static_cast<float>(P.H) * word_to_uniform(Bw.w) - P.cy) * px * P.inv_fy;
+    }
+    // label: the nearest frame's exact SDF at world = Rc p + t_c
+    const float wx = Rc.m[0][0] * px + Rc.m[0][1] * py + Rc.m[0][2] * pz + cp[0];
+    const float wy = Rc.m[1][0] * px + Rc.m[1][1] * py + Rc.m[1][2] * pz + cp[1];
+    const float wz = Rc.m[2][0] * px + Rc.m[2][1] * py + Rc.m[2][2] * pz + cp[2];
+    float best = __int_as_float(0x7f800000);
+    for (int g = 0; g < P.n_gates; ++g) {
+        const float* gp = gates + g * 7;
+        const Mat3 Rg = quat_to_mat(gp[3], gp[4], gp[5], gp[6]);
+        const float dx = wx - gp[0], dy = wy - gp[1], dz = wz - gp[2];
+        const float gx = Rg.m[0][0] * dx + Rg.m[1][0] * dy + Rg.m[2][0] * dz;
+        const float gy = Rg.m[0][1] * dx + Rg.m[1][1] * dy + Rg.m[2][1] * dz;
+        const float gz = Rg.m[0][2] * dx + Rg.m[1][2] * dy + Rg.m[2][2] * dz;
+        best = fminf(best, frame_sdf(gx, gy, gz, P.a_in, P.a_out, P.hd));
+    }
+    points[e * 3 + 0] = px;
+    points[e * 3 + 1] = py;
+    points[e * 3 + 2] = pz;
+    labels[e] = best;
+}
+
 int render_fail(const char* msg, int code = MPPI_E_INVALID, cudaError_t e = cudaSuccess) {
     char buf[256];
     if (e != cudaSuccess)
@@ -355,6 +414,48 @@ extern "C" int mppi_render_depth(const mppi_depth_camera* cam, int n_views, cons
         render_depth_kernel<true><<<grid, kRtThreads, 0, s>>>(P, d_cam_poses, d_gate_poses, d_depth);
     else
         render_depth_kernel<false><<<grid, kRtThreads, 0, s>>>(P, d_cam_poses, d_gate_poses, d_depth);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return render_fail("launch failed", MPPI_E_CUDA, e);
+    return MPPI_OK;
+}
+
+extern "C" int mppi_sample_sdf_queries(const mppi_depth_camera* cam, int n_views, const float* d_cam_poses,
+                                       int n_gates, const float* d_gate_poses, int n_points, float near_frac,
+                                       float* d_points, float* d_labels, void* stream) {
+    using namespace mppi;
+    if (!cam) return render_fail("NULL camera");
+    if (cam->width < 1 || cam->height < 1 || !finite_positive(cam->fx) || !finite_positive(cam->fy) ||
+        !finite_positive(cam->max_range) || !(cam->max_range > 0.2f))
+        return render_fail("camera size, focal lengths or max_range (> 0.2 m) out of range");
+    if (!finite_positive(cam->gate_inner_half) || !(cam->gate_outer_half > cam->gate_inner_half) ||
+        !finite_positive(cam->gate_half_depth))
+        return render_fail("frame geometry needs 0 < gate_inner_half < gate_outer_half and gate_half_depth > 0");
+    if (n_views < 0 || n_views > (1 << 24) || n_points < 1 || n_points > (1 << 20) ||
+        static_cast<long long>(n_views) * n_points > (1LL << 31))
+        return render_fail("n_views in [0, 2^24], n_points in [1, 2^20], n_views x n_points <= 2^31");
+    if (n_gates < 1 || n_gates > MPPI_MAX_RENDER_GATES) return render_fail("n_gates out of [1, MPPI_MAX_RENDER_GATES]");
+    if (!(near_frac >= 0.f && near_frac <= 1.f)) return render_fail("near_frac out of [0, 1]");
+    if (n_views == 0) return MPPI_OK;
+    if (!d_cam_poses || !d_gate_poses || !d_points || !d_labels) return render_fail("NULL pointer");
+    RenderParams P{};
+    P.W = cam->width;
+    P.H = cam->height;
+    P.n_views = n_views;
+    P.n_gates = n_gates;
+    P.inv_fx = 1.f / cam->fx;
+    P.inv_fy = 1.f / cam->fy;
+    P.cx = cam->cx;
+    P.cy = cam->cy;
+    P.max_range = cam->max_range;
+    P.a_in = cam->gate_inner_half;
+    P.a_out = cam->gate_outer_half;
+    P.hd = cam->gate_half_depth;
+    P.key0 = static_cast<uint32_t>(cam->seed);
+    P.key1 = static_cast<uint32_t>(cam->seed >> 32);
+    P.frame = cam->frame;
+    const long long total = static_cast<long long>(n_views) * n_points;
+    sample_queries_kernel<<<static_cast<unsigned>((total + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
+        P, d_cam_poses, d_gate_poses, n_points, near_frac, d_points, d_labels);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return render_fail("launch failed", MPPI_E_CUDA, e);
     return MPPI_OK;

@@ -164,3 +164,108 @@ def test_training_steps_are_bit_reproducible():
     for a, b in zip(runs[0][1], runs[1][1]):
         np.testing.assert_array_equal(a, b)
     assert runs[0][0][-1] < runs[0][0][0]
+
+
+# ---------------------------------------------------------------- SDF term (frozen decoder)
+QCAM = dict(width=53, height=37, fx=31.8, fy=31.8, cx=26.5, cy=18.5, max_range=10.0)
+
+
+def _qcam(seed=7, frame=0):
+    cam = B.mppi_depth_camera_default()
+    for k, v in QCAM.items():
+        setattr(cam, k, v)
+    cam.seed, cam.frame = seed, frame
+    return cam
+
+
+def test_query_sampler_matches_oracle():
+    """Points within 2e-5 m (+ 2e-6 relative: FP32 rotations of ~10-20 m coordinates) and labels
+    within 2e-5 m of the oracle's; a near / frustum decision taken differently would move a
+    point by metres."""
+    torch = _torch()
+    gates = W.gate_track(3, seed=13)
+    cams = W.camera_views(5, gates, seed=19)
+    d_cams = torch.from_numpy(np.ascontiguousarray(cams, np.float32)).cuda()
+    d_gates = torch.from_numpy(np.ascontiguousarray(gates, np.float32)).cuda()
+    pts = torch.empty(5, 96, 3, device="cuda")
+    lab = torch.empty(5, 96, device="cuda")
+    B.mppi_sample_sdf_queries(_qcam(), 5, d_cams, 3, d_gates, 96, 0.5, pts, lab)
+    torch.cuda.synchronize()
+    p_ref, l_ref = OT.sample_queries(cams, gates, 96, near_frac=0.5, seed=7, frame=0, **QCAM)
+    err_p = np.abs(pts.cpu().numpy() - p_ref)
+    assert np.all(err_p <= 2e-5 + 2e-6 * np.abs(p_ref)), err_p.max()
+    assert np.max(np.abs(lab.cpu().numpy() - l_ref)) <= 2e-5
+    assert 0.3 < np.mean(l_ref < 0.5) < 0.9
+    with pytest.raises(B.MppiError):
+        B.mppi_sample_sdf_queries(_qcam(), 5, d_cams, 0, d_gates, 96, 0.5, pts, lab)
+
+
+def test_sdf_term_gradients_match_oracle():
+    torch, enc, tr, enc_layers, dec, noisy, clean = _setup(37, 53, 3, 4)
+    gates = W.gate_track(2)
+    cams = W.camera_views(3, gates, seed=17)          # the views _data rendered
+    p, lab = OT.sample_queries(cams, gates, 64, near_frac=0.5, seed=5, frame=2, **QCAM)
+    sdf_dec = W.xavier_mlp(1, in_dim=3 + 6 * 2 + 64)
+    try:
+        B.mppi_encoder_train_set_sdf(tr, _flat(sdf_dec), 2, 100.0, 0.5, 1.0, 64)
+        grads = [np.zeros(s, np.float32) for s in _shapes(enc_layers, dec)]
+        tot, rec, sdf = B.mppi_encoder_train_loss_grads_sdf(
+            tr, 3, torch.from_numpy(noisy).cuda(), torch.from_numpy(clean).cuda(), 10.0,
+            torch.from_numpy(np.ascontiguousarray(p, np.float32)).cuda(),
+            torch.from_numpy(np.ascontiguousarray(lab, np.float32)).cuda(), 64, grads)
+    finally:
+        B.mppi_encoder_train_destroy(tr)
+        B.mppi_encoder_destroy(enc)
+    L, Lr, Ls, g_enc, g_dec = OT.gradients_joint(noisy, clean, 10.0, enc_layers, dec,
+                                                  p.astype(np.float32).astype(np.float64),
+                                                  lab.astype(np.float32).astype(np.float64), sdf_dec, 2, 0.5, 1.0)
+    assert abs(rec - Lr) <= 1e-5 * Lr and abs(sdf - Ls) <= 1e-4 * Ls and abs(tot - L) <= 1e-4 * L
+    want = [g for pair in g_enc for g in pair] + list(g_dec)
+    for i, (got, ref) in enumerate(zip(grads, want)):
+        scale = np.max(np.abs(ref))
+        assert scale > 0 and np.max(np.abs(got - ref)) <= 2e-3 * scale, (i, np.max(np.abs(got - ref)), scale)
+
+
+def test_sdf_term_training_lowers_heldout_sdf_error():
+    """1500 steps of the joint loss (reconstruction + SDF through a frozen Xavier decoder with two
+    encoding levels) on GPU-rendered pairs and GPU-sampled queries: the held-out SDF error falls by
+    more than 15 % and the reconstruction error by more than half.  (The frozen decoder is not a
+    trained one, so the latent cannot make it exact; the paper freezes its stage-1 decoder.)"""
+    torch = _torch()
+    h, w, n_train, n_test, batch, npts = 48, 64, 2048, 64, 32, 256
+    gates = W.gate_track(2)
+    cam = B.mppi_depth_camera_default()
+    for k, v in dict(width=w, height=h, fx=38.5, fy=38.5, cx=32.0, cy=24.0, max_range=10.0).items():
+        setattr(cam, k, v)
+    cams = torch.from_numpy(np.ascontiguousarray(W.camera_views(n_train + n_test, gates, seed=44), np.float32)).cuda()
+    d_gates = torch.from_numpy(np.ascontiguousarray(gates, np.float32)).cuda()
+    clean = torch.empty(n_train + n_test, h, w, device="cuda")
+    noisy = torch.empty_like(clean)
+    B.mppi_render_depth(cam, n_train + n_test, cams, 2, d_gates, clean)
+    cam.noise_depth_coeff, cam.dropout, cam.seed = 0.01, 0.03, 5
+    B.mppi_render_depth(cam, n_train + n_test, cams, 2, d_gates, noisy)
+    pts = torch.empty(n_train + n_test, npts, 3, device="cuda")
+    lab = torch.empty(n_train + n_test, npts, device="cuda")
+    cam.seed = 11
+    B.mppi_sample_sdf_queries(cam, n_train + n_test, cams, 2, d_gates, npts, 0.5, pts, lab)
+    enc = B.mppi_encoder_create(h, w, n_test, _flat(W.encoder_weights(7)))
+    Wd, bd = _decoder(48)
+    bd[:] = 0.9
+    tr = B.mppi_encoder_train_create(enc, n_test, 3e-3, Wd, bd)
+    sl = slice(n_train, None)
+    try:
+        B.mppi_encoder_train_set_sdf(tr, _flat(W.xavier_mlp(1, in_dim=3 + 12 + 64)), 2, 100.0, 1.0, 1.0, npts)
+        before = B.mppi_encoder_train_loss_grads_sdf(tr, n_test, noisy[sl], clean[sl], 10.0, pts[sl].contiguous(),
+                                                     lab[sl].contiguous(), npts)
+        rng = np.random.default_rng(0)
+        for _ in range(1500):
+            idx = torch.from_numpy(rng.choice(n_train, batch, replace=False)).cuda()
+            B.mppi_encoder_train_step_sdf(tr, batch, noisy[idx].contiguous(), clean[idx].contiguous(), 10.0,
+                                          pts[idx].contiguous(), lab[idx].contiguous(), npts, want_loss=False)
+        after = B.mppi_encoder_train_loss_grads_sdf(tr, n_test, noisy[sl], clean[sl], 10.0, pts[sl].contiguous(),
+                                                    lab[sl].contiguous(), npts)
+    finally:
+        B.mppi_encoder_train_destroy(tr)
+        B.mppi_encoder_destroy(enc)
+    print(f"held-out (total, recon, SDF) {before} -> {after}")
+    assert after[2] < 0.85 * before[2] and after[1] < 0.5 * before[1]
