@@ -245,3 +245,38 @@ def gradients_joint(noisy, clean, max_range, enc_layers, dec, points, labels, sd
             delta = dx * (x_in > 0.0)
     grads.append((gW5, gb5))
     return lam_recon * L_rec + lam_sdf * L_sdf, L_rec, L_sdf, grads, (gWd, gbd)
+
+
+# ---------------------------------------------------------------- stage 1 in full: the decoder trains too
+def decoder_grads(z, points, labels, dec_layers, pe_levels, beta=100.0):
+    """SDF term with the decoder trainable: (mean |r|, d/dz [N, 64], [(dW, db) of the 5 layers])."""
+    from .mlp import positional_encoding, softplus, softplus_grad
+    layers = [(np.asarray(W, dtype=np.float64), np.asarray(b, dtype=np.float64)) for W, b in dec_layers]
+    z = np.asarray(z, dtype=np.float64)
+    n, m, _ = np.asarray(points).shape
+    nf = 3 + 6 * pe_levels
+    gW = [np.zeros_like(W) for W, _ in layers]
+    gb = [np.zeros_like(b) for _, b in layers]
+    dz = np.zeros_like(z)
+    L = 0.0
+    for i in range(n):
+        x = np.concatenate([positional_encoding(points[i], pe_levels), np.broadcast_to(z[i], (m, z.shape[1]))], axis=1)
+        hs, pre = [x], []
+        for W, b in layers[:-1]:
+            a = hs[-1] @ W.T + b
+            pre.append(a)
+            hs.append(softplus(a, beta))
+        s = (hs[-1] @ layers[-1][0].T + layers[-1][1])[:, 0]
+        r = s - labels[i]
+        L += float(np.sum(np.abs(r)))
+        g = (np.sign(r) / (n * m))[:, None]                     # d L / d s, [m, 1]
+        gW[-1] += g.T @ hs[-1]
+        gb[-1] += g.sum(axis=0)
+        g = g @ layers[-1][0]                                    # d L / d h4
+        for l in range(len(layers) - 2, -1, -1):
+            g = g * softplus_grad(pre[l], beta)                  # d L / d a_{l+1}
+            gW[l] += g.T @ hs[l]
+            gb[l] += g.sum(axis=0)
+            g = g @ layers[l][0]                                 # d L / d (layer input)
+        dz[i] = g[:, nf:].sum(axis=0)
+    return L / (n * m), dz, list(zip(gW, gb))

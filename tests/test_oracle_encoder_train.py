@@ -147,3 +147,31 @@ def test_joint_gradients_reduce_to_reconstruction_and_match_differences():
             lm = sdf_loss()
             Wt[idx] = old
             assert abs((lp - lm) / (2 * h) - g[li][0][idx]) <= 1e-5 * scale + 1e-9
+
+
+def test_decoder_grads_match_frozen_dz_and_central_differences():
+    rng = np.random.default_rng(8)
+    gates, cams, kw = _scene()
+    p, lab = T.sample_queries(cams, gates, 48, near_frac=0.5, seed=3, frame=4, **kw)
+    dec = [(W.astype(np.float64), b.astype(np.float64) + 0.01 * rng.normal(size=b.shape))
+           for W, b in W.xavier_mlp(2, in_dim=3 + 6 + 64)]
+    z = rng.normal(0, 1, (3, 64))
+    L, dz, gl = T.decoder_grads(z, p, lab, dec, 1)
+    L2, dz2 = T.sdf_term(z, p, lab, dec, 1)
+    assert abs(L - L2) < 1e-12
+    np.testing.assert_allclose(dz, dz2, rtol=1e-10, atol=1e-14)
+    h = 1e-6
+    for li in range(5):
+        for which in (0, 1):
+            arr = dec[li][which]
+            ref = gl[li][which]
+            scale = np.max(np.abs(ref)) + 1e-12
+            for _ in range(4):
+                idx = tuple(rng.integers(s) for s in arr.shape)
+                old = arr[idx]
+                arr[idx] = old + h
+                lp = T.sdf_term(z, p, lab, dec, 1)[0]
+                arr[idx] = old - h
+                lm = T.sdf_term(z, p, lab, dec, 1)[0]
+                arr[idx] = old
+                assert abs((lp - lm) / (2 * h) - ref[idx]) <= 1e-5 * scale + 1e-10, (li, which, idx)
