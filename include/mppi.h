@@ -491,23 +491,28 @@ int mppi_encoder_train_loss_grads(mppi_encoder_trainer* trainer, int n, const fl
 int mppi_encoder_train_step(mppi_encoder_trainer* trainer, int n, const float* d_noisy, const float* d_clean,
                             float max_range, float* loss);
 /*
- * The SDF term of the same stage with the Gate-SDF decoder g_phi frozen (the paper freezes it
- * in its second stage): L = lambda_recon L_recon + lambda_sdf mean |g_phi(z_i, PE(p_ij)) - s_ij|
- * over camera-frame query points p_ij of image i with exact SDF labels s_ij (e.g. from
- * mppi_sample_sdf_queries); the decoder's input is [PE(p), z] as in mppi_set_sdf_weights with
- * pe_levels, its activation softplus with softplus_beta.
+ * The SDF term of the same stage: L = lambda_recon L_recon + lambda_sdf mean
+ * |g_phi(z_i, PE(p_ij)) - s_ij| over camera-frame query points p_ij of image i with exact SDF
+ * labels s_ij (e.g. from mppi_sample_sdf_queries); the decoder's input is [PE(p), z] as in
+ * mppi_set_sdf_weights with pe_levels, its activation softplus with softplus_beta.
  *   layers                10 host arrays W1 [128][3 + 6 pe_levels + 64], b1, W2..W4 [128][128],
- *                         b2..b4, w5 [1][128], b5 [1] (copied; the decoder is not trained)
+ *                         b2..b4, w5 [1][128], b5 [1]: g_phi's initial weights (copied)
  *   max_points_per_image  32 .. 65536, a multiple of 32: the most query points a call may pass
+ *   train_decoder         0: g_phi stays frozen (the paper's second stage); 1: g_phi trains with
+ *                         the encoder and D_psi (its first stage), Adam on its 10 tensors too
  * Errors: MPPI_E_INVALID (bad argument, or a decoder already set), MPPI_E_OOM, MPPI_E_CUDA.
  */
 int mppi_encoder_train_set_sdf(mppi_encoder_trainer* trainer, const float* const* layers, int pe_levels,
-                               float softplus_beta, float lambda_recon, float lambda_sdf, int max_points_per_image);
+                               float softplus_beta, float lambda_recon, float lambda_sdf, int max_points_per_image,
+                               int train_decoder);
+/* g_phi's current weights (10 host arrays as in mppi_encoder_train_set_sdf; NULL entries skipped). */
+int mppi_encoder_train_get_sdf_decoder(mppi_encoder_trainer* trainer, float* const* layers_out);
 /*
  * As mppi_encoder_train_loss_grads / _step with the SDF term: d_points n x n_points x 3 and
  * d_labels n x n_points floats (device), n_points a multiple of 32 up to max_points_per_image;
  * losses (nullable, host [3]): the weighted total, the reconstruction mean |r| and the SDF mean
- * |r|.  MPPI_E_NOT_READY before mppi_encoder_train_set_sdf.
+ * |r|; grads_out as before, followed, when g_phi trains, by its 10 gradients (22 arrays).
+ * MPPI_E_NOT_READY before mppi_encoder_train_set_sdf.
  */
 int mppi_encoder_train_loss_grads_sdf(mppi_encoder_trainer* trainer, int n, const float* d_noisy, const float* d_clean,
                                       float max_range, const float* d_points, const float* d_labels, int n_points,

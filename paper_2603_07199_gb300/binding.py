@@ -62,7 +62,7 @@ EXPORTS = [
     "mppi_encoder_get_weights", "mppi_encoder_train_create", "mppi_encoder_train_destroy",
     "mppi_encoder_train_last_error", "mppi_encoder_train_loss_grads", "mppi_encoder_train_step",
     "mppi_encoder_train_get_decoder", "mppi_encoder_train_set_sdf", "mppi_encoder_train_loss_grads_sdf",
-    "mppi_encoder_train_step_sdf",
+    "mppi_encoder_train_step_sdf", "mppi_encoder_train_get_sdf_decoder",
 ]
 
 
@@ -186,7 +186,8 @@ _SIGS = {
                                                ctypes.POINTER(ctypes.c_float)]),
     "mppi_encoder_train_get_decoder": (ctypes.c_int, [_vp, _vp, _vp]),
     "mppi_encoder_train_set_sdf": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_float,
-                                                  ctypes.c_float, ctypes.c_float, ctypes.c_int]),
+                                                  ctypes.c_float, ctypes.c_float, ctypes.c_int, ctypes.c_int]),
+    "mppi_encoder_train_get_sdf_decoder": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
     "mppi_encoder_train_loss_grads_sdf": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_float, _vp, _vp,
                                                          ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
     "mppi_encoder_train_step_sdf": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_float, _vp, _vp,
@@ -561,10 +562,15 @@ def mppi_encoder_train_get_decoder(trainer, W, b):
 
 
 def mppi_encoder_train_set_sdf(trainer, layers, pe_levels, softplus_beta, lambda_recon, lambda_sdf,
-                               max_points_per_image):
+                               max_points_per_image, train_decoder=False):
     arr = (_vp * len(layers))(*[_ptr(a) for a in layers])
     return _etcheck(load().mppi_encoder_train_set_sdf(trainer, arr, pe_levels, softplus_beta, lambda_recon,
-                                                      lambda_sdf, max_points_per_image), trainer)
+                                                      lambda_sdf, max_points_per_image, int(train_decoder)), trainer)
+
+
+def mppi_encoder_train_get_sdf_decoder(trainer, layers_out):
+    arr = (_vp * len(layers_out))(*[_ptr(a) for a in layers_out])
+    return _etcheck(load().mppi_encoder_train_get_sdf_decoder(trainer, arr), trainer)
 
 
 def mppi_encoder_train_loss_grads_sdf(trainer, n, d_noisy, d_clean, max_range, d_points, d_labels, n_points,

@@ -314,12 +314,24 @@ constexpr int kSdHidden = MPPI_HIDDEN;
 struct SdfNet {
     const float* W1;        // [128][NF + 64] as given
     const float* b1;        // [128]
-    const float* WT[3];     // layers 2..4 transposed: [in][out]
     const float* W[3];      // layers 2..4 as given: [out][in]
     const float* b[3];      // [128]
     const float* w5;        // [128]
-    float b5, beta;
+    const float* b5;        // [1]
+    float beta;
     int nf, pe;             // point features 3 + 6 pe
+};
+
+// Per-point records kept for the decoder's weight gradients (all NULL when it is frozen):
+// layer-1 input features X [P][NF], hidden activations H [4][P][128], pre-activation
+// gradients G [4][P][128] and output gradients g5 [P] (P = images x points per image).
+struct SdfRecord {
+    float* X;               // [P][NF + 64]: PE(p) then the image's latent
+    float* H;
+    float* G;
+    float* g5;
+    const float* z;         // [images][64]
+    long long P;
 };
 
 // per image: b1'_i = b1 + W1[:, NF:] z_i
@@ -327,7 +339,7 @@ __global__ void __launch_bounds__(kSdHidden) sdf_bias_kernel(SdfNet N, const flo
                                                               float* __restrict__ b1p) {
     const int i = blockIdx.x, c = threadIdx.x;
     const int ld = N.nf + kLat;
-    float acc = N.b1[c];
+    float acc = N.b1[c];   // (sdf_bias_kernel)
     for (int j = 0; j < kLat; ++j) acc = fmaf(N.W1[c * ld + N.nf + j], z[i * kLat + j], acc);
     b1p[i * kSdHidden + c] = acc;
 }
@@ -364,7 +376,8 @@ __device__ __forceinline__ void sd_gemm(const float (*in)[kSdHidden], const floa
 __global__ void __launch_bounds__(kSdThreads) sdf_dz_kernel(SdfNet N, const float* __restrict__ points,
                                                             const float* __restrict__ labels, int n_points,
                                                             const float* __restrict__ b1p, float coef,
-                                                            float* __restrict__ part, float* __restrict__ loss_part) {
+                                                            float* __restrict__ part, float* __restrict__ loss_part,
+                                                            SdfRecord rec) {
     extern __shared__ __align__(16) float sm[];
     float (*h)[kSdHidden] = reinterpret_cast<float (*)[kSdHidden]>(sm);                      // [32][128]
     float (*spd)[kSdPts][kSdHidden] = reinterpret_cast<float (*)[kSdPts][kSdHidden]>(sm + kSdPts * kSdHidden);
@@ -393,6 +406,13 @@ __global__ void __launch_bounds__(kSdThreads) sdf_dz_kernel(SdfNet N, const floa
         }
     }
     __syncthreads();
+    if (rec.X) {
+        const int ldx = N.nf + kLat;
+        for (int e = threadIdx.x; e < kSdPts * ldx; e += kSdThreads) {
+            const int pnt = e / ldx, f = e - pnt * ldx;
+            rec.X[(q0 + pnt) * ldx + f] = f < N.nf ? pe[f * kSdPts + pnt] : rec.z[img * kLat + f - N.nf];
+        }
+    }
     // layer 1: a1[p][c] = b1'_img[c] + W1[c][0:NF] pe[p]
     const int ld1 = N.nf + kLat;
     for (int e = threadIdx.x; e < kSdPts * kSdHidden; e += kSdThreads) {
@@ -401,12 +421,16 @@ __global__ void __launch_bounds__(kSdThreads) sdf_dz_kernel(SdfNet N, const floa
         for (int f = 0; f < N.nf; ++f) a = fmaf(N.W1[c * ld1 + f], pe[f * kSdPts + pnt], a);
         h[pnt][c] = sp_acc(a, N.beta);
         spd[0][pnt][c] = sp_grad(a, N.beta);
+        if (rec.H) rec.H[(q0 + pnt) * kSdHidden + c] = h[pnt][c];
     }
     // layers 2..4
     for (int l = 0; l < 3; ++l) {
         __syncthreads();
-        for (int e = threadIdx.x; e < kSdHidden * kSdHidden / 4; e += kSdThreads)
-            reinterpret_cast<float4*>(Mst)[e] = reinterpret_cast<const float4*>(N.WT[l])[e];
+        // stage W_l transposed (M[k][o] = W[o][k]): coalesced reads, strided shared writes
+        for (int e = threadIdx.x; e < kSdHidden * kSdHidden; e += kSdThreads) {
+            const int o = e / kSdHidden, k = e - o * kSdHidden;
+            Mst[k * kSdHidden + o] = N.W[l][e];
+        }
         __syncthreads();
         float acc[4][4] = {};
         sd_gemm(h, Mst, acc);
@@ -416,8 +440,10 @@ __global__ void __launch_bounds__(kSdThreads) sdf_dz_kernel(SdfNet N, const floa
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const float a = acc[i][c] + N.b[l][cq * 4 + c];
-                h[rp * 4 + i][cq * 4 + c] = sp_acc(a, N.beta);
+                const float hv = sp_acc(a, N.beta);
+                h[rp * 4 + i][cq * 4 + c] = hv;
                 spd[l + 1][rp * 4 + i][cq * 4 + c] = sp_grad(a, N.beta);
+                if (rec.H) rec.H[((l + 1) * rec.P + q0 + rp * 4 + i) * kSdHidden + cq * 4 + c] = hv;
             }
     }
     __syncthreads();
@@ -429,7 +455,7 @@ __global__ void __launch_bounds__(kSdThreads) sdf_dz_kernel(SdfNet N, const floa
             for (int c = lane; c < kSdHidden; c += 32) sacc = fmaf(N.w5[c], h[pnt][c], sacc);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-            if (lane == 0) sres[pnt] = sacc + N.b5 - labels[q0 + pnt];
+            if (lane == 0) sres[pnt] = sacc + N.b5[0] - labels[q0 + pnt];
         }
     }
     __syncthreads();
@@ -444,6 +470,8 @@ __global__ void __launch_bounds__(kSdThreads) sdf_dz_kernel(SdfNet N, const floa
         const float r = sres[pnt];
         const float sg = r > 0.f ? coef : (r < 0.f ? -coef : 0.f);
         h[pnt][c] = sg * N.w5[c] * spd[3][pnt][c];
+        if (rec.G) rec.G[(3 * rec.P + q0 + pnt) * kSdHidden + c] = h[pnt][c];
+        if (rec.g5 && c == 0) rec.g5[q0 + pnt] = sg;
     }
     for (int l = 2; l >= 0; --l) {
         __syncthreads();
@@ -456,8 +484,11 @@ __global__ void __launch_bounds__(kSdThreads) sdf_dz_kernel(SdfNet N, const floa
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-                h[rp * 4 + i][cq * 4 + c] = acc[i][c] * spd[l][rp * 4 + i][cq * 4 + c];
+            for (int c = 0; c < 4; ++c) {
+                const float gv = acc[i][c] * spd[l][rp * 4 + i][cq * 4 + c];
+                h[rp * 4 + i][cq * 4 + c] = gv;
+                if (rec.G) rec.G[(static_cast<long long>(l) * rec.P + q0 + rp * 4 + i) * kSdHidden + cq * 4 + c] = gv;
+            }
     }
     __syncthreads();
     if (threadIdx.x < kSdHidden) {
@@ -495,13 +526,83 @@ __global__ void __launch_bounds__(kSdHidden) sdf_dz_reduce_kernel(SdfNet N, cons
 constexpr size_t kSdSmem = sizeof(float) * (5 * kSdPts * kSdHidden + kSdHidden * kSdHidden + kSdMaxFeat * kSdPts +
                                             kSdPts);
 
+// Weight gradients of the decoder: out[r][c] = sum_p A[p][r] X[p][c] over the points p of a
+// slice (partials to ws[slice][R][C]), 32 x 32 outputs per block, 2 x 2 per thread.
+constexpr int kGxT = 32;
+constexpr int kGxP = 64;
+__global__ void __launch_bounds__(256) gtx_kernel(const float* __restrict__ A, int R, const float* __restrict__ X,
+                                                  int C, long long P, int chunks_per_slice, float* __restrict__ ws) {
+    __shared__ float sa[kGxP][kGxT + 1];
+    __shared__ float sx[kGxP][kGxT + 1];
+    const int r0 = blockIdx.x * kGxT, c0 = blockIdx.y * kGxT;
+    const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;      // rows 2 tr + {0, 1}, columns 2 tc + {0, 1}
+    float acc[2][2] = {};
+    const long long n_chunks = (P + kGxP - 1) / kGxP;
+    const long long cb = static_cast<long long>(blockIdx.z) * chunks_per_slice;
+    const long long ce = min(cb + chunks_per_slice, n_chunks);
+    for (long long ch = cb; ch < ce; ++ch) {
+        const long long p0 = ch * kGxP;
+        __syncthreads();
+        for (int e = threadIdx.x; e < kGxP * kGxT; e += 256) {
+            const int pp = e / kGxT, k = e - (e / kGxT) * kGxT;
+            const long long pt = p0 + pp;
+            sa[pp][k] = (pt < P && r0 + k < R) ? A[pt * R + r0 + k] : 0.f;
+            sx[pp][k] = (pt < P && c0 + k < C) ? X[pt * C + c0 + k] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int pp = 0; pp < kGxP; ++pp) {
+            const float a0 = sa[pp][2 * tr], a1 = sa[pp][2 * tr + 1];
+            const float x0 = sx[pp][2 * tc], x1 = sx[pp][2 * tc + 1];
+            acc[0][0] = fmaf(a0, x0, acc[0][0]);
+            acc[0][1] = fmaf(a0, x1, acc[0][1]);
+            acc[1][0] = fmaf(a1, x0, acc[1][0]);
+            acc[1][1] = fmaf(a1, x1, acc[1][1]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int r = r0 + 2 * tr + i, c = c0 + 2 * tc + j;
+            if (r < R && c < C) ws[(static_cast<size_t>(blockIdx.z) * R + r) * C + c] = acc[i][j];
+        }
+}
+
+// out[e] = sum over slices of ws[slice][e], in slice order
+__global__ void __launch_bounds__(256) slice_sum_kernel(const float* __restrict__ ws, int n_slices, int n,
+                                                        float* __restrict__ out) {
+    const int e = blockIdx.x * 256 + threadIdx.x;
+    if (e >= n) return;
+    float s = 0.f;
+    for (int q = 0; q < n_slices; ++q) s += ws[static_cast<size_t>(q) * n + e];
+    out[e] = s;
+}
+
+// out[r] = sum_p A[p][r]: one block per column, 256 strided partial sums and a fixed tree
+__global__ void __launch_bounds__(256) colsum_kernel(const float* __restrict__ A, int R, long long P,
+                                                     float* __restrict__ out) {
+    __shared__ float red[256];
+    const int r = blockIdx.x;
+    float s = 0.f;
+    for (long long p = threadIdx.x; p < P; p += 256) s += A[p * R + r];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[r] = red[0];
+}
+
 // ---------------------------------------------------------------- Adam
+constexpr int kMaxTensors = kNumTensors + 10;   // + the SDF decoder's, when it trains
 struct AdamTable {
-    float* p[kNumTensors];
-    const float* g[kNumTensors];
-    float* m[kNumTensors];
-    float* v[kNumTensors];
-    int size[kNumTensors];
+    float* p[kMaxTensors];
+    const float* g[kMaxTensors];
+    float* m[kMaxTensors];
+    float* v[kMaxTensors];
+    int size[kMaxTensors];
 };
 
 __global__ void __launch_bounds__(256) adam_kernel(AdamTable tab, float lr, float c1, float c2) {
@@ -546,6 +647,15 @@ struct mppi_encoder_trainer {
     float lam_recon = 1.f, lam_sdf = 0.f;
     int max_points = 0;
     mppi::SdfNet net{};
+    bool train_dec = false;                 // the SDF decoder trains too (stage 1)
+    float* dparam[10] = {};                 // W1, b1, W2, b2, W3, b3, W4, b4, w5, b5 (device)
+    int dsize[10] = {};
+    float* dgrad[10] = {};
+    float* dm[10] = {};
+    float* dv[10] = {};
+    mppi::SdfRecord rec{};
+    float* gx_ws = nullptr;
+    size_t gx_ws_floats = 0;
     float* sdf_b1p = nullptr;
     float* sdf_part = nullptr;
     float* sdf_loss_part = nullptr;
@@ -618,6 +728,20 @@ cudaError_t launch_dgrad(mppi_encoder_trainer* t, int l, int n, const float* del
     return cudaGetLastError();
 }
 
+// out[R][C] = A^T X over P points (A [P][R], X [P][C]): split over blocks, summed in slice order.
+void gtx(mppi_encoder_trainer* t, const float* A, int R, const float* X, int C, long long P, float* out) {
+    cudaStream_t s = t->enc->stream;
+    const int tiles = ((R + mppi::kGxT - 1) / mppi::kGxT) * ((C + mppi::kGxT - 1) / mppi::kGxT);
+    const long long chunks = (P + mppi::kGxP - 1) / mppi::kGxP;
+    int S = static_cast<int>(std::max(1LL, std::min<long long>((2LL * t->enc->n_sms + tiles - 1) / tiles, chunks)));
+    while (static_cast<size_t>(S) * R * C > t->gx_ws_floats && S > 1) --S;
+    const int cps = static_cast<int>((chunks + S - 1) / S);
+    S = static_cast<int>((chunks + cps - 1) / cps);
+    const dim3 grid((R + mppi::kGxT - 1) / mppi::kGxT, (C + mppi::kGxT - 1) / mppi::kGxT, S);
+    mppi::gtx_kernel<<<grid, 256, 0, s>>>(A, R, X, C, P, cps, t->gx_ws);
+    mppi::slice_sum_kernel<<<(R * C + 255) / 256, 256, 0, s>>>(t->gx_ws, S, R * C, out);
+}
+
 struct Queries {
     const float* points;   // [n][n_points][3] camera frame (device)
     const float* labels;   // [n][n_points] (device)
@@ -640,10 +764,31 @@ int loss_grads(mppi_encoder_trainer* t, int n, const float* d_noisy, const float
     if (q) {
         const int bpi = q->n_points / mppi::kSdPts;
         mppi::sdf_bias_kernel<<<n, mppi::kSdHidden, 0, s>>>(t->net, t->z, t->sdf_b1p);
+        mppi::SdfRecord rec{};
+        if (t->train_dec) {
+            rec = t->rec;
+            rec.P = static_cast<long long>(n) * q->n_points;
+            rec.z = t->z;
+        }
         mppi::sdf_dz_kernel<<<n * bpi, mppi::kSdThreads, mppi::kSdSmem, s>>>(
-            t->net, q->points, q->labels, q->n_points, t->sdf_b1p, t->lam_sdf * inv_q, t->sdf_part, t->sdf_loss_part);
+            t->net, q->points, q->labels, q->n_points, t->sdf_b1p, t->lam_sdf * inv_q, t->sdf_part, t->sdf_loss_part,
+            rec);
         mppi::sdf_dz_reduce_kernel<<<n, mppi::kSdHidden, 0, s>>>(t->net, t->sdf_part, t->sdf_loss_part, bpi, t->dz,
                                                                   t->sdf_loss_img);
+        if (t->train_dec) {
+            const long long P = rec.P;
+            const int H = mppi::kSdHidden, ldx = t->net.nf + mppi::kLat;
+            // dW1 = G1^T X, dW_l = G_l^T H_{l-1}, dw5 = g5^T H4; biases = column sums
+            gtx(t, rec.G, H, rec.X, ldx, P, t->dgrad[0]);
+            mppi::colsum_kernel<<<H, 256, 0, s>>>(rec.G, H, P, t->dgrad[1]);
+            for (int l = 1; l < 4; ++l) {
+                gtx(t, rec.G + static_cast<size_t>(l) * P * H, H, rec.H + static_cast<size_t>(l - 1) * P * H, H, P,
+                    t->dgrad[2 * l]);
+                mppi::colsum_kernel<<<H, 256, 0, s>>>(rec.G + static_cast<size_t>(l) * P * H, H, P, t->dgrad[2 * l + 1]);
+            }
+            gtx(t, rec.g5, 1, rec.H + static_cast<size_t>(3) * P * H, H, P, t->dgrad[8]);
+            mppi::colsum_kernel<<<1, 256, 0, s>>>(rec.g5, 1, P, t->dgrad[9]);
+        }
     }
     mppi::outer_sum_kernel<<<(t->T * mppi::kLat + 255) / 256, 256, 0, s>>>(t->g, t->z, n, t->T, mppi::kLat,
                                                                           t->grad[10], t->grad[11]);
@@ -686,31 +831,45 @@ int loss_grads(mppi_encoder_trainer* t, int n, const float* d_noisy, const float
     return MPPI_OK;
 }
 
-int adam_all(mppi_encoder_trainer* t) {
+int adam_all(mppi_encoder_trainer* t, bool with_decoder) {
     t->step += 1;
     mppi::AdamTable tab{};
-    int max_size = 0;
-    for (int i = 0; i < mppi::kNumTensors; ++i) {
-        tab.p[i] = t->param[i];
-        tab.g[i] = t->grad[i];
-        tab.m[i] = t->m[i];
-        tab.v[i] = t->v[i];
-        tab.size[i] = t->size[i];
+    int max_size = 0, nt = 0;
+    for (int i = 0; i < mppi::kNumTensors; ++i, ++nt) {
+        tab.p[nt] = t->param[i];
+        tab.g[nt] = t->grad[i];
+        tab.m[nt] = t->m[i];
+        tab.v[nt] = t->v[i];
+        tab.size[nt] = t->size[i];
         max_size = std::max(max_size, t->size[i]);
     }
+    if (t->train_dec && with_decoder)
+        for (int i = 0; i < 10; ++i, ++nt) {
+            tab.p[nt] = t->dparam[i];
+            tab.g[nt] = t->dgrad[i];
+            tab.m[nt] = t->dm[i];
+            tab.v[nt] = t->dv[i];
+            tab.size[nt] = t->dsize[i];
+            max_size = std::max(max_size, t->dsize[i]);
+        }
     const float c1 = static_cast<float>(1.0 - std::pow(0.9, t->step));
     const float c2 = static_cast<float>(1.0 - std::pow(0.999, t->step));
-    mppi::adam_kernel<<<dim3((max_size + 255) / 256, mppi::kNumTensors), 256, 0, t->enc->stream>>>(tab, t->lr, c1, c2);
+    mppi::adam_kernel<<<dim3((max_size + 255) / 256, nt), 256, 0, t->enc->stream>>>(tab, t->lr, c1, c2);
     const cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) return tfail(t, MPPI_E_CUDA, "Adam launch failed: %s", cudaGetErrorString(ce));
     return MPPI_OK;
 }
 
-int read_grads(mppi_encoder_trainer* t, float* const* grads_out) {
+int read_grads(mppi_encoder_trainer* t, float* const* grads_out, bool with_decoder) {
     cudaError_t ce = cudaStreamSynchronize(t->enc->stream);
     for (int i = 0; i < mppi::kNumTensors && ce == cudaSuccess; ++i)
         if (grads_out[i])
             ce = cudaMemcpy(grads_out[i], t->grad[i], t->size[i] * sizeof(float), cudaMemcpyDeviceToHost);
+    if (t->train_dec && with_decoder)
+        for (int i = 0; i < 10 && ce == cudaSuccess; ++i)
+            if (grads_out[mppi::kNumTensors + i])
+                ce = cudaMemcpy(grads_out[mppi::kNumTensors + i], t->dgrad[i], t->dsize[i] * sizeof(float),
+                                cudaMemcpyDeviceToHost);
     if (ce != cudaSuccess) return tfail(t, MPPI_E_CUDA, "gradient read-back failed: %s", cudaGetErrorString(ce));
     return MPPI_OK;
 }
@@ -838,7 +997,7 @@ extern "C" int mppi_encoder_train_loss_grads(mppi_encoder_trainer* t, int n, con
     rc = loss_grads(t, n, d_noisy, d_clean, max_range, nullptr, loss ? losses : nullptr);
     if (rc != MPPI_OK) return rc;
     if (loss) *loss = losses[0];
-    return grads_out ? read_grads(t, grads_out) : MPPI_OK;
+    return grads_out ? read_grads(t, grads_out, false) : MPPI_OK;
 }
 
 extern "C" int mppi_encoder_train_step(mppi_encoder_trainer* t, int n, const float* d_noisy, const float* d_clean,
@@ -850,12 +1009,12 @@ extern "C" int mppi_encoder_train_step(mppi_encoder_trainer* t, int n, const flo
     rc = loss_grads(t, n, d_noisy, d_clean, max_range, nullptr, loss ? losses : nullptr);
     if (rc != MPPI_OK) return rc;
     if (loss) *loss = losses[0];
-    return adam_all(t);
+    return adam_all(t, false);
 }
 
 extern "C" int mppi_encoder_train_set_sdf(mppi_encoder_trainer* t, const float* const* layers, int pe_levels,
                                           float softplus_beta, float lambda_recon, float lambda_sdf,
-                                          int max_points_per_image) {
+                                          int max_points_per_image, int train_decoder) {
     using namespace mppi;
     if (!t) return tfail(nullptr, MPPI_E_INVALID, "mppi_encoder_train_set_sdf: NULL trainer");
     if (!layers) return tfail(t, MPPI_E_INVALID, "mppi_encoder_train_set_sdf: NULL layers");
@@ -872,44 +1031,45 @@ extern "C" int mppi_encoder_train_set_sdf(mppi_encoder_trainer* t, const float* 
         cudaSuccess)
         return tfail(t, MPPI_E_CUDA, "shared-memory configuration of the SDF kernel failed");
     const int nf = 3 + 6 * pe_levels, ld = nf + kLat;
-    float *W1, *b1, *WT[3], *Wl[3], *bl[3], *w5;
-    bool ok = talloc(t, &W1, static_cast<size_t>(kSdHidden) * ld) && talloc(t, &b1, kSdHidden) &&
-              talloc(t, &w5, kSdHidden);
-    for (int l = 0; l < 3 && ok; ++l)
-        ok = talloc(t, &WT[l], kSdHidden * kSdHidden) && talloc(t, &Wl[l], kSdHidden * kSdHidden) &&
-             talloc(t, &bl[l], kSdHidden);
+    const int sizes[10] = {kSdHidden * ld, kSdHidden, kSdHidden * kSdHidden, kSdHidden, kSdHidden * kSdHidden,
+                           kSdHidden, kSdHidden * kSdHidden, kSdHidden, kSdHidden, 1};
+    bool ok = true;
+    for (int i = 0; i < 10 && ok; ++i) {
+        t->dsize[i] = sizes[i];
+        ok = talloc(t, &t->dparam[i], sizes[i]);
+    }
     const size_t per = static_cast<size_t>(t->batch) * (max_points_per_image / kSdPts);
     ok = ok && talloc(t, &t->sdf_b1p, static_cast<size_t>(t->batch) * kSdHidden) &&
          talloc(t, &t->sdf_part, per * kSdHidden) && talloc(t, &t->sdf_loss_part, per) &&
          talloc(t, &t->sdf_loss_img, t->batch);
+    if (ok && train_decoder) {
+        const size_t P = static_cast<size_t>(t->batch) * max_points_per_image;
+        for (int i = 0; i < 10 && ok; ++i)
+            ok = talloc(t, &t->dgrad[i], sizes[i]) && talloc(t, &t->dm[i], sizes[i]) && talloc(t, &t->dv[i], sizes[i]);
+        t->gx_ws_floats = static_cast<size_t>(kSdHidden) * kSdHidden * 32;
+        ok = ok && talloc(t, &t->rec.X, P * ld) && talloc(t, &t->rec.H, 4 * P * kSdHidden) &&
+             talloc(t, &t->rec.G, 4 * P * kSdHidden) && talloc(t, &t->rec.g5, P) && talloc(t, &t->gx_ws, t->gx_ws_floats);
+        for (int i = 0; i < 10 && ok; ++i)
+            ok = cudaMemset(t->dm[i], 0, sizes[i] * sizeof(float)) == cudaSuccess &&
+                 cudaMemset(t->dv[i], 0, sizes[i] * sizeof(float)) == cudaSuccess;
+    }
     if (!ok) return tfail(t, MPPI_E_OOM, "device allocation failed");
-    std::vector<float> tr(kSdHidden * kSdHidden);
-    cudaError_t ce = cudaMemcpy(W1, layers[0], sizeof(float) * kSdHidden * ld, cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess) ce = cudaMemcpy(b1, layers[1], sizeof(float) * kSdHidden, cudaMemcpyHostToDevice);
-    for (int l = 0; l < 3 && ce == cudaSuccess; ++l) {
-        const float* Wsrc = layers[2 + 2 * l];
-        for (int o = 0; o < kSdHidden; ++o)
-            for (int k = 0; k < kSdHidden; ++k) tr[k * kSdHidden + o] = Wsrc[o * kSdHidden + k];
-        ce = cudaMemcpy(WT[l], tr.data(), sizeof(float) * kSdHidden * kSdHidden, cudaMemcpyHostToDevice);
-        if (ce == cudaSuccess)
-            ce = cudaMemcpy(Wl[l], Wsrc, sizeof(float) * kSdHidden * kSdHidden, cudaMemcpyHostToDevice);
-        if (ce == cudaSuccess)
-            ce = cudaMemcpy(bl[l], layers[3 + 2 * l], sizeof(float) * kSdHidden, cudaMemcpyHostToDevice);
-    }
-    if (ce == cudaSuccess) ce = cudaMemcpy(w5, layers[8], sizeof(float) * kSdHidden, cudaMemcpyHostToDevice);
+    cudaError_t ce = cudaSuccess;
+    for (int i = 0; i < 10 && ce == cudaSuccess; ++i)
+        ce = cudaMemcpy(t->dparam[i], layers[i], sizes[i] * sizeof(float), cudaMemcpyHostToDevice);
     if (ce != cudaSuccess) return tfail(t, MPPI_E_CUDA, "weight upload failed: %s", cudaGetErrorString(ce));
-    t->net.W1 = W1;
-    t->net.b1 = b1;
+    t->net.W1 = t->dparam[0];
+    t->net.b1 = t->dparam[1];
     for (int l = 0; l < 3; ++l) {
-        t->net.WT[l] = WT[l];
-        t->net.W[l] = Wl[l];
-        t->net.b[l] = bl[l];
+        t->net.W[l] = t->dparam[2 + 2 * l];
+        t->net.b[l] = t->dparam[3 + 2 * l];
     }
-    t->net.w5 = w5;
-    t->net.b5 = layers[9][0];
+    t->net.w5 = t->dparam[8];
+    t->net.b5 = t->dparam[9];
     t->net.beta = softplus_beta;
     t->net.nf = nf;
     t->net.pe = pe_levels;
+    t->train_dec = train_decoder != 0;
     t->lam_recon = lambda_recon;
     t->lam_sdf = lambda_sdf;
     t->max_points = max_points_per_image;
@@ -928,7 +1088,7 @@ extern "C" int mppi_encoder_train_loss_grads_sdf(mppi_encoder_trainer* t, int n,
     const Queries q{d_points, d_labels, n_points};
     rc = loss_grads(t, n, d_noisy, d_clean, max_range, &q, losses);
     if (rc != MPPI_OK) return rc;
-    return grads_out ? read_grads(t, grads_out) : MPPI_OK;
+    return grads_out ? read_grads(t, grads_out, true) : MPPI_OK;
 }
 
 extern "C" int mppi_encoder_train_step_sdf(mppi_encoder_trainer* t, int n, const float* d_noisy, const float* d_clean,
@@ -941,7 +1101,7 @@ extern "C" int mppi_encoder_train_step_sdf(mppi_encoder_trainer* t, int n, const
     const Queries q{d_points, d_labels, n_points};
     rc = loss_grads(t, n, d_noisy, d_clean, max_range, &q, losses);
     if (rc != MPPI_OK) return rc;
-    return adam_all(t);
+    return adam_all(t, true);
 }
 
 extern "C" int mppi_encoder_train_get_decoder(mppi_encoder_trainer* t, float* W, float* b) {
@@ -950,6 +1110,17 @@ extern "C" int mppi_encoder_train_get_decoder(mppi_encoder_trainer* t, float* W,
     if (ce == cudaSuccess)
         ce = cudaMemcpy(W, t->Wd, static_cast<size_t>(t->T) * mppi::kLat * sizeof(float), cudaMemcpyDeviceToHost);
     if (ce == cudaSuccess) ce = cudaMemcpy(b, t->bd, t->T * sizeof(float), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return tfail(t, MPPI_E_CUDA, "decoder read-back failed: %s", cudaGetErrorString(ce));
+    return MPPI_OK;
+}
+
+extern "C" int mppi_encoder_train_get_sdf_decoder(mppi_encoder_trainer* t, float* const* layers_out) {
+    if (!t || !layers_out) return tfail(t, MPPI_E_INVALID, "mppi_encoder_train_get_sdf_decoder: NULL argument");
+    if (!t->sdf) return tfail(t, MPPI_E_NOT_READY, "no SDF decoder set");
+    cudaError_t ce = cudaStreamSynchronize(t->enc->stream);
+    for (int i = 0; i < 10 && ce == cudaSuccess; ++i)
+        if (layers_out[i])
+            ce = cudaMemcpy(layers_out[i], t->dparam[i], t->dsize[i] * sizeof(float), cudaMemcpyDeviceToHost);
     if (ce != cudaSuccess) return tfail(t, MPPI_E_CUDA, "decoder read-back failed: %s", cudaGetErrorString(ce));
     return MPPI_OK;
 }
