@@ -10,8 +10,11 @@ import pytest
 
 import workloads as W
 from oracle import encoder_train as OT
+from oracle import gate_sdf as GS
 from oracle import render as R
 from paper_2603_07199_gb300 import binding as B
+
+from .gpu_helpers import GpuController
 
 pytestmark = pytest.mark.gpu
 
@@ -351,3 +354,76 @@ def test_stage1_training_learns_the_gates():
     print(f"held-out SDF error {before[2]:.3f} -> {after[2]:.3f} m (best constant {const_l1:.3f} m)")
     assert after[2] < 0.3 * before[2] and after[2] < 0.3 * const_l1
     assert all(np.isfinite(a).all() for a in trained)
+
+
+def test_vision_guided_mppi_step_with_the_trained_networks():
+    """The paper's pipeline end to end on the GPU (Fig. 1): render a held-out view, encode it with
+    the stage-1-trained encoder, and run an MPPI step whose Gate-SDF MLP is the trained decoder,
+    queried in the view's cached camera frame (its pose stands in the gate-pose slot, Sec. IV-B);
+    at the rollout states the learned SDF must track the exact frame SDF of the true gates much
+    better than an untrained decoder does."""
+    torch = _torch()
+    h, w, n_train, batch, npts = 48, 64, 2048, 32, 256
+    gates = W.gate_track(2)
+    kwc = dict(width=w, height=h, fx=38.5, fy=38.5, cx=32.0, cy=24.0, max_range=10.0)
+    cam = B.mppi_depth_camera_default()
+    for k, v in kwc.items():
+        setattr(cam, k, v)
+    views = W.camera_views(n_train + 1, gates, seed=44)
+    cams = torch.from_numpy(np.ascontiguousarray(views, np.float32)).cuda()
+    d_gates = torch.from_numpy(np.ascontiguousarray(gates, np.float32)).cuda()
+    clean = torch.empty(n_train + 1, h, w, device="cuda")
+    noisy = torch.empty_like(clean)
+    B.mppi_render_depth(cam, n_train + 1, cams, 2, d_gates, clean)
+    cam.noise_depth_coeff, cam.dropout, cam.seed = 0.01, 0.03, 5
+    B.mppi_render_depth(cam, n_train + 1, cams, 2, d_gates, noisy)
+    pts = torch.empty(n_train, npts, 3, device="cuda")
+    lab = torch.empty(n_train, npts, device="cuda")
+    cam.seed = 11
+    B.mppi_sample_sdf_queries(cam, n_train, cams[:n_train].contiguous(), 2, d_gates, npts, 0.5, pts, lab)
+    untrained = W.xavier_mlp(1, in_dim=3 + 12 + 64)
+    enc = B.mppi_encoder_create(h, w, batch, _flat(W.encoder_weights(7)))
+    Wd, bd = _decoder(48)
+    bd[:] = 0.9
+    tr = B.mppi_encoder_train_create(enc, batch, 1e-3, Wd, bd)
+    try:
+        B.mppi_encoder_train_set_sdf(tr, _flat(untrained), 2, 100.0, 1.0, 1.0, npts, train_decoder=True)
+        rng = np.random.default_rng(0)
+        for _ in range(3000):
+            idx = torch.from_numpy(rng.choice(n_train, batch, replace=False)).cuda()
+            B.mppi_encoder_train_step_sdf(tr, batch, noisy[idx].contiguous(), clean[idx].contiguous(), 10.0,
+                                          pts[idx].contiguous(), lab[idx].contiguous(), npts, want_loss=False)
+        trained = [np.zeros(a.shape, np.float32) for pair in untrained for a in pair]
+        B.mppi_encoder_train_get_sdf_decoder(tr, trained)
+        z = torch.empty(batch, 64, device="cuda")
+        B.mppi_encode_depth(enc, 1, noisy[n_train:].contiguous(), 10.0, z)
+        torch.cuda.synchronize()
+        latent = z[:1].cpu().numpy()
+    finally:
+        B.mppi_encoder_train_destroy(tr)
+        B.mppi_encoder_destroy(enc)
+    view = views[n_train]
+    q = view[3:7] / np.linalg.norm(view[3:7])
+    fwd = np.array([1 - 2 * (q[2] ** 2 + q[3] ** 2), 2 * (q[1] * q[2] + q[0] * q[3]), 2 * (q[1] * q[3] - q[0] * q[2])])
+    state = W.hover_state(view[0:3] + 2.5 * fwd)
+    prm = dict(W.params(1024, 30), pe_levels=2)
+
+    def sdf_at_rollouts(mode, layers, poses, latents):
+        wl = dict(params=prm, poses=poses, latents=latents, layers=layers)
+        ctl = GpuController(wl, mode)
+        try:
+            ctl.step(state, W.hover_nominal(30))
+            return ctl.read(B.MPPI_BUF_SDF), ctl.read(B.MPPI_BUF_POSITIONS)
+        finally:
+            ctl.close()
+
+    pairs = lambda L: [(L[2 * i], L[2 * i + 1]) for i in range(5)]
+    learned, pos = sdf_at_rollouts("fp32", pairs(trained), view[None], latent)
+    random_net, pos_r = sdf_at_rollouts("fp32", untrained, view[None], latent)
+    np.testing.assert_array_equal(pos, pos_r)                    # the same rollouts
+    p = pos[..., :3].reshape(-1, 3).astype(np.float64)
+    exact = np.min([GS.frame_sdf(GS.to_gate_frame(p, gp)) for gp in gates], axis=0).reshape(learned.shape)
+    err_learned = float(np.median(np.abs(learned - exact)))
+    err_random = float(np.median(np.abs(random_net - exact)))
+    print(f"SDF at the rollout states, median |error|: trained {err_learned:.3f} m, untrained {err_random:.3f} m")
+    assert np.isfinite(learned).all() and err_learned < 0.5 * err_random
