@@ -259,6 +259,16 @@ int mppi_read_buffer(mppi_ctx* ctx, int which, float* host_out, size_t n);
 int mppi_read_noise_words(mppi_ctx* ctx, uint32_t* host_out, size_t n);
 
 /*
+ * Test hook for the failure path (no GPU fault is involved): the next step's update
+ * kernel waits at its grid barrier for arrivals that never come, so every one of its
+ * blocks gives up after its bounded wait (2 s of %globaltimer) and returns.  That step
+ * reports MPPI_E_TIMEOUT (mppi_step, or mppi_sync after mppi_step_async); the device
+ * error word and the barrier state are then reset and the context steps normally again.
+ * The controls and warm start of the failed step are unspecified.  Synchronous.
+ */
+int mppi_debug_inject_timeout(mppi_ctx* ctx);
+
+/*
  * Per-kernel timing of the last step run with timing enabled (milliseconds,
  * CUDA events on the context's stream).  mppi_set_timing(ctx, 1) makes each
  * following step record events around its kernels (this adds event records

@@ -17,38 +17,53 @@ __device__ __forceinline__ float warp_sum(float x) {
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     return x;
 }
+// Shuffles within segments of W consecutive lanes (W = 32: the whole warp); src and the
+// lane index of the scans count from the segment's first lane.
+template <int W>
 __device__ __forceinline__ Quat shfl_up(const Quat& q, int d) {
-    return Quat{__shfl_up_sync(0xffffffffu, q.w, d), __shfl_up_sync(0xffffffffu, q.x, d),
-                __shfl_up_sync(0xffffffffu, q.y, d), __shfl_up_sync(0xffffffffu, q.z, d)};
+    return Quat{__shfl_up_sync(0xffffffffu, q.w, d, W), __shfl_up_sync(0xffffffffu, q.x, d, W),
+                __shfl_up_sync(0xffffffffu, q.y, d, W), __shfl_up_sync(0xffffffffu, q.z, d, W)};
 }
+template <int W>
 __device__ __forceinline__ Vec3 shfl_up(const Vec3& v, int d) {
-    return v3(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d),
-              __shfl_up_sync(0xffffffffu, v.z, d));
+    return v3(__shfl_up_sync(0xffffffffu, v.x, d, W), __shfl_up_sync(0xffffffffu, v.y, d, W),
+              __shfl_up_sync(0xffffffffu, v.z, d, W));
 }
+template <int W>
 __device__ __forceinline__ Quat shfl_idx(const Quat& q, int src) {
-    return Quat{__shfl_sync(0xffffffffu, q.w, src), __shfl_sync(0xffffffffu, q.x, src),
-                __shfl_sync(0xffffffffu, q.y, src), __shfl_sync(0xffffffffu, q.z, src)};
+    return Quat{__shfl_sync(0xffffffffu, q.w, src, W), __shfl_sync(0xffffffffu, q.x, src, W),
+                __shfl_sync(0xffffffffu, q.y, src, W), __shfl_sync(0xffffffffu, q.z, src, W)};
 }
+template <int W>
 __device__ __forceinline__ Vec3 shfl_idx(const Vec3& v, int src) {
-    return v3(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
-              __shfl_sync(0xffffffffu, v.z, src));
+    return v3(__shfl_sync(0xffffffffu, v.x, src, W), __shfl_sync(0xffffffffu, v.y, src, W),
+              __shfl_sync(0xffffffffu, v.z, src, W));
 }
-// Inclusive prefix sum over the lanes (Hillis-Steele).
-__device__ __forceinline__ Vec3 warp_scan_add(Vec3 x, int lane) {
+// Sum over a segment of W lanes (every lane of the segment gets it).
+template <int W>
+__device__ __forceinline__ float seg_sum(float x) {
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const Vec3 t = shfl_up(x, d);
-        if (lane >= d) x = v3(t.x + x.x, t.y + x.y, t.z + x.z);
+    for (int o = W / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+// Inclusive prefix sum over the lanes of a segment (Hillis-Steele).
+template <int W>
+__device__ __forceinline__ Vec3 seg_scan_add(Vec3 x, int sub) {
+#pragma unroll
+    for (int d = 1; d < W; d <<= 1) {
+        const Vec3 t = shfl_up<W>(x, d);
+        if (sub >= d) x = v3(t.x + x.x, t.y + x.y, t.z + x.z);
     }
     return x;
 }
-// Inclusive ordered product x_0 (x) x_1 (x) ... (x) x_lane: at every round the
+// Inclusive ordered product x_0 (x) x_1 (x) ... (x) x_sub over a segment: at every round the
 // partial product of the earlier lanes multiplies from the left.
-__device__ __forceinline__ Quat warp_scan_qmul(Quat x, int lane) {
+template <int W>
+__device__ __forceinline__ Quat seg_scan_qmul(Quat x, int sub) {
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const Quat t = shfl_up(x, d);
-        if (lane >= d) x = qmul(t, x);
+    for (int d = 1; d < W; d <<= 1) {
+        const Quat t = shfl_up<W>(x, d);
+        if (sub >= d) x = qmul(t, x);
     }
     return x;
 }
@@ -64,9 +79,9 @@ __global__ void noise_words_kernel(StepParams P, const uint32_t* __restrict__ st
 }
 
 // ------------------------------------------------------------------ (a) + (b) noise and rollouts
-// One warp per rollout; the horizon runs across the lanes in chunks of
-// 32 x kSteps steps, lane l owning the kSteps consecutive steps
-// h = c0 + kSteps l + j.  For each of its steps a lane draws the noise
+// One segment of kLanes lanes per rollout (32 / kLanes rollouts per warp); the horizon runs
+// across the segment's lanes in chunks of kLanes x kSteps steps, lane l of the segment owning
+// the kSteps consecutive steps h = c0 + kSteps l + j.  For each of its steps a lane draws the noise
 // (Philox4x32-10 block (k, h, step, drone) -> four normals -> delta u,
 // Sec. IV-A, Eq. 5), stores it, clips U*_h + delta and adds the control cost.
 // With the body rate held over a step (dw/dt = 0) the RK4 attitude update is
@@ -78,15 +93,18 @@ __global__ void noise_words_kernel(StepParams P, const uint32_t* __restrict__ st
 // offsets V_j = sum_{i<j} dv_i and position offsets L_j relative to the
 // segment's start, with
 //   v_{h+1} = v_h + dt/6 (a1 + 2 a2 + 2 a3 + a4),  p_{h+1} = p_h + dt v_h + dt^2/6 (a1 + a2 + a3),
-// so p after j + 1 steps of the segment = p_s + (j + 1) dt v_s + L_j.  Two more
-// scans give every segment's v_s and p_s.  The serial chain of H dependent RK4
-// steps becomes 5 shuffle rounds per chunk.  Stores: one float4 per step,
+// so p after j + 1 steps of the lane's steps = p_s + (j + 1) dt v_s + L_j.  Two more
+// scans give every lane's v_s and p_s.  The serial chain of H dependent RK4 steps becomes
+// log2(kLanes) shuffle rounds per chunk; with 16 lanes x 4 steps (H > 32) a warp serves two
+// rollouts, so the scans' rounds are shared and fewer lanes idle at H = 50 than with one
+// 32-lane rollout per warp (about half the warp instructions per rollout).  Stores: one float4 per step,
 // contiguous across the warp in the [K][H] arrays.  In analytic mode the frame
 // SDF of every gate and the collision hinge are evaluated at every p_{h+1}.
 constexpr int kRollWarps = 4;
-constexpr int kSteps = 2;                      // consecutive horizon steps per lane
 
+template <int kLanes, int kSteps>
 __global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, StepBuffers B, int analytic) {
+    static_assert(kLanes == 16 || kLanes == 32, "a rollout's lanes are a half warp or a warp");
     extern __shared__ float4 sU[];                 // [H]
     __shared__ float sPose[kMaxGates * 8];
     pdl_trigger();
@@ -95,8 +113,12 @@ __global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, 
     for (int i = threadIdx.x; i < P.G * 8; i += blockDim.x) sPose[i] = B.poses[i];
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int k = blockIdx.x * kRollWarps + (threadIdx.x >> 5);
-    if (k >= P.K) return;                          // whole warps only
+    const int sub = lane & (kLanes - 1);          // lane within the rollout's segment
+    const int k_first = (blockIdx.x * kRollWarps + (threadIdx.x >> 5)) * (32 / kLanes);
+    if (k_first >= P.K) return;                    // whole warps only
+    // a segment past the last rollout (odd K) mirrors the last one and stores nothing
+    const bool valid = k_first + lane / kLanes < P.K;
+    const int k = valid ? k_first + lane / kLanes : P.K - 1;
     const int K = P.K, H = P.H;
     const uint32_t st = B.step[0];
 
@@ -120,8 +142,8 @@ __global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, 
     float jctl = 0.f, jcol = 0.f, jvis = 0.f;
     float4* noise_k = B.noise + static_cast<size_t>(k) * H;
     float4* pos_k = B.pos + static_cast<size_t>(k) * H;
-    for (int c0 = 0; c0 < H; c0 += 32 * kSteps) {
-        const int h0 = c0 + kSteps * lane;
+    for (int c0 = 0; c0 < H; c0 += kLanes * kSteps) {
+        const int h0 = c0 + kSteps * sub;
         // pass A: noise, clipped controls, control cost, the segment's attitude increment
         float4 u[kSteps];
         Quat N[kSteps];
@@ -133,7 +155,7 @@ __global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, 
             u[j] = make_float4(uh, 0.f, 0.f, 0.f);       // steps past H: no rotation, no increments
             if (h < H) {
                 const float4 d = noise_from_block(P, noise_block(P, k, h, st));
-                noise_k[h] = d;
+                if (valid) noise_k[h] = d;
                 const float4 un = sU[h];
                 u[j] = clip_control(P, make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w));
                 const float e0 = u[j].x - uh;
@@ -146,9 +168,9 @@ __global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, 
             N[j] = qnormalize(Quat{an, bn * u[j].y, bn * u[j].z, bn * u[j].w});
             seg = (j == 0) ? N[0] : qmul(seg, N[j]);
         }
-        const Quat S = warp_scan_qmul(seg, lane);
-        Quat E = shfl_up(S, 1);
-        if (lane == 0) E = Quat{1.f, 0.f, 0.f, 0.f};
+        const Quat S = seg_scan_qmul<kLanes>(seg, sub);
+        Quat E = shfl_up<kLanes>(S, 1);
+        if (sub == 0) E = Quat{1.f, 0.f, 0.f, 0.f};
         // attitude at the segment's start (the first step uses the state's attitude as given,
         // as the sequential form does)
         Quat q = (h0 == 0) ? qc : qnormalize(qmul(qc, E));
@@ -188,15 +210,15 @@ __global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, 
             Qa[j] = q;
         }
         // segment start velocities and positions: exclusive scans of the segments' totals
-        const Vec3 Sv = warp_scan_add(V, lane);
-        Vec3 ev = shfl_up(Sv, 1);
-        if (lane == 0) ev = v3(0.f, 0.f, 0.f);
+        const Vec3 Sv = seg_scan_add<kLanes>(V, sub);
+        Vec3 ev = shfl_up<kLanes>(Sv, 1);
+        if (sub == 0) ev = v3(0.f, 0.f, 0.f);
         const Vec3 vs = v3(vc.x + ev.x, vc.y + ev.y, vc.z + ev.z);
         const float tn = dt * static_cast<float>(nact);
         const Vec3 dP = v3(tn * vs.x + Lacc.x, tn * vs.y + Lacc.y, tn * vs.z + Lacc.z);
-        const Vec3 Sp = warp_scan_add(dP, lane);
-        Vec3 ep = shfl_up(Sp, 1);
-        if (lane == 0) ep = v3(0.f, 0.f, 0.f);
+        const Vec3 Sp = seg_scan_add<kLanes>(dP, sub);
+        Vec3 ep = shfl_up<kLanes>(Sp, 1);
+        if (sub == 0) ep = v3(0.f, 0.f, 0.f);
         const Vec3 ps = v3(pc.x + ep.x, pc.y + ep.y, pc.z + ep.z);
 
         // pass C: positions p_{h+1} = p_s + (j + 1) dt v_s + L_j
@@ -206,7 +228,7 @@ __global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, 
             if (h < H) {
                 const float tj = dt * static_cast<float>(j + 1);
                 const Vec3 p = v3(ps.x + tj * vs.x + L[j].x, ps.y + tj * vs.y + L[j].y, ps.z + tj * vs.z + L[j].z);
-                pos_k[h] = make_float4(p.x, p.y, p.z, 0.f);
+                if (valid) pos_k[h] = make_float4(p.x, p.y, p.z, 0.f);
                 if (P.paper) {
                     if (tgt >= 0) {
                         jvis += misalignment(Qa[j], p, wp);
@@ -223,16 +245,16 @@ __global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, 
             }
         }
         // state at the end of the chunk
-        const Vec3 pe = shfl_idx(Sp, 31);
+        const Vec3 pe = shfl_idx<kLanes>(Sp, kLanes - 1);
         pc = v3(pc.x + pe.x, pc.y + pe.y, pc.z + pe.z);
-        const Vec3 sv = shfl_idx(Sv, 31);
+        const Vec3 sv = shfl_idx<kLanes>(Sv, kLanes - 1);
         vc = v3(vc.x + sv.x, vc.y + sv.y, vc.z + sv.z);
-        qc = qnormalize(qmul(qc, shfl_idx(S, 31)));
+        qc = qnormalize(qmul(qc, shfl_idx<kLanes>(S, kLanes - 1)));
     }
-    jctl = warp_sum(jctl);
-    jcol = warp_sum(jcol);
-    jvis = warp_sum(jvis);
-    if (lane == 0) {
+    jctl = seg_sum<kLanes>(jctl);
+    jcol = seg_sum<kLanes>(jcol);
+    jvis = seg_sum<kLanes>(jvis);
+    if (sub == 0 && valid) {
         if (P.paper) {
             // Eq. 6 telescoped: sum_k |p_{k+1} - wp|^2 - |p_k - wp|^2 = |p_H - wp|^2 - |p_0 - wp|^2
             const float dHx = pc.x - wp.x, dHy = pc.y - wp.y, dHz = pc.z - wp.z;
@@ -330,7 +352,8 @@ __global__ void __launch_bounds__(kRotorThreads) rollout_rotor_kernel(StepParams
 //     paper's form), rho_b = min of the block's J_k,
 //     e_k = exp(-(J_k - rho_b) / lambda), eta_b = sum of the block's e_k;
 //  2. S_b[h] = sum_{k in b} e_k clip(U*_h + delta_{k,h});
-//  3. grid barrier (the kernel is a cooperative launch, so all its blocks are resident);
+//  3. grid barrier (the kernel is a cooperative launch, so all its blocks are resident; an
+//     arrival counter with release / acquire ordering);
 //  4. every block forms rho = min_b rho_b, F_b = exp(-(rho_b - rho) / lambda) and
 //     eta = sum_b F_b eta_b from the same data in the same order (bit-identical in every
 //     block), writes its own weights w_k = e_k F_b / eta (Eq. 5 with max subtraction) and
@@ -349,6 +372,17 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
     return t;
+}
+// GPU-scope release add (returns the old value) and acquire load of the grid barrier's counter
+__device__ __forceinline__ unsigned long long atom_add_release_gpu(unsigned long long* p, unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.release.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 constexpr int kCuHChunk = 64;                      // horizon steps per pass of the weighted sums
 constexpr int kCuBatch = 4;                        // rollouts per warp whose loads are in flight together
@@ -498,20 +532,23 @@ __global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, S
         __syncthreads();
     }
 
-    // 3. grid barrier (cooperative launch: every block is resident; the wait is bounded)
+    // 3. grid barrier (cooperative launch: every block is resident; the wait is bounded).  The
+    //    arrival counter (64 bits, ticket words 12-13) only grows: after the block's writes
+    //    (the __syncthreads above), one thread adds 1 with release semantics; the launch's
+    //    target is the next multiple of the grid size above the count it saw, and it polls
+    //    with acquire loads.  A launch that timed out leaves the count off a multiple of the
+    //    grid: the host zeroes the ticket words together with the error word.  Ticket word 31
+    //    (0 unless set by mppi_debug_inject_timeout) moves the target that many grids further,
+    //    so that every block's wait runs out: the test of the timeout path, with no fault.
     if (threadIdx.x == 0) {
-        volatile unsigned* gen_p = B.tickets + 10;
-        const unsigned gen = *gen_p;
-        __threadfence();
-        const unsigned tk = atomicAdd(&B.tickets[9], 1u);
+        unsigned long long* ctr = reinterpret_cast<unsigned long long*>(B.tickets + 12);
+        const unsigned long long skew = B.tickets[31];
+        const unsigned long long nbl = gridDim.x;
+        const unsigned long long target = (atom_add_release_gpu(ctr, 1ull) / nbl + 1ull + skew) * nbl;
         bool ok = true;
-        if (tk == gridDim.x - 1) {
-            B.tickets[9] = 0u;
-            __threadfence();
-            atomicAdd(&B.tickets[10], 1u);
-        } else {
+        if (ld_acquire_gpu(ctr) < target) {
             const uint64_t t0 = global_timer_ns();
-            while (*gen_p == gen) {
+            while (ld_acquire_gpu(ctr) < target) {
                 if (global_timer_ns() - t0 > kGridWaitLimitNs) {
                     atomicExch(B.err, kDevErrTimeout);
                     ok = false;
@@ -519,7 +556,6 @@ __global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, S
                 }
             }
         }
-        __threadfence();
         is_last = ok ? 1 : 0;
     }
     __syncthreads();
@@ -561,8 +597,8 @@ __global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, S
         B.w[k0 + i] = wk;
         if (B.out_w) B.out_w[k0 + i] = wk;
     }
-    // U*_new[h] for h = blockIdx.x, blockIdx.x + nb, ...: thread t < nb loads block t's partial,
-    // then a fixed-order tree in shared memory
+    // U*_new[h] for h = blockIdx.x, blockIdx.x + nb, ...: thread t < nb loads block t's partial;
+    // fixed-order sums: xor shuffles within each warp, then the warps' sums in warp order
     float4* sU = reinterpret_cast<float4*>(sRed);
     const float uh = P.u_hover;
     for (int h = blockIdx.x; h < H; h += nb) {
@@ -572,18 +608,19 @@ __global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, S
             const float f = sF[threadIdx.x] / eta;
             t = make_float4(f * sb.x, f * sb.y, f * sb.z, f * sb.w);
         }
-        sU[threadIdx.x] = t;
+        t.x = warp_sum(t.x);
+        t.y = warp_sum(t.y);
+        t.z = warp_sum(t.z);
+        t.w = warp_sum(t.w);
+        if (lane == 0) sU[wid] = t;
         __syncthreads();
-#pragma unroll
-        for (int o = kCuThreads / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o) {
-                const float4 a = sU[threadIdx.x], c = sU[threadIdx.x + o];
-                sU[threadIdx.x] = make_float4(a.x + c.x, a.y + c.y, a.z + c.z, a.w + c.w);
-            }
-            __syncthreads();
-        }
         if (threadIdx.x == 0) {
-            const float4 u = sU[0];
+            float4 u = sU[0];
+#pragma unroll
+            for (int i = 1; i < kCuWarps; ++i) {
+                const float4 o = sU[i];
+                u = make_float4(u.x + o.x, u.y + o.y, u.z + o.z, u.w + o.w);
+            }
             B.unew[h] = u;
             if (B.out_U) B.out_U[h] = u;
             if (h >= 1) B.nominal[h - 1] = u;                     // the warm start, shifted by one
@@ -648,8 +685,11 @@ cudaError_t launch_rollout(const StepParams& P, const StepBuffers& B, int analyt
     if (P.rotor)
         return launch_dependent(false, rollout_rotor_kernel, dim3((P.K + kRotorThreads - 1) / kRotorThreads),
                                 dim3(kRotorThreads), P.H * sizeof(float4), s, P, B, analytic);
-    return launch_dependent(false, rollout_kernel, dim3((P.K + kRollWarps - 1) / kRollWarps), dim3(kRollWarps * 32),
-                            P.H * sizeof(float4), s, P, B, analytic);
+    // two rollouts per warp: 16 lanes x 4 steps (or x 2 steps when the horizon fits in 32)
+    const int per_block = kRollWarps * 2;
+    const dim3 grid((P.K + per_block - 1) / per_block), block(kRollWarps * 32);
+    if (P.H <= 32) return launch_dependent(false, rollout_kernel<16, 2>, grid, block, P.H * sizeof(float4), s, P, B, analytic);
+    return launch_dependent(false, rollout_kernel<16, 4>, grid, block, P.H * sizeof(float4), s, P, B, analytic);
 }
 
 int update_rollouts_per_block(int K) {

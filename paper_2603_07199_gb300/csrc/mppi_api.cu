@@ -647,6 +647,14 @@ int mppi_set_sdf_weights(mppi_ctx* c, const float* const* layers, int n_layers, 
     return MPPI_OK;
 }
 
+int mppi_debug_inject_timeout(mppi_ctx* c) {
+    if (!c) return fail(nullptr, MPPI_E_INVALID, "ctx is NULL");
+    const unsigned one = 1u;
+    CUDA_TRY(c, cudaMemcpyAsync(c->B.tickets + 31, &one, sizeof(unsigned), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return MPPI_OK;
+}
+
 int mppi_step(mppi_ctx* c, const float* state, const float* gate_poses, const float* latents, const float* nominal,
               float* new_controls, float* weights, float* costs) {
     if (!c) return fail(nullptr, MPPI_E_INVALID, "ctx is NULL");
