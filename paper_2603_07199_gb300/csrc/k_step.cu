@@ -685,11 +685,18 @@ cudaError_t launch_rollout(const StepParams& P, const StepBuffers& B, int analyt
     if (P.rotor)
         return launch_dependent(false, rollout_rotor_kernel, dim3((P.K + kRotorThreads - 1) / kRotorThreads),
                                 dim3(kRotorThreads), P.H * sizeof(float4), s, P, B, analytic);
-    // two rollouts per warp: 16 lanes x 4 steps (or x 2 steps when the horizon fits in 32)
-    const int per_block = kRollWarps * 2;
-    const dim3 grid((P.K + per_block - 1) / per_block), block(kRollWarps * 32);
-    if (P.H <= 32) return launch_dependent(false, rollout_kernel<16, 2>, grid, block, P.H * sizeof(float4), s, P, B, analytic);
-    return launch_dependent(false, rollout_kernel<16, 4>, grid, block, P.H * sizeof(float4), s, P, B, analytic);
+    // two rollouts per warp (16 lanes x 4 steps, or x 2 when the horizon fits in 32), except for
+    // a long horizon at small K: there a warp per rollout (32 lanes x 2 steps) keeps more warps
+    // on each SM for the latency-bound scans (K = 4096, H = 50: the two forms are level; at
+    // K = 16384, H = 64 the half-warp form is 7 % faster)
+    const dim3 block(kRollWarps * 32);
+    const size_t smem = P.H * sizeof(float4);
+    if (P.H > 32 && P.K < 8192)
+        return launch_dependent(false, rollout_kernel<32, 2>, dim3((P.K + kRollWarps - 1) / kRollWarps), block, smem, s,
+                                P, B, analytic);
+    const dim3 grid((P.K + 2 * kRollWarps - 1) / (2 * kRollWarps));
+    if (P.H <= 32) return launch_dependent(false, rollout_kernel<16, 2>, grid, block, smem, s, P, B, analytic);
+    return launch_dependent(false, rollout_kernel<16, 4>, grid, block, smem, s, P, B, analytic);
 }
 
 int update_rollouts_per_block(int K) {
