@@ -128,6 +128,81 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+class NvmlClockSampler:
+    """SM clock, maximum SM clock and clock-event reasons read in-process through the driver's
+    NVML library (read-only queries; no setting is changed) every `period_s` on a background
+    thread, so that a timed region of a few milliseconds still holds several samples."""
+    REASONS = ((0x4, "sw_power_cap"), (0x8, "hw_slowdown"), (0x20, "sw_thermal_slowdown"),
+               (0x40, "hw_thermal_slowdown"), (0x80, "hw_power_brake_slowdown"))
+
+    def __init__(self, uuid, period_s=0.001):
+        import ctypes
+        self.ct = ctypes
+        self.uuid, self.period = uuid, period_s
+        self.nvml = None
+        self.samples = []
+        self.stop_flag = threading.Event()
+        self.thread = None
+
+    def start(self):
+        ct = self.ct
+        try:
+            nvml = ct.CDLL("libnvidia-ml.so.1")
+            if nvml.nvmlInit_v2() != 0:
+                return False
+            h = ct.c_void_p()
+            # by UUID only: NVML numbers all of the machine's GPUs, whatever this process sees
+            if not self.uuid or nvml.nvmlDeviceGetHandleByUUID(("GPU-" + self.uuid).encode(), ct.byref(h)) != 0:
+                nvml.nvmlShutdown()
+                return False
+            get_reasons = getattr(nvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nvml.nvmlDeviceGetCurrentClocksThrottleReasons
+        except (OSError, AttributeError):
+            return False
+        self.nvml, self.h, self.get_reasons = nvml, h, get_reasons
+        smax = ct.c_uint()
+        self.sm_max = float(smax.value) if nvml.nvmlDeviceGetMaxClockInfo(h, 1, ct.byref(smax)) == 0 else None
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+        return True
+
+    def _run(self):
+        ct, nvml, h = self.ct, self.nvml, self.h
+        mhz, reasons = ct.c_uint(), ct.c_ulonglong()
+        while not self.stop_flag.is_set():
+            if nvml.nvmlDeviceGetClockInfo(h, 1, ct.byref(mhz)) == 0 and self.get_reasons(h, ct.byref(reasons)) == 0:
+                self.samples.append((float(mhz.value), int(reasons.value)))
+            time.sleep(self.period)
+
+    def stop(self):
+        if self.nvml is None:
+            return None
+        self.stop_flag.set()
+        self.thread.join(timeout=2)
+        self.nvml.nvmlShutdown()
+        if not self.samples:
+            return None
+        sm = [m for m, _ in self.samples]
+        seen = sorted({name for _, r in self.samples for bit, name in self.REASONS if r & bit})
+        return {"sm_mhz": float(np.median(sm)), "sm_min_mhz": float(min(sm)),
+                "sm_max_mhz": self.sm_max if self.sm_max is not None else float(max(sm)), "reasons": seen,
+                "samples": len(sm), "source": f"NVML, every {self.period * 1e3:g} ms during the timed region"}
+
+
+def clock_sampler(torch, dev, local):
+    """An NVML sampler of this process's GPU when the driver library loads, else nvidia-smi."""
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except (AttributeError, RuntimeError):
+        uuid = None
+    s = NvmlClockSampler(uuid)
+    if s.start():
+        return s
+    s = ClockSampler(local)
+    s.start()
+    return s
+
+
 # ------------------------------------------------------------------ our arm
 def make_ctx(B, wl, mode, stream, drone_id):
     prm = wl["params"]
@@ -655,11 +730,10 @@ def run_ours(args):
 
     ctx = make_ctx(B, wl, "bf16", stream, drone_id=rank)
     per_launch = B.mppi_kernels_per_step(ctx)
-    sampler = ClockSampler(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    sampler.start()
+    sampler = clock_sampler(torch, dev, local)
     t_wall = time.perf_counter()
     ms = device_loop(torch, B, ctx, wl, args.steps, max(3, args.warmup), flush, dev)
     t_wall = time.perf_counter() - t_wall
