@@ -57,7 +57,8 @@ struct mppi_ctx {
     // completion of the last step enqueued by the serving path
     cudaEvent_t done = nullptr;
     // the step's kernels as one CUDA graph, re-captured when a launch argument changes
-    cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gexec = nullptr;          // the step's kernels
+    cudaGraphExec_t gexec_state = nullptr;    // the same after a copy of the pinned state slot to B.state
     bool graph_dirty = true;
     // timing
     cudaEvent_t ev[8] = {};
@@ -277,36 +278,50 @@ int enqueue_kernels(mppi_ctx* c) {
     return MPPI_OK;
 }
 
-// Launch the step: replay the captured graph, capturing it first when the
-// launch arguments changed.  When the caller's stream is itself being
-// captured, the kernels are enqueued directly into the caller's capture.
-int launch_step(mppi_ctx* c) {
+// Launch the step: replay the captured graph -- with state_copy, the one whose first node
+// copies the pinned state slot (h_in) to the device state, so that a step from a host state
+// is one submission -- capturing it first when the launch arguments changed.  When the
+// caller's stream is itself being captured, the copy and the kernels are enqueued directly
+// into the caller's capture.
+int launch_step(mppi_ctx* c, bool state_copy) {
+    const size_t state_bytes = state_dim(c->cfg) * sizeof(float);
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CUDA_TRY(c, cudaStreamIsCapturing(c->stream, &cs));
-    if (cs != cudaStreamCaptureStatusNone) return enqueue_kernels(c);
-    if (c->gexec == nullptr || c->graph_dirty) {
-        if (c->gexec) {
-            cudaGraphExecDestroy(c->gexec);
-            c->gexec = nullptr;
-        }
-        CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        const int rc = enqueue_kernels(c);
-        cudaGraph_t g = nullptr;
-        const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-        if (rc != MPPI_OK) {
-            if (g) cudaGraphDestroy(g);
-            return rc;
-        }
-        if (e != cudaSuccess) return fail(c, MPPI_E_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
-        const cudaError_t ei = cudaGraphInstantiate(&c->gexec, g, 0);
-        cudaGraphDestroy(g);
-        if (ei != cudaSuccess) {
-            c->gexec = nullptr;
-            return fail(c, MPPI_E_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+    if (cs != cudaStreamCaptureStatusNone) {
+        if (state_copy)
+            CUDA_TRY(c, cudaMemcpyAsync(c->B.state, c->h_in, state_bytes, cudaMemcpyHostToDevice, c->stream));
+        return enqueue_kernels(c);
+    }
+    if (c->graph_dirty) {
+        for (cudaGraphExec_t* e : {&c->gexec, &c->gexec_state}) {
+            if (*e) cudaGraphExecDestroy(*e);
+            *e = nullptr;
         }
         c->graph_dirty = false;
     }
-    CUDA_TRY(c, cudaGraphLaunch(c->gexec, c->stream));
+    cudaGraphExec_t& exec = state_copy ? c->gexec_state : c->gexec;
+    if (exec == nullptr) {
+        CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t ec = state_copy ? cudaMemcpyAsync(c->B.state, c->h_in, state_bytes,
+                                                            cudaMemcpyHostToDevice, c->stream)
+                                          : cudaSuccess;
+        const int rc = ec == cudaSuccess ? enqueue_kernels(c) : MPPI_OK;
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (ec != cudaSuccess || rc != MPPI_OK) {
+            if (g) cudaGraphDestroy(g);
+            return ec != cudaSuccess ? fail(c, MPPI_E_CUDA, "state copy capture failed: %s", cudaGetErrorString(ec))
+                                     : rc;
+        }
+        if (e != cudaSuccess) return fail(c, MPPI_E_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
+        const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            exec = nullptr;
+            return fail(c, MPPI_E_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+        }
+    }
+    CUDA_TRY(c, cudaGraphLaunch(exec, c->stream));
     return MPPI_OK;
 }
 
@@ -391,6 +406,7 @@ void mppi_destroy(mppi_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->gexec_state) cudaGraphExecDestroy(c->gexec_state);
     for (void* p : c->allocations) cudaFree(p);
     if (c->h_in) cudaFreeHost(c->h_in);
     if (c->h_out) cudaFreeHost(c->h_out);
@@ -685,11 +701,7 @@ int mppi_step(mppi_ctx* c, const float* state, const float* gate_poses, const fl
     int rc = check_ready(c);
     if (rc != MPPI_OK) return rc;
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // staging buffers are free
-    if (state) {
-        std::memcpy(c->h_in, state, state_dim(c->cfg) * sizeof(float));
-        CUDA_TRY(c, cudaMemcpyAsync(c->B.state, c->h_in, state_dim(c->cfg) * sizeof(float), cudaMemcpyHostToDevice,
-                                    c->stream));
-    }
+    if (state) std::memcpy(c->h_in, state, state_dim(c->cfg) * sizeof(float));   // copied by the step's graph
     if (nominal) {
         std::memcpy(c->h_in + kStateSlot, nominal, static_cast<size_t>(H) * 4 * sizeof(float));
         CUDA_TRY(c, cudaMemcpyAsync(c->B.nominal, c->h_in + kStateSlot, H * sizeof(float4), cudaMemcpyHostToDevice,
@@ -704,7 +716,7 @@ int mppi_step(mppi_ctx* c, const float* state, const float* gate_poses, const fl
     *herr = -1;
     set_outputs(c, reinterpret_cast<float4*>(dho), weights ? dho + H * 4 : nullptr, costs ? dho + H * 4 + K : nullptr,
                 reinterpret_cast<int*>(dho + H * 4 + 2 * K));
-    rc = launch_step(c);
+    rc = launch_step(c, state != nullptr);
     if (rc != MPPI_OK) return rc;
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     ++c->step_count;
@@ -743,7 +755,7 @@ int mppi_step_async(mppi_ctx* c, const float* d_state, const float* d_gate_poses
     // the step's last kernel writes the caller's buffers itself; a change of buffers is a
     // change of launch arguments (the step graph is captured again)
     set_outputs(c, reinterpret_cast<float4*>(d_new_controls), d_weights, d_costs, nullptr);
-    rc = launch_step(c);
+    rc = launch_step(c, false);
     if (rc != MPPI_OK) return rc;
     ++c->step_count;
     return MPPI_OK;
@@ -886,7 +898,6 @@ int ctx_enqueue_host_step(mppi_ctx* c, const float* state, int n_gates, const fl
     }
     if (c->n_gates != n_gates) c->graph_dirty = true;
     c->n_gates = n_gates;
-    CUDA_TRY(c, cudaMemcpyAsync(c->B.state, hs, state_dim(c->cfg) * sizeof(float), cudaMemcpyHostToDevice, c->stream));
     if (n_gates > 0) {
         CUDA_TRY(c, cudaMemcpyAsync(c->B.poses, hp, n_gates * 8 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
         if (latents) {
@@ -905,7 +916,7 @@ int ctx_enqueue_host_step(mppi_ctx* c, const float* state, int n_gates, const fl
     *reinterpret_cast<volatile int*>(c->h_out + H * 4 + 2 * c->cfg.K) = -1;
     set_outputs(c, reinterpret_cast<float4*>(c->d_hout), nullptr, nullptr,
                 reinterpret_cast<int*>(c->d_hout + H * 4 + 2 * c->cfg.K));
-    rc = launch_step(c);
+    rc = launch_step(c, true);                     // the graph copies the staged state first
     if (rc != MPPI_OK) return rc;
     CUDA_TRY(c, cudaEventRecord(c->done, c->stream));
     ++c->step_count;
