@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-seconds", type=float, default=1.0)
     ap.add_argument("--distill-steps", type=int, default=0)
+    ap.add_argument("--distill-schedule", default="constant", choices=["constant", "cosine"],
+                    help="Adam learning rate of the distillation: constant 1e-3, or 1e-3 cosine-decayed over the steps")
     ap.add_argument("--four-gate-steps", type=int, default=20)
     ap.add_argument("--render-steps", type=int, default=20)
     ap.add_argument("--vision-steps", type=int, default=20)
@@ -377,7 +379,7 @@ def serving_leg(torch, B, dev, duration_s, n_drones=64, rate_hz=100.0):
                            "solve_ms_by_config": {f"K{k}_H{h}_G{g}": t for (k, h, g), t in t32.items()}}}
 
 
-def distill_leg(torch, B, dev, steps):
+def distill_leg(torch, B, dev, steps, schedule="constant"):
     """Distil the exact frame SDF into the Gate-SDF MLP (2^21 points, batch 65536, Adam 1e-3,
     L1 + 0.1 Eikonal), then run the two-gate workload with the learned, the exact and the
     untrained SDF.  The learned SDF is used only when its held-out error stays within 5 mm
@@ -392,7 +394,16 @@ def distill_leg(torch, B, dev, steps):
     before = B.mppi_train_evaluate(tr)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    loss = B.mppi_train_step(tr, steps)
+    if schedule == "cosine":
+        # 1e-3 at the start, decayed by a half cosine over the run, set once per 500-step chunk
+        done, chunk, loss = 0, 500, None
+        while done < steps:
+            n = min(chunk, steps - done)
+            B.mppi_train_set_lr(tr, cfg.lr * 0.5 * (1.0 + np.cos(np.pi * (done + 0.5 * n) / steps)))
+            loss = B.mppi_train_step(tr, n)
+            done += n
+    else:
+        loss = B.mppi_train_step(tr, steps)
     train_s = time.perf_counter() - t0
     after = B.mppi_train_evaluate(tr)
     learned = [np.zeros_like(a) for a in init]
@@ -434,7 +445,7 @@ def distill_leg(torch, B, dev, steps):
         B.mppi_destroy(ctx)
     div = {n: float(np.max(np.abs(outs[n][0] - outs["exact"][0]))) for n in ("learned", "untrained")}
     pos_div = {n: float(np.linalg.norm(outs[n][1][:3] - outs["exact"][1][:3])) for n in ("learned", "untrained")}
-    return {"steps": steps, "batch": cfg.batch, "points": cfg.n_points, "train_s": train_s,
+    return {"steps": steps, "schedule": schedule, "batch": cfg.batch, "points": cfg.n_points, "train_s": train_s,
             "steps_per_s": steps / train_s if train_s > 0 else None, "final_loss": loss,
             "holdout_before_mm": {k: v * 1e3 for k, v in before.items()},
             "holdout_after_mm": {k: v * 1e3 for k, v in after.items()},
@@ -776,7 +787,7 @@ def run_ours(args):
               if args.render_steps > 0 else None)
     vision = vision_leg(torch, B, stream, flush, dev, args.vision_steps, rank) if args.vision_steps > 0 else None
     serving = serving_leg(torch, B, dev, args.serving_seconds) if args.serving_seconds > 0 else None
-    distill = distill_leg(torch, B, dev, args.distill_steps) if args.distill_steps > 0 else None
+    distill = distill_leg(torch, B, dev, args.distill_steps, args.distill_schedule) if args.distill_steps > 0 else None
 
     if rank != 0:
         if world > 1:

@@ -572,6 +572,9 @@ int mppi_train_create(const mppi_train_config* cfg, const float* const* init_lay
                       mppi_trainer** out);
 void mppi_train_destroy(mppi_trainer* trainer);
 const char* mppi_train_last_error(const mppi_trainer* trainer);
+/* Learning rate of the following steps (> 0, finite): a caller's schedule sets it between calls of
+ * mppi_train_step.  Errors: MPPI_E_INVALID. */
+int mppi_train_set_lr(mppi_trainer* trainer, float lr);
 /* Run n_steps Adam steps over consecutive batches of the training set; *last_loss (nullable) = last batch's loss. */
 int mppi_train_step(mppi_trainer* trainer, int n_steps, float* last_loss);
 /*

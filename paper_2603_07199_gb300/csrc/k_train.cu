@@ -696,6 +696,13 @@ int mppi_train_create(const mppi_train_config* cfg, const float* const* init_lay
     return MPPI_OK;
 }
 
+int mppi_train_set_lr(mppi_trainer* t, float lr) {
+    if (!t) return tfail(nullptr, MPPI_E_INVALID, "trainer is NULL");
+    if (!(lr > 0.f) || !std::isfinite(lr)) return tfail(t, MPPI_E_INVALID, "lr must be finite and > 0");
+    t->cfg.lr = lr;
+    return MPPI_OK;
+}
+
 int mppi_train_step(mppi_trainer* t, int n_steps, float* last_loss) {
     if (!t || n_steps < 0) return tfail(t, MPPI_E_INVALID, "bad arguments");
     const mppi_train_config& c = t->cfg;

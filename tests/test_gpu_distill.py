@@ -95,6 +95,31 @@ def test_adam_step_matches_the_oracle(lib):
     np.testing.assert_allclose(got, want, rtol=1e-6, atol=1e-9)
 
 
+def test_set_lr_takes_effect_on_the_next_step(lib):
+    """mppi_train_set_lr: the next Adam step uses the new rate (the oracle's step at 2.5e-4);
+    non-positive or non-finite rates are rejected."""
+    tr, layers, z0, cfg = _trainer(batch=512, n_points=512)
+    try:
+        pts = np.zeros(4 * 512, np.float32)
+        B.mppi_train_read_points(tr, 0, pts)
+        grads = np.zeros(B.mppi_train_num_params(), np.float32)
+        B.mppi_train_loss_grads(tr, pts.reshape(-1, 4), grads)
+        for bad in (0.0, -1e-3, float("nan"), float("inf")):
+            with pytest.raises(B.MppiError):
+                B.mppi_train_set_lr(tr, bad)
+        B.mppi_train_set_lr(tr, 2.5e-4)
+        B.mppi_train_step(tr, 1)
+        after = [np.zeros_like(a) for a in layers]
+        B.mppi_train_get_weights(tr, after)
+    finally:
+        B.mppi_train_destroy(tr)
+    theta0 = np.concatenate([a.ravel() for a in layers]).astype(np.float64)
+    want, _, _ = OD.adam_update(theta0, grads.astype(np.float64), 0.0, 0.0, t=1, lr=2.5e-4, b1=cfg.beta1,
+                                b2=cfg.beta2, eps=cfg.eps)
+    got = np.concatenate([a.ravel() for a in after]).astype(np.float64)
+    np.testing.assert_allclose(got, want, rtol=1e-6, atol=1e-9)
+
+
 def test_training_reduces_the_sdf_error(lib):
     """A few hundred Adam steps already cut the held-out error of the random network by a large factor."""
     tr, layers, z0, cfg = _trainer(batch=4096, n_points=1 << 16, n_holdout=8192, seed=11)
