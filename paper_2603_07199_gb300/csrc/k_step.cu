@@ -95,11 +95,12 @@ __global__ void noise_words_kernel(StepParams P, const uint32_t* __restrict__ st
 //   v_{h+1} = v_h + dt/6 (a1 + 2 a2 + 2 a3 + a4),  p_{h+1} = p_h + dt v_h + dt^2/6 (a1 + a2 + a3),
 // so p after j + 1 steps of the lane's steps = p_s + (j + 1) dt v_s + L_j.  Two more
 // scans give every lane's v_s and p_s.  The serial chain of H dependent RK4 steps becomes
-// log2(kLanes) shuffle rounds per chunk; with 16 lanes x 4 steps (H > 32) a warp serves two
-// rollouts, so the scans' rounds are shared and fewer lanes idle at H = 50 than with one
-// 32-lane rollout per warp (about half the warp instructions per rollout).  Stores: one float4 per step,
-// contiguous across the warp in the [K][H] arrays.  In analytic mode the frame
-// SDF of every gate and the collision hinge are evaluated at every p_{h+1}.
+// log2(kLanes) shuffle rounds per chunk; with 16 lanes x 4 steps a warp serves two rollouts,
+// so the scans' rounds are shared and fewer lanes idle at H = 50 than with one 32-lane
+// rollout per warp (17 % fewer warp instructions at K = 4096, H = 50; the launch picks the
+// form).  Stores: one float4 per step, contiguous across the rollout's lanes in the [K][H]
+// arrays.  In analytic mode the frame SDF of every gate and the collision hinge are
+// evaluated at every p_{h+1}.
 constexpr int kRollWarps = 4;
 
 template <int kLanes, int kSteps>
