@@ -281,6 +281,44 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 // Allow the next kernel in the stream to start launching (its prologue overlaps this kernel).
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// ---------------------------------------------------------------- grid barrier of a cooperative launch
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+// GPU-scope release add (returns the old value) and acquire load of a barrier's counter
+__device__ __forceinline__ unsigned long long atom_add_release_gpu(unsigned long long* p, unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.release.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+// Thread 0's half of a grid barrier over a counter that only grows (call after a
+// __syncthreads that follows the block's writes; broadcast the result through shared memory
+// and a second __syncthreads): one release add, the target is the next multiple of the grid
+// size (+ skew grids; 0 except in tests of the timeout path) above the count seen, acquire
+// polls bounded by limit_ns.  Returns false when the wait gave up (after setting *err).  A
+// launch that gave up leaves the count off a multiple of the grid: the host zeroes it.
+__device__ __forceinline__ bool grid_arrive_wait(unsigned long long* ctr, unsigned long long skew, int* err,
+                                                 uint64_t limit_ns) {
+    const unsigned long long nbl = gridDim.x;
+    const unsigned long long target = (atom_add_release_gpu(ctr, 1ull) / nbl + 1ull + skew) * nbl;
+    if (ld_acquire_gpu(ctr) >= target) return true;
+    const uint64_t t0 = global_timer_ns();
+    while (ld_acquire_gpu(ctr) < target) {
+        if (global_timer_ns() - t0 > limit_ns) {
+            atomicExch(err, kDevErrTimeout);
+            return false;
+        }
+    }
+    return true;
+}
+
 // ---------------------------------------------------------------- gate frame SDF
 // Exact signed distance to the square frame {|x| <= d, a_in <= max(|y|,|z|) <= a_out}.
 // The frame is symmetric in x, y and z, so the query is folded into the first

@@ -369,22 +369,7 @@ constexpr int kCuWarps = kCuThreads / 32;
 constexpr int kCuMaxBlocks = 128;
 constexpr uint64_t kGridWaitLimitNs = 2000000000ull;  // bound of the grid barrier's wait
 
-__device__ __forceinline__ uint64_t global_timer_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-// GPU-scope release add (returns the old value) and acquire load of the grid barrier's counter
-__device__ __forceinline__ unsigned long long atom_add_release_gpu(unsigned long long* p, unsigned long long v) {
-    unsigned long long old;
-    asm volatile("atom.release.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
-    return old;
-}
-__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
+
 constexpr int kCuHChunk = 64;                      // horizon steps per pass of the weighted sums
 constexpr int kCuBatch = 4;                        // rollouts per warp whose loads are in flight together
 
@@ -542,22 +527,10 @@ __global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, S
     //    (0 unless set by mppi_debug_inject_timeout) moves the target that many grids further,
     //    so that every block's wait runs out: the test of the timeout path, with no fault.
     if (threadIdx.x == 0) {
-        unsigned long long* ctr = reinterpret_cast<unsigned long long*>(B.tickets + 12);
-        const unsigned long long skew = B.tickets[31];
-        const unsigned long long nbl = gridDim.x;
-        const unsigned long long target = (atom_add_release_gpu(ctr, 1ull) / nbl + 1ull + skew) * nbl;
-        bool ok = true;
-        if (ld_acquire_gpu(ctr) < target) {
-            const uint64_t t0 = global_timer_ns();
-            while (ld_acquire_gpu(ctr) < target) {
-                if (global_timer_ns() - t0 > kGridWaitLimitNs) {
-                    atomicExch(B.err, kDevErrTimeout);
-                    ok = false;
-                    break;
-                }
-            }
-        }
-        is_last = ok ? 1 : 0;
+        is_last = grid_arrive_wait(reinterpret_cast<unsigned long long*>(B.tickets + 12), B.tickets[31], B.err,
+                                   kGridWaitLimitNs)
+                      ? 1
+                      : 0;
     }
     __syncthreads();
     if (!is_last) return;
