@@ -66,7 +66,7 @@ struct StepBuffers {
     float* out_J;
     int* err_out;          // optional: the step's last kernel copies *err here when it is done
     float* stats;          // [4] rho, eta of the last step
-    unsigned* tickets;     // [32] [9] grid-barrier arrivals, [10] grid-barrier generation
+    unsigned* tickets;     // [32]: [12..13] the update kernel's 64-bit grid-barrier arrival count, [31] test skew
     int* err;              // [1] device error word
 };
 
