@@ -50,9 +50,15 @@ def _check_costs(gpu_J, ref, rtol=COST_RTOL):
 
 
 def _report(name, data):
-    os.makedirs("gpurun_out", exist_ok=True)
-    with open(os.path.join("gpurun_out", "parity_report.jsonl"), "a") as f:
-        f.write(json.dumps(dict(test=name, **data)) + "\n")
+    """Append the measured errors to the JSON-lines file MPPI_PARITY_REPORT names (if set) and
+    print them."""
+    line = json.dumps(dict(test=name, **data))
+    print(line)
+    path = os.environ.get("MPPI_PARITY_REPORT")
+    if path:
+        os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+        with open(path, "a") as f:
+            f.write(line + "\n")
 
 
 # ---------------------------------------------------------------- tensor-core building block
