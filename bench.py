@@ -6,8 +6,10 @@ costs, softmax weights and weighted update -> plant update and warm-start
 shift.  Workload: K = 4096 rollouts, H = 50 horizon steps, two gates at
 seeded poses (6-10 m apart, yaw +-60 deg, pitch +-30 deg), Gate-SDF MLP
 67 -> 4 x 128 -> 1 with Xavier-uniform weights (seed 1) and N(0, 1) latents
-(seed 2).  Headline path: hidden GEMMs in BF16 on tcgen05 (FP32 accumulate);
-the plain FP32 path is timed on the same workload for the speedup.
+(seed 2).  Headline path: the chosen 16-bit form, hidden GEMMs in FP16 on
+tcgen05 (FP32 accumulate), which meets the 2 mm SDF target at p99 (BF16's 8-bit
+mantissa does not; it is timed beside it, as are E4M3 and the plain FP32 path,
+which gives the speedup).
 
 Metric: rollout-steps/s = K * H / step time, with per-step p50/p99 latency.
 Timing: CUDA events on the library's stream around every step, L2 flushed
@@ -39,10 +41,11 @@ UNIT = "rollout-steps/s"
 L2_FLUSH_BYTES = 256 << 20
 TENSOR_FLOPS_PER_QUERY = 3 * 2 * 128 * 128           # layers 2..4 on tcgen05
 FMA_FLOPS_PER_QUERY = 2 * 3 * 128 + 2 * 128           # layer 1 (point part) + output dot
-# dram__bytes_read.sum + dram__bytes_write.sum of one sdf_mlp_bf16 launch at this workload, from
-# the ncu capture summarised in profiles/sdf_mlp_tc_bf16_two_gate_K4096_H50_G2.md (None once the
-# kernel changes)
-SDF_BF16_DRAM_BYTES = 3415296
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the headline SDF kernel at this
+# workload, from an ncu capture of the current kernel (None when the kernel changed since)
+SDF_DRAM_BYTES = None
+SDF_DRAM_BYTES_SOURCE = "no ncu capture of the current kernel yet"
+HEADLINE_MODE = "fp16"
 # multiply-adds x 2 of the depth encoder's convolutions and head for one 160 x 120 image
 ENCODER_FLOPS_PER_IMAGE_160x120 = 2 * (60 * 80 * 16 * 9 * 1 + 30 * 40 * 32 * 9 * 16 + 15 * 20 * 64 * 9 * 32
                                        + 8 * 10 * 64 * 9 * 64 + 64 * 64)
@@ -454,9 +457,10 @@ def distill_leg(torch, B, dev, steps, schedule="constant"):
                                      "final_position_divergence_m_vs_exact": pos_div}}
 
 
-def cpu_baseline(wl, seconds):
-    """The FP64 oracle, as it stands, on the host cores: whole control steps until `seconds` pass."""
+def _oracle_steps(seconds):
+    """Whole FP64 oracle control steps of the bench workload until `seconds` pass: (steps, s)."""
     from oracle import mppi as O
+    wl = workload()
     prm = O.Params(**wl["params"])
     n, t0 = 0, time.perf_counter()
     while True:
@@ -464,9 +468,48 @@ def cpu_baseline(wl, seconds):
         n += 1
         if time.perf_counter() - t0 >= seconds:
             break
-    dt = time.perf_counter() - t0
-    return {"value": prm.K * prm.H * n / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-            "sample": f"{n} full oracle control steps (K={prm.K}, H={prm.H}, G=2, FP64 numpy) in {dt:.1f} s"}
+    return n, time.perf_counter() - t0
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def cpu_baseline(wl, seconds):
+    """The FP64 oracle, as it stands, on the host cores: whole control steps until `seconds` pass,
+    once with every core BLAS uses (in this process) and once on one core (a child process with
+    the BLAS thread pools at one thread; the oracle's other numpy work is single-threaded)."""
+    K, H = wl["params"]["K"], wl["params"]["H"]
+    n, dt = _oracle_steps(seconds)
+    res = {"value": K * H * n / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+           "sample": f"{n} full oracle control steps (K={K}, H={H}, G=2, FP64 numpy) in {dt:.1f} s",
+           "cpu_model": cpu_model(), "host_cores": os.cpu_count()}
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = f"import bench, json; print(json.dumps(bench._oracle_steps({seconds})))"
+    try:
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                           timeout=seconds * 10 + 120)
+        n1, dt1 = json.loads(r.stdout.strip().splitlines()[-1])
+        res["single_core"] = {"value": K * H * n1 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"{n1} full oracle control steps in {dt1:.1f} s"}
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError) as e:
+        res["single_core"] = {"value": None, "error": str(e)[:200]}
+    return res
 
 
 def blas_threads():
@@ -509,13 +552,13 @@ def four_gate_leg(torch, B, stream, flush, dev, steps, drone_id):
 
 
 def rotor_leg(torch, B, stream, flush, dev, steps, drone_id):
-    """The paper's rotor-thrust-rate model on the K=4096, H=50, two-gate workload (BF16 SDF)."""
+    """The paper's rotor-thrust-rate model on the K=4096, H=50, two-gate workload (SDF in the headline 16-bit form, FP16)."""
     import workloads as W
     wl = dict(W.two_gate_mlp())
     wl["params"] = W.rotor_params(4096, 50)
     wl["state"] = W.rotor_state([0.0, 0.0, 0.0])
     wl["nominal"] = np.zeros((50, 4), np.float32)
-    out = mode_leg(torch, B, wl, "bf16", stream, flush, dev, steps, drone_id)
+    out = mode_leg(torch, B, wl, HEADLINE_MODE, stream, flush, dev, steps, drone_id)
     out["workload"] = "rotor_two_gate_mlp_K4096_H50_G2"
     return out
 
@@ -580,7 +623,7 @@ def vision_leg(torch, B, stream, flush, dev, steps, drone_id):
     """The vision front end: (1) the 64 views of the two-gate track at 160 x 120 rendered with
     sensor noise and encoded into 64 latents (one render + one encode per timed step); (2) one
     control cycle of a drone -- render a view of each of the two gates, encode both, and run the
-    BF16 MPPI step (K=4096, H=50) on those latents -- per timed step, all on one stream."""
+    FP16 MPPI step (K=4096, H=50) on those latents -- per timed step, all on one stream."""
     import workloads as W
     wl = W.depth_views()
     kw = dict(wl["camera"], width=160, height=120, fx=96.25, fy=96.25, cx=80.0, cy=60.0)
@@ -618,7 +661,7 @@ def vision_leg(torch, B, stream, flush, dev, steps, drone_id):
     ms_enc = timed(lambda: B.mppi_encode_depth(enc, n, depth, kw["max_range"], z))
     # one drone's control cycle: a view of each gate (the first camera pose that faces it)
     wl_mppi = W.two_gate_mlp()
-    ctx = make_ctx(B, wl_mppi, "bf16", stream, drone_id)
+    ctx = make_ctx(B, wl_mppi, HEADLINE_MODE, stream, drone_id)
     U = torch.zeros(50, 4, device=dev)
     st = torch.from_numpy(wl_mppi["state"]).to(dev)
     nom = torch.from_numpy(wl_mppi["nominal"]).to(dev)
@@ -695,7 +738,7 @@ def vision_leg(torch, B, stream, flush, dev, steps, drone_id):
                                  "images_per_s": n / (ms_train.mean() * 1e-3)},
             "control_cycle": {"p50_ms": float(np.percentile(ms_cycle, 50)), "p99_ms": float(np.percentile(ms_cycle, 99)),
                               "mean_ms": float(ms_cycle.mean()),
-                              "stages": "render 2 views + encode 2 + MPPI step (BF16)",
+                              "stages": "render 2 views + encode 2 + MPPI step (FP16)",
                               "render_2_views_ms": float(ms_r2.mean()), "encode_2_ms": float(ms_e2.mean()),
                               "mppi_step_with_new_latents_ms": float(ms_s.mean())},
             "control_cycle_pipelined": {"period_ms": ms_pipe, "cycles": n_cyc,
@@ -739,7 +782,7 @@ def run_ours(args):
     assert stream != 0
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    ctx = make_ctx(B, wl, "bf16", stream, drone_id=rank)
+    ctx = make_ctx(B, wl, HEADLINE_MODE, stream, drone_id=rank)
     per_launch = B.mppi_kernels_per_step(ctx)
     if world > 1:
         dist.barrier()
@@ -759,10 +802,10 @@ def run_ours(args):
     e2e_ms, h2d, d2h = e2e_loop(torch, B, ctx, wl, args.e2e_steps, flush)
     B.mppi_destroy(ctx)
 
-    ctx16 = make_ctx(B, wl, "fp16", stream, drone_id=rank)
-    ms16 = device_loop(torch, B, ctx16, wl, args.steps, 3, flush, dev)
-    kt16 = kernel_times(torch, B, ctx16, 20, flush, wl, dev)
-    B.mppi_destroy(ctx16)
+    ctxbf = make_ctx(B, wl, "bf16", stream, drone_id=rank)
+    msbf = device_loop(torch, B, ctxbf, wl, args.steps, 3, flush, dev)
+    ktbf = kernel_times(torch, B, ctxbf, 20, flush, wl, dev)
+    B.mppi_destroy(ctxbf)
 
     ctx8 = make_ctx(B, wl, "fp8", stream, drone_id=rank)
     ms8 = device_loop(torch, B, ctx8, wl, args.steps, 3, flush, dev)
@@ -796,23 +839,26 @@ def run_ours(args):
     peak_tf = peaks.get("bf16_tflops")
     peak_src = "measured burst bf16 (MEASURED_PEAKS.json)" if peak_tf else "fallback 1900 TFLOP/s"
     peak_tf = peak_tf or 1900.0
-    t_sdf = ktimes.get("sdf_mlp_bf16")
+    t_sdf = ktimes.get("sdf_mlp_" + HEADLINE_MODE)
     tensor_flops = TENSOR_FLOPS_PER_QUERY * K * H * G
     achieved = tensor_flops / (t_sdf * 1e-3) / 1e12 if t_sdf else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": wl["name"], "K": K, "H": H, "gates": G, "sdf": "Gate-SDF MLP, BF16 tcgen05",
+        "scaling": "weak", "vs_baseline": None, "dtype": HEADLINE_MODE, "data": "synthetic",
+        "config": {"workload": wl["name"], "K": K, "H": H, "gates": G,
+                   "sdf": "Gate-SDF MLP, FP16 tcgen05 (the 16-bit form within the 2 mm SDF target at p99)",
                    "dynamics": "fp32 RK4", "l2": "flushed (256 MiB write) between timed steps",
                    "parallelism": "replicas" if world > 1 else "single"},
         "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
                        "mean": float(ms.mean()), "min": float(ms.min())},
         "fp32": {"value": K * H / (ms32.mean() * 1e-3), "p50_ms": float(np.percentile(ms32, 50)),
                  "p99_ms": float(np.percentile(ms32, 99)), "steps": args.fp32_steps, "kernel_ms": kt32},
-        "fp16": {"value": K * H / (ms16.mean() * 1e-3), "p50_ms": float(np.percentile(ms16, 50)),
-                 "p99_ms": float(np.percentile(ms16, 99)), "kernel_ms": kt16,
-                 "speedup_vs_fp32": float(ms32.mean() / ms16.mean())},
+        "bf16": {"value": K * H / (msbf.mean() * 1e-3), "p50_ms": float(np.percentile(msbf, 50)),
+                 "p99_ms": float(np.percentile(msbf, 99)), "kernel_ms": ktbf,
+                 "speedup_vs_fp32": float(ms32.mean() / msbf.mean()),
+                 "p99_speedup_vs_fp32": float(np.percentile(ms32, 99) / np.percentile(msbf, 99)),
+                 "note": "BF16 operands: SDF error p99 above the 2 mm target (MAE 1.24 mm, p99 3.06 mm)"},
         "fp8": {"value": K * H / (ms8.mean() * 1e-3), "p50_ms": float(np.percentile(ms8, 50)),
                 "p99_ms": float(np.percentile(ms8, 99)), "kernel_ms": kt8,
                 "speedup_vs_fp32": float(ms32.mean() / ms8.mean())},
@@ -820,9 +866,10 @@ def run_ours(args):
         "p99_speedup_vs_fp32": float(np.percentile(ms32, 99) / np.percentile(ms, 99)),
         "sdf_queries_per_s": K * H * G / (t_sdf * 1e-3) if t_sdf else None,
         "kernel_ms": ktimes,
-        "roofline": {"kernel": "sdf_mlp_bf16", "bound": "tensor", "achieved": achieved, "peak": peak_tf,
+        "roofline": {"kernel": "sdf_mlp_" + HEADLINE_MODE, "bound": "tensor", "achieved": achieved, "peak": peak_tf,
                      "unit": "TFLOP/s", "frac": achieved / peak_tf if achieved else None,
-                     "traffic": SDF_BF16_DRAM_BYTES, "peak_source": peak_src,
+                     "traffic": SDF_DRAM_BYTES, "traffic_source": SDF_DRAM_BYTES_SOURCE,
+                     "peak_source": peak_src + " (FP16 dense rate = BF16 nominally)",
                      "algorithmic_flops_per_launch": tensor_flops},
         "e2e": {"value": K * H / (e2e_ms.mean() * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "p50_ms": float(np.percentile(e2e_ms, 50)),
@@ -847,33 +894,48 @@ def run_ours(args):
 
 # ------------------------------------------------------------------ reference arm: the oracle
 def run_reference(args):
+    """The oracle as it stands on the host cores: every step is one whole FP64 control step of the
+    bench workload (K = 4096, H = 50, two gates), unless the requested steps would not end within
+    about three minutes, in which case every step runs the same step on a rollout sample (the
+    first K' rollouts: same start, gates, weights and noise keys) and the line says so."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from oracle import mppi as O
     wl = workload()
-    K_SAMPLE = 512
-    prm = O.Params(**dict(wl["params"], K=K_SAMPLE))
-    H = prm.H
-    for i in range(max(0, args.warmup)):
-        O.mppi_step(wl["state"], wl["nominal"], wl["poses"], prm, i, wl["latents"], wl["layers"])
-    t = []
-    for i in range(args.steps):
+    K_full, H = wl["params"]["K"], wl["params"]["H"]
+    budget_s = 180.0
+
+    def one(prm, i):
         t0 = time.perf_counter()
-        O.mppi_step(wl["state"], wl["nominal"], wl["poses"], prm, args.warmup + i, wl["latents"], wl["layers"])
-        t.append(time.perf_counter() - t0)
-    t = np.array(t)
-    value = K_SAMPLE * H / t.mean()
-    sample = (f"each step: one FP64 oracle control step on a {K_SAMPLE}-rollout sample of the K=4096, H=50, "
-              f"G=2 workload (rollout-steps/s scales with the sample)")
+        O.mppi_step(wl["state"], wl["nominal"], wl["poses"], prm, i, wl["latents"], wl["layers"])
+        return time.perf_counter() - t0
+
+    prm = O.Params(**wl["params"])
+    t_full = one(prm, 0)                         # also the first warm-up step
+    K_run = K_full
+    n_total = args.steps + max(0, args.warmup)
+    if n_total * t_full > budget_s:
+        K_run = max(128, int(K_full * budget_s / (n_total * t_full)) // 128 * 128)
+        prm = O.Params(**dict(wl["params"], K=K_run))
+    for i in range(1, max(0, args.warmup)):
+        one(prm, i)
+    t = np.array([one(prm, args.warmup + i) for i in range(args.steps)])
+    value = K_run * H / t.mean()
+    sample = (f"each step: one whole FP64 oracle control step of the K={K_full}, H={H}, G=2 workload"
+              if K_run == K_full else
+              f"each step: one FP64 oracle control step on a {K_run}-rollout sample of the K={K_full}, H={H}, G=2 "
+              f"workload (the whole workload would not fit the run's time budget)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(t.mean() * 1e3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["name"], "K": 4096, "H": H, "gates": 2, "sdf": "Gate-SDF MLP, FP64 numpy"},
+            "config": {"workload": wl["name"], "K": K_run, "H": H, "gates": 2, "sdf": "Gate-SDF MLP, FP64 numpy"},
             "latency_ms": {"p50": float(np.percentile(t, 50) * 1e3), "p99": float(np.percentile(t, 99) * 1e3)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "cpu_model": cpu_model(), "host_cores": os.cpu_count()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if K_run != K_full:
+        line["config"]["sample_of"] = {"K": K_full, "H": H, "gates": 2}
     print(json.dumps(line), flush=True)
 
 

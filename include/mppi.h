@@ -150,21 +150,27 @@ typedef struct mppi_ctx mppi_ctx;
 void mppi_config_default(mppi_config* cfg);
 
 /*
- * Create a controller.  cuda_stream is a cudaStream_t (NULL: the library
+ * Create a controller: the MPPI problem of Sec. IV-A (K sampled control
+ * sequences over a horizon of H steps, Eq. 5) with its cost of Sec. IV-B
+ * (Eq. 6-10) for one vehicle.  cuda_stream is a cudaStream_t (NULL: the library
  * creates and owns a non-blocking stream).  Allocates every device buffer the
  * step needs for (K, H, max_gates); later calls allocate nothing on the
  * device.  Initial state: hovering at the origin, nominal = H copies of
- * u_hover = (mass * gravity, 0, 0, 0), step counter 0, no gates, no weights.
+ * u_hover = (mass * gravity, 0, 0, 0) (the warm start of Sec. IV-A before any
+ * step has run), step counter 0, no gates, no weights.
  * Errors: MPPI_E_INVALID (cfg), MPPI_E_UNSUPPORTED (device), MPPI_E_OOM, MPPI_E_CUDA.
  * On error *out is NULL (the message is in the thread's last-error slot,
  * readable with mppi_last_error(NULL)).
  */
 int mppi_create(const mppi_config* cfg, void* cuda_stream, mppi_ctx** out);
 
-/* Free the context and its device buffers.  NULL is ignored. */
+/* Free the context and its device buffers (the controller of mppi_create, Sec. IV-A); waits for
+ * its stream first.  NULL is ignored. */
 void mppi_destroy(mppi_ctx* ctx);
 
-/* Last error message of ctx (or of the calling thread's last failed create when ctx is NULL). */
+/* Last error message of ctx (or of the calling thread's last failed create when ctx is NULL).  The
+ * paper defines no error reporting; the string is owned by the library and valid until the next
+ * call on ctx (or, for NULL, the next failing call of this thread). */
 const char* mppi_last_error(const mppi_ctx* ctx);
 
 /*
@@ -215,8 +221,10 @@ int mppi_step(mppi_ctx* ctx, const float* state, const float* gate_poses, const 
  * Same as mppi_step with DEVICE pointers (same shapes, same NULL rules),
  * enqueued on the context's stream and returned without synchronising; the
  * outputs are valid once the stream has reached this point.  No host-side
- * NaN check.  Device-side timeouts are reported by the next synchronous call
- * (mppi_sync, mppi_step, mppi_get_*).
+ * NaN check.  d_new_controls must be 16-byte aligned (it is written as
+ * float4); a misaligned or NULL d_new_controls returns MPPI_E_INVALID with
+ * nothing enqueued.  Device-side timeouts are reported by the next
+ * synchronous call (mppi_sync, mppi_step, mppi_get_*).
  */
 int mppi_step_async(mppi_ctx* ctx, const float* d_state, const float* d_gate_poses, const float* d_latents,
                     const float* d_nominal, float* d_new_controls, float* d_weights, float* d_costs);
@@ -224,7 +232,9 @@ int mppi_step_async(mppi_ctx* ctx, const float* d_state, const float* d_gate_pos
 /* Wait for the context's stream and report any device-side error. */
 int mppi_sync(mppi_ctx* ctx);
 
-/* Read back the device-resident warm-start sequence (H x 4) / true state (mppi_state_dim). Synchronous. */
+/* Read back the device-resident warm-start sequence (H x 4: the previous U*_new shifted by one,
+ * u_hover appended -- the receding-horizon initialisation of Sec. IV-A) / the true state
+ * (mppi_state_dim floats, after the plant step that applied U*_new[0]).  Synchronous. */
 int mppi_get_nominal(mppi_ctx* ctx, float* out);
 int mppi_get_state(mppi_ctx* ctx, float* out);
 
@@ -239,7 +249,8 @@ uint64_t mppi_get_step_counter(const mppi_ctx* ctx);
  *   MPPI_BUF_NOISE      K x H x 4  delta u, layout [k][h][4] (h fastest)
  *   MPPI_BUF_POSITIONS  K x H x 4  rollout positions p_1..p_H, [k][h][x,y,z,0]
  *   MPPI_BUF_COST_PARTS 3 x K      [J_col; J_prog; J_ctl] (MPPI_COST_PAPER: [Q_sdf J_sdf; Q_gate J_gate; Q_vis J_vis])
- *   MPPI_BUF_SDF        K x H      s(p_h) = min over gates of the SDF at every rollout state, [k][h] (MLP modes)
+ *   MPPI_BUF_SDF        K x H      s(p_h) = min over gates of the SDF at every rollout state, [k][h] (MLP
+ *                                  modes; written only while MPPI_DIAG_STORE_SDF is set, else MPPI_E_INVALID)
  *   MPPI_BUF_WEIGHTS    K
  *   MPPI_BUF_COSTS      K
  */
@@ -250,6 +261,18 @@ uint64_t mppi_get_step_counter(const mppi_ctx* ctx);
 #define MPPI_BUF_WEIGHTS     4
 #define MPPI_BUF_COSTS       5
 int mppi_read_buffer(mppi_ctx* ctx, int which, float* host_out, size_t n);
+
+/*
+ * Diagnostics of the following steps (a bit mask; 0 = none, the default):
+ *   MPPI_DIAG_STORE_SDF  the SDF kernel also stores s(p) of every rollout state for
+ *                        MPPI_BUF_SDF (K x H floats written per step).  Without it the kernel
+ *                        folds the safety cost of Eq. 8 over each rollout's states in its
+ *                        epilogue (Eq. 9-10) and writes only K x (floor((H + 126) / 128) + 1)
+ *                        partial sums; the step's results are bit-identical either way.
+ * Errors: MPPI_E_INVALID (unknown bit).
+ */
+#define MPPI_DIAG_STORE_SDF 1
+int mppi_set_diagnostics(mppi_ctx* ctx, int flags);
 
 /*
  * Raw Philox4x32-10 words of the step's noise for the current step counter
@@ -309,12 +332,16 @@ int mppi_selftest_tc_gemm(const uint16_t* d_A, const uint16_t* d_B, float* d_D, 
  *   d_new_controls  H x 4 out: U*_new[h] = sum_k w_k clip(U*_h + delta_{k,h}) (device)
  *   d_weights       K out: w_k = exp(-(J_k - min J) / lambda) / sum (device, nullable)
  *   stream          cudaStream_t (NULL: the legacy default stream)
+ * d_noise, d_nominal and d_new_controls must be 16-byte aligned (they are read and
+ * written as float4); a misaligned pointer returns MPPI_E_INVALID with nothing enqueued.
  * Enqueues two kernels and returns; the outputs are valid once the stream
  * has reached them.  Scratch: a file-scope device array of 2 * 1024 floats
  * (8 KB) that every GPU which loads this library holds until the process
  * exits; it caps K at MPPI_NOALLOC_MAX_K.  The first call on each device looks
  * up the array's device address with that device current (cudaGetSymbolAddress);
- * make that first call before any stream capture.  Every call on a device
+ * make that first call before any stream capture.  Calls made outside a capture
+ * look the address up again, so a device reset between calls is harmless; a call
+ * inside a capture uses the address of the last call outside one.  Every call on a device
  * shares the array and each call overwrites what it uses (nothing needs to
  * start at zero), so calls whose kernels overlap on the GPU -- on different
  * streams, or from several host threads -- race and must not be issued.
@@ -398,7 +425,8 @@ int mppi_render_depth(const mppi_depth_camera* cam, int n_views, const float* d_
  * point near gate g = ((A0 >> 8) n_gates) >> 24, uniform in its frame's box grown by
  * 0.3 m ((2 uB0 - 1)(d + 0.3), (2 uB1 - 1)(a_out + 0.3), (2 uB2 - 1)(a_out + 0.3)) in the
  * gate frame; else a point of the view frustum at depth 0.2 + uA1 (max_range - 0.2) on
- * the ray through image position (width uA2, height uB3) (R31's camera model).
+ * the ray through image position (width uA2, height uB3) (the pinhole camera of
+ * mppi_render_depth, standing in for the depth camera of Sec. III-B and Sec. V).
  *   cam           intrinsics, max_range (> 0.2), frame geometry, seed and frame
  *   n_views       0 .. 2^24 camera poses (device, n_views x 7)
  *   n_gates       1 .. MPPI_MAX_RENDER_GATES gate poses (device, n_gates x 7)

@@ -40,6 +40,7 @@ MPPI_BUF_COST_PARTS = 2
 MPPI_BUF_SDF = 3
 MPPI_BUF_WEIGHTS = 4
 MPPI_BUF_COSTS = 5
+MPPI_DIAG_STORE_SDF = 1
 
 LATENT_DIM = 64
 HIDDEN = 128
@@ -49,7 +50,7 @@ EXPORTS = [
     "mppi_config_default", "mppi_state_dim", "mppi_create", "mppi_destroy", "mppi_last_error", "mppi_set_gates",
     "mppi_set_sdf_weights", "mppi_step", "mppi_step_async", "mppi_sync", "mppi_get_nominal",
     "mppi_get_state", "mppi_set_step_counter", "mppi_get_step_counter", "mppi_read_buffer",
-    "mppi_read_noise_words", "mppi_debug_inject_timeout", "mppi_set_timing", "mppi_get_kernel_times", "mppi_kernels_per_step",
+    "mppi_read_noise_words", "mppi_debug_inject_timeout", "mppi_set_diagnostics", "mppi_set_timing", "mppi_get_kernel_times", "mppi_kernels_per_step",
     "mppi_selftest_tc_gemm", "mppi_softmax_update_noalloc",
     "mppi_server_config_default", "mppi_server_create", "mppi_server_destroy", "mppi_server_last_error",
     "mppi_server_set_sdf_weights", "mppi_server_submit", "mppi_server_poll", "mppi_server_next_result",
@@ -141,6 +142,7 @@ _SIGS = {
     "mppi_read_noise_words": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     "mppi_debug_inject_timeout": (ctypes.c_int, [_vp]),
     "mppi_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "mppi_set_diagnostics": (ctypes.c_int, [_vp, ctypes.c_int]),
     "mppi_get_kernel_times": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float),
                                              ctypes.c_int]),
     "mppi_kernels_per_step": (ctypes.c_int, [_vp]),
@@ -316,6 +318,10 @@ def mppi_read_noise_words(ctx, out):
 
 def mppi_debug_inject_timeout(ctx):
     return _check(load().mppi_debug_inject_timeout(ctx), ctx)
+
+
+def mppi_set_diagnostics(ctx, flags):
+    return _check(load().mppi_set_diagnostics(ctx, int(flags)), ctx)
 
 
 def mppi_set_timing(ctx, enable):

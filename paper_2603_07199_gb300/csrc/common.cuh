@@ -43,6 +43,7 @@ struct StepParams {
     float arm_d, kappa, t_rotor_max;  // rotor offset l / sqrt(2), reaction torque per newton, thrust bound
     float3 J, inv_J;       // diagonal inertia and its reciprocal
     int pe;                // positional-encoding levels of the decoder's query point
+    int store_sdf;         // the SDF kernels also store s(p) of every rollout state (diagnostics)
 };
 
 // Device buffers of one controller.
@@ -55,7 +56,8 @@ struct StepBuffers {
     float4* noise;         // [K][H] delta u (h fastest)
     float4* pos;           // [K][H] rollout positions p_1..p_H (x, y, z, 0)
     float* parts;          // [3][K] J_col, J_prog, J_ctl
-    float* sdf;            // [K][H] min-over-gates SDF at every rollout state (MLP modes)
+    float* sdf;            // [K][H] min-over-gates SDF at every rollout state (MLP modes, diagnostics only)
+    float* colp;           // [K][col_slots(H)] per-rollout partial sums of the stage hinge, one per SDF tile
     float* J;              // [K]
     float* w;              // [K]
     float4* unew;          // [H] updated sequence U*_new
@@ -360,6 +362,44 @@ __device__ __forceinline__ float hinge_sq(float s, float d_safe) {
 __device__ __forceinline__ float stage_hinge(float s, float d_safe, int paper) {
     const float e = fmaxf(d_safe - s, 0.f);
     return paper ? e : e * e;
+}
+
+// ---------------------------------------------------------------- collision-cost fold of an SDF tile
+// The SDF kernels fold the stage hinge of Eq. 8 over the horizon inside their epilogue (Eq. 9-10:
+// J_col of a rollout is a sum over its states) instead of storing s(p) for every state.  Rollout
+// k owns rows k H .. k H + H - 1 of the [K][H] state array, which touch the 128-row tiles
+// floor(k H / 128) .. floor((k H + H - 1) / 128): at most col_slots(H) of them.  Tile t writes
+// the sum over its rows of rollout k to colp[k][t - floor(k H / 128)]; the cost kernel adds a
+// rollout's slots in tile order, so every sum runs in a fixed order.
+__host__ __device__ inline int col_slots(int H) { return (H + 126) / kTileRows + 1; }
+
+// Step 1, run by each of the four warps that hold a tile's rows (local row = 32 warp + lane,
+// global row r, stage cost c, 0 for rows past the end): an inclusive scan over the warp's rows
+// that restarts at every rollout boundary; the last row of each run leaves the run's sum in
+// seg[local row].
+__device__ __forceinline__ void fold_warp_runs(float c, int r, int H, int lane, float* seg) {
+    const int key = r / H;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const float t = __shfl_up_sync(0xffffffffu, c, d);
+        const int kk = __shfl_up_sync(0xffffffffu, key, d);
+        if (lane >= d && kk == key) c += t;
+    }
+    const int knext = __shfl_down_sync(0xffffffffu, key, 1);
+    if (lane == 31 || knext != key) seg[r & (kTileRows - 1)] = c;
+}
+// Step 2, after a barrier over those warps: thread j adds the run sums of the tile's j-th rollout
+// over the warps in warp order and stores the tile's partial sum of that rollout.
+__device__ __forceinline__ void fold_store(const float* seg, int row0, int nvalid, int H, int tile, int j,
+                                           float* colp, int np) {
+    const int k = row0 / H + j;
+    const int last = row0 + nvalid - 1;
+    if (k > last / H) return;
+    const int lo = max(k * H, row0) - row0;
+    const int hi = min(k * H + H - 1, last) - row0;
+    float s = 0.f;
+    for (int w = lo >> 5; w <= (hi >> 5); ++w) s += seg[min(hi, 32 * w + 31)];
+    colp[static_cast<size_t>(k) * np + (tile - (k * H) / kTileRows)] = s;
 }
 
 // Index of the first gate whose plane the position p has not crossed (n_g . (p - t_g) < 0),

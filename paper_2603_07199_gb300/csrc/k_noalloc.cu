@@ -119,16 +119,21 @@ __global__ void __launch_bounds__(kNaUpdThreads) na_update_kernel(const float* _
 std::mutex g_scratch_mu;
 float* g_scratch[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once per
-// device with that device current (the array's name is not a device address in
-// host code).
-cudaError_t scratch_on_current_device(float** out) {
+// Device address of the scratch array on the current device, looked up with that
+// device current (the array's name is not a device address in host code).  Outside
+// a stream capture the address is looked up again on every call, so that a device
+// reset (which reloads the module, possibly elsewhere) never leaves a stale address;
+// inside a capture the address cached by an earlier call is used.
+cudaError_t scratch_on_current_device(cudaStream_t s, float** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (g_scratch[dev] == nullptr) {
+    if (g_scratch[dev] == nullptr || cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_partials);
         if (e != cudaSuccess) return e;
@@ -163,8 +168,15 @@ extern "C" int mppi_softmax_update_noalloc(const float* d_costs, const float* d_
     if (H < 1 || H > MPPI_MAX_H) return na_fail(MPPI_E_INVALID, "mppi_softmax_update_noalloc: H out of [1, MPPI_MAX_H]");
     if (!(lambda > 0.f) || !(thrust_min <= thrust_max) || !(rate_max >= 0.f))
         return na_fail(MPPI_E_INVALID, "mppi_softmax_update_noalloc: lambda <= 0 or inconsistent control bounds");
+    // the kernels move noise, nominal and controls as float4: misaligned buffers are refused here,
+    // before anything is enqueued
+    const auto misaligned = [](const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 != 0; };
+    if (misaligned(d_noise) || misaligned(d_nominal) || misaligned(d_new_controls))
+        return na_fail(MPPI_E_INVALID, "mppi_softmax_update_noalloc: d_noise, d_nominal and d_new_controls must be "
+                                       "16-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     float* part = nullptr;
-    cudaError_t e = scratch_on_current_device(&part);
+    cudaError_t e = scratch_on_current_device(s, &part);
     if (e != cudaSuccess) return na_fail(MPPI_E_CUDA, "mppi_softmax_update_noalloc: scratch address lookup failed", e);
     StepParams P{};
     P.K = K;
@@ -173,7 +185,6 @@ extern "C" int mppi_softmax_update_noalloc(const float* d_costs, const float* d_
     P.tmin = thrust_min;
     P.tmax = thrust_max;
     P.rmax = rate_max;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int nb = (K + kNaThreads - 1) / kNaThreads;
     na_partials_kernel<<<nb, kNaThreads, 0, s>>>(d_costs, K, lambda, part);
     na_update_kernel<<<H, kNaUpdThreads, 0, s>>>(d_costs, reinterpret_cast<const float4*>(d_noise),

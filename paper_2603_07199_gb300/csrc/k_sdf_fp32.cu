@@ -1,8 +1,9 @@
 // (c) Gate-SDF MLP at every rollout state, FP32 on the CUDA cores: the plain
 // FP32 path.  One CTA takes a tile of 128 rollouts at one horizon step, runs
 // the whole MLP for every gate with register-blocked FP32 GEMMs through
-// shared memory, keeps the minimum over gates and writes the per-state
-// minimum over gates s(p) of every rollout state.
+// shared memory, keeps the minimum over gates and folds the stage hinge of
+// that minimum s(p) into per-rollout partial sums of the collision cost (s(p)
+// itself is stored only for diagnostics).
 #include "kernels.h"
 
 namespace mppi {
@@ -33,7 +34,8 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_fp32_kernel(StepParams P,
     float* sW5 = sBias + 3 * kHidden;               // [128]
     float* sPg = sW5 + kHidden;                     // [NP][128]  point features of the tile's rows
     float* sMin = sPg + kMaxPoint * kTileRows;      // [128]      min over gates
-    float* sPose = sMin + kTileRows;                // [G][8]
+    float* sFold = sMin + kTileRows;                // [128]      run sums of the collision-cost fold
+    float* sPose = sFold + kTileRows;               // [G][8]
 
     const int tid = threadIdx.x;
     const int G = P.G;
@@ -66,6 +68,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_fp32_kernel(StepParams P,
     // tile = 128 consecutive rollout states of the [K][H] position array
     const int n_rows = P.K * P.H;
     const int n_items = (n_rows + kTileRows - 1) / kTileRows;
+    const int n_colp = col_slots(P.H);              // partial-sum slots per rollout
 
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         if (tid < kTileRows) sMin[tid] = __int_as_float(0x7f800000);
@@ -170,17 +173,23 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_fp32_kernel(StepParams P,
             }
         }
         __syncthreads();
+        // collision-cost fold (Eq. 8-10): stage hinge of every row, summed per rollout over the tile
+        const int row0 = item * kTileRows;
         if (tid < kTileRows) {
-            const int r = item * kTileRows + tid;
-            if (r < n_rows) B.sdf[r] = sMin[tid];
+            const int r = row0 + tid;
+            if (P.store_sdf && r < n_rows) B.sdf[r] = sMin[tid];
+            const float c = r < n_rows ? stage_hinge(sMin[tid], P.d_safe, P.paper) : 0.f;
+            fold_warp_runs(c, r, P.H, tid & 31, sFold);
         }
+        __syncthreads();
+        if (tid < kTileRows) fold_store(sFold, row0, min(kTileRows, n_rows - row0), P.H, item, tid, B.colp, n_colp);
         __syncthreads();
     }
 }
 
 constexpr size_t kSmemBytes = sizeof(float) * (kHidden * kLdA + kHidden * kHidden + kMaxPoint * kHidden +
                                                 kMaxGates * kHidden + 3 * kHidden + kHidden + kMaxPoint * kTileRows +
-                                                kTileRows + kMaxGates * 8);
+                                                2 * kTileRows + kMaxGates * 8);
 
 }  // namespace
 

@@ -9,7 +9,9 @@
 //   each followed by TMEM load -> (bias,) softplus -> 16-bit A tile (layers 1-3)
 //        or the FP32 output dot (layer 4)
 // and keeps the running minimum over gates in a register; the item ends by
-// storing that minimum s(p) for the 128 states of the tile.
+// folding the stage hinge of that minimum s(p) into per-rollout partial sums of
+// the collision cost (fold_warp_runs / fold_store; s(p) itself is stored only
+// for diagnostics).
 //
 // CTA = 3 tile groups of 8 warps.  A tile group owns one A tile (smem) and one
 // 128-column FP32 accumulator (TMEM); its warps w and w + 4 share TMEM lane
@@ -61,6 +63,7 @@ struct __align__(16) TcShared {
     float bias[3][kHidden];                   // c b2, c b3, c b4 (E4M3 path: added in the epilogue)
     float w5[kHidden];                        // (ln 2 / beta) w5
     float part[kGroups][kTileRows];           // output-layer partial sums of the upper column half
+    float fold[kGroups][kTileRows];           // run sums of the collision-cost fold (fold_warp_runs)
     float pose[kMaxGates][8];
     uint64_t acc_full[kGroups];               // MMA -> epilogue: accumulator ready
     uint32_t tmem_base;
@@ -336,6 +339,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
     }
     const int n_rows = P.K * P.H;
     const int n_tiles = (n_rows + kTileRows - 1) / kTileRows;
+    const int n_colp = col_slots(P.H);           // partial-sum slots per rollout
     const int nslots = gridDim.x * kGroups;
     const int slot = blockIdx.x + static_cast<int>(gridDim.x) * (warp / kGroupWarps);
     volatile int* abort_flag = &S.abort_flag;
@@ -573,7 +577,15 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                 }
             }
         }
-        if (ok && half == 0 && row < nvalid && r < n_rows) B.sdf[r] = smin;
+        if (ok && half == 0) {
+            // collision-cost fold (Eq. 8-10): stage hinge of every row, summed per rollout over
+            // the tile's rows; the four lower-half warps of the group meet at their own barrier
+            if (P.store_sdf && row < nvalid) B.sdf[r] = smin;
+            const float c = row < nvalid ? stage_hinge(smin, P.d_safe, P.paper) : 0.f;
+            fold_warp_runs(c, r, P.H, lane, S.fold[grp]);
+            tc::named_barrier(4 + grp, kGroupThreads / 2);
+            fold_store(S.fold[grp], row0, nvalid, P.H, tile, row, B.colp, n_colp);
+        }
     }
 
     // on abort: let the MMAs this group's leader issued finish before TMEM is released

@@ -348,9 +348,9 @@ __global__ void __launch_bounds__(kRotorThreads) rollout_rotor_kernel(StepParams
 
 // ------------------------------------------------------------------ (d) costs, weights, update, receding horizon
 // Block b owns R consecutive rollouts (R a multiple of 32, at most kCuMaxBlocks blocks):
-//  1. J_k = J_col + J_prog + J_ctl (MLP modes: J_col = w_col sum_h max(0, d_safe - s_h)^2
-//     over rollout k's row of the SDF array, or Q_sdf sum_h max(0, d_safe - s_h) in the
-//     paper's form), rho_b = min of the block's J_k,
+//  1. J_k = J_col + J_prog + J_ctl (MLP modes: J_col = w_col sum_h max(0, d_safe - s_h)^2,
+//     or Q_sdf sum_h max(0, d_safe - s_h) in the paper's form, from the per-tile partial sums
+//     the SDF kernel folded), rho_b = min of the block's J_k,
 //     e_k = exp(-(J_k - rho_b) / lambda), eta_b = sum of the block's e_k;
 //  2. S_b[h] = sum_{k in b} e_k clip(U*_h + delta_{k,h});
 //  3. grid barrier (the kernel is a cooperative launch, so all its blocks are resident; an
@@ -384,9 +384,8 @@ __global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, S
     __shared__ float sF[kCuMaxBlocks];
     __shared__ float s_rho, s_eta;
     __shared__ int is_last;
-    const float* __restrict__ sdf = B.sdf;
     const float4* __restrict__ noise = B.noise;
-    const float* __restrict__ parts_in = B.parts;
+    const float* parts_in = B.parts;             // also written below (J_col of the MLP modes)
     pdl_wait();
     const int K = P.K, H = P.H;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -406,40 +405,30 @@ __global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, S
         pre_b[u] = (i < nk && lane + 32 < H) ? __ldcs(nrow + 32 + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 
-    // 1. costs: one warp per rollout (the horizon across the lanes), kCuBatch rollouts at a time
+    // 1. costs: one thread per rollout.  MLP modes: J_col = w_col (or Q_sdf) times the sum of the
+    //    rollout's per-tile partial sums of the stage hinge, which the SDF kernel folded in its
+    //    epilogue (fold_store), added in tile order
     float mloc = inf;
-    for (int i0 = wid; i0 < nk; i0 += kCuWarps * kCuBatch) {
-        float acc[kCuBatch], pj[kCuBatch], pc[kCuBatch], pcol[kCuBatch];
-#pragma unroll
-        for (int u = 0; u < kCuBatch; ++u) {
-            const int i = i0 + u * kCuWarps;
-            const int k = k0 + (i < nk ? i : 0);
-            acc[u] = 0.f;
-            pcol[u] = 0.f;
-            if (mlp) {
-                const float* srow = sdf + static_cast<size_t>(k) * H;
-                const float s0 = (lane < H) ? __ldcs(srow + lane) : inf;
-                const float s1 = (lane + 32 < H) ? __ldcs(srow + lane + 32) : inf;
-                acc[u] = stage_hinge(s0, P.d_safe, P.paper) + stage_hinge(s1, P.d_safe, P.paper);
-                for (int h = lane + 64; h < H; h += 32) acc[u] += stage_hinge(__ldcs(srow + h), P.d_safe, P.paper);
-            } else {
-                pcol[u] = parts_in[k];
-            }
-            pj[u] = parts_in[K + k];
-            pc[u] = parts_in[2 * K + k];
+    const int n_colp = col_slots(H);
+    for (int i = threadIdx.x; i < nk; i += kCuThreads) {
+        const int k = k0 + i;
+        float jcol;
+        if (mlp) {
+            const int t0 = (k * H) / kTileRows;
+            const int n = (k * H + H - 1) / kTileRows - t0 + 1;
+            const float* cp = B.colp + static_cast<size_t>(k) * n_colp;
+            float a = __ldcs(cp);
+            for (int j = 1; j < n; ++j) a += __ldcs(cp + j);
+            jcol = (P.paper ? P.q_sdf : P.w_col) * a;
+            B.parts[k] = jcol;
+        } else {
+            jcol = parts_in[k];
         }
-#pragma unroll
-        for (int u = 0; u < kCuBatch; ++u) {
-            const int i = i0 + u * kCuWarps;
-            const float jcol = mlp ? (P.paper ? P.q_sdf : P.w_col) * warp_sum(acc[u]) : pcol[u];
-            if (i < nk) {
-                const float J = jcol + pj[u] + pc[u];
-                if (lane == 0) sE[i] = J;
-                if (mlp && lane == 1) B.parts[k0 + i] = jcol;
-                mloc = fminf(mloc, J);
-            }
-        }
+        const float J = jcol + parts_in[K + k] + parts_in[2 * K + k];
+        sE[i] = J;
+        mloc = fminf(mloc, J);
     }
+    mloc = warp_min(mloc);
     if (lane == 0) sWarp[wid] = mloc;
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -32,6 +32,7 @@ struct mppi_ctx {
     bool have_weights = false;
     bool have_latents = false;
     bool timing = false;
+    bool store_sdf = false;       // MPPI_DIAG_STORE_SDF
     uint64_t step_count = 0;
     char err[512] = "";
 
@@ -144,6 +145,7 @@ StepParams make_params(const mppi_ctx* c) {
     P.J = make_float3(g.inertia_x, g.inertia_y, g.inertia_z);
     P.t_rotor_max = g.rotor_thrust_max;
     P.pe = g.pe_levels;
+    P.store_sdf = c->store_sdf ? 1 : 0;
     // per-kernel event timing measures kernels one after the other
     P.pdl = c->timing ? 0 : 1;
     return P;
@@ -468,6 +470,7 @@ int mppi_create(const mppi_config* cfg, void* cuda_stream, mppi_ctx** out) {
     rc = rc ? rc : dev_alloc(c, &B.pos, KH);
     rc = rc ? rc : dev_alloc(c, &B.parts, 3 * static_cast<size_t>(K));
     rc = rc ? rc : dev_alloc(c, &B.sdf, KH);
+    rc = rc ? rc : dev_alloc(c, &B.colp, static_cast<size_t>(K) * col_slots(H));
     rc = rc ? rc : dev_alloc(c, &B.J, K);
     rc = rc ? rc : dev_alloc(c, &B.w, K);
     rc = rc ? rc : dev_alloc(c, &B.unew, H);
@@ -734,6 +737,10 @@ int mppi_step(mppi_ctx* c, const float* state, const float* gate_poses, const fl
 int mppi_step_async(mppi_ctx* c, const float* d_state, const float* d_gate_poses, const float* d_latents,
                     const float* d_nominal, float* d_new_controls, float* d_weights, float* d_costs) {
     if (!c) return fail(nullptr, MPPI_E_INVALID, "ctx is NULL");
+    if (!d_new_controls) return fail(c, MPPI_E_INVALID, "d_new_controls is NULL");
+    // the update kernel stores U*_new as float4: a misaligned buffer is refused before anything is enqueued
+    if (reinterpret_cast<uintptr_t>(d_new_controls) % 16 != 0)
+        return fail(c, MPPI_E_INVALID, "d_new_controls must be 16-byte aligned");
     const int K = c->cfg.K, H = c->cfg.H, G = c->n_gates;
     if (d_state)
         CUDA_TRY(c, cudaMemcpyAsync(c->B.state, d_state, state_dim(c->cfg) * sizeof(float), cudaMemcpyDeviceToDevice,
@@ -801,7 +808,12 @@ int mppi_read_buffer(mppi_ctx* c, int which, float* host_out, size_t n) {
         case MPPI_BUF_NOISE: src = c->B.noise; count = H * K * 4; break;
         case MPPI_BUF_POSITIONS: src = c->B.pos; count = H * K * 4; break;
         case MPPI_BUF_COST_PARTS: src = c->B.parts; count = 3 * K; break;
-        case MPPI_BUF_SDF: src = c->B.sdf; count = H * K; break;
+        case MPPI_BUF_SDF:
+            if (!c->store_sdf)
+                return fail(c, MPPI_E_INVALID, "MPPI_BUF_SDF is written only with MPPI_DIAG_STORE_SDF set");
+            src = c->B.sdf;
+            count = H * K;
+            break;
         case MPPI_BUF_WEIGHTS: src = c->B.w; count = K; break;
         case MPPI_BUF_COSTS: src = c->B.J; count = K; break;
         default: return fail(c, MPPI_E_INVALID, "unknown buffer %d", which);
@@ -824,6 +836,15 @@ int mppi_read_noise_words(mppi_ctx* c, uint32_t* host_out, size_t n) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cudaFree(tmp);
     if (e != cudaSuccess) return fail(c, MPPI_E_CUDA, "noise words: %s", cudaGetErrorString(e));
+    return MPPI_OK;
+}
+
+int mppi_set_diagnostics(mppi_ctx* c, int flags) {
+    if (!c) return fail(nullptr, MPPI_E_INVALID, "ctx is NULL");
+    if (flags & ~MPPI_DIAG_STORE_SDF) return fail(c, MPPI_E_INVALID, "unknown diagnostics flags 0x%x", flags);
+    const bool store = (flags & MPPI_DIAG_STORE_SDF) != 0;
+    if (c->store_sdf != store) c->graph_dirty = true;
+    c->store_sdf = store;
     return MPPI_OK;
 }
 
@@ -961,8 +982,9 @@ int ctx_restore(mppi_ctx* c, const float* nominal, const float* state, uint64_t 
 size_t ctx_device_bytes(const mppi_config& g) {
     const size_t K = g.K, H = g.H, MG = g.max_gates;
     const size_t nub = static_cast<size_t>(update_blocks(g.K));
-    const size_t floats = 16 + 4 * H + 2 + MG * 8 + MG * kHidden + 4 * K * H * 2 + 3 * K + K * H + 2 * K + 4 * H +
-                          nub * (4 * H + 2) + 4 + 32 + 1 + MG * kLatent;
+    const size_t floats = 16 + 4 * H + 2 + MG * 8 + MG * kHidden + 4 * K * H * 2 + 3 * K + K * H +
+                          K * static_cast<size_t>(col_slots(g.H)) + 2 * K + 4 * H + nub * (4 * H + 2) + 4 + 32 + 1 +
+                          MG * kLatent;
     const size_t weights = sizeof(float) * (kHidden * (point_features(g) + kLatent) + kHidden +
                                             3 * (kHidden * kHidden + kHidden) + kHidden) +
                            3 * kHidden * kHidden * (2 + 2 + 1) + static_cast<size_t>(kHidden) * layer1_k(g) * 2;

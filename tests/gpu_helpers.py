@@ -43,7 +43,7 @@ def flat_layers(layers):
 class GpuController:
     """One library context set up from a workload dict (see ``workloads``)."""
 
-    def __init__(self, wl, mode, prm=None, stream=None, max_gates=None, fp8_scales=None):
+    def __init__(self, wl, mode, prm=None, stream=None, max_gates=None, fp8_scales=None, store_sdf=True):
         self.prm = dict(prm if prm is not None else wl["params"])
         poses = np.ascontiguousarray(wl["poses"], dtype=np.float32).reshape(-1, 7)
         self.G = poses.shape[0]
@@ -56,6 +56,9 @@ class GpuController:
             self._scales = None if fp8_scales is None else np.ascontiguousarray(fp8_scales, dtype=np.float32)
             B.mppi_set_sdf_weights(self.ctx, self._keep, self._scales)
         B.mppi_set_gates(self.ctx, self.G, poses if self.G else None, lat if self.G else None)
+        # tests read s(p) of every rollout state: the SDF kernel stores it beside its cost fold
+        if store_sdf and mode != "analytic":
+            B.mppi_set_diagnostics(self.ctx, B.MPPI_DIAG_STORE_SDF)
         self.K, self.H = self.prm["K"], self.prm["H"]
 
     def close(self):

@@ -5,8 +5,8 @@ warm start; the FP64 oracle computes that step once for every rollout.  The
 FP32 path must meet the FP32 tolerances of the parity tests (per-rollout cost
 1e-4 relative, controls 1e-4 absolute, SDF 2e-5 m); the BF16, FP16 and E4M3
 tensor-core paths report SDF error (mm), cost relative error and control
-absolute error, bounded loosely (a layout or scale mistake gives errors of
-metres).
+absolute error, held to bounds just above the measured errors (FP16, the chosen
+16-bit form, well inside the 2 mm target at p99).
 """
 import numpy as np
 import pytest
@@ -29,7 +29,9 @@ def four_gates():
     return wl, ref
 
 
-BOUNDS = {"fp32": None, "fp16": (1.0, 5.0), "bf16": (10.0, 60.0), "fp8": (60.0, 400.0)}
+# (MAE mm, p99 mm, max mm) above the measured MAE / p99 (FP16 0.097 / 0.31, BF16 1.21 / 3.04, E4M3
+# 10.4 / 35.8); FP16, the chosen 16-bit form, also meets the 2 mm target at p99
+BOUNDS = {"fp32": None, "fp16": (0.15, 0.45, 1.0), "bf16": (1.5, 3.5, 7.0), "fp8": (15.0, 50.0, 150.0)}
 
 
 @pytest.mark.parametrize("mode", ["fp32", "fp16", "bf16", "fp8"])
@@ -48,7 +50,7 @@ def test_four_gates_K16384_H64(lib, four_gates, mode):
             assert np.all(cerr <= COST_RTOL * cost_scale(ref) + 1e-7), cerr.max()
             np.testing.assert_allclose(out["U_new"], ref["U_new"], atol=CTRL_ATOL, rtol=0)
         else:
-            mae, mx = BOUNDS[mode]
-            assert err["sdf_mae_mm"] < mae and err["sdf_max_mm"] < mx, err
+            mae, p99, mx = BOUNDS[mode]
+            assert err["sdf_mae_mm"] < mae and err["sdf_p99_mm"] < p99 and err["sdf_max_mm"] < mx, err
     finally:
         g.close()

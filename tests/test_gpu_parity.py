@@ -8,9 +8,12 @@ Tolerances (stated once, used throughout):
 * Costs (FP32 paths): |J_gpu - J| <= 1e-4 * (|J_col| + |J_prog| + |J_ctl|) per rollout,
   i.e. 1e-4 relative to the magnitude of the summed terms.
 * Updated controls (FP32 paths): |U*_gpu - U*| <= 1e-4 absolute (N, rad/s).
-* BF16 path: SDF error (mm), cost and control errors are reported; the test
-  only bounds them loosely (a layout or descriptor bug gives errors of 100s of mm).
-* FP16 path: SDF error within 2 mm at p99 (and MAE < 1 mm) at the full size.
+* FP16 path (the chosen 16-bit form): SDF error within the 2 mm target at p99 at the full size,
+  plus regression bounds just above what it measures (MAE 0.10 mm, p99 0.31 mm, max 0.52 mm,
+  controls 2.3e-2): MAE < 0.15 mm, p99 < 0.45 mm, max < 0.8 mm, controls < 0.1.
+* BF16 path: its 8-bit mantissa misses the 2 mm target at p99 (MAE 1.24 mm, p99 3.06 mm, max
+  4.5 mm, controls 0.53-0.88 measured); the test holds it to MAE < 1.5 mm, p99 < 3.5 mm,
+  max < 6 mm, cost rel < 0.06 and controls < 1.5.
 """
 import json
 import os
@@ -307,6 +310,41 @@ def test_closed_loop_mlp_fp32_teacher_forced(lib):
     g.close()
 
 
+# ---------------------------------------------------------------- collision-cost fold in the SDF epilogue
+@pytest.mark.parametrize("mode", ["fp32", "fp16"])
+@pytest.mark.parametrize("K,H", [(513, 1), (300, 6), (257, 129), (100, 300)])
+def test_cost_fold_without_sdf_store(lib, mode, K, H):
+    """The SDF kernels fold the collision cost per rollout in their epilogue (Eq. 8-10) and store
+    s(p) only as a diagnostic: costs, weights and controls are bit-identical with and without the
+    store, and the FP32 path meets the oracle, for horizons whose rollouts span 1 to 4 SDF tiles
+    (H = 1: 128 rollouts per tile; H = 300: up to four tiles per rollout)."""
+    wl = W.two_gate_mlp()
+    prm = _params(wl, K=K, H=H)
+    nominal = W.hover_nominal(H)
+    runs = []
+    for store in (False, True):
+        g = GpuController(wl, mode, prm, store_sdf=store)
+        try:
+            out = g.step(state=wl["state"], nominal=nominal)
+            runs.append((out, g.read(B.MPPI_BUF_COST_PARTS)))
+            if not store:
+                with pytest.raises(B.MppiError):          # the diagnostic buffer was not written
+                    g.read(B.MPPI_BUF_SDF)
+        finally:
+            g.close()
+    (a, pa), (b, pb) = runs
+    for key in ("U_new", "weights", "J"):
+        np.testing.assert_array_equal(a[key], b[key])
+    np.testing.assert_array_equal(pa, pb)
+    ref = _oracle(wl, prm, wl["state"], nominal, 0, True)
+    assert np.all(ref["J_col"] > 0)                      # every rollout's hinge is active: the fold is exercised
+    if mode == "fp32":
+        _check_costs(a["J"], ref)
+        scale = cost_scale(ref) + 1e-7
+        assert np.all(np.abs(pa[0] - ref["J_col"]) <= COST_RTOL * scale)
+        np.testing.assert_allclose(a["U_new"], ref["U_new"], atol=CTRL_ATOL, rtol=0)
+
+
 # ---------------------------------------------------------------- Gate-SDF MLP, BF16 tensor-core path
 def _bf16_errors(g, ref, out):
     s = g.read(B.MPPI_BUF_SDF).astype(np.float64)
@@ -327,7 +365,7 @@ def test_step_mlp_bf16_small(lib, K, H):
     np.testing.assert_allclose(pos, ref["positions"], atol=POS_ATOL, rtol=0)
     err = _bf16_errors(g, ref, out)
     _report(f"bf16_K{K}_H{H}", err)
-    assert err["sdf_mae_mm"] < 10.0 and err["sdf_max_mm"] < 60.0, err
+    assert err["sdf_mae_mm"] < 1.5 and err["sdf_max_mm"] < 6.0, err
     g.close()
 
 
@@ -339,7 +377,8 @@ def test_step_mlp_bf16_full_size_two_gates(lib):
     ref = _oracle(wl, wl["params"], wl["state"], wl["nominal"], 0, True)
     err = _bf16_errors(g, ref, out)
     _report("bf16_full_size", err)
-    assert err["sdf_mae_mm"] < 10.0, err
+    assert err["sdf_mae_mm"] < 1.5 and err["sdf_p99_mm"] < 3.5 and err["sdf_max_mm"] < 6.0, err
+    assert err["cost_rel_max"] < 0.06 and err["control_abs_max"] < 1.5, err
     assert abs(float(out["weights"].astype(np.float64).sum()) - 1.0) < 1e-5
     g.close()
 
@@ -356,7 +395,7 @@ def test_step_mlp_fp16_small(lib, K, H):
     np.testing.assert_allclose(pos, ref["positions"], atol=POS_ATOL, rtol=0)
     err = _bf16_errors(g, ref, out)
     _report(f"fp16_K{K}_H{H}", err)
-    assert err["sdf_mae_mm"] < 1.0 and err["sdf_max_mm"] < 5.0, err
+    assert err["sdf_mae_mm"] < 0.15 and err["sdf_max_mm"] < 0.8, err
     g.close()
 
 
@@ -368,7 +407,9 @@ def test_step_mlp_fp16_full_size_two_gates(lib):
     ref = _oracle(wl, wl["params"], wl["state"], wl["nominal"], 0, True)
     err = _bf16_errors(g, ref, out)
     _report("fp16_full_size", err)
-    assert err["sdf_mae_mm"] < 1.0 and err["sdf_p99_mm"] < 2.0, err
+    assert err["sdf_p99_mm"] <= 2.0, err                  # the 16-bit form's SDF target
+    assert err["sdf_mae_mm"] < 0.15 and err["sdf_p99_mm"] < 0.45 and err["sdf_max_mm"] < 0.8, err
+    assert err["control_abs_max"] < 0.1, err
     g.close()
 
 
