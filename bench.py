@@ -291,27 +291,13 @@ def e2e_loop(torch, B, ctx, wl, steps, flush):
     return np.array(out), 13 * 4, H * 4 * 4 + 4
 
 
-def serving_leg(torch, B, dev, duration_s, n_drones=64, rate_hz=100.0):
-    """64 drones, each a Poisson request stream at rate_hz, per-drone K in {1024..8192},
-    H in {30, 50, 80}, 1-4 gates, BF16 SDF, through the serving engine; plus the same
-    requests' solve time alone in the plain FP32 path (a sample of drone configurations)."""
-    import workloads as W
-    fleet = W.serving_fleet(n_drones)
-    keep = []
-    for Wm, b in W.xavier_mlp(1):
-        keep += [np.ascontiguousarray(Wm, np.float32), np.ascontiguousarray(b, np.float32)]
-    cfgs = []
-    for d in fleet:
-        c = B.mppi_config_default()
-        for key in ("K", "H", "dt", "mass", "gravity", "thrust_min", "thrust_max", "rate_max", "sigma_thrust",
-                    "sigma_rate", "w_col", "d_safe", "w_u", "seed", "drone_id"):
-            setattr(c, key, d["params"][key])
-        c.lam = d["params"]["lam"]
-        c.max_gates = d["G"]
-        cfgs.append(c)
+def _serve(B, fleet, cfgs, keep, arrivals, duration_s, batching, max_inflight, mode):
+    """Replay Poisson arrivals through one server (after one warm-up request per drone); returns
+    achieved and offered rollout-steps/s, submit-to-result latency percentiles and batch counts."""
     scfg = B.mppi_server_config_default()
-    scfg.max_inflight = 32
-    scfg.sdf_mode = B.MPPI_SDF_MLP_BF16
+    scfg.max_inflight = max_inflight
+    scfg.sdf_mode = mode
+    scfg.batching = batching
     srv = B.mppi_server_create(scfg)
     B.mppi_server_set_sdf_weights(srv, keep)
     inputs = [(np.ascontiguousarray(d["state"], np.float32), np.ascontiguousarray(d["poses"]),
@@ -322,14 +308,14 @@ def serving_leg(torch, B, dev, duration_s, n_drones=64, rate_hz=100.0):
         st, po, la = inputs[i]
         return B.mppi_server_submit(srv, fleet[i]["drone_id"], cfgs[i], st, fleet[i]["G"], po, la)
 
-    # warm-up: one request per drone creates its context and captures its step graph
-    for i in range(n_drones):
+    # warm-up: one request per drone creates its context (per-drone mode: captures its step graph)
+    for i in range(len(fleet)):
         submit(i)
     got = 0
-    while got < n_drones:
+    while got < len(fleet):
         rc, _, _ = B.mppi_server_next_result(srv, out)
         got += rc == B.MPPI_OK
-    arrivals = W.poisson_arrivals(n_drones, rate_hz, duration_s)
+    b0 = B.mppi_server_get_stats(srv)["batches"]
     owner, lat, kh = {}, [], 0
     i, done = 0, 0
     t0 = time.perf_counter()
@@ -348,12 +334,49 @@ def serving_leg(torch, B, dev, duration_s, n_drones=64, rate_hz=100.0):
     stats = B.mppi_server_get_stats(srv)
     B.mppi_server_destroy(srv)
     offered = sum(fleet[d]["params"]["K"] * fleet[d]["params"]["H"] for _, d in arrivals) / duration_s
-    # the same solves alone, one at a time, in the plain FP32 path (device time per configuration)
+    lat = np.array(lat) / 1e3
+    return {"offered_rollout_steps_per_s": offered, "achieved_rollout_steps_per_s": kh / wall,
+            "requests": len(arrivals), "wall_s": wall, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "batches": int(stats["batches"] - b0) if batching else None,
+            "evictions": int(stats["evictions"]), "peak_device_bytes": int(stats["peak_device_bytes"])}
+
+
+def serving_leg(torch, B, dev, duration_s, n_drones=64, rate_hz=100.0, loads=(1, 2, 4, 8)):
+    """64 drones, each a Poisson request stream at rate_hz, per-drone K in {1024..8192}, H in {30,
+    50, 80}, 1-4 gates, SDF in the headline 16-bit form, through the serving engine -- batched
+    launches and, for comparison, one step graph per drone -- at 1x, 2x, 4x and 8x that rate
+    (beyond the GPU's capacity the queue grows, latency with it, and the achieved rate is the
+    engine's capacity); plus every drone configuration's solve alone in the plain FP32 path."""
+    import workloads as W
+    fleet = W.serving_fleet(n_drones)
+    keep = []
+    for Wm, b in W.xavier_mlp(1):
+        keep += [np.ascontiguousarray(Wm, np.float32), np.ascontiguousarray(b, np.float32)]
+    cfgs = []
+    for d in fleet:
+        c = B.mppi_config_default()
+        for key in ("K", "H", "dt", "mass", "gravity", "thrust_min", "thrust_max", "rate_max", "sigma_thrust",
+                    "sigma_rate", "w_col", "d_safe", "w_u", "seed", "drone_id"):
+            setattr(c, key, d["params"][key])
+        c.lam = d["params"]["lam"]
+        c.max_gates = d["G"]
+        cfgs.append(c)
+    mode = {"fp16": B.MPPI_SDF_MLP_FP16, "bf16": B.MPPI_SDF_MLP_BF16}[HEADLINE_MODE]
+    sweep = []
+    for mult in loads:
+        arrivals = W.poisson_arrivals(n_drones, rate_hz * mult, duration_s, seed=5 + mult)
+        point = {"load": mult, "rate_hz_per_drone": rate_hz * mult}
+        for name, batching in (("batched", 1), ("per_drone_graphs", 0)):
+            point[name] = _serve(B, fleet, cfgs, keep, arrivals, duration_s, batching, 64, mode)
+        sweep.append(point)
+    # every distinct drone configuration alone, one solve at a time, in the plain FP32 path
     t32 = {}
-    for d, c in list(zip(fleet, cfgs))[:8]:
+    for d, c in zip(fleet, cfgs):
+        key = (d["params"]["K"], d["params"]["H"], d["G"])
+        if key in t32:
+            continue
         c32 = B.mppi_config_default()
-        ctypes_copy = [f for f, _ in B.MppiConfig._fields_]
-        for f in ctypes_copy:
+        for f, _ in B.MppiConfig._fields_:
             setattr(c32, f, getattr(c, f))
         c32.sdf_mode = B.MPPI_SDF_MLP_FP32
         ctx = B.mppi_create(c32, torch.cuda.current_stream().cuda_stream)
@@ -361,24 +384,26 @@ def serving_leg(torch, B, dev, duration_s, n_drones=64, rate_hz=100.0):
         B.mppi_set_gates(ctx, d["G"], np.ascontiguousarray(d["poses"]), np.ascontiguousarray(d["latents"]))
         U = torch.zeros(d["params"]["H"], 4, device=dev)
         st = torch.from_numpy(np.ascontiguousarray(d["state"], np.float32)).to(dev)
-        for _ in range(2):
-            B.mppi_step_async(ctx, st, None, None, None, U, None, None)
+        B.mppi_step_async(ctx, st, None, None, None, U, None, None)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         ev[0].record()
-        for _ in range(3):
+        for _ in range(2):
             B.mppi_step_async(ctx, st, None, None, None, U, None, None)
         ev[1].record()
         torch.cuda.synchronize()
-        t32[(d["params"]["K"], d["params"]["H"], d["G"])] = ev[0].elapsed_time(ev[1]) / 3
+        t32[key] = ev[0].elapsed_time(ev[1]) / 2
         B.mppi_destroy(ctx)
-    fp32_kh_per_ms = np.mean([k * h / t for (k, h, g), t in t32.items()])
-    lat = np.array(lat)
-    return {"drones": n_drones, "rate_hz_per_drone": rate_hz, "requests": len(arrivals), "duration_s": duration_s,
-            "offered_rollout_steps_per_s": offered, "value": kh / wall, "unit": UNIT,
-            "p50_ms": float(np.percentile(lat, 50) / 1e3), "p99_ms": float(np.percentile(lat, 99) / 1e3),
-            "max_inflight": scfg.max_inflight, "sdf": "bf16", "evictions": stats["evictions"],
-            "peak_device_bytes": stats["peak_device_bytes"],
-            "fp32_alone": {"rollout_steps_per_s": fp32_kh_per_ms * 1e3,
+    # the fleet's solves one after another in the FP32 path: rollout-steps over the summed solve time
+    fp32_rate = sum(d["params"]["K"] * d["params"]["H"] for d in fleet) / (
+        1e-3 * sum(t32[(d["params"]["K"], d["params"]["H"], d["G"])] for d in fleet))
+    base = sweep[0]["batched"]
+    return {"drones": n_drones, "rate_hz_per_drone": rate_hz, "duration_s": duration_s, "sdf": HEADLINE_MODE,
+            "max_inflight": 64, "offered_rollout_steps_per_s": base["offered_rollout_steps_per_s"],
+            "value": base["achieved_rollout_steps_per_s"], "unit": UNIT, "p50_ms": base["p50_ms"],
+            "p99_ms": base["p99_ms"], "sweep": sweep,
+            "capacity_rollout_steps_per_s": {n: max(p[n]["achieved_rollout_steps_per_s"] for p in sweep)
+                                             for n in ("batched", "per_drone_graphs")},
+            "fp32_alone": {"rollout_steps_per_s": fp32_rate, "configurations": len(t32),
                            "solve_ms_by_config": {f"K{k}_H{h}_G{g}": t for (k, h, g), t in t32.items()}}}
 
 

@@ -623,53 +623,71 @@ int mppi_train_num_params(void);
 
 /* ======================================================================== serving
  * Continuous batching of control steps from many drones (one request = one
- * control step of one drone).  Each drone keeps a context on the device: its
- * warm-started nominal sequence, true state and Philox step counter persist
- * between its requests (the same chain as mppi_step), so a drone's results do
- * not depend on which other drones share the GPU.  Requests are admitted in
+ * control step of one drone).  The paper runs one MPPI controller per vehicle at a
+ * fixed control rate (Sec. IV-A, Sec. V); serving many vehicles' controllers from
+ * one GPU has no counterpart in the paper.  Each drone keeps a context on the
+ * device: its warm-started nominal sequence, true state and Philox step counter
+ * persist between its requests (the same chain as mppi_step), so a drone's results
+ * do not depend on which other drones share the GPU.  Requests are admitted in
  * arrival order as soon as the drone has no request in flight, fewer than
  * max_inflight requests run and the drone's context fits in the device-memory
- * budget; the least recently used idle drone is evicted to host memory (its
- * warm start, state and counter are restored on its next request) when it does
- * not.  Requests of different drones run concurrently, each on its drone's own
- * stream.  All functions are thread-safe; a worker thread owned by the server
- * issues the GPU work.
+ * budget; the least recently used idle drone is evicted to host memory (its warm
+ * start, state and counter are restored on its next request) when it does not.
+ * Batched mode (batching = 1): every admissible queued request joins one batch,
+ * launched as four kernels on the server's stream (inputs, one rollout launch over
+ * all drones, one persistent tensor-core SDF launch whose tiles span all drones,
+ * one update launch), while the next batch is gathered; each drone's results equal
+ * those of its own mppi_step.  Per-drone mode (batching = 0): each request is its
+ * drone's captured step graph on the drone's own stream, and requests of different
+ * drones overlap on the GPU.  All functions are thread-safe; a worker thread owned
+ * by the server issues the GPU work.
  */
 typedef struct mppi_server mppi_server;
 
 typedef struct mppi_server_config {
     size_t hbm_budget_bytes;   /* device bytes the drone contexts may hold together; 0 = no limit */
-    int32_t max_inflight;      /* requests on the device at once (1 .. 1024) */
+    int32_t max_inflight;      /* requests on the device at once (1 .. 1024); in batched mode also the
+                                  largest batch */
     int32_t sdf_mode;          /* MPPI_SDF_* used by every drone */
+    int32_t batching;          /* 1: batched launches (every drone then shares softplus_beta and
+                                  pe_levels); 0: one step graph per drone */
 } mppi_server_config;
 
 typedef struct mppi_server_stats {
     uint64_t submitted, completed, queued, inflight;
     uint64_t evictions, restores;      /* drone contexts moved to host memory / brought back */
     size_t device_bytes, peak_device_bytes;
+    uint64_t batches;                  /* batched mode: batches launched */
 } mppi_server_stats;
 
-/* Defaults: no budget, 16 requests in flight, BF16 tensor-core SDF. */
+/* Defaults: no budget, 16 requests in flight, FP16 tensor-core SDF, batched launches. */
 void mppi_server_config_default(mppi_server_config* cfg);
-/* Create a server on the current device (starts its worker thread).  *out is NULL on error. */
+/* Create a server on the current device (starts its worker thread; batched mode also allocates two
+ * pinned and two device batch blocks of max_inflight controllers each).  *out is NULL on error:
+ * MPPI_E_INVALID (cfg), MPPI_E_UNSUPPORTED (no device), MPPI_E_OOM. */
 int mppi_server_create(const mppi_server_config* cfg, mppi_server** out);
 /* Drain in-flight work, stop the worker and free every drone context.  NULL is ignored. */
 void mppi_server_destroy(mppi_server* server);
-/* Message of the server's last error (server NULL: the calling thread's last failed create). */
+/* Message of the server's last error (server NULL: the calling thread's last failed create); owned by
+ * the server, valid until its next failing call. */
 const char* mppi_server_last_error(const mppi_server* server);
-/* Gate-SDF MLP weights for every drone (same arrays as mppi_set_sdf_weights); call before the first request. */
+/* Gate-SDF MLP weights (Sec. III-B, Fig. 2) for every drone (same arrays as mppi_set_sdf_weights); call
+ * before the first request. */
 int mppi_server_set_sdf_weights(mppi_server* server, const float* const* layers, int n_layers,
                                 const float* fp8_scales);
 /*
- * Queue one control step of drone drone_id (host buffers, copied before the
- * call returns): cfg gives the drone's controller parameters (K, H and
- * max_gates must stay the same for a drone; the server's sdf_mode applies),
- * state mppi_state_dim(cfg) floats, n_gates gate poses (n x 7) and latents (n x 64; NULL in
- * analytic mode).  *ticket identifies the request.  Returns at once.
+ * Queue one control step (Sec. IV-A, Eq. 5 and its receding-horizon update) of drone drone_id
+ * (host buffers, copied before the call returns): cfg gives the drone's controller parameters
+ * (K, H and max_gates must stay the same for a drone; the server's sdf_mode applies; in batched
+ * mode softplus_beta and pe_levels must match the server's other drones), state
+ * mppi_state_dim(cfg) floats, n_gates gate poses (n x 7) and latents (n x 64; NULL in analytic
+ * mode).  *ticket identifies the request.  Returns at once.  Errors: MPPI_E_INVALID,
+ * MPPI_E_NOT_READY (no weights set); MPPI_E_ADMISSION is reported through the ticket.
  */
 int mppi_server_submit(mppi_server* server, int drone_id, const mppi_config* cfg, const float* state, int n_gates,
                        const float* poses, const float* latents, uint64_t* ticket);
 /*
+ * Result of one request (the new control sequence U*_new of Eq. 5).
  * Non-blocking: MPPI_PENDING while the request is queued or running; once it
  * is done, its status (MPPI_OK with new_controls = U*_new, H x 4, filled; or
  * the error of that request) and latency_us = submit-to-completion time in
@@ -683,7 +701,8 @@ int mppi_server_poll(mppi_server* server, uint64_t ticket, float* new_controls, 
  */
 int mppi_server_next_result(mppi_server* server, uint64_t* ticket, float* new_controls, size_t cap_floats,
                             double* latency_us);
-/* Counters of the server (submitted, completed, queued, in flight, evictions, restores, device bytes). */
+/* Counters of the server (submitted, completed, queued, in flight, evictions, restores, device bytes,
+ * batches launched; no counterpart in the paper). */
 int mppi_server_get_stats(mppi_server* server, mppi_server_stats* out);
 
 #ifdef __cplusplus

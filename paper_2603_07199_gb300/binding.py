@@ -93,13 +93,14 @@ class MppiConfig(ctypes.Structure):
 
 
 class MppiServerConfig(ctypes.Structure):
-    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32), ("sdf_mode", ctypes.c_int32)]
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32), ("sdf_mode", ctypes.c_int32),
+                ("batching", ctypes.c_int32)]
 
 
 class MppiServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("queued", ctypes.c_uint64),
                 ("inflight", ctypes.c_uint64), ("evictions", ctypes.c_uint64), ("restores", ctypes.c_uint64),
-                ("device_bytes", ctypes.c_size_t), ("peak_device_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("peak_device_bytes", ctypes.c_size_t), ("batches", ctypes.c_uint64)]
 
 
 class MppiTrainConfig(ctypes.Structure):

@@ -364,42 +364,31 @@ __device__ __forceinline__ float stage_hinge(float s, float d_safe, int paper) {
     return paper ? e : e * e;
 }
 
-// ---------------------------------------------------------------- collision-cost fold of an SDF tile
-// The SDF kernels fold the stage hinge of Eq. 8 over the horizon inside their epilogue (Eq. 9-10:
-// J_col of a rollout is a sum over its states) instead of storing s(p) for every state.  Rollout
-// k owns rows k H .. k H + H - 1 of the [K][H] state array, which touch the 128-row tiles
-// floor(k H / 128) .. floor((k H + H - 1) / 128): at most col_slots(H) of them.  Tile t writes
-// the sum over its rows of rollout k to colp[k][t - floor(k H / 128)]; the cost kernel adds a
-// rollout's slots in tile order, so every sum runs in a fixed order.
-__host__ __device__ inline int col_slots(int H) { return (H + 126) / kTileRows + 1; }
+// ---------------------------------------------------------------- collision-cost fold in the SDF kernels
+// The SDF kernels fold the stage hinge of Eq. 8 over the horizon in their epilogue (Eq. 9-10:
+// J_col of a rollout is a sum over its states) instead of storing s(p) for every state.  The
+// rows of the [K][H] state array are folded 32 at a time (one row per lane of a warp): rollout
+// k owns rows k H .. k H + H - 1, which touch the 32-row segments floor(k H / 32) ..
+// floor((k H + H - 1) / 32), at most col_slots(H) of them; segment w writes the sum over its
+// rows of rollout k to colp[k][w - floor(k H / 32)].  The cost kernel adds a rollout's slots in
+// segment order, so every sum runs in a fixed order.
+__host__ __device__ inline int col_slots(int H) { return (H + 30) / 32 + 1; }
 
-// Step 1, run by each of the four warps that hold a tile's rows (local row = 32 warp + lane,
-// global row r, stage cost c, 0 for rows past the end): an inclusive scan over the warp's rows
-// that restarts at every rollout boundary; the last row of each run leaves the run's sum in
-// seg[local row].
-__device__ __forceinline__ void fold_warp_runs(float c, int r, int H, int lane, float* seg) {
+// One warp, 32 consecutive rows r (one per lane, stage cost c, 0 for rows past the end): an
+// inclusive scan that restarts at every rollout boundary; the last row of each run in the warp
+// stores the run's sum.
+__device__ __forceinline__ void fold_warp(float c, int r, int n_rows, int H, int lane, float* colp) {
+    const unsigned full = 0xffffffffu;
     const int key = r / H;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const float t = __shfl_up_sync(0xffffffffu, c, d);
-        const int kk = __shfl_up_sync(0xffffffffu, key, d);
+        const float t = __shfl_up_sync(full, c, d);
+        const int kk = __shfl_up_sync(full, key, d);
         if (lane >= d && kk == key) c += t;
     }
-    const int knext = __shfl_down_sync(0xffffffffu, key, 1);
-    if (lane == 31 || knext != key) seg[r & (kTileRows - 1)] = c;
-}
-// Step 2, after a barrier over those warps: thread j adds the run sums of the tile's j-th rollout
-// over the warps in warp order and stores the tile's partial sum of that rollout.
-__device__ __forceinline__ void fold_store(const float* seg, int row0, int nvalid, int H, int tile, int j,
-                                           float* colp, int np) {
-    const int k = row0 / H + j;
-    const int last = row0 + nvalid - 1;
-    if (k > last / H) return;
-    const int lo = max(k * H, row0) - row0;
-    const int hi = min(k * H + H - 1, last) - row0;
-    float s = 0.f;
-    for (int w = lo >> 5; w <= (hi >> 5); ++w) s += seg[min(hi, 32 * w + 31)];
-    colp[static_cast<size_t>(k) * np + (tile - (k * H) / kTileRows)] = s;
+    const int knext = __shfl_down_sync(full, key, 1);
+    if ((lane == 31 || knext != key) && r < n_rows)
+        colp[static_cast<size_t>(key) * col_slots(H) + ((r >> 5) - ((key * H) >> 5))] = c;
 }
 
 // Index of the first gate whose plane the position p has not crossed (n_g . (p - t_g) < 0),

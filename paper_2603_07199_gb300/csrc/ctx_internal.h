@@ -21,4 +21,24 @@ int ctx_restore(mppi_ctx* c, const float* nominal, const float* state, uint64_t 
 // Device bytes a context of this configuration allocates.
 size_t ctx_device_bytes(const mppi_config& cfg);
 
+// ---- batched serving steps (the server's own stream launches the step kernels of many contexts)
+struct BatchSlot;
+struct MlpWeights;
+struct StepParams;
+// Prepare the context's next step for a batch: checks the inputs like ctx_enqueue_host_step, fills
+// the slot's parameters, buffers and pointers (outputs into the context's pinned staging) and packs
+// state, gate poses and latents into `in` from in[0] on.  Returns the floats written (> 0) or an error.
+int ctx_batch_slot(mppi_ctx* c, const float* state, int n_gates, const float* poses, const float* latents,
+                   BatchSlot* slot, float* in);
+// The step of the last batch slot of this context has been launched.
+void ctx_batch_launched(mppi_ctx* c);
+// After the batch completed: MPPI_OK with new_controls (H x 4) filled, or the step's error.
+int ctx_batch_result(mppi_ctx* c, float* new_controls);
+// Clear the context's device error word and barrier counter (after a timed-out batch).  Synchronous.
+int ctx_clear_error(mppi_ctx* c);
+// The context's SDF weights, parameters and device SM count (for the batched launches).
+MlpWeights ctx_weights(const mppi_ctx* c);
+StepParams ctx_params(const mppi_ctx* c);
+int ctx_num_sms(const mppi_ctx* c);
+
 }  // namespace mppi

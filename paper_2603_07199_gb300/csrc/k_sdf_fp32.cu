@@ -34,8 +34,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_fp32_kernel(StepParams P,
     float* sW5 = sBias + 3 * kHidden;               // [128]
     float* sPg = sW5 + kHidden;                     // [NP][128]  point features of the tile's rows
     float* sMin = sPg + kMaxPoint * kTileRows;      // [128]      min over gates
-    float* sFold = sMin + kTileRows;                // [128]      run sums of the collision-cost fold
-    float* sPose = sFold + kTileRows;               // [G][8]
+    float* sPose = sMin + kTileRows;                // [G][8]
 
     const int tid = threadIdx.x;
     const int G = P.G;
@@ -68,7 +67,6 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_fp32_kernel(StepParams P,
     // tile = 128 consecutive rollout states of the [K][H] position array
     const int n_rows = P.K * P.H;
     const int n_items = (n_rows + kTileRows - 1) / kTileRows;
-    const int n_colp = col_slots(P.H);              // partial-sum slots per rollout
 
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         if (tid < kTileRows) sMin[tid] = __int_as_float(0x7f800000);
@@ -178,18 +176,15 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_fp32_kernel(StepParams P,
         if (tid < kTileRows) {
             const int r = row0 + tid;
             if (P.store_sdf && r < n_rows) B.sdf[r] = sMin[tid];
-            const float c = r < n_rows ? stage_hinge(sMin[tid], P.d_safe, P.paper) : 0.f;
-            fold_warp_runs(c, r, P.H, tid & 31, sFold);
+            fold_warp(r < n_rows ? stage_hinge(sMin[tid], P.d_safe, P.paper) : 0.f, r, n_rows, P.H, tid & 31, B.colp);
         }
-        __syncthreads();
-        if (tid < kTileRows) fold_store(sFold, row0, min(kTileRows, n_rows - row0), P.H, item, tid, B.colp, n_colp);
         __syncthreads();
     }
 }
 
 constexpr size_t kSmemBytes = sizeof(float) * (kHidden * kLdA + kHidden * kHidden + kMaxPoint * kHidden +
                                                 kMaxGates * kHidden + 3 * kHidden + kHidden + kMaxPoint * kTileRows +
-                                                2 * kTileRows + kMaxGates * 8);
+                                                kTileRows + kMaxGates * 8);
 
 }  // namespace
 

@@ -9,9 +9,9 @@
 //   each followed by TMEM load -> (bias,) softplus -> 16-bit A tile (layers 1-3)
 //        or the FP32 output dot (layer 4)
 // and keeps the running minimum over gates in a register; the item ends by
-// folding the stage hinge of that minimum s(p) into per-rollout partial sums of
-// the collision cost (fold_warp_runs / fold_store; s(p) itself is stored only
-// for diagnostics).
+// summing the stage hinge of that minimum s(p) per rollout over 32-row segments
+// into partial sums of the collision cost (s(p) itself is stored only for
+// diagnostics).
 //
 // CTA = 3 tile groups of 8 warps.  A tile group owns one A tile (smem) and one
 // 128-column FP32 accumulator (TMEM); its warps w and w + 4 share TMEM lane
@@ -28,6 +28,7 @@
 // ln 2 / beta.  h is evaluated with one hardware exp2 and a quartic in
 // e = 2^-|y| (see kPolyDeg), in packed f32x2 (BF16) or f16x2 (FP16, E4M3) arithmetic.
 #include "kernels.h"
+#include "mppi.h"
 #include "tc.cuh"
 
 namespace mppi {
@@ -63,7 +64,6 @@ struct __align__(16) TcShared {
     float bias[3][kHidden];                   // c b2, c b3, c b4 (E4M3 path: added in the epilogue)
     float w5[kHidden];                        // (ln 2 / beta) w5
     float part[kGroups][kTileRows];           // output-layer partial sums of the upper column half
-    float fold[kGroups][kTileRows];           // run sums of the collision-cost fold (fold_warp_runs)
     float pose[kMaxGates][8];
     uint64_t acc_full[kGroups];               // MMA -> epilogue: accumulator ready
     uint32_t tmem_base;
@@ -253,8 +253,19 @@ __device__ __forceinline__ float from_operand16(uint16_t v) {
     }
 }
 
-template <int kFmt, bool kPE>
-__global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, StepBuffers B, MlpWeights W) {
+// The controllers of a batched launch (serving): tile t of the launch belongs to the slot whose
+// tiles [tile0, next tile0) hold it; every controller shares the weights and the softplus
+// sharpness.  Waits that time out set the batch's error word.
+struct BatchRef {
+    const BatchSlot* slots;
+    int n;          // controllers
+    int tiles;      // tiles of all of them
+    int* err;
+};
+
+template <int kFmt, bool kPE, bool kBatch>
+__global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, StepBuffers B, MlpWeights W,
+                                                                 BatchRef R) {
     constexpr bool kF16 = (kFmt == kFmtFP16);
     constexpr bool kF8 = (kFmt == kFmtE4M3);
     constexpr bool kFold = !kF8 && !kPE;           // hidden biases ride in the GEMM (bias operands)
@@ -265,7 +276,10 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
     TcShared& S = *reinterpret_cast<TcShared*>(smem_raw);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int G = P.G;
+    // one controller: its gates' poses and first-layer biases are staged in shared memory; a
+    // batched launch reads them per tile from the tile's controller
+    const int G = kBatch ? 0 : P.G;
+    int* const errw = kBatch ? R.err : B.err;
 
     // ---- set-up: TMEM, barriers, resident weights
     if (warp == 0) {
@@ -331,15 +345,14 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
     // the first CTAs a tile more in every group when the last round is partial)
     // gates queried: all (min over gates), or the target gate only (the paper's form)
     int g_lo = 0, g_hi = G;
-    if (P.paper) {
+    if (!kBatch && P.paper) {
         Vec3 n;
         const int t = target_gate(&S.pose[0][0], G, v3(B.state[0], B.state[1], B.state[2]), &n);
         g_lo = t < 0 ? 0 : t;
         g_hi = t < 0 ? 0 : t + 1;
     }
-    const int n_rows = P.K * P.H;
-    const int n_tiles = (n_rows + kTileRows - 1) / kTileRows;
-    const int n_colp = col_slots(P.H);           // partial-sum slots per rollout
+    int n_rows = P.K * P.H;
+    const int n_tiles = kBatch ? R.tiles : (n_rows + kTileRows - 1) / kTileRows;
     const int nslots = gridDim.x * kGroups;
     const int slot = blockIdx.x + static_cast<int>(gridDim.x) * (warp / kGroupWarps);
     volatile int* abort_flag = &S.abort_flag;
@@ -396,12 +409,37 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
         ++outstanding;
     };
 
+    // batched launches: c b1'_g of the tile's controller from global memory (the product the
+    // one-controller launch stages in shared memory, so both round the same way)
+    auto b1_4 = [&](const float* b1p, int g, int c) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(b1p + g * kHidden + c));
+        return make_float4(cl2 * v.x, cl2 * v.y, cl2 * v.z, cl2 * v.w);
+    };
+    // the tile's controller: the launch's, or (batched launches) the slot a cursor over the slots
+    // (ascending tiles) points to, whose fields are read where they are used
+    int cur = 0, ltile = 0;
+    const BatchSlot* sl = kBatch ? R.slots : nullptr;
     for (int tile = slot; tile < n_tiles && ok; tile += nslots) {
-        const int row0 = tile * kTileRows;
+        ltile = tile;
+        if constexpr (kBatch) {
+            while (cur + 1 < R.n && R.slots[cur + 1].tile0 <= tile) ++cur;
+            sl = R.slots + cur;
+            ltile = tile - sl->tile0;
+            n_rows = sl->P.K * sl->P.H;
+            g_lo = 0;
+            g_hi = sl->P.G;
+            if (sl->P.paper) {
+                Vec3 n;
+                const int t = target_gate(sl->B.poses, sl->P.G, v3(sl->B.state[0], sl->B.state[1], sl->B.state[2]), &n);
+                g_lo = t < 0 ? 0 : t;
+                g_hi = t < 0 ? 0 : t + 1;
+            }
+        }
+        const int row0 = ltile * kTileRows;
         const int nvalid = min(kTileRows, n_rows - row0);          // the last tile may be ragged
         const bool active = quad * 32 < nvalid;                   // this warp's quadrant has rows
         const int r = row0 + row;
-        const float4 p = B.pos[min(r, n_rows - 1)];
+        const float4 p = (kBatch ? sl->B.pos : B.pos)[min(r, n_rows - 1)];
         float smin = __int_as_float(0x7f800000);
         for (int g = g_lo; g < g_hi && ok; ++g) {
             // layer-1 A operand (K = 16): the gate-frame point split p = hi + lo in BF16,
@@ -409,7 +447,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
             // hi.W_hi + lo.W_hi + hi.W_lo (relative error ~2^-16); the latent's part
             // of the first layer is the per-gate bias of the epilogue
             if (half == 0 && active) {
-                const Vec3 pg = to_gate(S.pose[g], v3(p.x, p.y, p.z));
+                const Vec3 pg = to_gate(kBatch ? sl->B.poses + 8 * g : S.pose[g], v3(p.x, p.y, p.z));
                 const float hx = bf16_round(pg.x), hy = bf16_round(pg.y), hz = bf16_round(pg.z);
                 const float lx = pg.x - hx, ly = pg.y - hy, lz = pg.z - hz;
                 tc::st_shared_v4(a_base + tc::operand_offset_bytes(row, 0), tc::pack_bf16x2(hx, hy),
@@ -449,7 +487,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
             for (int l = 0; l < 4; ++l) {
                 // every thread of the group agrees on the outcome before going on, so a
                 // timeout seen by one thread cannot strand the others at a named barrier
-                const bool got = tc::mbar_wait_bounded(acc_bar, acc_phase, abort_flag, B.err, kDevErrTimeout);
+                const bool got = tc::mbar_wait_bounded(acc_bar, acc_phase, abort_flag, errw, kDevErrTimeout);
                 if (!tc::named_barrier_and(bar_id, kGroupThreads, got)) {
                     ok = false;
                     break;
@@ -467,7 +505,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                         const int cc = col0 + ch;
                         if (kF8 && l < 3) {
                             // y = D dequant + bias -> softplus (f16x2) -> / activation scale -> E4M3
-                            const float* bias = (l == 0) ? S.b1[g] : S.bias[l - 1];
+                            const float* bias = (l == 0) ? S.b1[kBatch ? 0 : g] : S.bias[l - 1];
                             const float dq = (l == 0) ? 1.f : W.f8_dequant[l - 1];
                             const uint64_t dq2 = pk(dq, dq);
                             const uint32_t isa = f32x2_to_f16x2(W.f8_inv_act[l], W.f8_inv_act[l]);
@@ -477,7 +515,8 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
 #pragma unroll
                                 for (int t = 0; t < 4; ++t) {
                                     const int e = j + 4 * t;
-                                    const float4 bb = *reinterpret_cast<const float4*>(bias + cc + e);
+                                    const float4 bb = (kBatch && l == 0) ? b1_4(sl->B.b1p, g, cc + e)
+                                                                         : *reinterpret_cast<const float4*>(bias + cc + e);
                                     const float2 y0 = upk(fma2(pk(__uint_as_float(v[e]), __uint_as_float(v[e + 1])),
                                                                dq2, pk(bb.x, bb.y)));
                                     const float2 y1 = upk(fma2(pk(__uint_as_float(v[e + 2]), __uint_as_float(v[e + 3])),
@@ -489,11 +528,12 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                             }
                         } else if (l == 0) {
                             // layer 1: + the gate's first-layer bias
-                            const float* bias = S.b1[g];
+                            const float* bias = S.b1[kBatch ? 0 : g];
 #pragma unroll
                             for (int j = 0; j < 32; j += 8) {
-                                const float4 b0 = *reinterpret_cast<const float4*>(bias + cc + j);
-                                const float4 b1 = *reinterpret_cast<const float4*>(bias + cc + j + 4);
+                                const float4 b0 = kBatch ? b1_4(sl->B.b1p, g, cc + j) : *reinterpret_cast<const float4*>(bias + cc + j);
+                                const float4 b1 = kBatch ? b1_4(sl->B.b1p, g, cc + j + 4)
+                                                         : *reinterpret_cast<const float4*>(bias + cc + j + 4);
                                 tc::st_shared_v4(
                                     a_base + tc::operand_offset_bytes(row, cc + j),
                                     act_pair<kFmt>(add2(pk(__uint_as_float(v[j]), __uint_as_float(v[j + 1])), pk(b0.x, b0.y))),
@@ -578,20 +618,20 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
             }
         }
         if (ok && half == 0) {
-            // collision-cost fold (Eq. 8-10): stage hinge of every row, summed per rollout over
-            // the tile's rows; the four lower-half warps of the group meet at their own barrier
-            if (P.store_sdf && row < nvalid) B.sdf[r] = smin;
-            const float c = row < nvalid ? stage_hinge(smin, P.d_safe, P.paper) : 0.f;
-            fold_warp_runs(c, r, P.H, lane, S.fold[grp]);
-            tc::named_barrier(4 + grp, kGroupThreads / 2);
-            fold_store(S.fold[grp], row0, nvalid, P.H, tile, row, B.colp, n_colp);
+            // collision-cost fold (Eq. 8-10): the stage hinge of every row, summed per rollout over
+            // each 32-row segment by the group's four lower-half warps (measured faster here than
+            // deferring it behind the next tile's first GEMM or handing it to a separate warp)
+            const StepParams& tP = kBatch ? sl->P : P;
+            const StepBuffers& tB = kBatch ? sl->B : B;
+            if (tP.store_sdf && row < nvalid) tB.sdf[r] = smin;
+            fold_warp(row < nvalid ? stage_hinge(smin, tP.d_safe, tP.paper) : 0.f, r, n_rows, tP.H, lane, tB.colp);
         }
     }
 
     // on abort: let the MMAs this group's leader issued finish before TMEM is released
     if (leader && outstanding > 0) {
         int dummy = 0;
-        tc::mbar_wait_bounded(acc_bar, acc_phase, &dummy, B.err, kDevErrTimeout);
+        tc::mbar_wait_bounded(acc_bar, acc_phase, &dummy, errw, kDevErrTimeout);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -664,12 +704,13 @@ __global__ void __launch_bounds__(128, 1) tc_selftest_kernel(const uint16_t* __r
 }
 
 constexpr size_t kSmemBytes = sizeof(TcShared);
+static_assert(kSmemBytes <= 227 * 1024, "the tile groups' shared memory exceeds the 227 KB a CTA may hold");
 
 }  // namespace
 
-template <int kFmt, bool kPE>
+template <int kFmt, bool kPE, bool kBatch = false>
 cudaError_t configure_one() {
-    return cudaFuncSetAttribute(sdf_mlp_tc_kernel<kFmt, kPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(sdf_mlp_tc_kernel<kFmt, kPE, kBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(kSmemBytes));
 }
 
@@ -678,11 +719,12 @@ cudaError_t launch_tc(const StepParams& P, const StepBuffers& B, const MlpWeight
     const int n_items = (P.K * P.H + kTileRows - 1) / kTileRows;
     const int want = (n_items + kGroups - 1) / kGroups;
     const int grid = want < num_sms ? want : num_sms;
+    const BatchRef none{nullptr, 0, 0, nullptr};
     if (P.pe > 0)
-        return launch_dependent(P.pdl != 0, sdf_mlp_tc_kernel<kFmt, true>, dim3(grid), dim3(kThreads), kSmemBytes, s, P,
-                                B, W);
-    return launch_dependent(P.pdl != 0, sdf_mlp_tc_kernel<kFmt, false>, dim3(grid), dim3(kThreads), kSmemBytes, s, P, B,
-                            W);
+        return launch_dependent(P.pdl != 0, sdf_mlp_tc_kernel<kFmt, true, false>, dim3(grid), dim3(kThreads),
+                                kSmemBytes, s, P, B, W, none);
+    return launch_dependent(P.pdl != 0, sdf_mlp_tc_kernel<kFmt, false, false>, dim3(grid), dim3(kThreads), kSmemBytes,
+                            s, P, B, W, none);
 }
 
 cudaError_t configure_sdf_mlp_bf16() {
@@ -692,6 +734,9 @@ cudaError_t configure_sdf_mlp_bf16() {
     if (e == cudaSuccess) e = configure_one<kFmtBF16, true>();
     if (e == cudaSuccess) e = configure_one<kFmtFP16, true>();
     if (e == cudaSuccess) e = configure_one<kFmtE4M3, true>();
+    if (e == cudaSuccess) e = configure_one<kFmtBF16, false, true>();
+    if (e == cudaSuccess) e = configure_one<kFmtFP16, false, true>();
+    if (e == cudaSuccess) e = configure_one<kFmtE4M3, false, true>();
     return e;
 }
 
@@ -708,6 +753,28 @@ cudaError_t launch_sdf_mlp_fp16(const StepParams& P, const StepBuffers& B, const
 cudaError_t launch_sdf_mlp_fp8(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms,
                                cudaStream_t s) {
     return launch_tc<kFmtE4M3>(P, B, W, num_sms, s);
+}
+
+cudaError_t launch_sdf_batch(int sdf_mode, const BatchSlot* slots, int n, int tiles, const StepParams& P0,
+                             const MlpWeights& W, int* err, int num_sms, cudaStream_t s) {
+    if (n <= 0 || tiles <= 0) return cudaSuccess;
+    const int want = (tiles + kGroups - 1) / kGroups;
+    const int grid = want < num_sms ? want : num_sms;
+    const BatchRef R{slots, n, tiles, err};
+    const StepBuffers none{};
+    switch (sdf_mode) {
+        case MPPI_SDF_MLP_BF16:
+            return launch_dependent(false, sdf_mlp_tc_kernel<kFmtBF16, false, true>, dim3(grid), dim3(kThreads),
+                                    kSmemBytes, s, P0, none, W, R);
+        case MPPI_SDF_MLP_FP16:
+            return launch_dependent(false, sdf_mlp_tc_kernel<kFmtFP16, false, true>, dim3(grid), dim3(kThreads),
+                                    kSmemBytes, s, P0, none, W, R);
+        case MPPI_SDF_MLP_FP8:
+            return launch_dependent(false, sdf_mlp_tc_kernel<kFmtE4M3, false, true>, dim3(grid), dim3(kThreads),
+                                    kSmemBytes, s, P0, none, W, R);
+        default:
+            return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_tc_selftest(const uint16_t* A, const uint16_t* Bm, float* D, int* err, cudaStream_t s) {

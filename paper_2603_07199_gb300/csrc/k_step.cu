@@ -103,11 +103,13 @@ __global__ void noise_words_kernel(StepParams P, const uint32_t* __restrict__ st
 // evaluated at every p_{h+1}.
 constexpr int kRollWarps = 4;
 
+// The body of one block (block = the block's index among this controller's rollout blocks;
+// sU: H floats4 and sPose: kMaxGates x 8 floats of shared memory); the per-controller kernel
+// and the batched serving kernel both run it.
 template <int kLanes, int kSteps>
-__global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, StepBuffers B, int analytic) {
+__device__ __forceinline__ void rollout_body(const StepParams& P, const StepBuffers& B, int analytic, int block,
+                                             float4* sU, float* sPose) {
     static_assert(kLanes == 16 || kLanes == 32, "a rollout's lanes are a half warp or a warp");
-    extern __shared__ float4 sU[];                 // [H]
-    __shared__ float sPose[kMaxGates * 8];
     pdl_trigger();
     pdl_wait();
     for (int i = threadIdx.x; i < P.H; i += blockDim.x) sU[i] = B.nominal[i];
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, 
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int sub = lane & (kLanes - 1);          // lane within the rollout's segment
-    const int k_first = (blockIdx.x * kRollWarps + (threadIdx.x >> 5)) * (32 / kLanes);
+    const int k_first = (block * kRollWarps + (threadIdx.x >> 5)) * (32 / kLanes);
     if (k_first >= P.K) return;                    // whole warps only
     // a segment past the last rollout (odd K) mirrors the last one and stores nothing
     const bool valid = k_first + lane / kLanes < P.K;
@@ -275,6 +277,13 @@ __global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, 
     }
 }
 
+template <int kLanes, int kSteps>
+__global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, StepBuffers B, int analytic) {
+    extern __shared__ float4 sU[];                 // [H]
+    __shared__ float sPose[kMaxGates * 8];
+    rollout_body<kLanes, kSteps>(P, B, analytic, blockIdx.x, sU, sPose);
+}
+
 // ------------------------------------------------------------------ (a) + (b) rotor-thrust-rate model
 // The paper's command (Sec. IV-A): the four rotor-thrust rates, the body rate following from
 // the rotors' torques (rk4_rotor).  The body rate now has dynamics of its own, so the attitude
@@ -283,15 +292,14 @@ __global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, 
 // model, scaled by sigma_tdot), storing noise and positions in the [K][H] arrays.
 constexpr int kRotorThreads = 64;
 
-__global__ void __launch_bounds__(kRotorThreads) rollout_rotor_kernel(StepParams P, StepBuffers B, int analytic) {
-    extern __shared__ float4 sU[];                 // [H]
-    __shared__ float sPose[kMaxGates * 8];
+__device__ __forceinline__ void rotor_body(const StepParams& P, const StepBuffers& B, int analytic, int block,
+                                           float4* sU, float* sPose) {
     pdl_trigger();
     pdl_wait();
     for (int i = threadIdx.x; i < P.H; i += blockDim.x) sU[i] = B.nominal[i];
     for (int i = threadIdx.x; i < P.G * 8; i += blockDim.x) sPose[i] = B.poses[i];
     __syncthreads();
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = block * static_cast<int>(blockDim.x) + static_cast<int>(threadIdx.x);
     if (k >= P.K) return;
     const int K = P.K, H = P.H;
     const uint32_t st = B.step[0];
@@ -346,6 +354,12 @@ __global__ void __launch_bounds__(kRotorThreads) rollout_rotor_kernel(StepParams
     }
 }
 
+__global__ void __launch_bounds__(kRotorThreads) rollout_rotor_kernel(StepParams P, StepBuffers B, int analytic) {
+    extern __shared__ float4 sU[];                 // [H]
+    __shared__ float sPose[kMaxGates * 8];
+    rotor_body(P, B, analytic, blockIdx.x, sU, sPose);
+}
+
 // ------------------------------------------------------------------ (d) costs, weights, update, receding horizon
 // Block b owns R consecutive rollouts (R a multiple of 32, at most kCuMaxBlocks blocks):
 //  1. J_k = J_col + J_prog + J_ctl (MLP modes: J_col = w_col sum_h max(0, d_safe - s_h)^2,
@@ -377,19 +391,28 @@ __device__ __forceinline__ float4 f4_fma(float a, float4 x, float4 y) {
     return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
 }
 
-__global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, StepBuffers B, int mlp, int R) {
-    extern __shared__ float sE[];                  // [R] J_k, then e_k
-    __shared__ float4 sRed[kCuWarps][kCuHChunk];
-    __shared__ float sWarp[kCuWarps];
-    __shared__ float sF[kCuMaxBlocks];
-    __shared__ float s_rho, s_eta;
-    __shared__ int is_last;
+// Shared scratch of the update kernels (besides R floats of dynamic shared memory).
+struct UpdShared {
+    float4 red[kCuWarps][kCuHChunk];
+    float warp[kCuWarps];
+    float F[kCuMaxBlocks];
+    float rho, eta;
+    int flag;
+};
+
+// Phases 1 and 2 of update block `block` of a controller (R rollouts from k0 = block R; sE: R
+// floats of shared memory): J_k, e_k (into B.w), the block statistics B.bstat[block] and the
+// partial sums B.upart[block][h].  The per-controller kernel and the batched serving kernel
+// both run it.
+__device__ __forceinline__ void update_local(const StepParams& P, const StepBuffers& B, int mlp, int R, int block,
+                                             float* sE, UpdShared& U) {
+    float4 (&sRed)[kCuWarps][kCuHChunk] = U.red;
+    float* sWarp = U.warp;
     const float4* __restrict__ noise = B.noise;
     const float* parts_in = B.parts;             // also written below (J_col of the MLP modes)
-    pdl_wait();
     const int K = P.K, H = P.H;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int k0 = blockIdx.x * R;
+    const int k0 = block * R;
     const int nk = min(K, k0 + R) - k0;
     const float inv_lam = 1.f / P.lam;
     const float inf = __int_as_float(0x7f800000);
@@ -406,16 +429,15 @@ __global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, S
     }
 
     // 1. costs: one thread per rollout.  MLP modes: J_col = w_col (or Q_sdf) times the sum of the
-    //    rollout's per-tile partial sums of the stage hinge, which the SDF kernel folded in its
-    //    epilogue (fold_store), added in tile order
+    //    rollout's per-segment partial sums of the stage hinge, which the SDF kernel folded in its
+    //    epilogue (fold_warp), added in segment order
     float mloc = inf;
     const int n_colp = col_slots(H);
     for (int i = threadIdx.x; i < nk; i += kCuThreads) {
         const int k = k0 + i;
         float jcol;
         if (mlp) {
-            const int t0 = (k * H) / kTileRows;
-            const int n = (k * H + H - 1) / kTileRows - t0 + 1;
+            const int n = ((k * H + H - 1) >> 5) - ((k * H) >> 5) + 1;     // the rollout's 32-row segments
             const float* cp = B.colp + static_cast<size_t>(k) * n_colp;
             float a = __ldcs(cp);
             for (int j = 1; j < n; ++j) a += __ldcs(cp + j);
@@ -435,10 +457,10 @@ __global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, S
         float m = sWarp[0];
 #pragma unroll
         for (int i = 1; i < kCuWarps; ++i) m = fminf(m, sWarp[i]);
-        s_rho = m;
+        U.rho = m;
     }
     __syncthreads();
-    const float rho_b = s_rho;
+    const float rho_b = U.rho;
     float eloc = 0.f;
     for (int i = threadIdx.x; i < nk; i += kCuThreads) {
         const float J = sE[i];
@@ -456,7 +478,7 @@ __global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, S
         float e = sWarp[0];
 #pragma unroll
         for (int i = 1; i < kCuWarps; ++i) e += sWarp[i];
-        B.bstat[blockIdx.x] = make_float2(rho_b, e);
+        B.bstat[block] = make_float2(rho_b, e);
     }
 
     // 2. e-weighted sums of the rolled-out (clipped) controls, kCuHChunk horizon steps per pass
@@ -502,31 +524,26 @@ __global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, S
                 const float4 o = sRed[i][threadIdx.x];
                 t.x += o.x; t.y += o.y; t.z += o.z; t.w += o.w;
             }
-            B.upart[static_cast<size_t>(blockIdx.x) * H + c0 + threadIdx.x] = t;
+            B.upart[static_cast<size_t>(block) * H + c0 + threadIdx.x] = t;
         }
         __syncthreads();
     }
+}
 
-    // 3. grid barrier (cooperative launch: every block is resident; the wait is bounded).  The
-    //    arrival counter (64 bits, ticket words 12-13) only grows: after the block's writes
-    //    (the __syncthreads above), one thread adds 1 with release semantics; the launch's
-    //    target is the next multiple of the grid size above the count it saw, and it polls
-    //    with acquire loads.  A launch that timed out leaves the count off a multiple of the
-    //    grid: the host zeroes the ticket words together with the error word.  Ticket word 31
-    //    (0 unless set by mppi_debug_inject_timeout) moves the target that many grids further,
-    //    so that every block's wait runs out: the test of the timeout path, with no fault.
-    if (threadIdx.x == 0) {
-        is_last = grid_arrive_wait(reinterpret_cast<unsigned long long*>(B.tickets + 12), B.tickets[31], B.err,
-                                   kGridWaitLimitNs)
-                      ? 1
-                      : 0;
-    }
-    __syncthreads();
-    if (!is_last) return;
+// Phase 4: rho = min_b rho_b, F_b = exp(-(rho_b - rho) / lambda), eta = sum_b F_b eta_b from the
+// nb blocks' statistics (warp 0, the same data in the same order wherever it runs), then the
+// weights w_k = e_k F_b / eta of the rollouts of blocks [b_lo, b_hi) and U*_new[h] = sum_b
+// (F_b / eta) S_b[h] for h = h0, h0 + hs, ..., written in place as the shifted warm start; the
+// caller that covers h = 0 also applies U*_new[0] to the device-resident state with one RK4 step
+// and bumps the step counter.
+__device__ __forceinline__ void update_combine(const StepParams& P, const StepBuffers& B, int nb, int R, int b_lo,
+                                               int b_hi, int h0, int hs, UpdShared& U) {
+    float* sF = U.F;
+    const int K = P.K, H = P.H;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const float inv_lam = 1.f / P.lam;
+    const float inf = __int_as_float(0x7f800000);
 
-    // 4. every block combines the blocks' statistics the same way (same data, same order):
-    //    rho = min_b rho_b, F_b = exp(-(rho_b - rho) / lambda), eta = sum_b F_b eta_b
-    const int nb = gridDim.x;
     if (wid == 0) {
         float2 bs[kCuMaxBlocks / 32];
         float m = inf;
@@ -547,24 +564,28 @@ __global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, S
         }
         const float eta = warp_sum(e);
         if (lane == 0) {
-            s_rho = rho;
-            s_eta = eta;
+            U.rho = rho;
+            U.eta = eta;
         }
     }
     __syncthreads();
-    const float eta = s_eta;
-    // this block's weights: w_k = e_k F_b / eta
-    const float fw = sF[blockIdx.x] / eta;
-    for (int i = threadIdx.x; i < nk; i += kCuThreads) {
-        const float wk = sE[i] * fw;
-        B.w[k0 + i] = wk;
-        if (B.out_w) B.out_w[k0 + i] = wk;
+    const float eta = U.eta;
+    // weights w_k = e_k F_b / eta of blocks [b_lo, b_hi) (e_k as update_local stored it in B.w)
+    for (int b = b_lo; b < b_hi; ++b) {
+        const int k0 = b * R;
+        const int nk = min(K, k0 + R) - k0;
+        const float fw = sF[b] / eta;
+        for (int i = threadIdx.x; i < nk; i += kCuThreads) {
+            const float wk = __ldcg(B.w + k0 + i) * fw;
+            B.w[k0 + i] = wk;
+            if (B.out_w) B.out_w[k0 + i] = wk;
+        }
     }
-    // U*_new[h] for h = blockIdx.x, blockIdx.x + nb, ...: thread t < nb loads block t's partial;
-    // fixed-order sums: xor shuffles within each warp, then the warps' sums in warp order
-    float4* sU = reinterpret_cast<float4*>(sRed);
+    // U*_new[h] for h = h0, h0 + hs, ...: thread t < nb loads block t's partial; fixed-order
+    // sums: xor shuffles within each warp, then the warps' sums in warp order
+    float4* sU = reinterpret_cast<float4*>(U.red);
     const float uh = P.u_hover;
-    for (int h = blockIdx.x; h < H; h += nb) {
+    for (int h = h0; h < H; h += hs) {
         float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
         if (threadIdx.x < nb) {
             const float4 sb = __ldcg(B.upart + static_cast<size_t>(threadIdx.x) * H + h);
@@ -590,7 +611,7 @@ __global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, S
             if (h == H - 1) B.nominal[H - 1] = make_float4(uh, 0.f, 0.f, 0.f);
             if (h == 0) {
                 // apply U*_new[0] to the device-resident state
-                B.stats[0] = s_rho;
+                B.stats[0] = U.rho;
                 B.stats[1] = eta;
                 float* st = B.state;
                 Vec3 p = v3(st[0], st[1], st[2]);
@@ -612,12 +633,39 @@ __global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, S
                 const uint32_t lo = B.step[0] + 1u;
                 B.step[0] = lo;
                 if (lo == 0u) B.step[1] += 1u;
-                // every earlier wait of this step has ended (this block passed the grid barrier)
+                // every earlier wait of this step has ended (every block's phases are done)
                 if (B.err_out) *B.err_out = *reinterpret_cast<volatile int*>(B.err);
             }
         }
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(kCuThreads) cost_update_kernel(StepParams P, StepBuffers B, int mlp, int R) {
+    extern __shared__ float sE[];                  // [R] J_k, then e_k
+    __shared__ UpdShared U;
+    pdl_wait();
+    update_local(P, B, mlp, R, blockIdx.x, sE, U);
+    // 3. grid barrier (cooperative launch: every block is resident; the wait is bounded).  The
+    //    arrival counter (64 bits, ticket words 12-13) only grows: after the block's writes
+    //    (the __syncthreads above), one thread adds 1 with release semantics; the launch's
+    //    target is the next multiple of the grid size above the count it saw, and it polls
+    //    with acquire loads.  A launch that timed out leaves the count off a multiple of the
+    //    grid: the host zeroes the ticket words together with the error word.  Ticket word 31
+    //    (0 unless set by mppi_debug_inject_timeout) moves the target that many grids further,
+    //    so that every block's wait runs out: the test of the timeout path, with no fault.
+    if (threadIdx.x == 0) {
+        U.flag = grid_arrive_wait(reinterpret_cast<unsigned long long*>(B.tickets + 12), B.tickets[31], B.err,
+                                   kGridWaitLimitNs)
+                      ? 1
+                      : 0;
+    }
+    __syncthreads();
+    if (!U.flag) return;
+
+    // 4. every block combines the blocks' statistics the same way, writes its own weights and its
+    //    share of the horizon
+    update_combine(P, B, gridDim.x, R, blockIdx.x, blockIdx.x + 1, blockIdx.x, gridDim.x, U);
 }
 
 // ------------------------------------------------------------------ per-gate first-layer bias
@@ -635,6 +683,100 @@ __global__ void first_layer_bias_kernel(const float* __restrict__ W1, const floa
     b1p[i] = b1[c] + acc;
 }
 
+
+// ------------------------------------------------------------------ batched serving step
+// The index of the slot whose range [start, next start) holds x (starts ascending, slot 0 at 0).
+template <typename Start>
+__device__ __forceinline__ int find_slot(const BatchSlot* __restrict__ slots, int n, int x, Start start) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start(slots[mid]) <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One block per controller: its state, gate poses and latents from the batch's input block into
+// its buffers, and the first-layer bias of every gate (the arithmetic of first_layer_bias_kernel).
+__global__ void __launch_bounds__(128) batch_prep_kernel(const BatchSlot* __restrict__ slots,
+                                                         const float* __restrict__ in) {
+    const BatchSlot& S = slots[blockIdx.x];
+    const float* src = in + S.in_off;
+    const int G = S.P.G;
+    for (int i = threadIdx.x; i < S.state_floats; i += blockDim.x) S.B.state[i] = src[i];
+    const float* poses = src + kBatchStateSlot;
+    for (int i = threadIdx.x; i < G * 8; i += blockDim.x) S.B.poses[i] = poses[i];
+    if (!S.mlp) return;
+    const float* lat = poses + G * 8;
+    for (int i = threadIdx.x; i < G * kLatent; i += blockDim.x) S.latents[i] = lat[i];
+    for (int i = threadIdx.x; i < G * kHidden; i += blockDim.x) {
+        const int g = i / kHidden, c = i - g * kHidden;
+        const float* wr = S.W1 + c * (S.n_point + kLatent) + S.n_point;
+        const float* z = lat + g * kLatent;
+        float acc = 0.f;
+        for (int j = 0; j < kLatent; ++j) acc = fmaf(wr[j], z[j], acc);
+        S.B.b1p[i] = S.b1[c] + acc;
+    }
+}
+
+// Rollout blocks of every controller of the batch (128 threads each): a block finds its
+// controller and runs that controller's rollout form on its parameters and buffers.
+__global__ void __launch_bounds__(kRollWarps * 32) rollout_batch_kernel(const BatchSlot* __restrict__ slots, int n) {
+    extern __shared__ float4 sU[];                 // [max H]
+    __shared__ float sPose[kMaxGates * 8];
+    __shared__ StepParams sP;
+    __shared__ StepBuffers sB;
+    __shared__ int s_form, s_block, s_analytic;
+    if (threadIdx.x == 0) {
+        const int d = find_slot(slots, n, static_cast<int>(blockIdx.x), [](const BatchSlot& t) { return t.roll_block0; });
+        sP = slots[d].P;
+        sB = slots[d].B;
+        s_form = slots[d].roll_form;
+        s_block = static_cast<int>(blockIdx.x) - slots[d].roll_block0;
+        s_analytic = slots[d].mlp ? 0 : 1;
+    }
+    __syncthreads();
+    switch (s_form) {
+        case 0: rollout_body<32, 2>(sP, sB, s_analytic, s_block, sU, sPose); break;
+        case 1: rollout_body<16, 2>(sP, sB, s_analytic, s_block, sU, sPose); break;
+        case 2: rollout_body<16, 4>(sP, sB, s_analytic, s_block, sU, sPose); break;
+        default: rotor_body(sP, sB, s_analytic, s_block, sU, sPose); break;
+    }
+}
+
+// Update blocks of every controller of the batch: phases 1 and 2 as in cost_update_kernel, then
+// the last of a controller's blocks to finish (an arrival count on the controller's barrier
+// counter, release / acquire) combines all of them with the same arithmetic, so no block waits
+// for another and the launch needs no co-residency.
+__global__ void __launch_bounds__(kCuThreads) cost_update_batch_kernel(const BatchSlot* __restrict__ slots, int n) {
+    extern __shared__ float sE[];                  // [max R]
+    __shared__ UpdShared U;
+    __shared__ StepParams sP;
+    __shared__ StepBuffers sB;
+    __shared__ int s_block, s_R, s_nb, s_mlp;
+    pdl_wait();
+    if (threadIdx.x == 0) {
+        const int d = find_slot(slots, n, static_cast<int>(blockIdx.x), [](const BatchSlot& t) { return t.upd_block0; });
+        sP = slots[d].P;
+        sB = slots[d].B;
+        s_R = slots[d].upd_R;
+        s_nb = (sP.K + s_R - 1) / s_R;
+        s_block = static_cast<int>(blockIdx.x) - slots[d].upd_block0;
+        s_mlp = slots[d].mlp;
+    }
+    __syncthreads();
+    update_local(sP, sB, s_mlp, s_R, s_block, sE, U);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned long long prev = atomicAdd(reinterpret_cast<unsigned long long*>(sB.tickets + 12), 1ull);
+        U.flag = ((prev + 1ull) % static_cast<unsigned long long>(s_nb) == 0ull) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!U.flag) return;
+    __threadfence();
+    update_combine(sP, sB, s_nb, s_R, 0, s_nb, 0, 1, U);
+}
 }  // namespace
 
 cudaError_t launch_noise_words(const StepParams& P, const StepBuffers& B, uint4* out, cudaStream_t s) {
@@ -677,8 +819,15 @@ int update_blocks(int K) {
 
 cudaError_t configure_cost_update() {
     // R floats of dynamic shared memory: up to MPPI_MAX_K / kCuMaxBlocks
-    return cudaFuncSetAttribute(cost_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(sizeof(float) * update_rollouts_per_block(kMaxRollouts)));
+    const int bytes = static_cast<int>(sizeof(float) * update_rollouts_per_block(kMaxRollouts));
+    cudaError_t e = cudaFuncSetAttribute(cost_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(cost_update_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    // the batched rollout's H float4 of dynamic shared memory (up to MPPI_MAX_H)
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(rollout_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(1024 * sizeof(float4)));
+    return e;
 }
 
 cudaError_t launch_cost_update(const StepParams& P, const StepBuffers& B, int mlp, cudaStream_t s) {
@@ -695,6 +844,39 @@ cudaError_t launch_cost_update(const StepParams& P, const StepBuffers& B, int ml
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, cost_update_kernel, P, B, mlp, R);
+}
+
+int rollout_form(const StepParams& P) {
+    if (P.rotor) return 3;
+    if (P.H > 32 && P.K < 8192) return 0;
+    return P.H <= 32 ? 1 : 2;
+}
+
+int rollout_batch_blocks(const StepParams& P) {
+    switch (rollout_form(P)) {
+        case 0: return (P.K + kRollWarps - 1) / kRollWarps;
+        case 1:
+        case 2: return (P.K + 2 * kRollWarps - 1) / (2 * kRollWarps);
+        default: return (P.K + kRollWarps * 32 - 1) / (kRollWarps * 32);
+    }
+}
+
+cudaError_t launch_batch_prep(const BatchSlot* slots, int n, const float* inputs, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    batch_prep_kernel<<<n, 128, 0, s>>>(slots, inputs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rollout_batch(const BatchSlot* slots, int n, int blocks, int max_h, cudaStream_t s) {
+    if (n <= 0 || blocks <= 0) return cudaSuccess;
+    rollout_batch_kernel<<<blocks, kRollWarps * 32, max_h * sizeof(float4), s>>>(slots, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cost_update_batch(const BatchSlot* slots, int n, int blocks, int max_r, cudaStream_t s) {
+    if (n <= 0 || blocks <= 0) return cudaSuccess;
+    cost_update_batch_kernel<<<blocks, kCuThreads, max_r * sizeof(float), s>>>(slots, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_first_layer_bias(const float* W1, const float* b1, const float* latents, int G, int n_point,

@@ -69,6 +69,43 @@ cudaError_t launch_first_layer_bias(const float* W1, const float* b1, const floa
 // tensor-core self-test (one 128x128x128 tile)
 cudaError_t launch_tc_selftest(const uint16_t* A, const uint16_t* B, float* D, int* err, cudaStream_t s);
 
+// ---------------------------------------------------------------- batched serving step
+// One controller of a batched serving step (device memory): its parameters and buffers, where
+// its inputs sit in the batch's input block and where its blocks and tiles start in the
+// batched launches.  Every controller's results equal those of its own step (same kernels'
+// arithmetic, same reduction orders).
+constexpr int kBatchStateSlot = 24;    // floats reserved for a state in the batch's input block
+struct BatchSlot {
+    StepParams P;
+    StepBuffers B;             // with the controller's output and error pointers set
+    const float* W1;           // first-layer weights [128][n_point + 64] (MLP modes)
+    const float* b1;           // [128]
+    float* latents;            // the controller's latent buffer [max_gates][64]
+    int n_point;               // point features of the first layer (3 + 6 pe_levels)
+    int state_floats;          // 13 or 17
+    int in_off;                // floats: state (kBatchStateSlot), then G x 8 poses, then G x 64 latents
+    int roll_form;             // 0: 32 lanes x 2 steps, 1: 16 x 2, 2: 16 x 4, 3: rotor model
+    int roll_block0;           // first block in the batched rollout launch
+    int tile0;                 // first tile in the batched SDF launch
+    int upd_block0;            // first block in the batched update launch
+    int upd_R;                 // rollouts per update block
+    int mlp;                   // SDF from the MLP (else analytic, folded into the rollout)
+};
+// Rollout form launch_rollout uses for P (0..3 as BatchSlot::roll_form) and the blocks of 128
+// threads a batched launch gives it.
+int rollout_form(const StepParams& P);
+int rollout_batch_blocks(const StepParams& P);
+// rollouts per update block for K rollouts (the per-controller update kernel's partition)
+int update_rollouts_per_block(int K);
+// The batched launches, all on one stream: inputs (state, gates, latents, first-layer biases)
+// of every controller, rollouts, SDF (MLP modes; every controller shares the weights W and
+// the softplus sharpness / encoding levels of P0) and costs / update / plant step.
+cudaError_t launch_batch_prep(const BatchSlot* slots, int n, const float* inputs, cudaStream_t s);
+cudaError_t launch_rollout_batch(const BatchSlot* slots, int n, int blocks, int max_h, cudaStream_t s);
+cudaError_t launch_cost_update_batch(const BatchSlot* slots, int n, int blocks, int max_r, cudaStream_t s);
+cudaError_t launch_sdf_batch(int sdf_mode, const BatchSlot* slots, int n, int tiles, const StepParams& P0,
+                             const MlpWeights& W, int* err, int num_sms, cudaStream_t s);
+
 // Store a message in the calling thread's error slot (read by mppi_last_error(NULL)).
 void set_thread_error(const char* msg);
 // Host helpers: BF16 / FP16 (round to nearest even) of a float.

@@ -944,6 +944,70 @@ int ctx_enqueue_host_step(mppi_ctx* c, const float* state, int n_gates, const fl
     return MPPI_OK;
 }
 
+int ctx_batch_slot(mppi_ctx* c, const float* state, int n_gates, const float* poses, const float* latents,
+                   BatchSlot* slot, float* in) {
+    const int H = c->cfg.H, K = c->cfg.K;
+    const bool mlp = is_mlp(c);
+    if (n_gates < 0 || n_gates > c->cfg.max_gates) return fail(c, MPPI_E_INVALID, "n_gates out of range");
+    if (!finite_all(state, state_dim(c->cfg))) return fail(c, MPPI_E_INVALID, "non-finite state");
+    if (n_gates > 0 && (!poses || !finite_all(poses, static_cast<size_t>(n_gates) * 7)))
+        return fail(c, MPPI_E_INVALID, "bad gate poses");
+    if (n_gates > 0 && mlp && (!latents || !finite_all(latents, static_cast<size_t>(n_gates) * kLatent)))
+        return fail(c, MPPI_E_INVALID, "bad latents");
+    if (mlp && !c->have_weights) return fail(c, MPPI_E_NOT_READY, "MLP SDF mode but no weights set");
+    if (c->n_gates != n_gates) c->graph_dirty = true;
+    c->n_gates = n_gates;
+    if (mlp && n_gates > 0) c->have_latents = true;
+    // state, gate poses (7 + 1 pad each) and latents, as the batch's prep kernel reads them
+    std::memset(in, 0, kBatchStateSlot * sizeof(float));
+    std::memcpy(in, state, state_dim(c->cfg) * sizeof(float));
+    float* hp = in + kBatchStateSlot;
+    for (int g = 0; g < n_gates; ++g) {
+        for (int i = 0; i < 7; ++i) hp[8 * g + i] = poses[7 * g + i];
+        hp[8 * g + 7] = 0.f;
+    }
+    int used = kBatchStateSlot + 8 * n_gates;
+    if (mlp) {
+        std::memcpy(in + used, latents, static_cast<size_t>(n_gates) * kLatent * sizeof(float));
+        used += kLatent * n_gates;
+    }
+    // U*_new and the error word straight into pinned staging (-1 stays if the step's last kernel
+    // did not finish its work)
+    *reinterpret_cast<volatile int*>(c->h_out + H * 4 + 2 * K) = -1;
+    set_outputs(c, reinterpret_cast<float4*>(c->d_hout), nullptr, nullptr,
+                reinterpret_cast<int*>(c->d_hout + H * 4 + 2 * K));
+    slot->P = make_params(c);
+    slot->P.pdl = 0;
+    slot->B = c->B;
+    slot->W1 = c->d_W1;
+    slot->b1 = c->d_b1;
+    slot->latents = c->d_latents;
+    slot->n_point = point_features(c->cfg);
+    slot->state_floats = state_dim(c->cfg);
+    slot->mlp = mlp ? 1 : 0;
+    return used;
+}
+
+void ctx_batch_launched(mppi_ctx* c) { ++c->step_count; }
+
+int ctx_batch_result(mppi_ctx* c, float* new_controls) {
+    const int H = c->cfg.H;
+    const volatile int* herr = reinterpret_cast<const volatile int*>(c->h_out + H * 4 + 2 * c->cfg.K);
+    if (*herr != 0) return fail(c, MPPI_E_TIMEOUT, "a device-side wait timed out (error word %d)", *herr);
+    std::memcpy(new_controls, c->h_out, static_cast<size_t>(H) * 4 * sizeof(float));
+    return MPPI_OK;
+}
+
+int ctx_clear_error(mppi_ctx* c) {
+    CUDA_TRY(c, clear_device_error(c));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return MPPI_OK;
+}
+
+MlpWeights ctx_weights(const mppi_ctx* c) { return make_weights(c); }
+StepParams ctx_params(const mppi_ctx* c) { return make_params(c); }
+int ctx_num_sms(const mppi_ctx* c) { return c->num_sms; }
+
 int ctx_poll_host_step(mppi_ctx* c, float* new_controls) {
     const cudaError_t q = cudaEventQuery(c->done);
     if (q == cudaErrorNotReady) return 1;

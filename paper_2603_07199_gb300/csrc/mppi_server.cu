@@ -7,9 +7,17 @@
 // an in-flight slot is free and the drone's context fits in the budget; when it
 // does not fit, the least recently used idle drone is evicted (its warm start,
 // state and counter go to host memory and come back on its next request).
-// Requests of different drones run concurrently on their own streams, so work
-// that arrives while other solves are on the GPU overlaps with them.  Results
-// are collected per ticket with their submit-to-completion latency.
+// Batched mode (the default): the worker gathers every admissible queued request
+// into one batch and launches it as four kernels on the server's stream -- the
+// inputs of all drones, one rollout launch over all drones' rollouts, one
+// persistent tensor-core SDF launch whose tiles span all drones, and one update
+// launch whose per-drone combine is done by the last of the drone's blocks -- so
+// that a batch of small solves fills the GPU like one large solve; a second batch
+// is prepared and queued while the first runs.  Per-drone mode: each drone's step
+// is its own captured graph on its own stream and requests of different drones
+// overlap on the GPU.  Either way a drone's results are those of its own step
+// (same kernels' arithmetic, per-drone noise counters, fixed-order reductions).
+// Results are collected per ticket with their submit-to-completion latency.
 #include <chrono>
 #include <condition_variable>
 #include <cstdarg>
@@ -63,6 +71,20 @@ struct Result {
     double latency_us = 0.0;
 };
 
+// One batch buffer: pinned host block (slots, then packed inputs), its device copy, the
+// batch's SDF error word (pinned, mapped) and completion event.
+struct BatchBuf {
+    char* h = nullptr;
+    char* d = nullptr;
+    int* h_err = nullptr;
+    int* d_err = nullptr;
+    cudaEvent_t done = nullptr;
+    std::vector<Inflight> reqs;
+    bool busy = false;
+};
+
+constexpr int kBatchInFloats = mppi::kBatchStateSlot + MPPI_MAX_GATES * (8 + MPPI_LATENT_DIM);
+
 }  // namespace
 
 struct mppi_server {
@@ -82,6 +104,14 @@ struct mppi_server {
     uint64_t lru_clock = 0;
     size_t used_bytes = 0, peak_bytes = 0;
     uint64_t completed = 0, evictions = 0, restores = 0, admitted = 0;
+    // batched mode
+    cudaStream_t bstream = nullptr;
+    BatchBuf buf[2];
+    std::deque<int> order;                 // busy batch buffers, oldest first
+    size_t slots_bytes = 0;
+    float beta = 0.f;                      // softplus sharpness and encoding levels every drone shares
+    int pe_levels = -1;
+    uint64_t batches = 0;
     char err[512] = "";
 };
 
@@ -233,6 +263,166 @@ void worker_loop(mppi_server* s) {
     }
 }
 
+// ---------------------------------------------------------------- batched mode
+// Launch a prepared batch on the server's stream: one copy of its block (slots and inputs), the
+// prep, rollout, SDF and update launches, and the completion event.  With positional encoding or
+// the FP32 MLP the SDF runs per drone (the batched SDF launch is the tensor-core one without
+// encoding), still on the batch's stream.
+int launch_batch(mppi_server* s, BatchBuf& b, int n, size_t in_floats, int roll_blocks, int tiles, int upd_blocks,
+                 int max_h, int max_r, const std::vector<mppi_ctx*>& ctxs) {
+    using namespace mppi;
+    cudaStream_t st = s->bstream;
+    const BatchSlot* hs = reinterpret_cast<const BatchSlot*>(b.h);
+    const BatchSlot* ds = reinterpret_cast<const BatchSlot*>(b.d);
+    const float* din = reinterpret_cast<const float*>(b.d + s->slots_bytes);
+    cudaError_t e = cudaMemcpyAsync(b.d, b.h, s->slots_bytes + in_floats * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_batch_prep(ds, n, din, st);
+    if (e == cudaSuccess) e = launch_rollout_batch(ds, n, roll_blocks, max_h, st);
+    const int mode = s->cfg.sdf_mode;
+    if (e == cudaSuccess && mode != MPPI_SDF_ANALYTIC) {
+        if (s->pe_levels == 0 && mode != MPPI_SDF_MLP_FP32) {
+            e = launch_sdf_batch(mode, ds, n, tiles, ctx_params(ctxs[0]), ctx_weights(ctxs[0]), b.d_err,
+                                 ctx_num_sms(ctxs[0]), st);
+        } else {
+            for (int i = 0; i < n && e == cudaSuccess; ++i) {
+                const MlpWeights W = ctx_weights(ctxs[i]);
+                const int sms = ctx_num_sms(ctxs[i]);
+                switch (mode) {
+                    case MPPI_SDF_MLP_FP32: e = launch_sdf_mlp_fp32(hs[i].P, hs[i].B, W, sms, st); break;
+                    case MPPI_SDF_MLP_BF16: e = launch_sdf_mlp_bf16(hs[i].P, hs[i].B, W, sms, st); break;
+                    case MPPI_SDF_MLP_FP16: e = launch_sdf_mlp_fp16(hs[i].P, hs[i].B, W, sms, st); break;
+                    default: e = launch_sdf_mlp_fp8(hs[i].P, hs[i].B, W, sms, st); break;
+                }
+            }
+        }
+    }
+    if (e == cudaSuccess) e = launch_cost_update_batch(ds, n, upd_blocks, max_r, st);
+    if (e == cudaSuccess) e = cudaEventRecord(b.done, st);
+    if (e != cudaSuccess) return sfail(s, MPPI_E_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
+    return MPPI_OK;
+}
+
+void batched_worker_loop(mppi_server* s) {
+    using namespace mppi;
+    cudaSetDevice(s->device);
+    std::vector<float> scratch;
+    std::vector<mppi_ctx*> ctxs;
+    while (true) {
+        bool progress = false, idle = false;
+        {
+            std::lock_guard<std::mutex> lock(s->mu);
+            // completions, oldest batch first
+            while (!s->order.empty()) {
+                BatchBuf& b = s->buf[s->order.front()];
+                const cudaError_t q = cudaEventQuery(b.done);
+                if (q == cudaErrorNotReady) break;
+                const int berr = *reinterpret_cast<volatile int*>(b.h_err);
+                for (const Inflight& f : b.reqs) {
+                    Drone& d = s->drones[f.drone];
+                    scratch.assign(static_cast<size_t>(d.cfg.H) * 4, 0.f);
+                    int rc;
+                    if (q != cudaSuccess) {
+                        rc = sfail(s, MPPI_E_CUDA, "batch failed: %s", cudaGetErrorString(q));
+                    } else if (berr != 0) {
+                        rc = sfail(s, MPPI_E_TIMEOUT, "a device-side wait of the batch timed out");
+                    } else {
+                        rc = ctx_batch_result(d.ctx, scratch.data());
+                        if (rc != MPPI_OK) sfail(s, rc, "drone %d: %s", f.drone, mppi_last_error(d.ctx));
+                    }
+                    if (rc == MPPI_E_TIMEOUT) ctx_clear_error(d.ctx);
+                    finish(s, f, rc, std::vector<float>(scratch.begin(), scratch.end()));
+                    d.busy = false;
+                }
+                if (berr != 0) *reinterpret_cast<volatile int*>(b.h_err) = 0;
+                b.reqs.clear();
+                b.busy = false;
+                s->order.pop_front();
+                progress = true;
+            }
+            // the next batch: every admissible queued request, in arrival order, into a free buffer
+            const int fb = !s->buf[0].busy ? 0 : (!s->buf[1].busy ? 1 : -1);
+            if (fb >= 0 && !s->queue.empty()) {
+                BatchBuf& b = s->buf[fb];
+                BatchSlot* slots = reinterpret_cast<BatchSlot*>(b.h);
+                float* in = reinterpret_cast<float*>(b.h + s->slots_bytes);
+                size_t inflight = 0;
+                for (int i : s->order) inflight += s->buf[i].reqs.size();
+                int n = 0, roll = 0, tiles = 0, upd = 0, max_h = 1, max_r = 32;
+                size_t in_used = 0;
+                ctxs.clear();
+                for (auto it = s->queue.begin(); it != s->queue.end();) {
+                    if (inflight + static_cast<size_t>(n) >= static_cast<size_t>(s->cfg.max_inflight)) break;
+                    Drone& d = s->drones[it->drone];
+                    if (d.busy) {
+                        ++it;
+                        continue;
+                    }
+                    const int rc = ensure_context(s, it->drone, d);
+                    if (rc == 1) break;                   // wait for memory to free up
+                    Inflight f{it->ticket, it->drone, it->t_submit};
+                    if (rc != MPPI_OK) {
+                        finish(s, f, rc, {});
+                        it = s->queue.erase(it);
+                        continue;
+                    }
+                    BatchSlot& sl = slots[n];
+                    const int used = ctx_batch_slot(d.ctx, it->state, it->n_gates,
+                                                    it->poses.empty() ? nullptr : it->poses.data(),
+                                                    it->latents.empty() ? nullptr : it->latents.data(), &sl,
+                                                    in + in_used);
+                    if (used < 0) {
+                        sfail(s, used, "drone %d: %s", it->drone, mppi_last_error(d.ctx));
+                        finish(s, f, used, {});
+                        it = s->queue.erase(it);
+                        continue;
+                    }
+                    sl.in_off = static_cast<int>(in_used);
+                    in_used += static_cast<size_t>(used);
+                    sl.roll_form = rollout_form(sl.P);
+                    sl.roll_block0 = roll;
+                    roll += rollout_batch_blocks(sl.P);
+                    sl.tile0 = tiles;
+                    if (sl.mlp) tiles += (sl.P.K * sl.P.H + kTileRows - 1) / kTileRows;
+                    sl.upd_R = update_rollouts_per_block(sl.P.K);
+                    sl.upd_block0 = upd;
+                    upd += (sl.P.K + sl.upd_R - 1) / sl.upd_R;
+                    if (sl.P.H > max_h) max_h = sl.P.H;
+                    if (sl.upd_R > max_r) max_r = sl.upd_R;
+                    ctxs.push_back(d.ctx);
+                    d.busy = true;
+                    d.last_use = ++s->lru_clock;
+                    ++s->admitted;
+                    b.reqs.push_back(f);
+                    ++n;
+                    it = s->queue.erase(it);
+                }
+                if (n > 0) {
+                    const int rc = launch_batch(s, b, n, in_used, roll, tiles, upd, max_h, max_r, ctxs);
+                    if (rc != MPPI_OK) {
+                        for (const Inflight& f : b.reqs) {
+                            finish(s, f, rc, {});
+                            s->drones[f.drone].busy = false;
+                        }
+                        b.reqs.clear();
+                    } else {
+                        for (mppi_ctx* c : ctxs) ctx_batch_launched(c);
+                        b.busy = true;
+                        s->order.push_back(fb);
+                        ++s->batches;
+                    }
+                    progress = true;
+                }
+            }
+            idle = s->queue.empty() && s->order.empty();
+            if (idle && s->stop) break;
+        }
+        if (idle)
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        else if (!progress)
+            std::this_thread::yield();
+    }
+}
+
 bool finite(const float* x, size_t n) {
     for (size_t i = 0; i < n; ++i)
         if (!(x[i] == x[i]) || x[i] > 3.0e38f || x[i] < -3.0e38f) return false;
@@ -248,7 +438,8 @@ void mppi_server_config_default(mppi_server_config* c) {
     std::memset(c, 0, sizeof(*c));
     c->hbm_budget_bytes = 0;
     c->max_inflight = 16;
-    c->sdf_mode = MPPI_SDF_MLP_BF16;
+    c->sdf_mode = MPPI_SDF_MLP_FP16;
+    c->batching = 1;
 }
 
 int mppi_server_create(const mppi_server_config* cfg, mppi_server** out) {
@@ -265,7 +456,27 @@ int mppi_server_create(const mppi_server_config* cfg, mppi_server** out) {
         delete s;
         return sfail(nullptr, MPPI_E_UNSUPPORTED, "no CUDA device");
     }
-    s->worker = std::thread(worker_loop, s);
+    if (cfg->batching) {
+        // two batch buffers of max_inflight slots and inputs each, a stream and the batches' error words
+        s->slots_bytes = (static_cast<size_t>(cfg->max_inflight) * sizeof(mppi::BatchSlot) + 255) & ~size_t(255);
+        const size_t bytes = s->slots_bytes + static_cast<size_t>(cfg->max_inflight) * kBatchInFloats * sizeof(float);
+        bool ok = cudaStreamCreateWithFlags(&s->bstream, cudaStreamNonBlocking) == cudaSuccess;
+        for (BatchBuf& b : s->buf) {
+            ok = ok && cudaMallocHost(&b.h, bytes) == cudaSuccess && cudaMalloc(&b.d, bytes) == cudaSuccess &&
+                 cudaHostAlloc(&b.h_err, sizeof(int), cudaHostAllocMapped) == cudaSuccess &&
+                 cudaHostGetDevicePointer(reinterpret_cast<void**>(&b.d_err), b.h_err, 0) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) == cudaSuccess;
+            if (ok) *b.h_err = 0;
+        }
+        if (!ok) {
+            cudaGetLastError();
+            mppi_server_destroy(s);
+            return sfail(nullptr, MPPI_E_OOM, "batch buffers could not be allocated");
+        }
+        s->worker = std::thread(batched_worker_loop, s);
+    } else {
+        s->worker = std::thread(worker_loop, s);
+    }
     *out = s;
     return MPPI_OK;
 }
@@ -277,8 +488,16 @@ void mppi_server_destroy(mppi_server* s) {
         s->stop = true;
     }
     if (s->worker.joinable()) s->worker.join();
+    if (s->bstream) cudaStreamSynchronize(s->bstream);
     for (auto& kv : s->drones)
         if (kv.second.ctx) mppi_destroy(kv.second.ctx);
+    for (BatchBuf& b : s->buf) {
+        if (b.h) cudaFreeHost(b.h);
+        if (b.d) cudaFree(b.d);
+        if (b.h_err) cudaFreeHost(b.h_err);
+        if (b.done) cudaEventDestroy(b.done);
+    }
+    if (s->bstream) cudaStreamDestroy(s->bstream);
     delete s;
 }
 
@@ -321,6 +540,16 @@ int mppi_server_submit(mppi_server* s, int drone_id, const mppi_config* cfg, con
     std::lock_guard<std::mutex> lock(s->mu);
     if (s->cfg.sdf_mode != MPPI_SDF_ANALYTIC && !s->have_weights)
         return sfail(s, MPPI_E_NOT_READY, "no SDF weights set");
+    if (s->cfg.batching) {
+        // one batched SDF launch serves every drone: they share the softplus sharpness and encoding levels
+        if (s->pe_levels < 0) {
+            s->beta = cfg->softplus_beta;
+            s->pe_levels = cfg->pe_levels;
+        } else if (cfg->softplus_beta != s->beta || cfg->pe_levels != s->pe_levels) {
+            return sfail(s, MPPI_E_INVALID, "drone %d: softplus_beta and pe_levels must match the server's drones",
+                         drone_id);
+        }
+    }
     auto it = s->drones.find(drone_id);
     if (it == s->drones.end()) {
         Drone d;
@@ -380,11 +609,14 @@ int mppi_server_get_stats(mppi_server* s, mppi_server_stats* out) {
     out->submitted = s->next_ticket - 1;
     out->completed = s->completed;
     out->queued = s->queue.size();
-    out->inflight = s->inflight.size();
+    size_t batched = 0;
+    for (int i : s->order) batched += s->buf[i].reqs.size();
+    out->inflight = s->inflight.size() + batched;
     out->evictions = s->evictions;
     out->restores = s->restores;
     out->device_bytes = s->used_bytes;
     out->peak_device_bytes = s->peak_bytes;
+    out->batches = s->batches;
     return MPPI_OK;
 }
 

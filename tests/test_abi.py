@@ -68,3 +68,21 @@ def test_defaults_and_create_without_gpu(built):
         with pytest.raises(binding.MppiError) as e:
             binding.mppi_create(cfg)
         assert e.value.code == binding.MPPI_E_UNSUPPORTED
+
+
+def test_server_and_other_struct_layouts_match_header(built, tmp_path):
+    """Every struct the binding mirrors has the header's size (a field added on one side only
+    would shift the others')."""
+    src = tmp_path / "sz2.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mppi.h"\n'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(mppi_server_config),'
+                   ' offsetof(mppi_server_config, batching), sizeof(mppi_server_stats),'
+                   ' offsetof(mppi_server_stats, batches), sizeof(mppi_train_config), sizeof(mppi_depth_camera));'
+                   ' return 0;}\n')
+    exe = tmp_path / "sz2"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()))
+    from paper_2603_07199_gb300 import binding
+    assert vals == [ctypes.sizeof(binding.MppiServerConfig), binding.MppiServerConfig.batching.offset,
+                    ctypes.sizeof(binding.MppiServerStats), binding.MppiServerStats.batches.offset,
+                    ctypes.sizeof(binding.MppiTrainConfig), ctypes.sizeof(binding.MppiDepthCamera)]

@@ -3,7 +3,10 @@
 The bar: every drone's results are the same alone and in the mix (bit-identical:
 each drone's warm start and Philox counter live on the device, and every kernel
 reduces in a fixed order), also when a small device-memory budget forces its
-context to be evicted to host memory and restored between requests.
+context to be evicted to host memory and restored between requests.  Both
+engines are held to it: batched launches (every admissible request of a window
+in one set of launches) and one captured step graph per drone; the batched
+engine's results also equal the per-drone engine's and mppi_step's bit for bit.
 """
 import time
 
@@ -18,16 +21,21 @@ from .gpu_helpers import flat_layers, make_config
 pytestmark = pytest.mark.gpu
 
 
+MODES = {"bf16": B.MPPI_SDF_MLP_BF16, "fp16": B.MPPI_SDF_MLP_FP16, "fp8": B.MPPI_SDF_MLP_FP8,
+         "fp32": B.MPPI_SDF_MLP_FP32, "analytic": B.MPPI_SDF_ANALYTIC}
+
+
 def _drone_cfg(d, mode="bf16"):
     return make_config(d["params"], mode, d["G"])
 
 
-def _run(fleet, requests, budget=0, max_inflight=16, mode="bf16", layers=None):
+def _run(fleet, requests, budget=0, max_inflight=16, mode="bf16", layers=None, batching=1):
     """Submit (drone index, state) requests in order without waiting; return controls per request."""
     cfg = B.mppi_server_config_default()
     cfg.hbm_budget_bytes = budget
     cfg.max_inflight = max_inflight
-    cfg.sdf_mode = {"bf16": B.MPPI_SDF_MLP_BF16, "fp32": B.MPPI_SDF_MLP_FP32, "analytic": B.MPPI_SDF_ANALYTIC}[mode]
+    cfg.sdf_mode = MODES[mode]
+    cfg.batching = batching
     srv = B.mppi_server_create(cfg)
     keep = flat_layers(layers) if layers is not None else None
     if keep is not None:
@@ -61,20 +69,53 @@ def _states(fleet, n_steps, seed=7):
         [1, 1, 1, 1, 1, 1, 0, 0, 0, 0, 1, 1, 1], np.float32) for _ in range(n_steps)] for i, d in enumerate(fleet)}
 
 
-def test_results_are_the_same_alone_and_in_the_mix(lib):
+@pytest.mark.parametrize("batching", [1, 0])
+def test_results_are_the_same_alone_and_in_the_mix(lib, batching):
     fleet = W.serving_fleet(8, seed=4, Ks=(256, 512, 1024), Hs=(10, 20, 30))
     layers = W.xavier_mlp(1)
     n_steps = 4
     states = _states(fleet, n_steps)
     target = 3
-    alone, _, _ = _run(fleet, [(target, states[target][s]) for s in range(n_steps)], layers=layers)
+    alone, _, _ = _run(fleet, [(target, states[target][s]) for s in range(n_steps)], layers=layers, batching=batching)
     mix_reqs = [(i, states[i][s]) for s in range(n_steps) for i in range(len(fleet))]
-    mix, lats, stats = _run(fleet, mix_reqs, layers=layers)
+    mix, lats, stats = _run(fleet, mix_reqs, layers=layers, batching=batching)
     got = [mix[j] for j, (i, _) in enumerate(mix_reqs) if i == target]
     for a, b in zip(alone, got):
         np.testing.assert_array_equal(a, b)
     assert stats["completed"] == len(mix_reqs) and stats["evictions"] == 0
     assert all(l > 0 for l in lats)
+    if batching:
+        assert 0 < stats["batches"] < len(mix_reqs)      # several drones' steps shared launches
+
+
+def _mixed_fleet():
+    """Drones that take every rollout form: a warp per rollout (H > 32, K < 8192), half warps with
+    two and four steps per lane (H <= 32; K >= 8192), and the rotor-thrust-rate model."""
+    fleet = W.serving_fleet(4, seed=21, Ks=(300,), Hs=(50,))
+    fleet[1]["params"] = dict(fleet[1]["params"], K=256, H=10)
+    fleet[2]["params"] = dict(fleet[2]["params"], K=8192, H=40)
+    rot = fleet[3]
+    rot["params"] = dict(W.rotor_params(512, 20), seed=rot["params"]["seed"], drone_id=rot["params"]["drone_id"])
+    rot["state"] = W.rotor_state([0.2, -0.1, 0.3])
+    return fleet
+
+
+@pytest.mark.parametrize("mode", ["fp16", "bf16", "fp8", "fp32", "analytic"])
+def test_batched_engine_equals_per_drone_engine(lib, mode):
+    """The batched launches give every drone the results of its own step graph, bit for bit, in
+    every SDF mode (FP32 runs its SDF kernel per drone inside the batch) and for every rollout form."""
+    fleet = _mixed_fleet()
+    layers = W.xavier_mlp(1)
+    n_steps = 3
+    rng = np.random.default_rng(22)
+    states = {i: [np.asarray(d["state"], np.float32) + np.float32(0.05) * rng.standard_normal(len(d["state"])).astype(
+        np.float32) * (np.arange(len(d["state"])) < 6) for _ in range(n_steps)] for i, d in enumerate(fleet)}
+    reqs = [(i, states[i][s]) for s in range(n_steps) for i in range(len(fleet))]
+    batched, _, st_b = _run(fleet, reqs, mode=mode, layers=layers, batching=1)
+    per_drone, _, _ = _run(fleet, reqs, mode=mode, layers=layers, batching=0)
+    for a, b in zip(batched, per_drone):
+        np.testing.assert_array_equal(a, b)
+    assert st_b["batches"] < len(reqs)
 
 
 def test_small_budget_evicts_and_restores_without_changing_results(lib):
@@ -92,13 +133,14 @@ def test_small_budget_evicts_and_restores_without_changing_results(lib):
         np.testing.assert_array_equal(a, b)
 
 
-def test_serving_matches_a_plain_context(lib):
+@pytest.mark.parametrize("batching", [1, 0])
+def test_serving_matches_a_plain_context(lib, batching):
     """One drone through the server equals the same steps through mppi_step."""
     fleet = W.serving_fleet(1, seed=11, Ks=(700,), Hs=(12,))
     layers = W.xavier_mlp(1)
     d = fleet[0]
     states = _states(fleet, 3, seed=12)[0]
-    served, _, _ = _run(fleet, [(0, s) for s in states], layers=layers)
+    served, _, _ = _run(fleet, [(0, s) for s in states], layers=layers, batching=batching)
     ctx = B.mppi_create(_drone_cfg(d))
     keep = flat_layers(layers)
     B.mppi_set_sdf_weights(ctx, keep)
