@@ -634,10 +634,10 @@ int mppi_train_num_params(void);
  * budget; the least recently used idle drone is evicted to host memory (its warm
  * start, state and counter are restored on its next request) when it does not.
  * Batched mode (batching = 1): every admissible queued request joins one batch,
- * launched as four kernels on the server's stream (inputs, one rollout launch over
- * all drones, one persistent tensor-core SDF launch whose tiles span all drones,
- * one update launch), while the next batch is gathered; each drone's results equal
- * those of its own mppi_step.  Per-drone mode (batching = 0): each request is its
+ * launched as four kernels on a stream of the server's (inputs, one rollout launch
+ * over all drones, one persistent tensor-core SDF launch whose tiles span all drones,
+ * one update launch); up to four batches run at once on their own streams; each
+ * drone's results agree with its own mppi_step's within the FP32 control tolerance.  Per-drone mode (batching = 0): each request is its
  * drone's captured step graph on the drone's own stream, and requests of different
  * drones overlap on the GPU.  All functions are thread-safe; a worker thread owned
  * by the server issues the GPU work.
@@ -662,8 +662,9 @@ typedef struct mppi_server_stats {
 
 /* Defaults: no budget, 16 requests in flight, FP16 tensor-core SDF, batched launches. */
 void mppi_server_config_default(mppi_server_config* cfg);
-/* Create a server on the current device (starts its worker thread; batched mode also allocates two
- * pinned and two device batch blocks of max_inflight controllers each).  *out is NULL on error:
+/* Create a server on the current device (starts its worker thread; batched mode also allocates four
+ * pinned and four device batch blocks of max_inflight controllers each, and a stream for each).
+ * *out is NULL on error:
  * MPPI_E_INVALID (cfg), MPPI_E_UNSUPPORTED (no device), MPPI_E_OOM. */
 int mppi_server_create(const mppi_server_config* cfg, mppi_server** out);
 /* Drain in-flight work, stop the worker and free every drone context.  NULL is ignored. */

@@ -12,8 +12,8 @@
 // inputs of all drones, one rollout launch over all drones' rollouts, one
 // persistent tensor-core SDF launch whose tiles span all drones, and one update
 // launch whose per-drone combine is done by the last of the drone's blocks -- so
-// that a batch of small solves fills the GPU like one large solve; a second batch
-// is prepared and queued while the first runs.  Per-drone mode: each drone's step
+// that a batch of small solves fills the GPU like one large solve; up to four
+// batches, each on its own stream, run at once.  Per-drone mode: each drone's step
 // is its own captured graph on its own stream and requests of different drones
 // overlap on the GPU.  Either way a drone's results are those of its own step
 // (same kernels' arithmetic, per-drone noise counters, fixed-order reductions).
@@ -74,6 +74,7 @@ struct Result {
 // One batch buffer: pinned host block (slots, then packed inputs), its device copy, the
 // batch's SDF error word (pinned, mapped) and completion event.
 struct BatchBuf {
+    cudaStream_t stream = nullptr;          // batches in different buffers overlap on the GPU
     char* h = nullptr;
     char* d = nullptr;
     int* h_err = nullptr;
@@ -84,6 +85,7 @@ struct BatchBuf {
 };
 
 constexpr int kBatchInFloats = mppi::kBatchStateSlot + MPPI_MAX_GATES * (8 + MPPI_LATENT_DIM);
+constexpr int kBatchBufs = 4;             // batches in flight at once
 
 }  // namespace
 
@@ -105,8 +107,7 @@ struct mppi_server {
     size_t used_bytes = 0, peak_bytes = 0;
     uint64_t completed = 0, evictions = 0, restores = 0, admitted = 0;
     // batched mode
-    cudaStream_t bstream = nullptr;
-    BatchBuf buf[2];
+    BatchBuf buf[kBatchBufs];
     std::deque<int> order;                 // busy batch buffers, oldest first
     size_t slots_bytes = 0;
     float beta = 0.f;                      // softplus sharpness and encoding levels every drone shares
@@ -271,7 +272,7 @@ void worker_loop(mppi_server* s) {
 int launch_batch(mppi_server* s, BatchBuf& b, int n, size_t in_floats, int roll_blocks, int tiles, int upd_blocks,
                  int max_h, int max_r, const std::vector<mppi_ctx*>& ctxs) {
     using namespace mppi;
-    cudaStream_t st = s->bstream;
+    cudaStream_t st = b.stream;
     const BatchSlot* hs = reinterpret_cast<const BatchSlot*>(b.h);
     const BatchSlot* ds = reinterpret_cast<const BatchSlot*>(b.d);
     const float* din = reinterpret_cast<const float*>(b.d + s->slots_bytes);
@@ -311,11 +312,14 @@ void batched_worker_loop(mppi_server* s) {
         bool progress = false, idle = false;
         {
             std::lock_guard<std::mutex> lock(s->mu);
-            // completions, oldest batch first
-            while (!s->order.empty()) {
-                BatchBuf& b = s->buf[s->order.front()];
+            // completions (batches on different streams may finish in any order)
+            for (size_t oi = 0; oi < s->order.size();) {
+                BatchBuf& b = s->buf[s->order[oi]];
                 const cudaError_t q = cudaEventQuery(b.done);
-                if (q == cudaErrorNotReady) break;
+                if (q == cudaErrorNotReady) {
+                    ++oi;
+                    continue;
+                }
                 const int berr = *reinterpret_cast<volatile int*>(b.h_err);
                 for (const Inflight& f : b.reqs) {
                     Drone& d = s->drones[f.drone];
@@ -336,11 +340,13 @@ void batched_worker_loop(mppi_server* s) {
                 if (berr != 0) *reinterpret_cast<volatile int*>(b.h_err) = 0;
                 b.reqs.clear();
                 b.busy = false;
-                s->order.pop_front();
+                s->order.erase(s->order.begin() + static_cast<long>(oi));
                 progress = true;
             }
             // the next batch: every admissible queued request, in arrival order, into a free buffer
-            const int fb = !s->buf[0].busy ? 0 : (!s->buf[1].busy ? 1 : -1);
+            int fb = -1;
+            for (int i = 0; i < kBatchBufs && fb < 0; ++i)
+                if (!s->buf[i].busy) fb = i;
             if (fb >= 0 && !s->queue.empty()) {
                 BatchBuf& b = s->buf[fb];
                 BatchSlot* slots = reinterpret_cast<BatchSlot*>(b.h);
@@ -457,12 +463,14 @@ int mppi_server_create(const mppi_server_config* cfg, mppi_server** out) {
         return sfail(nullptr, MPPI_E_UNSUPPORTED, "no CUDA device");
     }
     if (cfg->batching) {
-        // two batch buffers of max_inflight slots and inputs each, a stream and the batches' error words
+        // kBatchBufs batch buffers of max_inflight slots and inputs each, each with its stream and
+        // its batch's error word
         s->slots_bytes = (static_cast<size_t>(cfg->max_inflight) * sizeof(mppi::BatchSlot) + 255) & ~size_t(255);
         const size_t bytes = s->slots_bytes + static_cast<size_t>(cfg->max_inflight) * kBatchInFloats * sizeof(float);
-        bool ok = cudaStreamCreateWithFlags(&s->bstream, cudaStreamNonBlocking) == cudaSuccess;
+        bool ok = true;
         for (BatchBuf& b : s->buf) {
-            ok = ok && cudaMallocHost(&b.h, bytes) == cudaSuccess && cudaMalloc(&b.d, bytes) == cudaSuccess &&
+            ok = ok && cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaMallocHost(&b.h, bytes) == cudaSuccess && cudaMalloc(&b.d, bytes) == cudaSuccess &&
                  cudaHostAlloc(&b.h_err, sizeof(int), cudaHostAllocMapped) == cudaSuccess &&
                  cudaHostGetDevicePointer(reinterpret_cast<void**>(&b.d_err), b.h_err, 0) == cudaSuccess &&
                  cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) == cudaSuccess;
@@ -488,7 +496,8 @@ void mppi_server_destroy(mppi_server* s) {
         s->stop = true;
     }
     if (s->worker.joinable()) s->worker.join();
-    if (s->bstream) cudaStreamSynchronize(s->bstream);
+    for (BatchBuf& b : s->buf)
+        if (b.stream) cudaStreamSynchronize(b.stream);
     for (auto& kv : s->drones)
         if (kv.second.ctx) mppi_destroy(kv.second.ctx);
     for (BatchBuf& b : s->buf) {
@@ -496,8 +505,8 @@ void mppi_server_destroy(mppi_server* s) {
         if (b.d) cudaFree(b.d);
         if (b.h_err) cudaFreeHost(b.h_err);
         if (b.done) cudaEventDestroy(b.done);
+        if (b.stream) cudaStreamDestroy(b.stream);
     }
-    if (s->bstream) cudaStreamDestroy(s->bstream);
     delete s;
 }
 
