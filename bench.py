@@ -43,8 +43,9 @@ TENSOR_FLOPS_PER_QUERY = 3 * 2 * 128 * 128           # layers 2..4 on tcgen05
 FMA_FLOPS_PER_QUERY = 2 * 3 * 128 + 2 * 128           # layer 1 (point part) + output dot
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the headline SDF kernel at this
 # workload, from an ncu capture of the current kernel (None when the kernel changed since)
-SDF_DRAM_BYTES = None
-SDF_DRAM_BYTES_SOURCE = "no ncu capture of the current kernel yet"
+SDF_DRAM_BYTES = 3416832 + 0
+SDF_DRAM_BYTES_SOURCE = ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture (--set full) of the "
+                         "current FP16 kernel at K=4096, H=50, G=2 (a constant in bench.py, not measured in this run)")
 HEADLINE_MODE = "fp16"
 # multiply-adds x 2 of the depth encoder's convolutions and head for one 160 x 120 image
 ENCODER_FLOPS_PER_IMAGE_160x120 = 2 * (60 * 80 * 16 * 9 * 1 + 30 * 40 * 32 * 9 * 16 + 15 * 20 * 64 * 9 * 32
@@ -63,8 +64,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-seconds", type=float, default=1.0)
     ap.add_argument("--distill-steps", type=int, default=0)
-    ap.add_argument("--distill-schedule", default="constant", choices=["constant", "cosine"],
-                    help="Adam learning rate of the distillation: constant 1e-3, or 1e-3 cosine-decayed over the steps")
+    ap.add_argument("--distill-schedule", default="constant", choices=["constant", "cosine", "warmup-cosine"],
+                    help="Adam learning rate of the distillation: constant, cosine-decayed from the peak over the "
+                         "steps, or a linear warm-up to the peak followed by the cosine decay")
+    ap.add_argument("--distill-peak-lr", type=float, default=1e-3)
+    ap.add_argument("--distill-warmup", type=int, default=1000)
     ap.add_argument("--four-gate-steps", type=int, default=20)
     ap.add_argument("--render-steps", type=int, default=20)
     ap.add_argument("--vision-steps", type=int, default=20)
@@ -407,7 +411,7 @@ def serving_leg(torch, B, dev, duration_s, n_drones=64, rate_hz=100.0, loads=(1,
                            "solve_ms_by_config": {f"K{k}_H{h}_G{g}": t for (k, h, g), t in t32.items()}}}
 
 
-def distill_leg(torch, B, dev, steps, schedule="constant"):
+def distill_leg(torch, B, dev, steps, schedule="constant", peak_lr=1e-3, warmup=1000):
     """Distil the exact frame SDF into the Gate-SDF MLP (2^21 points, batch 65536, Adam 1e-3,
     L1 + 0.1 Eikonal), then run the two-gate workload with the learned, the exact and the
     untrained SDF.  The learned SDF is used only when its held-out error stays within 5 mm
@@ -422,15 +426,20 @@ def distill_leg(torch, B, dev, steps, schedule="constant"):
     before = B.mppi_train_evaluate(tr)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    if schedule == "cosine":
-        # 1e-3 at the start, decayed by a half cosine over the run, set once per 500-step chunk
-        done, chunk, loss = 0, 500, None
+    if schedule in ("cosine", "warmup-cosine"):
+        # the peak rate, decayed by a half cosine over the run (after a linear warm-up over `warmup`
+        # steps for warmup-cosine), set once per 250-step chunk at the chunk's midpoint
+        w = warmup if schedule == "warmup-cosine" else 0
+        done, chunk, loss = 0, 250, None
         while done < steps:
             n = min(chunk, steps - done)
-            B.mppi_train_set_lr(tr, cfg.lr * 0.5 * (1.0 + np.cos(np.pi * (done + 0.5 * n) / steps)))
+            mid = done + 0.5 * n
+            lr = peak_lr * mid / w if mid < w else peak_lr * 0.5 * (1.0 + np.cos(np.pi * (mid - w) / max(1, steps - w)))
+            B.mppi_train_set_lr(tr, lr)
             loss = B.mppi_train_step(tr, n)
             done += n
     else:
+        B.mppi_train_set_lr(tr, peak_lr)
         loss = B.mppi_train_step(tr, steps)
     train_s = time.perf_counter() - t0
     after = B.mppi_train_evaluate(tr)
@@ -473,7 +482,8 @@ def distill_leg(torch, B, dev, steps, schedule="constant"):
         B.mppi_destroy(ctx)
     div = {n: float(np.max(np.abs(outs[n][0] - outs["exact"][0]))) for n in ("learned", "untrained")}
     pos_div = {n: float(np.linalg.norm(outs[n][1][:3] - outs["exact"][1][:3])) for n in ("learned", "untrained")}
-    return {"steps": steps, "schedule": schedule, "batch": cfg.batch, "points": cfg.n_points, "train_s": train_s,
+    return {"steps": steps, "schedule": schedule, "peak_lr": peak_lr, "warmup_steps": warmup if schedule == "warmup-cosine"
+            else 0, "batch": cfg.batch, "points": cfg.n_points, "train_s": train_s,
             "steps_per_s": steps / train_s if train_s > 0 else None, "final_loss": loss,
             "holdout_before_mm": {k: v * 1e3 for k, v in before.items()},
             "holdout_after_mm": {k: v * 1e3 for k, v in after.items()},
@@ -855,7 +865,8 @@ def run_ours(args):
               if args.render_steps > 0 else None)
     vision = vision_leg(torch, B, stream, flush, dev, args.vision_steps, rank) if args.vision_steps > 0 else None
     serving = serving_leg(torch, B, dev, args.serving_seconds) if args.serving_seconds > 0 else None
-    distill = distill_leg(torch, B, dev, args.distill_steps, args.distill_schedule) if args.distill_steps > 0 else None
+    distill = (distill_leg(torch, B, dev, args.distill_steps, args.distill_schedule, args.distill_peak_lr,
+                           args.distill_warmup) if args.distill_steps > 0 else None)
 
     if rank != 0:
         if world > 1:

@@ -125,16 +125,41 @@ def test_batched_engine_equals_per_drone_engine(lib, mode):
 
 
 def test_batched_engine_shares_launches(lib):
-    """32 drones' requests submitted back to back cannot all get a batch of their own (four
-    batches run at once): several drones' steps share launches, with the per-drone results."""
+    """After one warm-up request per drone (which creates the drones' contexts), 32 drones' next
+    requests submitted back to back cannot all get a batch of their own (four batches run at
+    once): several drones' steps share launches, with the per-drone engine's results."""
     fleet = W.serving_fleet(32, seed=31, Ks=(256, 512), Hs=(10, 20))
     layers = W.xavier_mlp(1)
-    states = _states(fleet, 1, seed=32)
-    reqs = [(i, states[i][0]) for i in range(len(fleet))]
-    batched, _, st_b = _run(fleet, reqs, mode="fp16", layers=layers, batching=1, max_inflight=64)
-    per_drone, _, _ = _run(fleet, reqs, mode="fp16", layers=layers, batching=0, max_inflight=64)
-    assert st_b["batches"] < len(reqs)
-    for a, b in zip(batched, per_drone):
+    states = _states(fleet, 3, seed=32)
+    reqs = [(i, states[i][s]) for s in range(3) for i in range(len(fleet))]
+    results = {}
+    for batching in (1, 0):
+        cfg = B.mppi_server_config_default()
+        cfg.max_inflight = 64
+        cfg.sdf_mode = MODES["fp16"]
+        cfg.batching = batching
+        srv = B.mppi_server_create(cfg)
+        B.mppi_server_set_sdf_weights(srv, flat_layers(layers))
+        outs = []
+        for phase in (reqs[:32], reqs[32:]):
+            if phase is reqs[32:]:
+                b0 = B.mppi_server_get_stats(srv)["batches"]
+            tickets = [B.mppi_server_submit(srv, fleet[i]["drone_id"], _drone_cfg(fleet[i], "fp16"),
+                                            np.ascontiguousarray(st, np.float32), fleet[i]["G"],
+                                            np.ascontiguousarray(fleet[i]["poses"]),
+                                            np.ascontiguousarray(fleet[i]["latents"])) for i, st in phase]
+            for (i, _), t in zip(phase, tickets):
+                U = np.zeros((fleet[i]["params"]["H"], 4), np.float32)
+                t0 = time.time()
+                while B.mppi_server_poll(srv, t, U)[0] != B.MPPI_OK:
+                    assert time.time() - t0 < 60, "request did not finish"
+                    time.sleep(0.0002)
+                outs.append(U)
+        batches = B.mppi_server_get_stats(srv)["batches"] - b0
+        B.mppi_server_destroy(srv)
+        results[batching] = (outs, batches)
+    assert 0 < results[1][1] < len(reqs) - 32
+    for a, b in zip(results[1][0], results[0][0]):
         np.testing.assert_allclose(a, b, atol=CTRL_ATOL, rtol=0)
 
 
