@@ -140,9 +140,9 @@ def test_batched_engine_shares_launches(lib):
         cfg.batching = batching
         srv = B.mppi_server_create(cfg)
         B.mppi_server_set_sdf_weights(srv, flat_layers(layers))
-        outs = []
-        for phase in (reqs[:32], reqs[32:]):
-            if phase is reqs[32:]:
+        outs, b0 = [], 0
+        for n_phase, phase in enumerate((reqs[:32], reqs[32:])):
+            if n_phase == 1:                  # contexts exist: count the batches of the second phase
                 b0 = B.mppi_server_get_stats(srv)["batches"]
             tickets = [B.mppi_server_submit(srv, fleet[i]["drone_id"], _drone_cfg(fleet[i], "fp16"),
                                             np.ascontiguousarray(st, np.float32), fleet[i]["G"],
