@@ -172,3 +172,28 @@ def test_learned_sdf_steers_mppi_like_the_exact_one(lib):
         assert l["sdf_mae"] < 0.2 * u["sdf_mae"], (l, u)
         assert l["cost_corr"] > u["cost_corr"] and l["cost_corr"] > 0.9, (l, u)
     assert np.mean([l["ctrl"] for l in L]) < np.mean([u["ctrl"] for u in U]), (L, U)
+
+
+def test_configured_distillation_passes_the_5mm_bar(lib):
+    """The configured distillation (2^21 points, batch 65,536, 20,000 Adam steps, L1 + 0.1
+    Eikonal) with a linear warm-up to 2e-3 over 1,000 steps and a half-cosine decay to 0 (mean
+    rate 1e-3): the held-out error against the exact SDF stays within 5 mm in the mean and at
+    p99 within 0.3 m of the frame, so the learned network replaces the exact SDF.  (About 150 s;
+    the training is deterministic: 1.17 mm and 4.46 mm measured.)"""
+    cfg = B.mppi_train_config_default()
+    tr = B.mppi_train_create(cfg, flat_layers(W.xavier_mlp(1)), W.latents(1, seed=2)[0])
+    try:
+        steps, warmup, peak, done = 20000, 1000, 2e-3, 0
+        while done < steps:
+            n = min(250, steps - done)
+            mid = done + 0.5 * n
+            lr = peak * mid / warmup if mid < warmup else \
+                peak * 0.5 * (1.0 + np.cos(np.pi * (mid - warmup) / (steps - warmup)))
+            B.mppi_train_set_lr(tr, lr)
+            B.mppi_train_step(tr, n)
+            done += n
+        ev = B.mppi_train_evaluate(tr)
+    finally:
+        B.mppi_train_destroy(tr)
+    print({k: v * 1e3 for k, v in ev.items()})
+    assert ev["mae"] <= 5e-3 and ev["near_p99"] <= 5e-3, ev
