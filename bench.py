@@ -69,6 +69,8 @@ def parse():
                          "steps, or a linear warm-up to the peak followed by the cosine decay")
     ap.add_argument("--distill-peak-lr", type=float, default=1e-3)
     ap.add_argument("--distill-warmup", type=int, default=1000)
+    ap.add_argument("--distill-gemm", default="bf16", choices=["bf16", "fp32"],
+                    help="precision of the distillation's hidden-layer GEMMs (BF16 tensor cores or FP32 CUDA cores)")
     ap.add_argument("--four-gate-steps", type=int, default=20)
     ap.add_argument("--render-steps", type=int, default=20)
     ap.add_argument("--vision-steps", type=int, default=20)
@@ -411,18 +413,34 @@ def serving_leg(torch, B, dev, duration_s, n_drones=64, rate_hz=100.0, loads=(1,
                            "solve_ms_by_config": {f"K{k}_H{h}_G{g}": t for (k, h, g), t in t32.items()}}}
 
 
-def distill_leg(torch, B, dev, steps, schedule="constant", peak_lr=1e-3, warmup=1000):
+def distill_leg(torch, B, dev, steps, schedule="constant", peak_lr=1e-3, warmup=1000, gemm="bf16"):
     """Distil the exact frame SDF into the Gate-SDF MLP (2^21 points, batch 65536, Adam 1e-3,
     L1 + 0.1 Eikonal), then run the two-gate workload with the learned, the exact and the
     untrained SDF.  The learned SDF is used only when its held-out error stays within 5 mm
-    (mean, and p99 of the points within 0.3 m of the frame); otherwise the exact SDF is kept."""
+    (mean, and p99 of the points within 0.3 m of the frame); otherwise the exact SDF is kept.
+    `gemm` selects the hidden-layer GEMMs of training; the steps/s of both precisions are
+    reported (the other one over a short run from the same start)."""
     import workloads as W
     cfg = B.mppi_train_config_default()
     init = []
     for Wm, b in W.xavier_mlp(1):
         init += [np.ascontiguousarray(Wm, np.float32), np.ascontiguousarray(b, np.float32)]
     z0 = W.latents(1, seed=2)[0]
+    prec = {"bf16": B.MPPI_TRAIN_GEMM_BF16, "fp32": B.MPPI_TRAIN_GEMM_FP32}
+
+    def rate(which, n=100):
+        t = B.mppi_train_create(cfg, init, z0)
+        B.mppi_train_set_gemm_precision(t, prec[which])
+        B.mppi_train_step(t, 5)
+        t1 = time.perf_counter()
+        B.mppi_train_step(t, n)
+        r = n / (time.perf_counter() - t1)
+        B.mppi_train_destroy(t)
+        return r
+
+    rates = {k: rate(k) for k in ("fp32", "bf16")}
     tr = B.mppi_train_create(cfg, init, z0)
+    B.mppi_train_set_gemm_precision(tr, prec[gemm])
     before = B.mppi_train_evaluate(tr)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -483,8 +501,9 @@ def distill_leg(torch, B, dev, steps, schedule="constant", peak_lr=1e-3, warmup=
     div = {n: float(np.max(np.abs(outs[n][0] - outs["exact"][0]))) for n in ("learned", "untrained")}
     pos_div = {n: float(np.linalg.norm(outs[n][1][:3] - outs["exact"][1][:3])) for n in ("learned", "untrained")}
     return {"steps": steps, "schedule": schedule, "peak_lr": peak_lr, "warmup_steps": warmup if schedule == "warmup-cosine"
-            else 0, "batch": cfg.batch, "points": cfg.n_points, "train_s": train_s,
-            "steps_per_s": steps / train_s if train_s > 0 else None, "final_loss": loss,
+            else 0, "gemm": gemm, "batch": cfg.batch, "points": cfg.n_points, "train_s": train_s,
+            "steps_per_s": steps / train_s if train_s > 0 else None,
+            "steps_per_s_100_step_runs": rates, "final_loss": loss,
             "holdout_before_mm": {k: v * 1e3 for k, v in before.items()},
             "holdout_after_mm": {k: v * 1e3 for k, v in after.items()},
             "fallback_to_exact_sdf": not use_learned,
@@ -866,7 +885,7 @@ def run_ours(args):
     vision = vision_leg(torch, B, stream, flush, dev, args.vision_steps, rank) if args.vision_steps > 0 else None
     serving = serving_leg(torch, B, dev, args.serving_seconds) if args.serving_seconds > 0 else None
     distill = (distill_leg(torch, B, dev, args.distill_steps, args.distill_schedule, args.distill_peak_lr,
-                           args.distill_warmup) if args.distill_steps > 0 else None)
+                           args.distill_warmup, args.distill_gemm) if args.distill_steps > 0 else None)
 
     if rank != 0:
         if world > 1:

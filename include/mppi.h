@@ -603,6 +603,21 @@ const char* mppi_train_last_error(const mppi_trainer* trainer);
 /* Learning rate of the following steps (> 0, finite): a caller's schedule sets it between calls of
  * mppi_train_step.  Errors: MPPI_E_INVALID. */
 int mppi_train_set_lr(mppi_trainer* trainer, float lr);
+/*
+ * Precision of the hidden layers' GEMMs (layers 2-4: forward values and
+ * tangents, input and weight gradients) in mppi_train_step and
+ * mppi_train_loss_grads.  MPPI_TRAIN_GEMM_FP32 (the default): FP32 on the CUDA
+ * cores.  MPPI_TRAIN_GEMM_BF16: tcgen05 tensor cores with operands rounded to
+ * BF16 and FP32 accumulation; weights, Adam state, activations and adjoints
+ * stay FP32.  mppi_train_evaluate always runs the FP32 forward pass.  Errors:
+ * MPPI_E_INVALID (unknown value), MPPI_E_UNSUPPORTED (BF16 on a device other
+ * than sm_103), MPPI_E_CUDA.  A bounded device wait that gives up inside a
+ * BF16 kernel makes the next mppi_train_step / mppi_train_loss_grads return
+ * MPPI_E_TIMEOUT; the trainer stays usable.
+ */
+#define MPPI_TRAIN_GEMM_FP32 0
+#define MPPI_TRAIN_GEMM_BF16 1
+int mppi_train_set_gemm_precision(mppi_trainer* trainer, int precision);
 /* Run n_steps Adam steps over consecutive batches of the training set; *last_loss (nullable) = last batch's loss. */
 int mppi_train_step(mppi_trainer* trainer, int n_steps, float* last_loss);
 /*

@@ -41,6 +41,10 @@ MPPI_BUF_SDF = 3
 MPPI_BUF_WEIGHTS = 4
 MPPI_BUF_COSTS = 5
 MPPI_DIAG_STORE_SDF = 1
+MPPI_LATENT_DIM = 64
+MPPI_HIDDEN = 128
+MPPI_TRAIN_GEMM_FP32 = 0
+MPPI_TRAIN_GEMM_BF16 = 1
 
 LATENT_DIM = 64
 HIDDEN = 128
@@ -56,7 +60,7 @@ EXPORTS = [
     "mppi_server_set_sdf_weights", "mppi_server_submit", "mppi_server_poll", "mppi_server_next_result",
     "mppi_server_get_stats",
     "mppi_train_config_default", "mppi_train_create", "mppi_train_destroy", "mppi_train_last_error",
-    "mppi_train_step", "mppi_train_set_lr", "mppi_train_loss_grads", "mppi_train_get_weights", "mppi_train_evaluate",
+    "mppi_train_step", "mppi_train_set_lr", "mppi_train_set_gemm_precision", "mppi_train_loss_grads", "mppi_train_get_weights", "mppi_train_evaluate",
     "mppi_train_read_points", "mppi_train_num_params",
     "mppi_depth_camera_default", "mppi_render_depth", "mppi_sample_sdf_queries",
     "mppi_encoder_create", "mppi_encoder_destroy", "mppi_encoder_last_error", "mppi_encode_depth",
@@ -168,6 +172,7 @@ _SIGS = {
     "mppi_train_last_error": (ctypes.c_char_p, [_vp]),
     "mppi_train_step": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
     "mppi_train_set_lr": (ctypes.c_int, [_vp, ctypes.c_float]),
+    "mppi_train_set_gemm_precision": (ctypes.c_int, [_vp, ctypes.c_int]),
     "mppi_train_loss_grads": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float), _vp]),
     "mppi_train_get_weights": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
     "mppi_train_evaluate": (ctypes.c_int, [_vp] + [ctypes.POINTER(ctypes.c_float)] * 4),
@@ -448,6 +453,10 @@ def mppi_train_destroy(trainer):
 
 def mppi_train_set_lr(trainer, lr):
     return _tcheck(load().mppi_train_set_lr(trainer, ctypes.c_float(lr)), trainer)
+
+
+def mppi_train_set_gemm_precision(trainer, precision):
+    return _tcheck(load().mppi_train_set_gemm_precision(trainer, int(precision)), trainer)
 
 
 def mppi_train_step(trainer, n_steps):

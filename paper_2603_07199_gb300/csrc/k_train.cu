@@ -9,7 +9,8 @@
 // the values, "stream" 0 = values, 1..3 = d/dp_x, d/dp_y, d/dp_z) and the whole
 // computation is differentiated in reverse mode; Adam updates FP32 master
 // weights.  Kernels (FP32 on the CUDA cores, 128-point tiles, register-blocked
-// GEMMs through shared memory, deterministic fixed-order reductions):
+// GEMMs through shared memory, deterministic fixed-order reductions; the hidden
+// layers' GEMMs can run instead in BF16 on the tensor cores, k_train_tc.cu):
 //   sample -> [per step] first-layer bias -> forward layer 1 -> forward layers 2..4
 //   -> output + loss + adjoints -> per layer 4..2: weight gradients, input
 //   gradients -> layer-1 gradients -> reduce partials -> Adam.
@@ -23,59 +24,15 @@
 
 #include "kernels.h"
 #include "mppi.h"
+#include "train_internal.cuh"
 
 namespace mppi {
 namespace {
 
-constexpr int kH = kHidden;
-constexpr int kIn = 3 + kLatent;
+using namespace train;
+
 constexpr int kT = 256;
 constexpr int kLd = kH + 4;
-// offsets of the parameters in the flat vector theta: W1 [128][67], b1, W2, b2, W3, b3, W4, b4, w5 [128], b5
-constexpr int oW1 = 0;
-constexpr int oB1 = oW1 + kH * kIn;
-constexpr int oW2 = oB1 + kH;
-constexpr int oB2 = oW2 + kH * kH;
-constexpr int oW3 = oB2 + kH;
-constexpr int oB3 = oW3 + kH * kH;
-constexpr int oW4 = oB3 + kH;
-constexpr int oB4 = oW4 + kH * kH;
-constexpr int oW5 = oB4 + kH;
-constexpr int oB5 = oW5 + kH;
-constexpr int kNumParams = oB5 + 1;
-__host__ __device__ constexpr int offW(int l) { return l == 2 ? oW2 : l == 3 ? oW3 : oW4; }
-__host__ __device__ constexpr int offB(int l) { return l == 2 ? oB2 : l == 3 ? oB3 : oB4; }
-
-struct TrainBufs {
-    float* theta;        // parameters
-    float* grad;         // reduced gradient
-    float* partial;      // [n_cta][kNumParams] per-CTA gradient partials
-    float* b1p;          // [128] b1 + W1[:, 3:] z0
-    float* z0;           // [64]
-    const float4* pts;   // batch points (x, y, z, target)
-    float* A[5];         // A[l]: [B][128] pre-activations of layer l (1..4)
-    float* AT[5];        // AT[l]: [3][B][128] tangents of layer l (2..4)
-    float* dA[5];        // adjoints of A[l]
-    float* dAT[5];       // adjoints of AT[l]
-    float* loss;         // [B] per-point loss
-    int B;
-    float beta, lam_e;
-};
-
-__device__ __forceinline__ float sp_beta(float a, float beta) {
-    return fmaxf(a, 0.f) + log1pf(expf(-beta * fabsf(a))) / beta;
-}
-__device__ __forceinline__ float sig_beta(float a, float beta) { return 1.f / (1.f + expf(-beta * a)); }
-
-// Input stream s of a hidden layer, element (point pt, feature k), built from the
-// layer below: s = 0: sp(A), s = 1..3: sp'(A) * tangent (layer 1's tangent is W1[k, s-1]).
-__device__ __forceinline__ float stream_in(const TrainBufs& T, int lower, int s, int pt, int k) {
-    const float a = T.A[lower][static_cast<size_t>(pt) * kH + k];
-    if (s == 0) return sp_beta(a, T.beta);
-    const float t = (lower == 1) ? T.theta[oW1 + k * kIn + (s - 1)]
-                                 : T.AT[lower][(static_cast<size_t>(s - 1) * T.B + pt) * kH + k];
-    return sig_beta(a, T.beta) * t;
-}
 
 // acc[i][j] += sum_k Xs[k][row_i] Ms[k][col_j] over k < 128; rows/cols of thread (tr, tn)
 // are two 4-wide strips 64 apart.
@@ -205,15 +162,17 @@ __global__ void __launch_bounds__(kT, 1) fwd_hidden_kernel(TrainBufs T, int l) {
 }
 
 // ------------------------------------------------------------------ output layer, loss, adjoints of layer 4
-// One warp per point (lane holds features lane + 32 i).  Also the w5 / b5 partial gradients.
-__global__ void __launch_bounds__(kT) output_kernel(TrainBufs T) {
-    __shared__ float s_w5[kT / 32][kH];
-    __shared__ float s_b5[kT / 32];
+// One warp per point (lane holds features lane + 32 i), 16 warps per CTA.  Also the w5 / b5
+// partial gradients.
+constexpr int kOutT = 512;
+__global__ void __launch_bounds__(kOutT) output_kernel(TrainBufs T) {
+    __shared__ float s_w5[kOutT / 32][kH];
+    __shared__ float s_b5[kOutT / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nw = gridDim.x * (kT / 32);
+    const int nw = gridDim.x * (kOutT / 32);
     float gw5[4] = {0.f, 0.f, 0.f, 0.f}, gb5 = 0.f;
     const float invB = 1.f / static_cast<float>(T.B);
-    for (int pt = blockIdx.x * (kT / 32) + wid; pt < T.B; pt += nw) {
+    for (int pt = blockIdx.x * (kOutT / 32) + wid; pt < T.B; pt += nw) {
         float a[4], sg[4], at[3][4], w5[4];
         float s = 0.f, g[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -266,12 +225,12 @@ __global__ void __launch_bounds__(kT) output_kernel(TrainBufs T) {
     __syncthreads();
     if (threadIdx.x < kH) {
         float t = 0.f;
-        for (int w = 0; w < kT / 32; ++w) t += s_w5[w][threadIdx.x];
+        for (int w = 0; w < kOutT / 32; ++w) t += s_w5[w][threadIdx.x];
         T.partial[static_cast<size_t>(blockIdx.x) * kNumParams + oW5 + threadIdx.x] = t;
     }
     if (threadIdx.x == 0) {
         float t = 0.f;
-        for (int w = 0; w < kT / 32; ++w) t += s_b5[w];
+        for (int w = 0; w < kOutT / 32; ++w) t += s_b5[w];
         T.partial[static_cast<size_t>(blockIdx.x) * kNumParams + oB5] = t;
     }
 }
@@ -379,24 +338,41 @@ __global__ void __launch_bounds__(kT, 1) bwd_input_kernel(TrainBufs T, int l) {
 
 // ------------------------------------------------------------------ layer-1 gradients
 // dW1[c][k] = sum_pt dA1[pt][c] p_k + sum_pt dAT1^k[pt][c] (k < 3);  db1[c] = sum_pt dA1[pt][c].
-__global__ void __launch_bounds__(kH) layer1_grad_kernel(TrainBufs T) {
-    const int c = threadIdx.x;
+// CTA b takes a contiguous range of points; thread (c, q) sums every kL1Phases-th point of it
+// from q, and the phases are added in a fixed order.
+constexpr int kL1Phases = 4;
+__global__ void __launch_bounds__(kH * kL1Phases) layer1_grad_kernel(TrainBufs T) {
+    __shared__ float red[kL1Phases][4][kH];
+    const int c = threadIdx.x & (kH - 1), q = threadIdx.x / kH;
     const int per = (T.B + gridDim.x - 1) / gridDim.x;
     const int p0 = blockIdx.x * per, p1 = min(T.B, p0 + per);
+    const size_t plane = static_cast<size_t>(T.B) * kH;
     float g0 = 0.f, g1 = 0.f, g2 = 0.f, gb = 0.f;
-    for (int pt = p0; pt < p1; ++pt) {
+#pragma unroll 4
+    for (int pt = p0 + q; pt < p1; pt += kL1Phases) {
         const float4 p = T.pts[pt];
-        const float d = T.dA[1][static_cast<size_t>(pt) * kH + c];
+        const size_t i = static_cast<size_t>(pt) * kH + c;
+        const float d = T.dA[1][i];
         gb += d;
-        g0 += d * p.x + T.dAT[1][(static_cast<size_t>(0) * T.B + pt) * kH + c];
-        g1 += d * p.y + T.dAT[1][(static_cast<size_t>(1) * T.B + pt) * kH + c];
-        g2 += d * p.z + T.dAT[1][(static_cast<size_t>(2) * T.B + pt) * kH + c];
+        g0 += d * p.x + T.dAT[1][i];
+        g1 += d * p.y + T.dAT[1][plane + i];
+        g2 += d * p.z + T.dAT[1][2 * plane + i];
     }
-    float* part = T.partial + static_cast<size_t>(blockIdx.x) * kNumParams;
-    part[oW1 + c * kIn + 0] = g0;
-    part[oW1 + c * kIn + 1] = g1;
-    part[oW1 + c * kIn + 2] = g2;
-    part[oB1 + c] = gb;
+    red[q][0][c] = g0;
+    red[q][1][c] = g1;
+    red[q][2][c] = g2;
+    red[q][3][c] = gb;
+    __syncthreads();
+    if (q == 0) {
+        float r[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int h = 0; h < kL1Phases; ++h)
+            for (int k = 0; k < 4; ++k) r[k] += red[h][k][c];
+        float* part = T.partial + static_cast<size_t>(blockIdx.x) * kNumParams;
+        part[oW1 + c * kIn + 0] = r[0];
+        part[oW1 + c * kIn + 1] = r[1];
+        part[oW1 + c * kIn + 2] = r[2];
+        part[oB1 + c] = r[3];
+    }
 }
 
 // Sum the per-CTA partials of every parameter in a fixed order (n_part[p] CTAs wrote parameter p),
@@ -486,6 +462,8 @@ struct mppi_trainer {
     float* loss = nullptr;
     float* loss_mean = nullptr;
     float* errs = nullptr;
+    int* dev_err = nullptr;                  // device error word of the tensor-core kernels
+    int gemm = MPPI_TRAIN_GEMM_FP32;         // precision of the hidden-layer GEMMs in training
     cudaStream_t stream = nullptr;
     TrainBufs T{};
 };
@@ -536,34 +514,54 @@ void bind_batch(mppi_trainer* t, const float4* pts, int B) {
     }
 }
 
-// Forward through layer 4 for the bound batch (values and tangents).
-int forward(mppi_trainer* t) {
+// Forward through layer 4 for the bound batch (values and tangents); tc: the hidden
+// layers' GEMMs in BF16 on the tensor cores.
+int forward(mppi_trainer* t, bool tc) {
     TrainBufs& T = t->T;
     cudaStream_t s = t->stream;
     first_bias_kernel<<<1, kH, 0, s>>>(T);
     fwd_layer1_kernel<<<(T.B * kH + 255) / 256, 256, 0, s>>>(T);
     const int grid = std::min(t->n_cta, T.B / kTileRows);
-    for (int l = 2; l <= 4; ++l) fwd_hidden_kernel<<<grid, kT, kGemmSmem, s>>>(T, l);
+    for (int l = 2; l <= 4; ++l) {
+        if (tc) TRY(t, launch_fwd_hidden_tc(T, l, grid, s));
+        else fwd_hidden_kernel<<<grid, kT, kGemmSmem, s>>>(T, l);
+    }
     TRY(t, cudaGetLastError());
     return MPPI_OK;
 }
 
 // Loss, adjoints, gradients (reduced into T.grad) for the bound batch.
-int backward(mppi_trainer* t) {
+int backward(mppi_trainer* t, bool tc) {
     TrainBufs& T = t->T;
     cudaStream_t s = t->stream;
     const int grid = std::min(t->n_cta, T.B / kTileRows);
-    const int out_grid = std::min(t->n_cta, (T.B + kT / 32 - 1) / (kT / 32));
-    output_kernel<<<out_grid, kT, 0, s>>>(T);
+    const int out_grid = std::min(t->n_cta, (T.B + kOutT / 32 - 1) / (kOutT / 32));
+    output_kernel<<<out_grid, kOutT, 0, s>>>(T);
     for (int l = 4; l >= 2; --l) {
-        bwd_weight_kernel<<<grid, kT, kGemmSmem, s>>>(T, l);
-        bwd_input_kernel<<<grid, kT, kGemmSmem, s>>>(T, l);
+        if (tc) {
+            TRY(t, launch_bwd_weight_tc(T, l, grid, s));
+            TRY(t, launch_bwd_input_tc(T, l, grid, s));
+        } else {
+            bwd_weight_kernel<<<grid, kT, kGemmSmem, s>>>(T, l);
+            bwd_input_kernel<<<grid, kT, kGemmSmem, s>>>(T, l);
+        }
     }
     const int l1_grid = std::min(t->n_cta, T.B);
-    layer1_grad_kernel<<<l1_grid, kH, 0, s>>>(T);
+    layer1_grad_kernel<<<l1_grid, kH * kL1Phases, 0, s>>>(T);
     reduce_kernel<<<(kNumParams + 255) / 256, 256, 0, s>>>(T, grid, out_grid, l1_grid);
     loss_mean_kernel<<<1, kT, 0, s>>>(T.loss, T.B, t->loss_mean);
     TRY(t, cudaGetLastError());
+    return MPPI_OK;
+}
+
+// After the stream has drained: a bounded wait that gave up inside a tensor-core kernel.
+int check_device_error(mppi_trainer* t) {
+    int e = 0;
+    TRY(t, cudaMemcpy(&e, t->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e != 0) {
+        TRY(t, cudaMemset(t->dev_err, 0, sizeof(int)));
+        return tfail(t, MPPI_E_TIMEOUT, "a tensor-core GEMM kernel gave up waiting for its MMAs (code %d)", e);
+    }
     return MPPI_OK;
 }
 
@@ -647,6 +645,7 @@ int mppi_train_create(const mppi_train_config* cfg, const float* const* init_lay
     rc = rc ? rc : talloc(t, &t->loss, B);
     rc = rc ? rc : talloc(t, &t->loss_mean, 1);
     rc = rc ? rc : talloc(t, &t->errs, cfg->n_holdout);
+    rc = rc ? rc : talloc(t, &t->dev_err, 1);
     if (rc != MPPI_OK) {
         std::snprintf(g_train_err, sizeof(g_train_err), "%s", t->err);
         mppi_train_destroy(t);
@@ -658,6 +657,7 @@ int mppi_train_create(const mppi_train_config* cfg, const float* const* init_lay
               cudaMemcpy(t->z0, latent, kLatent * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemset(t->m, 0, kNumParams * sizeof(float)) == cudaSuccess &&
               cudaMemset(t->v, 0, kNumParams * sizeof(float)) == cudaSuccess &&
+              cudaMemset(t->dev_err, 0, sizeof(int)) == cudaSuccess &&
               cudaFuncSetAttribute(fwd_hidden_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    static_cast<int>(kGemmSmem)) == cudaSuccess &&
               cudaFuncSetAttribute(bwd_weight_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -677,6 +677,7 @@ int mppi_train_create(const mppi_train_config* cfg, const float* const* init_lay
     T.b1p = t->b1p;
     T.z0 = t->z0;
     T.loss = t->loss;
+    T.err = t->dev_err;
     T.beta = cfg->softplus_beta;
     T.lam_e = cfg->eikonal_weight;
     // training and held-out points from two Philox keys
@@ -703,14 +704,33 @@ int mppi_train_set_lr(mppi_trainer* t, float lr) {
     return MPPI_OK;
 }
 
+int mppi_train_set_gemm_precision(mppi_trainer* t, int precision) {
+    if (!t) return tfail(nullptr, MPPI_E_INVALID, "trainer is NULL");
+    if (precision != MPPI_TRAIN_GEMM_FP32 && precision != MPPI_TRAIN_GEMM_BF16)
+        return tfail(t, MPPI_E_INVALID, "unknown GEMM precision %d", precision);
+    if (precision == MPPI_TRAIN_GEMM_BF16) {
+        int dev = 0, major = 0, minor = 0;
+        TRY(t, cudaGetDevice(&dev));
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+        if (major != 10 || minor != 3)
+            return tfail(t, MPPI_E_UNSUPPORTED, "BF16 tensor-core GEMMs need an sm_103 device (found sm_%d%d)", major,
+                         minor);
+        TRY(t, configure_tc_train());
+    }
+    t->gemm = precision;
+    return MPPI_OK;
+}
+
 int mppi_train_step(mppi_trainer* t, int n_steps, float* last_loss) {
     if (!t || n_steps < 0) return tfail(t, MPPI_E_INVALID, "bad arguments");
     const mppi_train_config& c = t->cfg;
     const int per_epoch = c.n_points / c.batch;
     for (int i = 0; i < n_steps; ++i) {
         bind_batch(t, t->data + static_cast<size_t>(t->step % per_epoch) * c.batch, c.batch);
-        int rc = forward(t);
-        if (rc == MPPI_OK) rc = backward(t);
+        const bool tc = t->gemm == MPPI_TRAIN_GEMM_BF16;
+        int rc = forward(t, tc);
+        if (rc == MPPI_OK) rc = backward(t, tc);
         if (rc != MPPI_OK) return rc;
         ++t->step;
         const float c1 = 1.f - std::pow(c.beta1, static_cast<float>(t->step));
@@ -723,7 +743,7 @@ int mppi_train_step(mppi_trainer* t, int n_steps, float* last_loss) {
         TRY(t, cudaMemcpyAsync(last_loss, t->loss_mean, sizeof(float), cudaMemcpyDeviceToHost, t->stream));
     }
     TRY(t, cudaStreamSynchronize(t->stream));
-    return MPPI_OK;
+    return check_device_error(t);
 }
 
 int mppi_train_loss_grads(mppi_trainer* t, const float* points, int n, float* loss, float* grads) {
@@ -732,13 +752,14 @@ int mppi_train_loss_grads(mppi_trainer* t, const float* points, int n, float* lo
     TRY(t, cudaMemcpyAsync(t->batch_pts, points, static_cast<size_t>(n) * sizeof(float4), cudaMemcpyHostToDevice,
                            t->stream));
     bind_batch(t, t->batch_pts, n);
-    int rc = forward(t);
-    if (rc == MPPI_OK) rc = backward(t);
+    const bool tc = t->gemm == MPPI_TRAIN_GEMM_BF16;
+    int rc = forward(t, tc);
+    if (rc == MPPI_OK) rc = backward(t, tc);
     if (rc != MPPI_OK) return rc;
     if (loss) TRY(t, cudaMemcpyAsync(loss, t->loss_mean, sizeof(float), cudaMemcpyDeviceToHost, t->stream));
     if (grads) TRY(t, cudaMemcpyAsync(grads, t->grad, kNumParams * sizeof(float), cudaMemcpyDeviceToHost, t->stream));
     TRY(t, cudaStreamSynchronize(t->stream));
-    return MPPI_OK;
+    return check_device_error(t);
 }
 
 int mppi_train_get_weights(mppi_trainer* t, float* const* layers_out) {
@@ -756,11 +777,12 @@ int mppi_train_get_weights(mppi_trainer* t, float* const* layers_out) {
 int mppi_train_evaluate(mppi_trainer* t, float* mae, float* p99, float* max_err, float* near_p99) {
     if (!t) return tfail(nullptr, MPPI_E_INVALID, "NULL trainer");
     const int n = t->cfg.n_holdout;
-    // the held-out set goes through the forward pass in batch-sized chunks
+    // the held-out set goes through the FP32 forward pass in batch-sized chunks (whatever the
+    // training GEMMs' precision, the error is the learned weights' own)
     for (int p0 = 0; p0 < n; p0 += t->cfg.batch) {
         const int len = std::min(t->cfg.batch, n - p0);
         bind_batch(t, t->holdout + p0, len);
-        int rc = forward(t);
+        int rc = forward(t, false);
         if (rc != MPPI_OK) return rc;
         eval_output_kernel<<<(len + 7) / 8, 256, 0, t->stream>>>(t->T, t->errs + p0);
         TRY(t, cudaGetLastError());

@@ -4,6 +4,15 @@ Eikonal loss against the FP64 oracle, Adam, and what training buys.
 Tolerances: targets 1e-6 m (the exact frame SDF in FP32); loss 1e-5 relative;
 gradients within 2e-3 of each tensor's largest entry (FP32 sums over the batch
 against FP64); Adam 1e-6 relative.
+
+BF16 tensor-core GEMMs (operands rounded to BF16, unit roundoff u = 2^-9, FP32
+accumulation): a product of two rounded operands is off by at most 2u of its
+magnitude, and between any parameter and the loss there are at most six such
+GEMMs in a chain (forward layers 2-4, input gradients 4-2, the weight gradient),
+each adding its 2u; with a factor of about 1.3 for cancellation in the sums that
+is 16u = 3.1e-2 of each gradient tensor's largest entry (1.0e-2 measured).  The
+loss, a mean over the batch of |s - s*| + the Eikonal term, moves by the
+forward pass's error: 4u = 7.8e-3 relative (2.9e-4 measured).
 """
 import math
 
@@ -78,6 +87,65 @@ def test_gradients_match_the_oracle(lib):
         assert np.max(np.abs(g - r)) <= 2e-3 * scale + 1e-9, (name, np.max(np.abs(g - r)), scale)
 
 
+BF16_U = 2.0 ** -9
+
+
+def _grads_on_a_fixed_batch(prec, n=512, seed=3):
+    tr, layers, z0, cfg = _trainer(batch=n, n_points=2 * n)
+    try:
+        B.mppi_train_set_gemm_precision(tr, prec)
+        rng = np.random.default_rng(seed)
+        P = np.concatenate([rng.normal(0, 0.6, (n // 2, 3)), rng.uniform(-3, 3, (n // 2, 3))]).astype(np.float32)
+        tgt = gate_sdf.frame_sdf(P.astype(np.float64)).astype(np.float32)
+        pts = np.ascontiguousarray(np.concatenate([P, tgt[:, None]], axis=1), dtype=np.float32)
+        grads = np.zeros(B.mppi_train_num_params(), np.float32)
+        loss = B.mppi_train_loss_grads(tr, pts, grads)
+    finally:
+        B.mppi_train_destroy(tr)
+    return loss, grads, layers, z0, P, tgt
+
+
+@pytest.mark.parametrize("n", [512, 4096])
+def test_bf16_tensor_core_gradients_match_the_oracle(lib, n):
+    """The hidden layers' forward and backward GEMMs on tcgen05 in BF16 (FP32 accumulation, FP32
+    master weights): loss and every gradient tensor against the FP64 oracle at the BF16 bar of the
+    module docstring.  n = 4096 spans 32 tiles, so every CTA accumulates several tiles."""
+    loss, grads, layers, z0, P, tgt = _grads_on_a_fixed_batch(B.MPPI_TRAIN_GEMM_BF16, n=n, seed=3 + n)
+    pairs = [(layers[2 * i], layers[2 * i + 1]) for i in range(5)]
+    ref_loss, ref = OD.loss_and_grads(pairs, P.astype(np.float64), z0.astype(np.float64),
+                                      tgt.astype(np.float64), lam_e=0.1)
+    assert abs(loss - ref_loss) <= 4 * BF16_U * abs(ref_loss), (loss, ref_loss)
+    got = _split(grads.astype(np.float64), layers)
+    worst = {}
+    for i, (name, g) in enumerate(zip(NAMES, got)):
+        r = ref[i // 2][i % 2].reshape(g.shape)
+        scale = np.max(np.abs(r))
+        worst[name] = float(np.max(np.abs(g - r)) / max(scale, 1e-30))
+        assert np.max(np.abs(g - r)) <= 16 * BF16_U * scale + 1e-9, (name, np.max(np.abs(g - r)), scale)
+    print("largest error / largest entry:", {k: f"{v:.2e}" for k, v in worst.items()})
+
+
+def test_bf16_training_is_deterministic_and_precision_is_checked(lib):
+    """Two BF16 trainers from the same start take bit-identical Adam steps (fixed-order reductions,
+    one accumulator order per tile); an unknown precision is rejected."""
+    outs = []
+    for _ in range(2):
+        tr, layers, z0, cfg = _trainer(batch=1024, n_points=4096)
+        try:
+            with pytest.raises(B.MppiError):
+                B.mppi_train_set_gemm_precision(tr, 7)
+            B.mppi_train_set_gemm_precision(tr, B.MPPI_TRAIN_GEMM_BF16)
+            B.mppi_train_step(tr, 5)
+            w = [np.zeros_like(a) for a in layers]
+            B.mppi_train_get_weights(tr, w)
+            outs.append(w)
+        finally:
+            B.mppi_train_destroy(tr)
+    for a, b in zip(*outs):
+        np.testing.assert_array_equal(a, b)
+    assert any(np.any(a != b) for a, b in zip(outs[0], layers))
+
+
 def test_adam_step_matches_the_oracle(lib):
     tr, layers, z0, cfg = _trainer(batch=512, n_points=512)
     pts = np.zeros(4 * 512, np.float32)
@@ -120,9 +188,11 @@ def test_set_lr_takes_effect_on_the_next_step(lib):
     np.testing.assert_allclose(got, want, rtol=1e-6, atol=1e-9)
 
 
-def test_training_reduces_the_sdf_error(lib):
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_training_reduces_the_sdf_error(lib, prec):
     """A few hundred Adam steps already cut the held-out error of the random network by a large factor."""
     tr, layers, z0, cfg = _trainer(batch=4096, n_points=1 << 16, n_holdout=8192, seed=11)
+    B.mppi_train_set_gemm_precision(tr, B.MPPI_TRAIN_GEMM_BF16 if prec == "bf16" else B.MPPI_TRAIN_GEMM_FP32)
     before = B.mppi_train_evaluate(tr)
     l0 = B.mppi_train_step(tr, 1)
     l1 = B.mppi_train_step(tr, 299)
@@ -174,15 +244,18 @@ def test_learned_sdf_steers_mppi_like_the_exact_one(lib):
     assert np.mean([l["ctrl"] for l in L]) < np.mean([u["ctrl"] for u in U]), (L, U)
 
 
-def test_configured_distillation_passes_the_5mm_bar(lib):
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_configured_distillation_passes_the_5mm_bar(lib, prec):
     """The configured distillation (2^21 points, batch 65,536, 20,000 Adam steps, L1 + 0.1
     Eikonal) with a linear warm-up to 2e-3 over 1,000 steps and a half-cosine decay to 0 (mean
     rate 1e-3): the held-out error against the exact SDF stays within 5 mm in the mean and at
-    p99 within 0.3 m of the frame, so the learned network replaces the exact SDF.  (About 150 s;
-    the training is deterministic: 1.17 mm and 4.46 mm measured.)"""
+    p99 within 0.3 m of the frame, so the learned network replaces the exact SDF.  Both GEMM
+    precisions (BF16 on the tensor cores about 45 s, FP32 about 150 s; the training is
+    deterministic: FP32 1.17 mm and 4.46 mm measured, BF16 1.27 mm and 3.77 mm)."""
     cfg = B.mppi_train_config_default()
     tr = B.mppi_train_create(cfg, flat_layers(W.xavier_mlp(1)), W.latents(1, seed=2)[0])
     try:
+        B.mppi_train_set_gemm_precision(tr, B.MPPI_TRAIN_GEMM_BF16 if prec == "bf16" else B.MPPI_TRAIN_GEMM_FP32)
         steps, warmup, peak, done = 20000, 1000, 2e-3, 0
         while done < steps:
             n = min(250, steps - done)
