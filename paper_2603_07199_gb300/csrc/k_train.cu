@@ -165,6 +165,8 @@ __global__ void __launch_bounds__(kT, 1) fwd_hidden_kernel(TrainBufs T, int l) {
 // One warp per point (lane holds features lane + 32 i), 16 warps per CTA.  Also the w5 / b5
 // partial gradients.
 constexpr int kOutT = 512;
+// the output and layer-1 kernels launch up to this many CTAs per SM (their partials are small)
+constexpr int kSmallGridPerSm = 4;
 __global__ void __launch_bounds__(kOutT) output_kernel(TrainBufs T) {
     __shared__ float s_w5[kOutT / 32][kH];
     __shared__ float s_b5[kOutT / 32];
@@ -226,12 +228,12 @@ __global__ void __launch_bounds__(kOutT) output_kernel(TrainBufs T) {
     if (threadIdx.x < kH) {
         float t = 0.f;
         for (int w = 0; w < kOutT / 32; ++w) t += s_w5[w][threadIdx.x];
-        T.partial[static_cast<size_t>(blockIdx.x) * kNumParams + oW5 + threadIdx.x] = t;
+        T.opart[static_cast<size_t>(blockIdx.x) * (kH + 1) + threadIdx.x] = t;
     }
     if (threadIdx.x == 0) {
         float t = 0.f;
         for (int w = 0; w < kOutT / 32; ++w) t += s_b5[w];
-        T.partial[static_cast<size_t>(blockIdx.x) * kNumParams + oB5] = t;
+        T.opart[static_cast<size_t>(blockIdx.x) * (kH + 1) + kH] = t;
     }
 }
 
@@ -367,32 +369,48 @@ __global__ void __launch_bounds__(kH * kL1Phases) layer1_grad_kernel(TrainBufs T
         float r[4] = {0.f, 0.f, 0.f, 0.f};
         for (int h = 0; h < kL1Phases; ++h)
             for (int k = 0; k < 4; ++k) r[k] += red[h][k][c];
-        float* part = T.partial + static_cast<size_t>(blockIdx.x) * kNumParams;
-        part[oW1 + c * kIn + 0] = r[0];
-        part[oW1 + c * kIn + 1] = r[1];
-        part[oW1 + c * kIn + 2] = r[2];
-        part[oB1 + c] = r[3];
+        float* part = T.l1part + static_cast<size_t>(blockIdx.x) * 4 * kH;
+        for (int k = 0; k < 4; ++k) part[k * kH + c] = r[k];
     }
 }
 
-// Sum the per-CTA partials of every parameter in a fixed order (n_part[p] CTAs wrote parameter p),
-// then the latent part of the first layer: dW1[c][3 + j] = db1[c] z0[j].
-__global__ void reduce_kernel(TrainBufs T, int n_lin, int n_out, int n_l1) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= kNumParams) return;
-    int n;
-    if (p >= oW2 && p < oW5) n = n_lin;
-    else if (p >= oW5) n = n_out;
-    else n = n_l1;
+// Sum the per-CTA partials of layers 2-4 (n_lin rows of T.partial) in a fixed order.
+__global__ void reduce_kernel(TrainBufs T, int n_lin) {
+    const int p = oW2 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= oW5) return;
     float acc = 0.f;
-    if (p >= oW1 && p < oB1 && (p - oW1) % kIn >= 3) {
-        const int c = (p - oW1) / kIn, j = (p - oW1) % kIn - 3;
-        for (int b = 0; b < n_l1; ++b) acc += T.partial[static_cast<size_t>(b) * kNumParams + oB1 + c];
-        acc *= T.z0[j];
-    } else {
-        for (int b = 0; b < n; ++b) acc += T.partial[static_cast<size_t>(b) * kNumParams + p];
-    }
+    for (int b = 0; b < n_lin; ++b) acc += T.partial[static_cast<size_t>(b) * kNumParams + p];
     T.grad[p] = acc;
+}
+
+// The small partial areas, one warp per sum (lanes take rows lane, lane + 32, ..., then a fixed
+// shuffle tree): sums 0..4 kH - 1 are W1[:, 0..2] and b1 over n_l1 rows of T.l1part (the warp
+// of db1[c] also writes the latent columns dW1[c][3 + j] = db1[c] z0[j]); sums 4 kH .. 5 kH are
+// w5 and b5 over n_out rows of T.opart.
+constexpr int kSmallSums = 5 * kH + 1;
+__global__ void reduce_small_kernel(TrainBufs T, int n_out, int n_l1) {
+    const int w = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (w >= kSmallSums) return;
+    float acc = 0.f;
+    if (w < 4 * kH) {
+        const int k = w / kH, c = w - k * kH;
+        for (int b = lane; b < n_l1; b += 32) acc += T.l1part[(static_cast<size_t>(b) * 4 + k) * kH + c];
+    } else {
+        const int q = w - 4 * kH;
+        for (int b = lane; b < n_out; b += 32) acc += T.opart[static_cast<size_t>(b) * (kH + 1) + q];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (w < 3 * kH) {
+        const int k = w / kH, c = w - k * kH;
+        if (lane == 0) T.grad[oW1 + c * kIn + k] = acc;
+    } else if (w < 4 * kH) {
+        const int c = w - 3 * kH;
+        if (lane == 0) T.grad[oB1 + c] = acc;
+        for (int j = lane; j < kLatent; j += 32) T.grad[oW1 + c * kIn + 3 + j] = acc * T.z0[j];
+    } else {
+        if (lane == 0) T.grad[oW5 + (w - 4 * kH)] = acc;
+    }
 }
 
 __global__ void adam_kernel(float* theta, const float* grad, float* m, float* v, int n, float lr, float b1, float b2,
@@ -453,6 +471,8 @@ struct mppi_trainer {
     float* v = nullptr;
     float* grad = nullptr;
     float* partial = nullptr;
+    float* opart = nullptr;
+    float* l1part = nullptr;
     float* b1p = nullptr;
     float* z0 = nullptr;
     float4* data = nullptr;        // training set
@@ -535,7 +555,7 @@ int backward(mppi_trainer* t, bool tc) {
     TrainBufs& T = t->T;
     cudaStream_t s = t->stream;
     const int grid = std::min(t->n_cta, T.B / kTileRows);
-    const int out_grid = std::min(t->n_cta, (T.B + kOutT / 32 - 1) / (kOutT / 32));
+    const int out_grid = std::min(kSmallGridPerSm * t->n_cta, (T.B + kOutT / 32 - 1) / (kOutT / 32));
     output_kernel<<<out_grid, kOutT, 0, s>>>(T);
     for (int l = 4; l >= 2; --l) {
         if (tc) {
@@ -546,9 +566,10 @@ int backward(mppi_trainer* t, bool tc) {
             bwd_input_kernel<<<grid, kT, kGemmSmem, s>>>(T, l);
         }
     }
-    const int l1_grid = std::min(t->n_cta, T.B);
+    const int l1_grid = std::min(kSmallGridPerSm * t->n_cta, T.B / kL1Phases);
     layer1_grad_kernel<<<l1_grid, kH * kL1Phases, 0, s>>>(T);
-    reduce_kernel<<<(kNumParams + 255) / 256, 256, 0, s>>>(T, grid, out_grid, l1_grid);
+    reduce_kernel<<<(oW5 - oW2 + 255) / 256, 256, 0, s>>>(T, grid);
+    reduce_small_kernel<<<(kSmallSums + 7) / 8, 256, 0, s>>>(T, out_grid, l1_grid);
     loss_mean_kernel<<<1, kT, 0, s>>>(T.loss, T.B, t->loss_mean);
     TRY(t, cudaGetLastError());
     return MPPI_OK;
@@ -636,6 +657,8 @@ int mppi_train_create(const mppi_train_config* cfg, const float* const* init_lay
     rc = rc ? rc : talloc(t, &t->v, kNumParams);
     rc = rc ? rc : talloc(t, &t->grad, kNumParams);
     rc = rc ? rc : talloc(t, &t->partial, static_cast<size_t>(n_part) * kNumParams);
+    rc = rc ? rc : talloc(t, &t->opart, static_cast<size_t>(kSmallGridPerSm) * n_part * (kH + 1));
+    rc = rc ? rc : talloc(t, &t->l1part, static_cast<size_t>(kSmallGridPerSm) * n_part * 4 * kH);
     rc = rc ? rc : talloc(t, &t->b1p, kH);
     rc = rc ? rc : talloc(t, &t->z0, kLatent);
     rc = rc ? rc : talloc(t, &t->data, cfg->n_points);
@@ -674,6 +697,8 @@ int mppi_train_create(const mppi_train_config* cfg, const float* const* init_lay
     T.theta = t->theta;
     T.grad = t->grad;
     T.partial = t->partial;
+    T.opart = t->opart;
+    T.l1part = t->l1part;
     T.b1p = t->b1p;
     T.z0 = t->z0;
     T.loss = t->loss;

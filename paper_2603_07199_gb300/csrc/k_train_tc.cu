@@ -93,6 +93,37 @@ __device__ __forceinline__ void sync_for_mma() {
     tc::fence_after_sync();
 }
 
+// Epilogue transpose through shared memory (the operand buffers, free once the tile's MMAs
+// completed): tcgen05.ld gives thread i TMEM lane (row) i, while whole-row global accesses want
+// the eight lanes of a quarter warp on one row.  Per warp a 32 x 32 FP32 block with a 36-float
+// row pitch: the 16-byte row writes of eight consecutive rows, and the 16-byte reads of one
+// row by eight lanes, each fall on eight distinct bank quadruples.
+constexpr int kScrLd = 36;
+constexpr int kScrFloats = 32 * kScrLd;
+
+__device__ __forceinline__ void ld_shared_v4(uint32_t addr, float (&v)[4]) {
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+                 : "r"(addr)
+                 : "memory");
+}
+
+// TMEM columns [col, col + 32) of this warp's 32 lanes -> the warp's scratch block (row = lane).
+__device__ __forceinline__ void tmem_to_scratch(uint32_t taddr, uint32_t scr, int lane) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t v[16];
+        tc::tmem_ld_32x32b_x16(taddr + static_cast<uint32_t>(16 * h), v);
+        tc::tmem_wait_ld();
+        tc::reg_fence16(v);
+#pragma unroll
+        for (int j = 0; j < 16; j += 4)
+            tc::st_shared_v4(scr + static_cast<uint32_t>((lane * kScrLd + 16 * h + j) * 4), v[j], v[j + 1], v[j + 2],
+                             v[j + 3]);
+    }
+    __syncwarp();
+}
+
 // Work item it in [0, 2048) of a row-major [128][128] source -> (row, 8-column chunk).  The
 // eight lanes of a quarter warp take eight consecutive rows of one chunk, so their 16-byte
 // shared-memory stores fill one contiguous 128-byte core matrix (no bank conflicts), and a
@@ -155,7 +186,7 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_hidden_tc_kernel(TrainBufs T,
     sync_for_mma();
     const uint32_t tmem = S.tmem_base, bar = tc::smem_u32(&S.bar);
     const uint32_t xs = tc::smem_u32(S.x[0]);
-    const int wq = warp & 3, col0 = (warp >> 2) * kEpiCols, m = wq * 32 + lane;
+    const int wq = warp & 3, col0 = (warp >> 2) * kEpiCols;
     const uint32_t lane_addr = tmem + (static_cast<uint32_t>(wq * 32) << 16);
     const size_t plane = static_cast<size_t>(T.B) * kH;
     const int n_tiles = T.B / kTileRows;
@@ -203,30 +234,34 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_hidden_tc_kernel(TrainBufs T,
         pending = false;
         phase ^= 1u;
         tc::fence_after_sync();
-        // epilogue: this warp's rows and 32 columns of the four accumulators
-        const size_t row = static_cast<size_t>(p0 + m) * kH;
+        // epilogue: this warp's 32 rows x 32 columns of each accumulator, transposed through its
+        // scratch block; lane reads row 4 i + lane / 8, columns 4 (lane mod 8) .. + 3
+        {
+            const uint32_t scr = xs + static_cast<uint32_t>(warp * kScrFloats * 4);
+            const int rq = lane >> 3, cc = (lane & 7) * 4;
 #pragma unroll 1
-        for (int s = 0; s < 4; ++s) {
-            float* dst = (s == 0 ? T.A[l] : T.AT[l] + static_cast<size_t>(s - 1) * plane) + row;
-            {
-                uint32_t v[32];
-                tc::tmem_ld_32x32b_x32(lane_addr + static_cast<uint32_t>(s * kH + col0), v);
-                tc::tmem_wait_ld();
-                tc::reg_fence32(v);
+            for (int s = 0; s < 4; ++s) {
+                tmem_to_scratch(lane_addr + static_cast<uint32_t>(s * kH + col0), scr, lane);
+                float* dst = (s == 0 ? T.A[l] : T.AT[l] + static_cast<size_t>(s - 1) * plane) +
+                             static_cast<size_t>(p0 + wq * 32) * kH + col0 + cc;
+                float bq[4] = {0.f, 0.f, 0.f, 0.f};
+                if (s == 0) {
 #pragma unroll
-                for (int j = 0; j < 32; j += 4) {
-                    float4 o = make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
-                                           __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
-                    if (s == 0) {
-                        o.x += S.bias[col0 + j];
-                        o.y += S.bias[col0 + j + 1];
-                        o.z += S.bias[col0 + j + 2];
-                        o.w += S.bias[col0 + j + 3];
-                    }
-                    *reinterpret_cast<float4*>(dst + col0 + j) = o;
+                    for (int q = 0; q < 4; ++q) bq[q] = S.bias[col0 + cc + q];
                 }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int rr = 4 * i + rq;
+                    float o[4];
+                    ld_shared_v4(scr + static_cast<uint32_t>((rr * kScrLd + cc) * 4), o);
+                    *reinterpret_cast<float4*>(dst + static_cast<size_t>(rr) * kH) =
+                        make_float4(o[0] + bq[0], o[1] + bq[1], o[2] + bq[2], o[3] + bq[3]);
+                }
+                __syncwarp();
             }
         }
+        // the next tile's staging overwrites the scratch blocks
+        __syncthreads();
         // the next tile's MMAs overwrite TMEM only after the barrier that ends its staging
         tc::fence_before_sync();
     }
@@ -257,7 +292,7 @@ __global__ void __launch_bounds__(kThreads, 1) bwd_input_tc_kernel(TrainBufs T, 
     sync_for_mma();
     const uint32_t tmem = S.tmem_base, bar = tc::smem_u32(&S.bar);
     const uint32_t xs = tc::smem_u32(S.x[0]);
-    const int wq = warp & 3, m = wq * 32 + lane;
+    const int wq = warp & 3;
     const uint32_t lane_addr = tmem + (static_cast<uint32_t>(wq * 32) << 16);
     const size_t plane = static_cast<size_t>(T.B) * kH;
     const float beta = T.beta;
@@ -286,62 +321,72 @@ __global__ void __launch_bounds__(kThreads, 1) bwd_input_tc_kernel(TrainBufs T, 
         pending = false;
         phase ^= 1u;
         tc::fence_after_sync();
-        const size_t row = static_cast<size_t>(p0 + m) * kH;
-        // epilogue: this warp's rows, its 32 columns in two 16-column slices (registers stay below
-        // the 128 a thread of a 512-thread CTA may hold)
-#pragma unroll 1
-        for (int c = 0; c < 2; ++c) {
-            const int col0 = (warp >> 2) * kEpiCols + c * 16;
-            float sg[16], tot[16];
+        // epilogue: this warp's 32 rows x 32 columns, each stream's dX transposed through the
+        // warp's scratch block, so that A, AT of layer l-1 are read and dA, dAT written by whole
+        // rows; lane holds rows 4 i + lane / 8 (i < 8), columns 4 (lane mod 8) .. + 3
+        {
+            const uint32_t scr = xs + static_cast<uint32_t>(warp * kScrFloats * 4);
+            const int rq = lane >> 3, cc = (lane & 7) * 4;
+            const int col0 = (warp >> 2) * kEpiCols;
+            const size_t base = static_cast<size_t>(p0 + wq * 32) * kH + col0 + cc;
+            float sg[8][4], tot[8][4];
 #pragma unroll
-            for (int j = 0; j < 16; j += 4) {
-                const float4 a = __ldg(reinterpret_cast<const float4*>(T.A[lower] + row + col0 + j));
-                sg[j] = sig_beta(a.x, beta);
-                sg[j + 1] = sig_beta(a.y, beta);
-                sg[j + 2] = sig_beta(a.z, beta);
-                sg[j + 3] = sig_beta(a.w, beta);
+            for (int i = 0; i < 8; ++i) {
+                const float4 a = __ldg(reinterpret_cast<const float4*>(
+                    T.A[lower] + base + static_cast<size_t>(4 * i + rq) * kH));
+                sg[i][0] = sig_beta(a.x, beta);
+                sg[i][1] = sig_beta(a.y, beta);
+                sg[i][2] = sig_beta(a.z, beta);
+                sg[i][3] = sig_beta(a.w, beta);
             }
-            uint32_t v[16];
-            tc::tmem_ld_32x32b_x16(lane_addr + static_cast<uint32_t>(col0), v);
-            tc::tmem_wait_ld();
-            tc::reg_fence16(v);
+            tmem_to_scratch(lane_addr + static_cast<uint32_t>(col0), scr, lane);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) tot[j] = __uint_as_float(v[j]) * sg[j];
+            for (int i = 0; i < 8; ++i) {
+                float d[4];
+                ld_shared_v4(scr + static_cast<uint32_t>(((4 * i + rq) * kScrLd + cc) * 4), d);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) tot[i][q] = d[q] * sg[i][q];
+            }
+            __syncwarp();
 #pragma unroll 1
             for (int s = 1; s < 4; ++s) {
-                float t[16];
+                tmem_to_scratch(lane_addr + static_cast<uint32_t>(s * kH + col0), scr, lane);
+                float w1[4];
                 if (lower == 1) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) t[j] = __ldg(T.theta + oW1 + (col0 + j) * kIn + (s - 1));
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 16; j += 4) {
-                        const float4 t4 = __ldg(reinterpret_cast<const float4*>(
-                            T.AT[lower] + static_cast<size_t>(s - 1) * plane + row + col0 + j));
-                        t[j] = t4.x; t[j + 1] = t4.y; t[j + 2] = t4.z; t[j + 3] = t4.w;
-                    }
+                    for (int q = 0; q < 4; ++q) w1[q] = __ldg(T.theta + oW1 + (col0 + cc + q) * kIn + (s - 1));
                 }
-                tc::tmem_ld_32x32b_x16(lane_addr + static_cast<uint32_t>(s * kH + col0), v);
-                tc::tmem_wait_ld();
-                tc::reg_fence16(v);
-                float* dat = T.dAT[lower] + static_cast<size_t>(s - 1) * plane + row + col0;
+                const size_t so = static_cast<size_t>(s - 1) * plane + base;
 #pragma unroll
-                for (int j = 0; j < 16; j += 4) {
-                    float o[4];
+                for (int i = 0; i < 8; ++i) {
+                    const size_t ro = so + static_cast<size_t>(4 * i + rq) * kH;
+                    float t[4];
+                    if (lower == 1) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) t[q] = w1[q];
+                    } else {
+                        const float4 t4 = __ldg(reinterpret_cast<const float4*>(T.AT[lower] + ro));
+                        t[0] = t4.x; t[1] = t4.y; t[2] = t4.z; t[3] = t4.w;
+                    }
+                    float d[4], o[4];
+                    ld_shared_v4(scr + static_cast<uint32_t>(((4 * i + rq) * kScrLd + cc) * 4), d);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const float d = __uint_as_float(v[j + q]), g = sg[j + q];
-                        tot[j + q] = fmaf(d * t[j + q], beta * g * (1.f - g), tot[j + q]);
-                        o[q] = d * g;
+                        const float g = sg[i][q];
+                        tot[i][q] = fmaf(d[q] * t[q], beta * g * (1.f - g), tot[i][q]);
+                        o[q] = d[q] * g;
                     }
-                    *reinterpret_cast<float4*>(dat + j) = make_float4(o[0], o[1], o[2], o[3]);
+                    *reinterpret_cast<float4*>(T.dAT[lower] + ro) = make_float4(o[0], o[1], o[2], o[3]);
                 }
+                __syncwarp();
             }
-            float* da = T.dA[lower] + row + col0;
 #pragma unroll
-            for (int j = 0; j < 16; j += 4)
-                *reinterpret_cast<float4*>(da + j) = make_float4(tot[j], tot[j + 1], tot[j + 2], tot[j + 3]);
+            for (int i = 0; i < 8; ++i)
+                *reinterpret_cast<float4*>(T.dA[lower] + base + static_cast<size_t>(4 * i + rq) * kH) =
+                    make_float4(tot[i][0], tot[i][1], tot[i][2], tot[i][3]);
         }
+        // the next tile's staging overwrites the scratch blocks
+        __syncthreads();
         tc::fence_before_sync();
     }
     if (pending && tid == 0) {

@@ -33,7 +33,9 @@ __host__ __device__ constexpr int offB(int l) { return l == 2 ? oB2 : l == 3 ? o
 struct TrainBufs {
     float* theta;        // parameters
     float* grad;         // reduced gradient
-    float* partial;      // [n_cta][kNumParams] per-CTA gradient partials
+    float* partial;      // [n_cta][kNumParams] per-CTA gradient partials of layers 2-4
+    float* opart;        // [n_out_cta][kH + 1] per-CTA partials of w5, b5
+    float* l1part;       // [n_l1_cta][4][kH] per-CTA partials of W1[:, 0..2], b1
     float* b1p;          // [128] b1 + W1[:, 3:] z0
     float* z0;           // [64]
     const float4* pts;   // batch points (x, y, z, target)
