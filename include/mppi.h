@@ -482,6 +482,29 @@ const char* mppi_encoder_last_error(const mppi_encoder* enc);
 int mppi_encode_depth(mppi_encoder* enc, int n_images, const float* d_depth, float max_range, float* d_latents);
 
 /*
+ * Convolution kernels of the encoder's four layers (the same arithmetic as above, Sec. III-B):
+ *   MPPI_ENC_CONV_TC    (the default) tcgen05 tensor cores: each input and weight split into
+ *                       a BF16 high part and a BF16 remainder, the three products hi.hi +
+ *                       hi.lo + lo.hi accumulated in FP32 (each product within ~2^-16 of
+ *                       its FP32 value); one CTA per 128 output pixels, no split reduction.
+ *                       A bounded wait that gives up sets the encoder's error word
+ *                       (mppi_encoder_check reports it).
+ *   MPPI_ENC_CONV_FP32  FP32 implicit GEMMs on the CUDA cores.
+ * Applies to later mppi_encode_depth calls and to the trainer's forward passes.
+ * Errors: MPPI_E_INVALID (NULL encoder, unknown path).
+ */
+#define MPPI_ENC_CONV_FP32 0
+#define MPPI_ENC_CONV_TC   1
+int mppi_encoder_set_conv_path(mppi_encoder* enc, int path);
+/*
+ * Wait for the encoder's stream and read its device error word: MPPI_OK, or
+ * MPPI_E_TIMEOUT when a tensor-core convolution gave up a bounded wait since the last
+ * check (the word is cleared; the latents of that call are not valid).  MPPI_E_CUDA when
+ * the stream itself failed.
+ */
+int mppi_encoder_check(mppi_encoder* enc);
+
+/*
  * Copy the encoder's current weights to host arrays (same 10 arrays and layouts as
  * mppi_encoder_create; a NULL entry is skipped).  Synchronous.
  */

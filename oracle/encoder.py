@@ -44,6 +44,34 @@ def conv3x3_s2(x, W, b):
     return out
 
 
+def bf16_round(a):
+    """Values rounded to the nearest bfloat16 (8 significant bits, ties to even), from their
+    float32 rounding: the 16 high bits of the float32 pattern after adding half of the dropped
+    low 16 bits' unit (0x7FFF, plus one when the kept part is odd).  Returned as float64."""
+    u = np.ascontiguousarray(np.asarray(a, dtype=np.float32)).view(np.uint32).astype(np.uint64)
+    kept = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return (kept << 16).astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def bf16_split(a):
+    """a (rounded to float32) = hi + lo + e with hi = bf16(a), lo = bf16(a - hi), |e| <= 2^-16 |a|."""
+    a32 = np.asarray(a, dtype=np.float32).astype(np.float64)
+    hi = bf16_round(a32)
+    return hi, bf16_round(a32 - hi)
+
+
+def conv3x3_s2_split(x, W, b):
+    """The convolution of ``conv3x3_s2`` with every product x w replaced by x_hi w_hi + x_hi w_lo
+    + x_lo w_hi of the operands' BF16 splits (``bf16_split``), summed exactly: the precision
+    model of a tensor-core convolution on BF16 operand pairs.  Each product is within
+    ~3 x 2^-16 of x w.  Used to take the ReLU decisions of a gradient check in the precision
+    that kernel computes in."""
+    xh, xl = bf16_split(x)
+    wh, wl = bf16_split(W)
+    zero = np.zeros_like(np.asarray(b, dtype=np.float64))
+    return conv3x3_s2(xh, wh, b) + conv3x3_s2(xh, wl, zero) + conv3x3_s2(xl, wh, zero)
+
+
 def encode(depth, max_range, layers):
     """Latent codes [N, 64] of depth images [N, H, W]; layers = [(W1, b1) .. (W4, b4), (W5, b5)]."""
     depth = np.asarray(depth, dtype=np.float64)

@@ -23,7 +23,7 @@ to its nine taps).
 
 import numpy as np
 
-from .encoder import conv3x3_s2
+from .encoder import conv3x3_s2, conv3x3_s2_split
 
 POOL = 8
 
@@ -40,11 +40,18 @@ def pooled_target(clean, max_range):
     return out
 
 
-def forward(noisy, max_range, enc_layers):
-    """Encoder forward keeping every activation: returns (inputs x0..x4, z [N, 64])."""
+def forward(noisy, max_range, enc_layers, split=False):
+    """Encoder forward keeping every activation: returns (inputs x0..x4, z [N, 64]).  With
+    split=True the convolutions use the BF16 operand-split products of ``conv3x3_s2_split`` (each
+    layer's input and output rounded to float32, as a kernel stores them), so that the ReLU
+    decisions are taken in the precision of a tensor-core forward pass."""
     xs = [np.asarray(noisy, dtype=np.float64)[:, None] / max_range]
     for W, b in enc_layers[:4]:
-        xs.append(np.stack([np.maximum(conv3x3_s2(x, W, b), 0.0) for x in xs[-1]]))
+        if split:
+            xs.append(np.stack([np.maximum(conv3x3_s2_split(x, W, b), 0.0) for x in xs[-1]])
+                      .astype(np.float32).astype(np.float64))
+        else:
+            xs.append(np.stack([np.maximum(conv3x3_s2(x, W, b), 0.0) for x in xs[-1]]))
     W5, b5 = (np.asarray(a, dtype=np.float64) for a in enc_layers[4])
     m = xs[-1].mean(axis=(2, 3))
     return xs, m @ W5.T + b5
@@ -85,11 +92,13 @@ def conv_input_grad(delta, W, h, w):
     return gp[:, :, 1:h + 1, 1:w + 1]
 
 
-def gradients(noisy, clean, max_range, enc_layers, dec):
-    """Loss and the gradients of every tensor: (loss, [(gW1, gb1) .. (gW5, gb5)], (gWd, gbd))."""
+def gradients(noisy, clean, max_range, enc_layers, dec, split=False):
+    """Loss and the gradients of every tensor: (loss, [(gW1, gb1) .. (gW5, gb5)], (gWd, gbd)).
+    split: the forward pass of ``forward(..., split=True)`` (the gradients of the network as a
+    BF16-operand-split tensor-core forward pass computes it; ReLU kinks decided there)."""
     enc = [(np.asarray(W, dtype=np.float64), np.asarray(b, dtype=np.float64)) for W, b in enc_layers]
     Wd, bd = (np.asarray(a, dtype=np.float64) for a in dec)
-    xs, z = forward(noisy, max_range, enc)
+    xs, z = forward(noisy, max_range, enc, split=split)
     n = len(z)
     t = pooled_target(clean, max_range).reshape(n, -1)
     r = z @ Wd.T + bd - t
@@ -215,12 +224,13 @@ def sdf_term(z, points, labels, dec_layers, pe_levels):
 
 
 def gradients_joint(noisy, clean, max_range, enc_layers, dec, points, labels, sdf_layers, pe_levels, lam_recon,
-                    lam_sdf):
+                    lam_sdf, split=False):
     """Loss lam_recon L_recon + lam_sdf L_sdf and the gradients of the encoder's tensors and D_psi
-    (the SDF decoder frozen): (loss, L_recon, L_sdf, enc grads, dec grads)."""
+    (the SDF decoder frozen): (loss, L_recon, L_sdf, enc grads, dec grads).  split as in
+    ``gradients``."""
     enc = [(np.asarray(W, dtype=np.float64), np.asarray(b, dtype=np.float64)) for W, b in enc_layers]
     Wd, bd = (np.asarray(a, dtype=np.float64) for a in dec)
-    xs, z = forward(noisy, max_range, enc)
+    xs, z = forward(noisy, max_range, enc, split=split)
     n = len(z)
     t = pooled_target(clean, max_range).reshape(n, -1)
     r = z @ Wd.T + bd - t

@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmppi_gb300.so")
 
-SOURCES = ["mppi_api.cu", "k_step.cu", "k_sdf_fp32.cu", "k_sdf_tc.cu", "k_noalloc.cu", "mppi_server.cu", "k_train.cu", "k_train_tc.cu", "k_render.cu", "k_encoder.cu", "k_encoder_train.cu"]
+SOURCES = ["mppi_api.cu", "k_step.cu", "k_sdf_fp32.cu", "k_sdf_tc.cu", "k_noalloc.cu", "mppi_server.cu", "k_train.cu", "k_train_tc.cu", "k_render.cu", "k_encoder.cu", "k_encoder_tc.cu", "k_encoder_train.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--ptxas-options=-v",
          "-I" + INCLUDE, "-I" + CSRC]

@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "mppi.h"
 
 struct mppi_encoder {
@@ -16,10 +18,21 @@ struct mppi_encoder {
     float* b5 = nullptr;
     float* act[4] = {nullptr, nullptr, nullptr, nullptr};  // x_1 .. x_4 of the last encoded batch
     int n_sms = 152;
+    int conv_path = MPPI_ENC_CONV_TC;   // which convolution kernels mppi_encode_depth runs
+    int* d_err = nullptr;               // device error word of the tensor-core kernels' bounded waits
+    uint8_t* wpack[4] = {nullptr, nullptr, nullptr, nullptr};  // conv weights, BF16 hi / lo operand stages
     char err[512] = "";
 };
 
 namespace mppi {
 constexpr int kEncCin[4] = {1, 16, 32, 64};
 constexpr int kEncCout[4] = {16, 32, 64, 64};
+// tensor-core convolution of encoder layer 0..3 (k_encoder_tc.cu); configure once per encoder;
+// the weights are read from their packed form, which pack_conv_tc_weights refreshes from wt[]
+// (at creation and after every optimiser step)
+cudaError_t configure_conv_tc();
+size_t conv_tc_packed_bytes(int layer);
+cudaError_t pack_conv_tc_weights(const float* const* wt, uint8_t* const* out, cudaStream_t s);
+cudaError_t launch_conv_tc(int layer, const float* x, int n_img, int H, int W, int Ho, int Wo, const uint8_t* wpack,
+                           const float* b, float scale, float* y, int* err, cudaStream_t s);
 }  // namespace mppi

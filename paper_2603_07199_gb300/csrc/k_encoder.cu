@@ -273,9 +273,11 @@ void encoder_free(mppi_encoder* e) {
         cudaFree(e->wt[l]);
         cudaFree(e->bias[l]);
         cudaFree(e->act[l]);
+        cudaFree(e->wpack[l]);
     }
     cudaFree(e->W5);
     cudaFree(e->b5);
+    cudaFree(e->d_err);
 }
 
 // Split the reduction so that a layer with few output tiles still puts about two blocks on
@@ -360,6 +362,11 @@ extern "C" int mppi_encoder_create(int height, int width, int max_images, const 
         if (e->n_sms < 1) e->n_sms = 1;
     }
     constexpr int kZ = MPPI_LATENT_DIM;
+    ok = ok && cudaMalloc(&e->d_err, sizeof(int)) == cudaSuccess && cudaMemset(e->d_err, 0, sizeof(int)) == cudaSuccess &&
+         configure_conv_tc() == cudaSuccess;
+    for (int l = 0; l < 4 && ok; ++l) ok = cudaMalloc(&e->wpack[l], conv_tc_packed_bytes(l)) == cudaSuccess;
+    ok = ok && pack_conv_tc_weights(e->wt, e->wpack, e->stream) == cudaSuccess &&
+         cudaStreamSynchronize(e->stream) == cudaSuccess;
     ok = ok && alloc(&e->W5, kZ * kZ) && alloc(&e->b5, kZ) &&
          cudaMemcpy(e->W5, layers[8], kZ * kZ * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(e->b5, layers[9], kZ * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
@@ -391,15 +398,49 @@ extern "C" int mppi_encode_depth(mppi_encoder* e, int n_images, const float* d_d
     if (!(max_range > 0.f && max_range <= 3.0e38f)) return efail(e, MPPI_E_INVALID, "mppi_encode_depth: max_range must be > 0");
     if (n_images == 0) return MPPI_OK;
     if (!d_depth || !d_latents) return efail(e, MPPI_E_INVALID, "mppi_encode_depth: NULL pointer");
-    cudaError_t ce = launch_conv<1, 16, true>(e, 0, n_images, d_depth, 1.f / max_range, e->act[0]);
-    if (ce == cudaSuccess) ce = launch_conv<16, 32, false>(e, 1, n_images, e->act[0], 1.f, e->act[1]);
-    if (ce == cudaSuccess) ce = launch_conv<32, 64, false>(e, 2, n_images, e->act[1], 1.f, e->act[2]);
-    if (ce == cudaSuccess) ce = launch_conv<64, 64, false>(e, 3, n_images, e->act[2], 1.f, e->act[3]);
+    cudaError_t ce = cudaSuccess;
+    if (e->conv_path == MPPI_ENC_CONV_TC) {
+        const float* in = d_depth;
+        for (int l = 0; l < 4 && ce == cudaSuccess; ++l) {
+            ce = mppi::launch_conv_tc(l, in, n_images, e->h[l], e->w[l], e->h[l + 1], e->w[l + 1], e->wpack[l],
+                                      e->bias[l], l == 0 ? 1.f / max_range : 1.f, e->act[l], e->d_err, e->stream);
+            in = e->act[l];
+        }
+    } else {
+        ce = launch_conv<1, 16, true>(e, 0, n_images, d_depth, 1.f / max_range, e->act[0]);
+        if (ce == cudaSuccess) ce = launch_conv<16, 32, false>(e, 1, n_images, e->act[0], 1.f, e->act[1]);
+        if (ce == cudaSuccess) ce = launch_conv<32, 64, false>(e, 2, n_images, e->act[1], 1.f, e->act[2]);
+        if (ce == cudaSuccess) ce = launch_conv<64, 64, false>(e, 3, n_images, e->act[2], 1.f, e->act[3]);
+    }
     if (ce == cudaSuccess) {
         ce = mppi::launch_dependent(true, mppi::encoder_head_kernel, dim3(n_images), dim3(mppi::kHeadThreads), 0,
                                     e->stream, static_cast<const float*>(e->act[3]), e->h[4] * e->w[4],
                                     static_cast<const float*>(e->W5), static_cast<const float*>(e->b5), d_latents);
     }
     if (ce != cudaSuccess) return efail(e, MPPI_E_CUDA, "mppi_encode_depth: launch failed: %s", cudaGetErrorString(ce));
+    return MPPI_OK;
+}
+
+extern "C" int mppi_encoder_set_conv_path(mppi_encoder* e, int path) {
+    if (!e) return efail(nullptr, MPPI_E_INVALID, "mppi_encoder_set_conv_path: NULL encoder");
+    if (path != MPPI_ENC_CONV_FP32 && path != MPPI_ENC_CONV_TC)
+        return efail(e, MPPI_E_INVALID, "mppi_encoder_set_conv_path: unknown path %d", path);
+    e->conv_path = path;
+    return MPPI_OK;
+}
+
+extern "C" int mppi_encoder_check(mppi_encoder* e) {
+    if (!e) return efail(nullptr, MPPI_E_INVALID, "mppi_encoder_check: NULL encoder");
+    int word = 0;
+    cudaError_t ce = cudaMemcpyAsync(&word, e->d_err, sizeof(int), cudaMemcpyDeviceToHost, e->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
+    if (ce != cudaSuccess) return efail(e, MPPI_E_CUDA, "mppi_encoder_check: %s", cudaGetErrorString(ce));
+    if (word != 0) {
+        ce = cudaMemsetAsync(e->d_err, 0, sizeof(int), e->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
+        if (ce != cudaSuccess) return efail(e, MPPI_E_CUDA, "mppi_encoder_check: %s", cudaGetErrorString(ce));
+        return efail(e, MPPI_E_TIMEOUT, "a tensor-core convolution gave up waiting for its MMAs (device error word %d)",
+                     word);
+    }
     return MPPI_OK;
 }

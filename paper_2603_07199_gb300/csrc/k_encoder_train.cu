@@ -855,7 +855,9 @@ int adam_all(mppi_encoder_trainer* t, bool with_decoder) {
     const float c1 = static_cast<float>(1.0 - std::pow(0.9, t->step));
     const float c2 = static_cast<float>(1.0 - std::pow(0.999, t->step));
     mppi::adam_kernel<<<dim3((max_size + 255) / 256, nt), 256, 0, t->enc->stream>>>(tab, t->lr, c1, c2);
-    const cudaError_t ce = cudaGetLastError();
+    cudaError_t ce = cudaGetLastError();
+    // the tensor-core convolutions read the weights in their packed form
+    if (ce == cudaSuccess) ce = mppi::pack_conv_tc_weights(t->enc->wt, t->enc->wpack, t->enc->stream);
     if (ce != cudaSuccess) return tfail(t, MPPI_E_CUDA, "Adam launch failed: %s", cudaGetErrorString(ce));
     return MPPI_OK;
 }

@@ -4,7 +4,11 @@ FP64 oracle, through the C ABI, on depth images the oracle renders.
 Tolerance: each latent is a 64-term dot product of means of FP32 convolution chains whose
 sums have at most 9 x 64 terms of O(1); FP32 rounding gives about 1e-6 relative, so
 |z_gpu - z_oracle| <= 1e-4 (1 + |z|) leaves a wide margin while catching any wrong tap, channel
-or scale.  A ReLU decided differently by rounding changes z by at most the rounding itself."""
+or scale.  A ReLU decided differently by rounding changes z by at most the rounding itself.
+Both convolution paths are held to that bar: the FP32 CUDA-core GEMMs and the tensor-core
+kernels, whose BF16 hi/lo split keeps every product within ~3 x 2^-16 of its FP32 value
+(the dropped lo x lo term and the split's own rounding), errors that average out over the
+sums instead of adding up."""
 import numpy as np
 import pytest
 
@@ -30,15 +34,20 @@ def _flat(layers):
     return out
 
 
-def _encode(layers, imgs, max_range, max_images=None):
+PATHS = {"tc": B.MPPI_ENC_CONV_TC, "fp32": B.MPPI_ENC_CONV_FP32}
+
+
+def _encode(layers, imgs, max_range, max_images=None, path="tc"):
     torch = _torch()
     imgs = np.ascontiguousarray(imgs, np.float32)
     n, h, w = imgs.shape
     enc = B.mppi_encoder_create(h, w, max_images or max(n, 1), _flat(layers))
     try:
+        B.mppi_encoder_set_conv_path(enc, PATHS[path])
         d = torch.from_numpy(imgs).cuda()
         z = torch.full((max(n, 1), 64), 7.0, device="cuda")
         B.mppi_encode_depth(enc, n, d, max_range, z)
+        B.mppi_encoder_check(enc)
         torch.cuda.synchronize()
         return z.cpu().numpy()[:n]
     finally:
@@ -58,44 +67,65 @@ def _views(n, kw, seed):
     return R.depth_images(cams, gates, **kw)
 
 
-def test_encoder_parity_rendered_views():
+@pytest.mark.parametrize("path", ["tc", "fp32"])
+def test_encoder_parity_rendered_views(path):
     layers = W.encoder_weights(7)
     imgs = _views(6, SMALL_CAM, seed=31)
     assert np.mean(imgs < 10.0) > 0.01
-    got = _encode(layers, imgs, 10.0)
-    print("encoder max err", _check(got, E.encode(imgs, 10.0, layers)))
+    got = _encode(layers, imgs, 10.0, path=path)
+    print("encoder", path, "max err", _check(got, E.encode(imgs, 10.0, layers)))
 
 
+@pytest.mark.parametrize("path", ["tc", "fp32"])
 @pytest.mark.parametrize("h,w", [(37, 53), (1, 1), (2, 3), (97, 203)])
-def test_encoder_parity_ragged_sizes(h, w):
+def test_encoder_parity_ragged_sizes(h, w, path):
     layers = W.encoder_weights(8)
     rng = np.random.default_rng(h * 1000 + w)
     imgs = rng.uniform(0.0, 12.0, (3, h, w))
     imgs[:, ::3, ::2] = 12.0
-    _check(_encode(layers, imgs, 12.0), E.encode(imgs, 12.0, layers))
+    _check(_encode(layers, imgs, 12.0, path=path), E.encode(imgs, 12.0, layers))
 
 
-def test_encoder_noisy_views_and_full_batch():
+@pytest.mark.parametrize("path", ["tc", "fp32"])
+def test_encoder_noisy_views_and_full_batch(path):
     """The 64-view batch of the bench at 160 x 120, with sensor noise (depth dropouts read 0)."""
     layers = W.encoder_weights(7)
     clean = _views(64, SMALL_CAM, seed=6)
     noisy = R.add_sensor_noise(clean, 10.0, 0.005, 0.02, seed=9, frame=0)
-    got = _encode(layers, noisy, 10.0)
-    _check(got, E.encode(noisy, 10.0, layers))
+    got = _encode(layers, noisy, 10.0, path=path)
+    print("encoder", path, "64-view max err", _check(got, E.encode(noisy, 10.0, layers)))
+
+
+def test_encoder_paths_agree_and_tc_batch_is_exact():
+    """The tensor-core path computes every output pixel in one CTA over the whole reduction, in
+    the same order whatever the batch, so an image's code alone equals its code in a batch bit
+    for bit; the two paths agree within the rounding of their different summation orders."""
+    layers = W.encoder_weights(9)
+    imgs = _views(5, SMALL_CAM, seed=40)
+    batch = _encode(layers, imgs, 10.0, max_images=8, path="tc")
+    for i in range(5):
+        np.testing.assert_array_equal(_encode(layers, imgs[i:i + 1], 10.0, path="tc"), batch[i:i + 1])
+    np.testing.assert_allclose(_encode(layers, imgs, 10.0, path="fp32"), batch, rtol=1e-4, atol=1e-4)
 
 
 def test_encoder_batch_independence_and_errors():
     torch = _torch()
     layers = W.encoder_weights(9)
     imgs = _views(5, SMALL_CAM, seed=40)
-    batch = _encode(layers, imgs, 10.0, max_images=8)
+    batch = _encode(layers, imgs, 10.0, max_images=8, path="fp32")
     # a batch may split the reductions differently (fewer output tiles -> more split-K
     # slices), so an image's code matches its code alone up to summation order
     for i in range(5):
-        np.testing.assert_allclose(_encode(layers, imgs[i:i + 1], 10.0), batch[i:i + 1], rtol=1e-5, atol=1e-5)
-    np.testing.assert_array_equal(_encode(layers, imgs, 10.0, max_images=8), batch)     # same batch: same bits
+        np.testing.assert_allclose(_encode(layers, imgs[i:i + 1], 10.0, path="fp32"), batch[i:i + 1], rtol=1e-5,
+                                   atol=1e-5)
+    np.testing.assert_array_equal(_encode(layers, imgs, 10.0, max_images=8, path="fp32"), batch)  # same bits
     enc = B.mppi_encoder_create(120, 160, 2, _flat(layers))
     try:
+        for bad in (-1, 2, 7):
+            with pytest.raises(B.MppiError) as e:
+                B.mppi_encoder_set_conv_path(enc, bad)
+            assert e.value.code == B.MPPI_E_INVALID
+        assert B.mppi_encoder_check(enc) == B.MPPI_OK
         d = torch.zeros(3, 120, 160, device="cuda")
         z = torch.zeros(3, 64, device="cuda")
         for args in [(3, d, 10.0, z), (1, d, 0.0, z), (1, None, 10.0, z), (-1, d, 10.0, z)]:

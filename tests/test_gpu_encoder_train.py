@@ -45,10 +45,19 @@ def _decoder(T, seed=3):
     return rng.normal(0.0, 0.1, (T, 64)).astype(np.float32), np.zeros(T, np.float32)
 
 
-def _setup(h, w, n, batch):
+# The encoder's forward pass runs its tensor-core convolutions by default (BF16 hi/lo operand
+# split, FP32 accumulation); the oracle then takes its ReLU decisions in that precision model
+# (split=True), because a pre-activation within the split's rounding of zero may fall on either
+# side of its kink and the gradient jumps with it.  The FP32 CUDA-core path is checked against
+# the exact FP64 oracle.
+SPLIT = {"tc": True, "fp32": False}
+
+
+def _setup(h, w, n, batch, path="tc"):
     torch = _torch()
     enc_layers = W.encoder_weights(7)
     enc = B.mppi_encoder_create(h, w, batch, _flat(enc_layers))
+    B.mppi_encoder_set_conv_path(enc, B.MPPI_ENC_CONV_TC if path == "tc" else B.MPPI_ENC_CONV_FP32)
     T = -(-h // 8) * -(-w // 8)
     Wd, bd = _decoder(T)
     tr = B.mppi_encoder_train_create(enc, batch, 1e-3, Wd, bd)
@@ -60,8 +69,9 @@ def _shapes(enc_layers, dec):
     return [a.shape for pair in enc_layers for a in pair] + [dec[0].shape, dec[1].shape]
 
 
-def test_gradients_match_oracle():
-    torch, enc, tr, enc_layers, dec, noisy, clean = _setup(37, 53, 3, 4)
+@pytest.mark.parametrize("path", ["tc", "fp32"])
+def test_gradients_match_oracle(path):
+    torch, enc, tr, enc_layers, dec, noisy, clean = _setup(37, 53, 3, 4, path)
     try:
         grads = [np.zeros(s, np.float32) for s in _shapes(enc_layers, dec)]
         loss = B.mppi_encoder_train_loss_grads(tr, 3, torch.from_numpy(noisy).cuda(),
@@ -69,7 +79,7 @@ def test_gradients_match_oracle():
     finally:
         B.mppi_encoder_train_destroy(tr)
         B.mppi_encoder_destroy(enc)
-    L, g_enc, g_dec = OT.gradients(noisy, clean, 10.0, enc_layers, dec)
+    L, g_enc, g_dec = OT.gradients(noisy, clean, 10.0, enc_layers, dec, split=SPLIT[path])
     assert abs(loss - L) <= 1e-5 * L
     want = [g for pair in g_enc for g in pair] + list(g_dec)
     for i, (got, ref) in enumerate(zip(grads, want)):
@@ -88,7 +98,7 @@ def test_one_adam_step_matches_oracle():
     finally:
         B.mppi_encoder_train_destroy(tr)
         B.mppi_encoder_destroy(enc)
-    _, g_enc, g_dec = OT.gradients(noisy, clean, 10.0, enc_layers, dec)
+    _, g_enc, g_dec = OT.gradients(noisy, clean, 10.0, enc_layers, dec, split=True)
     grads = [g for pair in g_enc for g in pair] + list(g_dec)
     params = [np.asarray(a, np.float64) for pair in enc_layers for a in pair] + [np.asarray(a, np.float64) for a in dec]
     want, _, _ = OT.adam_step(params, grads, [np.zeros_like(p) for p in params], [np.zeros_like(p) for p in params],
@@ -221,7 +231,8 @@ def test_sdf_term_gradients_match_oracle():
         B.mppi_encoder_destroy(enc)
     L, Lr, Ls, g_enc, g_dec = OT.gradients_joint(noisy, clean, 10.0, enc_layers, dec,
                                                   p.astype(np.float32).astype(np.float64),
-                                                  lab.astype(np.float32).astype(np.float64), sdf_dec, 2, 0.5, 1.0)
+                                                  lab.astype(np.float32).astype(np.float64), sdf_dec, 2, 0.5, 1.0,
+                                                  split=True)
     assert abs(rec - Lr) <= 1e-5 * Lr and abs(sdf - Ls) <= 1e-4 * Ls and abs(tot - L) <= 1e-4 * L
     want = [g for pair in g_enc for g in pair] + list(g_dec)
     for i, (got, ref) in enumerate(zip(grads, want)):
@@ -296,8 +307,9 @@ def test_stage1_decoder_gradients_match_oracle():
         B.mppi_encoder_train_destroy(tr)
         B.mppi_encoder_destroy(enc)
     pts, labs = p32.astype(np.float64), l32.astype(np.float64)
-    _, _, _, g_enc, g_dec = OT.gradients_joint(noisy, clean, 10.0, enc_layers, dec, pts, labs, sdf_dec, 1, 0.5, 1.0)
-    _, z = OT.forward(noisy, 10.0, enc_layers)
+    _, _, _, g_enc, g_dec = OT.gradients_joint(noisy, clean, 10.0, enc_layers, dec, pts, labs, sdf_dec, 1, 0.5, 1.0,
+                                               split=True)
+    _, z = OT.forward(noisy, 10.0, enc_layers, split=True)
     _, _, g_sdf = OT.decoder_grads(z, pts, labs, sdf_dec, 1)
     want = [g for pair in g_enc for g in pair] + list(g_dec) + [g for pair in g_sdf for g in pair]
     for i, (got, ref) in enumerate(zip(grads, want)):

@@ -93,3 +93,47 @@ def test_encode_scale_invariance_and_batch():
     np.testing.assert_allclose(E.encode(imgs * 2.5, 25.0, layers), z, rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(E.encode(imgs[1], 10.0, layers)[0], z[1], rtol=0, atol=0)
     assert np.std(z[0] - z[1]) > 1e-3            # different images give different codes
+
+
+def test_bf16_round_known_values_and_torch():
+    """bfloat16 rounding: exact values stay, ties go to the even pattern, the rest to nearest;
+    against PyTorch's CPU float32 -> bfloat16 conversion on random and extreme values."""
+    one = 1.0
+    assert E.bf16_round(np.array([one]))[0] == 1.0
+    assert E.bf16_round(np.array([1.0 + 2.0 ** -8]))[0] == 1.0                    # tie -> even (1.0)
+    assert E.bf16_round(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6    # tie -> even (up)
+    assert E.bf16_round(np.array([1.0 + 2.0 ** -8 + 2.0 ** -12]))[0] == 1.0 + 2.0 ** -7
+    assert E.bf16_round(np.array([-3.0]))[0] == -3.0
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    v = np.concatenate([rng.standard_normal(10000) * 10.0 ** rng.integers(-30, 30, 10000),
+                        [0.0, -0.0, 1e-40, 3.0e38]]).astype(np.float32)
+    ref = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(E.bf16_round(v), ref)
+
+
+def test_bf16_split_bound_and_exact_cases():
+    rng = np.random.default_rng(6)
+    a = (rng.standard_normal(20000) * 10.0 ** rng.integers(-8, 8, 20000)).astype(np.float32).astype(np.float64)
+    hi, lo = E.bf16_split(a)
+    assert np.all(np.abs(a - hi - lo) <= 2.0 ** -16 * np.abs(a))
+    exact = E.bf16_round(a)                     # already bfloat16: the remainder is zero
+    h2, l2 = E.bf16_split(exact)
+    np.testing.assert_array_equal(h2, exact)
+    assert not np.any(l2)
+
+
+def test_split_conv_exact_on_bf16_operands_and_close_otherwise():
+    """On operands that are bfloat16 numbers the split convolution is the exact one (the lo parts
+    vanish); on general FP32 operands it stays within 3 x 2^-16 of the sum of |products|."""
+    rng = np.random.default_rng(7)
+    x = E.bf16_round(rng.standard_normal((3, 9, 11)))
+    wt = E.bf16_round(rng.standard_normal((4, 3, 3, 3)))
+    b = rng.standard_normal(4)
+    np.testing.assert_allclose(E.conv3x3_s2_split(x, wt, b), E.conv3x3_s2(x, wt, b), rtol=0, atol=1e-12)
+    x = rng.standard_normal((3, 9, 11)).astype(np.float32).astype(np.float64)
+    wt = rng.standard_normal((4, 3, 3, 3)).astype(np.float32).astype(np.float64)
+    bound = 3 * 2.0 ** -16 * E.conv3x3_s2(np.abs(x), np.abs(wt), np.zeros(4))
+    err = np.abs(E.conv3x3_s2_split(x, wt, b) - E.conv3x3_s2(x, wt, b))
+    assert np.all(err <= bound + 1e-12)
+    assert err.max() > 0.0

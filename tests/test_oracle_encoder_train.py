@@ -61,6 +61,32 @@ def test_gradients_match_central_differences():
             assert abs(num - g_dec[which][idx]) <= 1e-5 * (np.max(np.abs(g_dec[which])) + 1e-12) + 1e-9
 
 
+def test_split_precision_gradients_reduce_to_the_exact_ones():
+    """The split-operand forward (tensor-core precision model) changes only the forward values:
+    with bfloat16-representable weights and inputs its products are exact, so its gradients
+    equal the exact ones up to the float32 storage of the activations; on general weights they
+    stay within the split's rounding of the exact gradients when no ReLU or residual sign sits
+    that close to its kink."""
+    from oracle import encoder as E
+    noisy, clean, enc, dec = _setup()
+    enc_b = [(E.bf16_round(Wm), E.bf16_round(b)) for Wm, b in enc]
+    noisy_b = E.bf16_round(noisy / 10.0) * 10.0          # depth / 10 is then a bfloat16 number
+    L0, g0, d0 = T.gradients(noisy_b, clean, 10.0, enc_b, dec)
+    L1, g1, d1 = T.gradients(noisy_b, clean, 10.0, enc_b, dec, split=True)
+    assert abs(L1 - L0) <= 1e-6 * L0
+    for (a, b), (c, d) in zip(g0, g1):
+        assert np.max(np.abs(a - c)) <= 1e-5 * np.max(np.abs(a))
+        assert np.max(np.abs(b - d)) <= 1e-5 * np.max(np.abs(b))
+    L2, g2, _ = T.gradients(noisy, clean, 10.0, enc, dec, split=True)
+    Lx, gx, _ = T.gradients(noisy, clean, 10.0, enc, dec)
+    xs, _ = T.forward(noisy, 10.0, enc)
+    margin = min(np.min(np.abs(x[np.abs(x) > 0])) for x in xs[1:])
+    assert abs(L2 - Lx) <= 1e-4 * Lx
+    if margin > 1e-4:                                   # no kink within reach of the split's rounding
+        for (a, _), (c, _) in zip(gx, g2):
+            assert np.max(np.abs(a - c)) <= 1e-3 * np.max(np.abs(a))
+
+
 def test_adam_first_step_is_lr_sign():
     p = [np.array([1.0, -2.0, 3.0])]
     g = [np.array([0.5, -1e-3, 0.0])]
