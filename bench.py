@@ -713,6 +713,11 @@ def vision_leg(torch, B, stream, flush, dev, steps, drone_id):
 
     ms_batch = timed(batch)
     ms_enc = timed(lambda: B.mppi_encode_depth(enc, n, depth, kw["max_range"], z))
+    # the same encoding with the FP32 CUDA-core convolutions (the tensor-core ones are the default)
+    B.mppi_encoder_set_conv_path(enc, B.MPPI_ENC_CONV_FP32)
+    ms_enc32 = timed(lambda: B.mppi_encode_depth(enc, n, depth, kw["max_range"], z))
+    B.mppi_encoder_set_conv_path(enc, B.MPPI_ENC_CONV_TC)
+    B.mppi_encoder_check(enc)
     # one drone's control cycle: a view of each gate (the first camera pose that faces it)
     wl_mppi = W.two_gate_mlp()
     ctx = make_ctx(B, wl_mppi, HEADLINE_MODE, stream, drone_id)
@@ -785,8 +790,13 @@ def vision_leg(torch, B, stream, flush, dev, steps, drone_id):
             "batch_render_encode": {"images": n, "mean_ms": float(ms_batch.mean()),
                                     "images_per_s": n / (ms_batch.mean() * 1e-3)},
             "encode_only": {"images": n, "mean_ms": float(ms_enc.mean()), "images_per_s": n / (ms_enc.mean() * 1e-3),
+                            "convolutions": "tcgen05, BF16 hi/lo operand split (3 products), FP32 accumulation",
                             "gflop_per_launch": n * ENCODER_FLOPS_PER_IMAGE_160x120 / 1e9,
-                            "achieved_tflops_fp32": n * ENCODER_FLOPS_PER_IMAGE_160x120 / (ms_enc.mean() * 1e-3) / 1e12},
+                            "achieved_tflops": n * ENCODER_FLOPS_PER_IMAGE_160x120 / (ms_enc.mean() * 1e-3) / 1e12,
+                            "fp32_cuda_cores": {"mean_ms": float(ms_enc32.mean()),
+                                                "achieved_tflops": n * ENCODER_FLOPS_PER_IMAGE_160x120 /
+                                                (ms_enc32.mean() * 1e-3) / 1e12},
+                            "speedup_vs_fp32": float(ms_enc32.mean() / ms_enc.mean())},
             "encoder_training": {"images_per_step": n, "mean_ms": float(ms_train.mean()),
                                  "steps_per_s": 1e3 / float(ms_train.mean()),
                                  "images_per_s": n / (ms_train.mean() * 1e-3)},

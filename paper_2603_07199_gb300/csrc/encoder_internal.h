@@ -35,4 +35,10 @@ size_t conv_tc_packed_bytes(int layer);
 cudaError_t pack_conv_tc_weights(const float* const* wt, uint8_t* const* out, cudaStream_t s);
 cudaError_t launch_conv_tc(int layer, const float* x, int n_img, int H, int W, int Ho, int Wo, const uint8_t* wpack,
                            const float* b, float scale, float* y, int* err, cudaStream_t s);
+// weight gradient of layer 0..3 on the tensor cores: partial sums of `slices` pixel slices of
+// stages_per_slice x conv_wgrad_tc_stage_pixels() output pixels into ws[slice][c_out][9 c_in + 1]
+int conv_wgrad_tc_stage_pixels();
+int conv_wgrad_tc_k_tiles(int layer);
+cudaError_t launch_conv_wgrad_tc(int layer, const float* x, const float* delta, int n_img, int H, int W, int Ho, int Wo,
+                                 float scale, int slices, int stages_per_slice, float* ws, int* err, cudaStream_t s);
 }  // namespace mppi

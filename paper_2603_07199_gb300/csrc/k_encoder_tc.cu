@@ -366,6 +366,222 @@ __global__ void __launch_bounds__(kEtThreads) conv3x3s2_tc_kernel(const float* _
     }
 }
 
+// ---------------------------------------------------------------- weight gradients
+// Partial sums over a slice of output pixels of the weight gradient of one convolution as the
+// GEMM  D[k][co] = sum_p X[p][k] delta[p][co]  (M = 128 rows of k = ci 9 + t, the weights' own
+// order, with the ones row k = 9 CI giving the bias gradient; N = CO; the reduction over pixels
+// p in stages of kWgStage), both operands K-major (pixels contiguous): row k of the X stage holds
+// X[p][k] for the stage's 64 pixels (gathered from the NCHW input of the layer), row co of the
+// delta stage delta[n][co][i][j] of the same pixels.  The same BF16 hi/lo split and three
+// products as the forward pass, two stage buffers, one commit per stage.  Each CTA writes its
+// slice's partial D to ws[slice][co][k] (k < 9 CI + 1); the caller sums the slices in order.
+constexpr int kWgStage = 64;   // pixels per stage
+constexpr int kWgRows = 128;   // k rows per CTA (M)
+
+template <int CI, int CO>
+struct WgradShape {
+    static constexpr int K1 = 9 * CI + 1;
+    static constexpr uint32_t kXHalf = kWgRows * kWgStage * 2;
+    static constexpr uint32_t kDHalf = CO * kWgStage * 2;
+    static constexpr uint32_t kBuf = 2 * kXHalf + 2 * kDHalf;
+    static constexpr uint32_t kHead = 1024;
+    static constexpr uint32_t kSmem = kHead + 2 * kBuf;
+    static constexpr uint32_t kTmemCols = CO <= 32 ? 32 : CO;
+    static constexpr uint32_t kSbo = kWgStage * 16;
+    static constexpr int kXTasks = kWgRows * kWgStage / 8 / kEtThreads;       // 8-pixel chunks per thread
+    static constexpr int kDTasks = (CO * kWgStage / 8 + kEtThreads - 1) / kEtThreads;
+    static_assert(kXTasks * kEtThreads * 8 == kWgRows * kWgStage, "whole X chunks per thread");
+};
+
+// Flat output pixel p -> (image n, row i, column j) of an Ho x Wo output; advanced one pixel at a
+// time without divisions.
+struct PixCursor {
+    int n, i, j;
+    __device__ __forceinline__ void start(long long p, int hw, int Wo) {
+        n = static_cast<int>(p / hw);
+        const int rem = static_cast<int>(p - static_cast<long long>(n) * hw);
+        i = rem / Wo;
+        j = rem - i * Wo;
+    }
+    __device__ __forceinline__ void next(int Ho, int Wo) {
+        if (++j == Wo) {
+            j = 0;
+            if (++i == Ho) {
+                i = 0;
+                ++n;
+            }
+        }
+    }
+};
+
+template <int CI, int CO, bool kScale>
+__global__ void __launch_bounds__(kEtThreads) conv_wgrad_tc_kernel(const float* __restrict__ x,
+                                                                   const float* __restrict__ delta, int n_img, int H,
+                                                                   int W, int Ho, int Wo, float scale,
+                                                                   int stages_per_slice, float* __restrict__ ws,
+                                                                   int* err) {
+    using S = WgradShape<CI, CO>;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 16);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 20);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_u32(tmem_slot), S::kTmemCols);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(tc::smem_u32(&bar[0]), 1);
+        tc::mbar_init(tc::smem_u32(&bar[1]), 1);
+        *abort_flag = 0;
+        tc::mbar_fence_init();
+    }
+    pdl_trigger();
+    pdl_wait();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const int hw = Ho * Wo;
+    const long long P = static_cast<long long>(n_img) * hw;
+    const long long n_stages = (P + kWgStage - 1) / kWgStage;
+    const long long s_begin = static_cast<long long>(blockIdx.y) * stages_per_slice;
+    const int n_local = static_cast<int>(max(0LL, min(static_cast<long long>(stages_per_slice), n_stages - s_begin)));
+    const int k_base = blockIdx.x * kWgRows;
+    const size_t plane = static_cast<size_t>(H) * W;
+    const uint32_t buf0 = tc::smem_u32(smem + S::kHead);
+    constexpr uint32_t kIdesc = tc::idesc_bf16_f32(kWgRows, CO);
+
+    bool ok = true;
+    int last_commit = -1;
+#pragma unroll 1
+    for (int sl = 0; sl < n_local; ++sl) {
+        const long long p0 = (s_begin + sl) * kWgStage;
+        const uint32_t buf = buf0 + static_cast<uint32_t>(sl & 1) * S::kBuf;
+        // X chunks: task -> row r (8 consecutive rows per quarter warp), 8-pixel chunk c
+        float xv[S::kXTasks][8];
+#pragma unroll
+        for (int u = 0; u < S::kXTasks; ++u) {
+            const int task = tid + u * kEtThreads;
+            const int r = (task & 7) + 8 * ((task >> 3) & 15), c = task >> 7;
+            const int k = k_base + r;
+            const int ci = k / 9, t = k - 9 * (k / 9);
+            const int ky = t / 3, kx = t - 3 * (t / 3);
+            PixCursor pc;
+            pc.start(p0 + 8 * c, hw, Wo);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const bool live = p0 + 8 * c + q < P;
+                float v = 0.f;
+                if (live && k < 9 * CI) {
+                    const int yy = 2 * pc.i + ky - 1, xx = 2 * pc.j + kx - 1;
+                    if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+                        v = __ldg(x + (static_cast<size_t>(pc.n) * CI + ci) * plane + static_cast<size_t>(yy) * W + xx);
+                        if (kScale) v *= scale;
+                    }
+                } else if (live && k == 9 * CI) {
+                    v = 1.f;
+                }
+                xv[u][q] = v;
+                pc.next(Ho, Wo);
+            }
+        }
+        // delta chunks: task -> row co, 8-pixel chunk c (a quarter warp: eight rows of one chunk)
+        float dv[S::kDTasks][8];
+#pragma unroll
+        for (int u = 0; u < S::kDTasks; ++u) {
+            const int task = tid + u * kEtThreads;
+            const int co = (task & 7) + 8 * ((task >> 3) % (CO / 8)), c = task / CO;
+            PixCursor pc;
+            pc.start(p0 + 8 * c, hw, Wo);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                float v = 0.f;
+                if (task < CO * kWgStage / 8 && p0 + 8 * c + q < P)
+                    v = __ldg(delta + (static_cast<size_t>(pc.n) * CO + co) * hw + pc.i * Wo + pc.j);
+                dv[u][q] = v;
+                pc.next(Ho, Wo);
+            }
+        }
+        if (sl >= 2) ok = tc::mbar_wait_bounded(tc::smem_u32(&bar[sl & 1]), static_cast<uint32_t>(((sl - 2) >> 1) & 1),
+                                                abort_flag, err, kDevErrTimeout);
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+#pragma unroll
+        for (int u = 0; u < S::kXTasks; ++u) {
+            const int task = tid + u * kEtThreads;
+            const int r = (task & 7) + 8 * ((task >> 3) & 15), c = task >> 7;
+            const uint32_t off = stage_offset<kWgStage>(r, 8 * c);
+            store_split8(buf + off, buf + S::kXHalf + off, xv[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < S::kDTasks; ++u) {
+            const int task = tid + u * kEtThreads;
+            if (task < CO * kWgStage / 8) {
+                const int co = (task & 7) + 8 * ((task >> 3) % (CO / 8)), c = task / CO;
+                const uint32_t off = stage_offset<kWgStage>(co, 8 * c);
+                store_split8(buf + 2 * S::kXHalf + off, buf + 2 * S::kXHalf + S::kDHalf + off, dv[u]);
+            }
+        }
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+#pragma unroll
+            for (int j = 0; j < kWgStage / 16; ++j) {
+                const uint32_t dj = static_cast<uint32_t>(256 * j);
+                const uint64_t ahi = tc::smem_desc(buf + dj, 128, S::kSbo);
+                const uint64_t alo = tc::smem_desc(buf + S::kXHalf + dj, 128, S::kSbo);
+                const uint64_t bhi = tc::smem_desc(buf + 2 * S::kXHalf + dj, 128, S::kSbo);
+                const uint64_t blo = tc::smem_desc(buf + 2 * S::kXHalf + S::kDHalf + dj, 128, S::kSbo);
+                tc::mma_bf16(tmem, ahi, bhi, kIdesc, (sl > 0 || j > 0) ? 1u : 0u);
+                tc::mma_bf16(tmem, ahi, blo, kIdesc, 1u);
+                tc::mma_bf16(tmem, alo, bhi, kIdesc, 1u);
+            }
+            tc::mma_commit(tc::smem_u32(&bar[sl & 1]));
+            last_commit = sl;
+        }
+    }
+    const int last = n_local - 1;
+    if (ok && last >= 0)
+        ok = tc::mbar_wait_bounded(tc::smem_u32(&bar[last & 1]), static_cast<uint32_t>((last >> 1) & 1), abort_flag,
+                                   err, kDevErrTimeout);
+    ok = __syncthreads_and(ok);
+    if (!ok && tid == 0 && last_commit >= 0) {
+        int dummy = 0;
+        tc::mbar_wait_bounded(tc::smem_u32(&bar[last_commit & 1]), static_cast<uint32_t>((last_commit >> 1) & 1),
+                              &dummy, err, kDevErrTimeout);
+    }
+    tc::fence_after_sync();
+    {
+        const int row = tid & (kWgRows - 1), half = tid >> 7;
+        const int k = k_base + row;
+        const uint32_t lane_addr = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);
+        constexpr int kHalfCo = CO / 2;
+#pragma unroll
+        for (int c0 = half * kHalfCo; c0 < (half + 1) * kHalfCo; c0 += 8) {
+            uint32_t v[8];
+            tmem_ld_32x32b_x8(lane_addr + static_cast<uint32_t>(c0), v);
+            tc::tmem_wait_ld();
+            if (k < S::K1) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    ws[(static_cast<size_t>(blockIdx.y) * CO + c0 + q) * S::K1 + k] =
+                        (ok && n_local > 0) ? __uint_as_float(v[q]) : 0.f;
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, S::kTmemCols);
+    }
+}
+
 template <int CI, int CO, bool kScale, int kSplit>
 cudaError_t configure_one() {
     return cudaFuncSetAttribute(conv3x3s2_tc_kernel<CI, CO, kScale, kSplit>,
@@ -402,8 +618,27 @@ constexpr int kSplit3 = 4;   // 64 -> 64 channels: 12 stages, 3 per CTA
 
 }  // namespace
 
+template <int CI, int CO, bool kScale>
+cudaError_t configure_wgrad() {
+    return cudaFuncSetAttribute(conv_wgrad_tc_kernel<CI, CO, kScale>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(WgradShape<CI, CO>::kSmem));
+}
+
+template <int CI, int CO, bool kScale>
+cudaError_t wgrad_one(const float* x, const float* delta, int n_img, int H, int W, int Ho, int Wo, float scale,
+                      int slices, int stages_per_slice, float* ws, int* err, cudaStream_t s) {
+    const int k_tiles = (WgradShape<CI, CO>::K1 + kWgRows - 1) / kWgRows;
+    return launch_dependent(true, conv_wgrad_tc_kernel<CI, CO, kScale>, dim3(k_tiles, slices), dim3(kEtThreads),
+                            WgradShape<CI, CO>::kSmem, s, x, delta, n_img, H, W, Ho, Wo, scale, stages_per_slice, ws,
+                            err);
+}
+
 cudaError_t configure_conv_tc() {
-    cudaError_t e = configure_one<1, 16, true, 1>();
+    cudaError_t e = configure_wgrad<1, 16, true>();
+    if (e == cudaSuccess) e = configure_wgrad<16, 32, false>();
+    if (e == cudaSuccess) e = configure_wgrad<32, 64, false>();
+    if (e == cudaSuccess) e = configure_wgrad<64, 64, false>();
+    if (e == cudaSuccess) e = configure_one<1, 16, true, 1>();
     if (e == cudaSuccess) e = configure_one<16, 32, false, 1>();
     if (e == cudaSuccess) e = configure_one<32, 64, false, kSplit2>();
     if (e == cudaSuccess) e = configure_one<64, 64, false, kSplit3>();
@@ -417,6 +652,23 @@ cudaError_t launch_conv_tc(int layer, const float* x, int n_img, int H, int W, i
         case 1: return launch_one<16, 32, false, 1>(x, n_img, H, W, Ho, Wo, wt, b, scale, y, err, s);
         case 2: return launch_one<32, 64, false, kSplit2>(x, n_img, H, W, Ho, Wo, wt, b, scale, y, err, s);
         case 3: return launch_one<64, 64, false, kSplit3>(x, n_img, H, W, Ho, Wo, wt, b, scale, y, err, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int conv_wgrad_tc_stage_pixels() { return kWgStage; }
+int conv_wgrad_tc_k_tiles(int layer) {
+    static constexpr int kCin[4] = {1, 16, 32, 64};
+    return (9 * kCin[layer] + 1 + kWgRows - 1) / kWgRows;
+}
+
+cudaError_t launch_conv_wgrad_tc(int layer, const float* x, const float* delta, int n_img, int H, int W, int Ho, int Wo,
+                                 float scale, int slices, int stages_per_slice, float* ws, int* err, cudaStream_t s) {
+    switch (layer) {
+        case 0: return wgrad_one<1, 16, true>(x, delta, n_img, H, W, Ho, Wo, scale, slices, stages_per_slice, ws, err, s);
+        case 1: return wgrad_one<16, 32, false>(x, delta, n_img, H, W, Ho, Wo, scale, slices, stages_per_slice, ws, err, s);
+        case 2: return wgrad_one<32, 64, false>(x, delta, n_img, H, W, Ho, Wo, scale, slices, stages_per_slice, ws, err, s);
+        case 3: return wgrad_one<64, 64, false>(x, delta, n_img, H, W, Ho, Wo, scale, slices, stages_per_slice, ws, err, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -210,6 +210,72 @@ __global__ void __launch_bounds__(kWgThreads) conv_wgrad_kernel(const float* __r
     }
 }
 
+// The first layer's weight gradient (one input channel: K = 9 taps + the bias column) over a
+// slice of output pixels: every thread keeps the 8 x 10 sums of half of the 16 channels
+// (blockIdx.y) for its pixels (one 3 x 3 input window and 8 output gradients each), then the
+// block sums them in a fixed order (warp shuffle tree, then the warps in index order) and writes
+// ws[slice][co][k].  The reduction is short and the pixels many, so the CUDA cores keep it.
+constexpr int kW1Threads = 256;
+template <bool kScale>
+__global__ void __launch_bounds__(kW1Threads) conv1_wgrad_kernel(const float* __restrict__ x,
+                                                                 const float* __restrict__ delta, int n_img, int H,
+                                                                 int W, int Ho, int Wo, float scale,
+                                                                 long long pixels_per_slice, float* __restrict__ ws) {
+    constexpr int CO = 16, K1 = 10, CH = 8;
+    __shared__ float red[kW1Threads / 32][CH * K1];
+    const int hw = Ho * Wo;
+    const long long P = static_cast<long long>(n_img) * hw;
+    const long long p_begin = static_cast<long long>(blockIdx.x) * pixels_per_slice;
+    const long long p_end = min(p_begin + pixels_per_slice, P);
+    const int co0 = blockIdx.y * CH;
+    float acc[CH][K1];
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int k = 0; k < K1; ++k) acc[c][k] = 0.f;
+    for (long long p = p_begin + threadIdx.x; p < p_end; p += kW1Threads) {
+        const int n = static_cast<int>(p / hw);
+        const int rem = static_cast<int>(p - static_cast<long long>(n) * hw);
+        const int i = rem / Wo, j = rem - (rem / Wo) * Wo;
+        float xv[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int yy = 2 * i + t / 3 - 1, xx = 2 * j + t % 3 - 1;
+            float v = 0.f;
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+                v = __ldg(x + (static_cast<size_t>(n) * H + yy) * W + xx);
+                if (kScale) v *= scale;
+            }
+            xv[t] = v;
+        }
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const float d = __ldg(delta + (static_cast<size_t>(n) * CO + co0 + c) * hw + rem);
+#pragma unroll
+            for (int t = 0; t < 9; ++t) acc[c][t] = fmaf(d, xv[t], acc[c][t]);
+            acc[c][9] += d;
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int k = 0; k < K1; ++k) {
+            float v = acc[c][k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][c * K1 + k] = v;
+        }
+    __syncthreads();
+    if (threadIdx.x < CH * K1) {
+        float v = 0.f;
+#pragma unroll
+        for (int w = 0; w < kW1Threads / 32; ++w) v += red[w][threadIdx.x];
+        const int c = threadIdx.x / K1, k = threadIdx.x - (threadIdx.x / K1) * K1;
+        ws[(static_cast<size_t>(blockIdx.x) * CO + co0 + c) * K1 + k] = v;
+    }
+}
+
 // gW[co][k] (= the [co][ci][ky][kx] layout) and gb[co] from the slices' partial sums, in slice
 // order: one thread per element.
 __global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float* __restrict__ ws, int n_slices, int CO, int K1,
@@ -700,8 +766,28 @@ template <int CI, int CO, bool kScale>
 cudaError_t launch_wgrad(mppi_encoder_trainer* t, int l, int n, const float* x, float scale, const float* delta) {
     const mppi_encoder* e = t->enc;
     constexpr int K1 = 9 * CI + 1;
-    const int k_tiles = (K1 + mppi::kWgK - 1) / mppi::kWgK;
     const long long P = static_cast<long long>(n) * e->h[l + 1] * e->w[l + 1];
+    if (e->conv_path == MPPI_ENC_CONV_TC) {
+        // tensor cores: 128 k rows x all channels per CTA, pixel slices of whole 64-pixel stages,
+        // about two CTAs per SM
+        const int kt = mppi::conv_wgrad_tc_k_tiles(l);
+        const long long stages = (P + mppi::conv_wgrad_tc_stage_pixels() - 1) / mppi::conv_wgrad_tc_stage_pixels();
+        long long S = std::max(1LL, std::min(stages, (2LL * e->n_sms + kt - 1) / kt));
+        while (static_cast<size_t>(S) * CO * K1 > t->ws_floats && S > 1) --S;
+        const int cps = static_cast<int>((stages + S - 1) / S);
+        S = (stages + cps - 1) / cps;
+        cudaError_t ce = mppi::launch_conv_wgrad_tc(l, x, delta, n, e->h[l], e->w[l], e->h[l + 1], e->w[l + 1], scale,
+                                                    static_cast<int>(S), cps, t->ws, e->d_err, e->stream);
+        if (ce != cudaSuccess) return ce;
+        if (S > 32)
+            mppi::wgrad_reduce_wide_kernel<<<CO * K1, 128, 0, e->stream>>>(t->ws, static_cast<int>(S), CO, K1,
+                                                                           t->grad[2 * l], t->grad[2 * l + 1]);
+        else
+            mppi::wgrad_reduce_kernel<<<(CO * K1 + 255) / 256, 256, 0, e->stream>>>(
+                t->ws, static_cast<int>(S), CO, K1, t->grad[2 * l], t->grad[2 * l + 1]);
+        return cudaGetLastError();
+    }
+    const int k_tiles = (K1 + mppi::kWgK - 1) / mppi::kWgK;
     const long long chunks = (P + mppi::kWgP - 1) / mppi::kWgP;
     int S = wgrad_slices(e, k_tiles, chunks);
     while (static_cast<size_t>(S) * CO * K1 > t->ws_floats && S > 1) --S;
@@ -715,6 +801,28 @@ cudaError_t launch_wgrad(mppi_encoder_trainer* t, int l, int n, const float* x, 
     else
         mppi::wgrad_reduce_kernel<<<(CO * K1 + 255) / 256, 256, 0, e->stream>>>(t->ws, S, CO, K1, t->grad[2 * l],
                                                                                t->grad[2 * l + 1]);
+    return cudaGetLastError();
+}
+
+// The first layer's weight gradient (conv1_wgrad_kernel, slices of whole 256-pixel rounds, about
+// four blocks per SM), then the slices summed in order.
+cudaError_t launch_wgrad1(mppi_encoder_trainer* t, int n, const float* x, float scale, const float* delta) {
+    const mppi_encoder* e = t->enc;
+    constexpr int CO = 16, K1 = 10;
+    const long long P = static_cast<long long>(n) * e->h[1] * e->w[1];
+    const long long rounds = (P + mppi::kW1Threads - 1) / mppi::kW1Threads;
+    long long S = std::max(1LL, std::min(rounds, 2LL * e->n_sms));
+    while (static_cast<size_t>(S) * CO * K1 > t->ws_floats && S > 1) --S;
+    const long long per = (rounds + S - 1) / S * mppi::kW1Threads;
+    S = (P + per - 1) / per;
+    mppi::conv1_wgrad_kernel<true><<<dim3(static_cast<unsigned>(S), 2), mppi::kW1Threads, 0, e->stream>>>(
+        x, delta, n, e->h[0], e->w[0], e->h[1], e->w[1], scale, per, t->ws);
+    if (S > 32)
+        mppi::wgrad_reduce_wide_kernel<<<CO * K1, 128, 0, e->stream>>>(t->ws, static_cast<int>(S), CO, K1, t->grad[0],
+                                                                       t->grad[1]);
+    else
+        mppi::wgrad_reduce_kernel<<<(CO * K1 + 255) / 256, 256, 0, e->stream>>>(t->ws, static_cast<int>(S), CO, K1,
+                                                                               t->grad[0], t->grad[1]);
     return cudaGetLastError();
 }
 
@@ -808,7 +916,7 @@ int loss_grads(mppi_encoder_trainer* t, int n, const float* d_noisy, const float
     if (ce == cudaSuccess) ce = launch_wgrad<16, 32, false>(t, 1, n, e->act[0], 1.f, cur);
     if (ce == cudaSuccess) ce = launch_dgrad<16, 32>(t, 1, n, cur, nxt);
     std::swap(cur, nxt);
-    if (ce == cudaSuccess) ce = launch_wgrad<1, 16, true>(t, 0, n, d_noisy, 1.f / max_range, cur);
+    if (ce == cudaSuccess) ce = launch_wgrad1(t, n, d_noisy, 1.f / max_range, cur);
     if (ce != cudaSuccess) return tfail(t, MPPI_E_CUDA, "launch failed: %s", cudaGetErrorString(ce));
     if (losses) {
         t->h_loss.resize(n);
@@ -953,7 +1061,10 @@ extern "C" int mppi_encoder_train_create(mppi_encoder* enc, int batch, float lr,
     for (int l = 0; l < 4; ++l)
         delta_floats = std::max(delta_floats, static_cast<size_t>(batch) * kEncCout[l] * enc->h[l + 1] * enc->w[l + 1]);
     // a split layer has S <= ceil(2 SMs / k_tiles) slices of CO x K1 <= 64 x 32 k_tiles floats
-    t->ws_floats = static_cast<size_t>(64) * kWgK * (2 * enc->n_sms + 32);
+    // enough for the CUDA-core slicing and for the tensor-core one (the 64 -> 64 layer: 5 k tiles,
+    // about two CTAs per SM, 64 x 577 partial sums each)
+    t->ws_floats = std::max(static_cast<size_t>(64) * kWgK * (2 * enc->n_sms + 32),
+                            static_cast<size_t>((2 * enc->n_sms + 4) / 5) * 64 * (9 * 64 + 1));
     ok = ok && talloc(t, &t->z, static_cast<size_t>(batch) * kLat) &&
          talloc(t, &t->g, static_cast<size_t>(batch) * t->T) && talloc(t, &t->dz, static_cast<size_t>(batch) * kLat) &&
          talloc(t, &t->m4, static_cast<size_t>(batch) * kLat) && talloc(t, &t->loss_img, batch) &&
