@@ -21,6 +21,7 @@ struct mppi_encoder {
     int conv_path = MPPI_ENC_CONV_TC;   // which convolution kernels mppi_encode_depth runs
     int* d_err = nullptr;               // device error word of the tensor-core kernels' bounded waits
     uint8_t* wpack[4] = {nullptr, nullptr, nullptr, nullptr};  // conv weights, BF16 hi / lo operand stages
+    uint8_t* dgpack[4] = {nullptr, nullptr, nullptr, nullptr}; // the same per parity class for input gradients (1..3)
     char err[512] = "";
 };
 
@@ -32,13 +33,18 @@ constexpr int kEncCout[4] = {16, 32, 64, 64};
 // (at creation and after every optimiser step)
 cudaError_t configure_conv_tc();
 size_t conv_tc_packed_bytes(int layer);
-cudaError_t pack_conv_tc_weights(const float* const* wt, uint8_t* const* out, cudaStream_t s);
+size_t conv_dgrad_tc_packed_bytes(int layer);
+cudaError_t pack_conv_tc_weights(const float* const* wt, uint8_t* const* out, uint8_t* const* out_dgrad,
+                                 cudaStream_t s);
 cudaError_t launch_conv_tc(int layer, const float* x, int n_img, int H, int W, int Ho, int Wo, const uint8_t* wpack,
                            const float* b, float scale, float* y, int* err, cudaStream_t s);
 // weight gradient of layer 0..3 on the tensor cores: partial sums of `slices` pixel slices of
 // stages_per_slice x conv_wgrad_tc_stage_pixels() output pixels into ws[slice][c_out][9 c_in + 1]
 int conv_wgrad_tc_stage_pixels();
 int conv_wgrad_tc_k_tiles(int layer);
+// input gradient (ReLU mask of the input applied) of layer 1..3 on the tensor cores
+cudaError_t launch_conv_dgrad_tc(int layer, const float* delta, const uint8_t* wpack, const float* x_in, int n_img,
+                                 int H, int W, int Ho, int Wo, float* delta_in, int* err, cudaStream_t s);
 cudaError_t launch_conv_wgrad_tc(int layer, const float* x, const float* delta, int n_img, int H, int W, int Ho, int Wo,
                                  float scale, int slices, int stages_per_slice, float* ws, int* err, cudaStream_t s);
 }  // namespace mppi

@@ -274,6 +274,7 @@ void encoder_free(mppi_encoder* e) {
         cudaFree(e->bias[l]);
         cudaFree(e->act[l]);
         cudaFree(e->wpack[l]);
+        cudaFree(e->dgpack[l]);
     }
     cudaFree(e->W5);
     cudaFree(e->b5);
@@ -365,7 +366,8 @@ extern "C" int mppi_encoder_create(int height, int width, int max_images, const 
     ok = ok && cudaMalloc(&e->d_err, sizeof(int)) == cudaSuccess && cudaMemset(e->d_err, 0, sizeof(int)) == cudaSuccess &&
          configure_conv_tc() == cudaSuccess;
     for (int l = 0; l < 4 && ok; ++l) ok = cudaMalloc(&e->wpack[l], conv_tc_packed_bytes(l)) == cudaSuccess;
-    ok = ok && pack_conv_tc_weights(e->wt, e->wpack, e->stream) == cudaSuccess &&
+    for (int l = 1; l < 4 && ok; ++l) ok = cudaMalloc(&e->dgpack[l], conv_dgrad_tc_packed_bytes(l)) == cudaSuccess;
+    ok = ok && pack_conv_tc_weights(e->wt, e->wpack, e->dgpack, e->stream) == cudaSuccess &&
          cudaStreamSynchronize(e->stream) == cudaSuccess;
     ok = ok && alloc(&e->W5, kZ * kZ) && alloc(&e->b5, kZ) &&
          cudaMemcpy(e->W5, layers[8], kZ * kZ * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&

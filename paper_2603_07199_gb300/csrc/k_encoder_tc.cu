@@ -582,6 +582,232 @@ __global__ void __launch_bounds__(kEtThreads) conv_wgrad_tc_kernel(const float* 
     }
 }
 
+// ---------------------------------------------------------------- input gradients
+// The gradient at the input of a convolution (ReLU mask of that input applied),
+//   delta_in[n][ci][y][x] = [x_in > 0] sum_{co, (ky, kx)} W[co][ci][ky][kx] delta[n][co][i][j],
+// over the windows (i, j) = ((y + 1 - ky) / 2, (x + 1 - kx) / 2) that read pixel (y, x).  The
+// taps that can reach (y, x) depend only on its parity class (y mod 2, x mod 2): ky = 1 for even
+// y, ky in {0, 2} for odd y (kx likewise), so each class is one GEMM  D[q][ci] = sum_k A[q][k]
+// B[ci][k]  over its pixels q (M = 128 per CTA, blockIdx.y = class), N = CI, and k = tap_index CO
+// + co (1, 2 or 4 taps): A[q][k] = delta at the tap's window (zero outside the output), B the
+// class's weights, packed per class (pack_dgrad_weights_kernel) and loaded by one bulk copy.
+// Stages of 32 columns, two threads per row, the same BF16 hi/lo split and three products.
+constexpr int kDgStage = 32;
+
+template <int CI, int CO>
+struct DgradShape {
+    static constexpr uint32_t kAHalf = kEtRows * kDgStage * 2;
+    static constexpr uint32_t kBuf = 2 * kAHalf;
+    static constexpr uint32_t kBHalf = CI * kDgStage * 2;
+    static constexpr uint32_t kBStage = 2 * kBHalf;
+    static constexpr int kMaxStages = 4 * CO / kDgStage;      // the class with four taps
+    static constexpr uint32_t kHead = 1024;
+    static constexpr uint32_t kSmem = kHead + 2 * kBuf + kMaxStages * kBStage;
+    static constexpr uint32_t kTmemCols = CI <= 32 ? 32 : CI;
+    static constexpr uint32_t kSbo = kDgStage * 16;
+    static_assert(CO % kDgStage == 0 && CI % 16 == 0, "whole stages per tap, N a multiple of 16");
+    __host__ __device__ static constexpr int stages(int cls) { return (1 + (cls >> 1)) * (1 + (cls & 1)) * CO / kDgStage; }
+    __host__ __device__ static constexpr size_t class_offset(int cls) {
+        size_t o = 0;
+        for (int c = 0; c < cls; ++c) o += static_cast<size_t>(stages(c)) * kBStage;
+        return o;
+    }
+};
+
+// (ky, kx) of tap index t of parity class cls: ky = 1 for even rows, {0, 2} for odd ones.
+__device__ __forceinline__ void class_tap(int cls, int t, int& ky, int& kx) {
+    const int py = cls >> 1, px = cls & 1;
+    const int nkx = 1 + px;
+    const int a = t / nkx, b = t - a * nkx;
+    ky = py ? 2 * a : 1;
+    kx = px ? 2 * b : 1;
+}
+
+template <int CI, int CO>
+__global__ void __launch_bounds__(256) pack_dgrad_weights_kernel(const float* __restrict__ wt, uint8_t* __restrict__ out) {
+    using S = DgradShape<CI, CO>;
+    constexpr int kChunks = CI * kDgStage / 8;                 // per stage
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int cls = 0, rem = e;
+    while (cls < 4 && rem >= S::stages(cls) * kChunks) {
+        rem -= S::stages(cls) * kChunks;
+        ++cls;
+    }
+    if (cls >= 4) return;
+    const int s = rem / kChunks, r = rem - s * kChunks;
+    const int ci = r / (kDgStage / 8), c = (r - ci * (kDgStage / 8)) * 8;
+    const int k0 = s * kDgStage + c;
+    const int t = k0 / CO, co0 = k0 - t * CO;
+    int ky, kx;
+    class_tap(cls, t, ky, kx);
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = wt[((static_cast<size_t>(co0 + q) * CI + ci) * 3 + ky) * 3 + kx];
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        h[q] = tc::pack_bf16x2(v[2 * q], v[2 * q + 1]);
+        l[q] = tc::pack_bf16x2(v[2 * q] - __uint_as_float(h[q] << 16), v[2 * q + 1] - __uint_as_float(h[q] & 0xFFFF0000u));
+    }
+    uint8_t* st = out + S::class_offset(cls) + static_cast<size_t>(s) * S::kBStage + stage_offset<kDgStage>(ci, c);
+    *reinterpret_cast<uint4*>(st) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(st + S::kBHalf) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+template <int CI, int CO>
+__global__ void __launch_bounds__(kEtThreads) conv_dgrad_tc_kernel(const float* __restrict__ delta,
+                                                                   const uint8_t* __restrict__ wpack,
+                                                                   const float* __restrict__ x_in, int n_img, int H,
+                                                                   int W, int Ho, int Wo,
+                                                                   float* __restrict__ delta_in, int* err) {
+    using S = DgradShape<CI, CO>;
+    const int cls = blockIdx.y, py = cls >> 1, px = cls & 1;
+    const int ny = (H - py + 1) / 2, nx = (W - px + 1) / 2;
+    const long long count = static_cast<long long>(n_img) * ny * nx;
+    if (static_cast<long long>(blockIdx.x) * kEtRows >= count) return;   // the class has fewer tiles
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* bar_w = reinterpret_cast<uint64_t*>(smem + 32);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 16);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 20);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int row = tid & (kEtRows - 1), half = tid >> 7;
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_u32(tmem_slot), S::kTmemCols);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(tc::smem_u32(&bar[0]), 1);
+        tc::mbar_init(tc::smem_u32(&bar[1]), 1);
+        tc::mbar_init(tc::smem_u32(bar_w), 1);
+        *abort_flag = 0;
+        tc::mbar_fence_init();
+    }
+    pdl_trigger();
+    pdl_wait();
+    const int n_st = S::stages(cls);
+    const uint32_t bres = tc::smem_u32(smem + S::kHead + 2 * S::kBuf);
+    if (tid == 0)
+        bulk_load(bres, wpack + S::class_offset(cls), static_cast<uint32_t>(n_st) * S::kBStage, tc::smem_u32(bar_w));
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    // this thread's pixel of the class
+    const long long f = static_cast<long long>(blockIdx.x) * kEtRows + row;
+    const bool live = f < count;
+    int n = 0, y = 0, x = 0;
+    if (live) {
+        n = static_cast<int>(f / (static_cast<long long>(ny) * nx));
+        const int r = static_cast<int>(f - static_cast<long long>(n) * ny * nx);
+        y = 2 * (r / nx) + py;
+        x = 2 * (r - (r / nx) * nx) + px;
+    }
+    const size_t hwo = static_cast<size_t>(Ho) * Wo;
+    const float* dn = delta + static_cast<size_t>(n) * CO * hwo;
+    const uint32_t buf0 = tc::smem_u32(smem + S::kHead);
+    constexpr uint32_t kIdesc = tc::idesc_bf16_f32(kEtRows, CI);
+    constexpr int kHalfCols = kDgStage / 2;
+
+    auto gather = [&](int s, float (&a)[kHalfCols]) {
+        const int k0 = s * kDgStage + half * kHalfCols;
+        const int t = k0 / CO, co0 = k0 - t * CO;
+        int ky, kx;
+        class_tap(cls, t, ky, kx);
+        const int i = (y + 1 - ky) >> 1, j = (x + 1 - kx) >> 1;
+        const bool v = live && i < Ho && j < Wo;
+        const float* src = dn + static_cast<size_t>(co0) * hwo + static_cast<size_t>(i) * Wo + j;
+#pragma unroll
+        for (int q = 0; q < kHalfCols; ++q) a[q] = v ? __ldg(src + static_cast<size_t>(q) * hwo) : 0.f;
+    };
+
+    bool ok = true;
+    int last_commit = -1;
+    float a_next[kHalfCols];
+    gather(0, a_next);
+#pragma unroll 1
+    for (int sl = 0; sl < n_st; ++sl) {
+        const uint32_t buf = buf0 + static_cast<uint32_t>(sl & 1) * S::kBuf;
+        float a[kHalfCols];
+#pragma unroll
+        for (int c = 0; c < kHalfCols; ++c) a[c] = a_next[c];
+        if (sl + 1 < n_st) gather(sl + 1, a_next);
+        if (sl >= 2) ok = tc::mbar_wait_bounded(tc::smem_u32(&bar[sl & 1]), static_cast<uint32_t>(((sl - 2) >> 1) & 1),
+                                                abort_flag, err, kDevErrTimeout);
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+#pragma unroll
+        for (int c8 = 0; c8 < kHalfCols; c8 += 8) {
+            const uint32_t off = stage_offset<kDgStage>(row, half * kHalfCols + c8);
+            store_split8(buf + off, buf + S::kAHalf + off, a + c8);
+        }
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const bool go = sl > 0 || tc::mbar_wait_bounded(tc::smem_u32(bar_w), 0u, abort_flag, err, kDevErrTimeout);
+            if (!go) ok = false;
+            if (go) {
+                const uint32_t wb = bres + static_cast<uint32_t>(sl) * S::kBStage;
+#pragma unroll
+                for (int jj = 0; jj < kDgStage / 16; ++jj) {
+                    const uint32_t dj = static_cast<uint32_t>(256 * jj);
+                    const uint64_t ahi = tc::smem_desc(buf + dj, 128, S::kSbo);
+                    const uint64_t alo = tc::smem_desc(buf + S::kAHalf + dj, 128, S::kSbo);
+                    const uint64_t bhi = tc::smem_desc(wb + dj, 128, S::kSbo);
+                    const uint64_t blo = tc::smem_desc(wb + S::kBHalf + dj, 128, S::kSbo);
+                    tc::mma_bf16(tmem, ahi, bhi, kIdesc, (sl > 0 || jj > 0) ? 1u : 0u);
+                    tc::mma_bf16(tmem, ahi, blo, kIdesc, 1u);
+                    tc::mma_bf16(tmem, alo, bhi, kIdesc, 1u);
+                }
+                tc::mma_commit(tc::smem_u32(&bar[sl & 1]));
+                last_commit = sl;
+            }
+        }
+    }
+    const int last = n_st - 1;
+    if (ok) ok = tc::mbar_wait_bounded(tc::smem_u32(&bar[last & 1]), static_cast<uint32_t>((last >> 1) & 1), abort_flag,
+                                       err, kDevErrTimeout);
+    ok = __syncthreads_and(ok);
+    if (!ok && tid == 0) {
+        int dummy = 0;
+        if (last_commit >= 0)
+            tc::mbar_wait_bounded(tc::smem_u32(&bar[last_commit & 1]), static_cast<uint32_t>((last_commit >> 1) & 1),
+                                  &dummy, err, kDevErrTimeout);
+        tc::mbar_wait_bounded(tc::smem_u32(bar_w), 0u, &dummy, err, kDevErrTimeout);
+    }
+    tc::fence_after_sync();
+    if (ok) {
+        const uint32_t lane_addr = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);
+        constexpr int kHalfCi = CI / 2;
+        const size_t hw = static_cast<size_t>(H) * W;
+        const size_t o0 = static_cast<size_t>(n) * CI * hw + static_cast<size_t>(y) * W + x;
+#pragma unroll
+        for (int c0 = half * kHalfCi; c0 < (half + 1) * kHalfCi; c0 += 8) {
+            uint32_t v[8];
+            tmem_ld_32x32b_x8(lane_addr + static_cast<uint32_t>(c0), v);
+            tc::tmem_wait_ld();
+            if (live) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const size_t o = o0 + static_cast<size_t>(c0 + q) * hw;
+                    delta_in[o] = __ldg(x_in + o) > 0.f ? __uint_as_float(v[q]) : 0.f;
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, S::kTmemCols);
+    }
+}
+
 template <int CI, int CO, bool kScale, int kSplit>
 cudaError_t configure_one() {
     return cudaFuncSetAttribute(conv3x3s2_tc_kernel<CI, CO, kScale, kSplit>,
@@ -633,8 +859,36 @@ cudaError_t wgrad_one(const float* x, const float* delta, int n_img, int H, int 
                             err);
 }
 
+template <int CI, int CO>
+cudaError_t configure_dgrad() {
+    return cudaFuncSetAttribute(conv_dgrad_tc_kernel<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(DgradShape<CI, CO>::kSmem));
+}
+
+template <int CI, int CO>
+cudaError_t dgrad_one(const float* delta, const uint8_t* wpack, const float* x_in, int n_img, int H, int W, int Ho,
+                      int Wo, float* delta_in, int* err, cudaStream_t s) {
+    // the most tiles of a class: the one with the even rows and columns
+    const long long most = static_cast<long long>(n_img) * ((H + 1) / 2) * ((W + 1) / 2);
+    const unsigned tiles = static_cast<unsigned>((most + kEtRows - 1) / kEtRows);
+    return launch_dependent(true, conv_dgrad_tc_kernel<CI, CO>, dim3(tiles, 4), dim3(kEtThreads),
+                            DgradShape<CI, CO>::kSmem, s, delta, wpack, x_in, n_img, H, W, Ho, Wo, delta_in, err);
+}
+
+template <int CI, int CO>
+cudaError_t pack_dgrad_one(const float* wt, uint8_t* out, cudaStream_t s) {
+    using S = DgradShape<CI, CO>;
+    int n = 0;
+    for (int c = 0; c < 4; ++c) n += S::stages(c) * CI * kDgStage / 8;
+    pack_dgrad_weights_kernel<CI, CO><<<(n + 255) / 256, 256, 0, s>>>(wt, out);
+    return cudaGetLastError();
+}
+
 cudaError_t configure_conv_tc() {
-    cudaError_t e = configure_wgrad<1, 16, true>();
+    cudaError_t e = configure_dgrad<16, 32>();
+    if (e == cudaSuccess) e = configure_dgrad<32, 64>();
+    if (e == cudaSuccess) e = configure_dgrad<64, 64>();
+    if (e == cudaSuccess) e = configure_wgrad<1, 16, true>();
     if (e == cudaSuccess) e = configure_wgrad<16, 32, false>();
     if (e == cudaSuccess) e = configure_wgrad<32, 64, false>();
     if (e == cudaSuccess) e = configure_wgrad<64, 64, false>();
@@ -673,6 +927,25 @@ cudaError_t launch_conv_wgrad_tc(int layer, const float* x, const float* delta, 
     }
 }
 
+size_t conv_dgrad_tc_packed_bytes(int layer) {
+    switch (layer) {
+        case 1: return DgradShape<16, 32>::class_offset(4);
+        case 2: return DgradShape<32, 64>::class_offset(4);
+        case 3: return DgradShape<64, 64>::class_offset(4);
+        default: return 0;
+    }
+}
+
+cudaError_t launch_conv_dgrad_tc(int layer, const float* delta, const uint8_t* wpack, const float* x_in, int n_img,
+                                 int H, int W, int Ho, int Wo, float* delta_in, int* err, cudaStream_t s) {
+    switch (layer) {
+        case 1: return dgrad_one<16, 32>(delta, wpack, x_in, n_img, H, W, Ho, Wo, delta_in, err, s);
+        case 2: return dgrad_one<32, 64>(delta, wpack, x_in, n_img, H, W, Ho, Wo, delta_in, err, s);
+        case 3: return dgrad_one<64, 64>(delta, wpack, x_in, n_img, H, W, Ho, Wo, delta_in, err, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 size_t conv_tc_packed_bytes(int layer) {
     switch (layer) {
         case 0: return packed_bytes<1, 16>();
@@ -691,11 +964,15 @@ cudaError_t pack_one(const float* wt, uint8_t* out, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t pack_conv_tc_weights(const float* const* wt, uint8_t* const* out, cudaStream_t s) {
+cudaError_t pack_conv_tc_weights(const float* const* wt, uint8_t* const* out, uint8_t* const* out_dgrad,
+                                 cudaStream_t s) {
     cudaError_t e = pack_one<1, 16>(wt[0], out[0], s);
     if (e == cudaSuccess) e = pack_one<16, 32>(wt[1], out[1], s);
     if (e == cudaSuccess) e = pack_one<32, 64>(wt[2], out[2], s);
     if (e == cudaSuccess) e = pack_one<64, 64>(wt[3], out[3], s);
+    if (e == cudaSuccess) e = pack_dgrad_one<16, 32>(wt[1], out_dgrad[1], s);
+    if (e == cudaSuccess) e = pack_dgrad_one<32, 64>(wt[2], out_dgrad[2], s);
+    if (e == cudaSuccess) e = pack_dgrad_one<64, 64>(wt[3], out_dgrad[3], s);
     return e;
 }
 

@@ -829,6 +829,9 @@ cudaError_t launch_wgrad1(mppi_encoder_trainer* t, int n, const float* x, float 
 template <int CI, int CO>
 cudaError_t launch_dgrad(mppi_encoder_trainer* t, int l, int n, const float* delta, float* delta_in) {
     const mppi_encoder* e = t->enc;
+    if (e->conv_path == MPPI_ENC_CONV_TC)
+        return mppi::launch_conv_dgrad_tc(l, delta, e->dgpack[l], e->act[l - 1], n, e->h[l], e->w[l], e->h[l + 1],
+                                          e->w[l + 1], delta_in, e->d_err, e->stream);
     const long long pix = static_cast<long long>(n) * e->h[l] * e->w[l];
     const dim3 grid(static_cast<unsigned>((pix + mppi::kDgThreads - 1) / mppi::kDgThreads), CI / mppi::kDgGroup);
     mppi::conv_dgrad_kernel<CI, CO><<<grid, mppi::kDgThreads, 0, e->stream>>>(
@@ -965,7 +968,7 @@ int adam_all(mppi_encoder_trainer* t, bool with_decoder) {
     mppi::adam_kernel<<<dim3((max_size + 255) / 256, nt), 256, 0, t->enc->stream>>>(tab, t->lr, c1, c2);
     cudaError_t ce = cudaGetLastError();
     // the tensor-core convolutions read the weights in their packed form
-    if (ce == cudaSuccess) ce = mppi::pack_conv_tc_weights(t->enc->wt, t->enc->wpack, t->enc->stream);
+    if (ce == cudaSuccess) ce = mppi::pack_conv_tc_weights(t->enc->wt, t->enc->wpack, t->enc->dgpack, t->enc->stream);
     if (ce != cudaSuccess) return tfail(t, MPPI_E_CUDA, "Adam launch failed: %s", cudaGetErrorString(ce));
     return MPPI_OK;
 }
