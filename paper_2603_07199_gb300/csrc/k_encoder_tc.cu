@@ -452,14 +452,10 @@ __global__ void __launch_bounds__(kEtThreads) conv_wgrad_tc_kernel(const float* 
     const uint32_t buf0 = tc::smem_u32(smem + S::kHead);
     constexpr uint32_t kIdesc = tc::idesc_bf16_f32(kWgRows, CO);
 
-    bool ok = true;
-    int last_commit = -1;
-#pragma unroll 1
-    for (int sl = 0; sl < n_local; ++sl) {
+    // X chunks: task -> row r (8 consecutive rows per quarter warp), 8-pixel chunk c; delta chunks:
+    // task -> row co, 8-pixel chunk c (a quarter warp: eight rows of one chunk)
+    auto gather = [&](int sl, float (&xv)[S::kXTasks][8], float (&dv)[S::kDTasks][8]) {
         const long long p0 = (s_begin + sl) * kWgStage;
-        const uint32_t buf = buf0 + static_cast<uint32_t>(sl & 1) * S::kBuf;
-        // X chunks: task -> row r (8 consecutive rows per quarter warp), 8-pixel chunk c
-        float xv[S::kXTasks][8];
 #pragma unroll
         for (int u = 0; u < S::kXTasks; ++u) {
             const int task = tid + u * kEtThreads;
@@ -486,8 +482,6 @@ __global__ void __launch_bounds__(kEtThreads) conv_wgrad_tc_kernel(const float* 
                 pc.next(Ho, Wo);
             }
         }
-        // delta chunks: task -> row co, 8-pixel chunk c (a quarter warp: eight rows of one chunk)
-        float dv[S::kDTasks][8];
 #pragma unroll
         for (int u = 0; u < S::kDTasks; ++u) {
             const int task = tid + u * kEtThreads;
@@ -503,6 +497,26 @@ __global__ void __launch_bounds__(kEtThreads) conv_wgrad_tc_kernel(const float* 
                 pc.next(Ho, Wo);
             }
         }
+    };
+
+    bool ok = true;
+    int last_commit = -1;
+    float xn_[S::kXTasks][8], dn_[S::kDTasks][8];
+    if (n_local > 0) gather(0, xn_, dn_);
+#pragma unroll 1
+    for (int sl = 0; sl < n_local; ++sl) {
+        const uint32_t buf = buf0 + static_cast<uint32_t>(sl & 1) * S::kBuf;
+        float xv[S::kXTasks][8], dv[S::kDTasks][8];
+#pragma unroll
+        for (int u = 0; u < S::kXTasks; ++u)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) xv[u][q] = xn_[u][q];
+#pragma unroll
+        for (int u = 0; u < S::kDTasks; ++u)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) dv[u][q] = dn_[u][q];
+        // the next stage's loads are in flight while this one is stored and issued
+        if (sl + 1 < n_local) gather(sl + 1, xn_, dn_);
         if (sl >= 2) ok = tc::mbar_wait_bounded(tc::smem_u32(&bar[sl & 1]), static_cast<uint32_t>(((sl - 2) >> 1) & 1),
                                                 abort_flag, err, kDevErrTimeout);
         if (!__syncthreads_and(ok)) {

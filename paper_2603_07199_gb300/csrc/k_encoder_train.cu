@@ -779,7 +779,9 @@ cudaError_t launch_wgrad(mppi_encoder_trainer* t, int l, int n, const float* x, 
         cudaError_t ce = mppi::launch_conv_wgrad_tc(l, x, delta, n, e->h[l], e->w[l], e->h[l + 1], e->w[l + 1], scale,
                                                     static_cast<int>(S), cps, t->ws, e->d_err, e->stream);
         if (ce != cudaSuccess) return ce;
-        if (S > 32)
+        // a block per element only when the elements are few (its strided reads are slow); otherwise a
+        // thread per element reads the slices in order with coalesced loads
+        if (S > 32 && CO * K1 < 4096)
             mppi::wgrad_reduce_wide_kernel<<<CO * K1, 128, 0, e->stream>>>(t->ws, static_cast<int>(S), CO, K1,
                                                                            t->grad[2 * l], t->grad[2 * l + 1]);
         else
