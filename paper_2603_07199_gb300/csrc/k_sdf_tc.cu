@@ -419,6 +419,9 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
     // (ascending tiles) points to, whose fields are read where they are used
     int cur = 0, ltile = 0;
     const BatchSlot* sl = kBatch ? R.slots : nullptr;
+    // one-controller launches: the next tile's position is loaded while this tile runs
+    float4 p_next = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!kBatch && slot < n_tiles) p_next = B.pos[min(slot * kTileRows + row, n_rows - 1)];
     for (int tile = slot; tile < n_tiles && ok; tile += nslots) {
         ltile = tile;
         if constexpr (kBatch) {
@@ -439,7 +442,13 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
         const int nvalid = min(kTileRows, n_rows - row0);          // the last tile may be ragged
         const bool active = quad * 32 < nvalid;                   // this warp's quadrant has rows
         const int r = row0 + row;
-        const float4 p = (kBatch ? sl->B.pos : B.pos)[min(r, n_rows - 1)];
+        float4 p;
+        if constexpr (kBatch) {
+            p = sl->B.pos[min(r, n_rows - 1)];
+        } else {
+            p = p_next;
+            if (tile + nslots < n_tiles) p_next = B.pos[min((tile + nslots) * kTileRows + row, n_rows - 1)];
+        }
         float smin = __int_as_float(0x7f800000);
         for (int g = g_lo; g < g_hi && ok; ++g) {
             // layer-1 A operand (K = 16): the gate-frame point split p = hi + lo in BF16,
@@ -487,7 +496,10 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
             for (int l = 0; l < 4; ++l) {
                 // every thread of the group agrees on the outcome before going on, so a
                 // timeout seen by one thread cannot strand the others at a named barrier
-                const bool got = tc::mbar_wait_bounded(acc_bar, acc_phase, abort_flag, errw, kDevErrTimeout);
+                // one warp of the group polls the accumulator barrier; the others sleep in the named
+                // barrier until it arrives (no issue slots spent spinning)
+                bool got = true;
+                if ((warp % kGroupWarps) == 0) got = tc::mbar_wait_bounded(acc_bar, acc_phase, abort_flag, errw, kDevErrTimeout);
                 if (!tc::named_barrier_and(bar_id, kGroupThreads, got)) {
                     ok = false;
                     break;
