@@ -198,11 +198,21 @@ void finish(mppi_server* s, const Inflight& f, int status, std::vector<float>&& 
     ++s->completed;
 }
 
+// A request admitted under the server's lock, launched after the lock is released (so that a
+// submitting thread never waits for GPU launches).
+struct Admitted {
+    Inflight f;
+    mppi_ctx* ctx;
+    Request req;
+};
+
 void worker_loop(mppi_server* s) {
     cudaSetDevice(s->device);
     std::vector<float> scratch;
+    std::vector<Admitted> todo;
     while (true) {
         bool progress = false, idle = false;
+        todo.clear();
         {
             std::lock_guard<std::mutex> lock(s->mu);
             // completions
@@ -238,24 +248,35 @@ void worker_loop(mppi_server* s) {
                     it = s->queue.erase(it);
                     continue;
                 }
-                const int e = mppi::ctx_enqueue_host_step(d.ctx, it->state, it->n_gates,
-                                                          it->poses.empty() ? nullptr : it->poses.data(),
-                                                          it->latents.empty() ? nullptr : it->latents.data());
-                if (e != MPPI_OK) {
-                    sfail(s, e, "drone %d: %s", it->drone, mppi_last_error(d.ctx));
-                    finish(s, f, e, {});
-                    it = s->queue.erase(it);
-                    continue;
-                }
+                // busy: no eviction and no second admission of this drone until it completes
                 d.busy = true;
                 d.last_use = ++s->lru_clock;
                 ++s->admitted;
                 s->inflight.push_back(f);
+                todo.push_back(Admitted{f, d.ctx, std::move(*it)});
                 it = s->queue.erase(it);
                 progress = true;
             }
             idle = s->queue.empty() && s->inflight.empty();
             if (idle && s->stop) break;
+        }
+        // launches outside the lock (only this thread uses a busy drone's context); a request whose
+        // launch fails is finished with its error under the lock
+        for (Admitted& a : todo) {
+            const Request& r = a.req;
+            const int e = mppi::ctx_enqueue_host_step(a.ctx, r.state, r.n_gates, r.poses.empty() ? nullptr : r.poses.data(),
+                                                      r.latents.empty() ? nullptr : r.latents.data());
+            if (e != MPPI_OK) {
+                std::lock_guard<std::mutex> lock(s->mu);
+                sfail(s, e, "drone %d: %s", a.f.drone, mppi_last_error(a.ctx));
+                finish(s, a.f, e, {});
+                s->drones[a.f.drone].busy = false;
+                for (size_t i = 0; i < s->inflight.size(); ++i)
+                    if (s->inflight[i].ticket == a.f.ticket) {
+                        s->inflight.erase(s->inflight.begin() + static_cast<long>(i));
+                        break;
+                    }
+            }
         }
         if (idle)
             std::this_thread::sleep_for(std::chrono::microseconds(50));
@@ -269,8 +290,8 @@ void worker_loop(mppi_server* s) {
 // prep, rollout, SDF and update launches, and the completion event.  With positional encoding or
 // the FP32 MLP the SDF runs per drone (the batched SDF launch is the tensor-core one without
 // encoding), still on the batch's stream.
-int launch_batch(mppi_server* s, BatchBuf& b, int n, size_t in_floats, int roll_blocks, int tiles, int upd_blocks,
-                 int max_h, int max_r, const std::vector<mppi_ctx*>& ctxs) {
+cudaError_t launch_batch(mppi_server* s, BatchBuf& b, int n, size_t in_floats, int roll_blocks, int tiles,
+                         int upd_blocks, int max_h, int max_r, const std::vector<mppi_ctx*>& ctxs) {
     using namespace mppi;
     cudaStream_t st = b.stream;
     const BatchSlot* hs = reinterpret_cast<const BatchSlot*>(b.h);
@@ -299,8 +320,7 @@ int launch_batch(mppi_server* s, BatchBuf& b, int n, size_t in_floats, int roll_
     }
     if (e == cudaSuccess) e = launch_cost_update_batch(ds, n, upd_blocks, max_r, st);
     if (e == cudaSuccess) e = cudaEventRecord(b.done, st);
-    if (e != cudaSuccess) return sfail(s, MPPI_E_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
-    return MPPI_OK;
+    return e;
 }
 
 void batched_worker_loop(mppi_server* s) {
@@ -310,6 +330,11 @@ void batched_worker_loop(mppi_server* s) {
     std::vector<mppi_ctx*> ctxs;
     while (true) {
         bool progress = false, idle = false;
+        // a batch formed under the lock is launched after it is released (so that a submitting
+        // thread never waits for GPU launches); its buffer is already in s->order, and the next
+        // completion check (this thread, after the launch) sees its recorded event
+        int launch_fb = -1, launch_n = 0, l_roll = 0, l_tiles = 0, l_upd = 0, l_max_h = 1, l_max_r = 32;
+        size_t l_in = 0;
         {
             std::lock_guard<std::mutex> lock(s->mu);
             // completions (batches on different streams may finish in any order)
@@ -403,24 +428,43 @@ void batched_worker_loop(mppi_server* s) {
                     it = s->queue.erase(it);
                 }
                 if (n > 0) {
-                    const int rc = launch_batch(s, b, n, in_used, roll, tiles, upd, max_h, max_r, ctxs);
-                    if (rc != MPPI_OK) {
-                        for (const Inflight& f : b.reqs) {
-                            finish(s, f, rc, {});
-                            s->drones[f.drone].busy = false;
-                        }
-                        b.reqs.clear();
-                    } else {
-                        for (mppi_ctx* c : ctxs) ctx_batch_launched(c);
-                        b.busy = true;
-                        s->order.push_back(fb);
-                        ++s->batches;
-                    }
+                    b.busy = true;
+                    s->order.push_back(fb);
+                    launch_fb = fb;
+                    launch_n = n;
+                    l_roll = roll;
+                    l_tiles = tiles;
+                    l_upd = upd;
+                    l_max_h = max_h;
+                    l_max_r = max_r;
+                    l_in = in_used;
                     progress = true;
                 }
             }
             idle = s->queue.empty() && s->order.empty();
             if (idle && s->stop) break;
+        }
+        if (launch_fb >= 0) {
+            BatchBuf& b = s->buf[launch_fb];
+            const cudaError_t le = launch_batch(s, b, launch_n, l_in, l_roll, l_tiles, l_upd, l_max_h, l_max_r, ctxs);
+            std::lock_guard<std::mutex> lock(s->mu);
+            if (le != cudaSuccess) {
+                const int rc = sfail(s, MPPI_E_CUDA, "batch launch failed: %s", cudaGetErrorString(le));
+                for (const Inflight& f : b.reqs) {
+                    finish(s, f, rc, {});
+                    s->drones[f.drone].busy = false;
+                }
+                b.reqs.clear();
+                b.busy = false;
+                for (size_t oi = 0; oi < s->order.size(); ++oi)
+                    if (s->order[oi] == launch_fb) {
+                        s->order.erase(s->order.begin() + static_cast<long>(oi));
+                        break;
+                    }
+            } else {
+                for (mppi_ctx* c : ctxs) ctx_batch_launched(c);
+                ++s->batches;
+            }
         }
         if (idle)
             std::this_thread::sleep_for(std::chrono::microseconds(50));
