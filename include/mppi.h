@@ -503,6 +503,15 @@ int mppi_encoder_set_conv_path(mppi_encoder* enc, int path);
  * the stream itself failed.
  */
 int mppi_encoder_check(mppi_encoder* enc);
+/*
+ * Test hook for the tensor-core convolutions' failure path (no GPU fault is involved): in the
+ * next mppi_encode_depth, every CTA of the first convolution waits for a phase of its
+ * weight-copy barrier that never completes, gives up after its bounded wait (2 s of
+ * %globaltimer), sets the encoder's error word and returns; mppi_encoder_check then reports
+ * MPPI_E_TIMEOUT once and the encoder works normally again.  The latents of that call are
+ * unspecified.  Errors: MPPI_E_INVALID (NULL encoder, or the FP32 convolution path).
+ */
+int mppi_encoder_debug_inject_timeout(mppi_encoder* enc);
 
 /*
  * Copy the encoder's current weights to host arrays (same 10 arrays and layouts as

@@ -64,7 +64,8 @@ EXPORTS = [
     "mppi_train_read_points", "mppi_train_num_params",
     "mppi_depth_camera_default", "mppi_render_depth", "mppi_sample_sdf_queries",
     "mppi_encoder_create", "mppi_encoder_destroy", "mppi_encoder_last_error", "mppi_encode_depth",
-    "mppi_encoder_get_weights", "mppi_encoder_set_conv_path", "mppi_encoder_check", "mppi_encoder_train_create", "mppi_encoder_train_destroy",
+    "mppi_encoder_get_weights", "mppi_encoder_set_conv_path", "mppi_encoder_check",
+    "mppi_encoder_debug_inject_timeout", "mppi_encoder_train_create", "mppi_encoder_train_destroy",
     "mppi_encoder_train_last_error", "mppi_encoder_train_loss_grads", "mppi_encoder_train_step",
     "mppi_encoder_train_get_decoder", "mppi_encoder_train_set_sdf", "mppi_encoder_train_loss_grads_sdf",
     "mppi_encoder_train_step_sdf", "mppi_encoder_train_get_sdf_decoder",
@@ -189,6 +190,7 @@ _SIGS = {
     "mppi_encoder_get_weights": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
     "mppi_encoder_set_conv_path": (ctypes.c_int, [_vp, ctypes.c_int]),
     "mppi_encoder_check": (ctypes.c_int, [_vp]),
+    "mppi_encoder_debug_inject_timeout": (ctypes.c_int, [_vp]),
     "mppi_encoder_train_create": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_float, _vp, _vp, ctypes.POINTER(_vp)]),
     "mppi_encoder_train_destroy": (None, [_vp]),
     "mppi_encoder_train_last_error": (ctypes.c_char_p, [_vp]),
@@ -554,6 +556,10 @@ def mppi_encoder_set_conv_path(enc, path):
 
 def mppi_encoder_check(enc):
     return _echeck(load().mppi_encoder_check(enc), enc)
+
+
+def mppi_encoder_debug_inject_timeout(enc):
+    return _echeck(load().mppi_encoder_debug_inject_timeout(enc), enc)
 
 
 def mppi_encoder_get_weights(enc, layers_out):

@@ -20,6 +20,7 @@ struct mppi_encoder {
     int n_sms = 152;
     int conv_path = MPPI_ENC_CONV_TC;   // which convolution kernels mppi_encode_depth runs
     int* d_err = nullptr;               // device error word of the tensor-core kernels' bounded waits
+    int inject_timeout = 0;             // test hook: the next encoding's first convolution waits in vain
     uint8_t* wpack[4] = {nullptr, nullptr, nullptr, nullptr};  // conv weights, BF16 hi / lo operand stages
     uint8_t* dgpack[4] = {nullptr, nullptr, nullptr, nullptr}; // the same per parity class for input gradients (1..3)
     char err[512] = "";
@@ -36,8 +37,10 @@ size_t conv_tc_packed_bytes(int layer);
 size_t conv_dgrad_tc_packed_bytes(int layer);
 cudaError_t pack_conv_tc_weights(const float* const* wt, uint8_t* const* out, uint8_t* const* out_dgrad,
                                  cudaStream_t s);
+// inject != 0 (a test hook): the launch's first weight wait waits for a phase that never completes,
+// so every CTA gives up after its bounded wait and sets *err
 cudaError_t launch_conv_tc(int layer, const float* x, int n_img, int H, int W, int Ho, int Wo, const uint8_t* wpack,
-                           const float* b, float scale, float* y, int* err, cudaStream_t s);
+                           const float* b, float scale, float* y, int* err, int inject, cudaStream_t s);
 // weight gradient of layer 0..3 on the tensor cores: partial sums of `slices` pixel slices of
 // stages_per_slice x conv_wgrad_tc_stage_pixels() output pixels into ws[slice][c_out][9 c_in + 1]
 int conv_wgrad_tc_stage_pixels();

@@ -405,9 +405,11 @@ extern "C" int mppi_encode_depth(mppi_encoder* e, int n_images, const float* d_d
         const float* in = d_depth;
         for (int l = 0; l < 4 && ce == cudaSuccess; ++l) {
             ce = mppi::launch_conv_tc(l, in, n_images, e->h[l], e->w[l], e->h[l + 1], e->w[l + 1], e->wpack[l],
-                                      e->bias[l], l == 0 ? 1.f / max_range : 1.f, e->act[l], e->d_err, e->stream);
+                                      e->bias[l], l == 0 ? 1.f / max_range : 1.f, e->act[l], e->d_err,
+                                      l == 0 ? e->inject_timeout : 0, e->stream);
             in = e->act[l];
         }
+        e->inject_timeout = 0;
     } else {
         ce = launch_conv<1, 16, true>(e, 0, n_images, d_depth, 1.f / max_range, e->act[0]);
         if (ce == cudaSuccess) ce = launch_conv<16, 32, false>(e, 1, n_images, e->act[0], 1.f, e->act[1]);
@@ -444,5 +446,13 @@ extern "C" int mppi_encoder_check(mppi_encoder* e) {
         return efail(e, MPPI_E_TIMEOUT, "a tensor-core convolution gave up waiting for its MMAs (device error word %d)",
                      word);
     }
+    return MPPI_OK;
+}
+
+extern "C" int mppi_encoder_debug_inject_timeout(mppi_encoder* e) {
+    if (!e) return efail(nullptr, MPPI_E_INVALID, "mppi_encoder_debug_inject_timeout: NULL encoder");
+    if (e->conv_path != MPPI_ENC_CONV_TC)
+        return efail(e, MPPI_E_INVALID, "mppi_encoder_debug_inject_timeout: the FP32 convolutions have no device waits");
+    e->inject_timeout = 1;
     return MPPI_OK;
 }

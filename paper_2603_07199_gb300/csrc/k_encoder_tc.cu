@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kEtThreads) conv3x3s2_tc_kernel(const float* _
                                                                   int W, int Ho, int Wo,
                                                                   const uint8_t* __restrict__ wpack,
                                                                   const float* __restrict__ bias, float scale,
-                                                                  float* __restrict__ y, int* err) {
+                                                                  float* __restrict__ y, int* err, int inject) {
     using S = ConvTcShape<CI, CO, kSplit>;
     constexpr int KS = S::KS;
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -276,8 +276,10 @@ __global__ void __launch_bounds__(kEtThreads) conv3x3s2_tc_kernel(const float* _
         __syncthreads();
         if (tid == 0) {
             tc::fence_after_sync();
-            // the weights' bulk copy must have landed before the first MMA reads them
-            const bool go = sl > 0 || tc::mbar_wait_bounded(tc::smem_u32(bar_w), 0u, abort_flag, err, kDevErrTimeout);
+            // the weights' bulk copy must have landed before the first MMA reads them (a test hook
+            // waits for a phase that never completes instead, so that the bounded wait runs out)
+            const bool go = sl > 0 || tc::mbar_wait_bounded(tc::smem_u32(bar_w), inject ? 1u : 0u, abort_flag, err,
+                                                            kDevErrTimeout);
             if (!go) ok = false;   // every thread sees the flag it set at its next wait
             if (go) {
                 const uint32_t wb = bres + static_cast<uint32_t>(sl) * S::kBStage;
@@ -831,7 +833,7 @@ cudaError_t configure_one() {
 
 template <int CI, int CO, bool kScale, int kSplit>
 cudaError_t launch_one(const float* x, int n_img, int H, int W, int Ho, int Wo, const uint8_t* wt, const float* b,
-                       float scale, float* y, int* err, cudaStream_t s) {
+                       float scale, float* y, int* err, int inject, cudaStream_t s) {
     const long long P = static_cast<long long>(n_img) * Ho * Wo;
     const long long tiles = (P + kEtRows - 1) / kEtRows;
     cudaLaunchConfig_t cfg = {};
@@ -849,7 +851,7 @@ cudaError_t launch_one(const float* x, int n_img, int H, int W, int Ho, int Wo, 
     cfg.attrs = attr;
     cfg.numAttrs = kSplit > 1 ? 2 : 1;
     return cudaLaunchKernelEx(&cfg, conv3x3s2_tc_kernel<CI, CO, kScale, kSplit>, x, n_img, H, W, Ho, Wo, wt, b, scale,
-                              y, err);
+                              y, err, inject);
 }
 
 // reduction split of each layer: the deep layers with few output tiles use a cluster
@@ -914,12 +916,12 @@ cudaError_t configure_conv_tc() {
 }
 
 cudaError_t launch_conv_tc(int layer, const float* x, int n_img, int H, int W, int Ho, int Wo, const uint8_t* wt,
-                           const float* b, float scale, float* y, int* err, cudaStream_t s) {
+                           const float* b, float scale, float* y, int* err, int inject, cudaStream_t s) {
     switch (layer) {
-        case 0: return launch_one<1, 16, true, 1>(x, n_img, H, W, Ho, Wo, wt, b, scale, y, err, s);
-        case 1: return launch_one<16, 32, false, 1>(x, n_img, H, W, Ho, Wo, wt, b, scale, y, err, s);
-        case 2: return launch_one<32, 64, false, kSplit2>(x, n_img, H, W, Ho, Wo, wt, b, scale, y, err, s);
-        case 3: return launch_one<64, 64, false, kSplit3>(x, n_img, H, W, Ho, Wo, wt, b, scale, y, err, s);
+        case 0: return launch_one<1, 16, true, 1>(x, n_img, H, W, Ho, Wo, wt, b, scale, y, err, inject, s);
+        case 1: return launch_one<16, 32, false, 1>(x, n_img, H, W, Ho, Wo, wt, b, scale, y, err, inject, s);
+        case 2: return launch_one<32, 64, false, kSplit2>(x, n_img, H, W, Ho, Wo, wt, b, scale, y, err, inject, s);
+        case 3: return launch_one<64, 64, false, kSplit3>(x, n_img, H, W, Ho, Wo, wt, b, scale, y, err, inject, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -61,3 +61,40 @@ def test_barrier_timeout_through_the_async_path():
         assert torch.isfinite(U).all()
     finally:
         ctl.close()
+
+
+def test_encoder_tensor_core_wait_timeout_is_reported_and_recovers():
+    """The tensor-core convolutions' waits are bounded too: with the test hook, every CTA of the
+    next encoding's first convolution waits for a barrier phase that never completes, gives up
+    after 2 s, sets the encoder's error word and returns; mppi_encoder_check reports
+    MPPI_E_TIMEOUT once, and the next encoding equals one from before, bit for bit."""
+    import torch
+    layers = []
+    for Wm, b in W.encoder_weights(7):
+        layers += [np.ascontiguousarray(Wm, np.float32), np.ascontiguousarray(b, np.float32)]
+    rng = np.random.default_rng(3)
+    d = torch.from_numpy(rng.uniform(0.5, 9.5, (1, 120, 160)).astype(np.float32)).cuda()
+    z = torch.zeros(1, 64, device="cuda")
+    enc = B.mppi_encoder_create(120, 160, 1, layers)     # one image: the first layer is one wave of CTAs
+    try:
+        B.mppi_encode_depth(enc, 1, d, 10.0, z)
+        assert B.mppi_encoder_check(enc) == B.MPPI_OK
+        want = z.cpu().numpy().copy()
+        B.mppi_encoder_debug_inject_timeout(enc)
+        t0 = time.perf_counter()
+        B.mppi_encode_depth(enc, 1, d, 10.0, z)
+        with pytest.raises(B.MppiError) as e:
+            B.mppi_encoder_check(enc)
+        waited = time.perf_counter() - t0
+        assert e.value.code == B.MPPI_E_TIMEOUT, e.value
+        assert 1.5 < waited < 30.0, waited
+        assert B.mppi_encoder_check(enc) == B.MPPI_OK       # reported once
+        B.mppi_encode_depth(enc, 1, d, 10.0, z)
+        assert B.mppi_encoder_check(enc) == B.MPPI_OK
+        np.testing.assert_array_equal(z.cpu().numpy(), want)
+        B.mppi_encoder_set_conv_path(enc, B.MPPI_ENC_CONV_FP32)
+        with pytest.raises(B.MppiError) as e:
+            B.mppi_encoder_debug_inject_timeout(enc)
+        assert e.value.code == B.MPPI_E_INVALID
+    finally:
+        B.mppi_encoder_destroy(enc)
