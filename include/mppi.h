@@ -553,7 +553,8 @@ const char* mppi_encoder_train_last_error(const mppi_encoder_trainer* trainer);
  *   loss              host float out (nullable): mean |r|
  *   grads_out         12 host arrays (nullable; NULL entries skipped): dL/dW1, dL/db1, ..,
  *                     dL/dW4, dL/db4, dL/dW5, dL/db5 (encoder layouts), dL/dW_D, dL/db_D
- * Synchronous when loss or grads_out is given.
+ * Synchronous when loss or grads_out is given; a synchronous call reports MPPI_E_TIMEOUT (its
+ * results then unspecified) when a bounded wait of the tensor-core convolutions gave up.
  */
 int mppi_encoder_train_loss_grads(mppi_encoder_trainer* trainer, int n, const float* d_noisy, const float* d_clean,
                                   float max_range, float* loss, float* const* grads_out);

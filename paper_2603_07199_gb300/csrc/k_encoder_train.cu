@@ -863,6 +863,8 @@ struct Queries {
 
 // Forward, loss and every gradient of one batch.  losses (nullable, host): total, reconstruction
 // mean |r|, SDF mean |r| (0 without queries).
+int check_device_error(mppi_encoder_trainer* t);
+
 int loss_grads(mppi_encoder_trainer* t, int n, const float* d_noisy, const float* d_clean, float max_range,
                const Queries* q, float* losses) {
     mppi_encoder* e = t->enc;
@@ -931,6 +933,8 @@ int loss_grads(mppi_encoder_trainer* t, int n, const float* d_noisy, const float
             ce = cudaMemcpyAsync(t->h_loss2.data(), t->sdf_loss_img, n * sizeof(float), cudaMemcpyDeviceToHost, s);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
         if (ce != cudaSuccess) return tfail(t, MPPI_E_CUDA, "loss read-back failed: %s", cudaGetErrorString(ce));
+        const int rc = check_device_error(t);
+        if (rc != MPPI_OK) return rc;
         double rsum = 0.0, ssum = 0.0;
         for (int i = 0; i < n; ++i) {
             rsum += t->h_loss[i];
@@ -941,6 +945,23 @@ int loss_grads(mppi_encoder_trainer* t, int n, const float* d_noisy, const float
         losses[1] = static_cast<float>(l_rec);
         losses[2] = static_cast<float>(l_sdf);
     }
+    return MPPI_OK;
+}
+
+// After the trainer's work on the encoder's stream: MPPI_E_TIMEOUT (the word cleared) when a
+// bounded wait of a tensor-core convolution gave up since the last check.  Synchronous.
+int check_device_error(mppi_encoder_trainer* t) {
+    mppi_encoder* e = t->enc;
+    int word = 0;
+    cudaError_t ce = cudaMemcpyAsync(&word, e->d_err, sizeof(int), cudaMemcpyDeviceToHost, e->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
+    if (ce == cudaSuccess && word != 0) {
+        ce = cudaMemsetAsync(e->d_err, 0, sizeof(int), e->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
+        if (ce == cudaSuccess)
+            return tfail(t, MPPI_E_TIMEOUT, "a tensor-core convolution gave up waiting for its MMAs (word %d)", word);
+    }
+    if (ce != cudaSuccess) return tfail(t, MPPI_E_CUDA, "error-word read-back failed: %s", cudaGetErrorString(ce));
     return MPPI_OK;
 }
 
@@ -976,6 +997,8 @@ int adam_all(mppi_encoder_trainer* t, bool with_decoder) {
 }
 
 int read_grads(mppi_encoder_trainer* t, float* const* grads_out, bool with_decoder) {
+    const int rc = check_device_error(t);
+    if (rc != MPPI_OK) return rc;
     cudaError_t ce = cudaStreamSynchronize(t->enc->stream);
     for (int i = 0; i < mppi::kNumTensors && ce == cudaSuccess; ++i)
         if (grads_out[i])

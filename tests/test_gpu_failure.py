@@ -98,3 +98,30 @@ def test_encoder_tensor_core_wait_timeout_is_reported_and_recovers():
         assert e.value.code == B.MPPI_E_INVALID
     finally:
         B.mppi_encoder_destroy(enc)
+
+
+def test_encoder_trainer_reports_a_tensor_core_timeout():
+    """The trainer's forward pass is the encoder's: after the hook, a training step that reads its
+    loss reports MPPI_E_TIMEOUT (and applies no Adam step); the next step runs normally."""
+    import torch
+    layers = []
+    for Wm, b in W.encoder_weights(7):
+        layers += [np.ascontiguousarray(Wm, np.float32), np.ascontiguousarray(b, np.float32)]
+    rng = np.random.default_rng(4)
+    noisy = torch.from_numpy(rng.uniform(0.5, 9.5, (1, 48, 64)).astype(np.float32)).cuda()
+    clean = torch.from_numpy(rng.uniform(0.5, 9.5, (1, 48, 64)).astype(np.float32)).cuda()
+    enc = B.mppi_encoder_create(48, 64, 1, layers)
+    T = 6 * 8
+    tr = B.mppi_encoder_train_create(enc, 1, 1e-3, rng.normal(0, 0.1, (T, 64)).astype(np.float32),
+                                     np.zeros(T, np.float32))
+    try:
+        l0 = B.mppi_encoder_train_loss_grads(tr, 1, noisy, clean, 10.0)
+        B.mppi_encoder_debug_inject_timeout(enc)
+        with pytest.raises(B.MppiError) as e:
+            B.mppi_encoder_train_step(tr, 1, noisy, clean, 10.0)
+        assert e.value.code == B.MPPI_E_TIMEOUT, e.value
+        assert B.mppi_encoder_train_loss_grads(tr, 1, noisy, clean, 10.0) == l0   # no update was applied
+        assert np.isfinite(B.mppi_encoder_train_step(tr, 1, noisy, clean, 10.0))
+    finally:
+        B.mppi_encoder_train_destroy(tr)
+        B.mppi_encoder_destroy(enc)
