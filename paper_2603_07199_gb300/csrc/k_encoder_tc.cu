@@ -1,30 +1,31 @@
 // Depth-encoder convolutions (Sec. III-B, the convolutional reading of E_theta stated in
-// include/mppi.h) on the Blackwell tensor cores.
+// include/mppi.h) on the Blackwell tensor cores: the forward pass (conv3x3s2_tc_kernel), the
+// weight gradients (conv_wgrad_tc_kernel) and the input gradients (conv_dgrad_tc_kernel) of the
+// encoder's training.  Every contraction runs as tcgen05.mma kind::f16 on BF16 operand splits:
+// each FP32 value v is stored as v_hi = bf16(v) and v_lo = bf16(v - v_hi), and per 16-deep slice
+// one thread issues the three products A_hi B_hi + A_hi B_lo + A_lo B_hi into an FP32 TMEM
+// accumulator (the dropped A_lo B_lo and the split's own rounding are ~2^-16 of each product:
+// the accuracy of the FP32 path's reading of the encoder).  Operands are K-major, no swizzle,
+// in 8 x 16-byte core matrices (stage_offset).
 //
-// One 3x3 stride-2 convolution is the GEMM  Y[p][co] = sum_k X[p][k] W'[co][k]  over the output
-// pixels p = (image, i, j) and the reduction index k = t CI + ci, tap-major (t = 3 ky + kx), so
-// that for CI >= 8 every 8 consecutive k share one tap: X[p][k] = x[ci][2i + ky - 1][2j + kx - 1]
-// (zero outside the image) is gathered on the fly from the NCHW input at one precomputed offset
-// per tap, and W'[co][k] = W[co][ci][ky][kx] from the weights as given.  A CTA owns 128
-// consecutive output pixels (M = 128, one TMEM lane each) and all CO channels (N = CO, an FP32
-// accumulator of CO TMEM columns); two threads share each pixel row, each gathering half of a
-// stage's KS reduction columns.  The reduction runs in stages through two shared-memory
-// buffers: every thread first issues all its loads of the stage (inputs and a share of the
-// weights), then waits until the MMAs two stages back are done with the buffer, splits each value
-// v into BF16 v_hi + v_lo (v_lo = bf16(v - v_hi)), stores both halves in the K-major operand
-// layout, and thread 0 issues, per 16-deep slice, the three products X_hi W_hi + X_hi W_lo +
-// X_lo W_hi into the accumulator (the dropped X_lo W_lo and the split's own rounding are ~2^-16
-// of each product, the accuracy of the FP32 path's reading of the encoder) and commits them to
+// Forward: Y[p][co] = sum_k X[p][k] W'[co][k] over the output pixels p = (image, i, j) and the
+// reduction index k = t CI + ci, tap-major (t = 3 ky + kx), so that for CI >= 8 every 8
+// consecutive k share one tap: X[p][k] = x[ci][2i + ky - 1][2j + kx - 1] (zero outside the image)
+// is gathered on the fly from the NCHW input at one precomputed offset per tap, W'[co][k] =
+// W[co][ci][ky][kx] comes from the weights' packed hi / lo stages (pack_conv_weights_kernel,
+// refreshed whenever the weights change) by one bulk copy per CTA.  A CTA owns 128 consecutive
+// output pixels (M = 128, one TMEM lane each) and all CO channels (N = CO); two threads share
+// each pixel row, each gathering half of a stage's KS columns; two stage buffers, the next
+// stage's loads in flight while the current one is stored and its MMAs issued and committed to
 // the buffer's mbarrier.  Layers with few output tiles split their stages over the kSplit CTAs
-// of a thread-block cluster: each leaves its partial accumulator in its shared memory and, after
-// a cluster barrier, sums a 1 / kSplit share of the tile over the partials in rank order through
-// distributed shared memory.  The epilogue adds the bias, applies the ReLU and writes NCHW FP32
-// (the activations the head and the trainer read); a warp's stores of one channel are 32
-// consecutive pixels.
+// of a thread-block cluster, whose partial accumulators meet through distributed shared memory
+// in rank order.  The epilogue adds the bias, applies the ReLU and writes NCHW FP32 (the
+// activations the head and the trainer read); a warp's stores of one channel are 32 consecutive
+// pixels.
 //
-// Every wait is bounded (tc::kWaitLimitNs of %globaltimer): on timeout the kernel sets
-// *err = kDevErrTimeout, lets its issued MMAs finish, still takes part in every cluster barrier,
-// frees TMEM and returns.
+// Every wait is bounded (tc::kWaitLimitNs of %globaltimer): on timeout a kernel sets
+// *err = kDevErrTimeout, lets its issued MMAs and copies finish, still takes part in every
+// cluster barrier, frees TMEM and returns.
 #include <cooperative_groups.h>
 
 #include "encoder_internal.h"
