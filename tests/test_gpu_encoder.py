@@ -168,3 +168,14 @@ def test_render_then_encode_pipeline():
     err = np.abs(got - want)
     print("render+encode max err", float(err.max()))
     assert np.all(err <= 1e-2 * (1.0 + np.abs(want)))
+
+
+@pytest.mark.parametrize("path", ["tc", "fp32"])
+def test_encoder_parity_full_resolution(path):
+    """The renderer's full 640 x 480 views (2,400 output tiles of the first layer per image pair,
+    320 x 240 .. 40 x 30 activations): every convolution path against the FP64 encoder."""
+    layers = W.encoder_weights(7)
+    kw = dict(width=640, height=480, fx=385.0, fy=385.0, cx=320.0, cy=240.0, max_range=10.0)
+    imgs = _views(2, kw, seed=12)
+    got = _encode(layers, imgs, 10.0, path=path)
+    print("encoder", path, "640 x 480 max err", _check(got, E.encode(imgs, 10.0, layers)))
