@@ -70,11 +70,14 @@ def _shapes(enc_layers, dec):
 
 
 @pytest.mark.parametrize("path", ["tc", "fp32"])
-def test_gradients_match_oracle(path):
-    torch, enc, tr, enc_layers, dec, noisy, clean = _setup(37, 53, 3, 4, path)
+@pytest.mark.parametrize("h,w,n", [(37, 53, 3), (5, 7, 2), (2, 3, 2), (1, 1, 2)])
+def test_gradients_match_oracle(path, h, w, n):
+    """Ragged and degenerate sizes too: 1 x 1 images leave every layer 1 x 1 (three of the input
+    gradients' four parity classes empty), 2 x 3 and 5 x 7 odd edges."""
+    torch, enc, tr, enc_layers, dec, noisy, clean = _setup(h, w, n, 4, path)
     try:
         grads = [np.zeros(s, np.float32) for s in _shapes(enc_layers, dec)]
-        loss = B.mppi_encoder_train_loss_grads(tr, 3, torch.from_numpy(noisy).cuda(),
+        loss = B.mppi_encoder_train_loss_grads(tr, n, torch.from_numpy(noisy).cuda(),
                                                torch.from_numpy(clean).cuda(), 10.0, grads)
     finally:
         B.mppi_encoder_train_destroy(tr)
