@@ -8,6 +8,8 @@ a negative status raises MppiError with the library's message.
 import ctypes
 import os
 
+from numpy import ndarray as _np_ndarray
+
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libmppi_gb300.so")
 
@@ -229,8 +231,15 @@ def load(path=LIB_PATH):
 
 
 def _ptr(x):
+    """Address of a buffer: None, an int, a NumPy array (C-contiguous) or a tensor with
+    data_ptr() (contiguous).  NumPy arrays are tested first by type: a host-buffer step passes
+    two of them per call, and the attribute probes cost more than the call's own marshalling."""
     if x is None:
         return None
+    if type(x) is _np_ndarray:
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
     if isinstance(x, int):
         return x
     if hasattr(x, "data_ptr"):
