@@ -468,21 +468,38 @@ __global__ void __launch_bounds__(kEtThreads) conv_wgrad_tc_kernel(const float* 
             const int ky = t / 3, kx = t - 3 * (t / 3);
             PixCursor pc;
             pc.start(p0 + 8 * c, hw, Wo);
+            if (k < 9 * CI && pc.j + 8 <= Wo && p0 + 8 * c + 7 < P) {
+                // the chunk's eight pixels lie in one output row: one input row, columns 2 apart
+                const int yy = 2 * pc.i + ky - 1, xx0 = 2 * pc.j + kx - 1;
+                const bool row_ok = yy >= 0 && yy < H;
+                const float* src = x + (static_cast<size_t>(pc.n) * CI + ci) * plane + static_cast<size_t>(row_ok ? yy : 0) * W;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const bool live = p0 + 8 * c + q < P;
-                float v = 0.f;
-                if (live && k < 9 * CI) {
-                    const int yy = 2 * pc.i + ky - 1, xx = 2 * pc.j + kx - 1;
-                    if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
-                        v = __ldg(x + (static_cast<size_t>(pc.n) * CI + ci) * plane + static_cast<size_t>(yy) * W + xx);
+                for (int q = 0; q < 8; ++q) {
+                    const int xx = xx0 + 2 * q;
+                    float v = 0.f;
+                    if (row_ok && xx >= 0 && xx < W) {
+                        v = __ldg(src + xx);
                         if (kScale) v *= scale;
                     }
-                } else if (live && k == 9 * CI) {
-                    v = 1.f;
+                    xv[u][q] = v;
                 }
-                xv[u][q] = v;
-                pc.next(Ho, Wo);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const bool live = p0 + 8 * c + q < P;
+                    float v = 0.f;
+                    if (live && k < 9 * CI) {
+                        const int yy = 2 * pc.i + ky - 1, xx = 2 * pc.j + kx - 1;
+                        if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+                            v = __ldg(x + (static_cast<size_t>(pc.n) * CI + ci) * plane + static_cast<size_t>(yy) * W + xx);
+                            if (kScale) v *= scale;
+                        }
+                    } else if (live && k == 9 * CI) {
+                        v = 1.f;
+                    }
+                    xv[u][q] = v;
+                    pc.next(Ho, Wo);
+                }
             }
         }
 #pragma unroll
@@ -491,13 +508,20 @@ __global__ void __launch_bounds__(kEtThreads) conv_wgrad_tc_kernel(const float* 
             const int co = (task & 7) + 8 * ((task >> 3) % (CO / 8)), c = task / CO;
             PixCursor pc;
             pc.start(p0 + 8 * c, hw, Wo);
+            if (task < CO * kWgStage / 8 && pc.j + 8 <= Wo && p0 + 8 * c + 7 < P) {
+                // eight consecutive pixels of one output row: contiguous
+                const float* src = delta + (static_cast<size_t>(pc.n) * CO + co) * hw + pc.i * Wo + pc.j;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                float v = 0.f;
-                if (task < CO * kWgStage / 8 && p0 + 8 * c + q < P)
-                    v = __ldg(delta + (static_cast<size_t>(pc.n) * CO + co) * hw + pc.i * Wo + pc.j);
-                dv[u][q] = v;
-                pc.next(Ho, Wo);
+                for (int q = 0; q < 8; ++q) dv[u][q] = __ldg(src + q);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    float v = 0.f;
+                    if (task < CO * kWgStage / 8 && p0 + 8 * c + q < P)
+                        v = __ldg(delta + (static_cast<size_t>(pc.n) * CO + co) * hw + pc.i * Wo + pc.j);
+                    dv[u][q] = v;
+                    pc.next(Ho, Wo);
+                }
             }
         }
     };
