@@ -269,9 +269,15 @@ int mppi_read_buffer(mppi_ctx* ctx, int which, float* host_out, size_t n);
  *                        folds the safety cost of Eq. 8 over each rollout's states in its
  *                        epilogue (Eq. 9-10) and writes only K x (floor((H + 126) / 128) + 1)
  *                        partial sums; the step's results are bit-identical either way.
+ *   MPPI_DIAG_SDF_SINGLE_CTA  the BF16 / FP16 SDF MLP kernel (without positional encoding) runs
+ *                        in its single-CTA form (three tiles of 128 states in flight per SM, the
+ *                        whole hidden weights in every CTA) instead of the default CTA-pair form
+ *                        (clusters of two CTAs issuing 256-row tcgen05 MMAs, each CTA holding half
+ *                        of every hidden weight matrix and four tiles in flight); for comparisons.
  * Errors: MPPI_E_INVALID (unknown bit).
  */
 #define MPPI_DIAG_STORE_SDF 1
+#define MPPI_DIAG_SDF_SINGLE_CTA 2
 int mppi_set_diagnostics(mppi_ctx* ctx, int flags);
 
 /*

@@ -43,6 +43,7 @@ MPPI_BUF_SDF = 3
 MPPI_BUF_WEIGHTS = 4
 MPPI_BUF_COSTS = 5
 MPPI_DIAG_STORE_SDF = 1
+MPPI_DIAG_SDF_SINGLE_CTA = 2
 MPPI_LATENT_DIM = 64
 MPPI_HIDDEN = 128
 MPPI_TRAIN_GEMM_FP32 = 0

@@ -44,6 +44,7 @@ struct StepParams {
     float3 J, inv_J;       // diagonal inertia and its reciprocal
     int pe;                // positional-encoding levels of the decoder's query point
     int store_sdf;         // the SDF kernels also store s(p) of every rollout state (diagnostics)
+    int sdf_pair;          // host side: 16-bit SDF MLP kernel in its CTA-pair form (else one CTA per tile group set)
 };
 
 // Device buffers of one controller.

@@ -35,11 +35,9 @@ namespace mppi {
 
 namespace {
 
-constexpr int kGroups = 3;                          // tile groups (tiles in flight per CTA)
 constexpr int kGroupWarps = 8;                      // 4 (one warp per TMEM lane quadrant) or 8 (two)
 constexpr int kGroupThreads = kGroupWarps * 32;
 constexpr int kHalves = kGroupWarps / 4;            // column slices per row
-constexpr int kThreads = kGroups * kGroupThreads;
 constexpr int kHalf = kHidden / kHalves;            // accumulator columns per thread
 constexpr uint32_t kTileBytes = kHidden * kHidden * 2;     // one 128 x 128 BF16 operand
 constexpr uint32_t kTmemCols = 512;
@@ -50,14 +48,31 @@ constexpr uint32_t kSlabBytes = kHidden * 16 * 2;
 constexpr uint32_t kIdescFull = tc::idesc_bf16_f32(128, 128);
 constexpr uint32_t kIdescFullF16 = tc::idesc_f16_f32(128, 128);
 constexpr uint32_t kIdescE4M3 = tc::idesc_e4m3_f32(128, 128);
+constexpr uint32_t kIdescPair = tc::idesc_bf16_f32(256, 128);
+constexpr uint32_t kIdescPairF16 = tc::idesc_f16_f32(256, 128);
 
+// The two forms of the kernel:
+//   single CTA: 3 tile groups (768 threads), W2..W4 whole in every CTA (96 KB);
+//   CTA pair (cta_group::2, a cluster of 2): M = 256 MMAs whose B operand (N = 128) is split
+//   between the two CTAs (64 weight rows each, 48 KB), which leaves room for 4 tile groups
+//   (1024 threads, 4 A tiles of 32 KB, the 512 TMEM columns as 4 accumulators).
+template <bool kPair>
+struct Form {
+    static constexpr int kGroups = kPair ? 4 : 3;                     // tiles in flight per CTA
+    static constexpr int kThreads = kGroups * kGroupThreads;
+    static constexpr uint32_t kWBytes = kPair ? kTileBytes / 2 : kTileBytes;   // this CTA's part of W2..W4
+};
+
+template <bool kPair>
 struct __align__(16) TcShared {
-    uint8_t w[3][kTileBytes];                 // W2, W3, W4 (B operands, N = out, K = in)
+    static constexpr int kGroups = Form<kPair>::kGroups;
+    uint8_t w[3][Form<kPair>::kWBytes];       // W2, W3, W4 (B operands, N = out, K = in; a pair: this CTA's 64 rows)
     uint8_t a[kGroups][kTileBytes];           // activation tiles (A operands, M = rows, K = features)
     // layer-1 B operand and, without positional encoding, the bias operands of the hidden GEMMs:
     //   [0, 4 KB)   layer-1 B: c W1[:, 0:3] split hi/lo (BF16, K = 16)
     //   [4, 8 KB)   K = 16 A operand with columns 0, 1 = 1 (16-bit hidden paths)
     //   [8, 20 KB)  three K = 16 B operands: columns 0, 1 = hi, lo of c b2, c b3, c b4
+    // (a pair holds the first half of each B operand: its 64 of the 128 rows)
     // with positional encoding: [0, 16 KB) layer-1 B with K = 16 .. 64 (the PE columns in BF16)
     uint8_t l1[kL1Bytes];
     float b1[kMaxGates][kHidden];             // c (per-gate first-layer bias)
@@ -66,6 +81,8 @@ struct __align__(16) TcShared {
     float part[kGroups][kTileRows];           // output-layer partial sums of the upper column half
     float pose[kMaxGates][8];
     uint64_t acc_full[kGroups];               // MMA -> epilogue: accumulator ready
+    uint64_t a_ready[kGroups];                // pair, even CTA: the odd CTA's group has written its A tile
+    uint64_t done;                            // pair: the other CTA has left its tile loop
     uint32_t tmem_base;
     int abort_flag;
 };
@@ -263,12 +280,27 @@ struct BatchRef {
     int* err;
 };
 
-template <int kFmt, bool kPE, bool kBatch>
-__global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, StepBuffers B, MlpWeights W,
-                                                                 BatchRef R) {
+template <int kFmt, bool kPE, bool kBatch, bool kPair = false>
+__global__ void __launch_bounds__(Form<kPair>::kThreads, 1) sdf_mlp_tc_kernel(StepParams P, StepBuffers B,
+                                                                              MlpWeights W, BatchRef R) {
     constexpr bool kF16 = (kFmt == kFmtFP16);
     constexpr bool kF8 = (kFmt == kFmtE4M3);
     constexpr bool kFold = !kF8 && !kPE;           // hidden biases ride in the GEMM (bias operands)
+    static_assert(!kPair || (kFold && !kBatch), "the CTA-pair form covers the 16-bit one-controller kernels");
+    constexpr int kGroups = Form<kPair>::kGroups;
+    constexpr int kThreads = Form<kPair>::kThreads;
+    using TcShared = mppi::TcShared<kPair>;
+    // accumulator columns per TMEM load in the epilogue: 16 in the pair form (1024 threads, at
+    // most 64 registers each), 32 otherwise
+    constexpr int kChunk = kPair ? 16 : 32;
+    auto tmem_ld_chunk = [](uint32_t taddr, uint32_t (&v)[kChunk]) {
+        if constexpr (kChunk == 8)
+            tc::tmem_ld_32x32b_x8(taddr, v);
+        else if constexpr (kChunk == 16)
+            tc::tmem_ld_32x32b_x16(taddr, v);
+        else
+            tc::tmem_ld_32x32b_x32(taddr, v);
+    };
     // the kernel has no static shared memory, so the dynamic block starts at the
     // (1024-byte aligned) base of the CTA's window; indexing it directly keeps the
     // shared address space visible to the compiler (no generic loads)
@@ -281,39 +313,59 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
     const int G = kBatch ? 0 : P.G;
     int* const errw = kBatch ? R.err : B.err;
 
+    // CTA pair: this CTA's rank (0 = the even CTA, which issues the pair's MMAs)
+    const uint32_t rank = kPair ? tc::cluster_ctarank() : 0u;
+
     // ---- set-up: TMEM, barriers, resident weights
     if (warp == 0) {
-        tc::tmem_alloc(tc::smem_u32(&S.tmem_base), kTmemCols);
-        tc::tmem_relinquish();
+        if constexpr (kPair) {
+            tc::tmem_alloc_pair(tc::smem_u32(&S.tmem_base), kTmemCols);
+            tc::tmem_relinquish_pair();
+        } else {
+            tc::tmem_alloc(tc::smem_u32(&S.tmem_base), kTmemCols);
+            tc::tmem_relinquish();
+        }
     }
     if (tid == 0) {
         for (int i = 0; i < kGroups; ++i) tc::mbar_init(tc::smem_u32(&S.acc_full[i]), 1);
+        if constexpr (kPair) {
+            for (int i = 0; i < kGroups; ++i) tc::mbar_init(tc::smem_u32(&S.a_ready[i]), 1);
+            tc::mbar_init(tc::smem_u32(&S.done), 1);
+        }
         S.abort_flag = 0;
         tc::mbar_fence_init();
     }
     for (int l = 0; l < 3; ++l) {
+        // a pair: rows [64 rank, 64 rank + 64) of the N = 128 operand, i.e. the rank-th half of
+        // its bytes (core-matrix rows are the slowest dimension of the layout)
         const uint4* src = reinterpret_cast<const uint4*>(kF8 ? static_cast<const void*>(W.W8[l])
                                                           : kF16 ? static_cast<const void*>(W.Wh[l])
-                                                                 : static_cast<const void*>(W.Wbf[l]));
+                                                                 : static_cast<const void*>(W.Wbf[l])) +
+                           rank * (Form<kPair>::kWBytes / 16);
         uint4* dst = reinterpret_cast<uint4*>(S.w[l]);
-        const int n16 = int((kF8 ? kTileBytes / 2 : kTileBytes) / 16);
+        const int n16 = int((kF8 ? kTileBytes / 2 : Form<kPair>::kWBytes) / 16);
         for (int i = tid; i < n16; i += kThreads) dst[i] = __ldg(src + i);
     }
     const float cl2 = P.beta * 1.4426950408889634f;          // beta log2(e)
-    // layer-1 B operand: K = k1 columns (SBO k1 / 8 core matrices of 128 B)
+    // layer-1 B operand: K = k1 columns (SBO k1 / 8 core matrices of 128 B); a pair: this CTA's half
     const int k1 = kPE ? layer1_gemm_k(P.pe) : 16;
-    for (int i = tid; i < k1 * kHidden * 2 / 16; i += kThreads)
-        reinterpret_cast<uint4*>(S.l1)[i] = __ldg(reinterpret_cast<const uint4*>(W.W1tc) + i);
+    {
+        const int n16 = k1 * kHidden * 2 / 16 / (kPair ? 2 : 1);
+        for (int i = tid; i < n16; i += kThreads)
+            reinterpret_cast<uint4*>(S.l1)[i] = __ldg(reinterpret_cast<const uint4*>(W.W1tc) + rank * n16 + i);
+    }
     for (int i = tid; i < 3 * kHidden; i += kThreads) {
         const int j = i / kHidden, n = i - j * kHidden;
         const float b = cl2 * W.b[j][n];
         S.bias[j][n] = b;
-        if constexpr (kFold) {
+        const int nl = n - static_cast<int>(rank) * (kHidden / 2);      // a pair: this CTA's rows
+        if (kFold && (!kPair || (nl >= 0 && nl < kHidden / 2))) {
+            const int nb = kPair ? nl : n;
             // bias row n of layer j as the K = 16 operand row [hi, lo, 0, ..., 0]
             const uint16_t hi = to_operand16<kFmt>(b);
             const uint16_t lo = to_operand16<kFmt>(b - from_operand16<kFmt>(hi));
             uint8_t* slab = S.l1 + kSlabOff + j * kSlabBytes;
-            const uint32_t off = static_cast<uint32_t>((n >> 3) * 256 + (n & 7) * 16);
+            const uint32_t off = static_cast<uint32_t>((nb >> 3) * 256 + (nb & 7) * 16);
             *reinterpret_cast<uint4*>(slab + off) = make_uint4(static_cast<uint32_t>(hi) | (static_cast<uint32_t>(lo) << 16), 0u, 0u, 0u);
             *reinterpret_cast<uint4*>(slab + off + 128) = make_uint4(0u, 0u, 0u, 0u);
         }
@@ -331,7 +383,10 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
     for (int i = tid; i < G * 8; i += kThreads) S.pose[i / 8][i % 8] = B.poses[i];
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
-    __syncthreads();
+    if constexpr (kPair)
+        tc::cluster_sync();     // both CTAs' barriers initialised before either arrives on the other's
+    else
+        __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem_base = S.tmem_base;
     // everything above only reads weights and gate data set before the step; the
@@ -353,8 +408,13 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
     }
     int n_rows = P.K * P.H;
     const int n_tiles = kBatch ? R.tiles : (n_rows + kTileRows - 1) / kTileRows;
-    const int nslots = gridDim.x * kGroups;
-    const int slot = blockIdx.x + static_cast<int>(gridDim.x) * (warp / kGroupWarps);
+    // a pair takes work units of two consecutive tiles (256 rows), the even CTA the first; the
+    // odd CTA's tile of the last unit may lie beyond the array (no valid rows)
+    const int n_units = kPair ? (n_tiles + 1) / 2 : n_tiles;
+    const int n_ctas = kPair ? static_cast<int>(gridDim.x) / 2 : static_cast<int>(gridDim.x);
+    const int nslots = n_ctas * kGroups;
+    const int slot = (kPair ? static_cast<int>(blockIdx.x) / 2 : static_cast<int>(blockIdx.x)) + n_ctas * (warp / kGroupWarps);
+    auto tile_of = [&](int unit) { return kPair ? 2 * unit + static_cast<int>(rank) : unit; };
     volatile int* abort_flag = &S.abort_flag;
 
     const int grp = warp / kGroupWarps;
@@ -372,18 +432,34 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
     uint32_t acc_phase = 0;
     int outstanding = 0;                                          // leader: commits not yet waited for
     bool ok = true;
+    // a pair: the even CTA's group waits on its a_ready barrier for the odd CTA's group, which
+    // arrives on it remotely
+    const uint32_t ready_bar = tc::smem_u32(&S.a_ready[grp]);
+    uint32_t ready_phase = 0;
 
+    // one K = 16 slice (kind::f16): one CTA's M = 128, or the pair's M = 256
+    auto mma16 = [&](uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+        if constexpr (kPair)
+            tc::mma_f16_pair(d, a, b, idesc, acc);
+        else
+            tc::mma_bf16(d, a, b, idesc, acc);
+    };
     // The group's leader issues GEMM l (0: layer 1, 1..3: layers 2..4) once the whole
-    // group has written its A tile (named barrier + proxy fences on every writer).
+    // group has written its A tile (named barrier + proxy fences on every writer); a pair's
+    // even CTA also waits (bounded) for the odd CTA's group to have written its A tile.
     auto issue = [&](int l) {
+        if constexpr (kPair) {
+            if (!tc::mbar_wait_bounded(ready_bar, ready_phase, abort_flag, errw, kDevErrTimeout)) return;
+            ready_phase ^= 1u;
+        }
         tc::fence_after_sync();
         const uint64_t ad = tc::smem_desc(a_base, 128, 2048);
         if (l == 0) {
             // layer 1: K = k1 (hi/lo split point x weights, then the PE columns), always BF16
             const uint64_t b1d = tc::smem_desc(tc::smem_u32(S.l1), 128, static_cast<uint32_t>(k1 / 8 * 128));
             for (int s = 0; s < k1 / 16; ++s)
-                tc::mma_bf16(d_tmem, ad + static_cast<uint64_t>(s * 16), b1d + static_cast<uint64_t>(s * 16), kIdescFull,
-                             s > 0 ? 1u : 0u);
+                mma16(d_tmem, ad + static_cast<uint64_t>(s * 16), b1d + static_cast<uint64_t>(s * 16),
+                      kPair ? kIdescPair : kIdescFull, s > 0 ? 1u : 0u);
         } else if constexpr (kF8) {
             // E4M3 x E4M3 -> FP32, K = 32 per instruction (256 B along K), SBO 1024 B
             const uint64_t a8 = tc::smem_desc(a_base, 128, 1024);
@@ -393,20 +469,31 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                 tc::mma_e4m3(d_tmem, a8 + static_cast<uint64_t>(s * 16), bd + static_cast<uint64_t>(s * 16), kIdescE4M3,
                              s > 0 ? 1u : 0u);
         } else {
-            const uint32_t idesc = kF16 ? kIdescFullF16 : kIdescFull;
+            const uint32_t idesc = kPair ? (kF16 ? kIdescPairF16 : kIdescPair) : (kF16 ? kIdescFullF16 : kIdescFull);
             const uint64_t bd = tc::smem_desc(tc::smem_u32(S.w[l - 1]), 128, 2048);
 #pragma unroll
             for (int s = 0; s < kHidden / 16; ++s)   // K = 16 per instruction: 256 B along K
-                tc::mma_bf16(d_tmem, ad + static_cast<uint64_t>(s * 16), bd + static_cast<uint64_t>(s * 16), idesc,
-                             s > 0 ? 1u : 0u);
+                mma16(d_tmem, ad + static_cast<uint64_t>(s * 16), bd + static_cast<uint64_t>(s * 16), idesc,
+                      s > 0 ? 1u : 0u);
             if constexpr (kFold) {
                 // + bias: ones (M x 16) against [hi, lo, 0..] (N x 16)
-                tc::mma_bf16(d_tmem, tc::smem_desc(tc::smem_u32(S.l1 + kOnesOff), 128, 256),
-                             tc::smem_desc(tc::smem_u32(S.l1 + kSlabOff + (l - 1) * kSlabBytes), 128, 256), idesc, 1u);
+                mma16(d_tmem, tc::smem_desc(tc::smem_u32(S.l1 + kOnesOff), 128, 256),
+                      tc::smem_desc(tc::smem_u32(S.l1 + kSlabOff + (l - 1) * kSlabBytes), 128, 256), idesc, 1u);
             }
         }
-        tc::mma_commit(acc_bar);
+        if constexpr (kPair)
+            tc::mma_commit_pair(acc_bar);     // arrives on acc_full[grp] of both CTAs
+        else
+            tc::mma_commit(acc_bar);
         ++outstanding;
+    };
+    // the group's A tile is written: issue (one CTA, a pair's even CTA) or tell the even CTA
+    auto a_tile_written = [&](int l) {
+        if (!leader) return;
+        if (kPair && rank != 0)
+            tc::mbar_arrive_remote(tc::mapa_shared(ready_bar, 0));
+        else
+            issue(l);
     };
 
     // batched launches: c b1'_g of the tile's controller from global memory (the product the
@@ -421,8 +508,9 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
     const BatchSlot* sl = kBatch ? R.slots : nullptr;
     // one-controller launches: the next tile's position is loaded while this tile runs
     float4 p_next = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (!kBatch && slot < n_tiles) p_next = B.pos[min(slot * kTileRows + row, n_rows - 1)];
-    for (int tile = slot; tile < n_tiles && ok; tile += nslots) {
+    if (!kBatch && slot < n_units) p_next = B.pos[min(tile_of(slot) * kTileRows + row, n_rows - 1)];
+    for (int unit = slot; unit < n_units && ok; unit += nslots) {
+        const int tile = tile_of(unit);
         ltile = tile;
         if constexpr (kBatch) {
             while (cur + 1 < R.n && R.slots[cur + 1].tile0 <= tile) ++cur;
@@ -447,7 +535,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
             p = sl->B.pos[min(r, n_rows - 1)];
         } else {
             p = p_next;
-            if (tile + nslots < n_tiles) p_next = B.pos[min((tile + nslots) * kTileRows + row, n_rows - 1)];
+            if (unit + nslots < n_units) p_next = B.pos[min(tile_of(unit + nslots) * kTileRows + row, n_rows - 1)];
         }
         float smin = __int_as_float(0x7f800000);
         for (int g = g_lo; g < g_hi && ok; ++g) {
@@ -491,7 +579,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
             tc::fence_proxy_async_smem();
             tc::fence_before_sync();
             tc::named_barrier(bar_id, kGroupThreads);
-            if (leader) issue(0);
+            a_tile_written(0);
 
             for (int l = 0; l < 4; ++l) {
                 // every thread of the group agrees on the outcome before going on, so a
@@ -510,9 +598,9 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                 uint64_t s2 = pk(0.f, 0.f);
                 if (active) {
 #pragma unroll 1
-                    for (int ch = 0; ch < kHalf; ch += 32) {
-                        uint32_t v[32];
-                        tc::tmem_ld_32x32b_x32(t_row + static_cast<uint32_t>(ch), v);
+                    for (int ch = 0; ch < kHalf; ch += kChunk) {
+                        uint32_t v[kChunk];
+                        tmem_ld_chunk(t_row + static_cast<uint32_t>(ch), v);
                         tc::tmem_wait_ld();
                         const int cc = col0 + ch;
                         if (kF8 && l < 3) {
@@ -522,7 +610,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                             const uint64_t dq2 = pk(dq, dq);
                             const uint32_t isa = f32x2_to_f16x2(W.f8_inv_act[l], W.f8_inv_act[l]);
 #pragma unroll
-                            for (int j = 0; j < 32; j += 16) {
+                            for (int j = 0; j < kChunk; j += 16) {
                                 uint32_t q[4];
 #pragma unroll
                                 for (int t = 0; t < 4; ++t) {
@@ -542,7 +630,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                             // layer 1: + the gate's first-layer bias
                             const float* bias = S.b1[kBatch ? 0 : g];
 #pragma unroll
-                            for (int j = 0; j < 32; j += 8) {
+                            for (int j = 0; j < kChunk; j += 8) {
                                 const float4 b0 = kBatch ? b1_4(sl->B.b1p, g, cc + j) : *reinterpret_cast<const float4*>(bias + cc + j);
                                 const float4 b1 = kBatch ? b1_4(sl->B.b1p, g, cc + j + 4)
                                                          : *reinterpret_cast<const float4*>(bias + cc + j + 4);
@@ -556,7 +644,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                         } else if (l < 3 && kFold) {
                             // hidden layers 2, 3: the bias is already in the accumulator
 #pragma unroll
-                            for (int j = 0; j < 32; j += 8) {
+                            for (int j = 0; j < kChunk; j += 8) {
                                 tc::st_shared_v4(a_base + tc::operand_offset_bytes(row, cc + j),
                                                  act_pair<kFmt>(pk(__uint_as_float(v[j]), __uint_as_float(v[j + 1]))),
                                                  act_pair<kFmt>(pk(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]))),
@@ -567,7 +655,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                             // hidden layers 2, 3 (positional-encoding form): + the layer's bias
                             const float* bias = S.bias[l - 1];
 #pragma unroll
-                            for (int j = 0; j < 32; j += 8) {
+                            for (int j = 0; j < kChunk; j += 8) {
                                 const float4 b0 = *reinterpret_cast<const float4*>(bias + cc + j);
                                 const float4 b1 = *reinterpret_cast<const float4*>(bias + cc + j + 4);
                                 tc::st_shared_v4(
@@ -579,7 +667,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                             }
                         } else if constexpr (kF8) {
 #pragma unroll
-                            for (int j = 0; j < 32; j += 4) {
+                            for (int j = 0; j < kChunk; j += 4) {
                                 const float4 b0 = *reinterpret_cast<const float4*>(&S.bias[2][cc + j]);
                                 const float4 w0 = *reinterpret_cast<const float4*>(&S.w5[cc + j]);
                                 const uint64_t dq2 = pk(W.f8_dequant[2], W.f8_dequant[2]);
@@ -591,7 +679,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                         } else if constexpr (kFold) {
                             // output layer: the bias b4 is already in the accumulator
 #pragma unroll
-                            for (int j = 0; j < 32; j += 4) {
+                            for (int j = 0; j < kChunk; j += 4) {
                                 const float4 w0 = *reinterpret_cast<const float4*>(&S.w5[cc + j]);
                                 s2 = out_pair<kFmt>(pk(__uint_as_float(v[j]), __uint_as_float(v[j + 1])), pk(w0.x, w0.y), s2);
                                 s2 = out_pair<kFmt>(pk(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3])), pk(w0.z, w0.w), s2);
@@ -599,7 +687,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                         } else {
                             // output layer (positional-encoding form): + b4
 #pragma unroll
-                            for (int j = 0; j < 32; j += 4) {
+                            for (int j = 0; j < kChunk; j += 4) {
                                 const float4 b0 = *reinterpret_cast<const float4*>(&S.bias[2][cc + j]);
                                 const float4 w0 = *reinterpret_cast<const float4*>(&S.w5[cc + j]);
                                 s2 = out_pair<kFmt>(add2(pk(__uint_as_float(v[j]), __uint_as_float(v[j + 1])), pk(b0.x, b0.y)),
@@ -614,7 +702,7 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
                 if (l < 3) {
                     tc::fence_proxy_async_smem();
                     tc::named_barrier(bar_id, kGroupThreads);
-                    if (leader) issue(l + 1);
+                    a_tile_written(l + 1);
                 } else {
                     const float2 sp2 = upk(s2);
                     const float sh = sp2.x + sp2.y;
@@ -647,9 +735,23 @@ __global__ void __launch_bounds__(kThreads, 1) sdf_mlp_tc_kernel(StepParams P, S
     }
     tc::fence_before_sync();
     __syncthreads();
+    if constexpr (kPair) {
+        // neither CTA frees the pair's TMEM or leaves (its shared memory holds operands of the
+        // pair's MMAs and the barriers the other CTA arrives on) before the other has left its
+        // tile loop (bounded)
+        if (tid == 0) {
+            int dummy = 0;
+            tc::mbar_arrive_remote(tc::mapa_shared(tc::smem_u32(&S.done), rank ^ 1u));
+            tc::mbar_wait_bounded(tc::smem_u32(&S.done), 0, &dummy, errw, kDevErrTimeout);
+        }
+        __syncthreads();
+    }
     if (warp == 0) {
         tc::fence_after_sync();
-        tc::tmem_dealloc(tmem_base, kTmemCols);
+        if constexpr (kPair)
+            tc::tmem_dealloc_pair(tmem_base, kTmemCols);
+        else
+            tc::tmem_dealloc(tmem_base, kTmemCols);
     }
 }
 
@@ -715,23 +817,78 @@ __global__ void __launch_bounds__(128, 1) tc_selftest_kernel(const uint16_t* __r
     }
 }
 
-constexpr size_t kSmemBytes = sizeof(TcShared);
+constexpr size_t kSmemBytes = sizeof(TcShared<false>);
+constexpr size_t kSmemPairBytes = sizeof(TcShared<true>);
 static_assert(kSmemBytes <= 227 * 1024, "the tile groups' shared memory exceeds the 227 KB a CTA may hold");
+static_assert(kSmemPairBytes <= 227 * 1024, "the tile groups' shared memory exceeds the 227 KB a CTA may hold");
+constexpr int kGroups = Form<false>::kGroups;
+constexpr int kThreads = Form<false>::kThreads;
+
+// CTA pairs of the pair form that the device holds at once (0: the form is not used)
+int g_pair_clusters = 0;
+
+// Launch of the pair form: clusters of two CTAs, optionally as a programmatic dependent.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pair(bool pdl, void (*kernel)(KArgs...), int clusters, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * clusters);
+    cfg.blockDim = dim3(Form<true>::kThreads);
+    cfg.dynamicSmemBytes = kSmemPairBytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 2 : 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 }  // namespace
 
-template <int kFmt, bool kPE, bool kBatch = false>
+template <int kFmt, bool kPE, bool kBatch = false, bool kPair = false>
 cudaError_t configure_one() {
-    return cudaFuncSetAttribute(sdf_mlp_tc_kernel<kFmt, kPE, kBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(kSmemBytes));
+    return cudaFuncSetAttribute(sdf_mlp_tc_kernel<kFmt, kPE, kBatch, kPair>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kPair ? kSmemPairBytes : kSmemBytes));
+}
+
+// The pair form's kernel attributes and how many of its clusters fit on the device at once.
+template <int kFmt>
+cudaError_t configure_pair(int* clusters) {
+    cudaError_t e = configure_one<kFmt, false, false, true>();
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2);
+    cfg.blockDim = dim3(Form<true>::kThreads);
+    cfg.dynamicSmemBytes = kSmemPairBytes;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(clusters, sdf_mlp_tc_kernel<kFmt, false, false, true>, &cfg);
 }
 
 template <int kFmt>
 cudaError_t launch_tc(const StepParams& P, const StepBuffers& B, const MlpWeights& W, int num_sms, cudaStream_t s) {
     const int n_items = (P.K * P.H + kTileRows - 1) / kTileRows;
+    const BatchRef none{nullptr, 0, 0, nullptr};
+    if constexpr (kFmt != kFmtE4M3) {
+        if (P.pe == 0 && P.sdf_pair && g_pair_clusters > 0) {
+            // one unit = two tiles, four per pair
+            const int want = ((n_items + 1) / 2 + Form<true>::kGroups - 1) / Form<true>::kGroups;
+            int clusters = g_pair_clusters < num_sms / 2 ? g_pair_clusters : num_sms / 2;
+            if (want < clusters) clusters = want;
+            return launch_pair(P.pdl != 0, sdf_mlp_tc_kernel<kFmt, false, false, true>, clusters, s, P, B, W, none);
+        }
+    }
     const int want = (n_items + kGroups - 1) / kGroups;
     const int grid = want < num_sms ? want : num_sms;
-    const BatchRef none{nullptr, 0, 0, nullptr};
     if (P.pe > 0)
         return launch_dependent(P.pdl != 0, sdf_mlp_tc_kernel<kFmt, true, false>, dim3(grid), dim3(kThreads),
                                 kSmemBytes, s, P, B, W, none);
@@ -749,6 +906,10 @@ cudaError_t configure_sdf_mlp_bf16() {
     if (e == cudaSuccess) e = configure_one<kFmtBF16, false, true>();
     if (e == cudaSuccess) e = configure_one<kFmtFP16, false, true>();
     if (e == cudaSuccess) e = configure_one<kFmtE4M3, false, true>();
+    int c16 = 0, cbf = 0;
+    if (e == cudaSuccess) e = configure_pair<kFmtFP16>(&c16);
+    if (e == cudaSuccess) e = configure_pair<kFmtBF16>(&cbf);
+    if (e == cudaSuccess) g_pair_clusters = c16 < cbf ? c16 : cbf;
     return e;
 }
 

@@ -33,6 +33,7 @@ struct mppi_ctx {
     bool have_latents = false;
     bool timing = false;
     bool store_sdf = false;       // MPPI_DIAG_STORE_SDF
+    bool sdf_single_cta = false;  // MPPI_DIAG_SDF_SINGLE_CTA
     uint64_t step_count = 0;
     char err[512] = "";
 
@@ -146,6 +147,7 @@ StepParams make_params(const mppi_ctx* c) {
     P.t_rotor_max = g.rotor_thrust_max;
     P.pe = g.pe_levels;
     P.store_sdf = c->store_sdf ? 1 : 0;
+    P.sdf_pair = c->sdf_single_cta ? 0 : 1;
     // per-kernel event timing measures kernels one after the other
     P.pdl = c->timing ? 0 : 1;
     return P;
@@ -841,10 +843,13 @@ int mppi_read_noise_words(mppi_ctx* c, uint32_t* host_out, size_t n) {
 
 int mppi_set_diagnostics(mppi_ctx* c, int flags) {
     if (!c) return fail(nullptr, MPPI_E_INVALID, "ctx is NULL");
-    if (flags & ~MPPI_DIAG_STORE_SDF) return fail(c, MPPI_E_INVALID, "unknown diagnostics flags 0x%x", flags);
+    if (flags & ~(MPPI_DIAG_STORE_SDF | MPPI_DIAG_SDF_SINGLE_CTA))
+        return fail(c, MPPI_E_INVALID, "unknown diagnostics flags 0x%x", flags);
     const bool store = (flags & MPPI_DIAG_STORE_SDF) != 0;
-    if (c->store_sdf != store) c->graph_dirty = true;
+    const bool single = (flags & MPPI_DIAG_SDF_SINGLE_CTA) != 0;
+    if (c->store_sdf != store || c->sdf_single_cta != single) c->graph_dirty = true;
     c->store_sdf = store;
+    c->sdf_single_cta = single;
     return MPPI_OK;
 }
 

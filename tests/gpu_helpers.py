@@ -43,7 +43,8 @@ def flat_layers(layers):
 class GpuController:
     """One library context set up from a workload dict (see ``workloads``)."""
 
-    def __init__(self, wl, mode, prm=None, stream=None, max_gates=None, fp8_scales=None, store_sdf=True):
+    def __init__(self, wl, mode, prm=None, stream=None, max_gates=None, fp8_scales=None, store_sdf=True,
+                 single_cta=False):
         self.prm = dict(prm if prm is not None else wl["params"])
         poses = np.ascontiguousarray(wl["poses"], dtype=np.float32).reshape(-1, 7)
         self.G = poses.shape[0]
@@ -56,9 +57,12 @@ class GpuController:
             self._scales = None if fp8_scales is None else np.ascontiguousarray(fp8_scales, dtype=np.float32)
             B.mppi_set_sdf_weights(self.ctx, self._keep, self._scales)
         B.mppi_set_gates(self.ctx, self.G, poses if self.G else None, lat if self.G else None)
-        # tests read s(p) of every rollout state: the SDF kernel stores it beside its cost fold
-        if store_sdf and mode != "analytic":
-            B.mppi_set_diagnostics(self.ctx, B.MPPI_DIAG_STORE_SDF)
+        # tests read s(p) of every rollout state: the SDF kernel stores it beside its cost fold;
+        # single_cta selects the 16-bit SDF kernel's single-CTA form instead of the CTA pairs
+        flags = (B.MPPI_DIAG_STORE_SDF if store_sdf and mode != "analytic" else 0) | \
+            (B.MPPI_DIAG_SDF_SINGLE_CTA if single_cta else 0)
+        if flags:
+            B.mppi_set_diagnostics(self.ctx, flags)
         self.K, self.H = self.prm["K"], self.prm["H"]
 
     def close(self):

@@ -413,6 +413,45 @@ def test_step_mlp_fp16_full_size_two_gates(lib):
     g.close()
 
 
+# ---------------------------------------------------------------- the SDF kernel's two forms
+@pytest.mark.parametrize("mode", ["fp16", "bf16"])
+@pytest.mark.parametrize("K,H", [(4096, 50), (300, 6), (129, 2), (1, 1), (257, 129), (16384, 64)])
+def test_sdf_pair_form_matches_single_cta_form(lib, mode, K, H):
+    """The default CTA-pair form of the 16-bit SDF kernel (256-row MMAs over two CTAs, each holding
+    half of every hidden weight matrix) against its single-CTA form on the same step: s(p) at every
+    rollout state within 1e-6 m (both accumulate the same FP32 products; measured identical), and
+    the step's costs and controls follow. Tile counts: 1600, 15 and 3 (odd: the odd CTA's tile of
+    the last unit lies beyond the array), 1 (one row), 260 (ragged), 8192 (13.5 rounds of the
+    4 x 76 pair slots)."""
+    wl = W.two_gate_mlp()
+    prm = _params(wl, K=K, H=H)
+    nominal = W.hover_nominal(H)
+    outs = []
+    for single in (False, True):
+        g = GpuController(wl, mode, prm, single_cta=single)
+        try:
+            out = g.step(state=wl["state"], nominal=nominal)
+            outs.append((out, g.read(B.MPPI_BUF_SDF).astype(np.float64), g.read(B.MPPI_BUF_COST_PARTS)))
+        finally:
+            g.close()
+    (a, sa, pa), (b, sb, pb) = outs
+    assert np.all(np.isfinite(sa)) and np.all(np.isfinite(sb))
+    d = np.abs(sa - sb)
+    _report(f"pair_vs_single_{mode}_K{K}_H{H}", dict(sdf_max_diff_m=float(d.max()),
+                                                       identical=bool(np.array_equal(sa, sb))))
+    assert d.max() <= 1e-6, d.max()
+    np.testing.assert_allclose(pa, pb, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(a["U_new"], b["U_new"], rtol=0, atol=1e-3)
+    # and the pair form meets the oracle at the bounds of the single-CTA tests above (the mean
+    # bound is a statistic: applied where there are a few hundred states)
+    if K * H <= 300 * 6:
+        ref = _oracle(wl, prm, wl["state"], nominal, 0, True)
+        e = np.abs(sa - ref["sdf"]) * 1000.0
+        assert e.max() < (0.8 if mode == "fp16" else 6.0), e.max()
+        if e.size >= 200:
+            assert e.mean() < (0.15 if mode == "fp16" else 1.5), e.mean()
+
+
 # ---------------------------------------------------------------- Gate-SDF MLP, FP8 E4M3 tensor-core path
 @pytest.mark.parametrize("K,H", [(300, 6), (4096, 50)])
 def test_step_mlp_fp8_errors(lib, K, H):
