@@ -43,10 +43,12 @@ TENSOR_FLOPS_PER_QUERY = 3 * 2 * 128 * 128           # layers 2..4 on tcgen05
 FMA_FLOPS_PER_QUERY = 2 * 3 * 128 + 2 * 128           # layer 1 (point part) + output dot
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the headline SDF kernel at this
 # workload, from an ncu capture of the current kernel (None when the kernel changed since)
-SDF_DRAM_BYTES = 3417344 + 0
+SDF_DRAM_BYTES = {"pair": 3416576 + 0, "single": 3417344 + 0}
 SDF_DRAM_BYTES_SOURCE = ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture (--set full) of the "
-                         "current FP16 kernel at K=4096, H=50, G=2 (a constant in bench.py, not measured in this run)")
+                         "current FP16 kernel in the timed form at K=4096, H=50, G=2 (a constant in bench.py, not "
+                         "measured in this run)")
 HEADLINE_MODE = "fp16"
+SDF_FORM = "pair"           # --sdf-form: the 16-bit SDF kernel's form (CTA pairs or single CTAs)
 # multiply-adds x 2 of the depth encoder's convolutions and head for one 160 x 120 image
 ENCODER_FLOPS_PER_IMAGE_160x120 = 2 * (60 * 80 * 16 * 9 * 1 + 30 * 40 * 32 * 9 * 16 + 15 * 20 * 64 * 9 * 32
                                        + 8 * 10 * 64 * 9 * 64 + 64 * 64)
@@ -76,7 +78,12 @@ def parse():
     ap.add_argument("--four-gate-steps", type=int, default=20)
     ap.add_argument("--render-steps", type=int, default=20)
     ap.add_argument("--vision-steps", type=int, default=20)
-    return ap.parse_args()
+    ap.add_argument("--sdf-form", default="pair", choices=["pair", "single"],
+                    help="form of the 16-bit SDF kernel: CTA pairs (default) or single CTAs")
+    args = ap.parse_args()
+    global SDF_FORM
+    SDF_FORM = args.sdf_form
+    return args
 
 
 def workload():
@@ -234,6 +241,8 @@ def make_ctx(B, wl, mode, stream, drone_id):
         cfg.arm_length, cfg.torque_coeff = prm["arm_length"], prm["kappa"]
         cfg.inertia_x, cfg.inertia_y, cfg.inertia_z = prm["inertia"]
     ctx = B.mppi_create(cfg, stream)
+    if SDF_FORM == "single":
+        B.mppi_set_diagnostics(ctx, B.MPPI_DIAG_SDF_SINGLE_CTA)
     if mode != "analytic":
         keep = []
         for Wm, b in wl["layers"]:
@@ -925,6 +934,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": HEADLINE_MODE, "data": "synthetic",
         "config": {"workload": wl["name"], "K": K, "H": H, "gates": G,
                    "sdf": "Gate-SDF MLP, FP16 tcgen05 (the 16-bit form within the 2 mm SDF target at p99)",
+                   "sdf_kernel_form": {"pair": "CTA pairs (cta_group::2, M = 256)", "single": "single CTAs"}[SDF_FORM],
                    "dynamics": "fp32 RK4", "l2": "flushed (256 MiB write) between timed steps",
                    "parallelism": "replicas" if world > 1 else "single"},
         "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
@@ -945,7 +955,7 @@ def run_ours(args):
         "kernel_ms": ktimes,
         "roofline": {"kernel": "sdf_mlp_" + HEADLINE_MODE, "bound": "tensor", "achieved": achieved, "peak": peak_tf,
                      "unit": "TFLOP/s", "frac": achieved / peak_tf if achieved else None,
-                     "traffic": SDF_DRAM_BYTES, "traffic_source": SDF_DRAM_BYTES_SOURCE,
+                     "traffic": SDF_DRAM_BYTES[SDF_FORM], "traffic_source": SDF_DRAM_BYTES_SOURCE,
                      "peak_source": peak_src + " (FP16 dense rate = BF16 nominally)",
                      "algorithmic_flops_per_launch": tensor_flops},
         "e2e": {"value": K * H / (e2e_ms.mean() * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
