@@ -738,11 +738,14 @@ __global__ void __launch_bounds__(Form<kPair>::kThreads, 1) sdf_mlp_tc_kernel(St
     if constexpr (kPair) {
         // neither CTA frees the pair's TMEM or leaves (its shared memory holds operands of the
         // pair's MMAs and the barriers the other CTA arrives on) before the other has left its
-        // tile loop (bounded)
+        // tile loop. Bounded by three wait limits: after an abort the other CTA may still spend
+        // one limit in an accumulator wait before it arrives here.
         if (tid == 0) {
-            int dummy = 0;
             tc::mbar_arrive_remote(tc::mapa_shared(tc::smem_u32(&S.done), rank ^ 1u));
-            tc::mbar_wait_bounded(tc::smem_u32(&S.done), 0, &dummy, errw, kDevErrTimeout);
+            for (int attempt = 0; attempt < 3; ++attempt) {
+                int dummy = 0;
+                if (tc::mbar_wait_bounded(tc::smem_u32(&S.done), 0, &dummy, errw, kDevErrTimeout)) break;
+            }
         }
         __syncthreads();
     }
