@@ -48,7 +48,7 @@ SDF_DRAM_BYTES_SOURCE = ("dram__bytes_read.sum + dram__bytes_write.sum of one nc
                          "current FP16 kernel in the timed form at K=4096, H=50, G=2 (a constant in bench.py, not "
                          "measured in this run)")
 HEADLINE_MODE = "fp16"
-SDF_FORM = "pair"           # --sdf-form: the 16-bit SDF kernel's form (CTA pairs or single CTAs)
+SDF_FORM = "auto"           # --sdf-form: the 16-bit SDF kernel's form (library defaults, CTA pairs or single CTAs)
 # multiply-adds x 2 of the depth encoder's convolutions and head for one 160 x 120 image
 ENCODER_FLOPS_PER_IMAGE_160x120 = 2 * (60 * 80 * 16 * 9 * 1 + 30 * 40 * 32 * 9 * 16 + 15 * 20 * 64 * 9 * 32
                                        + 8 * 10 * 64 * 9 * 64 + 64 * 64)
@@ -78,8 +78,9 @@ def parse():
     ap.add_argument("--four-gate-steps", type=int, default=20)
     ap.add_argument("--render-steps", type=int, default=20)
     ap.add_argument("--vision-steps", type=int, default=20)
-    ap.add_argument("--sdf-form", default="pair", choices=["pair", "single"],
-                    help="form of the 16-bit SDF kernel: CTA pairs (default) or single CTAs")
+    ap.add_argument("--sdf-form", default="auto", choices=["auto", "pair", "single"],
+                    help="form of the 16-bit SDF kernel: the library's defaults (CTA pairs for one "
+                         "controller's step, single CTAs in the serving engine), or one form everywhere")
     args = ap.parse_args()
     global SDF_FORM
     SDF_FORM = args.sdf_form
@@ -315,6 +316,8 @@ def _serve(B, fleet, cfgs, keep, arrivals, duration_s, batching, max_inflight, m
     scfg.max_inflight = max_inflight
     scfg.sdf_mode = mode
     scfg.batching = batching
+    if SDF_FORM != "auto":
+        scfg.sdf_single_cta = 1 if SDF_FORM == "single" else 0
     srv = B.mppi_server_create(scfg)
     B.mppi_server_set_sdf_weights(srv, keep)
     inputs = [(np.ascontiguousarray(d["state"], np.float32), np.ascontiguousarray(d["poses"]),
@@ -934,7 +937,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": HEADLINE_MODE, "data": "synthetic",
         "config": {"workload": wl["name"], "K": K, "H": H, "gates": G,
                    "sdf": "Gate-SDF MLP, FP16 tcgen05 (the 16-bit form within the 2 mm SDF target at p99)",
-                   "sdf_kernel_form": {"pair": "CTA pairs (cta_group::2, M = 256)", "single": "single CTAs"}[SDF_FORM],
+                   "sdf_kernel_form": {"auto": "CTA pairs (cta_group::2, M = 256)", "pair": "CTA pairs (cta_group::2, M = 256)",
+                                       "single": "single CTAs"}[SDF_FORM],
                    "dynamics": "fp32 RK4", "l2": "flushed (256 MiB write) between timed steps",
                    "parallelism": "replicas" if world > 1 else "single"},
         "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
@@ -955,7 +959,8 @@ def run_ours(args):
         "kernel_ms": ktimes,
         "roofline": {"kernel": "sdf_mlp_" + HEADLINE_MODE, "bound": "tensor", "achieved": achieved, "peak": peak_tf,
                      "unit": "TFLOP/s", "frac": achieved / peak_tf if achieved else None,
-                     "traffic": SDF_DRAM_BYTES[SDF_FORM], "traffic_source": SDF_DRAM_BYTES_SOURCE,
+                     "traffic": SDF_DRAM_BYTES["single" if SDF_FORM == "single" else "pair"],
+                     "traffic_source": SDF_DRAM_BYTES_SOURCE,
                      "peak_source": peak_src + " (FP16 dense rate = BF16 nominally)",
                      "algorithmic_flops_per_launch": tensor_flops},
         "e2e": {"value": K * H / (e2e_ms.mean() * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -705,6 +705,11 @@ typedef struct mppi_server_config {
     int32_t sdf_mode;          /* MPPI_SDF_* used by every drone */
     int32_t batching;          /* 1: batched launches (every drone then shares softplus_beta and
                                   pe_levels); 0: one step graph per drone */
+    int32_t sdf_single_cta;    /* 1 (default): BF16 / FP16 SDF kernels (batched or per drone) in their
+                                  single-CTA form; 0: the CTA-pair form where it applies (see
+                                  MPPI_DIAG_SDF_SINGLE_CTA).  With many drones' kernels in flight at
+                                  once the single-CTA form measured faster: per-drone graphs 2.40e9
+                                  vs 2.33e9 rollout-steps/s, batched 2.32e9 vs 2.26e9 (64 drones) */
 } mppi_server_config;
 
 typedef struct mppi_server_stats {
@@ -714,7 +719,8 @@ typedef struct mppi_server_stats {
     uint64_t batches;                  /* batched mode: batches launched */
 } mppi_server_stats;
 
-/* Defaults: no budget, 16 requests in flight, FP16 tensor-core SDF, batched launches. */
+/* Defaults: no budget, 16 requests in flight, FP16 tensor-core SDF, batched launches, single-CTA
+ * SDF kernels. */
 void mppi_server_config_default(mppi_server_config* cfg);
 /* Create a server on the current device (starts its worker thread; batched mode also allocates four
  * pinned and four device batch blocks of max_inflight controllers each, and a stream for each).

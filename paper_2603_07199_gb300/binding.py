@@ -102,7 +102,7 @@ class MppiConfig(ctypes.Structure):
 
 class MppiServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32), ("sdf_mode", ctypes.c_int32),
-                ("batching", ctypes.c_int32)]
+                ("batching", ctypes.c_int32), ("sdf_single_cta", ctypes.c_int32)]
 
 
 class MppiServerStats(ctypes.Structure):

@@ -31,6 +31,8 @@
 #include "mppi.h"
 #include "tc.cuh"
 
+#include <atomic>
+
 namespace mppi {
 
 namespace {
@@ -286,7 +288,7 @@ __global__ void __launch_bounds__(Form<kPair>::kThreads, 1) sdf_mlp_tc_kernel(St
     constexpr bool kF16 = (kFmt == kFmtFP16);
     constexpr bool kF8 = (kFmt == kFmtE4M3);
     constexpr bool kFold = !kF8 && !kPE;           // hidden biases ride in the GEMM (bias operands)
-    static_assert(!kPair || (kFold && !kBatch), "the CTA-pair form covers the 16-bit one-controller kernels");
+    static_assert(!kPair || kFold, "the CTA-pair form covers the 16-bit kernels without positional encoding");
     constexpr int kGroups = Form<kPair>::kGroups;
     constexpr int kThreads = Form<kPair>::kThreads;
     using TcShared = mppi::TcShared<kPair>;
@@ -827,8 +829,9 @@ static_assert(kSmemPairBytes <= 227 * 1024, "the tile groups' shared memory exce
 constexpr int kGroups = Form<false>::kGroups;
 constexpr int kThreads = Form<false>::kThreads;
 
-// CTA pairs of the pair form that the device holds at once (0: the form is not used)
-int g_pair_clusters = 0;
+// CTA pairs of the pair form that the device holds at once (0: the form is not used); written
+// when the kernels are configured (every context creation, the same value), read by launches
+std::atomic<int> g_pair_clusters{0};
 
 // Launch of the pair form: clusters of two CTAs, optionally as a programmatic dependent.
 template <typename... KArgs, typename... Args>
@@ -882,10 +885,11 @@ cudaError_t launch_tc(const StepParams& P, const StepBuffers& B, const MlpWeight
     const int n_items = (P.K * P.H + kTileRows - 1) / kTileRows;
     const BatchRef none{nullptr, 0, 0, nullptr};
     if constexpr (kFmt != kFmtE4M3) {
-        if (P.pe == 0 && P.sdf_pair && g_pair_clusters > 0) {
+        const int pair_clusters = g_pair_clusters.load(std::memory_order_relaxed);
+        if (P.pe == 0 && P.sdf_pair && pair_clusters > 0) {
             // one unit = two tiles, four per pair
             const int want = ((n_items + 1) / 2 + Form<true>::kGroups - 1) / Form<true>::kGroups;
-            int clusters = g_pair_clusters < num_sms / 2 ? g_pair_clusters : num_sms / 2;
+            int clusters = pair_clusters < num_sms / 2 ? pair_clusters : num_sms / 2;
             if (want < clusters) clusters = want;
             return launch_pair(P.pdl != 0, sdf_mlp_tc_kernel<kFmt, false, false, true>, clusters, s, P, B, W, none);
         }
@@ -912,7 +916,9 @@ cudaError_t configure_sdf_mlp_bf16() {
     int c16 = 0, cbf = 0;
     if (e == cudaSuccess) e = configure_pair<kFmtFP16>(&c16);
     if (e == cudaSuccess) e = configure_pair<kFmtBF16>(&cbf);
-    if (e == cudaSuccess) g_pair_clusters = c16 < cbf ? c16 : cbf;
+    if (e == cudaSuccess) e = configure_one<kFmtFP16, false, true, true>();
+    if (e == cudaSuccess) e = configure_one<kFmtBF16, false, true, true>();
+    if (e == cudaSuccess) g_pair_clusters.store(c16 < cbf ? c16 : cbf, std::memory_order_relaxed);
     return e;
 }
 
@@ -931,13 +937,30 @@ cudaError_t launch_sdf_mlp_fp8(const StepParams& P, const StepBuffers& B, const 
     return launch_tc<kFmtE4M3>(P, B, W, num_sms, s);
 }
 
-cudaError_t launch_sdf_batch(int sdf_mode, const BatchSlot* slots, int n, int tiles, const StepParams& P0,
-                             const MlpWeights& W, int* err, int num_sms, cudaStream_t s) {
+bool sdf_batch_pairs_available(int sdf_mode) {
+    return (sdf_mode == MPPI_SDF_MLP_BF16 || sdf_mode == MPPI_SDF_MLP_FP16) &&
+           g_pair_clusters.load(std::memory_order_relaxed) > 0;
+}
+
+cudaError_t launch_sdf_batch(int sdf_mode, bool pairs, const BatchSlot* slots, int n, int tiles,
+                             const StepParams& P0, const MlpWeights& W, int* err, int num_sms, cudaStream_t s) {
     if (n <= 0 || tiles <= 0) return cudaSuccess;
-    const int want = (tiles + kGroups - 1) / kGroups;
-    const int grid = want < num_sms ? want : num_sms;
     const BatchRef R{slots, n, tiles, err};
     const StepBuffers none{};
+    if (pairs) {
+        // every controller's tiles start at an even tile (the caller's layout), so the two tiles of
+        // a unit belong to one controller
+        if (tiles % 2 != 0 || !sdf_batch_pairs_available(sdf_mode)) return cudaErrorInvalidValue;
+        const int want = (tiles / 2 + Form<true>::kGroups - 1) / Form<true>::kGroups;
+        const int pair_clusters = g_pair_clusters.load(std::memory_order_relaxed);
+        int clusters = pair_clusters < num_sms / 2 ? pair_clusters : num_sms / 2;
+        if (want < clusters) clusters = want;
+        if (sdf_mode == MPPI_SDF_MLP_BF16)
+            return launch_pair(false, sdf_mlp_tc_kernel<kFmtBF16, false, true, true>, clusters, s, P0, none, W, R);
+        return launch_pair(false, sdf_mlp_tc_kernel<kFmtFP16, false, true, true>, clusters, s, P0, none, W, R);
+    }
+    const int want = (tiles + kGroups - 1) / kGroups;
+    const int grid = want < num_sms ? want : num_sms;
     switch (sdf_mode) {
         case MPPI_SDF_MLP_BF16:
             return launch_dependent(false, sdf_mlp_tc_kernel<kFmtBF16, false, true>, dim3(grid), dim3(kThreads),

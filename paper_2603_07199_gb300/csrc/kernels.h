@@ -103,8 +103,13 @@ int update_rollouts_per_block(int K);
 cudaError_t launch_batch_prep(const BatchSlot* slots, int n, const float* inputs, cudaStream_t s);
 cudaError_t launch_rollout_batch(const BatchSlot* slots, int n, int blocks, int max_h, cudaStream_t s);
 cudaError_t launch_cost_update_batch(const BatchSlot* slots, int n, int blocks, int max_r, cudaStream_t s);
-cudaError_t launch_sdf_batch(int sdf_mode, const BatchSlot* slots, int n, int tiles, const StepParams& P0,
+// pairs: run the CTA-pair form (only where sdf_batch_pairs_available); every controller's tiles
+// then start at an even tile (tile0 even, its tile count rounded up to even) and tiles is even.
+cudaError_t launch_sdf_batch(int sdf_mode, bool pairs, const BatchSlot* slots, int n, int tiles, const StepParams& P0,
                              const MlpWeights& W, int* err, int num_sms, cudaStream_t s);
+// Whether this mode's batched SDF launch can run in the CTA-pair form (BF16 / FP16, after the
+// kernels were configured on a device that holds the form's clusters).
+bool sdf_batch_pairs_available(int sdf_mode);
 
 // Store a message in the calling thread's error slot (read by mppi_last_error(NULL)).
 void set_thread_error(const char* msg);

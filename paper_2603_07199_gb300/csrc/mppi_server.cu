@@ -82,6 +82,7 @@ struct BatchBuf {
     cudaEvent_t done = nullptr;
     std::vector<Inflight> reqs;
     bool busy = false;
+    bool pair_tiles = false;                // the batch's tile layout is for the pair form of the SDF kernel
 };
 
 constexpr int kBatchInFloats = mppi::kBatchStateSlot + MPPI_MAX_GATES * (8 + MPPI_LATENT_DIM);
@@ -162,6 +163,7 @@ int ensure_context(mppi_server* s, int id, Drone& d) {
     mppi_ctx* c = nullptr;
     int rc = mppi_create(&d.cfg, nullptr, &c);
     if (rc != MPPI_OK) return sfail(s, rc, "drone %d: %s", id, mppi_last_error(nullptr));
+    if (s->cfg.sdf_single_cta) mppi_set_diagnostics(c, MPPI_DIAG_SDF_SINGLE_CTA);
     if (s->have_weights && d.cfg.sdf_mode != MPPI_SDF_ANALYTIC) {
         const float* ptrs[2 * MPPI_MLP_LAYERS];
         for (int i = 0; i < 2 * MPPI_MLP_LAYERS; ++i) ptrs[i] = s->layers[i].data();
@@ -303,8 +305,8 @@ cudaError_t launch_batch(mppi_server* s, BatchBuf& b, int n, size_t in_floats, i
     const int mode = s->cfg.sdf_mode;
     if (e == cudaSuccess && mode != MPPI_SDF_ANALYTIC) {
         if (s->pe_levels == 0 && mode != MPPI_SDF_MLP_FP32) {
-            e = launch_sdf_batch(mode, ds, n, tiles, ctx_params(ctxs[0]), ctx_weights(ctxs[0]), b.d_err,
-                                 ctx_num_sms(ctxs[0]), st);
+            e = launch_sdf_batch(mode, b.pair_tiles, ds, n, tiles, ctx_params(ctxs[0]), ctx_weights(ctxs[0]),
+                                 b.d_err, ctx_num_sms(ctxs[0]), st);
         } else {
             for (int i = 0; i < n && e == cudaSuccess; ++i) {
                 const MlpWeights W = ctx_weights(ctxs[i]);
@@ -380,6 +382,10 @@ void batched_worker_loop(mppi_server* s) {
                 for (int i : s->order) inflight += s->buf[i].reqs.size();
                 int n = 0, roll = 0, tiles = 0, upd = 0, max_h = 1, max_r = 32;
                 size_t in_used = 0;
+                // decided once per batch: the same flag lays out the tiles and picks the kernel form
+                const bool pair_tiles = s->pe_levels == 0 && !s->cfg.sdf_single_cta &&
+                                        sdf_batch_pairs_available(s->cfg.sdf_mode);
+                b.pair_tiles = pair_tiles;
                 ctxs.clear();
                 for (auto it = s->queue.begin(); it != s->queue.end();) {
                     if (inflight + static_cast<size_t>(n) >= static_cast<size_t>(s->cfg.max_inflight)) break;
@@ -413,7 +419,10 @@ void batched_worker_loop(mppi_server* s) {
                     sl.roll_block0 = roll;
                     roll += rollout_batch_blocks(sl.P);
                     sl.tile0 = tiles;
-                    if (sl.mlp) tiles += (sl.P.K * sl.P.H + kTileRows - 1) / kTileRows;
+                    if (sl.mlp) {
+                        const int t = (sl.P.K * sl.P.H + kTileRows - 1) / kTileRows;
+                        tiles += pair_tiles ? (t + 1) & ~1 : t;     // a pair unit never spans two drones
+                    }
                     sl.upd_R = update_rollouts_per_block(sl.P.K);
                     sl.upd_block0 = upd;
                     upd += (sl.P.K + sl.upd_R - 1) / sl.upd_R;
@@ -490,6 +499,7 @@ void mppi_server_config_default(mppi_server_config* c) {
     c->max_inflight = 16;
     c->sdf_mode = MPPI_SDF_MLP_FP16;
     c->batching = 1;
+    c->sdf_single_cta = 1;
 }
 
 int mppi_server_create(const mppi_server_config* cfg, mppi_server** out) {
@@ -499,6 +509,8 @@ int mppi_server_create(const mppi_server_config* cfg, mppi_server** out) {
         return sfail(nullptr, MPPI_E_INVALID, "max_inflight=%d out of [1, 1024]", cfg->max_inflight);
     if (cfg->sdf_mode < MPPI_SDF_ANALYTIC || cfg->sdf_mode > MPPI_SDF_MLP_FP8)
         return sfail(nullptr, MPPI_E_INVALID, "sdf_mode=%d", cfg->sdf_mode);
+    if (cfg->sdf_single_cta != 0 && cfg->sdf_single_cta != 1)
+        return sfail(nullptr, MPPI_E_INVALID, "sdf_single_cta=%d", cfg->sdf_single_cta);
     mppi_server* s = new (std::nothrow) mppi_server();
     if (!s) return sfail(nullptr, MPPI_E_OOM, "host allocation failed");
     s->cfg = *cfg;

@@ -75,8 +75,9 @@ def test_server_and_other_struct_layouts_match_header(built, tmp_path):
     would shift the others')."""
     src = tmp_path / "sz2.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mppi.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(mppi_server_config),'
-                   ' offsetof(mppi_server_config, batching), sizeof(mppi_server_stats),'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mppi_server_config),'
+                   ' offsetof(mppi_server_config, batching), offsetof(mppi_server_config, sdf_single_cta),'
+                   ' sizeof(mppi_server_stats),'
                    ' offsetof(mppi_server_stats, batches), sizeof(mppi_train_config), sizeof(mppi_depth_camera));'
                    ' return 0;}\n')
     exe = tmp_path / "sz2"
@@ -84,5 +85,5 @@ def test_server_and_other_struct_layouts_match_header(built, tmp_path):
     vals = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()))
     from paper_2603_07199_gb300 import binding
     assert vals == [ctypes.sizeof(binding.MppiServerConfig), binding.MppiServerConfig.batching.offset,
-                    ctypes.sizeof(binding.MppiServerStats), binding.MppiServerStats.batches.offset,
+                    binding.MppiServerConfig.sdf_single_cta.offset, ctypes.sizeof(binding.MppiServerStats), binding.MppiServerStats.batches.offset,
                     ctypes.sizeof(binding.MppiTrainConfig), ctypes.sizeof(binding.MppiDepthCamera)]

@@ -33,13 +33,15 @@ def _drone_cfg(d, mode="bf16"):
     return make_config(d["params"], mode, d["G"])
 
 
-def _run(fleet, requests, budget=0, max_inflight=16, mode="bf16", layers=None, batching=1):
+def _run(fleet, requests, budget=0, max_inflight=16, mode="bf16", layers=None, batching=1, single_cta=None):
     """Submit (drone index, state) requests in order without waiting; return controls per request."""
     cfg = B.mppi_server_config_default()
     cfg.hbm_budget_bytes = budget
     cfg.max_inflight = max_inflight
     cfg.sdf_mode = MODES[mode]
     cfg.batching = batching
+    if single_cta is not None:
+        cfg.sdf_single_cta = single_cta
     srv = B.mppi_server_create(cfg)
     keep = flat_layers(layers) if layers is not None else None
     if keep is not None:
@@ -102,6 +104,27 @@ def _mixed_fleet():
     rot["params"] = dict(W.rotor_params(512, 20), seed=rot["params"]["seed"], drone_id=rot["params"]["drone_id"])
     rot["state"] = W.rotor_state([0.2, -0.1, 0.3])
     return fleet
+
+
+@pytest.mark.parametrize("batching", [1, 0])
+@pytest.mark.parametrize("mode", ["fp16", "bf16"])
+def test_sdf_kernel_forms_give_the_same_results(lib, mode, batching):
+    """The server's default single-CTA SDF kernels and the CTA-pair form (batched: every drone's
+    tiles padded to an even count, so a pair's two tiles belong to one drone) give every drone
+    bit-identical controls, for a fleet whose drones have odd and even tile counts."""
+    fleet = _mixed_fleet()
+    fleet[0]["params"] = dict(fleet[0]["params"], H=43)          # 101 tiles
+    layers = W.xavier_mlp(1)
+    assert len({(d["params"]["K"] * d["params"]["H"] + 127) // 128 % 2 for d in fleet}) == 2
+    n_steps = 2
+    rng = np.random.default_rng(23)
+    states = {i: [np.asarray(d["state"], np.float32) + np.float32(0.05) * rng.standard_normal(len(d["state"])).astype(
+        np.float32) * (np.arange(len(d["state"])) < 6) for _ in range(n_steps)] for i, d in enumerate(fleet)}
+    reqs = [(i, states[i][s]) for s in range(n_steps) for i in range(len(fleet))]
+    single, _, _ = _run(fleet, reqs, mode=mode, layers=layers, batching=batching)
+    pair, _, _ = _run(fleet, reqs, mode=mode, layers=layers, batching=batching, single_cta=0)
+    for a, b in zip(single, pair):
+        np.testing.assert_array_equal(a, b)
 
 
 @pytest.mark.parametrize("mode", ["fp16", "bf16", "fp8", "fp32", "analytic"])
