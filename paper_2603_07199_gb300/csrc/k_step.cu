@@ -287,10 +287,26 @@ __global__ void __launch_bounds__(kRollWarps * 32) rollout_kernel(StepParams P, 
 // ------------------------------------------------------------------ (a) + (b) rotor-thrust-rate model
 // The paper's command (Sec. IV-A): the four rotor-thrust rates, the body rate following from
 // the rotors' torques (rk4_rotor).  The body rate now has dynamics of its own, so the attitude
-// is no longer a product of state-independent factors: one rollout per thread, sequential
-// over the horizon, drawing its noise (the same Philox blocks as the thrust / body-rate
-// model, scaled by sigma_tdot), storing noise and positions in the [K][H] arrays.
-constexpr int kRotorThreads = 64;
+// is no longer a product of state-independent factors: each rollout is integrated by one
+// thread, sequentially over the horizon.  A block (4 warps) owns 32 rollouts: warp 0 integrates
+// them (one lane each) while warps 1-3 draw the noise of the next kRotorChunk steps (the same
+// Philox blocks as the thrust / body-rate model, scaled by sigma_tdot) into the [K][H] noise
+// array, from which warp 0 reads it after the block's barrier; the draws are off the
+// integration's serial chain.  Positions are stored in the [K][H] array.
+constexpr int kRotorThreads = 128;
+constexpr int kRotorRollouts = 32;               // rollouts per block (warp 0's lanes)
+constexpr int kRotorChunk = 16;                  // horizon steps drawn ahead per block barrier
+static_assert(kRotorThreads == kRollWarps * 32, "the batched rollout kernel runs the rotor body in its 128-thread blocks");
+
+// the noise of rollouts [k0, k0 + 32) x steps [h0, h0 + n), drawn by `nthreads` threads from t0
+__device__ __forceinline__ void rotor_draw(const StepParams& P, const StepBuffers& B, int k0, int h0, int n,
+                                           uint32_t st, int t, int nthreads) {
+    for (int i = t; i < kRotorRollouts * n; i += nthreads) {
+        const int r = i / n, h = h0 + (i - r * n);
+        const int k = k0 + r;
+        if (k < P.K) B.noise[static_cast<size_t>(k) * P.H + h] = noise_from_block(P, noise_block(P, k, h, st));
+    }
+}
 
 __device__ __forceinline__ void rotor_body(const StepParams& P, const StepBuffers& B, int analytic, int block,
                                            float4* sU, float* sPose) {
@@ -298,11 +314,15 @@ __device__ __forceinline__ void rotor_body(const StepParams& P, const StepBuffer
     pdl_wait();
     for (int i = threadIdx.x; i < P.H; i += blockDim.x) sU[i] = B.nominal[i];
     for (int i = threadIdx.x; i < P.G * 8; i += blockDim.x) sPose[i] = B.poses[i];
-    __syncthreads();
-    const int k = block * static_cast<int>(blockDim.x) + static_cast<int>(threadIdx.x);
-    if (k >= P.K) return;
     const int K = P.K, H = P.H;
+    const int k0 = block * kRotorRollouts;
     const uint32_t st = B.step[0];
+    // the first chunk's noise, drawn by the whole block
+    rotor_draw(P, B, k0, 0, min(kRotorChunk, H), st, threadIdx.x, blockDim.x);
+    __syncthreads();
+    const bool integrator = threadIdx.x < 32;
+    const int k = k0 + static_cast<int>(threadIdx.x);
+    const bool valid = integrator && k < K;
     const float* s0 = B.state;
     const Vec3 p0 = v3(s0[0], s0[1], s0[2]);
     Vec3 p = p0, v = v3(s0[3], s0[4], s0[5]), w = v3(s0[10], s0[11], s0[12]);
@@ -313,31 +333,44 @@ __device__ __forceinline__ void rotor_body(const StepParams& P, const StepBuffer
     const float* pose_t = sPose + 8 * (tgt < 0 ? 0 : tgt);
     const Vec3 wp = v3(pose_t[0], pose_t[1], pose_t[2]);
     float jctl = 0.f, jcol = 0.f, jvis = 0.f;
-    float4* noise_k = B.noise + static_cast<size_t>(k) * H;
-    float4* pos_k = B.pos + static_cast<size_t>(k) * H;
-    for (int h = 0; h < H; ++h) {
-        const float4 d = noise_from_block(P, noise_block(P, k, h, st));
-        noise_k[h] = d;
-        const float4 un = sU[h];
-        const float4 u = clip_control(P, make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w));
-        const float e0 = u.x - P.u_hover;
-        jctl += e0 * e0 + u.y * u.y + u.z * u.z + u.w * u.w;
-        rk4_rotor(P, p, v, q, w, T, u);
-        pos_k[h] = make_float4(p.x, p.y, p.z, 0.f);
-        if (P.paper) {
-            if (tgt >= 0) {
-                jvis += misalignment(q, p, wp);
-                if (analytic) jcol += fmaxf(P.d_safe - guide_sdf(to_gate(pose_t, p), P.a_in, P.tan_alpha), 0.f);
+    const float4* noise_k = B.noise + static_cast<size_t>(valid ? k : 0) * H;
+    float4* pos_k = B.pos + static_cast<size_t>(valid ? k : 0) * H;
+    for (int h0 = 0; h0 < H; h0 += kRotorChunk) {
+        const int n = min(kRotorChunk, H - h0);
+        if (!integrator) {
+            // warps 1-3: the next chunk's noise while warp 0 integrates this one
+            if (h0 + n < H)
+                rotor_draw(P, B, k0, h0 + n, min(kRotorChunk, H - h0 - n), st, threadIdx.x - 32, blockDim.x - 32);
+        } else if (valid) {
+            float4 d = noise_k[h0];
+            for (int j = 0; j < n; ++j) {
+                const int h = h0 + j;
+                const float4 d_next = (j + 1 < n) ? noise_k[h + 1] : d;   // loaded while this step runs
+                const float4 un = sU[h];
+                const float4 u = clip_control(P, make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w));
+                const float e0 = u.x - P.u_hover;
+                jctl += e0 * e0 + u.y * u.y + u.z * u.z + u.w * u.w;
+                rk4_rotor(P, p, v, q, w, T, u);
+                pos_k[h] = make_float4(p.x, p.y, p.z, 0.f);
+                if (P.paper) {
+                    if (tgt >= 0) {
+                        jvis += misalignment(q, p, wp);
+                        if (analytic) jcol += fmaxf(P.d_safe - guide_sdf(to_gate(pose_t, p), P.a_in, P.tan_alpha), 0.f);
+                    }
+                } else if (analytic) {
+                    float smin = __int_as_float(0x7f800000);
+                    for (int g = 0; g < P.G; ++g) {
+                        const Vec3 pg = to_gate(sPose + 8 * g, p);
+                        smin = fminf(smin, frame_sdf(pg.x, pg.y, pg.z, P.a_in, P.a_out, P.half_depth));
+                    }
+                    jcol += hinge_sq(smin, P.d_safe);
+                }
+                d = d_next;
             }
-        } else if (analytic) {
-            float smin = __int_as_float(0x7f800000);
-            for (int g = 0; g < P.G; ++g) {
-                const Vec3 pg = to_gate(sPose + 8 * g, p);
-                smin = fminf(smin, frame_sdf(pg.x, pg.y, pg.z, P.a_in, P.a_out, P.half_depth));
-            }
-            jcol += hinge_sq(smin, P.d_safe);
         }
+        __syncthreads();
     }
+    if (!valid) return;
     if (P.paper) {
         const float dHx = p.x - wp.x, dHy = p.y - wp.y, dHz = p.z - wp.z;
         const float d0x = p0.x - wp.x, d0y = p0.y - wp.y, d0z = p0.z - wp.z;
@@ -788,7 +821,7 @@ cudaError_t launch_noise_words(const StepParams& P, const StepBuffers& B, uint4*
 cudaError_t launch_rollout(const StepParams& P, const StepBuffers& B, int analytic, cudaStream_t s) {
     // first kernel of the step: ordered after the previous step's last kernel by the stream
     if (P.rotor)
-        return launch_dependent(false, rollout_rotor_kernel, dim3((P.K + kRotorThreads - 1) / kRotorThreads),
+        return launch_dependent(false, rollout_rotor_kernel, dim3((P.K + kRotorRollouts - 1) / kRotorRollouts),
                                 dim3(kRotorThreads), P.H * sizeof(float4), s, P, B, analytic);
     // two rollouts per warp (16 lanes x 4 steps, or x 2 when the horizon fits in 32), except for
     // a long horizon at small K: there a warp per rollout (32 lanes x 2 steps) keeps more warps
@@ -857,7 +890,7 @@ int rollout_batch_blocks(const StepParams& P) {
         case 0: return (P.K + kRollWarps - 1) / kRollWarps;
         case 1:
         case 2: return (P.K + 2 * kRollWarps - 1) / (2 * kRollWarps);
-        default: return (P.K + kRollWarps * 32 - 1) / (kRollWarps * 32);
+        default: return (P.K + kRotorRollouts - 1) / kRotorRollouts;
     }
 }
 
