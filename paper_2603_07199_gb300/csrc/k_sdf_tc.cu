@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(Form<kPair>::kThreads, 1) sdf_mlp_tc_kernel(St
     if (tid == 0) {
         for (int i = 0; i < kGroups; ++i) tc::mbar_init(tc::smem_u32(&S.acc_full[i]), 1);
         if constexpr (kPair) {
-            for (int i = 0; i < kGroups; ++i) tc::mbar_init(tc::smem_u32(&S.a_ready[i]), 1);
+            for (int i = 0; i < kGroups; ++i) tc::mbar_init(tc::smem_u32(&S.a_ready[i]), kGroupWarps);
             tc::mbar_init(tc::smem_u32(&S.done), 1);
         }
         S.abort_flag = 0;
@@ -489,13 +489,18 @@ __global__ void __launch_bounds__(Form<kPair>::kThreads, 1) sdf_mlp_tc_kernel(St
             tc::mma_commit(acc_bar);
         ++outstanding;
     };
-    // the group's A tile is written: issue (one CTA, a pair's even CTA) or tell the even CTA
+    // this thread's part of the group's A tile is written (and fenced): one CTA or a pair's even
+    // CTA meets in the group's named barrier, after which the leader issues; in a pair's odd CTA
+    // every warp arrives on the even CTA's a_ready barrier itself (8 arrivals per phase), so no
+    // barrier of the odd group lies on the path to the MMA
     auto a_tile_written = [&](int l) {
-        if (!leader) return;
-        if (kPair && rank != 0)
-            tc::mbar_arrive_remote(tc::mapa_shared(ready_bar, 0));
-        else
-            issue(l);
+        if (kPair && rank != 0) {
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive_remote(tc::mapa_shared(ready_bar, 0));
+        } else {
+            tc::named_barrier(bar_id, kGroupThreads);
+            if (leader) issue(l);
+        }
     };
 
     // batched launches: c b1'_g of the tile's controller from global memory (the product the
@@ -580,7 +585,6 @@ __global__ void __launch_bounds__(Form<kPair>::kThreads, 1) sdf_mlp_tc_kernel(St
             }
             tc::fence_proxy_async_smem();
             tc::fence_before_sync();
-            tc::named_barrier(bar_id, kGroupThreads);
             a_tile_written(0);
 
             for (int l = 0; l < 4; ++l) {
@@ -703,7 +707,6 @@ __global__ void __launch_bounds__(Form<kPair>::kThreads, 1) sdf_mlp_tc_kernel(St
                 tc::fence_before_sync();
                 if (l < 3) {
                     tc::fence_proxy_async_smem();
-                    tc::named_barrier(bar_id, kGroupThreads);
                     a_tile_written(l + 1);
                 } else {
                     const float2 sp2 = upk(s2);
