@@ -13,13 +13,22 @@
 // into partial sums of the collision cost (s(p) itself is stored only for
 // diagnostics).
 //
-// CTA = 3 tile groups of 8 warps.  A tile group owns one A tile (smem) and one
-// 128-column FP32 accumulator (TMEM); its warps w and w + 4 share TMEM lane
-// quadrant w % 4 (rows 32 (w % 4) .. + 31) and split the 128 columns into
-// halves.  Once all 256 threads of a group have written its A tile (named
+// Single-CTA form: CTA = 3 tile groups of 8 warps.  A tile group owns one A tile
+// (smem) and one 128-column FP32 accumulator (TMEM); its warps w and w + 4 share
+// TMEM lane quadrant w % 4 (rows 32 (w % 4) .. + 31) and split the 128 columns
+// into halves.  Once all 256 threads of a group have written its A tile (named
 // barrier), the group's leader thread issues that layer's MMAs and commits them
 // to the group's mbarrier, on which the group's warps wait (bounded).  W2..W4
 // (96 KB in BF16/FP16) stay in shared memory for the life of the persistent CTA.
+//
+// CTA-pair form (BF16 / FP16 without positional encoding, the default there): a
+// cluster of two CTAs issues tcgen05.mma.cta_group::2 with M = 256 -- each CTA's
+// own 128-row tile as A, each CTA holding 64 of the 128 rows (N) of every B
+// operand -- so a CTA keeps half of W2..W4 (48 KB) and fits 4 tile groups (1024
+// threads); a work unit is two consecutive tiles, the even CTA's and the odd's.
+// Per layer the odd CTA's warps arrive on the even CTA's a_ready barrier, whose
+// group leader then issues the MMAs and commits them to both CTAs' accumulator
+// barriers (multicast).  Both forms give bit-identical results.
 //
 // Activations are carried in log2 units: with c = beta log2(e) and y = c x,
 //   sp_beta(x) = (ln 2 / beta) h(y),   h(y) = log2(1 + 2^y) = max(y, 0) + log2(1 + 2^-|y|),

@@ -260,12 +260,13 @@ __device__ __forceinline__ uint32_t mapa_shared(uint32_t saddr, uint32_t rank) {
     return r;
 }
 // Arrive on an mbarrier of another CTA of the cluster (default semantics of mbarrier.arrive).
-// Used for the pair MMA's operand hand-off: the arriving CTA's threads have written their half
-// of the A operand and made it visible to the async proxy (fence.proxy.async), and the other
-// CTA issues the MMA that reads it only after this arrival completed the barrier's phase, the
-// same ordering a TMA load's completion gives an MMA.  The release/acquire pair at cluster
-// scope (mbarrier.arrive.release.cluster / try_wait.acquire.cluster) measured 20-25 % slower
-// for the whole SDF kernel, with results bit-identical to this form.
+// Used for the pair MMA's operand hand-off: the arriving warp's threads have written their
+// rows of the A operand in their own CTA's shared memory and fenced them for the async proxy
+// (fence.proxy.async), and the other CTA issues the MMA that reads them only after the
+// arrivals completed the barrier's phase; the reader is the tensor core's async-proxy read,
+// not a thread of the other CTA.  A release/acquire pair at cluster scope
+// (mbarrier.arrive.release.cluster / try_wait.acquire.cluster) measured 20-25 % slower for the
+// whole SDF kernel, with results bit-identical to this form.
 __device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
     asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
