@@ -87,3 +87,18 @@ def test_server_and_other_struct_layouts_match_header(built, tmp_path):
     assert vals == [ctypes.sizeof(binding.MppiServerConfig), binding.MppiServerConfig.batching.offset,
                     binding.MppiServerConfig.sdf_single_cta.offset, ctypes.sizeof(binding.MppiServerStats), binding.MppiServerStats.batches.offset,
                     ctypes.sizeof(binding.MppiTrainConfig), ctypes.sizeof(binding.MppiDepthCamera)]
+
+
+def test_server_config_defaults_and_validation_without_gpu(built):
+    """The server's defaults (FP16, batched, 16 in flight, single-CTA SDF kernels) and the
+    rejection of an out-of-range kernel-form flag, which happens before any device call."""
+    from paper_2603_07199_gb300 import binding
+    cfg = binding.mppi_server_config_default()
+    assert (cfg.sdf_mode, cfg.batching, cfg.max_inflight, cfg.sdf_single_cta, cfg.hbm_budget_bytes) == \
+        (binding.MPPI_SDF_MLP_FP16, 1, 16, 1, 0)
+    for bad in (-1, 2):
+        cfg.sdf_single_cta = bad
+        with pytest.raises(binding.MppiError) as e:
+            binding.mppi_server_create(cfg)
+        assert e.value.code == binding.MPPI_E_INVALID
+        assert "sdf_single_cta" in str(e.value)
