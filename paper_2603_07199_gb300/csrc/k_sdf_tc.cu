@@ -259,10 +259,6 @@ __device__ __forceinline__ float bf16_round(float x) {
     return __uint_as_float(tc::pack_bf16x2(x, 0.f) << 16);
 }
 
-__device__ __forceinline__ int items_of_slot(int slot, int nslots, int n_items) {
-    return slot < n_items ? (n_items - slot + nslots - 1) / nslots : 0;
-}
-
 // 16-bit pattern of x in the operand type of the hidden GEMMs (round to nearest even).
 template <int kFmt>
 __device__ __forceinline__ uint16_t to_operand16(float x) {

@@ -743,7 +743,7 @@ int mppi_step_async(mppi_ctx* c, const float* d_state, const float* d_gate_poses
     // the update kernel stores U*_new as float4: a misaligned buffer is refused before anything is enqueued
     if (reinterpret_cast<uintptr_t>(d_new_controls) % 16 != 0)
         return fail(c, MPPI_E_INVALID, "d_new_controls must be 16-byte aligned");
-    const int K = c->cfg.K, H = c->cfg.H, G = c->n_gates;
+    const int H = c->cfg.H, G = c->n_gates;
     if (d_state)
         CUDA_TRY(c, cudaMemcpyAsync(c->B.state, d_state, state_dim(c->cfg) * sizeof(float), cudaMemcpyDeviceToDevice,
                                     c->stream));
